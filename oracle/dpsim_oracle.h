@@ -1,0 +1,98 @@
+/*
+ * CPU FP64 oracle for the dual-porosity oil-water Newton-step solve.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, sequential restatement of
+ * the method of "Numerical Simulation of Two-phase Flow in Natural Fractured
+ * Reservoirs Using Dual Porosity Method on Parallel Computers" (Shen et al.):
+ * the dual-porosity model (Section 2, Eq. "prob"), the fully implicit
+ * cell-centred discretisation (Section 3), the inexact Newton method
+ * (Algorithm 1), decoupling (Eq. "decoupled-eq") and GMRES with the CPR-FPF
+ * preconditioner (Section 3.2).  Only tests, the smoke check and the timed
+ * CPU baseline of the benchmark may load it.  It shares no code, header or
+ * constant table with the CUDA library.
+ *
+ * Every exported function returns 0 on success, a negative code on failure.
+ */
+#ifndef DPSIM_ORACLE_H
+#define DPSIM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { int32_t nx, ny, nz; double dx, dy, dz, top_depth; } og_grid;
+typedef struct {
+  const double *kf, *km, *phi_f, *phi_m; /* [nL] each, SI */
+  double sigma, c_rock, p_ref;
+} og_rock;
+typedef struct {
+  double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
+} og_fluid;
+typedef struct {
+  int32_t kind, i, j, k_top, k_bot;  /* kind 0: water rate injector, 1: BHP */
+  double target, rw, skin;
+} og_well;
+typedef struct {
+  double newton_tol, newton_atol; int32_t newton_max;
+  int32_t eta_mode;       /* 0 fixed, 1..3 the three forcing-term choices */
+  double eta_fixed, eta_gamma, eta_beta, eta_min, eta_max;
+  int32_t gmres_restart, gmres_maxit;
+  double amg_theta; int32_t amg_coarse_max, amg_max_levels;
+  int32_t precond;        /* 0 none, 1 block ILU(0) only, 2 CPR-FPF */
+  double ds_max;
+} og_options;
+typedef struct {
+  int32_t newton_iters, linear_iters, converged, amg_levels;
+  double res0, res, lin_relres, eta;
+} og_stats;
+
+int  oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
+                   const og_well *w, int32_t nwells, const og_options *o,
+                   void **out);
+void oracle_destroy(void *h);
+int  oracle_sizes(void *h, int32_t *nb, int32_t *nnzb);
+int  oracle_set_state(void *h, const double *p, const double *sw, const double *bhp);
+int  oracle_set_iterate(void *h, const double *p, const double *sw, const double *bhp);
+int  oracle_get_state(void *h, double *p, double *sw, double *bhp);
+int  oracle_assemble(void *h, double dt);
+int  oracle_get_jacobian(void *h, int32_t *rowptr, int32_t *col, double *val, double *res);
+int  oracle_get_norms(void *h, double *out8);
+int  oracle_solve_step(void *h, og_stats *st);
+int  oracle_advance(void *h, double dt, og_stats *st);
+int  oracle_get_update(void *h, double *y);
+int  oracle_get_decoupled(void *h, double *val, double *rhs);
+int  oracle_get_colours(void *h, int32_t *colour);
+int  oracle_amg_level_info(void *h, int32_t level, int32_t *n, int32_t *nnz, int32_t *nagg);
+int  oracle_amg_level_arrays(void *h, int32_t level, int32_t *rowptr, int32_t *col,
+                             double *val, int32_t *agg, int32_t *colour);
+int  oracle_well_index(void *h, double *wi);
+
+/* Component entry points used by the pinning tests. */
+int  oracle_greedy_colour(int32_t n, const int32_t *rowptr, const int32_t *col,
+                          int32_t *colour);
+int  oracle_ilu0_solve(int32_t n, const int32_t *rowptr, const int32_t *col,
+                       const double *val, const int32_t *colour,
+                       const double *b, double *x);
+int  oracle_amg_create(int32_t n, const int32_t *rowptr, const int32_t *col,
+                       const double *val, double theta, int32_t coarse_max,
+                       int32_t max_levels, void **out);
+int  oracle_amg_vcycle(void *amg, const double *b, double *x);
+int  oracle_amg_info(void *amg, int32_t level, int32_t *n, int32_t *nnz, int32_t *nagg);
+int  oracle_amg_arrays(void *amg, int32_t level, int32_t *rowptr, int32_t *col,
+                       double *val, int32_t *agg, int32_t *colour);
+void oracle_amg_destroy(void *amg);
+int  oracle_fgmres_bsr(int32_t n, const int32_t *rowptr, const int32_t *col,
+                       const double *val, const double *b, double *x,
+                       int32_t precond, int32_t restart, int32_t maxit, double tol,
+                       int32_t *iters, double *relres);
+int  oracle_fgmres_amg(int32_t n, const int32_t *rowptr, const int32_t *col,
+                       const double *val, const double *b, double *x,
+                       double theta, int32_t coarse_max, int32_t restart,
+                       int32_t maxit, double tol, int32_t *iters, double *relres);
+uint32_t oracle_hash32(uint32_t i);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
