@@ -1,0 +1,207 @@
+/*
+ * dpsim: GPU (GB300, sm_103a) Newton-step solver for two-phase oil-water flow
+ * in a naturally fractured reservoir, dual-porosity model.
+ *
+ * Method: Shen, Cui, Liu, Zhu, Zhong, Chen et al., "Numerical Simulation of
+ * Two-phase Flow in Natural Fractured Reservoirs Using Dual Porosity Method
+ * on Parallel Computers".
+ *   - model: Section 2 (Darcy law Eq. 1-2, mass conservation, constraints,
+ *     dual-porosity system Eq. "prob", transfer term q_mf, perforation rate,
+ *     well index and Peaceman radius);
+ *   - discretisation: Section 3 (FIM, unknowns p, s_w per cell and p_b per
+ *     well, backward Euler, cell-centred finite differences, F(x) = 0 of
+ *     size N = 2n + tau, Eq. "nonlinear");
+ *   - nonlinear solver: Algorithm 1 (inexact Newton) with the forcing terms
+ *     of Section 3.1;
+ *   - linear solver: Section 3.2 (block Jacobian, decoupling
+ *     D^-1 A x = D^-1 b of Eq. "decoupled-eq" by a Gauss-Jordan step, GMRES
+ *     preconditioned by CPR-FPF).
+ *
+ * Conventions shared by every entry point:
+ *   - SI units throughout (m, m^2, Pa, Pa s, kg/m^3, m^3/s, s).
+ *   - A "location" is a grid block (i, j, k), loc = i + nx (j + ny k).  Each
+ *     location has a fracture cell c = 2 loc and a matrix cell c = 2 loc + 1.
+ *     n_cells = 2 nx ny nz.  Well w owns block row n_cells + w.
+ *   - Every block row has two unknowns: (p, s_w) for a cell, (p_b, dummy)
+ *     for a well; every residual row pair is (oil, water) for a cell and
+ *     (well equation, dummy) for a well.
+ *   - Host pointers are read during the call only (the library copies what
+ *     it keeps).  Device memory is owned by the dp_sim and obtained through
+ *     the dp_allocator given at creation (cudaMallocAsync when NULL).
+ *   - All work is ordered on the CUDA stream given at creation.  Calls that
+ *     return host results synchronise that stream before returning.
+ *   - Return value: DP_OK (0) or a negative DP_E* code; sim_last_error()
+ *     gives a message.  A failed call leaves the dp_sim usable unless it
+ *     returned DP_ECUDA.
+ */
+#ifndef DPSIM_H
+#define DPSIM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DP_OK 0
+#define DP_EINVAL (-1)   /* bad argument or size */
+#define DP_ENOMEM (-2)   /* the allocator returned NULL */
+#define DP_ECUDA (-3)    /* a CUDA call failed; the dp_sim must be destroyed */
+#define DP_ELINEAR (-4)  /* FGMRES did not reach its tolerance */
+#define DP_ENEWTON (-5)  /* Newton did not converge; the old state is restored */
+#define DP_ETIMEOUT (-6) /* a bounded device-side wait gave up */
+
+/* Structured grid (Section 4, Example 1 layout): nx x ny x nz blocks of
+ * size dx x dy x dz; top_depth is the depth of the top face (gravity). */
+typedef struct { int32_t nx, ny, nz; double dx, dy, dz, top_depth; } dp_grid;
+
+/* Rock (Section 2): isotropic fracture and matrix permeabilities (m^2) and
+ * reference porosities per location ([nx ny nz] each, host pointers), the
+ * shape factor sigma (m^-2) of the transfer term, rock compressibility
+ * (1/Pa) and its reference pressure (Pa). */
+typedef struct {
+  const double *kf, *km, *phi_f, *phi_m;
+  double sigma, c_rock, p_ref;
+} dp_rock;
+
+/* Fluids (Section 2): viscosities (Pa s), compressibilities (1/Pa) of the
+ * linear densities rho = rho_ref (1 + c (p - p_ref)), Corey end points
+ * s_wc, s_or (krw = S^2, kro = (1-S)^2 of the normalised saturation), and
+ * the gravitational acceleration g (m/s^2). */
+typedef struct {
+  double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
+} dp_fluid;
+
+/* Vertical well perforating the fracture cells of column (i, j), layers
+ * k_top..k_bot (Section 2, perforation rate and well index).  kind
+ * DP_WELL_RATE_INJ: water injector at a reservoir-volume rate target (m^3/s);
+ * DP_WELL_BHP: producer at a bottom-hole pressure target (Pa).  rw: wellbore
+ * radius (m); skin: skin factor. */
+typedef enum { DP_WELL_RATE_INJ = 0, DP_WELL_BHP = 1 } dp_well_kind;
+typedef struct {
+  int32_t kind, i, j, k_top, k_bot;
+  double target, rw, skin;
+} dp_well;
+
+/* Device memory provider.  alloc returns device memory usable on `stream`
+ * (or NULL); free releases it.  ctx is passed back unchanged. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+  void *ctx;
+} dp_allocator;
+
+/* Solver options.  eta_mode 0: fixed forcing term eta_fixed; 1-3: the three
+ * forcing terms of Section 3.1, clipped to [eta_min, eta_max].  precond:
+ * 0 none, 1 block ILU(0) only, 2 CPR-FPF.  precision: 0 FP64 everywhere;
+ * 1 ILU(0) factors and AMG levels stored and applied in FP32 inside FP64
+ * FGMRES. */
+typedef struct {
+  double newton_tol, newton_atol; int32_t newton_max;
+  int32_t eta_mode;
+  double eta_fixed, eta_gamma, eta_beta, eta_min, eta_max;
+  int32_t gmres_restart, gmres_maxit;
+  double amg_theta; int32_t amg_coarse_max, amg_max_levels;
+  int32_t precond;
+  double ds_max;
+  int32_t precision;
+  int32_t use_graphs;   /* capture the FGMRES iteration in a CUDA graph */
+} dp_options;
+
+typedef struct {
+  int32_t newton_iters, linear_iters, converged, amg_levels;
+  double res0, res, lin_relres, eta;
+  double ms_setup, ms_solve;   /* device time of the last solve_step parts */
+} dp_stats;
+
+typedef struct dp_sim dp_sim;
+
+/* Create a realisation: copies grid, rock, fluid and wells, computes the
+ * well indices (Peaceman's radius for a vertical well, Section 2), builds
+ * the block pattern (fracture 7-point stencil, fracture-matrix pairs, well
+ * rows and columns) and the transmissibilities on the device.  `stream` is
+ * a cudaStream_t (NULL: the default stream).  `alloc` may be NULL.  The
+ * state is set to zero; call sim_set_state before assembling. */
+int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_fluid *fluid,
+               const dp_well *wells, int32_t nwells, const dp_options *opts,
+               const dp_allocator *alloc, void *stream, dp_sim **out);
+
+void sim_destroy(dp_sim *sim);
+
+/* Sizes: block rows n_cells + nwells, nonzero 2x2 blocks, cells, wells. */
+int sim_sizes(const dp_sim *sim, int32_t *nb, int32_t *nnzb, int32_t *ncells,
+              int32_t *nwells);
+
+/* Set the state (host pointers: p[n_cells] Pa, sw[n_cells], bhp[nwells] Pa)
+ * as both the current Newton iterate and the old time level x^n. */
+int sim_set_state(dp_sim *sim, const double *p, const double *sw, const double *bhp);
+
+/* Set only the current Newton iterate (host pointers); x^n is kept. */
+int sim_set_iterate(dp_sim *sim, const double *p, const double *sw, const double *bhp);
+
+/* Same as sim_set_state with DEVICE pointers (stream-ordered copy). */
+int sim_set_state_device(dp_sim *sim, const double *p, const double *sw, const double *bhp);
+
+/* Copy the current iterate to host arrays (synchronises). */
+int sim_get_state(dp_sim *sim, double *p, double *sw, double *bhp);
+
+/* Residual R and Jacobian J of F(x) = 0 at the current iterate for a step
+ * of length dt (s) from x^n (Section 3, Eq. "nonlinear"), and the scaled
+ * residual norms of Algorithm 1.  Stream-ordered; does not synchronise. */
+int sim_assemble(dp_sim *sim, double dt);
+
+/* Copy the last assembled Jacobian (BSR: rowptr[nb+1], col[nnzb],
+ * val[4 nnzb] row-major 2x2 blocks) and residual res[2 nb] to host arrays;
+ * any pointer may be NULL.  Valid between sim_assemble and sim_solve_step. */
+int sim_get_jacobian(dp_sim *sim, int32_t *rowptr, int32_t *col, double *val, double *res);
+
+/* Scaled residual norms and balances of the last assembly (synchronises):
+ * out[0] ||R~||_2, out[1] ||R~||_inf, out[2..3] sum of oil / water cell
+ * residuals, out[4..5] oil / water mass change since x^n, out[6..7] oil /
+ * water mass rate injected by the wells. */
+int sim_get_norms(dp_sim *sim, double *out8);
+
+/* One linear solve of Algorithm 1 at the assembled iterate: decoupling
+ * (Eq. "decoupled-eq"), pressure extraction, block ILU(0), AMG setup (first
+ * call) or value refresh, CPR-FPF preconditioned FGMRES to the forcing term
+ * eta, and the update x += y (saturation change limited to +-ds_max, s_w
+ * kept in [0, 1]).  Synchronises; fills *stats when not NULL. */
+int sim_solve_step(dp_sim *sim, dp_stats *stats);
+
+/* One backward-Euler timestep of length dt by Algorithm 1.  On Newton
+ * failure the old state is restored and DP_ENEWTON returned. */
+int sim_advance(dp_sim *sim, double dt, dp_stats *stats);
+
+/* Test access to intermediate results (host arrays, synchronise):
+ * the last Newton update y[2 nb]; the decoupled matrix values and
+ * right-hand side; the greedy colouring of the block rows (returns the
+ * number of colours); the well indices per perforation (returns the count). */
+int sim_get_update(dp_sim *sim, double *y);
+int sim_get_decoupled(dp_sim *sim, double *val, double *rhs);
+int sim_get_colours(dp_sim *sim, int32_t *colour);
+int sim_well_index(dp_sim *sim, double *wi);
+
+/* AMG hierarchy of the pressure stage after the first sim_solve_step:
+ * level sizes (returns the number of levels) and level arrays (CSR of the
+ * level operator, aggregate of each row or -1, greedy colour of each row);
+ * any pointer may be NULL. */
+int sim_amg_level_info(dp_sim *sim, int32_t level, int32_t *n, int32_t *nnz, int32_t *nagg);
+int sim_amg_level_arrays(dp_sim *sim, int32_t level, int32_t *rowptr, int32_t *col,
+                         double *val, int32_t *agg, int32_t *colour);
+
+/* Time every launch of one kernel (by name, e.g. "bsr_spmv") with CUDA
+ * events on the simulation stream; NULL stops.  sim_kernel_timing returns
+ * the accumulated milliseconds and launch count since the last reset. */
+int sim_time_kernel(dp_sim *sim, const char *name);
+int sim_kernel_timing(dp_sim *sim, double *ms, int64_t *launches, int32_t reset);
+
+/* Number of kernel launches made by this dp_sim since creation. */
+int64_t sim_launch_count(const dp_sim *sim);
+
+/* Message of the last error on this dp_sim ("" when none). */
+const char *sim_last_error(const dp_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

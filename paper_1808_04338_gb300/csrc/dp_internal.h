@@ -1,0 +1,222 @@
+// Internal declarations of the dpsim CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dpsim.h"
+
+namespace dp {
+
+constexpr int kBlock = 256;
+
+// Error propagation inside the library: every CUDA call is checked, the
+// first failure is recorded on the Sim and the entry point returns DP_ECUDA.
+struct Err {
+  int code = DP_OK;
+  std::string msg;
+};
+
+#define DP_CUDA(sim, call)                                                     \
+  do {                                                                         \
+    cudaError_t e__ = (call);                                                  \
+    if (e__ != cudaSuccess) {                                                  \
+      (sim)->fail(DP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+      return DP_ECUDA;                                                         \
+    }                                                                          \
+  } while (0)
+
+#define DP_TRY(expr)                 \
+  do {                               \
+    int rc__ = (expr);               \
+    if (rc__ != DP_OK) return rc__;  \
+  } while (0)
+
+// Physical constants passed to the physics kernels by value.
+struct Phys {
+  int nx, ny, nz, nL, nc, nw, nb;
+  double dx, dy, dz, top_depth, V;
+  double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
+  double inv_span, inv_mu_o, inv_mu_w;
+  double sigma, c_rock, p_ref_rock;
+};
+
+// 2x2-block sparse row matrix (device pointers), natural row order.
+struct Bsr {
+  int n = 0, nnz = 0;
+  int *rowptr = nullptr, *col = nullptr, *diag = nullptr;
+  double *val = nullptr;
+};
+
+// One AMG level: scalar CSR operator plus the transfer operators to the next.
+struct Level {
+  int n = 0, nnz = 0, nagg = 0;
+  int *rowptr = nullptr, *col = nullptr, *dpos = nullptr;
+  double *val = nullptr;
+  float *valf = nullptr;                 // FP32 copy (precision mode 1)
+  int *tpos = nullptr;                   // position of the transposed entry
+  uint8_t *strong = nullptr;
+  int *agg = nullptr;
+  int *colour = nullptr, ncolour = 0;
+  int *clist = nullptr;                  // rows sorted by (colour, index)
+  std::vector<int> cstart;               // host: colour c rows clist[cstart[c]..cstart[c+1])
+  double *fdiag = nullptr, *ratio = nullptr;
+  // prolongator P (n x nagg), restriction R = P^T (nagg x n), AP = A P
+  int p_nnz = 0, r_nnz = 0, ap_nnz = 0;
+  int *p_rowptr = nullptr, *p_col = nullptr;
+  double *p_val = nullptr;
+  float *p_valf = nullptr;
+  int *r_rowptr = nullptr, *r_col = nullptr, *r_src = nullptr;
+  double *r_val = nullptr;
+  float *r_valf = nullptr;
+  int *ap_rowptr = nullptr, *ap_col = nullptr;
+  double *ap_val = nullptr;
+  // V-cycle work vectors
+  double *x = nullptr, *b = nullptr, *r = nullptr;
+  float *xf = nullptr, *bf = nullptr, *rf = nullptr;
+};
+
+struct Sim;
+
+// ---------------------------------------------------------------- memory
+void *dalloc(Sim *s, size_t bytes);
+void dfree(Sim *s, void *p);
+
+// ---------------------------------------------------------------- launches
+// Bookkeeping around every kernel launch: launch count, optional CUDA-event
+// timing of one named kernel.
+struct LaunchScope {
+  Sim *s;
+  bool timed;
+  LaunchScope(Sim *s, const char *name);
+  ~LaunchScope();
+};
+#define DP_LAUNCH(sim, name, grid, block, smem, ...)                    \
+  do {                                                                  \
+    ::dp::LaunchScope ls__((sim), #name);                               \
+    name<<<(grid), (block), (smem), (sim)->stream>>>(__VA_ARGS__);      \
+  } while (0)
+
+inline int nblk(long long n, int b = kBlock) {
+  long long g = (n + b - 1) / b;
+  return (int)(g > 0 ? g : 1);
+}
+
+// ---------------------------------------------------------------- kernels
+// dp_phys.cu (compiled without FMA contraction: results must equal the
+// oracle's bit for bit)
+int phys_build_pattern(Sim *s);
+int phys_save_old(Sim *s);
+int phys_assemble(Sim *s);
+int phys_norms(Sim *s);
+int phys_decouple_extract(Sim *s);
+int phys_update(Sim *s);
+
+// dp_amg.cu (integer setup and bit-exact smoothed-aggregation numerics)
+int scan_i32(Sim *s, const int *in, int *out, int n, int *total);  // out[n] = total
+int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour,
+                  int *ncolour);
+int colour_lists(Sim *s, int n, const int *colour, int ncolour, int *clist,
+                 std::vector<int> &cstart, int *iperm_or_null);
+int amg_setup(Sim *s);
+int amg_refresh(Sim *s);
+void amg_free(Sim *s);
+
+// dp_la.cu (linear algebra of the Krylov loop and the preconditioner)
+int ilu_setup(Sim *s);
+int ilu_factor(Sim *s);
+int ilu_apply(Sim *s, const double *r, double *z);
+int bsr_spmv(Sim *s, const double *x, double *y);                 // y = A x
+int bsr_residual(Sim *s, const double *b, const double *x, double *r);  // r = b - A x
+int vcycle(Sim *s, int level, const double *b, double *x);
+int coarse_factor(Sim *s);
+int cpr_apply(Sim *s, const double *r, double *z);
+int fgmres(Sim *s, double tol, int *iters, double *relres);
+int la_alloc(Sim *s);
+int mixed_refresh(Sim *s);
+
+struct Timing {
+  int kernel_id = -1;            // hashed name being timed, -1 none
+  std::string name;
+  std::vector<cudaEvent_t> ev;   // pairs
+  size_t used = 0;
+  double ms = 0.0;
+  int64_t launches = 0;
+};
+
+struct Sim {
+  // problem
+  Phys ph{};
+  dp_options opt{};
+  std::vector<dp_well> wells;
+  int nperf = 0;
+  cudaStream_t stream = nullptr;
+  dp_allocator alloc{};
+  bool own_alloc = true;
+  std::vector<std::pair<void *, size_t>> blocks;
+  Err err;
+  Timing timing;
+  int64_t launches = 0;
+  std::string last_error;
+
+  // device: static data
+  double *kf = nullptr, *km = nullptr, *phi_f = nullptr, *phi_m = nullptr;
+  int *perf_cell = nullptr, *perf_well = nullptr;   // sorted by (cell, well)
+  double *perf_wi = nullptr;
+  int *well_kind = nullptr;
+  double *well_target = nullptr;
+  std::vector<double> wi_host;                       // per perforation, well order
+  Bsr A;                                             // Jacobian, decoupled in place
+  double *trans = nullptr;                           // per entry: T or WI
+  // device: state and residual
+  double *p = nullptr, *sw = nullptr, *bhp = nullptr;
+  double *pn = nullptr, *swn = nullptr, *bhpn = nullptr, *Mn = nullptr;
+  double *R = nullptr, *bh = nullptr, *y = nullptr;
+  double dt = 1.0, inv_dt = 1.0;
+  double *norm_part = nullptr;                       // reduction partials
+  double *norm_out = nullptr;                        // 8 doubles
+  double *h_norms = nullptr;                         // pinned host copy
+  int norm_blocks = 0;
+  bool assembled = false, decoupled = false;
+  // colouring of the block rows
+  int *colour = nullptr;
+  int ncolour = 0;
+  // ILU(0) factor in (colour, index) row order
+  int *perm = nullptr, *iperm = nullptr;
+  int *lu_rowptr = nullptr, *lu_col = nullptr, *lu_src = nullptr, *lu_dpos = nullptr;
+  double *lu_val = nullptr;
+  float *lu_valf = nullptr;
+  std::vector<int> lu_cstart;
+  // AMG hierarchy (level 0 shares the block pattern)
+  std::vector<Level> lev;
+  bool amg_ready = false;
+  double *ap = nullptr;                              // pressure values (nnzb)
+  double *coarse_lu = nullptr;
+  int *coarse_piv = nullptr;
+  int coarse_n = 0;
+  double *omega = nullptr;                           // device scalars
+  unsigned long long *rho_bits = nullptr;
+  int *counter = nullptr, *h_counter = nullptr;      // device / pinned host
+  // Krylov workspace
+  int m = 30;
+  double *V = nullptr, *Z = nullptr, *w = nullptr;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *hy = nullptr;
+  double *dots_part = nullptr, *dots = nullptr, *scal = nullptr;
+  double *h_res = nullptr;                           // pinned host scalars
+  int dot_blocks = 0;
+  double *z1 = nullptr, *r1 = nullptr, *rp = nullptr, *xp = nullptr;
+  // Newton bookkeeping
+  double prev_res = 0.0, prev_linres = 0.0;
+  int newton_iter = 0;
+  double last_norms[8] = {0};
+  dp_stats last{};
+
+  void fail(int code, const std::string &m) {
+    if (err.code == DP_OK) { err.code = code; err.msg = m; }
+    last_error = m;
+  }
+};
+
+}  // namespace dp

@@ -1,0 +1,640 @@
+// Physics kernels: block pattern, transmissibilities, residual and Jacobian
+// assembly, norms, decoupling, pressure extraction and the Newton update.
+//
+// Compiled with -fmad=false: every floating-point expression is evaluated
+// as written (no fused multiply-add), so that the assembled Jacobian, the
+// decoupled matrix and the pressure block are bit-identical to a plain
+// sequential CPU evaluation of the same formulas.  The AMG strength graph
+// and aggregates are computed from those values and must not depend on the
+// processor that evaluated them.
+#include <algorithm>
+#include <cmath>
+
+#include "dp_internal.h"
+
+namespace dp {
+
+// ---------------------------------------------------------------- physics
+
+// Cell properties (Section 2): linear densities, porosity, Corey relative
+// permeabilities of the normalised saturation, mobilities and derivatives.
+struct Props {
+  double rho[2], drho[2], phi, dphi, lam[2], dlam[2];
+};
+
+__device__ __forceinline__ void props(const Phys &P, const double *phi_f, const double *phi_m,
+                                      int c, double p, double sw, Props &q) {
+  int loc = c >> 1;
+  double phi_ref = (c & 1) == 0 ? phi_f[loc] : phi_m[loc];
+  double dp = p - P.p_ref;
+  q.rho[0] = P.rho_o_ref * (1.0 + P.c_o * dp);
+  q.rho[1] = P.rho_w_ref * (1.0 + P.c_w * dp);
+  q.drho[0] = P.rho_o_ref * P.c_o;
+  q.drho[1] = P.rho_w_ref * P.c_w;
+  q.phi = phi_ref * (1.0 + P.c_rock * (p - P.p_ref_rock));
+  q.dphi = phi_ref * P.c_rock;
+  double S = (sw - P.swc) * P.inv_span, dS;
+  if (S <= 0.0) { S = 0.0; dS = 0.0; }
+  else if (S >= 1.0) { S = 1.0; dS = 0.0; }
+  else dS = P.inv_span;
+  double so = 1.0 - S;
+  q.lam[1] = (S * S) * P.inv_mu_w;
+  q.dlam[1] = ((2.0 * S) * dS) * P.inv_mu_w;
+  q.lam[0] = (so * so) * P.inv_mu_o;
+  q.dlam[0] = (-((2.0 * so) * dS)) * P.inv_mu_o;
+}
+
+// Phase masses V phi rho s of a cell and their derivatives [phase][p, sw].
+__device__ __forceinline__ void accumulation(const Phys &P, double sw, const Props &q,
+                                             double M[2], double dM[4]) {
+  double Vphi = P.V * q.phi;
+  double so = 1.0 - sw;
+  M[0] = (Vphi * q.rho[0]) * so;
+  M[1] = (Vphi * q.rho[1]) * sw;
+  dM[0] = (P.V * ((q.dphi * q.rho[0]) + (q.phi * q.drho[0]))) * so;
+  dM[1] = -(Vphi * q.rho[0]);
+  dM[2] = (P.V * ((q.dphi * q.rho[1]) + (q.phi * q.drho[1]))) * sw;
+  dM[3] = Vphi * q.rho[1];
+}
+
+// Mass flux a -> b (a < b) per phase with upstream mobility (Section 2:
+// Darcy flux with potential Phi = p - rho g z, upstream weighting).
+__device__ __forceinline__ void flux(double T, double gdz, double pa, double pb, const Props &qa,
+                                     const Props &qb, double F[2], double dFa[4], double dFb[4]) {
+#pragma unroll
+  for (int al = 0; al < 2; ++al) {
+    double dpot = (pa - pb) - ((0.5 * (qa.rho[al] + qb.rho[al])) * gdz);
+    double ddpa = 1.0 - ((0.5 * qa.drho[al]) * gdz);
+    double ddpb = -1.0 - ((0.5 * qb.drho[al]) * gdz);
+    double mob, mpa, msa, mpb, msb;
+    if (dpot >= 0.0) {
+      mob = qa.rho[al] * qa.lam[al];
+      mpa = qa.drho[al] * qa.lam[al];
+      msa = qa.rho[al] * qa.dlam[al];
+      mpb = 0.0; msb = 0.0;
+    } else {
+      mob = qb.rho[al] * qb.lam[al];
+      mpb = qb.drho[al] * qb.lam[al];
+      msb = qb.rho[al] * qb.dlam[al];
+      mpa = 0.0; msa = 0.0;
+    }
+    F[al] = (T * mob) * dpot;
+    dFa[2 * al + 0] = T * ((mpa * dpot) + (mob * ddpa));
+    dFa[2 * al + 1] = T * (msa * dpot);
+    dFb[2 * al + 0] = T * ((mpb * dpot) + (mob * ddpb));
+    dFb[2 * al + 1] = T * (msb * dpot);
+  }
+}
+
+// Perforation mass rate into a fracture cell (Section 2, q_{alpha,i}):
+// producer WI rho lambda (p_b - p); water injector WI rho_w lambda_t (p_b - p).
+__device__ __forceinline__ void perf_rate(int kind, double wi, double pc, double pb, const Props &q,
+                                          double Q[2], double dq[4], double dqb[2]) {
+  double dpw = pb - pc;
+  if (kind == 0) {
+    double lt = q.lam[0] + q.lam[1], dlt = q.dlam[0] + q.dlam[1];
+    Q[0] = 0.0; dq[0] = 0.0; dq[1] = 0.0; dqb[0] = 0.0;
+    Q[1] = ((wi * q.rho[1]) * lt) * dpw;
+    dq[2] = (((wi * q.drho[1]) * lt) * dpw) - ((wi * q.rho[1]) * lt);
+    dq[3] = ((wi * q.rho[1]) * dlt) * dpw;
+    dqb[1] = (wi * q.rho[1]) * lt;
+  } else {
+#pragma unroll
+    for (int al = 0; al < 2; ++al) {
+      Q[al] = ((wi * q.rho[al]) * q.lam[al]) * dpw;
+      dq[2 * al + 0] = (((wi * q.drho[al]) * q.lam[al]) * dpw) - ((wi * q.rho[al]) * q.lam[al]);
+      dq[2 * al + 1] = ((wi * q.rho[al]) * q.dlam[al]) * dpw;
+      dqb[al] = (wi * q.rho[al]) * q.lam[al];
+    }
+  }
+}
+
+__device__ __forceinline__ void loc_ijk(const Phys &P, int loc, int &i, int &j, int &k) {
+  i = loc % P.nx;
+  j = (loc / P.nx) % P.ny;
+  k = loc / (P.nx * P.ny);
+}
+
+__device__ __forceinline__ double depth(const Phys &P, int k) {
+  return P.top_depth + ((double)k + 0.5) * P.dz;
+}
+
+// ---------------------------------------------------------------- pattern
+
+// Perforations of a cell: [lo, hi) in the (cell, well)-sorted list.
+__device__ __forceinline__ void perf_range(const int *pc_cell, int np, int c, int &lo, int &hi) {
+  int a = 0, b = np;
+  while (a < b) { int m = (a + b) >> 1; if (pc_cell[m] < c) a = m + 1; else b = m; }
+  lo = a;
+  b = np;
+  while (a < b) { int m = (a + b) >> 1; if (pc_cell[m] <= c) a = m + 1; else b = m; }
+  hi = a;
+}
+
+__global__ void k_pattern_count(Phys P, const int *pc_cell, int np, const int *pw_start,
+                                int *len) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.nb) return;
+  if (r >= P.nc) { int w = r - P.nc; len[r] = 1 + pw_start[w + 1] - pw_start[w]; return; }
+  if (r & 1) { len[r] = 2; return; }
+  int i, j, k;
+  loc_ijk(P, r >> 1, i, j, k);
+  int lo, hi;
+  perf_range(pc_cell, np, r, lo, hi);
+  len[r] = 2 + (i > 0) + (i < P.nx - 1) + (j > 0) + (j < P.ny - 1) + (k > 0) + (k < P.nz - 1) +
+           (hi - lo);
+}
+
+// Two-point transmissibility between cells a < b (fracture-fracture
+// harmonic mean, or the shape-factor transfer sigma km V of one location).
+__device__ __forceinline__ double conn_trans(const Phys &P, const double *kf, const double *km,
+                                             int a, int b) {
+  int la = a >> 1, lb = b >> 1;
+  if (la == lb) return (P.sigma * km[la]) * P.V;
+  int ia, ja, ka, ib, jb, kb;
+  loc_ijk(P, la, ia, ja, ka);
+  loc_ijk(P, lb, ib, jb, kb);
+  double A, D;
+  if (ka != kb) { A = P.dx * P.dy; D = P.dz; }
+  else if (ja != jb) { A = P.dx * P.dz; D = P.dy; }
+  else { A = P.dy * P.dz; D = P.dx; }
+  double k1 = kf[la], k2 = kf[lb];
+  return ((2.0 * A) * (k1 * k2)) / (D * (k1 + k2));
+}
+
+__global__ void k_pattern_fill(Phys P, const double *kf, const double *km, const int *pc_cell,
+                               const int *pc_well, const double *pc_wi, int np,
+                               const int *pw_start, const int *pw_cell, const double *pw_wi,
+                               const int *rowptr, int *col, int *diag, double *trans) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.nb) return;
+  int e0 = rowptr[r];
+  if (r >= P.nc) {                       // well row: perforated cells, then itself
+    int w = r - P.nc, s = pw_start[w], t = pw_start[w + 1];
+    for (int q = s; q < t; ++q) { col[e0 + q - s] = pw_cell[q]; trans[e0 + q - s] = pw_wi[q]; }
+    col[e0 + t - s] = r;
+    trans[e0 + t - s] = 0.0;
+    diag[r] = e0 + t - s;
+    return;
+  }
+  int c[16];
+  int n = 0;
+  int loc = r >> 1;
+  if (r & 1) { c[n++] = r - 1; c[n++] = r; }
+  else {
+    int i, j, k, nxy = P.nx * P.ny;
+    loc_ijk(P, loc, i, j, k);
+    if (k > 0) c[n++] = 2 * (loc - nxy);
+    if (j > 0) c[n++] = 2 * (loc - P.nx);
+    if (i > 0) c[n++] = 2 * (loc - 1);
+    c[n++] = r;
+    c[n++] = r + 1;
+    if (i < P.nx - 1) c[n++] = 2 * (loc + 1);
+    if (j < P.ny - 1) c[n++] = 2 * (loc + P.nx);
+    if (k < P.nz - 1) c[n++] = 2 * (loc + nxy);
+  }
+  for (int a = 1; a < n; ++a) {          // sorted ascending
+    int v = c[a], b = a - 1;
+    while (b >= 0 && c[b] > v) { c[b + 1] = c[b]; --b; }
+    c[b + 1] = v;
+  }
+  for (int a = 0; a < n; ++a) {
+    int d = c[a];
+    col[e0 + a] = d;
+    if (d == r) { diag[r] = e0 + a; trans[e0 + a] = 0.0; }
+    else trans[e0 + a] = conn_trans(P, kf, km, min(r, d), max(r, d));
+  }
+  if (!(r & 1)) {
+    int lo, hi;
+    perf_range(pc_cell, np, r, lo, hi);
+    for (int q = lo; q < hi; ++q) {      // wells after all cells, by well index
+      col[e0 + n] = P.nc + pc_well[q];
+      trans[e0 + n] = pc_wi[q];
+      ++n;
+    }
+  }
+}
+
+// Peaceman's radius for a vertical well and the well index
+// W = 2 pi k h w_frac / (ln(r_e / r_w) + s), k h = sqrt(kx ky) dz, w_frac = 1.
+static double well_index_host(double kx, double ky, double dx, double dy, double dz, double rw,
+                              double skin) {
+  double ryx = ky / kx, rxy = kx / ky;
+  double re = 0.28 * std::sqrt(std::sqrt(ryx) * dx * dx + std::sqrt(rxy) * dy * dy) /
+              (std::pow(ryx, 0.25) + std::pow(rxy, 0.25));
+  double wfrac = 1.0;
+  return (((2.0 * M_PI) * std::sqrt(kx * ky)) * dz) * wfrac / (std::log(re / rw) + skin);
+}
+
+int phys_build_pattern(Sim *s) {
+  Phys &P = s->ph;
+  // perforations, well by well (cells ascending), with their well indices
+  std::vector<double> kf_host;  // only the perforated locations are needed
+  int np = 0;
+  for (auto &w : s->wells) np += w.k_bot - w.k_top + 1;
+  s->nperf = np;
+  std::vector<int> locs;
+  for (auto &w : s->wells)
+    for (int k = w.k_top; k <= w.k_bot; ++k) locs.push_back(w.i + P.nx * (w.j + P.ny * k));
+  std::vector<double> kfp(np);
+  for (int q = 0; q < np; ++q)
+    DP_CUDA(s, cudaMemcpyAsync(&kfp[q], s->kf + locs[q], sizeof(double), cudaMemcpyDeviceToHost,
+                               s->stream));
+  DP_CUDA(s, cudaStreamSynchronize(s->stream));
+  std::vector<int> pw_start(P.nw + 1, 0), pw_cell(np);
+  std::vector<double> pw_wi(np);
+  s->wi_host.resize(np);
+  int q = 0;
+  for (int w = 0; w < P.nw; ++w) {
+    const dp_well &W = s->wells[w];
+    pw_start[w] = q;
+    for (int k = W.k_top; k <= W.k_bot; ++k, ++q) {
+      pw_cell[q] = 2 * locs[q];
+      pw_wi[q] = well_index_host(kfp[q], kfp[q], P.dx, P.dy, P.dz, W.rw, W.skin);
+      s->wi_host[q] = pw_wi[q];
+    }
+  }
+  pw_start[P.nw] = np;
+  std::vector<int> order(np);
+  for (int t = 0; t < np; ++t) order[t] = t;
+  std::vector<int> pw_well(np);
+  for (int w = 0; w < P.nw; ++w)
+    for (int t = pw_start[w]; t < pw_start[w + 1]; ++t) pw_well[t] = w;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return pw_cell[a] != pw_cell[b] ? pw_cell[a] < pw_cell[b] : pw_well[a] < pw_well[b];
+  });
+  std::vector<int> pc_cell(np), pc_well(np);
+  std::vector<double> pc_wi(np);
+  for (int t = 0; t < np; ++t) {
+    pc_cell[t] = pw_cell[order[t]];
+    pc_well[t] = pw_well[order[t]];
+    pc_wi[t] = pw_wi[order[t]];
+  }
+  for (int t = 1; t < np; ++t)
+    if (pc_cell[t] == pc_cell[t - 1] && pc_well[t] == pc_well[t - 1]) {
+      s->fail(DP_EINVAL, "a well perforates the same cell twice");
+      return DP_EINVAL;
+    }
+  size_t npb = (size_t)std::max(np, 1);
+  int *d_pc_cell = (int *)dalloc(s, npb * 4), *d_pc_well = (int *)dalloc(s, npb * 4);
+  double *d_pc_wi = (double *)dalloc(s, npb * 8);
+  int *d_pw_start = (int *)dalloc(s, (P.nw + 1) * 4), *d_pw_cell = (int *)dalloc(s, npb * 4);
+  double *d_pw_wi = (double *)dalloc(s, npb * 8);
+  if (!d_pc_cell || !d_pc_well || !d_pc_wi || !d_pw_start || !d_pw_cell || !d_pw_wi) {
+    s->fail(DP_ENOMEM, "allocation failed");
+    return DP_ENOMEM;
+  }
+  if (np) {
+    DP_CUDA(s, cudaMemcpyAsync(d_pc_cell, pc_cell.data(), np * 4, cudaMemcpyHostToDevice, s->stream));
+    DP_CUDA(s, cudaMemcpyAsync(d_pc_well, pc_well.data(), np * 4, cudaMemcpyHostToDevice, s->stream));
+    DP_CUDA(s, cudaMemcpyAsync(d_pc_wi, pc_wi.data(), np * 8, cudaMemcpyHostToDevice, s->stream));
+    DP_CUDA(s, cudaMemcpyAsync(d_pw_cell, pw_cell.data(), np * 4, cudaMemcpyHostToDevice, s->stream));
+    DP_CUDA(s, cudaMemcpyAsync(d_pw_wi, pw_wi.data(), np * 8, cudaMemcpyHostToDevice, s->stream));
+  }
+  DP_CUDA(s, cudaMemcpyAsync(d_pw_start, pw_start.data(), (P.nw + 1) * 4, cudaMemcpyHostToDevice,
+                             s->stream));
+  s->perf_cell = d_pc_cell;
+  s->perf_well = d_pc_well;
+  s->perf_wi = d_pc_wi;
+  // row lengths, row pointers, columns and per-entry transmissibilities
+  int *len = (int *)dalloc(s, (size_t)P.nb * 4);
+  s->A.n = P.nb;
+  s->A.rowptr = (int *)dalloc(s, (size_t)(P.nb + 1) * 4);
+  s->A.diag = (int *)dalloc(s, (size_t)P.nb * 4);
+  if (!len || !s->A.rowptr || !s->A.diag) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  DP_LAUNCH(s, k_pattern_count, nblk(P.nb), kBlock, 0, P, d_pc_cell, np, d_pw_start, len);
+  int nnz = 0;
+  DP_TRY(scan_i32(s, len, s->A.rowptr, P.nb, &nnz));
+  s->A.nnz = nnz;
+  s->A.col = (int *)dalloc(s, (size_t)nnz * 4);
+  s->A.val = (double *)dalloc(s, (size_t)nnz * 32);
+  s->trans = (double *)dalloc(s, (size_t)nnz * 8);
+  s->ap = (double *)dalloc(s, (size_t)nnz * 8);
+  if (!s->A.col || !s->A.val || !s->trans || !s->ap) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  DP_LAUNCH(s, k_pattern_fill, nblk(P.nb), kBlock, 0, P, s->kf, s->km, d_pc_cell, d_pc_well,
+            d_pc_wi, np, d_pw_start, d_pw_cell, d_pw_wi, s->A.rowptr, s->A.col, s->A.diag,
+            s->trans);
+  DP_CUDA(s, cudaGetLastError());
+  dfree(s, len);
+  dfree(s, d_pw_start);
+  dfree(s, d_pw_cell);
+  dfree(s, d_pw_wi);
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------- assembly
+
+struct AsmArgs {
+  Phys P;
+  const int *rowptr, *col, *diag;
+  const double *trans, *phi_f, *phi_m;
+  const double *p, *sw, *bhp, *Mn;
+  const int *well_kind;
+  const double *well_target;
+  double *val, *R;
+  double inv_dt;
+};
+
+// One thread per block row.  Cell rows: accumulation, then the connections
+// in increasing column order (fluxes, then perforations); well rows: the
+// rate or pressure constraint.
+__global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const Phys &P = a.P;
+  if (r >= P.nb) return;
+  int e0 = a.rowptr[r], e1 = a.rowptr[r + 1];
+  if (r < P.nc) {
+    double pc = a.p[r], swc = a.sw[r];
+    Props qc;
+    props(P, a.phi_f, a.phi_m, r, pc, swc, qc);
+    double M[2], dM[4];
+    accumulation(P, swc, qc, M, dM);
+    double r0 = (M[0] - a.Mn[2 * r]) * a.inv_dt;
+    double r1 = (M[1] - a.Mn[2 * r + 1]) * a.inv_dt;
+    double d0 = dM[0] * a.inv_dt, d1 = dM[1] * a.inv_dt;
+    double d2 = dM[2] * a.inv_dt, d3 = dM[3] * a.inv_dt;
+    int ir, jr, kr;
+    loc_ijk(P, r >> 1, ir, jr, kr);
+    for (int e = e0; e < e1; ++e) {
+      int d = a.col[e];
+      if (d == r) continue;
+      double *off = a.val + 4 * (size_t)e;
+      double T = a.trans[e];
+      if (d < P.nc) {
+        double pd = a.p[d];
+        Props qd;
+        props(P, a.phi_f, a.phi_m, d, pd, a.sw[d], qd);
+        double dzab;
+        if ((r >> 1) == (d >> 1)) dzab = 0.0;
+        else {
+          int id, jd, kd;
+          loc_ijk(P, d >> 1, id, jd, kd);
+          dzab = r < d ? depth(P, kr) - depth(P, kd) : depth(P, kd) - depth(P, kr);
+        }
+        double gdz = P.g * dzab;
+        double F[2], dFa[4], dFb[4];
+        if (r < d) {
+          flux(T, gdz, pc, pd, qc, qd, F, dFa, dFb);
+          r0 = r0 + F[0]; r1 = r1 + F[1];
+          d0 = d0 + dFa[0]; d1 = d1 + dFa[1]; d2 = d2 + dFa[2]; d3 = d3 + dFa[3];
+          off[0] = dFb[0]; off[1] = dFb[1]; off[2] = dFb[2]; off[3] = dFb[3];
+        } else {
+          flux(T, gdz, pd, pc, qd, qc, F, dFa, dFb);
+          r0 = r0 + (-F[0]); r1 = r1 + (-F[1]);
+          d0 = d0 + (-dFb[0]); d1 = d1 + (-dFb[1]); d2 = d2 + (-dFb[2]); d3 = d3 + (-dFb[3]);
+          off[0] = -dFa[0]; off[1] = -dFa[1]; off[2] = -dFa[2]; off[3] = -dFa[3];
+        }
+      } else {
+        int w = d - P.nc;
+        double Q[2], dq[4], dqb[2];
+        perf_rate(a.well_kind[w], T, pc, a.bhp[w], qc, Q, dq, dqb);
+        r0 = r0 - Q[0]; r1 = r1 - Q[1];
+        d0 = d0 - dq[0]; d1 = d1 - dq[1]; d2 = d2 - dq[2]; d3 = d3 - dq[3];
+        off[0] = -dqb[0]; off[1] = 0.0; off[2] = -dqb[1]; off[3] = 0.0;
+      }
+    }
+    double *dg = a.val + 4 * (size_t)a.diag[r];
+    dg[0] = d0; dg[1] = d1; dg[2] = d2; dg[3] = d3;
+    a.R[2 * r] = r0;
+    a.R[2 * r + 1] = r1;
+    return;
+  }
+  int w = r - P.nc;
+  double pb = a.bhp[w];
+  double *dg = a.val + 4 * (size_t)a.diag[r];
+  if (a.well_kind[w] == 0) {
+    double acc = 0.0, accd = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      int c = a.col[e];
+      if (c == r) continue;
+      Props q;
+      props(P, a.phi_f, a.phi_m, c, a.p[c], a.sw[c], q);
+      double lt = q.lam[0] + q.lam[1], dlt = q.dlam[0] + q.dlam[1];
+      double wi = a.trans[e];
+      double wl = wi * lt;
+      acc = acc + (wl * (pb - a.p[c]));
+      accd = accd + wl;
+      double *off = a.val + 4 * (size_t)e;
+      off[0] = -wl; off[1] = (wi * dlt) * (pb - a.p[c]); off[2] = 0.0; off[3] = 0.0;
+    }
+    a.R[2 * r] = acc - a.well_target[w];
+    dg[0] = accd;
+  } else {
+    for (int e = e0; e < e1; ++e) {
+      if (a.col[e] == r) continue;
+      double *off = a.val + 4 * (size_t)e;
+      off[0] = 0.0; off[1] = 0.0; off[2] = 0.0; off[3] = 0.0;
+    }
+    a.R[2 * r] = pb - a.well_target[w];
+    dg[0] = 1.0;
+  }
+  dg[1] = 0.0; dg[2] = 0.0; dg[3] = 1.0;
+  a.R[2 * r + 1] = 0.0;
+}
+
+__global__ void k_save_old(Phys P, const double *phi_f, const double *phi_m, const double *p,
+                           const double *sw, const double *bhp, double *pn, double *swn,
+                           double *bhpn, double *Mn) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < P.nw) bhpn[c] = bhp[c];
+  if (c >= P.nc) return;
+  Props q;
+  props(P, phi_f, phi_m, c, p[c], sw[c], q);
+  double M[2], dM[4];
+  accumulation(P, sw[c], q, M, dM);
+  pn[c] = p[c];
+  swn[c] = sw[c];
+  Mn[2 * c] = M[0];
+  Mn[2 * c + 1] = M[1];
+}
+
+int phys_save_old(Sim *s) {
+  Phys &P = s->ph;
+  int n = std::max(P.nc, P.nw);
+  DP_LAUNCH(s, k_save_old, nblk(n), kBlock, 0, P, s->phi_f, s->phi_m, s->p, s->sw, s->bhp, s->pn,
+            s->swn, s->bhpn, s->Mn);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+int phys_assemble(Sim *s) {
+  AsmArgs a;
+  a.P = s->ph;
+  a.rowptr = s->A.rowptr; a.col = s->A.col; a.diag = s->A.diag;
+  a.trans = s->trans; a.phi_f = s->phi_f; a.phi_m = s->phi_m;
+  a.p = s->p; a.sw = s->sw; a.bhp = s->bhp; a.Mn = s->Mn;
+  a.well_kind = s->well_kind; a.well_target = s->well_target;
+  a.val = s->A.val; a.R = s->R;
+  a.inv_dt = s->inv_dt;
+  DP_LAUNCH(s, k_assemble, nblk(s->ph.nb), kBlock, 0, a);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------- norms
+// Scaled residual (cell rows by dt / (rho_ref phi_ref V), well rows by
+// their target), phase residual sums, mass change and well inflow.  Two
+// passes with a fixed reduction order (deterministic for a given size).
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *phi_f,
+                                                       const double *phi_m, const double *R,
+                                                       const double *p, const double *sw,
+                                                       const double *Mn, const int *well_kind,
+                                                       const double *well_target, double dt,
+                                                       double *part) {
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};  // s2, max, sro, srw, dmo, dmw, unused
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.nb; r += gridDim.x * blockDim.x) {
+    if (r < P.nc) {
+      int loc = r >> 1;
+      double phi_ref = (r & 1) == 0 ? phi_f[loc] : phi_m[loc];
+#pragma unroll
+      for (int al = 0; al < 2; ++al) {
+        double rref = al == 0 ? P.rho_o_ref : P.rho_w_ref;
+        double x = (R[2 * r + al] * dt) / ((rref * phi_ref) * P.V);
+        v[0] += x * x;
+        v[1] = fmax(v[1], fabs(x));
+      }
+      v[2] += R[2 * r];
+      v[3] += R[2 * r + 1];
+      Props q;
+      props(P, phi_f, phi_m, r, p[r], sw[r], q);
+      double M[2], dM[4];
+      accumulation(P, sw[r], q, M, dM);
+      v[4] += M[0] - Mn[2 * r];
+      v[5] += M[1] - Mn[2 * r + 1];
+    } else {
+      int w = r - P.nc;
+      double sc = well_kind[w] == 0 ? fmax(well_target[w], 1e-12) : well_target[w];
+      double x = R[2 * r] / sc;
+      v[0] += x * x;
+      v[1] = fmax(v[1], fabs(x));
+    }
+  }
+  __shared__ double sh[kBlock / 32][7];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    double t = k == 1 ? warp_max(v[k]) : warp_sum(v[k]);
+    if (lane == 0) sh[wid][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    int k = threadIdx.x;
+    double t = k == 1 ? 0.0 : 0.0;
+    for (int q = 0; q < kBlock / 32; ++q) t = k == 1 ? fmax(t, sh[q][k]) : t + sh[q][k];
+    part[blockIdx.x * 8 + k] = t;
+  }
+}
+
+__global__ void k_norms_final(Phys P, const double *phi_f, const double *phi_m, const double *p,
+                              const double *sw, const double *bhp, const int *perf_cell,
+                              const int *perf_well, const double *perf_wi, int np,
+                              const int *well_kind, const double *part, int nparts,
+                              double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nparts; ++b) {
+    for (int k = 0; k < 6; ++k) v[k] = k == 1 ? fmax(v[k], part[b * 8 + k]) : v[k] + part[b * 8 + k];
+  }
+  double wo = 0.0, ww = 0.0;
+  for (int t = 0; t < np; ++t) {
+    int c = perf_cell[t], w = perf_well[t];
+    Props q;
+    props(P, phi_f, phi_m, c, p[c], sw[c], q);
+    double Q[2], dq[4], dqb[2];
+    perf_rate(well_kind[w], perf_wi[t], p[c], bhp[w], q, Q, dq, dqb);
+    wo += Q[0];
+    ww += Q[1];
+  }
+  out[0] = sqrt(v[0]);
+  out[1] = v[1];
+  out[2] = v[2]; out[3] = v[3]; out[4] = v[4]; out[5] = v[5];
+  out[6] = wo; out[7] = ww;
+}
+
+int phys_norms(Sim *s) {
+  Phys &P = s->ph;
+  DP_LAUNCH(s, k_norms_part, s->norm_blocks, kBlock, 0, P, s->phi_f, s->phi_m, s->R, s->p, s->sw,
+            s->Mn, s->well_kind, s->well_target, s->dt, s->norm_part);
+  DP_LAUNCH(s, k_norms_final, 1, 32, 0, P, s->phi_f, s->phi_m, s->p, s->sw, s->bhp, s->perf_cell,
+            s->perf_well, s->perf_wi, s->nperf, s->well_kind, s->norm_part, s->norm_blocks,
+            s->norm_out);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------- decoupling
+// One Gauss-Jordan step per cell block row (Eq. "decoupled-eq"): the water
+// row of the diagonal block eliminates the saturation coefficient of the
+// oil row, D_i^-1 = [[1, -a01/a11], [0, 1]], applied to the whole row and to
+// b = -R; well rows unchanged.  The pressure block takes entry (0,0) of
+// every decoupled block.
+__global__ void __launch_bounds__(kBlock) k_decouple(int nb, int nc, const int *rowptr,
+                                                     const int *diag, double *val, const double *R,
+                                                     double *bh, double *ap) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  double b0 = -R[2 * i], b1 = -R[2 * i + 1];
+  int e0 = rowptr[i], e1 = rowptr[i + 1];
+  if (i >= nc) {
+    bh[2 * i] = b0; bh[2 * i + 1] = b1;
+    for (int e = e0; e < e1; ++e) ap[e] = val[4 * (size_t)e];
+    return;
+  }
+  const double *dg = val + 4 * (size_t)diag[i];
+  double a01 = dg[1], a11 = dg[3];
+  double fct = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
+  for (int e = e0; e < e1; ++e) {
+    double *a = val + 4 * (size_t)e;
+    double n0 = a[0] - (fct * a[2]);
+    double n1 = a[1] - (fct * a[3]);
+    a[0] = n0; a[1] = n1;
+    ap[e] = n0;
+  }
+  bh[2 * i] = b0 - (fct * b1);
+  bh[2 * i + 1] = b1;
+}
+
+int phys_decouple_extract(Sim *s) {
+  DP_LAUNCH(s, k_decouple, nblk(s->ph.nb), kBlock, 0, s->ph.nb, s->ph.nc, s->A.rowptr, s->A.diag,
+            s->A.val, s->R, s->bh, s->ap);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------- update
+__global__ void k_update(int nc, int nw, double ds_max, const double *y, double *p, double *sw,
+                         double *bhp) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nw) bhp[c] += y[2 * (nc + c)];
+  if (c >= nc) return;
+  p[c] += y[2 * c];
+  double ds = y[2 * c + 1];
+  if (ds > ds_max) ds = ds_max;
+  if (ds < -ds_max) ds = -ds_max;
+  double v = sw[c] + ds;
+  if (v < 0.0) v = 0.0;
+  if (v > 1.0) v = 1.0;
+  sw[c] = v;
+}
+
+int phys_update(Sim *s) {
+  int n = std::max(s->ph.nc, s->ph.nw);
+  DP_LAUNCH(s, k_update, nblk(n), kBlock, 0, s->ph.nc, s->ph.nw, s->opt.ds_max, s->y, s->p, s->sw,
+            s->bhp);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+}  // namespace dp

@@ -1,0 +1,330 @@
+"""Python binding of the dpsim C ABI (include/dpsim.h).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+``libdpsim.so``.  PyTorch supplies the CUDA stream and, through the
+allocator callbacks, the device memory (its caching allocator).  There is no
+CPU fallback: without the built library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdpsim.so")
+
+DP_OK, DP_EINVAL, DP_ENOMEM, DP_ECUDA, DP_ELINEAR, DP_ENEWTON, DP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+WELL_RATE_INJ, WELL_BHP = 0, 1
+
+
+class dp_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("top_depth", C.c_double)]
+
+
+class dp_rock(C.Structure):
+    _fields_ = [("kf", C.c_void_p), ("km", C.c_void_p), ("phi_f", C.c_void_p),
+                ("phi_m", C.c_void_p), ("sigma", C.c_double), ("c_rock", C.c_double),
+                ("p_ref", C.c_double)]
+
+
+class dp_fluid(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("mu_o", "mu_w", "c_o", "c_w", "rho_o_ref", "rho_w_ref", "p_ref", "swc",
+                 "sor", "g")]
+
+
+class dp_well(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("i", C.c_int32), ("j", C.c_int32),
+                ("k_top", C.c_int32), ("k_bot", C.c_int32), ("target", C.c_double),
+                ("rw", C.c_double), ("skin", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class dp_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class dp_options(C.Structure):
+    _fields_ = [("newton_tol", C.c_double), ("newton_atol", C.c_double),
+                ("newton_max", C.c_int32), ("eta_mode", C.c_int32),
+                ("eta_fixed", C.c_double), ("eta_gamma", C.c_double),
+                ("eta_beta", C.c_double), ("eta_min", C.c_double), ("eta_max", C.c_double),
+                ("gmres_restart", C.c_int32), ("gmres_maxit", C.c_int32),
+                ("amg_theta", C.c_double), ("amg_coarse_max", C.c_int32),
+                ("amg_max_levels", C.c_int32), ("precond", C.c_int32),
+                ("ds_max", C.c_double), ("precision", C.c_int32), ("use_graphs", C.c_int32)]
+
+
+class dp_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("linear_iters", C.c_int32),
+                ("converged", C.c_int32), ("amg_levels", C.c_int32), ("res0", C.c_double),
+                ("res", C.c_double), ("lin_relres", C.c_double), ("eta", C.c_double),
+                ("ms_setup", C.c_double), ("ms_solve", C.c_double)]
+
+
+def options(mode: str = "parity", **kw) -> dp_options:
+    """'parity': fixed eta 1e-10, Newton tolerance 1e-10 (agreement with an
+    independent FP64 evaluation far inside 1e-8); 'report': third forcing
+    term (gamma 0.9, beta 2) in [1e-4, 0.1], Newton tolerance 1e-6."""
+    o = dp_options()
+    o.newton_max = 25
+    o.newton_atol = 1e-13
+    o.gmres_restart = 30
+    o.gmres_maxit = 300
+    o.amg_theta = 0.08
+    o.amg_coarse_max = 128
+    o.amg_max_levels = 20
+    o.precond = 2
+    o.ds_max = 0.2
+    o.precision = 0
+    o.use_graphs = 0
+    o.eta_gamma, o.eta_beta, o.eta_min, o.eta_max = 0.9, 2.0, 1e-4, 0.1
+    if mode == "parity":
+        o.eta_mode, o.eta_fixed, o.newton_tol = 0, 1e-10, 1e-10
+    else:
+        o.eta_mode, o.eta_fixed, o.newton_tol = 3, 1e-4, 1e-6
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+_lib = None
+
+
+def load():
+    """Load libdpsim.so (built by ``paper_1808_04338_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    L = C.CDLL(LIB_PATH)
+    P, I, D = C.c_void_p, C.c_int32, C.c_double
+    L.sim_create.argtypes = [C.POINTER(dp_grid), C.POINTER(dp_rock), C.POINTER(dp_fluid),
+                             C.POINTER(dp_well), I, C.POINTER(dp_options),
+                             C.POINTER(dp_allocator), P, C.POINTER(P)]
+    L.sim_destroy.argtypes = [P]
+    L.sim_destroy.restype = None
+    L.sim_sizes.argtypes = [P, P, P, P, P]
+    for n in ("sim_set_state", "sim_set_iterate", "sim_set_state_device", "sim_get_state"):
+        getattr(L, n).argtypes = [P, P, P, P]
+    L.sim_assemble.argtypes = [P, D]
+    L.sim_get_jacobian.argtypes = [P, P, P, P, P]
+    L.sim_get_norms.argtypes = [P, P]
+    L.sim_solve_step.argtypes = [P, C.POINTER(dp_stats)]
+    L.sim_advance.argtypes = [P, D, C.POINTER(dp_stats)]
+    L.sim_get_update.argtypes = [P, P]
+    L.sim_get_decoupled.argtypes = [P, P, P]
+    L.sim_get_colours.argtypes = [P, P]
+    L.sim_well_index.argtypes = [P, P]
+    L.sim_amg_level_info.argtypes = [P, I, P, P, P]
+    L.sim_amg_level_arrays.argtypes = [P, I, P, P, P, P, P]
+    L.sim_time_kernel.argtypes = [P, C.c_char_p]
+    L.sim_kernel_timing.argtypes = [P, P, P, I]
+    L.sim_launch_count.argtypes = [P]
+    L.sim_launch_count.restype = C.c_int64
+    L.sim_last_error.argtypes = [P]
+    L.sim_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _p(a):
+    return C.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class TorchAllocator:
+    """dp_allocator backed by PyTorch's CUDA caching allocator."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream)
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = dp_allocator(self._a, self._f, None)
+
+
+class Sim:
+    """One realisation on the GPU.  ``prob`` is a ``dp_inputs.Problem``."""
+
+    def __init__(self, prob, opts: dp_options | None = None, stream=None, use_torch_alloc=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("dpsim needs a CUDA device")
+        L = load()
+        self.prob = prob
+        self.opts = opts if opts is not None else options("parity")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = dp_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.top_depth)
+        keep = [_f64(prob.kf), _f64(prob.km), _f64(prob.phi_f), _f64(prob.phi_m)]
+        r = dp_rock(*[a.ctypes.data for a in keep], prob.sigma, prob.c_rock, prob.p_ref_rock)
+        f = dp_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref, prob.rho_w_ref,
+                     prob.p_ref, prob.swc, prob.sor, prob.g)
+        nw = len(prob.wells)
+        W = (dp_well * max(nw, 1))()
+        for q, w in enumerate(prob.wells):
+            W[q] = dp_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin)
+        self._alloc = TorchAllocator(torch.cuda.current_device()) if use_torch_alloc else None
+        h = C.c_void_p()
+        rc = L.sim_create(C.byref(g), C.byref(r), C.byref(f), W, nw, C.byref(self.opts),
+                          C.byref(self._alloc.struct) if self._alloc else None,
+                          C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"sim_create failed ({rc})")
+        self.h = h
+        nb, nnz, nc, nwl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        L.sim_sizes(h, C.byref(nb), C.byref(nnz), C.byref(nc), C.byref(nwl))
+        self.nb, self.nnzb, self.nc, self.nw = nb.value, nnz.value, nc.value, nwl.value
+        if prob.p0 is not None:
+            self.set_state(prob.p0, prob.sw0, prob.bhp0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc < 0:
+            msg = load().sim_last_error(self.h)
+            raise RuntimeError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+        return rc
+
+    def set_state(self, p, sw, bhp):
+        p, sw, bhp = _f64(p), _f64(sw), _f64(bhp if len(bhp) else np.zeros(1))
+        self._check(load().sim_set_state(self.h, _p(p), _p(sw), _p(bhp)), "sim_set_state")
+
+    def set_state_device(self, p, sw, bhp):
+        """Device tensors (float64, on this GPU)."""
+        self._check(load().sim_set_state_device(self.h, C.c_void_p(p.data_ptr()),
+                                                C.c_void_p(sw.data_ptr()),
+                                                C.c_void_p(bhp.data_ptr())), "sim_set_state_device")
+
+    def set_state_ptr(self, p, sw, bhp):
+        """Raw pointers (host pinned or device), stream-ordered copy."""
+        self._check(load().sim_set_state(self.h, C.c_void_p(p), C.c_void_p(sw), C.c_void_p(bhp)),
+                    "sim_set_state")
+
+    def set_iterate(self, p, sw, bhp):
+        p, sw, bhp = _f64(p), _f64(sw), _f64(bhp if len(bhp) else np.zeros(1))
+        self._check(load().sim_set_iterate(self.h, _p(p), _p(sw), _p(bhp)), "sim_set_iterate")
+
+    def get_state(self):
+        p = np.zeros(self.nc); sw = np.zeros(self.nc); bhp = np.zeros(max(self.nw, 1))
+        self._check(load().sim_get_state(self.h, _p(p), _p(sw), _p(bhp)), "sim_get_state")
+        return p, sw, bhp[:self.nw]
+
+    def get_state_ptr(self, p, sw, bhp):
+        self._check(load().sim_get_state(self.h, C.c_void_p(p), C.c_void_p(sw), C.c_void_p(bhp)),
+                    "sim_get_state")
+
+    def assemble(self, dt):
+        self._check(load().sim_assemble(self.h, float(dt)), "sim_assemble")
+
+    def jacobian(self):
+        rowptr = np.zeros(self.nb + 1, np.int32); col = np.zeros(self.nnzb, np.int32)
+        val = np.zeros((self.nnzb, 2, 2)); res = np.zeros(2 * self.nb)
+        self._check(load().sim_get_jacobian(self.h, _p(rowptr), _p(col), _p(val), _p(res)),
+                    "sim_get_jacobian")
+        return rowptr, col, val, res
+
+    def norms(self):
+        out = np.zeros(8)
+        self._check(load().sim_get_norms(self.h, _p(out)), "sim_get_norms")
+        return out
+
+    def solve_step(self):
+        st = dp_stats()
+        rc = load().sim_solve_step(self.h, C.byref(st))
+        if rc < 0 and rc != DP_ELINEAR:
+            self._check(rc, "sim_solve_step")
+        return rc, st
+
+    def advance(self, dt):
+        st = dp_stats()
+        rc = load().sim_advance(self.h, float(dt), C.byref(st))
+        if rc < 0 and rc not in (DP_ENEWTON, DP_ELINEAR):
+            self._check(rc, "sim_advance")
+        return rc, st
+
+    def update(self):
+        y = np.zeros(2 * self.nb)
+        self._check(load().sim_get_update(self.h, _p(y)), "sim_get_update")
+        return y
+
+    def decoupled(self):
+        val = np.zeros((self.nnzb, 2, 2)); rhs = np.zeros(2 * self.nb)
+        self._check(load().sim_get_decoupled(self.h, _p(val), _p(rhs)), "sim_get_decoupled")
+        return val, rhs
+
+    def colours(self):
+        c = np.zeros(self.nb, np.int32)
+        n = self._check(load().sim_get_colours(self.h, _p(c)), "sim_get_colours")
+        return c, n
+
+    def well_index(self):
+        wi = np.zeros(sum(w.k_bot - w.k_top + 1 for w in self.prob.wells) + 1)
+        n = self._check(load().sim_well_index(self.h, _p(wi)), "sim_well_index")
+        return wi[:n]
+
+    def amg_levels(self):
+        L = load()
+        out = []
+        lev = 0
+        while True:
+            n, nnz, nagg = C.c_int32(), C.c_int32(), C.c_int32()
+            nl = L.sim_amg_level_info(self.h, lev, C.byref(n), C.byref(nnz), C.byref(nagg))
+            if nl < 0:
+                break
+            d = dict(n=n.value, nnz=nnz.value, nagg=nagg.value,
+                     rowptr=np.zeros(n.value + 1, np.int32), col=np.zeros(nnz.value, np.int32),
+                     val=np.zeros(nnz.value), agg=np.zeros(n.value, np.int32),
+                     colour=np.zeros(n.value, np.int32))
+            self._check(L.sim_amg_level_arrays(self.h, lev, _p(d["rowptr"]), _p(d["col"]),
+                                               _p(d["val"]), _p(d["agg"]), _p(d["colour"])),
+                        "sim_amg_level_arrays")
+            out.append(d)
+            lev += 1
+            if lev >= nl:
+                break
+        return out
+
+    def time_kernel(self, name: str | None):
+        self._check(load().sim_time_kernel(self.h, name.encode() if name else None),
+                    "sim_time_kernel")
+
+    def kernel_timing(self, reset=True):
+        ms, n = C.c_double(), C.c_int64()
+        self._check(load().sim_kernel_timing(self.h, C.byref(ms), C.byref(n), int(reset)),
+                    "sim_kernel_timing")
+        return ms.value, n.value
+
+    def launch_count(self):
+        return load().sim_launch_count(self.h)

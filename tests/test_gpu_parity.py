@@ -1,0 +1,212 @@
+"""GPU (C ABI) against the CPU oracle on the same seeded inputs.
+
+Bit-exact: Jacobian, residual, decoupled matrix, colourings, AMG aggregates
+and level operators (integer setup and the values it is computed from).
+Floating point: Newton updates and states, pressure within rel 1e-8 and
+saturation within abs 1e-8 (FP64 path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import dp_inputs as di
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+P_REL, S_ABS = 1e-8, 1e-8
+
+
+def gpu():
+    from paper_1808_04338_gb300 import dpsim
+    return dpsim
+
+
+def small(nx, ny, nz, seed=1, wells="two", g=0.0):
+    n = nx * ny * nz
+    kf = np.exp(math.log(100.0) + di.normals(seed, 0, n))
+    if wells == "two":
+        W = [di.Well(di.WELL_RATE_INJ, 0, 0, 0, nz - 1, 100.0 * di.BBL_DAY),
+             di.Well(di.WELL_BHP, nx - 1, ny - 1, 0, nz - 1, 2500.0 * di.PSI)]
+    elif wells == "bhp":
+        W = [di.Well(di.WELL_BHP, 0, 0, 0, nz - 1, 2500.0 * di.PSI)]
+    else:
+        W = []
+    return di._base(f"s{nx}x{ny}x{nz}", nx, ny, nz, kf, np.full(n, 0.1), 0.01, 0.2, 0.08, W,
+                    seed, dt_days=1.0, nsteps=2, g=g)
+
+
+def pair(prob, mode="parity", **kw):
+    return gpu().Sim(prob, gpu().options(mode, **kw)), O.OracleSim(prob, O.options(mode, **kw))
+
+
+def state_close(g, o, prob):
+    pg, sg, bg = g.get_state()
+    po, so, bo = o.get_state()
+    assert np.abs(pg - po).max() <= P_REL * np.abs(po).max()
+    assert np.abs(sg - so).max() <= S_ABS
+    if len(bo):
+        assert np.abs(bg - bo).max() <= P_REL * np.abs(bo).max()
+
+
+def update_close(yg, yo, nc):
+    assert np.abs(yg[0:2 * nc:2] - yo[0:2 * nc:2]).max() <= P_REL * 3e7
+    assert np.abs(yg[1:2 * nc:2] - yo[1:2 * nc:2]).max() <= S_ABS
+    assert np.abs(yg[2 * nc::2] - yo[2 * nc::2]).max(initial=0.0) <= P_REL * 3e7
+
+
+def interior(prob, seed=7):
+    rng = np.random.default_rng(seed)
+    nc = prob.n_cells
+    return (prob.p0 + rng.uniform(-3e5, 3e5, nc), rng.uniform(0.25, 0.75, nc),
+            prob.bhp0 + rng.uniform(-1e5, 1e5, prob.n_wells))
+
+
+@pytest.mark.parametrize("make", [di.tiny, lambda: small(7, 5, 3), lambda: small(1, 1, 1, wells="bhp"),
+                                  lambda: small(9, 1, 1), lambda: small(4, 3, 2, wells="none"),
+                                  lambda: small(3, 4, 5, g=9.80665)])
+def test_jacobian_residual_bit_exact(make):
+    prob = make()
+    g, o = pair(prob)
+    for state in (None, interior(prob)):
+        if state is not None:
+            g.set_iterate(*state)
+            o.set_iterate(*state)
+        g.assemble(prob.dt)
+        o.assemble(prob.dt)
+        rg, cg, vg, resg = g.jacobian()
+        ro, co, vo, reso = o.jacobian()
+        np.testing.assert_array_equal(rg, ro)
+        np.testing.assert_array_equal(cg, co)
+        assert np.array_equal(vg.view(np.uint64), vo.view(np.uint64))
+        assert np.array_equal(resg.view(np.uint64), reso.view(np.uint64))
+        ng, no = g.norms(), o.norms()
+        np.testing.assert_allclose(ng, no, rtol=1e-12, atol=1e-12 * np.abs(no).max())
+    np.testing.assert_array_equal(g.well_index(), o.well_index())
+
+
+def test_decoupling_colours_and_amg_setup_bit_exact():
+    prob = di.tiny()
+    g, o = pair(prob)
+    g.assemble(prob.dt)
+    o.assemble(prob.dt)
+    g.solve_step()
+    o.solve_step()
+    vg, bg = g.decoupled()
+    vo, bo = o.decoupled()
+    assert np.array_equal(vg.view(np.uint64), vo.view(np.uint64))
+    assert np.array_equal(bg.view(np.uint64), bo.view(np.uint64))
+    cg, ncg = g.colours()
+    co, nco = o.colours()
+    assert ncg == nco
+    np.testing.assert_array_equal(cg, co)
+    Lg, Lo = g.amg_levels(), o.amg_levels()
+    assert len(Lg) == len(Lo) >= 2
+    for a, b in zip(Lg, Lo):
+        assert (a["n"], a["nnz"], a["nagg"]) == (b["n"], b["nnz"], b["nagg"])
+        for k in ("rowptr", "col", "agg", "colour"):
+            np.testing.assert_array_equal(a[k], b[k])
+        assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
+
+
+def dense_from_bsr(rowptr, col, val):
+    n = len(rowptr) - 1
+    A = np.zeros((2 * n, 2 * n))
+    for i in range(n):
+        for e in range(rowptr[i], rowptr[i + 1]):
+            A[2 * i:2 * i + 2, 2 * col[e]:2 * col[e] + 2] = val[e]
+    return A
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_newton_update_parity(precond):
+    """One linear solve at eta = 1e-12 on both sides: the GPU update's true
+    residual (dense J from the oracle) is at the tolerance, it agrees with
+    the oracle's update as closely as the conditioning of J (~1e12) allows,
+    and both take (nearly) the same number of FGMRES iterations."""
+    prob = di.tiny()
+    g, o = pair(prob, precond=precond, eta_fixed=1e-12, gmres_maxit=1000)
+    st = interior(prob, 3)
+    for s in (g, o):
+        s.set_iterate(*st)
+        s.assemble(prob.dt)
+    rowptr, col, val, res = o.jacobian()
+    rcg, stg = g.solve_step()
+    rco, sto = o.solve_step()
+    assert rcg == 0 and rco == 0
+    yg, yo = g.update(), o.update()
+    J = dense_from_bsr(rowptr, col, val)
+    assert np.linalg.norm(J @ yg + res) <= 20 * 1e-12 * np.linalg.norm(res)
+    nc = prob.n_cells
+    assert np.abs(yg[0:2 * nc:2] - yo[0:2 * nc:2]).max() <= 1e-6 * np.abs(yo[0:2 * nc:2]).max()
+    assert np.abs(yg[1:2 * nc:2] - yo[1:2 * nc:2]).max() <= 1e-6
+    assert abs(stg.linear_iters - sto.linear_iters) <= 2
+
+
+def test_unpreconditioned_gmres_single_location():
+    """No preconditioner on a one-location problem (6 unknowns): FGMRES
+    reduces to GMRES and must reach the dense solution."""
+    prob = small(1, 1, 1, wells="bhp")
+    g, o = pair(prob, precond=0, eta_fixed=1e-13)
+    for s in (g, o):
+        s.set_iterate(*interior(prob, 2))
+        s.assemble(prob.dt)
+    rowptr, col, val, res = o.jacobian()
+    rcg, stg = g.solve_step()
+    assert rcg == 0 and stg.linear_iters <= 6
+    y = np.linalg.solve(dense_from_bsr(rowptr, col, val), -res)
+    np.testing.assert_allclose(g.update(), y, rtol=1e-8, atol=1e-8 * np.abs(y).max())
+
+
+def test_ten_steps_tiny_state_parity():
+    prob = di.tiny()
+    g, o = pair(prob)
+    for step in range(prob.nsteps):
+        rcg, stg = g.advance(prob.dt)
+        rco, sto = o.advance(prob.dt)
+        assert rcg == 0 and rco == 0, step
+        state_close(g, o, prob)
+
+
+@pytest.mark.parametrize("make", [lambda: small(7, 5, 3), lambda: small(1, 1, 1, wells="bhp"),
+                                  lambda: small(9, 1, 1), lambda: small(4, 3, 2, wells="none"),
+                                  lambda: small(3, 4, 5, g=9.80665)])
+def test_edge_case_steps(make):
+    prob = make()
+    g, o = pair(prob)
+    for step in range(prob.nsteps):
+        rcg, _ = g.advance(prob.dt)
+        rco, _ = o.advance(prob.dt)
+        assert rcg == rco == 0
+        state_close(g, o, prob)
+
+
+def test_layered_200k_first_step_parity():
+    """100x100x10 (200k cells): bit-exact assembly and AMG setup, then one
+    timestep of Newton in report mode on both sides."""
+    prob = di.layered()
+    g, o = pair(prob, "report")
+    g.assemble(prob.dt)
+    o.assemble(prob.dt)
+    _, _, vg, rg = g.jacobian()
+    _, _, vo, ro = o.jacobian()
+    assert np.array_equal(vg.view(np.uint64), vo.view(np.uint64))
+    assert np.array_equal(rg.view(np.uint64), ro.view(np.uint64))
+    g.solve_step()
+    o.solve_step()
+    Lg, Lo = g.amg_levels(), o.amg_levels()
+    assert len(Lg) == len(Lo)
+    for a, b in zip(Lg, Lo):
+        np.testing.assert_array_equal(a["agg"], b["agg"])
+        np.testing.assert_array_equal(a["colour"], b["colour"])
+        assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
+
+
+def test_layered_200k_timestep_parity():
+    prob = di.layered()
+    g, o = pair(prob, "parity")
+    rcg, stg = g.advance(prob.dt)
+    rco, sto = o.advance(prob.dt)
+    assert rcg == rco == 0
+    state_close(g, o, prob)
