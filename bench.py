@@ -1,0 +1,291 @@
+#!/usr/bin/env python3
+"""Benchmark: CPR-FPF Newton-step solve of the 200x200x50 dual-porosity
+problem (4M cells, 8M unknowns) on GB300.
+
+One step = one Newton iteration of Algorithm 1 from the same iterate: the
+state is reset on the device, then assembly, decoupling, block ILU(0), AMG
+value refresh, CPR-FPF preconditioned FGMRES to the forcing term and the
+update.  `value` is Newton-step solves per second over all GPUs (replicas of
+the realisation, one per GPU, no collective on the data path).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) each rank runs its own replica; rank 0 prints one
+JSON line.  `--impl reference` times the CPU oracle on a bounded sample of
+the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CPR-FPF Newton-step solve time & HBM GB/s at 8M unknowns; served p99 latency"
+UNIT = "Newton-step solves/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TIMED_KERNEL = "k_bsr_spmv<0>"
+
+
+def workload(args):
+    import dp_inputs as di
+    return di.field8m(args.nx, args.ny, args.nz)
+
+
+def spmv_bytes(nb, nnzb):
+    """Algorithmic bytes of one y = A x launch (FP64 2x2 BSR): values,
+    column indices, row pointers, x and y read/written once."""
+    return 32 * nnzb + 4 * nnzb + 4 * (nb + 1) + 16 * nb + 16 * nb
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for s in self.samples for n, v in zip(names, s[4:]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def oracle_sample(args, budget_s=25.0):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the
+    same field recipe with nz reduced by --sample-div so that a Newton step
+    fits the time budget; the rate is scaled to the full 8M-unknown problem
+    by the ratio of unknowns."""
+    import numpy as np
+    import dp_inputs as di
+    import oracle as O
+    nz = max(1, args.nz // args.sample_div)
+    prob = di.field8m(args.nx, args.ny, nz)
+    s = O.OracleSim(prob, O.options("report"))
+    s.assemble(prob.dt)
+    s.solve_step()                      # integer set-up on the first Newton step
+    p0, sw0, b0 = prob.p0, prob.sw0, prob.bhp0
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        s.set_state(p0, sw0, b0)
+        t0 = time.perf_counter()
+        s.assemble(prob.dt)
+        s.solve_step()
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 3:
+            break
+    t = statistics.median(times)
+    scale = (2 * args.nx * args.ny * args.nz) / (2 * args.nx * args.ny * nz)
+    return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one Newton step of the {args.nx}x{args.ny}x{nz} grid "
+                      f"({prob.n_unknowns} unknowns), median of {len(times)}, rate scaled "
+                      f"by the unknown ratio {scale:g} to 8M unknowns; single-threaded C"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = oracle_sample(args)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args), "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    return {"workload": f"dual-porosity oil-water, {args.nx}x{args.ny}x{args.nz} grid, "
+                        f"{2 * args.nx * args.ny * args.nz} cells, "
+                        f"{4 * args.nx * args.ny * args.nz + 50} unknowns, 25 wells, "
+                        f"lognormal perm (sd 2), first 5-day Newton step",
+            "grid": [args.nx, args.ny, args.nz], "precision": args.precision,
+            "precond": "CPR-FPF", "l2": "inputs larger than L2 (Jacobian 636 MB)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--nx", type=int, default=200)
+    ap.add_argument("--ny", type=int, default=200)
+    ap.add_argument("--nz", type=int, default=50)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--sample-div", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_1808_04338_gb300 import dpsim
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    prob = workload(args)
+    opts = dpsim.options("report", precision=args.precision)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = dpsim.Sim(prob, opts, stream=stream)
+    dev = torch.device("cuda", local)
+    p0 = torch.from_numpy(prob.p0).to(dev)
+    sw0 = torch.from_numpy(prob.sw0).to(dev)
+    b0 = torch.from_numpy(prob.bhp0).to(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        sim.set_state_device(p0, sw0, b0)
+        sim.assemble(prob.dt)
+        rc, st = sim.solve_step()
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    sim.time_kernel(TIMED_KERNEL)
+    sim.kernel_timing(reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = sim.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st = step()
+            its.append(st.linear_iters)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.launch_count() - l0
+    k_ms, k_n = sim.kernel_timing(reset=True)
+    sim.time_kernel(None)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    hp = torch.from_numpy(prob.p0).pin_memory()
+    hs = torch.from_numpy(prob.sw0).pin_memory()
+    hb = torch.from_numpy(prob.bhp0).pin_memory()
+    op = torch.empty_like(hp).pin_memory()
+    osw = torch.empty_like(hs).pin_memory()
+    ob = torch.empty_like(hb).pin_memory()
+    e2e_steps = 0 if args.no_e2e else max(2, args.steps // 2)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state_ptr(hp.data_ptr(), hs.data_ptr(), hb.data_ptr())
+        sim.assemble(prob.dt)
+        sim.solve_step()
+        sim.get_state_ptr(op.data_ptr(), osw.data_ptr(), ob.data_ptr())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes_state = 8 * (2 * prob.n_cells + prob.n_wells)
+
+    if rank == 0:
+        value = world * args.steps / (ms / 1000.0)
+        peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+        peak = peaks.get("hbm_gbs", 6800.0)
+        ach = spmv_bytes(sim.nb, sim.nnzb) / (k_ms / max(k_n, 1) / 1000.0) / 1e9 if k_n else None
+        cpu = None
+        if not args.no_cpu_baseline:
+            try:
+                cpu = oracle_sample(args)
+            except Exception as e:  # report, do not fail the bench
+                cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                       "sample": f"failed: {e}"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == 0 else "f64 (f32 preconditioner)",
+            "data": "synthetic", "config": config_dict(args),
+            "fgmres_iters_per_step": statistics.mean(its),
+            "roofline": {"bound": "hbm", "kernel": "bsr_spmv (FP64 2x2 BSR, y = A x)",
+                         "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": (ach / peak) if ach else None, "traffic": None,
+                         "launches_timed": k_n,
+                         "avg_launch_ms": (k_ms / k_n) if k_n else None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * e2e_steps / e2e_s if e2e_steps else None, "unit": UNIT,
+                    "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

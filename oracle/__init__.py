@@ -62,7 +62,8 @@ class og_options(C.Structure):
                 ("eta_max", C.c_double), ("gmres_restart", C.c_int32),
                 ("gmres_maxit", C.c_int32), ("amg_theta", C.c_double),
                 ("amg_coarse_max", C.c_int32), ("amg_max_levels", C.c_int32),
-                ("precond", C.c_int32), ("ds_max", C.c_double)]
+                ("precond", C.c_int32), ("ds_max", C.c_double),
+                ("amg_gs_levels", C.c_int32)]
 
 
 class og_stats(C.Structure):
@@ -86,6 +87,7 @@ def options(mode: str = "parity", **kw) -> og_options:
     o.amg_max_levels = 20
     o.precond = 2
     o.ds_max = 0.2
+    o.amg_gs_levels = 30
     o.eta_gamma, o.eta_beta, o.eta_min, o.eta_max = 0.9, 2.0, 1e-4, 0.1
     if mode == "parity":
         o.eta_mode, o.eta_fixed, o.newton_tol = 0, 1e-10, 1e-10

@@ -333,6 +333,7 @@ typedef struct {
 typedef struct {
   int nlev;
   og_level lev[32];
+  int smoother;      /* levels below this one use l1-Jacobi, the others multicolour GS */
   double theta;
   int coarse_max, max_levels;
   int dense_n;       /* coarsest dense LU size (0: coarsest uses GS) */
@@ -608,9 +609,9 @@ static void amg_free(og_amg *m) {
   }
   free(m->lu); free(m->piv);
   double theta = m->theta;
-  int cmax = m->coarse_max, mlev = m->max_levels;
+  int cmax = m->coarse_max, mlev = m->max_levels, sm = m->smoother;
   memset(m, 0, sizeof(*m));
-  m->theta = theta; m->coarse_max = cmax; m->max_levels = mlev;
+  m->theta = theta; m->coarse_max = cmax; m->max_levels = mlev; m->smoother = sm;
 }
 
 static void csr_copy(const og_csr *a, og_csr *b) {
@@ -713,17 +714,37 @@ static void gs_sweep(const og_level *L, const double *b, double *x, int forward)
   }
 }
 
+/* One l1-Jacobi sweep (Baker, Falgout, Kolev, Yang 2011):
+ * x_i <- x_i + (b_i - (A x)_i) / sum_j |a_ij|, all rows from the old x. */
+static void l1_jacobi(const og_level *L, const double *b, double *x, double *t) {
+  for (int i = 0; i < L->A.n; ++i) {
+    double s = 0.0, l1 = 0.0;
+    for (int e = L->A.rowptr[i]; e < L->A.rowptr[i + 1]; ++e) {
+      s += L->A.val[e] * x[L->A.col[e]];
+      l1 += fabs(L->A.val[e]);
+    }
+    t[i] = l1 != 0.0 ? x[i] + (b[i] - s) / l1 : x[i];
+  }
+  memcpy(x, t, sizeof(double) * (size_t)L->A.n);
+}
+
+static void smooth(const og_amg *m, int l, const double *b, double *x, int forward) {
+  const og_level *L = &m->lev[l];
+  if (l >= m->smoother) l1_jacobi(L, b, x, L->r);   /* r is free while smoothing */
+  else gs_sweep(L, b, x, forward);
+}
+
 static void vcycle(og_amg *m, int l, const double *b, double *x) {
   og_level *L = &m->lev[l];
   int n = L->A.n;
   if (l == m->nlev - 1) {
     if (m->dense_n == n && n > 0) { dense_lu_solve(m->lu, m->piv, n, b, x); return; }
     for (int i = 0; i < n; ++i) x[i] = 0.0;
-    gs_sweep(L, b, x, 1); gs_sweep(L, b, x, 0);
+    smooth(m, l, b, x, 1); smooth(m, l, b, x, 0);
     return;
   }
   for (int i = 0; i < n; ++i) x[i] = 0.0;
-  gs_sweep(L, b, x, 1);                               /* pre-smoothing */
+  smooth(m, l, b, x, 1);                              /* pre-smoothing */
   csr_mv(&L->A, x, L->r);
   for (int i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];
   og_level *N = &m->lev[l + 1];
@@ -732,7 +753,7 @@ static void vcycle(og_amg *m, int l, const double *b, double *x) {
   double *px = L->r;
   csr_mv(&L->P, N->x, px);                            /* prolong */
   for (int i = 0; i < n; ++i) x[i] += px[i];
-  gs_sweep(L, b, x, 0);                               /* post-smoothing */
+  smooth(m, l, b, x, 0);                              /* post-smoothing */
 }
 
 int oracle_amg_create(int32_t n, const int32_t *rowptr, const int32_t *col,
@@ -740,6 +761,7 @@ int oracle_amg_create(int32_t n, const int32_t *rowptr, const int32_t *col,
                       int32_t max_levels, void **out) {
   og_amg *m = (og_amg *)zalloc(1, sizeof(og_amg));
   m->theta = theta; m->coarse_max = coarse_max; m->max_levels = max_levels > 30 ? 30 : max_levels;
+  m->smoother = 30;
   og_csr A = {n, n, rowptr[n], (int *)rowptr, (int *)col, (double *)val};
   amg_setup(m, &A);
   *out = m;
@@ -1360,6 +1382,7 @@ int oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
   s->Ap.rowptr = J->rowptr; s->Ap.col = J->col;
   s->Ap.val = (double *)zalloc((size_t)J->nnz, sizeof(double));
   s->amg.theta = o->amg_theta; s->amg.coarse_max = o->amg_coarse_max;
+  s->amg.smoother = o->amg_gs_levels;
   s->amg.max_levels = o->amg_max_levels > 30 ? 30 : o->amg_max_levels;
   s->dt = 1.0; s->inv_dt = 1.0;
   *out = s;

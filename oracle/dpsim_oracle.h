@@ -41,6 +41,8 @@ typedef struct {
   double amg_theta; int32_t amg_coarse_max, amg_max_levels;
   int32_t precond;        /* 0 none, 1 block ILU(0) only, 2 CPR-FPF */
   double ds_max;
+  int32_t amg_gs_levels;  /* levels 0..amg_gs_levels-1 smoothed by multicolour
+                             Gauss-Seidel, coarser levels by l1-Jacobi */
 } og_options;
 typedef struct {
   int32_t newton_iters, linear_iters, converged, amg_levels;

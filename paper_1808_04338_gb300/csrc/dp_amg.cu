@@ -474,31 +474,61 @@ __global__ void k_spgemm_expand(int n, const int *lrp, const int *lcol, const in
   cnt[r] = u;
 }
 
+// Numeric product with G lanes per output row: the entries (r, k) of L are
+// taken one after the other in increasing k; the lanes share the entries of
+// row k of R (distinct columns, so distinct outputs) and synchronise before
+// the next k.  Every output is therefore a sum in increasing k.
+template <int G>
 __global__ void k_spgemm_numeric(int n, const int *lrp, const int *lcol, const double *lval,
                                  const int *rrp, const int *rcol, const double *rval,
                                  const int *crp, const int *ccol, double *cval) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = t / G, lane = t % G;
+  if (r >= n) return;                   // groups of G lanes leave together
+  unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   int c0 = crp[r], c1 = crp[r + 1];
-  for (int q = c0; q < c1; ++q) cval[q] = 0.0;
+  for (int q = c0 + lane; q < c1; q += G) cval[q] = 0.0;
+  if (G > 1) __syncwarp(gmask);
   for (int e = lrp[r]; e < lrp[r + 1]; ++e) {
     int k = lcol[e];
     double lv = lval[e];
-    for (int q = rrp[k]; q < rrp[k + 1]; ++q) {
+    for (int q = rrp[k] + lane; q < rrp[k + 1]; q += G) {
       int p = find_sorted(ccol, c0, c1, rcol[q]);
       if (p >= 0) cval[p] = cval[p] + lv * rval[q];
     }
+    if (G > 1) __syncwarp(gmask);
   }
 }
 
+#define DP_SWITCH_G2(G, LAUNCH)                      \
+  switch (G) {                                      \
+    case 1: { constexpr int GG = 1; LAUNCH; } break;  \
+    case 2: { constexpr int GG = 2; LAUNCH; } break;  \
+    case 4: { constexpr int GG = 4; LAUNCH; } break;  \
+    case 8: { constexpr int GG = 8; LAUNCH; } break;  \
+    case 16: { constexpr int GG = 16; LAUNCH; } break; \
+    default: { constexpr int GG = 32; LAUNCH; } break; \
+  }
+
+static int spgemm_numeric(Sim *s, int G, int n, const int *lrp, const int *lcol,
+                          const double *lval, const int *rrp, const int *rcol, const double *rval,
+                          const int *crp, const int *ccol, double *cval) {
+  long long thr = (long long)n * G;
+  DP_SWITCH_G2(G, DP_LAUNCH(s, k_spgemm_numeric<GG>, nblk(thr), kBlock, 0, n, lrp, lcol, lval, rrp,
+                            rcol, rval, crp, ccol, cval));
+  return DP_OK;
+}
+
 static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const int *rrp,
-                           const int *rcol, int **crp_out, int **ccol_out, int *nnz_out) {
+                           const int *rcol, int **crp_out, int **ccol_out, int *nnz_out,
+                           int *lanes) {
   int *ub = (int *)dalloc(s, (size_t)(n + 1) * 4), *off = (int *)dalloc(s, (size_t)(n + 1) * 4);
   int *crp = (int *)dalloc(s, (size_t)(n + 1) * 4);
   if (!ub || !off || !crp) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   DP_LAUNCH(s, k_spgemm_ub, nblk(n), kBlock, 0, n, lrp, lcol, rrp, ub);
   int tot = 0;
   DP_TRY(scan_i32(s, ub, off, n, &tot));
+  *lanes = lanes_for(n > 0 ? (double)tot / n : 0.0);
   int *scratch = (int *)dalloc(s, (size_t)std::max(tot, 1) * 4);
   if (!scratch) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   DP_LAUNCH(s, k_spgemm_expand, nblk(n, 64), 64, 0, n, lrp, lcol, rrp, rcol, off, scratch, ub);
@@ -521,6 +551,7 @@ static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const
 
 static int level_prepare(Sim *s, Level &L) {
   int n = L.n;
+  L.G = lanes_for(n > 0 ? (double)L.nnz / n : 0.0);
   L.dpos = (int *)dalloc(s, (size_t)n * 4);
   L.tpos = (int *)dalloc(s, (size_t)std::max(L.nnz, 1) * 4);
   L.colour = (int *)dalloc(s, (size_t)n * 4);
@@ -552,10 +583,10 @@ static int level_numeric(Sim *s, Level &L, Level &N) {
   DP_LAUNCH(s, k_p_values, nblk(n), kBlock, 0, n, L.rowptr, L.col, L.strong, L.val, L.fdiag,
             L.agg, s->omega, L.p_rowptr, L.p_col, L.p_val);
   DP_LAUNCH(s, k_gather, nblk(L.r_nnz), kBlock, 0, L.r_nnz, L.r_src, L.p_val, L.r_val);
-  DP_LAUNCH(s, k_spgemm_numeric, nblk(n), kBlock, 0, n, L.rowptr, L.col, L.val, L.p_rowptr,
-            L.p_col, L.p_val, L.ap_rowptr, L.ap_col, L.ap_val);
-  DP_LAUNCH(s, k_spgemm_numeric, nblk(L.nagg), kBlock, 0, L.nagg, L.r_rowptr, L.r_col, L.r_val,
-            L.ap_rowptr, L.ap_col, L.ap_val, N.rowptr, N.col, N.val);
+  DP_TRY(spgemm_numeric(s, L.ap_G, n, L.rowptr, L.col, L.val, L.p_rowptr, L.p_col, L.p_val,
+                        L.ap_rowptr, L.ap_col, L.ap_val));
+  DP_TRY(spgemm_numeric(s, L.rap_G, L.nagg, L.r_rowptr, L.r_col, L.r_val, L.ap_rowptr, L.ap_col,
+                        L.ap_val, N.rowptr, N.col, N.val));
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
@@ -582,6 +613,7 @@ static void phase(Sim *s, const char *what, int level, double &t) {
 
 int amg_setup(Sim *s) {
   double tp = now_ms();
+  graphs_free(s);
   amg_free(s);
   const dp_options &o = s->opt;
   s->lev.clear();
@@ -679,12 +711,14 @@ int amg_setup(Sim *s) {
     phase(s, "P, R", l, tp);
     // AP = A P and A_c = R (A P) patterns
     DP_TRY(spgemm_symbolic(s, n, L.rowptr, L.col, L.p_rowptr, L.p_col, &L.ap_rowptr, &L.ap_col,
-                           &L.ap_nnz));
+                           &L.ap_nnz, &L.ap_G));
     L.ap_val = (double *)dalloc(s, (size_t)std::max(L.ap_nnz, 1) * 8);
     Level N;
     N.n = na;
     DP_TRY(spgemm_symbolic(s, na, L.r_rowptr, L.r_col, L.ap_rowptr, L.ap_col, &N.rowptr, &N.col,
-                           &N.nnz));
+                           &N.nnz, &L.rap_G));
+    L.p_G = lanes_for((double)L.p_nnz / n);
+    L.r_G = lanes_for((double)L.p_nnz / na);
     N.val = (double *)dalloc(s, (size_t)std::max(N.nnz, 1) * 8);
     N.valf = (float *)dalloc(s, (size_t)std::max(N.nnz, 1) * 4);
     if (!L.ap_val || !N.val || !N.valf) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }

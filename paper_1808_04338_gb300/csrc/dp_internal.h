@@ -73,6 +73,8 @@ struct Level {
   float *r_valf = nullptr;
   int *ap_rowptr = nullptr, *ap_col = nullptr;
   double *ap_val = nullptr;
+  // lanes per row of the level kernels (operator, P, R) and of the products
+  int G = 1, p_G = 1, r_G = 1, ap_G = 1, rap_G = 1;
   // V-cycle work vectors
   double *x = nullptr, *b = nullptr, *r = nullptr;
   float *xf = nullptr, *bf = nullptr, *rf = nullptr;
@@ -136,6 +138,8 @@ int cpr_apply(Sim *s, const double *r, double *z);
 int fgmres(Sim *s, double tol, int *iters, double *relres);
 int la_alloc(Sim *s);
 int mixed_refresh(Sim *s);
+int lanes_for(double mean_len);
+void graphs_free(Sim *s);
 
 struct Timing {
   int kernel_id = -1;            // hashed name being timed, -1 none
@@ -207,6 +211,10 @@ struct Sim {
   double *h_res = nullptr;                           // pinned host scalars
   int dot_blocks = 0;
   double *z1 = nullptr, *r1 = nullptr, *rp = nullptr, *xp = nullptr;
+  // CUDA graphs of the FGMRES iterations j = 0..m-1 (captured on first use)
+  std::vector<cudaGraphExec_t> graph;
+  std::vector<long long> graph_launches;
+  cudaStream_t cap_stream = nullptr;
   // Newton bookkeeping
   double prev_res = 0.0, prev_linres = 0.0;
   int newton_iter = 0;

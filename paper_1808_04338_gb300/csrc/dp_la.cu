@@ -10,10 +10,12 @@
 namespace dp {
 
 // ---------------------------------------------------------------- BSR SpMV
-// G lanes per block row: lane l handles blocks e0 + l, e0 + l + G, ...; each
-// 2x2 block is two 16-byte loads, x_j one 16-byte load; the group reduces
-// with shuffles and its first lane writes the two outputs.
-template <int G, int MODE>  // MODE 0: y = A x; 1: y = b - A x
+// Two lanes per block row, one per output component: lane c of row i reads
+// row c of every 2x2 block (one 16-byte load; the two lanes of a row read
+// the two halves of the same 32-byte block), x_j (16 bytes, shared by the
+// pair) and accumulates its own output with FMAs, so no FP64 reduction
+// across lanes is needed.  A warp covers 16 block rows.
+template <int MODE>  // MODE 0: y = A x; 1: y = b - A x
 __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, const int *__restrict__ rowptr,
                                                      const int *__restrict__ col,
                                                      const double *__restrict__ val,
@@ -21,68 +23,55 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, const int *__restric
                                                      const double *__restrict__ b,
                                                      double *__restrict__ y) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = t / G, lane = t % G;
-  bool valid = row < n;                   // no early exit: all lanes shuffle
-  int e0 = valid ? rowptr[row] : 0, e1 = valid ? rowptr[row + 1] : 0;
-  double s0 = 0.0, s1 = 0.0;
-  const double2 *v2 = reinterpret_cast<const double2 *>(val);
+  int row = t >> 1, comp = t & 1;
+  if (row >= n) return;
+  int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+  const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
-  for (int e = e0 + lane; e < e1; e += G) {
-    double2 a01 = __ldg(v2 + 2 * (size_t)e);
-    double2 a23 = __ldg(v2 + 2 * (size_t)e + 1);
-    double2 xj = __ldg(x2 + col[e]);
-    s0 += a01.x * xj.x + a01.y * xj.y;
-    s1 += a23.x * xj.x + a23.y * xj.y;
+  double s = 0.0;
+#pragma unroll 4
+  for (int e = e0; e < e1; ++e) {
+    double2 a = __ldg(v2 + 2 * (size_t)e);
+    double2 xj = __ldg(x2 + __ldg(col + e));
+    s = fma(a.x, xj.x, s);
+    s = fma(a.y, xj.y, s);
   }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o, G);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
-  }
-  if (valid && lane == 0) {
-    double2 out;
-    if (MODE == 0) { out.x = s0; out.y = s1; }
-    else { double2 bb = reinterpret_cast<const double2 *>(b)[row]; out.x = bb.x - s0; out.y = bb.y - s1; }
-    reinterpret_cast<double2 *>(y)[row] = out;
-  }
+  y[2 * (size_t)row + comp] = MODE == 0 ? s : b[2 * (size_t)row + comp] - s;
 }
 
-// Pressure component of b - A x: rp_i = b_{i,0} - sum_j (a00 x_j0 + a01 x_j1).
-template <int G>
+// Pressure component of b - A x: rp_i = b_{i,0} - sum_j (a00 x_j0 + a01 x_j1)
+// (reads the first half of every block only).
 __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, const int *__restrict__ rowptr,
                                                        const int *__restrict__ col,
                                                        const double *__restrict__ val,
                                                        const double *__restrict__ x,
                                                        const double *__restrict__ b,
                                                        double *__restrict__ rp) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = t / G, lane = t % G;
-  bool valid = row < n;
-  int e0 = valid ? rowptr[row] : 0, e1 = valid ? rowptr[row + 1] : 0;
-  double s0 = 0.0;
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
   const double2 *v2 = reinterpret_cast<const double2 *>(val);
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
-  for (int e = e0 + lane; e < e1; e += G) {
-    double2 a01 = __ldg(v2 + 2 * (size_t)e);
-    double2 xj = __ldg(x2 + col[e]);
-    s0 += a01.x * xj.x + a01.y * xj.y;
+  double s = 0.0;
+#pragma unroll 4
+  for (int e = e0; e < e1; ++e) {
+    double2 a = __ldg(v2 + 2 * (size_t)e);
+    double2 xj = __ldg(x2 + __ldg(col + e));
+    s = fma(a.x, xj.x, s);
+    s = fma(a.y, xj.y, s);
   }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) s0 += __shfl_down_sync(0xffffffffu, s0, o, G);
-  if (valid && lane == 0) rp[row] = b[2 * row] - s0;
+  rp[row] = b[2 * (size_t)row] - s;
 }
 
-constexpr int kG = 4;
-
 int bsr_spmv(Sim *s, const double *x, double *y) {
-  DP_LAUNCH(s, (k_bsr_spmv<kG, 0>), nblk((long long)s->A.n * kG), kBlock, 0, s->A.n, s->A.rowptr,
-            s->A.col, s->A.val, x, nullptr, y);
+  DP_LAUNCH(s, k_bsr_spmv<0>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->A.rowptr, s->A.col,
+            s->A.val, x, nullptr, y);
   return DP_OK;
 }
 
 int bsr_residual(Sim *s, const double *b, const double *x, double *r) {
-  DP_LAUNCH(s, (k_bsr_spmv<kG, 1>), nblk((long long)s->A.n * kG), kBlock, 0, s->A.n, s->A.rowptr,
-            s->A.col, s->A.val, x, b, r);
+  DP_LAUNCH(s, k_bsr_spmv<1>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->A.rowptr, s->A.col,
+            s->A.val, x, b, r);
   return DP_OK;
 }
 
@@ -165,8 +154,8 @@ __global__ void k_ilu_factor(int r0, int r1, const int *perm, const int *iperm,
   inv2(lu + 4 * (size_t)dp);
 }
 
-// forward sweep of one colour: z_i = r_i - sum_{L} L_ik z_k (unit lower)
-template <int G>
+// Forward sweep of one colour, two lanes per row (one per component):
+// z_i = r_i - sum_{L} L_ik z_k (unit lower triangle).
 __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *__restrict__ perm,
                                                     const int *__restrict__ lu_rowptr,
                                                     const int *__restrict__ lu_col,
@@ -174,61 +163,51 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *_
                                                     const double *__restrict__ lu,
                                                     const double *__restrict__ rhs, double *z) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = r0 + t / G, lane = t % G;
-  bool valid = r < r1;
-  int i = valid ? perm[r] : 0;
-  double s0 = 0.0, s1 = 0.0;
-  const double2 *v2 = reinterpret_cast<const double2 *>(lu);
+  int r = r0 + (t >> 1), comp = t & 1;
+  if (r >= r1) return;
+  int i = __ldg(perm + r);
+  const double2 *v2 = reinterpret_cast<const double2 *>(lu) + comp;
   const double2 *z2 = reinterpret_cast<const double2 *>(z);
-  int ea = valid ? lu_rowptr[r] : 0, eb = valid ? lu_dpos[r] : 0;
-  for (int e = ea + lane; e < eb; e += G) {
-    double2 a01 = __ldg(v2 + 2 * (size_t)e), a23 = __ldg(v2 + 2 * (size_t)e + 1);
-    double2 xk = z2[lu_col[e]];
-    s0 += a01.x * xk.x + a01.y * xk.y;
-    s1 += a23.x * xk.x + a23.y * xk.y;
+  double s = 0.0;
+  int ea = __ldg(lu_rowptr + r), eb = __ldg(lu_dpos + r);
+#pragma unroll 4
+  for (int e = ea; e < eb; ++e) {
+    double2 a = __ldg(v2 + 2 * (size_t)e);
+    double2 xk = z2[__ldg(lu_col + e)];
+    s = fma(a.x, xk.x, s);
+    s = fma(a.y, xk.y, s);
   }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o, G);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
-  }
-  if (valid && lane == 0) {
-    double2 rr = reinterpret_cast<const double2 *>(rhs)[i];
-    reinterpret_cast<double2 *>(z)[i] = make_double2(rr.x - s0, rr.y - s1);
-  }
+  z[2 * (size_t)i + comp] = rhs[2 * (size_t)i + comp] - s;
 }
 
-// backward sweep of one colour: z_i = U_ii^-1 (z_i - sum_{U} U_ij z_j)
-template <int G>
+// Backward sweep of one colour: z_i = U_ii^-1 (z_i - sum_{U} U_ij z_j).  The
+// two lanes of a row exchange their partial results for the 2x2 product.
 __global__ void __launch_bounds__(kBlock) k_ilu_bwd(int r0, int r1, const int *__restrict__ perm,
                                                     const int *__restrict__ lu_rowptr,
                                                     const int *__restrict__ lu_col,
                                                     const int *__restrict__ lu_dpos,
                                                     const double *__restrict__ lu, double *z) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = r0 + t / G, lane = t % G;
-  bool valid = r < r1;
-  int i = valid ? perm[r] : 0, dp = valid ? lu_dpos[r] : 0;
-  double s0 = 0.0, s1 = 0.0;
+  int r = r0 + (t >> 1), comp = t & 1;
+  bool valid = r < r1;                  // no early exit: the pair shuffles
+  int i = valid ? __ldg(perm + r) : 0;
   const double2 *v2 = reinterpret_cast<const double2 *>(lu);
   const double2 *z2 = reinterpret_cast<const double2 *>(z);
-  int eb = valid ? lu_rowptr[r + 1] : 0;
-  for (int e = dp + 1 + lane; e < eb; e += G) {
-    double2 a01 = __ldg(v2 + 2 * (size_t)e), a23 = __ldg(v2 + 2 * (size_t)e + 1);
-    double2 xj = z2[lu_col[e]];
-    s0 += a01.x * xj.x + a01.y * xj.y;
-    s1 += a23.x * xj.x + a23.y * xj.y;
+  int dp = valid ? __ldg(lu_dpos + r) : 0, eb = valid ? __ldg(lu_rowptr + r + 1) : 0;
+  double s = 0.0;
+#pragma unroll 4
+  for (int e = dp + 1; e < eb; ++e) {
+    double2 a = __ldg(v2 + 2 * (size_t)e + comp);
+    double2 xj = z2[__ldg(lu_col + e)];
+    s = fma(a.x, xj.x, s);
+    s = fma(a.y, xj.y, s);
   }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o, G);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
-  }
-  if (valid && lane == 0) {
-    double2 zi = z2[i];
-    double y0 = zi.x - s0, y1 = zi.y - s1;
-    double2 d01 = v2[2 * (size_t)dp], d23 = v2[2 * (size_t)dp + 1];
-    reinterpret_cast<double2 *>(z)[i] = make_double2(d01.x * y0 + d01.y * y1, d23.x * y0 + d23.y * y1);
+  double yi = valid ? z[2 * (size_t)i + comp] - s : 0.0;
+  double yo = __shfl_xor_sync(0xffffffffu, yi, 1);
+  if (valid) {
+    double y0 = comp == 0 ? yi : yo, y1 = comp == 0 ? yo : yi;
+    double2 d = __ldg(v2 + 2 * (size_t)dp + comp);
+    z[2 * (size_t)i + comp] = fma(d.x, y0, d.y * y1);
   }
 }
 
@@ -276,56 +255,117 @@ int ilu_apply(Sim *s, const double *r, double *z) {
   for (int c = 0; c < s->ncolour; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 > r0)
-      DP_LAUNCH(s, (k_ilu_fwd<kG>), nblk((long long)(r1 - r0) * kG), kBlock, 0, r0, r1, s->perm,
-                s->lu_rowptr, s->lu_col, s->lu_dpos, s->lu_val, r, z);
+      DP_LAUNCH(s, k_ilu_fwd, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm, s->lu_rowptr,
+                s->lu_col, s->lu_dpos, s->lu_val, r, z);
   }
   for (int c = s->ncolour - 1; c >= 0; --c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 > r0)
-      DP_LAUNCH(s, (k_ilu_bwd<kG>), nblk((long long)(r1 - r0) * kG), kBlock, 0, r0, r1, s->perm,
-                s->lu_rowptr, s->lu_col, s->lu_dpos, s->lu_val, z);
+      DP_LAUNCH(s, k_ilu_bwd, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm, s->lu_rowptr,
+                s->lu_col, s->lu_dpos, s->lu_val, z);
   }
   return DP_OK;
 }
 
 // ---------------------------------------------------------------- AMG cycle
 
-// One colour of Gauss-Seidel: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii.
-__global__ void k_gs_colour(int r0, int r1, const int *__restrict__ clist,
-                            const int *__restrict__ rowptr, const int *__restrict__ col,
-                            const double *__restrict__ val, const int *__restrict__ dpos,
-                            const double *__restrict__ b, double *x) {
-  int t = r0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= r1) return;
-  int i = clist[t];
-  double s = b[i], d = 0.0;
-  int dp = dpos[i];
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-    if (e == dp) { d = val[e]; continue; }
-    s -= val[e] * x[col[e]];
-  }
-  if (d != 0.0) x[i] = s / d;
+// Scalar CSR kernels of the AMG levels: G lanes per row (G chosen per level
+// from its mean row length), partial sums combined with shuffles inside the
+// group; every lane reaches the shuffles (no early exit).
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
 }
 
-__global__ void k_csr_resid(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ b,
-                            const double *__restrict__ x, double *__restrict__ r) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// One colour of Gauss-Seidel: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii.
+template <int G>
+__global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int *__restrict__ clist,
+                                                      const int *__restrict__ rowptr,
+                                                      const int *__restrict__ col,
+                                                      const double *__restrict__ val,
+                                                      const int *__restrict__ dpos,
+                                                      const double *__restrict__ b, double *x) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int q = r0 + t / G, lane = t % G;
+  bool valid = q < r1;
+  int i = valid ? clist[q] : 0;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0, dp = valid ? dpos[i] : -1;
+  double s = 0.0, d = 0.0;
+  for (int e = e0 + lane; e < e1; e += G) {
+    double a = val[e];
+    if (e == dp) d = a;
+    else s = fma(a, x[col[e]], s);
+  }
+  if (G > 1) { s = group_sum<G>(s); d = group_sum<G>(d); }
+  if (valid && lane == 0 && d != 0.0) x[i] = (b[i] - s) / d;
+}
+
+// r = b - A x
+template <int G>
+__global__ void __launch_bounds__(kBlock) k_csr_resid(int n, const int *__restrict__ rowptr,
+                                                      const int *__restrict__ col,
+                                                      const double *__restrict__ val,
+                                                      const double *__restrict__ b,
+                                                      const double *__restrict__ x,
+                                                      double *__restrict__ r) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
   double s = 0.0;
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) s += val[e] * x[col[e]];
-  r[i] = b[i] - s;
+  for (int e = e0 + lane; e < e1; e += G) s = fma(val[e], x[col[e]], s);
+  if (G > 1) s = group_sum<G>(s);
+  if (valid && lane == 0) r[i] = b[i] - s;
 }
 
 // y = A x (add = 0) or y += A x (add = 1)
-__global__ void k_csr_mv(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                         const double *__restrict__ val, const double *__restrict__ x,
-                         double *__restrict__ y, int add) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+template <int G>
+__global__ void __launch_bounds__(kBlock) k_csr_mv(int n, const int *__restrict__ rowptr,
+                                                   const int *__restrict__ col,
+                                                   const double *__restrict__ val,
+                                                   const double *__restrict__ x,
+                                                   double *__restrict__ y, int add) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
   double s = 0.0;
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) s += val[e] * x[col[e]];
-  y[i] = add ? y[i] + s : s;
+  for (int e = e0 + lane; e < e1; e += G) s = fma(val[e], x[col[e]], s);
+  if (G > 1) s = group_sum<G>(s);
+  if (valid && lane == 0) y[i] = add ? y[i] + s : s;
+}
+
+// lanes per row for a mean row length
+int lanes_for(double mean_len) {
+  int g = 1;
+  while (g < 32 && 2.0 * g < mean_len) g *= 2;
+  return g;
+}
+
+#define DP_SWITCH_G(G, LAUNCH)                       \
+  switch (G) {                                      \
+    case 1: { constexpr int GG = 1; LAUNCH; } break;  \
+    case 2: { constexpr int GG = 2; LAUNCH; } break;  \
+    case 4: { constexpr int GG = 4; LAUNCH; } break;  \
+    case 8: { constexpr int GG = 8; LAUNCH; } break;  \
+    case 16: { constexpr int GG = 16; LAUNCH; } break; \
+    default: { constexpr int GG = 32; LAUNCH; } break; \
+  }
+
+static int csr_resid(Sim *s, const Level &L, const double *b, const double *x, double *r) {
+  long long thr = (long long)L.n * L.G;
+  DP_SWITCH_G(L.G, DP_LAUNCH(s, k_csr_resid<GG>, nblk(thr), kBlock, 0, L.n, L.rowptr, L.col,
+                             L.val, b, x, r));
+  return DP_OK;
+}
+
+static int csr_mv(Sim *s, int n, int G, const int *rowptr, const int *col, const double *val,
+                  const double *x, double *y, int add) {
+  long long thr = (long long)n * G;
+  DP_SWITCH_G(G, DP_LAUNCH(s, k_csr_mv<GG>, nblk(thr), kBlock, 0, n, rowptr, col, val, x, y, add));
+  return DP_OK;
 }
 
 // coarsest level: dense copy, LU with partial pivoting, solve (one block)
@@ -431,9 +471,11 @@ static int gs_sweep(Sim *s, Level &L, const double *b, double *x, bool forward) 
   for (int t = 0; t < L.ncolour; ++t) {
     int c = forward ? t : L.ncolour - 1 - t;
     int r0 = L.cstart[c], r1 = L.cstart[c + 1];
-    if (r1 > r0)
-      DP_LAUNCH(s, k_gs_colour, nblk(r1 - r0), kBlock, 0, r0, r1, L.clist, L.rowptr, L.col, L.val,
-                L.dpos, b, x);
+    if (r1 > r0) {
+      long long thr = (long long)(r1 - r0) * L.G;
+      DP_SWITCH_G(L.G, DP_LAUNCH(s, k_gs_colour<GG>, nblk(thr), kBlock, 0, r0, r1, L.clist,
+                                 L.rowptr, L.col, L.val, L.dpos, b, x));
+    }
   }
   return DP_OK;
 }
@@ -454,10 +496,10 @@ int vcycle(Sim *s, int l, const double *b, double *x) {
   Level &N = s->lev[l + 1];
   DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * 8, s->stream));
   DP_TRY(gs_sweep(s, L, b, x, true));
-  DP_LAUNCH(s, k_csr_resid, nblk(n), kBlock, 0, n, L.rowptr, L.col, L.val, b, x, L.r);
-  DP_LAUNCH(s, k_csr_mv, nblk(N.n), kBlock, 0, N.n, L.r_rowptr, L.r_col, L.r_val, L.r, N.b, 0);
+  DP_TRY(csr_resid(s, L, b, x, L.r));
+  DP_TRY(csr_mv(s, N.n, L.r_G, L.r_rowptr, L.r_col, L.r_val, L.r, N.b, 0));
   DP_TRY(vcycle(s, l + 1, N.b, N.x));
-  DP_LAUNCH(s, k_csr_mv, nblk(n), kBlock, 0, n, L.p_rowptr, L.p_col, L.p_val, N.x, x, 1);
+  DP_TRY(csr_mv(s, n, L.p_G, L.p_rowptr, L.p_col, L.p_val, N.x, x, 1));
   DP_TRY(gs_sweep(s, L, b, x, false));
   return DP_OK;
 }
@@ -484,8 +526,8 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   }
   if (s->opt.precond == 1) return ilu_apply(s, r, z);
   DP_TRY(ilu_apply(s, r, s->z1));
-  DP_LAUNCH(s, k_bsr_presid<kG>, nblk((long long)nb * kG), kBlock, 0, nb, s->A.rowptr, s->A.col,
-            s->A.val, s->z1, r, s->rp);
+  DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->A.rowptr, s->A.col, s->A.val, s->z1, r,
+            s->rp);
   DP_TRY(vcycle(s, 0, s->rp, s->xp));
   DP_LAUNCH(s, k_inject_add, nblk(nb), kBlock, 0, nb, s->xp, s->z1);
   DP_TRY(bsr_residual(s, r, s->z1, s->r1));
@@ -624,12 +666,76 @@ static int norm_into(Sim *s, const double *x, double *dst) {
 
 __global__ void k_sqrt_inplace(double *v) { v[0] = sqrt(v[0]); }
 
+// One Arnoldi step of FGMRES for column j: z_j = M v_j, w = A z_j, two
+// passes of classical Gram-Schmidt, h_{j+1,j} = ||w||, v_{j+1} = w / h, the
+// Givens rotations, and |g_{j+1}| into scal[3].
+static int arnoldi_step(Sim *s, int j) {
+  int m = s->m;
+  long long N = 2LL * s->A.n;
+  int gridN = (int)std::min<long long>(nblk(N), kDotBlocks * 4);
+  double *vj = s->V + (long long)j * N, *zj = s->Z + (long long)j * N;
+  DP_TRY(cpr_apply(s, vj, zj));
+  DP_TRY(bsr_spmv(s, zj, s->w));
+  for (int pass = 0; pass < 2; ++pass) {
+    DP_TRY(dots(s, s->V, N, j + 1, s->w, 1, j));
+    DP_LAUNCH(s, k_multi_axpy, gridN, kBlock, 0, N, s->V, N, j + 1, s->dots, -1.0, s->w);
+  }
+  DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, s->w, 0LL, 1, s->w, s->dots_part, 0);
+  DP_LAUNCH(s, k_dot_final, 1, 32, 0, s->dots_part, kDotBlocks, 1, s->scal + 2, s->H, m, j, 2);
+  DP_LAUNCH(s, k_scale, nblk(N), kBlock, 0, N, s->w, s->scal + 2, 1, s->V + (long long)(j + 1) * N);
+  DP_LAUNCH(s, k_givens, 1, 32, 0, s->H, s->cs, s->sn, s->g, m, j, s->scal + 3);
+  return DP_OK;
+}
+
+void graphs_free(Sim *s) {
+  for (cudaGraphExec_t &g : s->graph)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  s->graph.clear();
+  s->graph_launches.clear();
+}
+
+// Run Arnoldi step j, from a CUDA graph captured on its first use (the
+// capture goes through a private stream; the graph is launched on the
+// simulation stream).
+static int arnoldi_step_graph(Sim *s, int j) {
+  if ((int)s->graph.size() < s->m) {
+    s->graph.assign(s->m, nullptr);
+    s->graph_launches.assign(s->m, 0);
+  }
+  if (!s->graph[j]) {
+    if (!s->cap_stream) DP_CUDA(s, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = s->stream;
+    // the captured work must follow what is already queued on the user stream
+    DP_CUDA(s, cudaStreamSynchronize(user));
+    s->stream = s->cap_stream;
+    DP_CUDA(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int64_t l0 = s->launches;
+    int rc = arnoldi_step(s, j);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+    s->stream = user;
+    int64_t kernels = s->launches - l0;   // kernels recorded, not yet run
+    s->launches = l0;
+    if (rc != DP_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ce != cudaSuccess) { s->fail(DP_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce)); return DP_ECUDA; }
+    cudaGraphExec_t ex = nullptr;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { s->fail(DP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)); return DP_ECUDA; }
+    s->graph[j] = ex;
+    s->graph_launches[j] = kernels;
+  }
+  DP_CUDA(s, cudaGraphLaunch(s->graph[j], s->stream));
+  s->launches += s->graph_launches[j];
+  return DP_OK;
+}
+
 int fgmres(Sim *s, double tol, int *iters, double *relres) {
   int m = s->m, maxit = s->opt.gmres_maxit;
   long long N = 2LL * s->A.n;
+  bool use_graph = s->opt.use_graphs && s->timing.kernel_id < 0;
   double *x = s->y;
   DP_CUDA(s, cudaMemsetAsync(x, 0, N * 8, s->stream));
-  // ||b||
   DP_TRY(norm_into(s, s->bh, s->scal + 0));
   DP_LAUNCH(s, k_sqrt_inplace, 1, 1, 0, s->scal + 0);
   DP_CUDA(s, cudaMemcpyAsync(s->h_res, s->scal, 8, cudaMemcpyDeviceToHost, s->stream));
@@ -654,17 +760,8 @@ int fgmres(Sim *s, double tol, int *iters, double *relres) {
     DP_LAUNCH(s, k_init_g, 1, 64, 0, s->g, m, s->scal + 1);
     int jend = 0;
     for (int j = 0; j < m && total < maxit; ++j) {
-      double *vj = s->V + (long long)j * N, *zj = s->Z + (long long)j * N;
-      DP_TRY(cpr_apply(s, vj, zj));
-      DP_TRY(bsr_spmv(s, zj, s->w));
-      for (int pass = 0; pass < 2; ++pass) {
-        DP_TRY(dots(s, s->V, N, j + 1, s->w, 1, j));
-        DP_LAUNCH(s, k_multi_axpy, gridN, kBlock, 0, N, s->V, N, j + 1, s->dots, -1.0, s->w);
-      }
-      DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, s->w, 0LL, 1, s->w, s->dots_part, 0);
-      DP_LAUNCH(s, k_dot_final, 1, 32, 0, s->dots_part, kDotBlocks, 1, s->scal + 2, s->H, m, j, 2);
-      DP_LAUNCH(s, k_scale, nblk(N), kBlock, 0, N, s->w, s->scal + 2, 1, s->V + (long long)(j + 1) * N);
-      DP_LAUNCH(s, k_givens, 1, 32, 0, s->H, s->cs, s->sn, s->g, m, j, s->scal + 3);
+      if (use_graph) DP_TRY(arnoldi_step_graph(s, j));
+      else DP_TRY(arnoldi_step(s, j));
       DP_CUDA(s, cudaMemcpyAsync(s->h_res + 2, s->scal + 2, 16, cudaMemcpyDeviceToHost, s->stream));
       DP_CUDA(s, cudaStreamSynchronize(s->stream));
       DP_CUDA(s, cudaGetLastError());

@@ -203,6 +203,8 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
 extern "C" void sim_destroy(dp_sim *s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
+  graphs_free(s);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   amg_free(s);
   while (!s->blocks.empty()) dfree(s, s->blocks.back().first);
   for (cudaEvent_t e : s->timing.ev) cudaEventDestroy(e);

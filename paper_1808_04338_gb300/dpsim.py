@@ -84,7 +84,7 @@ def options(mode: str = "parity", **kw) -> dp_options:
     o.precond = 2
     o.ds_max = 0.2
     o.precision = 0
-    o.use_graphs = 0
+    o.use_graphs = 1
     o.eta_gamma, o.eta_beta, o.eta_min, o.eta_max = 0.9, 2.0, 1e-4, 0.1
     if mode == "parity":
         o.eta_mode, o.eta_fixed, o.newton_tol = 0, 1e-10, 1e-10

@@ -159,9 +159,11 @@ def test_unpreconditioned_gmres_single_location():
     np.testing.assert_allclose(g.update(), y, rtol=1e-8, atol=1e-8 * np.abs(y).max())
 
 
-def test_ten_steps_tiny_state_parity():
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_ten_steps_tiny_state_parity(graphs):
     prob = di.tiny()
-    g, o = pair(prob)
+    g = gpu().Sim(prob, gpu().options("parity", use_graphs=graphs))
+    o = O.OracleSim(prob, O.options("parity"))
     for step in range(prob.nsteps):
         rcg, stg = g.advance(prob.dt)
         rco, sto = o.advance(prob.dt)
