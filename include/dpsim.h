@@ -201,6 +201,44 @@ int64_t sim_launch_count(const dp_sim *sim);
 /* Message of the last error on this dp_sim ("" when none). */
 const char *sim_last_error(const dp_sim *sim);
 
+/* Scaled residual norms computed without allocating any device memory.
+ *
+ * The paper has no counterpart of this call; it is a service for callers
+ * that must not allocate.  Examples: a serving loop that admits work by its
+ * device-memory footprint and keeps that budget exact, and that cannot
+ * afford the device-wide synchronisation cudaMalloc/cudaFree imply while
+ * other realisations are in flight; or a host program whose device memory
+ * is owned by another framework's pool.  It returns the same two numbers as
+ * out[0] and out[1] of sim_get_norms (the scaled residual's 2-norm and
+ * max-norm, cell rows scaled by dt / (rho_ref phi_ref V), well rows by their
+ * target), from a residual the caller already holds on the device.
+ *
+ * Arguments: grid and fluid are host pointers (only nx, ny, nz, dx, dy, dz
+ * and rho_o_ref, rho_w_ref are read); phi_f[nx ny nz], phi_m[nx ny nz],
+ * well_kind[nwells], well_target[nwells], res[2 (2 nx ny nz + nwells)] (the
+ * layout of sim_get_jacobian's res) and out2[2] are DEVICE pointers; dt is
+ * the step length (s); stream is a cudaStream_t (NULL: default stream).
+ * The result is written to out2 in stream order; the call does not
+ * synchronise.  err (may be NULL) receives a message of at most err_len
+ * bytes on failure.
+ *
+ * Limits and sharing: the block partial sums live in one static device
+ * array of 64 KiB (4096 blocks x 2 doubles) that every GPU loading the
+ * library keeps until the process exits; problems with more than 8,388,608
+ * block rows are rejected with DP_EINVAL and a message.  Every call
+ * overwrites the whole part of the array it reads, so nothing needs
+ * clearing between calls, but calls that overlap on the GPU (on different
+ * streams, or from different threads) share that array and race: order
+ * them on one stream.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  Returns DP_OK, DP_EINVAL or
+ * DP_ECUDA. */
+int dp_residual_norms_noalloc(const dp_grid *grid, const dp_fluid *fluid, const double *phi_f,
+                              const double *phi_m, int32_t nwells, const int32_t *well_kind,
+                              const double *well_target, const double *res, double dt,
+                              double *out2, void *stream, char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ UNITS = {
     "dp_amg.cu": ["-fmad=false"],
     "dp_la.cu": [],
     "dp_sim.cu": [],
+    "dp_noalloc.cu": [],
 }
 
 

@@ -132,6 +132,8 @@ def load():
     L.sim_launch_count.restype = C.c_int64
     L.sim_last_error.argtypes = [P]
     L.sim_last_error.restype = C.c_char_p
+    L.dp_residual_norms_noalloc.argtypes = [C.POINTER(dp_grid), C.POINTER(dp_fluid), P, P, I, P,
+                                            P, P, D, P, P, C.c_char_p, C.c_size_t]
     _lib = L
     return L
 
@@ -142,6 +144,25 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def residual_norms_noalloc(prob, phi_f, phi_m, well_kind, well_target, res, dt, out2,
+                           stream=0):
+    """Scaled residual 2-norm and max-norm into out2 (device tensors in, no
+    allocation by the library); returns (rc, message)."""
+    g = dp_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.top_depth)
+    f = dp_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref, prob.rho_w_ref,
+                 prob.p_ref, prob.swc, prob.sor, prob.g)
+    buf = C.create_string_buffer(256)
+
+    def ptr(t):
+        return C.c_void_p(t.data_ptr()) if t is not None else None
+
+    rc = load().dp_residual_norms_noalloc(C.byref(g), C.byref(f), ptr(phi_f), ptr(phi_m),
+                                          len(prob.wells), ptr(well_kind), ptr(well_target),
+                                          ptr(res), float(dt), ptr(out2), C.c_void_p(stream),
+                                          buf, 256)
+    return rc, buf.value.decode()
 
 
 class TorchAllocator:

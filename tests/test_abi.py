@@ -15,7 +15,7 @@ def declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(sim_\w+)\s*\(", src, flags=re.M):
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(sim_\w+|dp_\w+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return names
 
