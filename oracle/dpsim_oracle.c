@@ -1416,8 +1416,11 @@ int oracle_set_iterate(void *h, const double *p, const double *sw, const double 
 }
 
 int oracle_set_state(void *h, const double *p, const double *sw, const double *bhp) {
+  og_sim *s = (og_sim *)h;
   oracle_set_iterate(h, p, sw, bhp);
-  save_old((og_sim *)h);
+  save_old(s);
+  s->newton_iter = 0;            /* a new old time level starts a new timestep */
+  s->prev_res = 0.0; s->prev_linres = 0.0;
   return 0;
 }
 

@@ -26,6 +26,7 @@ UNITS = {
     "dp_la.cu": [],
     "dp_sim.cu": [],
     "dp_noalloc.cu": [],
+    "dp_cycle.cu": [],
 }
 
 
@@ -67,7 +68,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp])
+        run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-Xlinker", "-z,defs", *objs, "-o",
+             tmp])
         os.replace(tmp, LIB)
     return LIB
 

@@ -367,20 +367,25 @@ __global__ void k_copy_rows(int n, const int *src_rowptr, const int *scratch, co
 __global__ void k_filtered_diag(int n, const int *rowptr, const int *col, const uint8_t *strong,
                                 const double *val, double *fdiag, unsigned long long *rho_bits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  bool valid = i < n;                   // every lane reaches the shuffles
   double d = 0.0;
-  int e0 = rowptr[i], e1 = rowptr[i + 1];
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
   for (int e = e0; e < e1; ++e) if (col[e] == i) d = val[e];
   for (int e = e0; e < e1; ++e) if (col[e] != i && !strong[e]) d = d + val[e];
-  fdiag[i] = d;
-  if (d == 0.0) return;
-  double s = 0.0;
-  for (int e = e0; e < e1; ++e) {
-    if (col[e] == i) s = s + fabs(d);
-    else if (strong[e]) s = s + fabs(val[e]);
+  if (valid) fdiag[i] = d;
+  double ratio = 0.0;
+  if (d != 0.0) {
+    double s = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      if (col[e] == i) s = s + fabs(d);
+      else if (strong[e]) s = s + fabs(val[e]);
+    }
+    ratio = s / fabs(d);
   }
-  double ratio = s / fabs(d);
-  atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));  // ratio >= 0
+  // maximum over the block first (exact), then one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) ratio = fmax(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
+  if ((threadIdx.x & 31) == 0 && ratio > 0.0)
+    atomicMax(rho_bits, (unsigned long long)__double_as_longlong(ratio));  // ratio >= 0
 }
 
 __global__ void k_omega(const unsigned long long *rho_bits, double *omega) {
@@ -474,14 +479,29 @@ __global__ void k_spgemm_expand(int n, const int *lrp, const int *lcol, const in
   cnt[r] = u;
 }
 
+// Positions of every product in the output: for row r, the products are
+// enumerated (entry (r, k) of L in increasing k, entry (k, c) of R in
+// increasing c) and pos[off[r] + t] is the index of C_rc for product t.
+__global__ void k_spgemm_positions(int n, const int *lrp, const int *lcol, const int *rrp,
+                                   const int *rcol, const int *off, const int *crp,
+                                   const int *ccol, int *pos) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int c0 = crp[r], c1 = crp[r + 1], t = off[r];
+  for (int e = lrp[r]; e < lrp[r + 1]; ++e) {
+    int k = lcol[e];
+    for (int q = rrp[k]; q < rrp[k + 1]; ++q) pos[t++] = find_sorted(ccol, c0, c1, rcol[q]);
+  }
+}
+
 // Numeric product with G lanes per output row: the entries (r, k) of L are
 // taken one after the other in increasing k; the lanes share the entries of
 // row k of R (distinct columns, so distinct outputs) and synchronise before
 // the next k.  Every output is therefore a sum in increasing k.
 template <int G>
 __global__ void k_spgemm_numeric(int n, const int *lrp, const int *lcol, const double *lval,
-                                 const int *rrp, const int *rcol, const double *rval,
-                                 const int *crp, const int *ccol, double *cval) {
+                                 const int *rrp, const double *rval, const int *off,
+                                 const int *pos, const int *crp, double *cval) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = t / G, lane = t % G;
   if (r >= n) return;                   // groups of G lanes leave together
@@ -489,13 +509,16 @@ __global__ void k_spgemm_numeric(int n, const int *lrp, const int *lcol, const d
   int c0 = crp[r], c1 = crp[r + 1];
   for (int q = c0 + lane; q < c1; q += G) cval[q] = 0.0;
   if (G > 1) __syncwarp(gmask);
+  int base = off[r];
   for (int e = lrp[r]; e < lrp[r + 1]; ++e) {
     int k = lcol[e];
     double lv = lval[e];
-    for (int q = rrp[k] + lane; q < rrp[k + 1]; q += G) {
-      int p = find_sorted(ccol, c0, c1, rcol[q]);
+    int q0 = rrp[k], q1 = rrp[k + 1];
+    for (int q = q0 + lane; q < q1; q += G) {
+      int p = pos[base + q - q0];
       if (p >= 0) cval[p] = cval[p] + lv * rval[q];
     }
+    base += q1 - q0;
     if (G > 1) __syncwarp(gmask);
   }
 }
@@ -510,25 +533,30 @@ __global__ void k_spgemm_numeric(int n, const int *lrp, const int *lcol, const d
     default: { constexpr int GG = 32; LAUNCH; } break; \
   }
 
-static int spgemm_numeric(Sim *s, int G, int n, const int *lrp, const int *lcol,
-                          const double *lval, const int *rrp, const int *rcol, const double *rval,
-                          const int *crp, const int *ccol, double *cval) {
-  long long thr = (long long)n * G;
-  DP_SWITCH_G2(G, DP_LAUNCH(s, k_spgemm_numeric<GG>, nblk(thr), kBlock, 0, n, lrp, lcol, lval, rrp,
-                            rcol, rval, crp, ccol, cval));
+struct Product {                          // C = L R, pattern and product positions
+  int G = 1;
+  int *off = nullptr, *pos = nullptr;
+};
+
+static int spgemm_numeric(Sim *s, const Product &pr, int n, const int *lrp, const int *lcol,
+                          const double *lval, const int *rrp, const double *rval, const int *crp,
+                          double *cval) {
+  long long thr = (long long)n * pr.G;
+  DP_SWITCH_G2(pr.G, DP_LAUNCH(s, k_spgemm_numeric<GG>, nblk(thr), kBlock, 0, n, lrp, lcol, lval,
+                               rrp, rval, pr.off, pr.pos, crp, cval));
   return DP_OK;
 }
 
 static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const int *rrp,
                            const int *rcol, int **crp_out, int **ccol_out, int *nnz_out,
-                           int *lanes) {
+                           Product *prod) {
   int *ub = (int *)dalloc(s, (size_t)(n + 1) * 4), *off = (int *)dalloc(s, (size_t)(n + 1) * 4);
   int *crp = (int *)dalloc(s, (size_t)(n + 1) * 4);
   if (!ub || !off || !crp) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   DP_LAUNCH(s, k_spgemm_ub, nblk(n), kBlock, 0, n, lrp, lcol, rrp, ub);
   int tot = 0;
   DP_TRY(scan_i32(s, ub, off, n, &tot));
-  *lanes = lanes_for(n > 0 ? (double)tot / n : 0.0);
+  prod->G = lanes_for(n > 0 ? (double)tot / n : 0.0);
   int *scratch = (int *)dalloc(s, (size_t)std::max(tot, 1) * 4);
   if (!scratch) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   DP_LAUNCH(s, k_spgemm_expand, nblk(n, 64), 64, 0, n, lrp, lcol, rrp, rcol, off, scratch, ub);
@@ -540,7 +568,11 @@ static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const
   DP_CUDA(s, cudaGetLastError());
   dfree(s, scratch);
   dfree(s, ub);
-  dfree(s, off);
+  prod->off = off;
+  prod->pos = (int *)dalloc(s, (size_t)std::max(tot, 1) * 4);
+  if (!prod->pos) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  DP_LAUNCH(s, k_spgemm_positions, nblk(n), kBlock, 0, n, lrp, lcol, rrp, rcol, off, crp, ccol,
+            prod->pos);
   *crp_out = crp;
   *ccol_out = ccol;
   *nnz_out = nnz;
@@ -548,6 +580,19 @@ static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const
 }
 
 // ---------------------------------------------------------------- hierarchy
+
+// inverse diagonal of a level operator (0 where the diagonal is zero)
+__global__ void k_level_dinv(int n, const int *dpos, const double *val, double *dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = dpos[i] >= 0 ? val[dpos[i]] : 0.0;
+  dinv[i] = d != 0.0 ? 1.0 / d : 0.0;
+}
+
+int level_dinv(Sim *s, Level &L) {
+  if (L.dpos) DP_LAUNCH(s, k_level_dinv, nblk(L.n), kBlock, 0, L.n, L.dpos, L.val, L.dinv);
+  return DP_OK;
+}
 
 static int level_prepare(Sim *s, Level &L) {
   int n = L.n;
@@ -583,10 +628,12 @@ static int level_numeric(Sim *s, Level &L, Level &N) {
   DP_LAUNCH(s, k_p_values, nblk(n), kBlock, 0, n, L.rowptr, L.col, L.strong, L.val, L.fdiag,
             L.agg, s->omega, L.p_rowptr, L.p_col, L.p_val);
   DP_LAUNCH(s, k_gather, nblk(L.r_nnz), kBlock, 0, L.r_nnz, L.r_src, L.p_val, L.r_val);
-  DP_TRY(spgemm_numeric(s, L.ap_G, n, L.rowptr, L.col, L.val, L.p_rowptr, L.p_col, L.p_val,
-                        L.ap_rowptr, L.ap_col, L.ap_val));
-  DP_TRY(spgemm_numeric(s, L.rap_G, L.nagg, L.r_rowptr, L.r_col, L.r_val, L.ap_rowptr, L.ap_col,
-                        L.ap_val, N.rowptr, N.col, N.val));
+  Product ap{L.ap_G, L.ap_off, L.ap_pos}, rap{L.rap_G, L.rap_off, L.rap_pos};
+  DP_TRY(spgemm_numeric(s, ap, n, L.rowptr, L.col, L.val, L.p_rowptr, L.p_val, L.ap_rowptr,
+                        L.ap_val));
+  DP_TRY(spgemm_numeric(s, rap, L.nagg, L.r_rowptr, L.r_col, L.r_val, L.ap_rowptr, L.ap_val,
+                        N.rowptr, N.val));
+  DP_TRY(level_dinv(s, N));
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
@@ -624,11 +671,15 @@ int amg_setup(Sim *s) {
   L0.rowptr = s->A.rowptr;
   L0.col = s->A.col;
   L0.val = s->ap;
+  L0.dinv = (double *)dalloc(s, (size_t)L0.n * 8);
+  L0.dinvf = (float *)dalloc(s, (size_t)L0.n * 4);
+  if (!L0.dinv || !L0.dinvf) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   s->lev.push_back(L0);
   int maxlev = std::min(std::max(o.amg_max_levels, 1), 30);
   for (int l = 0;; ++l) {
     Level &L = s->lev[l];
     DP_TRY(level_prepare(s, L));
+    DP_TRY(level_dinv(s, L));
     phase(s, "prepare", l, tp);
     L.agg = (int *)dalloc(s, (size_t)L.n * 4);
     if (!L.agg) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
@@ -710,13 +761,19 @@ int amg_setup(Sim *s) {
     dfree(s, fill);
     phase(s, "P, R", l, tp);
     // AP = A P and A_c = R (A P) patterns
+    Product pap, prap;
     DP_TRY(spgemm_symbolic(s, n, L.rowptr, L.col, L.p_rowptr, L.p_col, &L.ap_rowptr, &L.ap_col,
-                           &L.ap_nnz, &L.ap_G));
+                           &L.ap_nnz, &pap));
+    L.ap_G = pap.G; L.ap_off = pap.off; L.ap_pos = pap.pos;
     L.ap_val = (double *)dalloc(s, (size_t)std::max(L.ap_nnz, 1) * 8);
     Level N;
     N.n = na;
     DP_TRY(spgemm_symbolic(s, na, L.r_rowptr, L.r_col, L.ap_rowptr, L.ap_col, &N.rowptr, &N.col,
-                           &N.nnz, &L.rap_G));
+                           &N.nnz, &prap));
+    L.rap_G = prap.G; L.rap_off = prap.off; L.rap_pos = prap.pos;
+    N.dinv = (double *)dalloc(s, (size_t)std::max(na, 1) * 8);
+    N.dinvf = (float *)dalloc(s, (size_t)std::max(na, 1) * 4);
+    if (!N.dinv || !N.dinvf) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
     L.p_G = lanes_for((double)L.p_nnz / n);
     L.r_G = lanes_for((double)L.p_nnz / na);
     N.val = (double *)dalloc(s, (size_t)std::max(N.nnz, 1) * 8);
@@ -731,11 +788,13 @@ int amg_setup(Sim *s) {
   s->lev[0].valf = (float *)dalloc(s, (size_t)s->lev[0].nnz * 4);
   if (!s->lev[0].valf) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   DP_TRY(coarse_factor(s));
+  DP_TRY(cluster_setup(s));
   s->amg_ready = true;
   return DP_OK;
 }
 
 int amg_refresh(Sim *s) {
+  DP_TRY(level_dinv(s, s->lev[0]));
   for (size_t l = 0; l + 1 < s->lev.size(); ++l) DP_TRY(level_numeric(s, s->lev[l], s->lev[l + 1]));
   DP_TRY(coarse_factor(s));
   return DP_OK;
@@ -747,11 +806,15 @@ void amg_free(Sim *s) {
     void *ptrs[] = {L.dpos, L.tpos, L.strong, L.agg, L.colour, L.clist, L.fdiag, L.ratio,
                     L.p_rowptr, L.p_col, L.p_val, L.p_valf, L.r_rowptr, L.r_col, L.r_src,
                     L.r_val, L.r_valf, L.ap_rowptr, L.ap_col, L.ap_val, L.x, L.b, L.r,
-                    L.xf, L.bf, L.rf, L.valf};
+                    L.xf, L.bf, L.rf, L.valf, L.dinv, L.dinvf, L.ap_off, L.ap_pos, L.rap_off,
+                    L.cstart_dev, L.ell_col, L.ell_src, L.ell_off, L.ell_K, L.ell_val,
+                    L.ell_valf,
+                    L.rap_pos};
     for (void *p : ptrs) if (p) dfree(s, p);
     if (l > 0) { dfree(s, L.rowptr); dfree(s, L.col); dfree(s, L.val); }
   }
   s->lev.clear();
+  s->cl_level = -1;
   if (s->coarse_lu) dfree(s, s->coarse_lu);
   if (s->coarse_piv) dfree(s, s->coarse_piv);
   s->coarse_lu = nullptr;

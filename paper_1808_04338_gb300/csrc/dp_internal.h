@@ -62,6 +62,11 @@ struct Level {
   int *colour = nullptr, ncolour = 0;
   int *clist = nullptr;                  // rows sorted by (colour, index)
   std::vector<int> cstart;               // host: colour c rows clist[cstart[c]..cstart[c+1])
+  int *cstart_dev = nullptr;             // the same on the device
+  int *ell_col = nullptr, *ell_src = nullptr, *ell_off = nullptr, *ell_K = nullptr;
+  double *ell_val = nullptr;             // padded per-colour copy (cluster cycle)
+  float *ell_valf = nullptr;
+  long long ell_total = 0;
   double *fdiag = nullptr, *ratio = nullptr;
   // prolongator P (n x nagg), restriction R = P^T (nagg x n), AP = A P
   int p_nnz = 0, r_nnz = 0, ap_nnz = 0;
@@ -73,6 +78,9 @@ struct Level {
   float *r_valf = nullptr;
   int *ap_rowptr = nullptr, *ap_col = nullptr;
   double *ap_val = nullptr;
+  double *dinv = nullptr;                 // 1 / a_ii
+  float *dinvf = nullptr;
+  int *ap_off = nullptr, *ap_pos = nullptr, *rap_off = nullptr, *rap_pos = nullptr;
   // lanes per row of the level kernels (operator, P, R) and of the products
   int G = 1, p_G = 1, r_G = 1, ap_G = 1, rap_G = 1;
   // V-cycle work vectors
@@ -124,6 +132,7 @@ int colour_lists(Sim *s, int n, const int *colour, int ncolour, int *clist,
                  std::vector<int> &cstart, int *iperm_or_null);
 int amg_setup(Sim *s);
 int amg_refresh(Sim *s);
+int level_dinv(Sim *s, Level &L);
 void amg_free(Sim *s);
 
 // dp_la.cu (linear algebra of the Krylov loop and the preconditioner)
@@ -140,6 +149,12 @@ int la_alloc(Sim *s);
 int mixed_refresh(Sim *s);
 int lanes_for(double mean_len);
 void graphs_free(Sim *s);
+
+// dp_cycle.cu (the coarse levels of the V-cycle in one cluster launch)
+constexpr int kClusterMaxRows = 20000;
+int cluster_setup(Sim *s);
+int cluster_refresh(Sim *s);
+template <typename T> int coarse_cycle(Sim *s, int l0, const T *b, T *x);
 
 struct Timing {
   int kernel_id = -1;            // hashed name being timed, -1 none
@@ -178,6 +193,8 @@ struct Sim {
   double *p = nullptr, *sw = nullptr, *bhp = nullptr;
   double *pn = nullptr, *swn = nullptr, *bhpn = nullptr, *Mn = nullptr;
   double *R = nullptr, *bh = nullptr, *y = nullptr;
+  double *pr = nullptr;                              // cell properties, 7 x nc (SoA)
+  double *Macc = nullptr;                            // phase masses at the iterate, 2 x nc
   double dt = 1.0, inv_dt = 1.0;
   double *norm_part = nullptr;                       // reduction partials
   double *norm_out = nullptr;                        // 8 doubles
@@ -192,14 +209,18 @@ struct Sim {
   int *lu_rowptr = nullptr, *lu_col = nullptr, *lu_src = nullptr, *lu_dpos = nullptr;
   double *lu_val = nullptr;
   float *lu_valf = nullptr;
+  int *upd_ptr = nullptr, *upd_e2 = nullptr, *upd_q = nullptr;   // IKJ update lists
   std::vector<int> lu_cstart;
   // AMG hierarchy (level 0 shares the block pattern)
   std::vector<Level> lev;
   bool amg_ready = false;
   double *ap = nullptr;                              // pressure values (nnzb)
+  double *ap01 = nullptr;                            // decoupled (0,1) entries (nnzb)
   double *coarse_lu = nullptr;
   int *coarse_piv = nullptr;
   int coarse_n = 0;
+  int cl_level = -1, cl_size = 0;                    // first level of the cluster cycle
+  void *cl_lev64 = nullptr, *cl_lev32 = nullptr;     // device level descriptors
   double *omega = nullptr;                           // device scalars
   unsigned long long *rho_bits = nullptr;
   int *counter = nullptr, *h_counter = nullptr;      // device / pinned host
@@ -211,6 +232,7 @@ struct Sim {
   double *h_res = nullptr;                           // pinned host scalars
   int dot_blocks = 0;
   double *z1 = nullptr, *r1 = nullptr, *rp = nullptr, *xp = nullptr;
+  float *zf = nullptr;                               // FP32 ILU vector (precision 1)
   // CUDA graphs of the FGMRES iterations j = 0..m-1 (captured on first use)
   std::vector<cudaGraphExec_t> graph;
   std::vector<long long> graph_launches;

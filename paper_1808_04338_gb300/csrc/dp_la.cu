@@ -15,16 +15,26 @@ namespace dp {
 // the two halves of the same 32-byte block), x_j (16 bytes, shared by the
 // pair) and accumulates its own output with FMAs, so no FP64 reduction
 // across lanes is needed.  A warp covers 16 block rows.
+//
+// Row order: pairs [0, nL) take the fracture rows 2q, pairs [nL, nc) the
+// matrix rows, the rest the well rows, so that a warp holds rows of one
+// length (8 blocks for an interior fracture row, 2 for a matrix row).
+__device__ __forceinline__ int row_of_pair(int q, int nL, int nc) {
+  return q < nL ? 2 * q : (q < nc ? 2 * (q - nL) + 1 : q);
+}
+
 template <int MODE>  // MODE 0: y = A x; 1: y = b - A x
-__global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, const int *__restrict__ rowptr,
+__global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
+                                                     const int *__restrict__ rowptr,
                                                      const int *__restrict__ col,
                                                      const double *__restrict__ val,
                                                      const double *__restrict__ x,
                                                      const double *__restrict__ b,
                                                      double *__restrict__ y) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = t >> 1, comp = t & 1;
-  if (row >= n) return;
+  int comp = t & 1;
+  if ((t >> 1) >= n) return;
+  int row = row_of_pair(t >> 1, nL, nc);
   int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
   const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
@@ -39,39 +49,41 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, const int *__restric
   y[2 * (size_t)row + comp] = MODE == 0 ? s : b[2 * (size_t)row + comp] - s;
 }
 
-// Pressure component of b - A x: rp_i = b_{i,0} - sum_j (a00 x_j0 + a01 x_j1)
-// (reads the first half of every block only).
-__global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, const int *__restrict__ rowptr,
+// Pressure component of b - A x: rp_i = b_{i,0} - sum_j (a00 x_j0 + a01 x_j1),
+// from the contiguous copies of the (0,0) and (0,1) entries that the
+// decoupling writes (the 2x2 blocks would be read half-used).
+__global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
+                                                       const int *__restrict__ rowptr,
                                                        const int *__restrict__ col,
-                                                       const double *__restrict__ val,
+                                                       const double *__restrict__ a00,
+                                                       const double *__restrict__ a01,
                                                        const double *__restrict__ x,
                                                        const double *__restrict__ b,
                                                        double *__restrict__ rp) {
-  int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int row = row_of_pair(t, nL, nc);
   int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
-  const double2 *v2 = reinterpret_cast<const double2 *>(val);
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
   double s = 0.0;
 #pragma unroll 4
   for (int e = e0; e < e1; ++e) {
-    double2 a = __ldg(v2 + 2 * (size_t)e);
     double2 xj = __ldg(x2 + __ldg(col + e));
-    s = fma(a.x, xj.x, s);
-    s = fma(a.y, xj.y, s);
+    s = fma(__ldg(a00 + e), xj.x, s);
+    s = fma(__ldg(a01 + e), xj.y, s);
   }
   rp[row] = b[2 * (size_t)row] - s;
 }
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
-  DP_LAUNCH(s, k_bsr_spmv<0>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->A.rowptr, s->A.col,
-            s->A.val, x, nullptr, y);
+  DP_LAUNCH(s, k_bsr_spmv<0>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
+            s->A.rowptr, s->A.col, s->A.val, x, nullptr, y);
   return DP_OK;
 }
 
 int bsr_residual(Sim *s, const double *b, const double *x, double *r) {
-  DP_LAUNCH(s, k_bsr_spmv<1>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->A.rowptr, s->A.col,
-            s->A.val, x, b, r);
+  DP_LAUNCH(s, k_bsr_spmv<1>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
+            s->A.rowptr, s->A.col, s->A.val, x, b, r);
   return DP_OK;
 }
 
@@ -105,108 +117,147 @@ __global__ void k_lu_pattern(int n, const int *perm, const int *iperm, const int
   for (int t = 0; t < m; ++t) if (lu_col[d0 + t] == i) lu_dpos[r] = d0 + t;
 }
 
-__device__ __forceinline__ void mul2(const double *a, const double *b, double *o) {
-  double t0 = a[0] * b[0] + a[1] * b[2];
-  double t1 = a[0] * b[1] + a[1] * b[3];
-  double t2 = a[2] * b[0] + a[3] * b[2];
-  double t3 = a[2] * b[1] + a[3] * b[3];
+// Two-component vector type of a value type (16-byte double2 or 8-byte
+// float2 loads of one row of a 2x2 block).
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+
+template <typename T>
+__device__ __forceinline__ void mul2(const T *a, const T *b, T *o) {
+  T t0 = a[0] * b[0] + a[1] * b[2];
+  T t1 = a[0] * b[1] + a[1] * b[3];
+  T t2 = a[2] * b[0] + a[3] * b[2];
+  T t3 = a[2] * b[1] + a[3] * b[3];
   o[0] = t0; o[1] = t1; o[2] = t2; o[3] = t3;
 }
 
-__device__ __forceinline__ void inv2(double *a) {
-  double det = a[0] * a[3] - a[1] * a[2];
-  double id = 1.0 / det;
-  double o0 = a[3] * id, o1 = -a[1] * id, o2 = -a[2] * id, o3 = a[0] * id;
+template <typename T>
+__device__ __forceinline__ void inv2(T *a) {
+  T det = a[0] * a[3] - a[1] * a[2];
+  T id = T(1) / det;
+  T o0 = a[3] * id, o1 = -a[1] * id, o2 = -a[2] * id, o3 = a[0] * id;
   a[0] = o0; a[1] = o1; a[2] = o2; a[3] = o3;
 }
 
-// IKJ block ILU(0) of the rows [r0, r1) of one colour: all their L blocks
-// refer to rows of earlier colours, which are final.
-__global__ void k_ilu_factor(int r0, int r1, const int *perm, const int *iperm,
-                             const int *lu_rowptr, const int *lu_col, const int *lu_src,
-                             const int *lu_dpos, const double *aval, double *lu) {
+// Update lists of the IKJ factorisation, built once from the pattern: for
+// every L block e = (i, k) of a row, the pairs (e2, q) such that block e2 =
+// (i, j) of the same row, j after k in the ordering, receives
+// A_ij -= L_ik U_kj with q the position of U_kj in row k.
+__device__ __forceinline__ int find_in(const int *col, int lo, int hi, int c) {
+  for (int t = lo; t < hi; ++t) if (col[t] == c) return t;
+  return -1;
+}
+
+__global__ void k_ilu_upd(int n, int fill, const int *iperm, const int *lu_rowptr,
+                          const int *lu_col, const int *lu_dpos, const int *upd_ptr, int *cnt,
+                          int *upd_e2, int *upd_q) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int s1 = lu_rowptr[r + 1], dp = lu_dpos[r];
+  for (int e = lu_rowptr[r]; e < dp; ++e) {
+    int rk = iperm[lu_col[e]];
+    int ku0 = lu_dpos[rk] + 1, ku1 = lu_rowptr[rk + 1];
+    int c = 0, base = fill ? upd_ptr[e] : 0;
+    for (int e2 = e + 1; e2 < s1; ++e2) {
+      int q = find_in(lu_col, ku0, ku1, lu_col[e2]);
+      if (q < 0) continue;
+      if (fill) { upd_e2[base + c] = e2; upd_q[base + c] = q; }
+      ++c;
+    }
+    if (!fill) cnt[e] = c;
+  }
+}
+
+// IKJ block ILU(0) of the rows [r0, r1) of one colour, in precision T: all
+// their L blocks refer to rows of earlier colours, which are final.
+template <typename T>
+__global__ void k_ilu_factor(int r0, int r1, const int *iperm, const int *lu_rowptr,
+                             const int *lu_col, const int *lu_src, const int *lu_dpos,
+                             const int *upd_ptr, const int *upd_e2, const int *upd_q,
+                             const double *aval, T *lu) {
   int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= r1) return;
   int s0 = lu_rowptr[r], s1 = lu_rowptr[r + 1], dp = lu_dpos[r];
   for (int e = s0; e < s1; ++e) {
     const double *src = aval + 4 * (size_t)lu_src[e];
-    double *dst = lu + 4 * (size_t)e;
-    dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+    T *dst = lu + 4 * (size_t)e;
+    dst[0] = T(src[0]); dst[1] = T(src[1]); dst[2] = T(src[2]); dst[3] = T(src[3]);
   }
   for (int e = s0; e < dp; ++e) {
-    int k = lu_col[e], rk = iperm[k];
-    double lik[4];
-    mul2(lu + 4 * (size_t)e, lu + 4 * (size_t)lu_dpos[rk], lik);   // A_ik U_kk^-1
-    double *le = lu + 4 * (size_t)e;
+    int rk = iperm[lu_col[e]];
+    T lik[4];
+    mul2<T>(lu + 4 * (size_t)e, lu + 4 * (size_t)lu_dpos[rk], lik);   // A_ik U_kk^-1
+    T *le = lu + 4 * (size_t)e;
     le[0] = lik[0]; le[1] = lik[1]; le[2] = lik[2]; le[3] = lik[3];
-    int ku0 = lu_dpos[rk] + 1, ku1 = lu_rowptr[rk + 1];
-    for (int e2 = e + 1; e2 < s1; ++e2) {
-      int j = lu_col[e2];
-      int q = -1;
-      for (int t = ku0; t < ku1; ++t) if (lu_col[t] == j) { q = t; break; }
-      if (q < 0) continue;
-      double u[4];
-      mul2(lik, lu + 4 * (size_t)q, u);
-      double *aij = lu + 4 * (size_t)e2;
+    for (int p = upd_ptr[e]; p < upd_ptr[e + 1]; ++p) {
+      T u[4];
+      mul2<T>(lik, lu + 4 * (size_t)upd_q[p], u);
+      T *aij = lu + 4 * (size_t)upd_e2[p];
       aij[0] -= u[0]; aij[1] -= u[1]; aij[2] -= u[2]; aij[3] -= u[3];
     }
   }
-  inv2(lu + 4 * (size_t)dp);
+  inv2<T>(lu + 4 * (size_t)dp);
 }
 
 // Forward sweep of one colour, two lanes per row (one per component):
-// z_i = r_i - sum_{L} L_ik z_k (unit lower triangle).
+// z_i = r_i - sum_{L} L_ik z_k (unit lower triangle).  Factor and z in T, the
+// right-hand side in TR.
+template <typename T, typename TR>
 __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *__restrict__ perm,
                                                     const int *__restrict__ lu_rowptr,
                                                     const int *__restrict__ lu_col,
                                                     const int *__restrict__ lu_dpos,
-                                                    const double *__restrict__ lu,
-                                                    const double *__restrict__ rhs, double *z) {
+                                                    const T *__restrict__ lu,
+                                                    const TR *__restrict__ rhs, T *z) {
+  using T2 = typename V2<T>::t;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = r0 + (t >> 1), comp = t & 1;
   if (r >= r1) return;
   int i = __ldg(perm + r);
-  const double2 *v2 = reinterpret_cast<const double2 *>(lu) + comp;
-  const double2 *z2 = reinterpret_cast<const double2 *>(z);
-  double s = 0.0;
+  const T2 *v2 = reinterpret_cast<const T2 *>(lu) + comp;
+  const T2 *z2 = reinterpret_cast<const T2 *>(z);
+  T s = T(0);
   int ea = __ldg(lu_rowptr + r), eb = __ldg(lu_dpos + r);
 #pragma unroll 4
   for (int e = ea; e < eb; ++e) {
-    double2 a = __ldg(v2 + 2 * (size_t)e);
-    double2 xk = z2[__ldg(lu_col + e)];
+    T2 a = __ldg(v2 + 2 * (size_t)e);
+    T2 xk = z2[__ldg(lu_col + e)];
     s = fma(a.x, xk.x, s);
     s = fma(a.y, xk.y, s);
   }
-  z[2 * (size_t)i + comp] = rhs[2 * (size_t)i + comp] - s;
+  z[2 * (size_t)i + comp] = T(rhs[2 * (size_t)i + comp]) - s;
 }
 
 // Backward sweep of one colour: z_i = U_ii^-1 (z_i - sum_{U} U_ij z_j).  The
 // two lanes of a row exchange their partial results for the 2x2 product.
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_ilu_bwd(int r0, int r1, const int *__restrict__ perm,
                                                     const int *__restrict__ lu_rowptr,
                                                     const int *__restrict__ lu_col,
                                                     const int *__restrict__ lu_dpos,
-                                                    const double *__restrict__ lu, double *z) {
+                                                    const T *__restrict__ lu, T *z) {
+  using T2 = typename V2<T>::t;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = r0 + (t >> 1), comp = t & 1;
   bool valid = r < r1;                  // no early exit: the pair shuffles
   int i = valid ? __ldg(perm + r) : 0;
-  const double2 *v2 = reinterpret_cast<const double2 *>(lu);
-  const double2 *z2 = reinterpret_cast<const double2 *>(z);
+  const T2 *v2 = reinterpret_cast<const T2 *>(lu);
+  const T2 *z2 = reinterpret_cast<const T2 *>(z);
   int dp = valid ? __ldg(lu_dpos + r) : 0, eb = valid ? __ldg(lu_rowptr + r + 1) : 0;
-  double s = 0.0;
+  T s = T(0);
 #pragma unroll 4
   for (int e = dp + 1; e < eb; ++e) {
-    double2 a = __ldg(v2 + 2 * (size_t)e + comp);
-    double2 xj = z2[__ldg(lu_col + e)];
+    T2 a = __ldg(v2 + 2 * (size_t)e + comp);
+    T2 xj = z2[__ldg(lu_col + e)];
     s = fma(a.x, xj.x, s);
     s = fma(a.y, xj.y, s);
   }
-  double yi = valid ? z[2 * (size_t)i + comp] - s : 0.0;
-  double yo = __shfl_xor_sync(0xffffffffu, yi, 1);
+  T yi = valid ? z[2 * (size_t)i + comp] - s : T(0);
+  T yo = __shfl_xor_sync(0xffffffffu, yi, 1);
   if (valid) {
-    double y0 = comp == 0 ? yi : yo, y1 = comp == 0 ? yo : yi;
-    double2 d = __ldg(v2 + 2 * (size_t)dp + comp);
+    T y0 = comp == 0 ? yi : yo, y1 = comp == 0 ? yo : yi;
+    T2 d = __ldg(v2 + 2 * (size_t)dp + comp);
     z[2 * (size_t)i + comp] = fma(d.x, y0, d.y * y1);
   }
 }
@@ -235,112 +286,160 @@ int ilu_setup(Sim *s) {
   DP_TRY(scan_i32(s, len, s->lu_rowptr, n, &nnz));
   DP_LAUNCH(s, k_lu_pattern, nblk(n), kBlock, 0, n, s->perm, s->iperm, s->A.rowptr, s->A.col,
             s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos);
+  // update lists of the factorisation
+  int *cnt = (int *)dalloc(s, (size_t)nnz * 4);
+  s->upd_ptr = (int *)dalloc(s, ((size_t)nnz + 1) * 4);
+  if (!cnt || !s->upd_ptr) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  DP_CUDA(s, cudaMemsetAsync(cnt, 0, (size_t)nnz * 4, s->stream));
+  DP_LAUNCH(s, k_ilu_upd, nblk(n), kBlock, 0, n, 0, s->iperm, s->lu_rowptr, s->lu_col, s->lu_dpos,
+            s->upd_ptr, cnt, nullptr, nullptr);
+  int npairs = 0;
+  DP_TRY(scan_i32(s, cnt, s->upd_ptr, nnz, &npairs));
+  s->upd_e2 = (int *)dalloc(s, (size_t)std::max(npairs, 1) * 4);
+  s->upd_q = (int *)dalloc(s, (size_t)std::max(npairs, 1) * 4);
+  if (!s->upd_e2 || !s->upd_q) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  DP_LAUNCH(s, k_ilu_upd, nblk(n), kBlock, 0, n, 1, s->iperm, s->lu_rowptr, s->lu_col, s->lu_dpos,
+            s->upd_ptr, cnt, s->upd_e2, s->upd_q);
   DP_CUDA(s, cudaGetLastError());
+  dfree(s, cnt);
   dfree(s, len);
   return DP_OK;
 }
 
 int ilu_factor(Sim *s) {
+  bool f32 = s->opt.precision == 1;
   for (int c = 0; c < s->ncolour; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
-    if (r1 > r0)
-      DP_LAUNCH(s, k_ilu_factor, nblk(r1 - r0, 128), 128, 0, r0, r1, s->perm, s->iperm,
-                s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos, s->A.val, s->lu_val);
+    if (r1 <= r0) continue;
+    if (f32)
+      DP_LAUNCH(s, k_ilu_factor<float>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->iperm,
+                s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos, s->upd_ptr, s->upd_e2, s->upd_q,
+                s->A.val, s->lu_valf);
+    else
+      DP_LAUNCH(s, k_ilu_factor<double>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->iperm,
+                s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos, s->upd_ptr, s->upd_e2, s->upd_q,
+                s->A.val, s->lu_val);
   }
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
 
-int ilu_apply(Sim *s, const double *r, double *z) {
+// z = (LU)^-1 r with the factor in T; r in TR.
+template <typename T, typename TR>
+static int ilu_apply_t(Sim *s, const T *lu, const TR *r, T *z) {
   for (int c = 0; c < s->ncolour; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 > r0)
-      DP_LAUNCH(s, k_ilu_fwd, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm, s->lu_rowptr,
-                s->lu_col, s->lu_dpos, s->lu_val, r, z);
+      DP_LAUNCH(s, (k_ilu_fwd<T, TR>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
+                s->lu_rowptr, s->lu_col, s->lu_dpos, lu, r, z);
   }
   for (int c = s->ncolour - 1; c >= 0; --c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 > r0)
-      DP_LAUNCH(s, k_ilu_bwd, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm, s->lu_rowptr,
-                s->lu_col, s->lu_dpos, s->lu_val, z);
+      DP_LAUNCH(s, k_ilu_bwd<T>, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
+                s->lu_rowptr, s->lu_col, s->lu_dpos, lu, z);
   }
   return DP_OK;
 }
 
+int ilu_apply(Sim *s, const double *r, double *z) { return ilu_apply_t<double, double>(s, s->lu_val, r, z); }
+
 // ---------------------------------------------------------------- AMG cycle
 
-// Scalar CSR kernels of the AMG levels: G lanes per row (G chosen per level
-// from its mean row length), partial sums combined with shuffles inside the
-// group; every lane reaches the shuffles (no early exit).
-template <int G>
-__device__ __forceinline__ double group_sum(double v) {
+// Scalar CSR kernels of the AMG levels in precision T: G lanes per row (G
+// chosen per level from its mean row length), partial sums combined with
+// shuffles inside the group; every lane reaches the shuffles (no early exit).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
   return v;
 }
 
-// One colour of Gauss-Seidel: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii.
-template <int G>
+// Row dot product sum_e val[e] x[col[e]] over the lane's entries e0+lane,
+// e0+lane+G, ...: four independent accumulators keep four loads in flight
+// per lane, so a long row is not one serial chain of dependent loads.
+template <int G, typename T>
+__device__ __forceinline__ T row_dot(int e0, int e1, int lane, const int *__restrict__ col,
+                                     const T *__restrict__ val, const T *__restrict__ x) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int e = e0 + lane;
+  for (; e + 3 * G < e1; e += 4 * G) {
+    int c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
+        c3 = __ldg(col + e + 3 * G);
+    T v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G),
+      v3 = __ldg(val + e + 3 * G);
+    s0 = fma(v0, x[c0], s0);
+    s1 = fma(v1, x[c1], s1);
+    s2 = fma(v2, x[c2], s2);
+    s3 = fma(v3, x[c3], s3);
+  }
+  for (; e < e1; e += G) s0 = fma(__ldg(val + e), x[__ldg(col + e)], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// One colour of Gauss-Seidel: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii,
+// evaluated as x_i + (b_i - (A x)_i) / a_ii with 1/a_ii precomputed per level
+// (0 where a_ii = 0: the row is left as is).
+template <int G, typename T>
 __global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int *__restrict__ clist,
                                                       const int *__restrict__ rowptr,
                                                       const int *__restrict__ col,
-                                                      const double *__restrict__ val,
-                                                      const int *__restrict__ dpos,
-                                                      const double *__restrict__ b, double *x) {
+                                                      const T *__restrict__ val,
+                                                      const T *__restrict__ dinv,
+                                                      const T *__restrict__ b, T *x) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int q = r0 + t / G, lane = t % G;
   bool valid = q < r1;
   int i = valid ? clist[q] : 0;
-  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0, dp = valid ? dpos[i] : -1;
-  double s = 0.0, d = 0.0;
-  for (int e = e0 + lane; e < e1; e += G) {
-    double a = val[e];
-    if (e == dp) d = a;
-    else s = fma(a, x[col[e]], s);
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) {
+    T di = dinv[i];
+    if (di != T(0)) x[i] = fma(b[i] - s, di, x[i]);
   }
-  if (G > 1) { s = group_sum<G>(s); d = group_sum<G>(d); }
-  if (valid && lane == 0 && d != 0.0) x[i] = (b[i] - s) / d;
 }
 
 // r = b - A x
-template <int G>
+template <int G, typename T>
 __global__ void __launch_bounds__(kBlock) k_csr_resid(int n, const int *__restrict__ rowptr,
                                                       const int *__restrict__ col,
-                                                      const double *__restrict__ val,
-                                                      const double *__restrict__ b,
-                                                      const double *__restrict__ x,
-                                                      double *__restrict__ r) {
+                                                      const T *__restrict__ val,
+                                                      const T *__restrict__ b,
+                                                      const T *__restrict__ x, T *__restrict__ r) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int i = t / G, lane = t % G;
   bool valid = i < n;
   int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
-  double s = 0.0;
-  for (int e = e0 + lane; e < e1; e += G) s = fma(val[e], x[col[e]], s);
-  if (G > 1) s = group_sum<G>(s);
+  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  if (G > 1) s = group_sum<G, T>(s);
   if (valid && lane == 0) r[i] = b[i] - s;
 }
 
 // y = A x (add = 0) or y += A x (add = 1)
-template <int G>
+template <int G, typename T>
 __global__ void __launch_bounds__(kBlock) k_csr_mv(int n, const int *__restrict__ rowptr,
                                                    const int *__restrict__ col,
-                                                   const double *__restrict__ val,
-                                                   const double *__restrict__ x,
-                                                   double *__restrict__ y, int add) {
+                                                   const T *__restrict__ val,
+                                                   const T *__restrict__ x, T *__restrict__ y,
+                                                   int add) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int i = t / G, lane = t % G;
   bool valid = i < n;
   int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
-  double s = 0.0;
-  for (int e = e0 + lane; e < e1; e += G) s = fma(val[e], x[col[e]], s);
-  if (G > 1) s = group_sum<G>(s);
+  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  if (G > 1) s = group_sum<G, T>(s);
   if (valid && lane == 0) y[i] = add ? y[i] + s : s;
 }
 
-// lanes per row for a mean row length
+// Lanes per row for a mean row length: enough lanes that each walks about
+// eight entries (two rounds of four loads in flight), no more, because on
+// GB300 FP64 issue is scarce (1.2 TFLOP/s for the whole GPU) and every lane
+// of a group takes part in the log2(G) shuffle additions.
 int lanes_for(double mean_len) {
   int g = 1;
-  while (g < 32 && 2.0 * g < mean_len) g *= 2;
+  while (g < 32 && 8.0 * g < mean_len) g *= 2;
   return g;
 }
 
@@ -354,17 +453,41 @@ int lanes_for(double mean_len) {
     default: { constexpr int GG = 32; LAUNCH; } break; \
   }
 
-static int csr_resid(Sim *s, const Level &L, const double *b, const double *x, double *r) {
+// The arrays of a level in precision T.
+template <typename T> struct LV;
+template <> struct LV<double> {
+  static const double *val(const Level &L) { return L.val; }
+  static const double *dinv(const Level &L) { return L.dinv; }
+  static const double *pval(const Level &L) { return L.p_val; }
+  static const double *rval(const Level &L) { return L.r_val; }
+  static double *x(const Level &L) { return L.x; }
+  static double *b(const Level &L) { return L.b; }
+  static double *r(const Level &L) { return L.r; }
+};
+template <> struct LV<float> {
+  static const float *val(const Level &L) { return L.valf; }
+  static const float *dinv(const Level &L) { return L.dinvf; }
+  static const float *pval(const Level &L) { return L.p_valf; }
+  static const float *rval(const Level &L) { return L.r_valf; }
+  static float *x(const Level &L) { return L.xf; }
+  static float *b(const Level &L) { return L.bf; }
+  static float *r(const Level &L) { return L.rf; }
+};
+
+template <typename T>
+static int csr_resid(Sim *s, const Level &L, const T *b, const T *x, T *r) {
   long long thr = (long long)L.n * L.G;
-  DP_SWITCH_G(L.G, DP_LAUNCH(s, k_csr_resid<GG>, nblk(thr), kBlock, 0, L.n, L.rowptr, L.col,
-                             L.val, b, x, r));
+  DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_csr_resid<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr, L.col,
+                             LV<T>::val(L), b, x, r));
   return DP_OK;
 }
 
-static int csr_mv(Sim *s, int n, int G, const int *rowptr, const int *col, const double *val,
-                  const double *x, double *y, int add) {
+template <typename T>
+static int csr_mv(Sim *s, int n, int G, const int *rowptr, const int *col, const T *val,
+                  const T *x, T *y, int add) {
   long long thr = (long long)n * G;
-  DP_SWITCH_G(G, DP_LAUNCH(s, k_csr_mv<GG>, nblk(thr), kBlock, 0, n, rowptr, col, val, x, y, add));
+  DP_SWITCH_G(G, DP_LAUNCH(s, (k_csr_mv<GG, T>), nblk(thr), kBlock, 0, n, rowptr, col, val, x, y,
+                           add));
   return DP_OK;
 }
 
@@ -423,31 +546,36 @@ __global__ void __launch_bounds__(1024) k_dense_lu(int n, double *a, int *piv) {
   }
 }
 
+constexpr int kDenseMax = 4096;
+
+// Solve with the FP64 LU factors; b and x in T, the solve itself in FP64 in
+// shared memory.
+template <typename T>
 __global__ void __launch_bounds__(1024) k_dense_solve(int n, const double *a, const int *piv,
-                                                      const double *b, double *x) {
+                                                      const T *b, T *x) {
+  __shared__ double xs[kDenseMax];
   int t = threadIdx.x, nt = blockDim.x;
-  for (int i = t; i < n; i += nt) x[i] = b[i];
+  for (int i = t; i < n; i += nt) xs[i] = double(b[i]);
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (t == 0) {
       int p = piv[k];
-      if (p != k && p >= 0 && p < n) { double tmp = x[k]; x[k] = x[p]; x[p] = tmp; }
+      if (p != k && p >= 0 && p < n) { double tmp = xs[k]; xs[k] = xs[p]; xs[p] = tmp; }
     }
     __syncthreads();
-    double xk = x[k];
-    for (int i = k + 1 + t; i < n; i += nt) x[i] -= a[(size_t)i * n + k] * xk;
+    double xk = xs[k];
+    for (int i = k + 1 + t; i < n; i += nt) xs[i] -= a[(size_t)i * n + k] * xk;
     __syncthreads();
   }
   for (int i = n - 1; i >= 0; --i) {
-    if (t == 0) { double d = a[(size_t)i * n + i]; x[i] = d != 0.0 ? x[i] / d : 0.0; }
+    if (t == 0) { double d = a[(size_t)i * n + i]; xs[i] = d != 0.0 ? xs[i] / d : 0.0; }
     __syncthreads();
-    double xi = x[i];
-    for (int r = t; r < i; r += nt) x[r] -= a[(size_t)r * n + i] * xi;
+    double xi = xs[i];
+    for (int r = t; r < i; r += nt) xs[r] -= a[(size_t)r * n + i] * xi;
     __syncthreads();
   }
+  for (int i = t; i < n; i += nt) x[i] = T(xs[i]);
 }
-
-constexpr int kDenseMax = 4096;
 
 int coarse_factor(Sim *s) {
   Level &L = s->lev.back();
@@ -467,72 +595,115 @@ int coarse_factor(Sim *s) {
   return DP_OK;
 }
 
-static int gs_sweep(Sim *s, Level &L, const double *b, double *x, bool forward) {
+template <typename T>
+static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
   for (int t = 0; t < L.ncolour; ++t) {
     int c = forward ? t : L.ncolour - 1 - t;
     int r0 = L.cstart[c], r1 = L.cstart[c + 1];
     if (r1 > r0) {
       long long thr = (long long)(r1 - r0) * L.G;
-      DP_SWITCH_G(L.G, DP_LAUNCH(s, k_gs_colour<GG>, nblk(thr), kBlock, 0, r0, r1, L.clist,
-                                 L.rowptr, L.col, L.val, L.dpos, b, x));
+      DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_gs_colour<GG, T>), nblk(thr), kBlock, 0, r0, r1, L.clist,
+                                 L.rowptr, L.col, LV<T>::val(L), LV<T>::dinv(L), b, x));
     }
   }
   return DP_OK;
 }
 
-int vcycle(Sim *s, int l, const double *b, double *x) {
+// V(1,1) cycle from level l in precision T: pre-smoothing (colours forward),
+// residual, restriction, coarse correction, prolongation, post-smoothing
+// (colours reversed); dense LU on the coarsest level.
+template <typename T>
+static int vcycle_t(Sim *s, int l, const T *b, T *x) {
+  if (l == s->cl_level) return coarse_cycle<T>(s, l, b, x);
   Level &L = s->lev[l];
   int n = L.n;
   if (l == (int)s->lev.size() - 1) {
     if (s->coarse_n == n && n > 0) {
-      DP_LAUNCH(s, k_dense_solve, 1, 1024, 0, n, s->coarse_lu, s->coarse_piv, b, x);
+      DP_LAUNCH(s, k_dense_solve<T>, 1, 1024, 0, n, s->coarse_lu, s->coarse_piv, b, x);
       return DP_OK;
     }
-    DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * 8, s->stream));
-    DP_TRY(gs_sweep(s, L, b, x, true));
-    DP_TRY(gs_sweep(s, L, b, x, false));
+    DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), s->stream));
+    DP_TRY(gs_sweep<T>(s, L, b, x, true));
+    DP_TRY(gs_sweep<T>(s, L, b, x, false));
     return DP_OK;
   }
   Level &N = s->lev[l + 1];
-  DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * 8, s->stream));
-  DP_TRY(gs_sweep(s, L, b, x, true));
-  DP_TRY(csr_resid(s, L, b, x, L.r));
-  DP_TRY(csr_mv(s, N.n, L.r_G, L.r_rowptr, L.r_col, L.r_val, L.r, N.b, 0));
-  DP_TRY(vcycle(s, l + 1, N.b, N.x));
-  DP_TRY(csr_mv(s, n, L.p_G, L.p_rowptr, L.p_col, L.p_val, N.x, x, 1));
-  DP_TRY(gs_sweep(s, L, b, x, false));
+  T *r = LV<T>::r(L), *nb = LV<T>::b(N), *nx = LV<T>::x(N);
+  DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), s->stream));
+  DP_TRY(gs_sweep<T>(s, L, b, x, true));
+  DP_TRY(csr_resid<T>(s, L, b, x, r));
+  DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, L.r_col, LV<T>::rval(L), r, nb, 0));
+  DP_TRY(vcycle_t<T>(s, l + 1, nb, nx));
+  DP_TRY(csr_mv<T>(s, n, L.p_G, L.p_rowptr, L.p_col, LV<T>::pval(L), nx, x, 1));
+  DP_TRY(gs_sweep<T>(s, L, b, x, false));
   return DP_OK;
 }
+
+int vcycle(Sim *s, int l, const double *b, double *x) { return vcycle_t<double>(s, l, b, x); }
 
 // ---------------------------------------------------------------- CPR-FPF
 // z1 = F r;  z2 = z1 + P V(R (r - A z1));  z = z2 + F (r - A z2)
 
-__global__ void k_inject_add(int n, const double *xp, double *z) {
+template <typename T>
+__global__ void k_inject_add(int n, const T *xp, double *z) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) z[2 * i] += xp[i];
+  if (i < n) z[2 * i] += double(xp[i]);
 }
 
-__global__ void k_axpy1(long long n, const double *x, double *y) {  // y += x
+template <typename T>
+__global__ void k_axpy1(long long n, const T *x, double *y) {  // y += x
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] += x[i];
+  if (i < n) y[i] += double(x[i]);
+}
+
+__global__ void k_to_f32(long long n, const double *x, float *y) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = float(x[i]);
+}
+
+__global__ void k_to_f64(long long n, const float *x, double *y) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = double(x[i]);
 }
 
 int cpr_apply(Sim *s, const double *r, double *z) {
   int nb = s->A.n;
   long long N = 2LL * nb;
+  bool f32 = s->opt.precision == 1;
   if (s->opt.precond == 0) {
     DP_CUDA(s, cudaMemcpyAsync(z, r, N * 8, cudaMemcpyDeviceToDevice, s->stream));
     return DP_OK;
   }
-  if (s->opt.precond == 1) return ilu_apply(s, r, z);
-  DP_TRY(ilu_apply(s, r, s->z1));
-  DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->A.rowptr, s->A.col, s->A.val, s->z1, r,
-            s->rp);
-  DP_TRY(vcycle(s, 0, s->rp, s->xp));
-  DP_LAUNCH(s, k_inject_add, nblk(nb), kBlock, 0, nb, s->xp, s->z1);
+  if (!f32) {
+    if (s->opt.precond == 1) return ilu_apply(s, r, z);
+    DP_TRY(ilu_apply(s, r, s->z1));
+    DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->A.rowptr, s->A.col,
+              s->ap, s->ap01, s->z1, r, s->rp);
+    DP_TRY(vcycle(s, 0, s->rp, s->xp));
+    DP_LAUNCH(s, k_inject_add<double>, nblk(nb), kBlock, 0, nb, s->xp, s->z1);
+    DP_TRY(bsr_residual(s, r, s->z1, s->r1));
+    DP_TRY(ilu_apply(s, s->r1, z));
+    DP_LAUNCH(s, k_axpy1<double>, nblk(N), kBlock, 0, N, s->z1, z);
+    return DP_OK;
+  }
+  // FP32 factor, FP32 V-cycle; the stage residuals stay in FP64
+  if (s->opt.precond == 1) {
+    DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r, s->zf)));
+    DP_LAUNCH(s, k_to_f64, nblk(N), kBlock, 0, N, s->zf, z);
+    return DP_OK;
+  }
+  Level &L0 = s->lev[0];
+  DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r, s->zf)));
+  DP_LAUNCH(s, k_to_f64, nblk(N), kBlock, 0, N, s->zf, s->z1);
+  DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->A.rowptr, s->A.col,
+            s->ap, s->ap01, s->z1, r, s->rp);
+  DP_LAUNCH(s, k_to_f32, nblk(nb), kBlock, 0, (long long)nb, s->rp, L0.bf);
+  DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
+  DP_LAUNCH(s, k_inject_add<float>, nblk(nb), kBlock, 0, nb, L0.xf, s->z1);
   DP_TRY(bsr_residual(s, r, s->z1, s->r1));
-  DP_TRY(ilu_apply(s, s->r1, z));
-  DP_LAUNCH(s, k_axpy1, nblk(N), kBlock, 0, N, s->z1, z);
+  DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, s->r1, s->zf)));
+  DP_CUDA(s, cudaMemcpyAsync(z, s->z1, N * 8, cudaMemcpyDeviceToDevice, s->stream));
+  DP_LAUNCH(s, k_axpy1<float>, nblk(N), kBlock, 0, N, s->zf, z);
   return DP_OK;
 }
 
@@ -575,12 +746,21 @@ __global__ void __launch_bounds__(kBlock) k_multidot(long long N, const double *
 
 // dots[k] = sum_b part[b][k] (fixed order); mode 1: also add into H[:, j];
 // mode 2: dots[0] = sqrt(sum), H[j+1][j] = it.
-__global__ void k_dot_final(const double *part, int nblocks, int nv, double *dots, double *H,
-                            int m, int j, int mode) {
-  int k = threadIdx.x;
-  if (k >= nv) return;
+// 256 threads: lane k of group g sums the partials of blocks g, g+8, ...;
+// the eight group sums are then added in group order.
+__global__ void __launch_bounds__(256) k_dot_final(const double *part, int nblocks, int nv,
+                                                   double *dots, double *H, int m, int j,
+                                                   int mode) {
+  __shared__ double sh[8][32];
+  int k = threadIdx.x & 31, grp = threadIdx.x >> 5;
   double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) v += part[(size_t)b * 32 + k];
+  if (k < nv)
+    for (int b = grp; b < nblocks; b += 8) v += part[(size_t)b * 32 + k];
+  sh[grp][k] = v;
+  __syncthreads();
+  if (grp != 0 || k >= nv) return;
+  v = 0.0;
+  for (int q = 0; q < 8; ++q) v += sh[q][k];
   if (mode == 2) { v = sqrt(v); dots[0] = v; H[(size_t)(j + 1) * m + j] = v; return; }
   dots[k] = v;
   if (mode == 1) H[(size_t)k * m + j] += v;
@@ -602,11 +782,17 @@ __global__ void __launch_bounds__(kBlock) k_multi_axpy(long long N, const double
   }
 }
 
+// y = x * alpha, or x / alpha (the reciprocal taken once per block: an FP64
+// division is a long instruction sequence on GB300)
 __global__ void k_scale(long long N, const double *x, const double *alpha, int invert, double *y) {
+  __shared__ double sa;
+  if (threadIdx.x == 0) {
+    double a = *alpha;
+    sa = invert ? (a != 0.0 ? 1.0 / a : 0.0) : a;
+  }
+  __syncthreads();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double a = *alpha;
-  if (invert) a = a != 0.0 ? 1.0 / a : 0.0;
-  if (i < N) y[i] = x[i] * a;
+  if (i < N) y[i] = x[i] * sa;
 }
 
 // Givens rotations on column j of the Hessenberg matrix and the rotated
@@ -652,7 +838,7 @@ static int dots(Sim *s, const double *V, long long ldv, int nv, const double *w,
     DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, V + (long long)v0 * ldv, ldv, cnt, w,
               s->dots_part, v0);
   }
-  DP_LAUNCH(s, k_dot_final, 1, 32, 0, s->dots_part, kDotBlocks, nv, s->dots, s->H, s->m, j, mode);
+  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, nv, s->dots, s->H, s->m, j, mode);
   return DP_OK;
 }
 
@@ -660,7 +846,7 @@ static int dots(Sim *s, const double *V, long long ldv, int nv, const double *w,
 static int norm_into(Sim *s, const double *x, double *dst) {
   long long N = 2LL * s->A.n;
   DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, x, 0LL, 1, x, s->dots_part, 0);
-  DP_LAUNCH(s, k_dot_final, 1, 32, 0, s->dots_part, kDotBlocks, 1, dst, s->H, s->m, 0, 0);
+  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, dst, s->H, s->m, 0, 0);
   return DP_OK;
 }
 
@@ -676,12 +862,12 @@ static int arnoldi_step(Sim *s, int j) {
   double *vj = s->V + (long long)j * N, *zj = s->Z + (long long)j * N;
   DP_TRY(cpr_apply(s, vj, zj));
   DP_TRY(bsr_spmv(s, zj, s->w));
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < 2; ++pass) {          // classical Gram-Schmidt, twice
     DP_TRY(dots(s, s->V, N, j + 1, s->w, 1, j));
     DP_LAUNCH(s, k_multi_axpy, gridN, kBlock, 0, N, s->V, N, j + 1, s->dots, -1.0, s->w);
   }
   DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, s->w, 0LL, 1, s->w, s->dots_part, 0);
-  DP_LAUNCH(s, k_dot_final, 1, 32, 0, s->dots_part, kDotBlocks, 1, s->scal + 2, s->H, m, j, 2);
+  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, s->scal + 2, s->H, m, j, 2);
   DP_LAUNCH(s, k_scale, nblk(N), kBlock, 0, N, s->w, s->scal + 2, 1, s->V + (long long)(j + 1) * N);
   DP_LAUNCH(s, k_givens, 1, 32, 0, s->H, s->cs, s->sn, s->g, m, j, s->scal + 3);
   return DP_OK;
@@ -801,14 +987,34 @@ int la_alloc(Sim *s) {
   s->r1 = (double *)dalloc(s, (size_t)N * 8);
   s->rp = (double *)dalloc(s, (size_t)s->A.n * 8);
   s->xp = (double *)dalloc(s, (size_t)s->A.n * 8);
+  s->zf = (float *)dalloc(s, (size_t)N * 4);
   if (!s->V || !s->Z || !s->w || !s->H || !s->cs || !s->sn || !s->g || !s->hy || !s->dots_part ||
-      !s->dots || !s->scal || !s->z1 || !s->r1 || !s->rp || !s->xp) {
+      !s->dots || !s->scal || !s->z1 || !s->r1 || !s->rp || !s->xp || !s->zf) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
   return DP_OK;
 }
 
-int mixed_refresh(Sim *) { return DP_OK; }
+__global__ void k_to_f32_i(long long n, const double *x, float *y) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = float(x[i]);
+}
+
+// FP32 copies of the AMG operators, transfer operators and inverse
+// diagonals (precision 1), refreshed with the FP64 values.
+int mixed_refresh(Sim *s) {
+  for (size_t l = 0; l < s->lev.size(); ++l) {
+    Level &L = s->lev[l];
+    DP_LAUNCH(s, k_to_f32_i, nblk(L.nnz), kBlock, 0, (long long)L.nnz, L.val, L.valf);
+    DP_LAUNCH(s, k_to_f32_i, nblk(L.n), kBlock, 0, (long long)L.n, L.dinv, L.dinvf);
+    if (l + 1 < s->lev.size()) {
+      DP_LAUNCH(s, k_to_f32_i, nblk(L.p_nnz), kBlock, 0, (long long)L.p_nnz, L.p_val, L.p_valf);
+      DP_LAUNCH(s, k_to_f32_i, nblk(L.r_nnz), kBlock, 0, (long long)L.r_nnz, L.r_val, L.r_valf);
+    }
+  }
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
 
 }  // namespace dp

@@ -310,7 +310,11 @@ int phys_build_pattern(Sim *s) {
   s->A.val = (double *)dalloc(s, (size_t)nnz * 32);
   s->trans = (double *)dalloc(s, (size_t)nnz * 8);
   s->ap = (double *)dalloc(s, (size_t)nnz * 8);
-  if (!s->A.col || !s->A.val || !s->trans || !s->ap) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  s->ap01 = (double *)dalloc(s, (size_t)nnz * 8);
+  if (!s->A.col || !s->A.val || !s->trans || !s->ap || !s->ap01) {
+    s->fail(DP_ENOMEM, "allocation failed");
+    return DP_ENOMEM;
+  }
   DP_LAUNCH(s, k_pattern_fill, nblk(P.nb), kBlock, 0, P, s->kf, s->km, d_pc_cell, d_pc_well,
             d_pc_wi, np, d_pw_start, d_pw_cell, d_pw_wi, s->A.rowptr, s->A.col, s->A.diag,
             s->trans);
@@ -324,31 +328,77 @@ int phys_build_pattern(Sim *s) {
 
 // ---------------------------------------------------------------- assembly
 
+// Cell properties stored structure-of-arrays, [k * nc + c]: rho_o, rho_w,
+// lam_o, lam_w, dlam_o, dlam_w, phi.  Evaluated once per cell so that the
+// rows that use a cell as a neighbour read them instead of re-evaluating.
+
+__global__ void __launch_bounds__(kBlock) k_props(Phys P, const double *phi_f, const double *phi_m,
+                                                  const double *p, const double *sw, double *pr) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.nc) return;
+  Props q;
+  props(P, phi_f, phi_m, c, p[c], sw[c], q);
+  size_t n = (size_t)P.nc;
+  pr[c] = q.rho[0];
+  pr[n + c] = q.rho[1];
+  pr[2 * n + c] = q.lam[0];
+  pr[3 * n + c] = q.lam[1];
+  pr[4 * n + c] = q.dlam[0];
+  pr[5 * n + c] = q.dlam[1];
+  pr[6 * n + c] = q.phi;
+}
+
+// The same values as props(): stored fields plus the constant derivatives.
+__device__ __forceinline__ void load_props(const Phys &P, const double *phi_f, const double *phi_m,
+                                           const double *__restrict__ pr, int c, Props &q) {
+  size_t n = (size_t)P.nc;
+  q.rho[0] = pr[c];
+  q.rho[1] = pr[n + c];
+  q.lam[0] = pr[2 * n + c];
+  q.lam[1] = pr[3 * n + c];
+  q.dlam[0] = pr[4 * n + c];
+  q.dlam[1] = pr[5 * n + c];
+  q.phi = pr[6 * n + c];
+  q.drho[0] = P.rho_o_ref * P.c_o;
+  q.drho[1] = P.rho_w_ref * P.c_w;
+  int loc = c >> 1;
+  double phi_ref = (c & 1) == 0 ? phi_f[loc] : phi_m[loc];
+  q.dphi = phi_ref * P.c_rock;
+}
+
 struct AsmArgs {
   Phys P;
   const int *rowptr, *col, *diag;
-  const double *trans, *phi_f, *phi_m;
+  const double *trans, *phi_f, *phi_m, *pr;
   const double *p, *sw, *bhp, *Mn;
   const int *well_kind;
   const double *well_target;
-  double *val, *R;
+  double *val, *R, *Macc;
   double inv_dt;
 };
 
-// One thread per block row.  Cell rows: accumulation, then the connections
+// One thread per block row.  Threads [0, nL) take the fracture rows, [nL, nc)
+// the matrix rows and [nc, nb) the well rows, so that a warp holds rows of
+// one kind and equal length.  Cell rows: accumulation, then the connections
 // in increasing column order (fluxes, then perforations); well rows: the
 // rate or pressure constraint.
 __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
   const Phys &P = a.P;
-  if (r >= P.nb) return;
+  int r;
+  if (t < P.nL) r = 2 * t;
+  else if (t < P.nc) r = 2 * (t - P.nL) + 1;
+  else if (t < P.nb) r = t;
+  else return;
   int e0 = a.rowptr[r], e1 = a.rowptr[r + 1];
   if (r < P.nc) {
     double pc = a.p[r], swc = a.sw[r];
     Props qc;
-    props(P, a.phi_f, a.phi_m, r, pc, swc, qc);
+    load_props(P, a.phi_f, a.phi_m, a.pr, r, qc);
     double M[2], dM[4];
     accumulation(P, swc, qc, M, dM);
+    a.Macc[2 * r] = M[0];
+    a.Macc[2 * r + 1] = M[1];
     double r0 = (M[0] - a.Mn[2 * r]) * a.inv_dt;
     double r1 = (M[1] - a.Mn[2 * r + 1]) * a.inv_dt;
     double d0 = dM[0] * a.inv_dt, d1 = dM[1] * a.inv_dt;
@@ -363,7 +413,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
       if (d < P.nc) {
         double pd = a.p[d];
         Props qd;
-        props(P, a.phi_f, a.phi_m, d, pd, a.sw[d], qd);
+        load_props(P, a.phi_f, a.phi_m, a.pr, d, qd);
         double dzab;
         if ((r >> 1) == (d >> 1)) dzab = 0.0;
         else {
@@ -408,7 +458,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
       int c = a.col[e];
       if (c == r) continue;
       Props q;
-      props(P, a.phi_f, a.phi_m, c, a.p[c], a.sw[c], q);
+      load_props(P, a.phi_f, a.phi_m, a.pr, c, q);
       double lt = q.lam[0] + q.lam[1], dlt = q.dlam[0] + q.dlam[1];
       double wi = a.trans[e];
       double wl = wi * lt;
@@ -458,10 +508,11 @@ int phys_save_old(Sim *s) {
 }
 
 int phys_assemble(Sim *s) {
+  DP_LAUNCH(s, k_props, nblk(s->ph.nc), kBlock, 0, s->ph, s->phi_f, s->phi_m, s->p, s->sw, s->pr);
   AsmArgs a;
   a.P = s->ph;
   a.rowptr = s->A.rowptr; a.col = s->A.col; a.diag = s->A.diag;
-  a.trans = s->trans; a.phi_f = s->phi_f; a.phi_m = s->phi_m;
+  a.trans = s->trans; a.phi_f = s->phi_f; a.phi_m = s->phi_m; a.pr = s->pr; a.Macc = s->Macc;
   a.p = s->p; a.sw = s->sw; a.bhp = s->bhp; a.Mn = s->Mn;
   a.well_kind = s->well_kind; a.well_target = s->well_target;
   a.val = s->A.val; a.R = s->R;
@@ -489,8 +540,8 @@ __device__ __forceinline__ double warp_max(double v) {
 
 __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *phi_f,
                                                        const double *phi_m, const double *R,
-                                                       const double *p, const double *sw,
-                                                       const double *Mn, const int *well_kind,
+                                                       const double *Macc, const double *Mn,
+                                                       const int *well_kind,
                                                        const double *well_target, double dt,
                                                        double *part) {
   double v[7] = {0, 0, 0, 0, 0, 0, 0};  // s2, max, sro, srw, dmo, dmw, unused
@@ -507,12 +558,8 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *phi
       }
       v[2] += R[2 * r];
       v[3] += R[2 * r + 1];
-      Props q;
-      props(P, phi_f, phi_m, r, p[r], sw[r], q);
-      double M[2], dM[4];
-      accumulation(P, sw[r], q, M, dM);
-      v[4] += M[0] - Mn[2 * r];
-      v[5] += M[1] - Mn[2 * r + 1];
+      v[4] += Macc[2 * r] - Mn[2 * r];
+      v[5] += Macc[2 * r + 1] - Mn[2 * r + 1];
     } else {
       int w = r - P.nc;
       double sc = well_kind[w] == 0 ? fmax(well_target[w], 1e-12) : well_target[w];
@@ -537,37 +584,48 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *phi
   }
 }
 
-__global__ void k_norms_final(Phys P, const double *phi_f, const double *phi_m, const double *p,
-                              const double *sw, const double *bhp, const int *perf_cell,
-                              const int *perf_well, const double *perf_wi, int np,
-                              const int *well_kind, const double *part, int nparts,
-                              double *out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double v[6] = {0, 0, 0, 0, 0, 0};
-  for (int b = 0; b < nparts; ++b) {
+// One block: partials and perforation rates summed in a fixed order.
+__global__ void __launch_bounds__(kBlock) k_norms_final(Phys P, const double *phi_f,
+                                                        const double *phi_m, const double *p,
+                                                        const double *sw, const double *bhp,
+                                                        const int *perf_cell, const int *perf_well,
+                                                        const double *perf_wi, int np,
+                                                        const int *well_kind, const double *part,
+                                                        int nparts, double *out) {
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x)
     for (int k = 0; k < 6; ++k) v[k] = k == 1 ? fmax(v[k], part[b * 8 + k]) : v[k] + part[b * 8 + k];
-  }
-  double wo = 0.0, ww = 0.0;
-  for (int t = 0; t < np; ++t) {
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
     int c = perf_cell[t], w = perf_well[t];
     Props q;
     props(P, phi_f, phi_m, c, p[c], sw[c], q);
     double Q[2], dq[4], dqb[2];
     perf_rate(well_kind[w], perf_wi[t], p[c], bhp[w], q, Q, dq, dqb);
-    wo += Q[0];
-    ww += Q[1];
+    v[6] += Q[0];
+    v[7] += Q[1];
   }
-  out[0] = sqrt(v[0]);
-  out[1] = v[1];
-  out[2] = v[2]; out[3] = v[3]; out[4] = v[4]; out[5] = v[5];
-  out[6] = wo; out[7] = ww;
+  __shared__ double sh[kBlock / 32][8];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    double t = k == 1 ? warp_max(v[k]) : warp_sum(v[k]);
+    if (lane == 0) sh[wid][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < kBlock / 32; ++q)
+      for (int k = 0; k < 8; ++k) o[k] = k == 1 ? fmax(o[k], sh[q][k]) : o[k] + sh[q][k];
+    out[0] = sqrt(o[0]);
+    for (int k = 1; k < 8; ++k) out[k] = o[k];
+  }
 }
 
 int phys_norms(Sim *s) {
   Phys &P = s->ph;
-  DP_LAUNCH(s, k_norms_part, s->norm_blocks, kBlock, 0, P, s->phi_f, s->phi_m, s->R, s->p, s->sw,
+  DP_LAUNCH(s, k_norms_part, s->norm_blocks, kBlock, 0, P, s->phi_f, s->phi_m, s->R, s->Macc,
             s->Mn, s->well_kind, s->well_target, s->dt, s->norm_part);
-  DP_LAUNCH(s, k_norms_final, 1, 32, 0, P, s->phi_f, s->phi_m, s->p, s->sw, s->bhp, s->perf_cell,
+  DP_LAUNCH(s, k_norms_final, 1, kBlock, 0, P, s->phi_f, s->phi_m, s->p, s->sw, s->bhp, s->perf_cell,
             s->perf_well, s->perf_wi, s->nperf, s->well_kind, s->norm_part, s->norm_blocks,
             s->norm_out);
   DP_CUDA(s, cudaGetLastError());
@@ -582,14 +640,14 @@ int phys_norms(Sim *s) {
 // every decoupled block.
 __global__ void __launch_bounds__(kBlock) k_decouple(int nb, int nc, const int *rowptr,
                                                      const int *diag, double *val, const double *R,
-                                                     double *bh, double *ap) {
+                                                     double *bh, double *ap, double *ap01) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   double b0 = -R[2 * i], b1 = -R[2 * i + 1];
   int e0 = rowptr[i], e1 = rowptr[i + 1];
   if (i >= nc) {
     bh[2 * i] = b0; bh[2 * i + 1] = b1;
-    for (int e = e0; e < e1; ++e) ap[e] = val[4 * (size_t)e];
+    for (int e = e0; e < e1; ++e) { ap[e] = val[4 * (size_t)e]; ap01[e] = val[4 * (size_t)e + 1]; }
     return;
   }
   const double *dg = val + 4 * (size_t)diag[i];
@@ -601,6 +659,7 @@ __global__ void __launch_bounds__(kBlock) k_decouple(int nb, int nc, const int *
     double n1 = a[1] - (fct * a[3]);
     a[0] = n0; a[1] = n1;
     ap[e] = n0;
+    ap01[e] = n1;
   }
   bh[2 * i] = b0 - (fct * b1);
   bh[2 * i + 1] = b1;
@@ -608,7 +667,7 @@ __global__ void __launch_bounds__(kBlock) k_decouple(int nb, int nc, const int *
 
 int phys_decouple_extract(Sim *s) {
   DP_LAUNCH(s, k_decouple, nblk(s->ph.nb), kBlock, 0, s->ph.nb, s->ph.nc, s->A.rowptr, s->A.diag,
-            s->A.val, s->R, s->bh, s->ap);
+            s->A.val, s->R, s->bh, s->ap, s->ap01);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }

@@ -183,11 +183,13 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   s->Mn = (double *)dalloc(s, 2 * nc8);
   s->R = (double *)dalloc(s, nb16); s->bh = (double *)dalloc(s, nb16);
   s->y = (double *)dalloc(s, nb16);
+  s->pr = (double *)dalloc(s, 7 * nc8);
+  s->Macc = (double *)dalloc(s, 2 * nc8);
   s->norm_blocks = std::min(nblk(P.nb), 1024);
   s->norm_part = (double *)dalloc(s, (size_t)s->norm_blocks * 64);
   s->norm_out = (double *)dalloc(s, 64);
   if (!s->p || !s->sw || !s->bhp || !s->pn || !s->swn || !s->bhpn || !s->Mn || !s->R || !s->bh ||
-      !s->y || !s->norm_part || !s->norm_out)
+      !s->y || !s->norm_part || !s->norm_out || !s->pr || !s->Macc)
     return fail(DP_ENOMEM);
   cudaMemsetAsync(s->p, 0, nc8, st); cudaMemsetAsync(s->sw, 0, nc8, st);
   cudaMemsetAsync(s->bhp, 0, nw8, st); cudaMemsetAsync(s->Mn, 0, 2 * nc8, st);
@@ -235,9 +237,18 @@ static int copy_state(dp_sim *s, const double *p, const double *sw, const double
   return DP_OK;
 }
 
+// A new old time level starts a new timestep of Algorithm 1: the Newton
+// counters that the forcing terms use start again.
+static void new_timestep(Sim *s) {
+  s->newton_iter = 0;
+  s->prev_res = 0.0;
+  s->prev_linres = 0.0;
+}
+
 extern "C" int sim_set_state(dp_sim *s, const double *p, const double *sw, const double *bhp) {
   DP_TRY(copy_state(s, p, sw, bhp, cudaMemcpyDefault));
   DP_TRY(phys_save_old(s));
+  new_timestep(s);
   return check(s);
 }
 
@@ -245,6 +256,7 @@ extern "C" int sim_set_state_device(dp_sim *s, const double *p, const double *sw
                                     const double *bhp) {
   DP_TRY(copy_state(s, p, sw, bhp, cudaMemcpyDeviceToDevice));
   DP_TRY(phys_save_old(s));
+  new_timestep(s);
   return check(s);
 }
 
@@ -311,6 +323,8 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   if (s->opt.precond == 2) {
     if (!s->amg_ready) DP_TRY(amg_setup(s));
     else DP_TRY(amg_refresh(s));
+    if (s->opt.precision == 1) DP_TRY(mixed_refresh(s));
+    DP_TRY(cluster_refresh(s));
   }
   cudaEventRecord(e1, s->stream);
   int it = 0;
@@ -340,9 +354,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
 extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
   if (!s || !(dt > 0.0)) return DP_EINVAL;
   DP_TRY(phys_save_old(s));
-  s->newton_iter = 0;
-  s->prev_res = 0.0;
-  s->prev_linres = 0.0;
+  new_timestep(s);
   int lin = 0;
   bool conv = false;
   double res0 = 0.0, res = 0.0, ms_setup = 0.0, ms_solve = 0.0;

@@ -212,3 +212,28 @@ def test_layered_200k_timestep_parity():
     rco, sto = o.advance(prob.dt)
     assert rcg == rco == 0
     state_close(g, o, prob)
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_mixed_precision_preconditioner_tiny_steps(precond):
+    """FP32 ILU(0) and AMG inside FP64 FGMRES: the Newton states still match
+    the FP64 oracle to the parity tolerance (FGMRES wins the accuracy back)."""
+    prob = di.tiny()
+    g = gpu().Sim(prob, gpu().options("parity", precision=1, precond=precond, gmres_maxit=600))
+    o = O.OracleSim(prob, O.options("parity", precond=precond, gmres_maxit=600))
+    for step in range(4):
+        rcg, stg = g.advance(prob.dt)
+        rco, sto = o.advance(prob.dt)
+        assert rcg == rco == 0, step
+        state_close(g, o, prob)
+
+
+def test_mixed_precision_layered_timestep():
+    prob = di.layered()
+    g = gpu().Sim(prob, gpu().options("parity", precision=1))
+    o = O.OracleSim(prob, O.options("parity"))
+    rcg, stg = g.advance(prob.dt)
+    rco, sto = o.advance(prob.dt)
+    assert rcg == rco == 0
+    state_close(g, o, prob)
+    assert stg.linear_iters <= 2 * sto.linear_iters
