@@ -167,6 +167,10 @@ def main():
     ap.add_argument("--sample-div", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "newton2"],
+                    help="newton2: create the realisation, run the first Newton solve of the "
+                         "first step (AMG set-up) and the second one, print their timings "
+                         "(a short run for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -187,6 +191,19 @@ def main():
 
     prob = workload(args)
     opts = dpsim.options("report", precision=args.precision)
+    if args.mode == "newton2":
+        sim = dpsim.Sim(prob, opts)
+        out = {}
+        for k in ("first", "second"):
+            sim.assemble(prob.dt)
+            rc, st = sim.solve_step()
+            out[k] = {"fgmres_iters": st.linear_iters, "ms_setup": st.ms_setup,
+                      "ms_solve": st.ms_solve}
+        torch.cuda.synchronize()
+        out["launches"] = sim.launch_count()
+        print(json.dumps(out), flush=True)
+        sim.close()
+        return
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = dpsim.Sim(prob, opts, stream=stream)
