@@ -109,6 +109,16 @@ struct LaunchScope {
     name<<<(grid), (block), (smem), (sim)->stream>>>(__VA_ARGS__);      \
   } while (0)
 
+// Storage order of the Krylov operator's copy: the fracture rows (cells 2q)
+// first, then the matrix rows (2q+1), then the well rows, so that a warp
+// streams rows of one kind and length from contiguous memory.
+__host__ __device__ __forceinline__ int row_of_pair(int q, int nL, int nc) {
+  return q < nL ? 2 * q : (q < nc ? 2 * (q - nL) + 1 : q);
+}
+__host__ __device__ __forceinline__ int storage_row(int i, int nL, int nc) {
+  return i < nc ? ((i & 1) ? nL + (i >> 1) : (i >> 1)) : i;
+}
+
 inline int nblk(long long n, int b = kBlock) {
   long long g = (n + b - 1) / b;
   return (int)(g > 0 ? g : 1);
@@ -215,7 +225,10 @@ struct Sim {
   std::vector<Level> lev;
   bool amg_ready = false;
   double *ap = nullptr;                              // pressure values (nnzb)
-  double *ap01 = nullptr;                            // decoupled (0,1) entries (nnzb)
+  // the decoupled matrix again in storage order (row_of_pair), with its
+  // pressure rows (entries (0,0) and (0,1) of every block) as separate arrays
+  int *srowptr = nullptr, *scol = nullptr;
+  double *sval = nullptr, *sa00 = nullptr, *sa01 = nullptr;
   double *coarse_lu = nullptr;
   int *coarse_piv = nullptr;
   int coarse_n = 0;

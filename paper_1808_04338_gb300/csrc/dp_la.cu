@@ -16,12 +16,9 @@ namespace dp {
 // pair) and accumulates its own output with FMAs, so no FP64 reduction
 // across lanes is needed.  A warp covers 16 block rows.
 //
-// Row order: pairs [0, nL) take the fracture rows 2q, pairs [nL, nc) the
-// matrix rows, the rest the well rows, so that a warp holds rows of one
-// length (8 blocks for an interior fracture row, 2 for a matrix row).
-__device__ __forceinline__ int row_of_pair(int q, int nL, int nc) {
-  return q < nL ? 2 * q : (q < nc ? 2 * (q - nL) + 1 : q);
-}
+// The operator is read from its storage-order copy (fracture rows, then
+// matrix rows, then wells): pair q processes storage row q, whose blocks are
+// contiguous with those of pair q+1, and writes natural row row_of_pair(q).
 
 template <int MODE>  // MODE 0: y = A x; 1: y = b - A x
 __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
@@ -32,10 +29,10 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
                                                      const double *__restrict__ b,
                                                      double *__restrict__ y) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int comp = t & 1;
-  if ((t >> 1) >= n) return;
-  int row = row_of_pair(t >> 1, nL, nc);
-  int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+  int comp = t & 1, q = t >> 1;
+  if (q >= n) return;
+  int row = row_of_pair(q, nL, nc);
+  int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
   const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
   double s = 0.0;
@@ -63,7 +60,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   int row = row_of_pair(t, nL, nc);
-  int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+  int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
   double s = 0.0;
 #pragma unroll 4
@@ -77,13 +74,13 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
   DP_LAUNCH(s, k_bsr_spmv<0>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
-            s->A.rowptr, s->A.col, s->A.val, x, nullptr, y);
+            s->srowptr, s->scol, s->sval, x, nullptr, y);
   return DP_OK;
 }
 
 int bsr_residual(Sim *s, const double *b, const double *x, double *r) {
   DP_LAUNCH(s, k_bsr_spmv<1>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
-            s->A.rowptr, s->A.col, s->A.val, x, b, r);
+            s->srowptr, s->scol, s->sval, x, b, r);
   return DP_OK;
 }
 
@@ -677,8 +674,8 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   if (!f32) {
     if (s->opt.precond == 1) return ilu_apply(s, r, z);
     DP_TRY(ilu_apply(s, r, s->z1));
-    DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->A.rowptr, s->A.col,
-              s->ap, s->ap01, s->z1, r, s->rp);
+    DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr, s->scol,
+              s->sa00, s->sa01, s->z1, r, s->rp);
     DP_TRY(vcycle(s, 0, s->rp, s->xp));
     DP_LAUNCH(s, k_inject_add<double>, nblk(nb), kBlock, 0, nb, s->xp, s->z1);
     DP_TRY(bsr_residual(s, r, s->z1, s->r1));
@@ -695,8 +692,8 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   Level &L0 = s->lev[0];
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r, s->zf)));
   DP_LAUNCH(s, k_to_f64, nblk(N), kBlock, 0, N, s->zf, s->z1);
-  DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->A.rowptr, s->A.col,
-            s->ap, s->ap01, s->z1, r, s->rp);
+  DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr, s->scol,
+            s->sa00, s->sa01, s->z1, r, s->rp);
   DP_LAUNCH(s, k_to_f32, nblk(nb), kBlock, 0, (long long)nb, s->rp, L0.bf);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
   DP_LAUNCH(s, k_inject_add<float>, nblk(nb), kBlock, 0, nb, L0.xf, s->z1);

@@ -215,6 +215,22 @@ __global__ void k_pattern_fill(Phys P, const double *kf, const double *km, const
   }
 }
 
+__global__ void k_storage_len(int nb, int nL, int nc, const int *rowptr, int *len) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nb) return;
+  int i = row_of_pair(q, nL, nc);
+  len[q] = rowptr[i + 1] - rowptr[i];
+}
+
+__global__ void k_storage_cols(int nb, int nL, int nc, const int *rowptr, const int *col,
+                               const int *srowptr, int *scol) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nb) return;
+  int i = row_of_pair(q, nL, nc);
+  int e0 = rowptr[i], m = rowptr[i + 1] - e0, d0 = srowptr[q];
+  for (int k = 0; k < m; ++k) scol[d0 + k] = col[e0 + k];
+}
+
 // Peaceman's radius for a vertical well and the well index
 // W = 2 pi k h w_frac / (ln(r_e / r_w) + s), k h = sqrt(kx ky) dz, w_frac = 1.
 static double well_index_host(double kx, double ky, double dx, double dy, double dz, double rw,
@@ -310,14 +326,26 @@ int phys_build_pattern(Sim *s) {
   s->A.val = (double *)dalloc(s, (size_t)nnz * 32);
   s->trans = (double *)dalloc(s, (size_t)nnz * 8);
   s->ap = (double *)dalloc(s, (size_t)nnz * 8);
-  s->ap01 = (double *)dalloc(s, (size_t)nnz * 8);
-  if (!s->A.col || !s->A.val || !s->trans || !s->ap || !s->ap01) {
+  s->sval = (double *)dalloc(s, (size_t)nnz * 32);
+  s->sa00 = (double *)dalloc(s, (size_t)nnz * 8);
+  s->sa01 = (double *)dalloc(s, (size_t)nnz * 8);
+  s->scol = (int *)dalloc(s, (size_t)nnz * 4);
+  s->srowptr = (int *)dalloc(s, ((size_t)P.nb + 1) * 4);
+  if (!s->A.col || !s->A.val || !s->trans || !s->ap || !s->sval || !s->sa00 || !s->sa01 ||
+      !s->scol || !s->srowptr) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
   DP_LAUNCH(s, k_pattern_fill, nblk(P.nb), kBlock, 0, P, s->kf, s->km, d_pc_cell, d_pc_well,
             d_pc_wi, np, d_pw_start, d_pw_cell, d_pw_wi, s->A.rowptr, s->A.col, s->A.diag,
             s->trans);
+  DP_CUDA(s, cudaGetLastError());
+  // the storage-order pattern of the Krylov operator's copy
+  DP_LAUNCH(s, k_storage_len, nblk(P.nb), kBlock, 0, P.nb, P.nL, P.nc, s->A.rowptr, len);
+  int snnz = 0;
+  DP_TRY(scan_i32(s, len, s->srowptr, P.nb, &snnz));
+  DP_LAUNCH(s, k_storage_cols, nblk(P.nb), kBlock, 0, P.nb, P.nL, P.nc, s->A.rowptr, s->A.col,
+            s->srowptr, s->scol);
   DP_CUDA(s, cudaGetLastError());
   dfree(s, len);
   dfree(s, d_pw_start);
@@ -638,36 +666,59 @@ int phys_norms(Sim *s) {
 // oil row, D_i^-1 = [[1, -a01/a11], [0, 1]], applied to the whole row and to
 // b = -R; well rows unchanged.  The pressure block takes entry (0,0) of
 // every decoupled block.
-__global__ void __launch_bounds__(kBlock) k_decouple(int nb, int nc, const int *rowptr,
-                                                     const int *diag, double *val, const double *R,
-                                                     double *bh, double *ap, double *ap01) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nb) return;
-  double b0 = -R[2 * i], b1 = -R[2 * i + 1];
-  int e0 = rowptr[i], e1 = rowptr[i + 1];
-  if (i >= nc) {
-    bh[2 * i] = b0; bh[2 * i + 1] = b1;
-    for (int e = e0; e < e1; ++e) { ap[e] = val[4 * (size_t)e]; ap01[e] = val[4 * (size_t)e + 1]; }
-    return;
+// The decoupled rows are also written, in the storage order of the Krylov
+// operator's copy, to sval (whole blocks) and sa00 / sa01 (pressure rows).
+struct DecArgs {
+  int nb, nc, nL;
+  const int *rowptr, *diag, *srowptr;
+  double *val, *bh, *ap, *sval, *sa00, *sa01;
+  const double *R;
+};
+
+__global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nb) return;
+  int i = row_of_pair(t, a.nL, a.nc);     // consecutive threads: consecutive storage rows
+  double b0 = -a.R[2 * i], b1 = -a.R[2 * i + 1];
+  int e0 = a.rowptr[i], e1 = a.rowptr[i + 1], sb = a.srowptr[t] - e0;
+  double fct = 0.0;
+  if (i < a.nc) {
+    const double *dg = a.val + 4 * (size_t)a.diag[i];
+    double a01 = dg[1], a11 = dg[3];
+    fct = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
   }
-  const double *dg = val + 4 * (size_t)diag[i];
-  double a01 = dg[1], a11 = dg[3];
-  double fct = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
   for (int e = e0; e < e1; ++e) {
-    double *a = val + 4 * (size_t)e;
-    double n0 = a[0] - (fct * a[2]);
-    double n1 = a[1] - (fct * a[3]);
-    a[0] = n0; a[1] = n1;
-    ap[e] = n0;
-    ap01[e] = n1;
+    double *v = a.val + 4 * (size_t)e;
+    double n0 = v[0], n1 = v[1], n2 = v[2], n3 = v[3];
+    if (i < a.nc) {
+      n0 = n0 - (fct * n2);
+      n1 = n1 - (fct * n3);
+      v[0] = n0; v[1] = n1;
+    }
+    a.ap[e] = n0;
+    size_t q = (size_t)(sb + e);
+    double2 *sv = reinterpret_cast<double2 *>(a.sval) + 2 * q;
+    sv[0] = make_double2(n0, n1);
+    sv[1] = make_double2(n2, n3);
+    a.sa00[q] = n0;
+    a.sa01[q] = n1;
   }
-  bh[2 * i] = b0 - (fct * b1);
-  bh[2 * i + 1] = b1;
+  if (i < a.nc) {
+    a.bh[2 * i] = b0 - (fct * b1);
+    a.bh[2 * i + 1] = b1;
+  } else {
+    a.bh[2 * i] = b0;
+    a.bh[2 * i + 1] = b1;
+  }
 }
 
 int phys_decouple_extract(Sim *s) {
-  DP_LAUNCH(s, k_decouple, nblk(s->ph.nb), kBlock, 0, s->ph.nb, s->ph.nc, s->A.rowptr, s->A.diag,
-            s->A.val, s->R, s->bh, s->ap, s->ap01);
+  DecArgs a;
+  a.nb = s->ph.nb; a.nc = s->ph.nc; a.nL = s->ph.nL;
+  a.rowptr = s->A.rowptr; a.diag = s->A.diag; a.srowptr = s->srowptr;
+  a.val = s->A.val; a.bh = s->bh; a.ap = s->ap; a.sval = s->sval; a.sa00 = s->sa00;
+  a.sa01 = s->sa01; a.R = s->R;
+  DP_LAUNCH(s, k_decouple, nblk(s->ph.nb), kBlock, 0, a);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
