@@ -142,6 +142,140 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args):
+    """The 64-realisation ensemble (20x20x5 to 80x80x20 locations, own seeds
+    and shape factors): one step = one 5-day timestep of every realisation
+    from its initial state.  Timed twice on the same resident realisations:
+    one after another on one host thread, and concurrently through
+    sim_advance_many (each realisation on its own stream).  Wall clock
+    around device-synchronised steps, since the work spans many streams."""
+    import torch
+    import dp_inputs as di
+    from paper_1808_04338_gb300 import dpsim
+    members = [di.ensemble_member(r) for r in range(64)]
+    opts = dpsim.options("report", precision=args.precision)
+    sims, x0, streams = [], [], []
+    for prob in members:
+        streams.append(dpsim.OwnedStream())
+        sims.append(dpsim.Sim(prob, opts, stream=streams[-1].torch))
+        x0.append([torch.from_numpy(a).cuda() for a in (prob.p0, prob.sw0, prob.bhp0)])
+    torch.cuda.synchronize()
+    dts = [p.dt for p in members]
+
+    def step(threads):
+        for s, (p, sw, b) in zip(sims, x0):
+            s.set_state_device(p, sw, b)
+        rc, stats, _ = dpsim.advance_many(sims, dts, threads=threads)
+        if rc != 0:
+            raise RuntimeError(f"sim_advance_many failed ({rc})")
+        return sum(st.newton_iters for st in stats), sum(st.linear_iters for st in stats)
+
+    def timed(threads):
+        for _ in range(args.warmup):
+            step(threads)
+        torch.cuda.synchronize()
+        l0 = sum(s.launch_count() for s in sims)
+        t0 = time.perf_counter()
+        solves = its = 0
+        for _ in range(args.steps):
+            a, b = step(threads)
+            solves += a
+            its += b
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        return {"sec": sec, "solves": solves, "its": its,
+                "launches": sum(s.launch_count() for s in sims) - l0}
+
+    clk = Clocks(torch.cuda.current_device())
+    one = timed(1)
+    clk.__enter__()
+    many = timed(args.threads)
+    clk.__exit__()
+    cells = sum(p.n_cells for p in members)
+    line = {"metric": "batched ensemble timesteps", "value": 64 * args.steps / many["sec"],
+            "unit": "realisation timesteps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * many["sec"] / args.steps,
+            "higher_is_better": True, "dtype": "f64" if args.precision == 0 else "f64 (f32 preconditioner)",
+            "data": "synthetic",
+            "config": {"workload": f"64 realisations, 20x20x5 to 80x80x20 locations, {cells} cells",
+                       "threads": args.threads, "precision": args.precision},
+            "newton_solves_per_s": many["solves"] / many["sec"],
+            "fgmres_iters_per_solve": many["its"] / max(many["solves"], 1),
+            "one_at_a_time": {"value": 64 * args.steps / one["sec"], "unit": "realisation timesteps/s",
+                              "ms_per_step": 1000 * one["sec"] / args.steps,
+                              "newton_solves_per_s": one["solves"] / one["sec"]},
+            "gpu_launches": many["launches"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    for s in sims:
+        s.close()
+    for st in streams:
+        st.close()
+
+
+def run_serve(args):
+    """The served stream: 512 timestep requests with Poisson arrivals (mean
+    200/s) over 128 realisations of about 10k to 1M cells, served by the
+    library's request server under a 160 GB device budget.  Every requested
+    realisation is made resident first by one untimed 1-day request; the
+    stream then arrives in real time.  Latency = result ready - arrival on
+    the server's clock.  Run twice: `--threads` workers with the FP32
+    preconditioner, and one worker with the plain FP64 path."""
+    import numpy as np
+    import torch
+    import dp_inputs as di
+    from paper_1808_04338_gb300 import dpsim
+    members = [di.served_member(r) for r in range(128)]
+    arrivals, real, dts = di.request_stream()
+    budget = 160 << 30
+
+    def once(workers, precision):
+        srv = dpsim.Server(workers, budget, dpsim.options("report", precision=precision))
+        ids = [srv.add(p) for p in members]
+        for t in [srv.submit(ids[r], di.DAY) for r in sorted(set(real.tolist()))]:
+            if srv.wait(t).status != 0:
+                raise RuntimeError("warm-up request failed")
+        torch.cuda.synchronize()
+        l0 = srv.info().launches
+        t0 = time.perf_counter()
+        tickets = []
+        for a, r, d in zip(arrivals, real, dts):
+            lag = a - (time.perf_counter() - t0)
+            if lag > 0:
+                time.sleep(lag)
+            tickets.append(srv.submit(ids[int(r)], float(d) * di.DAY))
+        res = [srv.wait(t) for t in tickets]
+        info = srv.info()
+        srv.close()
+        lat = np.array([x.t_done_ms - x.t_submit_ms for x in res])
+        span = (max(x.t_done_ms for x in res) - min(x.t_submit_ms for x in res)) / 1000.0
+        newton = sum(x.stats.newton_iters for x in res)
+        return {"solves_per_s": len(res) / span, "newton_solves_per_s": newton / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "makespan_s": span, "failed": int(sum(x.status != 0 for x in res)),
+                "newton_per_request": newton / len(res),
+                "resident_gb": info.peak_resident_bytes / 1e9, "evictions": info.evictions,
+                "launches": info.launches - l0}
+
+    clk = Clocks(torch.cuda.current_device())
+    clk.__enter__()
+    served = once(args.threads, args.precision)
+    clk.__exit__()
+    plain = once(1, 0)
+    cells = sum(p.n_cells for p in members)
+    line = {"metric": "served timestep-solve stream: p50/p99 latency and throughput",
+            "value": served["solves_per_s"], "unit": "timestep solves/s", "n_gpus": 1,
+            "higher_is_better": True, "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
+            "dtype": "f64" if args.precision == 0 else "f64 (f32 preconditioner)",
+            "data": "synthetic",
+            "config": {"workload": f"512 requests, Poisson 200/s, 128 realisations "
+                                   f"({cells} cells), dt 1-10 days, budget 160 GB",
+                       "workers": args.threads, "precision": args.precision},
+            "served": served,
+            "plain_fp64_one_worker": plain,
+            "gpu_launches": served["launches"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def config_dict(args):
     return {"workload": f"dual-porosity oil-water, {args.nx}x{args.ny}x{args.nz} grid, "
                         f"{2 * args.nx * args.ny * args.nz} cells, "
@@ -167,7 +301,9 @@ def main():
     ap.add_argument("--sample-div", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "newton2"],
+    ap.add_argument("--threads", type=int, default=16,
+                    help="ensemble mode: host threads driving realisations concurrently")
+    ap.add_argument("--mode", default="bench", choices=["bench", "newton2", "ensemble", "serve"],
                     help="newton2: create the realisation, run the first Newton solve of the "
                          "first step (AMG set-up) and the second one, print their timings "
                          "(a short run for profilers)")
@@ -189,6 +325,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
+    if args.mode == "ensemble":
+        return run_ensemble(args)
+    if args.mode == "serve":
+        return run_serve(args)
     prob = workload(args)
     opts = dpsim.options("report", precision=args.precision)
     if args.mode == "newton2":

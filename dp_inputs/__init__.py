@@ -240,3 +240,34 @@ CONFIGS = {
     "layered": layered,
     "field8m": field8m,
 }
+
+
+def served_member(r: int) -> Problem:
+    """Realisation r of the 128 of the served stream: a log-uniform size from
+    about 10k to 1M cells (5k to 500k locations, ten layers), its own seed
+    (1000 + r), fracture perm lognormal (ln 100 mD, sd 1), a shape factor in
+    [0.01, 0.2] and five-spot wells."""
+    seed = 1000 + r
+    u = float(splitmix64_uniform(seed, 3, np.array([0]))[0])
+    n_loc = 5000.0 * 100.0 ** u
+    nz = 10
+    nxy = max(3, int(round(math.sqrt(n_loc / nz))))
+    n = nxy * nxy * nz
+    kf = np.exp(math.log(100.0) + 1.0 * normals(seed, 0, n))
+    sigma = 0.01 + 0.19 * float(splitmix64_uniform(seed, 1, np.array([0]))[0])
+    return _base(f"served{r}_{nxy}x{nxy}x{nz}", nxy, nxy, nz, kf, np.full(n, 0.1), 0.01, 0.2,
+                 sigma, five_spot(nxy, nxy, nz), seed, dt_days=5.0, nsteps=1)
+
+
+def request_stream(n_requests: int = 512, rate_per_s: float = 200.0, n_real: int = 128,
+                   seed: int = 7):
+    """A seeded Poisson request stream: arrival times (s, exponential gaps of
+    mean 1/rate), the realisation of each request (uniform over n_real) and
+    its timestep in days (1, 2, 5 or 10, so that Newton counts differ)."""
+    k = np.arange(n_requests, dtype=np.uint64)
+    gaps = -np.log(splitmix64_uniform(seed, 0, k)) / rate_per_s
+    arrivals = np.cumsum(gaps) - gaps[0]
+    real = np.minimum((splitmix64_uniform(seed, 1, k) * n_real).astype(np.int64), n_real - 1)
+    dts = np.array([1.0, 2.0, 5.0, 10.0])[
+        np.minimum((splitmix64_uniform(seed, 2, k) * 4).astype(np.int64), 3)]
+    return arrivals, real, dts

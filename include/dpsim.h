@@ -172,6 +172,95 @@ int sim_solve_step(dp_sim *sim, dp_stats *stats);
  * failure the old state is restored and DP_ENEWTON returned. */
 int sim_advance(dp_sim *sim, double dt, dp_stats *stats);
 
+/* Batched timesteps of many realisations (no counterpart in the paper,
+ * which advances one grid on many processors; here many independent grids
+ * share one GPU).  Advances sims[k] by dt[k] for k < n, like sim_advance,
+ * with up to `threads` host threads (0: one per realisation, at most 16)
+ * taking realisations from a common queue in order, so that realisations of
+ * uneven size keep the GPU busy; each realisation runs on the stream given
+ * at its creation, and the kernels of realisations on different streams
+ * overlap on the device (realisations that share a stream are serialised by
+ * it).  A sim may appear once per call.  Results are those of sim_advance on
+ * each realisation alone, bit for bit.  stats[k] and status[k] (may be NULL)
+ * receive each realisation's statistics and return code.  Returns DP_OK when
+ * every realisation returned DP_OK, else the first failing code. */
+int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t threads,
+                     dp_stats *stats, int32_t *status);
+
+/* A non-blocking CUDA stream owned by the caller until dp_stream_destroy:
+ * for callers whose framework hands out pooled streams (many realisations
+ * need as many distinct streams to overlap).  No counterpart in the paper. */
+int dp_stream_create(void **stream);
+int dp_stream_destroy(void *stream);
+
+/* Device bytes the realisation holds through its allocator now, and the
+ * most it has held at once (both may be NULL).  Host only, no CUDA call. */
+int sim_footprint(dp_sim *s, uint64_t *current, uint64_t *peak);
+
+/* ------------------------------------------------------------- serving
+ * A request server for timestep solves of many realisations on one GPU
+ * (no counterpart in the paper, whose field runs advance one model on a CPU
+ * cluster).  Realisations are registered once (host copies of their inputs
+ * and state are kept); a request asks for one sim_advance of one
+ * realisation by dt.  `workers` host threads serve the queue concurrently
+ * (continuous batching: a request that arrives while others run starts as
+ * soon as a worker and device memory are free, and its kernels overlap
+ * theirs on the device).  A realisation that has been served stays
+ * resident (state, operator, ILU(0) factors, AMG hierarchy) on its own
+ * stream.  Admission is by device footprint: a request whose realisation is
+ * not resident is admitted when its estimated footprint (the largest bytes
+ * per block row measured so far, times its block rows; 4096 B per row before
+ * any measurement) fits in hbm_budget after evicting idle resident
+ * realisations, least recently used first; an evicted realisation's state
+ * goes back to its host copy, and the realisation is rebuilt (operator
+ * pattern and AMG set-up) when next served.  Requests are taken in arrival
+ * order, skipping those whose realisation is busy or does not fit yet.
+ * Results are those of sim_advance on the realisation alone: bit for bit
+ * while it stays resident; within the Newton tolerance after an eviction
+ * (the AMG aggregates are then rebuilt from the current iterate). */
+typedef struct dp_server dp_server;
+
+typedef struct dp_srv_result {
+  int32_t status;       /* sim_advance's return code; DP_ENOMEM if the realisation
+                           can never fit in the budget */
+  int32_t realisation;  /* id from srv_add */
+  int32_t loaded;       /* 1 if the realisation was (re)built for this request */
+  int32_t evicted;      /* realisations evicted to admit it */
+  double t_submit_ms;   /* server clock (ms since srv_create): request arrival */
+  double t_start_ms;    /* a worker took it */
+  double t_done_ms;     /* its result was ready */
+  dp_stats stats;
+} dp_srv_result;
+
+typedef struct dp_srv_info {
+  int32_t registered, resident, queued, running;
+  int64_t served, loads, evictions;
+  int64_t launches;      /* library kernel launches made for served requests */
+  uint64_t resident_bytes, peak_resident_bytes, budget_bytes;
+  double bytes_per_row;  /* current admission estimate */
+} dp_srv_info;
+
+/* workers >= 1 concurrent requests; hbm_budget > 0 bytes; opts as for
+ * sim_create (copied).  Device: the calling thread's current device; the
+ * default stream-ordered allocator is used. */
+int srv_create(int32_t workers, uint64_t hbm_budget, const dp_options *opts, dp_server **out);
+/* Copies the inputs (as for sim_create) and the initial state (p, sw: n_cells
+ * each; bhp: nwells).  Returns the realisation id in *id. */
+int srv_add(dp_server *srv, const dp_grid *grid, const dp_rock *rock, const dp_fluid *fluid,
+            const dp_well *wells, int32_t nwells, const double *p, const double *sw,
+            const double *bhp, int32_t *id);
+/* Queues one timestep of realisation id by dt (> 0); returns at once with a
+ * ticket.  Requests of one realisation run in the order submitted. */
+int srv_submit(dp_server *srv, int32_t id, double dt, int64_t *ticket);
+/* Blocks until the request is served, then fills *out (once per ticket). */
+int srv_wait(dp_server *srv, int64_t ticket, dp_srv_result *out);
+/* Waits until realisation id has no queued or running request and copies
+ * its state to host arrays (n_cells, n_cells, nwells doubles). */
+int srv_get_state(dp_server *srv, int32_t id, double *p, double *sw, double *bhp);
+int srv_info(dp_server *srv, dp_srv_info *out);
+/* Serves what is queued, stops the workers and frees every realisation. */
+int srv_destroy(dp_server *srv);
+
 /* Test access to intermediate results (host arrays, synchronise):
  * the last Newton update y[2 nb]; the decoupled matrix values and
  * right-hand side; the greedy colouring of the block rows (returns the

@@ -27,6 +27,7 @@ UNITS = {
     "dp_sim.cu": [],
     "dp_noalloc.cu": [],
     "dp_cycle.cu": [],
+    "dp_serve.cu": [],
 }
 
 

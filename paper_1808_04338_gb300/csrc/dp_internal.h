@@ -185,6 +185,7 @@ struct Sim {
   dp_allocator alloc{};
   bool own_alloc = true;
   std::vector<std::pair<void *, size_t>> blocks;
+  size_t cur_bytes = 0, peak_bytes = 0;   // device bytes held through the allocator
   Err err;
   Timing timing;
   int64_t launches = 0;

@@ -3,9 +3,12 @@
 // Algorithm 1.  Host code only orchestrates; every numerical step runs in
 // the library's kernels on the caller's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "dp_internal.h"
 
@@ -27,7 +30,11 @@ void *dalloc(Sim *s, size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~(size_t)255;
   void *p = s->alloc.alloc(bytes, (void *)s->stream, s->alloc.ctx);
-  if (p) s->blocks.push_back({p, bytes});
+  if (p) {
+    s->blocks.push_back({p, bytes});
+    s->cur_bytes += bytes;
+    s->peak_bytes = std::max(s->peak_bytes, s->cur_bytes);
+  }
   return p;
 }
 
@@ -36,6 +43,7 @@ void dfree(Sim *s, void *p) {
   for (size_t i = 0; i < s->blocks.size(); ++i)
     if (s->blocks[i].first == p) {
       s->alloc.free(p, s->blocks[i].second, (void *)s->stream, s->alloc.ctx);
+      s->cur_bytes -= s->blocks[i].second;
       s->blocks[i] = s->blocks.back();
       s->blocks.pop_back();
       return;
@@ -389,6 +397,62 @@ extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
     return DP_ENEWTON;
   }
   return check(s);
+}
+
+extern "C" int dp_stream_create(void **stream) {
+  if (!stream) return DP_EINVAL;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    *stream = nullptr;
+    return DP_ECUDA;
+  }
+  *stream = (void *)st;
+  return DP_OK;
+}
+
+extern "C" int dp_stream_destroy(void *stream) {
+  if (!stream) return DP_EINVAL;
+  return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? DP_OK : DP_ECUDA;
+}
+
+extern "C" int sim_footprint(dp_sim *s, uint64_t *current, uint64_t *peak) {
+  if (!s) return DP_EINVAL;
+  if (current) *current = s->cur_bytes;
+  if (peak) *peak = s->peak_bytes;
+  return DP_OK;
+}
+
+extern "C" int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t threads,
+                                dp_stats *stats, int32_t *status) {
+  if (n < 0 || (n > 0 && (!sims || !dt))) return DP_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    if (!sims[k] || !(dt[k] > 0.0)) return DP_EINVAL;
+    for (int q = 0; q < k; ++q)
+      if (sims[q] == sims[k]) return DP_EINVAL;
+  }
+  int nt = threads > 0 ? threads : std::min<int>(n, 16);
+  nt = std::max(1, std::min(nt, n));
+  std::vector<int> rc(n, DP_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      int k = next.fetch_add(1);
+      if (k >= n) return;
+      dp_stats st{};
+      rc[k] = sim_advance(sims[k], dt[k], &st);
+      if (stats) stats[k] = st;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+  int first = DP_OK;
+  for (int k = 0; k < n; ++k) {
+    if (status) status[k] = rc[k];
+    if (first == DP_OK && rc[k] != DP_OK) first = rc[k];
+  }
+  return first;
 }
 
 extern "C" int sim_get_update(dp_sim *s, double *y) {

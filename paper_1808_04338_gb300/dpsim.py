@@ -132,6 +132,17 @@ def load():
     L.sim_launch_count.restype = C.c_int64
     L.sim_last_error.argtypes = [P]
     L.sim_last_error.restype = C.c_char_p
+    L.sim_advance_many.argtypes = [P, I, P, I, P, P]
+    L.sim_footprint.argtypes = [P, P, P]
+    L.dp_stream_create.argtypes = [P]
+    L.dp_stream_destroy.argtypes = [P]
+    L.srv_create.argtypes = [I, C.c_uint64, P, P]
+    L.srv_add.argtypes = [P, P, P, P, P, I, P, P, P, P]
+    L.srv_submit.argtypes = [P, I, C.c_double, P]
+    L.srv_wait.argtypes = [P, C.c_int64, P]
+    L.srv_get_state.argtypes = [P, I, P, P, P]
+    L.srv_info.argtypes = [P, P]
+    L.srv_destroy.argtypes = [P]
     L.dp_residual_norms_noalloc.argtypes = [C.POINTER(dp_grid), C.POINTER(dp_fluid), P, P, I, P,
                                             P, P, D, P, P, C.c_char_p, C.c_size_t]
     _lib = L
@@ -163,6 +174,141 @@ def residual_norms_noalloc(prob, phi_f, phi_m, well_kind, well_target, res, dt, 
                                           ptr(res), float(dt), ptr(out2), C.c_void_p(stream),
                                           buf, 256)
     return rc, buf.value.decode()
+
+
+class OwnedStream:
+    """A distinct non-blocking stream made by the library (torch's pool
+    hands out at most 32 distinct streams); ``.torch`` wraps it for torch."""
+
+    def __init__(self):
+        import torch
+        h = C.c_void_p()
+        rc = load().dp_stream_create(C.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"dp_stream_create failed ({rc})")
+        self.h = h
+        self.torch = torch.cuda.ExternalStream(h.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            import torch
+            torch.cuda.synchronize()
+            load().dp_stream_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def advance_many(sims, dts, threads=0):
+    """One timestep of every realisation in `sims` (each with its own stream),
+    concurrently; returns (rc, stats list, status list)."""
+    n = len(sims)
+    H = (C.c_void_p * max(n, 1))(*[s.h.value for s in sims])
+    D = (C.c_double * max(n, 1))(*[float(d) for d in dts])
+    st = (dp_stats * max(n, 1))()
+    rs = (C.c_int32 * max(n, 1))()
+    rc = load().sim_advance_many(C.cast(H, C.c_void_p), n, C.cast(D, C.c_void_p), int(threads),
+                                 C.cast(st, C.c_void_p), C.cast(rs, C.c_void_p))
+    return rc, [st[k] for k in range(n)], [rs[k] for k in range(n)]
+
+
+class dp_srv_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("realisation", C.c_int32), ("loaded", C.c_int32),
+                ("evicted", C.c_int32), ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double),
+                ("t_done_ms", C.c_double), ("stats", dp_stats)]
+
+
+class dp_srv_info(C.Structure):
+    _fields_ = [("registered", C.c_int32), ("resident", C.c_int32), ("queued", C.c_int32),
+                ("running", C.c_int32), ("served", C.c_int64), ("loads", C.c_int64),
+                ("evictions", C.c_int64), ("launches", C.c_int64), ("resident_bytes", C.c_uint64),
+                ("peak_resident_bytes", C.c_uint64), ("budget_bytes", C.c_uint64),
+                ("bytes_per_row", C.c_double)]
+
+
+def _inputs(prob):
+    """ctypes views of a Problem's grid, rock, fluid and wells (the arrays
+    they point to are returned too and must outlive the call)."""
+    g = dp_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.top_depth)
+    keep = [_f64(prob.kf), _f64(prob.km), _f64(prob.phi_f), _f64(prob.phi_m)]
+    r = dp_rock(*[a.ctypes.data for a in keep], prob.sigma, prob.c_rock, prob.p_ref_rock)
+    f = dp_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref, prob.rho_w_ref,
+                 prob.p_ref, prob.swc, prob.sor, prob.g)
+    nw = len(prob.wells)
+    W = (dp_well * max(nw, 1))()
+    for q, w in enumerate(prob.wells):
+        W[q] = dp_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin)
+    return g, r, f, W, nw, keep
+
+
+class Server:
+    """Request server over resident realisations (srv_* in include/dpsim.h)."""
+
+    def __init__(self, workers: int, hbm_budget: int, opts: dp_options | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("dpsim needs a CUDA device")
+        self.opts = opts if opts is not None else options("report")
+        h = C.c_void_p()
+        rc = load().srv_create(int(workers), int(hbm_budget), C.byref(self.opts), C.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"srv_create failed ({rc})")
+        self.h = h
+        self.sizes = []
+
+    def add(self, prob) -> int:
+        g, r, f, W, nw, keep = _inputs(prob)
+        p, sw = _f64(prob.p0), _f64(prob.sw0)
+        bhp = _f64(prob.bhp0 if len(prob.bhp0) else np.zeros(1))
+        rid = C.c_int32()
+        rc = load().srv_add(self.h, C.byref(g), C.byref(r), C.byref(f), W, nw, _p(p), _p(sw),
+                            _p(bhp), C.byref(rid))
+        if rc != 0:
+            raise RuntimeError(f"srv_add failed ({rc})")
+        self.sizes.append((prob.n_cells, nw))
+        return rid.value
+
+    def submit(self, rid: int, dt: float) -> int:
+        t = C.c_int64()
+        rc = load().srv_submit(self.h, int(rid), float(dt), C.byref(t))
+        if rc != 0:
+            raise RuntimeError(f"srv_submit failed ({rc})")
+        return t.value
+
+    def wait(self, ticket: int) -> dp_srv_result:
+        out = dp_srv_result()
+        rc = load().srv_wait(self.h, int(ticket), C.byref(out))
+        if rc != 0:
+            raise RuntimeError(f"srv_wait failed ({rc})")
+        return out
+
+    def state(self, rid: int):
+        nc, nw = self.sizes[rid]
+        p = np.zeros(nc); sw = np.zeros(nc); bhp = np.zeros(max(nw, 1))
+        rc = load().srv_get_state(self.h, int(rid), _p(p), _p(sw), _p(bhp))
+        if rc != 0:
+            raise RuntimeError(f"srv_get_state failed ({rc})")
+        return p, sw, bhp[:nw]
+
+    def info(self) -> dp_srv_info:
+        out = dp_srv_info()
+        load().srv_info(self.h, C.byref(out))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().srv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class TorchAllocator:
@@ -309,6 +455,11 @@ class Sim:
         c = np.zeros(self.nb, np.int32)
         n = self._check(load().sim_get_colours(self.h, _p(c)), "sim_get_colours")
         return c, n
+
+    def footprint(self):
+        cur, peak = C.c_uint64(), C.c_uint64()
+        self._check(load().sim_footprint(self.h, C.byref(cur), C.byref(peak)), "sim_footprint")
+        return cur.value, peak.value
 
     def well_index(self):
         wi = np.zeros(sum(w.k_bot - w.k_top + 1 for w in self.prob.wells) + 1)

@@ -58,6 +58,11 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
                         ctypes.byref(out)) == dpsim.DP_EINVAL
     assert L.sim_assemble(None, 1.0) == dpsim.DP_EINVAL
     assert L.sim_solve_step(None, None) == dpsim.DP_EINVAL
+    srv = ctypes.c_void_p()
+    assert L.srv_create(0, 1 << 30, ctypes.byref(o), ctypes.byref(srv)) == dpsim.DP_EINVAL
+    assert L.srv_create(2, 0, ctypes.byref(o), ctypes.byref(srv)) == dpsim.DP_EINVAL
+    assert L.srv_submit(None, 0, 1.0, None) == dpsim.DP_EINVAL
+    assert L.sim_advance_many(None, 2, None, 0, None, None) == dpsim.DP_EINVAL
 
 
 def test_oracle_is_not_linked_into_the_library(lib):
