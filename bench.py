@@ -301,6 +301,8 @@ def main():
     ap.add_argument("--sample-div", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cluster-rows", type=int, default=0,
+                    help="AMG levels up to this many rows run in one cluster launch (0: default)")
     ap.add_argument("--threads", type=int, default=16,
                     help="ensemble mode: host threads driving realisations concurrently")
     ap.add_argument("--mode", default="bench", choices=["bench", "newton2", "ensemble", "serve"],
@@ -330,7 +332,7 @@ def main():
     if args.mode == "serve":
         return run_serve(args)
     prob = workload(args)
-    opts = dpsim.options("report", precision=args.precision)
+    opts = dpsim.options("report", precision=args.precision, cluster_rows=args.cluster_rows)
     if args.mode == "newton2":
         sim = dpsim.Sim(prob, opts)
         out = {}
@@ -445,7 +447,7 @@ def main():
 
     fp64 = None
     if args.precision != 0 and not args.no_fp64_path:
-        o64 = dpsim.options("report", precision=0)
+        o64 = dpsim.options("report", precision=0, cluster_rows=args.cluster_rows)
         with torch.cuda.stream(stream):
             sim64 = dpsim.Sim(prob, o64, stream=stream)
         r = measure(sim64, o64, max(2, args.steps // 2), args.warmup)

@@ -95,7 +95,11 @@ typedef struct {
  * forcing terms of Section 3.1, clipped to [eta_min, eta_max].  precond:
  * 0 none, 1 block ILU(0) only, 2 CPR-FPF.  precision: 0 FP64 everywhere;
  * 1 ILU(0) factors and AMG levels stored and applied in FP32 inside FP64
- * FGMRES. */
+ * FGMRES.  amg_gs_levels: AMG levels 0..amg_gs_levels-1 are smoothed by
+ * multicolour Gauss-Seidel (forward colour order before the coarse
+ * correction, reverse after), the coarser ones by one l1-Jacobi sweep
+ * before and after, x += (b - A x) / sum_j |a_ij| (Baker, Falgout, Kolev and
+ * Yang 2011): one parallel phase per sweep instead of one per colour. */
 typedef struct {
   double newton_tol, newton_atol; int32_t newton_max;
   int32_t eta_mode;
@@ -106,6 +110,12 @@ typedef struct {
   double ds_max;
   int32_t precision;
   int32_t use_graphs;   /* capture the FGMRES iteration in a CUDA graph */
+  int32_t amg_gs_levels;
+  int32_t cluster_rows;  /* AMG levels of at most this many rows run inside one
+                            thread-block-cluster launch per V-cycle (with
+                            use_graphs); < 0: never; 0: the library default,
+                            20000 rows when one of those levels uses
+                            Gauss-Seidel, else never */
 } dp_options;
 
 typedef struct {

@@ -76,7 +76,9 @@ class og_stats(C.Structure):
 def options(mode: str = "parity", **kw) -> og_options:
     """Solver options.  'parity': fixed eta 1e-10 and Newton tolerance 1e-10
     so that two correct implementations agree far inside 1e-8.  'report':
-    the third forcing term (gamma 0.9, beta 2) and Newton tolerance 1e-6."""
+    the third forcing term (gamma 0.9, beta 2), Newton tolerance 1e-6, and
+    l1-Jacobi instead of multicolour Gauss-Seidel on the AMG levels below
+    the finest."""
     o = og_options()
     o.newton_max = 25
     o.newton_atol = 1e-13
@@ -93,6 +95,7 @@ def options(mode: str = "parity", **kw) -> og_options:
         o.eta_mode, o.eta_fixed, o.newton_tol = 0, 1e-10, 1e-10
     else:
         o.eta_mode, o.eta_fixed, o.newton_tol = 3, 1e-4, 1e-6
+        o.amg_gs_levels = 1
     for k, v in kw.items():
         setattr(o, k, v)
     return o
@@ -128,6 +131,7 @@ def lib():
         L.oracle_ilu0_solve.argtypes = [I, P, P, P, P, P, P]
         L.oracle_amg_create.argtypes = [I, P, P, P, D, I, I, C.POINTER(P)]
         L.oracle_amg_vcycle.argtypes = [P, P, P]
+        L.oracle_amg_set_smoother.argtypes = [P, I]
         L.oracle_amg_info.argtypes = [P, I, P, P, P]
         L.oracle_amg_arrays.argtypes = [P, I, P, P, P, P, P]
         L.oracle_amg_destroy.argtypes = [P]
@@ -272,13 +276,15 @@ class OracleSim:
 class OracleAMG:
     """Smoothed-aggregation AMG of the oracle on a scalar CSR matrix."""
 
-    def __init__(self, rowptr, col, val, theta=0.08, coarse_max=128, max_levels=20):
+    def __init__(self, rowptr, col, val, theta=0.08, coarse_max=128, max_levels=20,
+                 gs_levels=30):
         self._a = (_i32(rowptr), _i32(col), _f64(val))
         self.n = len(rowptr) - 1
         h = C.c_void_p()
         lib().oracle_amg_create(self.n, *[_p(a) for a in self._a], float(theta),
                                 int(coarse_max), int(max_levels), C.byref(h))
         self.h = h
+        lib().oracle_amg_set_smoother(self.h, int(gs_levels))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -333,7 +333,7 @@ typedef struct {
 typedef struct {
   int nlev;
   og_level lev[32];
-  int smoother;      /* levels below this one use l1-Jacobi, the others multicolour GS */
+  int smoother;      /* levels from this one on use l1-Jacobi, the finer ones multicolour GS */
   double theta;
   int coarse_max, max_levels;
   int dense_n;       /* coarsest dense LU size (0: coarsest uses GS) */
@@ -765,6 +765,12 @@ int oracle_amg_create(int32_t n, const int32_t *rowptr, const int32_t *col,
   og_csr A = {n, n, rowptr[n], (int *)rowptr, (int *)col, (double *)val};
   amg_setup(m, &A);
   *out = m;
+  return 0;
+}
+
+int oracle_amg_set_smoother(void *amg, int32_t gs_levels) {
+  if (!amg || gs_levels < 0) return OG_EINVAL;
+  ((og_amg *)amg)->smoother = gs_levels;
   return 0;
 }
 

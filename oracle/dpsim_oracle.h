@@ -79,6 +79,9 @@ int  oracle_ilu0_solve(int32_t n, const int32_t *rowptr, const int32_t *col,
 int  oracle_amg_create(int32_t n, const int32_t *rowptr, const int32_t *col,
                        const double *val, double theta, int32_t coarse_max,
                        int32_t max_levels, void **out);
+/* levels 0..gs_levels-1 smoothed by multicolour Gauss-Seidel, the coarser
+ * ones by l1-Jacobi (default: Gauss-Seidel on every level) */
+int  oracle_amg_set_smoother(void *amg, int32_t gs_levels);
 int  oracle_amg_vcycle(void *amg, const double *b, double *x);
 int  oracle_amg_info(void *amg, int32_t level, int32_t *n, int32_t *nnz, int32_t *nagg);
 int  oracle_amg_arrays(void *amg, int32_t level, int32_t *rowptr, int32_t *col,

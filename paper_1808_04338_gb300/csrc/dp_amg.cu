@@ -581,16 +581,25 @@ static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const
 
 // ---------------------------------------------------------------- hierarchy
 
-// inverse diagonal of a level operator (0 where the diagonal is zero)
-__global__ void k_level_dinv(int n, const int *dpos, const double *val, double *dinv) {
+// Smoother scaling of a level operator: 1 / a_ii for Gauss-Seidel, or
+// 1 / sum_j |a_ij| for l1-Jacobi (0 where that is zero: the row is left as is)
+__global__ void k_level_dinv(int n, const int *dpos, const int *rowptr, const double *val, int l1,
+                             double *dinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double d = dpos[i] >= 0 ? val[dpos[i]] : 0.0;
+  double d = 0.0;
+  if (l1) {
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) d += fabs(val[e]);
+  } else {
+    d = dpos[i] >= 0 ? val[dpos[i]] : 0.0;
+  }
   dinv[i] = d != 0.0 ? 1.0 / d : 0.0;
 }
 
 int level_dinv(Sim *s, Level &L) {
-  if (L.dpos) DP_LAUNCH(s, k_level_dinv, nblk(L.n), kBlock, 0, L.n, L.dpos, L.val, L.dinv);
+  if (L.dpos)
+    DP_LAUNCH(s, k_level_dinv, nblk(L.n), kBlock, 0, L.n, L.dpos, L.rowptr, L.val, L.l1 ? 1 : 0,
+              L.dinv);
   return DP_OK;
 }
 
@@ -671,6 +680,7 @@ int amg_setup(Sim *s) {
   L0.rowptr = s->A.rowptr;
   L0.col = s->A.col;
   L0.val = s->ap;
+  L0.l1 = o.amg_gs_levels <= 0;
   L0.dinv = (double *)dalloc(s, (size_t)L0.n * 8);
   L0.dinvf = (float *)dalloc(s, (size_t)L0.n * 4);
   if (!L0.dinv || !L0.dinvf) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
@@ -768,6 +778,7 @@ int amg_setup(Sim *s) {
     L.ap_val = (double *)dalloc(s, (size_t)std::max(L.ap_nnz, 1) * 8);
     Level N;
     N.n = na;
+    N.l1 = l + 1 >= o.amg_gs_levels;
     DP_TRY(spgemm_symbolic(s, na, L.r_rowptr, L.r_col, L.ap_rowptr, L.ap_col, &N.rowptr, &N.col,
                            &N.nnz, &prap));
     L.rap_G = prap.G; L.rap_off = prap.off; L.rap_pos = prap.pos;
@@ -817,6 +828,13 @@ void amg_free(Sim *s) {
   s->cl_level = -1;
   if (s->coarse_lu) dfree(s, s->coarse_lu);
   if (s->coarse_piv) dfree(s, s->coarse_piv);
+  if (s->coarse_inv) dfree(s, s->coarse_inv);
+  s->coarse_inv = nullptr;
+  if (s->l0_pv) dfree(s, s->l0_pv);
+  if (s->l0_pvf) dfree(s, s->l0_pvf);
+  s->l0_pv = nullptr;
+  s->l0_pvf = nullptr;
+  s->l0_lu = false;
   s->coarse_lu = nullptr;
   s->coarse_piv = nullptr;
   s->coarse_n = 0;

@@ -3,8 +3,9 @@
 //
 // Below a size threshold every level of the hierarchy is small, but its
 // multicolour Gauss-Seidel still needs one ordered phase per colour (17-46
-// colours per level on the 8M-unknown problem).  Launching a kernel per
-// phase costs more than the phase's work.  Here one cluster of CTAs (up to
+// colours per level on the 8M-unknown problem), and even l1-Jacobi needs a
+// few phases per level.  Launching a kernel per phase costs more than the
+// phase's work.  Here one cluster of CTAs (up to
 // 16 CTAs of 512 threads, one per SM of a GPC) runs all phases of levels l0..L-1: the colour
 // sweeps, residuals, restrictions, the dense coarsest solve and the
 // prolongations, separated by hardware cluster barriers (barrier.cluster
@@ -26,6 +27,7 @@ namespace dp {
 template <typename T>
 struct LevelDev {
   int n, ncolour, lanes;
+  int l1;                         // l1-Jacobi smoothing; dinv = 1 / sum_j |a_ij|
   const int *rowptr, *col, *clist, *cstart;
   const T *val, *dinv;
   const int *r_rowptr, *r_col;   // restriction to the next level
@@ -61,6 +63,28 @@ __device__ __forceinline__ T row_dot_l2(int e0, int e1, int lane, int G, const i
   }
   for (; e < e1; e += G) s0 = fma(__ldg(val + e), __ldcg(x + __ldg(col + e)), s0);
   return (s0 + s1) + (s2 + s3);
+}
+
+// sum_j a_ij b_j d_j over the lane's entries: the residual of the l1-Jacobi
+// pre-smoothing from zero without storing x first (b through L2, d constant)
+template <typename T>
+__device__ __forceinline__ T row_dot_bd(int e0, int e1, int lane, int G, const int *__restrict__ col,
+                                        const T *__restrict__ val, const T *b,
+                                        const T *__restrict__ d) {
+  T s0 = T(0), s1 = T(0);
+  int e = e0 + lane;
+  for (; e + G < e1; e += 2 * G) {
+    int c0 = __ldg(col + e), c1 = __ldg(col + e + G);
+    T v0 = __ldg(val + e), v1 = __ldg(val + e + G);
+    T b0 = __ldcg(b + c0), b1 = __ldcg(b + c1);
+    s0 = fma(v0, b0 * __ldg(d + c0), s0);
+    s1 = fma(v1, b1 * __ldg(d + c1), s1);
+  }
+  if (e < e1) {
+    int c0 = __ldg(col + e);
+    s0 = fma(__ldg(val + e), __ldcg(b + c0) * __ldg(d + c0), s0);
+  }
+  return s0 + s1;
 }
 
 template <typename T>
@@ -170,12 +194,81 @@ __device__ void dense_solve_cta(int n, const double *a, const int *piv, const T 
   for (int i = t; i < n; i += nt) __stcg(x + i, T(xs[i]));
 }
 
+// l1-Jacobi pre-smoothing from zero and the residual in one phase:
+// x_i = b_i d_i, r_i = b_i - sum_j a_ij b_j d_j.
+template <typename T>
+__device__ void jacobi_pre_cl(const LevelDev<T> &L, const T *b, T *x, T *r, int gt, int nt) {
+  const int G = L.lanes;
+  const int *__restrict__ rowptr = L.rowptr;
+  const int *__restrict__ col = L.col;
+  const T *__restrict__ val = L.val;
+  const T *__restrict__ d = L.dinv;
+  for_rows<T>(
+      L.n, G, gt, nt,
+      [&](int i, int lane, bool valid) -> T {
+        return valid ? row_dot_bd<T>(__ldg(rowptr + i), __ldg(rowptr + i + 1), lane, G, col, val, b,
+                                     d)
+                     : T(0);
+      },
+      [&](int i, T s) {
+        T bi = __ldcg(b + i);
+        __stcg(x + i, bi * __ldg(d + i));
+        __stcg(r + i, bi - s);
+      });
+}
+
+// One l1-Jacobi sweep through t (t_i = x_i + (b_i - (A x)_i) d_i), then
+// t copied back into x: two phases.
+template <typename T>
+__device__ void jacobi_post_cl(const LevelDev<T> &L, const T *b, T *x, T *t, int gt, int nt,
+                               cg::cluster_group &cl) {
+  const int G = L.lanes;
+  const int *__restrict__ rowptr = L.rowptr;
+  const int *__restrict__ col = L.col;
+  const T *__restrict__ val = L.val;
+  const T *__restrict__ d = L.dinv;
+  for_rows<T>(
+      L.n, G, gt, nt,
+      [&](int i, int lane, bool valid) -> T {
+        return valid ? row_dot_l2<T>(__ldg(rowptr + i), __ldg(rowptr + i + 1), lane, G, col, val, x)
+                     : T(0);
+      },
+      [&](int i, T s) { __stcg(t + i, fma(__ldcg(b + i) - s, __ldg(d + i), __ldcg(x + i))); });
+  cl.sync();
+  for (int i = gt; i < L.n; i += nt) __stcg(x + i, __ldcg(t + i));
+  cl.sync();
+}
+
 constexpr int kClusterThreads = 512;
+
+// x = inv b for the coarsest level from its explicit FP64 inverse: one phase
+template <typename T>
+__device__ void dense_mv_cl(int n, const double *__restrict__ inv, const T *b, T *x, int gt,
+                            int nt) {
+  int G = 1;
+  while (G < 32 && 4 * G < n) G <<= 1;
+  for_rows<double>(
+      n, G, gt, nt,
+      [&](int i, int lane, bool valid) -> double {
+        double s0 = 0.0, s1 = 0.0;
+        if (valid) {
+          const double *row = inv + (size_t)i * n;
+          int j = lane;
+          for (; j + G < n; j += 2 * G) {
+            s0 = fma(__ldg(row + j), double(__ldcg(b + j)), s0);
+            s1 = fma(__ldg(row + j + G), double(__ldcg(b + j + G)), s1);
+          }
+          if (j < n) s0 = fma(__ldg(row + j), double(__ldcg(b + j)), s0);
+        }
+        return s0 + s1;
+      },
+      [&](int i, double s) { __stcg(x + i, T(s)); });
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kClusterThreads, 1)
     k_coarse_cycle(const LevelDev<T> *__restrict__ lv, int l0, int nl, const T *b0, T *x0,
-                   const double *lu, const int *piv, int dense_n) {
+                   const double *lu, const int *piv, const double *inv, int dense_n) {
   cg::cluster_group cl = cg::this_cluster();
   int gt = (int)cl.block_rank() * blockDim.x + threadIdx.x;
   int nt = (int)cl.num_blocks() * blockDim.x;
@@ -192,17 +285,21 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     const int *__restrict__ rcol = L.r_col;
     const T *__restrict__ rval = L.r_val;
     T *r = L.r, *nb = lv[l + 1].b;
-    for (int i = gt; i < n; i += nt) __stcg(x + i, T(0));
-    cl.sync();
-    gs_sweep_cl<T>(L, b, x, true, gt, nt, cl);
-    for_rows<T>(
-        n, G, gt, nt,
-        [&](int i, int lane, bool valid) -> T {
-          return valid ? row_dot_l2<T>(__ldg(rowptr + i), __ldg(rowptr + i + 1), lane, G, col, val,
-                                       x)
-                       : T(0);
-        },
-        [&](int i, T s) { __stcg(r + i, __ldcg(b + i) - s); });
+    if (L.l1) {
+      jacobi_pre_cl<T>(L, b, x, r, gt, nt);
+    } else {
+      for (int i = gt; i < n; i += nt) __stcg(x + i, T(0));
+      cl.sync();
+      gs_sweep_cl<T>(L, b, x, true, gt, nt, cl);
+      for_rows<T>(
+          n, G, gt, nt,
+          [&](int i, int lane, bool valid) -> T {
+            return valid ? row_dot_l2<T>(__ldg(rowptr + i), __ldg(rowptr + i + 1), lane, G, col,
+                                         val, x)
+                         : T(0);
+          },
+          [&](int i, T s) { __stcg(r + i, __ldcg(b + i) - s); });
+    }
     cl.sync();
     for_rows<T>(
         nn, rG, gt, nt,
@@ -218,9 +315,16 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     const LevelDev<T> &L = lv[nl - 1];
     const T *b = nl - 1 == l0 ? b0 : L.b;
     T *x = nl - 1 == l0 ? x0 : L.x;
-    if (dense_n == L.n && L.n > 0) {
+    if (dense_n == L.n && L.n > 0 && inv) {
+      dense_mv_cl<T>(L.n, inv, b, x, gt, nt);
+      cl.sync();
+    } else if (dense_n == L.n && L.n > 0) {
       if (cl.block_rank() == 0) dense_solve_cta<T>(L.n, lu, piv, b, x);
       cl.sync();
+    } else if (L.l1) {
+      jacobi_pre_cl<T>(L, b, x, L.r, gt, nt);
+      cl.sync();
+      jacobi_post_cl<T>(L, b, x, L.r, gt, nt, cl);
     } else {
       for (int i = gt; i < L.n; i += nt) __stcg(x + i, T(0));
       cl.sync();
@@ -247,7 +351,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         },
         [&](int i, T s) { __stcg(x + i, __ldcg(x + i) + s); });
     cl.sync();
-    gs_sweep_cl<T>(L, b, x, false, gt, nt, cl);
+    if (L.l1) jacobi_post_cl<T>(L, b, x, L.r, gt, nt, cl);
+    else gs_sweep_cl<T>(L, b, x, false, gt, nt, cl);
   }
 }
 
@@ -275,6 +380,7 @@ static int upload_levels(Sim *s, void **dst) {
     Level &L = s->lev[l];
     LevelDev<T> &d = h[l];
     d.n = L.n;
+    d.l1 = L.l1 ? 1 : 0;
     d.ncolour = L.ncolour;
     d.lanes = cluster_lanes(L.n ? (double)L.nnz / L.n : 0.0);
     d.rowptr = L.rowptr; d.col = L.col; d.clist = L.clist; d.cstart = L.cstart_dev;
@@ -427,11 +533,20 @@ int cluster_setup(Sim *s) {
   }
   s->cl_size = csize;
   if (csize == 0 || !s->opt.use_graphs) return DP_OK;  // the per-launch cycle stays in use
+  int rows = s->opt.cluster_rows == 0 ? kClusterMaxRows : s->opt.cluster_rows;
   int first = -1;
-  for (int l = 0; l < (int)s->lev.size(); ++l)
-    if (s->lev[l].n <= kClusterMaxRows) { first = l; break; }
+  for (int l = 0; l < (int)s->lev.size() && rows > 0; ++l)
+    if (s->lev[l].n <= rows) { first = l; break; }
   if (first < 0) return DP_OK;
-  for (int l = first; l < (int)s->lev.size(); ++l) DP_TRY(ell_build(s, s->lev[l]));
+  // By default the cluster runs only where it saves launches: a level with
+  // multicolour Gauss-Seidel has one phase per colour, an l1-Jacobi level
+  // five, and on GB300 five full-GPU launches of a small level (graph
+  // launched) cost less than the same phases on the cluster's 16 SMs.
+  bool gs = false;
+  for (int l = first; l < (int)s->lev.size(); ++l) gs |= !s->lev[l].l1;
+  if (s->opt.cluster_rows == 0 && !gs) return DP_OK;
+  for (int l = first; l < (int)s->lev.size(); ++l)
+    if (!s->lev[l].l1) DP_TRY(ell_build(s, s->lev[l]));   // Gauss-Seidel levels only
   DP_TRY(upload_levels<double>(s, &s->cl_lev64));
   DP_TRY(upload_levels<float>(s, &s->cl_lev32));
   s->cl_level = first;
@@ -455,7 +570,7 @@ int coarse_cycle(Sim *s, int l0, const T *b, T *x) {
     LaunchScope ls(s, "k_coarse_cycle");
     DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_coarse_cycle<T>, lv, l0, nl, b, x,
                                   (const double *)s->coarse_lu, (const int *)s->coarse_piv,
-                                  s->coarse_n));
+                                  (const double *)s->coarse_inv, s->coarse_n));
   }
   return DP_OK;
 }

@@ -78,6 +78,7 @@ struct Level {
   float *r_valf = nullptr;
   int *ap_rowptr = nullptr, *ap_col = nullptr;
   double *ap_val = nullptr;
+  bool l1 = false;                        // l1-Jacobi smoothing (dinv = 1 / sum_j |a_ij|)
   double *dinv = nullptr;                 // 1 / a_ii
   float *dinvf = nullptr;
   int *ap_off = nullptr, *ap_pos = nullptr, *rap_off = nullptr, *rap_pos = nullptr;
@@ -157,11 +158,12 @@ int cpr_apply(Sim *s, const double *r, double *z);
 int fgmres(Sim *s, double tol, int *iters, double *relres);
 int la_alloc(Sim *s);
 int mixed_refresh(Sim *s);
+int l0_refresh(Sim *s);
 int lanes_for(double mean_len);
 void graphs_free(Sim *s);
 
 // dp_cycle.cu (the coarse levels of the V-cycle in one cluster launch)
-constexpr int kClusterMaxRows = 20000;
+constexpr int kClusterMaxRows = 20000;   // default of dp_options.cluster_rows
 int cluster_setup(Sim *s);
 int cluster_refresh(Sim *s);
 template <typename T> int coarse_cycle(Sim *s, int l0, const T *b, T *x);
@@ -231,6 +233,12 @@ struct Sim {
   int *srowptr = nullptr, *scol = nullptr;
   double *sval = nullptr, *sa00 = nullptr, *sa01 = nullptr;
   double *coarse_lu = nullptr;
+  double *coarse_inv = nullptr;
+  // level-0 pressure values in the colour order of the ILU(0) pattern (the
+  // same greedy colouring), for contiguous Gauss-Seidel colour sweeps
+  bool l0_lu = false;
+  double *l0_pv = nullptr;
+  float *l0_pvf = nullptr;   // inverse from the LU factors (n <= kInverseMax), row-major
   int *coarse_piv = nullptr;
   int coarse_n = 0;
   int cl_level = -1, cl_size = 0;                    // first level of the cluster cycle

@@ -398,6 +398,59 @@ __global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int 
   }
 }
 
+// l1-Jacobi pre-smoothing from x = 0 fused with the residual: x_i = b_i d_i
+// and r_i = b_i - sum_j a_ij b_j d_j (d = 1 / sum_j |a_ij|, 0 for an empty row).
+template <int G, typename T>
+__global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restrict__ rowptr,
+                                                       const int *__restrict__ col,
+                                                       const T *__restrict__ val,
+                                                       const T *__restrict__ d,
+                                                       const T *__restrict__ b, T *__restrict__ x,
+                                                       T *__restrict__ r) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  T s0 = T(0), s1 = T(0);
+  int e = e0 + lane;
+  for (; e + G < e1; e += 2 * G) {
+    int c0 = __ldg(col + e), c1 = __ldg(col + e + G);
+    T v0 = __ldg(val + e), v1 = __ldg(val + e + G);
+    s0 = fma(v0, __ldg(b + c0) * __ldg(d + c0), s0);
+    s1 = fma(v1, __ldg(b + c1) * __ldg(d + c1), s1);
+  }
+  if (e < e1) {
+    int c0 = __ldg(col + e);
+    s0 = fma(__ldg(val + e), __ldg(b + c0) * __ldg(d + c0), s0);
+  }
+  T s = s0 + s1;
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) {
+    T bi = b[i];
+    x[i] = bi * d[i];
+    r[i] = bi - s;
+  }
+}
+
+// One l1-Jacobi sweep: t_i = x_i + (b_i - (A x)_i) d_i for every row from
+// the old x (t must not alias x).
+template <int G, typename T>
+__global__ void __launch_bounds__(kBlock) k_jacobi_sweep(int n, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         const T *__restrict__ val,
+                                                         const T *__restrict__ d,
+                                                         const T *__restrict__ b,
+                                                         const T *__restrict__ x,
+                                                         T *__restrict__ tout) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) tout[i] = fma(b[i] - s, d[i], x[i]);
+}
+
 // r = b - A x
 template <int G, typename T>
 __global__ void __launch_bounds__(kBlock) k_csr_resid(int n, const int *__restrict__ rowptr,
@@ -544,6 +597,7 @@ __global__ void __launch_bounds__(1024) k_dense_lu(int n, double *a, int *piv) {
 }
 
 constexpr int kDenseMax = 4096;
+constexpr int kInverseMax = 1024;   // coarsest levels up to this size keep an explicit inverse
 
 // Solve with the FP64 LU factors; b and x in T, the solve itself in FP64 in
 // shared memory.
@@ -574,6 +628,44 @@ __global__ void __launch_bounds__(1024) k_dense_solve(int n, const double *a, co
   for (int i = t; i < n; i += nt) x[i] = T(xs[i]);
 }
 
+// Inverse of the coarsest operator from its LU factors and row pivots, one
+// column per thread: the solve of k_dense_solve applied to the unit vector
+// e_c (the same steps in the same order), kept in column c of `inv`.
+__global__ void k_dense_inverse(int n, const double *a, const int *piv, double *inv) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = i == c ? 1.0 : 0.0;
+  for (int k = 0; k < n; ++k) {
+    int p = piv[k];
+    if (p != k && p >= 0 && p < n) {
+      double tmp = inv[(size_t)k * n + c];
+      inv[(size_t)k * n + c] = inv[(size_t)p * n + c];
+      inv[(size_t)p * n + c] = tmp;
+    }
+    double xk = inv[(size_t)k * n + c];
+    for (int i = k + 1; i < n; ++i) inv[(size_t)i * n + c] -= a[(size_t)i * n + k] * xk;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double d = a[(size_t)i * n + i];
+    double xi = d != 0.0 ? inv[(size_t)i * n + c] / d : 0.0;
+    inv[(size_t)i * n + c] = xi;
+    for (int r = 0; r < i; ++r) inv[(size_t)r * n + c] -= a[(size_t)r * n + i] * xi;
+  }
+}
+
+// x = inv b, one warp per row, FP64 accumulation
+template <typename T>
+__global__ void k_dense_mv(int n, const double *__restrict__ inv, const T *__restrict__ b,
+                           T *__restrict__ x) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n) return;   // whole warps leave together
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s = fma(inv[(size_t)w * n + j], double(b[j]), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[w] = T(s);
+}
+
 int coarse_factor(Sim *s) {
   Level &L = s->lev.back();
   int n = L.n;
@@ -584,16 +676,110 @@ int coarse_factor(Sim *s) {
     s->coarse_lu = (double *)dalloc(s, (size_t)n * n * 8);
     s->coarse_piv = (int *)dalloc(s, (size_t)n * 4);
     if (!s->coarse_lu || !s->coarse_piv) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+    if (s->coarse_inv) dfree(s, s->coarse_inv);
+    s->coarse_inv = nullptr;
+    if (n <= kInverseMax) {
+      s->coarse_inv = (double *)dalloc(s, (size_t)n * n * 8);
+      if (!s->coarse_inv) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+    }
   }
   s->coarse_n = n;
   DP_LAUNCH(s, k_csr_to_dense, nblk(n), kBlock, 0, n, L.rowptr, L.col, L.val, s->coarse_lu);
   DP_LAUNCH(s, k_dense_lu, 1, 1024, 0, n, s->coarse_lu, s->coarse_piv);
+  if (s->coarse_inv)
+    DP_LAUNCH(s, k_dense_inverse, nblk(n, 128), 128, 0, n, s->coarse_lu, s->coarse_piv,
+              s->coarse_inv);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// l1-Jacobi: pre-smoothing from zero fused with the residual into r, and a
+// sweep after the coarse correction through r (free by then) back into x.
+template <typename T>
+static int jacobi_pre(Sim *s, Level &L, const T *b, T *x, T *r) {
+  long long thr = (long long)L.n * L.G;
+  DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_pre<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
+                             L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
+  return DP_OK;
+}
+
+template <typename T>
+static int jacobi_post(Sim *s, Level &L, const T *b, T *x, T *r) {
+  long long thr = (long long)L.n * L.G;
+  DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_sweep<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
+                             L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
+  DP_CUDA(s, cudaMemcpyAsync(x, r, (size_t)L.n * sizeof(T), cudaMemcpyDeviceToDevice, s->stream));
+  return DP_OK;
+}
+
+// One colour of Gauss-Seidel on level 0 from its colour-ordered copy: the
+// rows q of a colour are contiguous in the ILU(0) pattern (row q is natural
+// row perm[q], entries lu_col[e] with values pv[e]), so a sweep streams the
+// operator once instead of touching every row's sectors for every colour.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_lu(int r0, int r1, const int *__restrict__ perm,
+                                                  const int *__restrict__ lu_rowptr,
+                                                  const int *__restrict__ lu_col,
+                                                  const T *__restrict__ pv,
+                                                  const T *__restrict__ dinv,
+                                                  const T *__restrict__ b, T *x) {
+  int q = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= r1) return;
+  int i = __ldg(perm + q);
+  T s = row_dot<1, T>(__ldg(lu_rowptr + q), __ldg(lu_rowptr + q + 1), 0, lu_col, pv, x);
+  T di = dinv[i];
+  if (di != T(0)) x[i] = fma(b[i] - s, di, x[i]);
+}
+
+template <typename T>
+__global__ void k_gather_vals(long long n, const int *__restrict__ src, const double *__restrict__ v,
+                              T *__restrict__ out) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = T(v[__ldg(src + e)]);
+}
+
+// The colour-ordered level-0 values, refreshed with the level's values
+// every Newton step (used when level 0 is smoothed by Gauss-Seidel: its
+// colouring is the ILU(0) colouring, same pattern and same algorithm).
+int l0_refresh(Sim *s) {
+  if (s->lev.empty() || s->opt.precond != 2) return DP_OK;
+  Level &L = s->lev[0];
+  if (!s->l0_lu) {
+    if (L.l1 || L.ncolour != s->ncolour || L.rowptr != s->A.rowptr) return DP_OK;
+    for (int c = 0; c <= L.ncolour; ++c)
+      if (L.cstart[c] != s->lu_cstart[c]) return DP_OK;
+    size_t nnz = (size_t)std::max(L.nnz, 1);
+    if (s->opt.precision == 1) s->l0_pvf = (float *)dalloc(s, nnz * 4);
+    else s->l0_pv = (double *)dalloc(s, nnz * 8);
+    if (!s->l0_pvf && !s->l0_pv) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+    s->l0_lu = true;
+  }
+  if (s->l0_pvf)
+    DP_LAUNCH(s, k_gather_vals<float>, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->lu_src, L.val,
+              s->l0_pvf);
+  else
+    DP_LAUNCH(s, k_gather_vals<double>, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->lu_src, L.val,
+              s->l0_pv);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
 
 template <typename T>
 static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
+  const T *pv = nullptr;
+  if (&L == &s->lev[0] && s->l0_lu) {
+    if constexpr (sizeof(T) == 8) pv = (const T *)s->l0_pv; else pv = (const T *)s->l0_pvf;
+  }
+  if (pv) {
+    for (int t = 0; t < L.ncolour; ++t) {
+      int c = forward ? t : L.ncolour - 1 - t;
+      int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
+      if (r1 > r0)
+        DP_LAUNCH(s, k_gs_lu<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->perm, s->lu_rowptr,
+                  s->lu_col, pv, LV<T>::dinv(L), b, x);
+    }
+    return DP_OK;
+  }
   for (int t = 0; t < L.ncolour; ++t) {
     int c = forward ? t : L.ncolour - 1 - t;
     int r0 = L.cstart[c], r1 = L.cstart[c + 1];
@@ -606,9 +792,10 @@ static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
   return DP_OK;
 }
 
-// V(1,1) cycle from level l in precision T: pre-smoothing (colours forward),
-// residual, restriction, coarse correction, prolongation, post-smoothing
-// (colours reversed); dense LU on the coarsest level.
+// V(1,1) cycle from level l in precision T: pre-smoothing (colours forward,
+// or one l1-Jacobi sweep), residual, restriction, coarse correction,
+// prolongation, post-smoothing (colours reversed, or one l1-Jacobi sweep);
+// dense LU on the coarsest level.
 template <typename T>
 static int vcycle_t(Sim *s, int l, const T *b, T *x) {
   if (l == s->cl_level) return coarse_cycle<T>(s, l, b, x);
@@ -616,7 +803,15 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x) {
   int n = L.n;
   if (l == (int)s->lev.size() - 1) {
     if (s->coarse_n == n && n > 0) {
-      DP_LAUNCH(s, k_dense_solve<T>, 1, 1024, 0, n, s->coarse_lu, s->coarse_piv, b, x);
+      if (s->coarse_inv)
+        DP_LAUNCH(s, k_dense_mv<T>, nblk(32LL * n), kBlock, 0, n, s->coarse_inv, b, x);
+      else
+        DP_LAUNCH(s, k_dense_solve<T>, 1, 1024, 0, n, s->coarse_lu, s->coarse_piv, b, x);
+      return DP_OK;
+    }
+    if (L.l1) {
+      DP_TRY(jacobi_pre<T>(s, L, b, x, LV<T>::r(L)));
+      DP_TRY(jacobi_post<T>(s, L, b, x, LV<T>::r(L)));
       return DP_OK;
     }
     DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), s->stream));
@@ -626,13 +821,18 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x) {
   }
   Level &N = s->lev[l + 1];
   T *r = LV<T>::r(L), *nb = LV<T>::b(N), *nx = LV<T>::x(N);
-  DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), s->stream));
-  DP_TRY(gs_sweep<T>(s, L, b, x, true));
-  DP_TRY(csr_resid<T>(s, L, b, x, r));
+  if (L.l1) {
+    DP_TRY(jacobi_pre<T>(s, L, b, x, r));
+  } else {
+    DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), s->stream));
+    DP_TRY(gs_sweep<T>(s, L, b, x, true));
+    DP_TRY(csr_resid<T>(s, L, b, x, r));
+  }
   DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, L.r_col, LV<T>::rval(L), r, nb, 0));
   DP_TRY(vcycle_t<T>(s, l + 1, nb, nx));
   DP_TRY(csr_mv<T>(s, n, L.p_G, L.p_rowptr, L.p_col, LV<T>::pval(L), nx, x, 1));
-  DP_TRY(gs_sweep<T>(s, L, b, x, false));
+  if (L.l1) DP_TRY(jacobi_post<T>(s, L, b, x, r));
+  else DP_TRY(gs_sweep<T>(s, L, b, x, false));
   return DP_OK;
 }
 
@@ -710,57 +910,151 @@ int cpr_apply(Sim *s, const double *r, double *z) {
 constexpr int kDotBlocks = 608;   // 4 x 152 SMs
 constexpr int kDotVec = 8;        // vectors per pass
 
-__global__ void __launch_bounds__(kBlock) k_multidot(long long N, const double *__restrict__ V,
-                                                     long long ldv, int nv,
+// part[b][part_off + k] = block b's share of V_k . w for k < NV; with SELF
+// also w . w into slot 31.  A gate that points at 0.0 makes the launch a
+// no-op (the reorthogonalisation pass of an Arnoldi step that needs none).
+// Each thread takes two double2 of w and of every V_k per trip (4 elements)
+// and issues all of those loads before the FMAs, so that enough bytes are in
+// flight to cover HBM latency; N is even and the vectors 16-byte aligned.
+template <int NV, bool SELF>
+__global__ void __launch_bounds__(kBlock, kDotBlocks / 152) k_multidot(long long N, const double *__restrict__ V,
+                                                     long long ldv,
                                                      const double *__restrict__ w,
-                                                     double *__restrict__ part, int part_off) {
-  double acc[kDotVec];
+                                                     double *__restrict__ part, int part_off,
+                                                     const double *__restrict__ gate) {
+  if (gate && *gate == 0.0) return;
+  double acc[NV];
+  double accw = 0.0;
 #pragma unroll
-  for (int k = 0; k < kDotVec; ++k) acc[k] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    double wi = w[i];
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  const long long N2 = N >> 1;   // double2 elements
+  const double2 *w2 = reinterpret_cast<const double2 *>(w);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < N2; i += 2 * stride) {
+    double2 wa = __ldg(w2 + i), wb = __ldg(w2 + i + stride);
+    double2 va[NV], vb[NV];
 #pragma unroll
-    for (int k = 0; k < kDotVec; ++k)
-      if (k < nv) acc[k] += V[k * ldv + i] * wi;
+    for (int k = 0; k < NV; ++k) {
+      const double2 *v2 = reinterpret_cast<const double2 *>(V + k * ldv);
+      va[k] = __ldg(v2 + i);
+      vb[k] = __ldg(v2 + i + stride);
+    }
+    if (SELF) {
+      accw = fma(wa.x, wa.x, accw); accw = fma(wa.y, wa.y, accw);
+      accw = fma(wb.x, wb.x, accw); accw = fma(wb.y, wb.y, accw);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      acc[k] = fma(va[k].x, wa.x, acc[k]); acc[k] = fma(va[k].y, wa.y, acc[k]);
+      acc[k] = fma(vb[k].x, wb.x, acc[k]); acc[k] = fma(vb[k].y, wb.y, acc[k]);
+    }
   }
-  __shared__ double sh[kBlock / 32][kDotVec];
+  if (i < N2) {
+    double2 wa = __ldg(w2 + i);
+    if (SELF) { accw = fma(wa.x, wa.x, accw); accw = fma(wa.y, wa.y, accw); }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double2 va = __ldg(reinterpret_cast<const double2 *>(V + k * ldv) + i);
+      acc[k] = fma(va.x, wa.x, acc[k]); acc[k] = fma(va.y, wa.y, acc[k]);
+    }
+  }
+  constexpr int NS = NV + (SELF ? 1 : 0);
+  __shared__ double sh[kBlock / 32][kDotVec + 1];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kDotVec; ++k) {
-    double v = acc[k];
+  for (int k = 0; k < NS; ++k) {
+    double v = k < NV ? acc[k] : accw;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) sh[wid][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < nv) {
+  if (threadIdx.x < NS) {
+    int k = threadIdx.x;
     double v = 0.0;
-    for (int q = 0; q < kBlock / 32; ++q) v += sh[q][threadIdx.x];
-    part[(size_t)blockIdx.x * 32 + part_off + threadIdx.x] = v;
+    for (int q = 0; q < kBlock / 32; ++q) v += sh[q][k];
+    part[(size_t)blockIdx.x * 32 + (k == NV ? 31 : part_off + k)] = v;
   }
 }
 
 // dots[k] = sum_b part[b][k] (fixed order); mode 1: also add into H[:, j];
 // mode 2: dots[0] = sqrt(sum), H[j+1][j] = it.
+// Modes 3 and 4 are the two passes of classical Gram-Schmidt with the DGKS
+// test (Daniel, Gragg, Kaufman and Stewart 1976): both add the projections
+// into H[:, j] and take ||w - V h||^2 = w.w - h.h (slot 31 holds w.w).
+// Mode 3 sets scal[4] = 1 when that is below half of w.w (cancellation: a
+// second pass is needed), else stores beta = h_{j+1,j} in H and scal[2].
+// Mode 4 runs only when scal[4] = 1 and stores beta.
 // 256 threads: lane k of group g sums the partials of blocks g, g+8, ...;
 // the eight group sums are then added in group order.
 __global__ void __launch_bounds__(256) k_dot_final(const double *part, int nblocks, int nv,
                                                    double *dots, double *H, int m, int j,
-                                                   int mode) {
+                                                   int mode, double *scal) {
+  if (mode == 4 && scal[4] == 0.0) return;
   __shared__ double sh[8][32];
   int k = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  bool self = mode >= 3;
+  bool active = k < nv || (self && k == 31);
   double v = 0.0;
-  if (k < nv)
+  if (active)
     for (int b = grp; b < nblocks; b += 8) v += part[(size_t)b * 32 + k];
   sh[grp][k] = v;
   __syncthreads();
-  if (grp != 0 || k >= nv) return;
+  if (grp != 0) return;
   v = 0.0;
   for (int q = 0; q < 8; ++q) v += sh[q][k];
-  if (mode == 2) { v = sqrt(v); dots[0] = v; H[(size_t)(j + 1) * m + j] = v; return; }
-  dots[k] = v;
-  if (mode == 1) H[(size_t)k * m + j] += v;
+  if (mode == 2) {
+    if (k == 0) { v = sqrt(v); dots[0] = v; H[(size_t)(j + 1) * m + j] = v; }
+    return;
+  }
+  if (k < nv) {
+    dots[k] = v;
+    if (mode != 0) H[(size_t)k * m + j] += v;
+  }
+  if (!self) return;
+  double hh = k < nv ? v * v : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+  double ww = __shfl_sync(0xffffffffu, v, 31);
+  if (k != 0) return;
+  double b2 = ww - hh;
+  if (mode == 3 && b2 < 0.5 * ww) { scal[4] = 1.0; return; }
+  double beta = sqrt(b2 > 0.0 ? b2 : 0.0);
+  if (mode == 3) scal[4] = 0.0;
+  H[(size_t)(j + 1) * m + j] = beta;
+  scal[2] = beta;
+}
+
+// One projection of the Arnoldi step: w - V c.  Pass 0 writes it back into
+// w when scal[4] = 1 (a second pass follows), else writes the normalised
+// vector (w - V c) / scal[2] into out; pass 1 runs only when scal[4] = 1 and
+// writes the normalised vector.
+__global__ void __launch_bounds__(kBlock) k_project(long long N, const double *__restrict__ V,
+                                                    long long ldv, int nv,
+                                                    const double *__restrict__ c,
+                                                    double *__restrict__ w,
+                                                    double *__restrict__ out,
+                                                    const double *__restrict__ scal, int pass) {
+  __shared__ double cs[32];
+  __shared__ double rb;
+  __shared__ int fin;
+  if (threadIdx.x == 0) {
+    bool again = scal[4] != 0.0;
+    fin = pass == 0 ? (again ? 0 : 1) : (again ? 1 : -1);
+    double b = scal[2];
+    rb = b != 0.0 ? 1.0 / b : 0.0;
+  }
+  if (threadIdx.x < nv) cs[threadIdx.x] = -c[threadIdx.x];
+  __syncthreads();
+  if (fin < 0) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int k = 0; k < nv; ++k) acc = fma(cs[k], V[k * ldv + i], acc);
+    if (fin) out[i] = acc * rb;
+    else w[i] = acc;
+  }
 }
 
 // w -= sum_k c_k V_k (sign -1) or w += sum_k c_k V_k (sign +1)
@@ -828,44 +1122,62 @@ __global__ void k_init_g(double *g, int m, const double *beta) {
   if (i <= m) g[i] = i == 0 ? *beta : 0.0;
 }
 
-static int dots(Sim *s, const double *V, long long ldv, int nv, const double *w, int mode, int j) {
+// V^T w (and, for modes 3 and 4, w.w) reduced by k_dot_final in `mode`;
+// `gate` as for k_multidot.
+static int dots(Sim *s, const double *V, long long ldv, int nv, const double *w, int mode, int j,
+                const double *gate = nullptr) {
   long long N = 2LL * s->A.n;
   for (int v0 = 0; v0 < nv; v0 += kDotVec) {
     int cnt = std::min(kDotVec, nv - v0);
-    DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, V + (long long)v0 * ldv, ldv, cnt, w,
-              s->dots_part, v0);
+    const double *Vb = V + (long long)v0 * ldv;
+#define DP_MD(NVC)                                                                             \
+  case NVC:                                                                                    \
+    if (mode >= 3 && v0 == 0)                                                                  \
+      DP_LAUNCH(s, (k_multidot<NVC, true>), kDotBlocks, kBlock, 0, N, Vb, ldv, w, s->dots_part, \
+                v0, gate);                                                                     \
+    else                                                                                       \
+      DP_LAUNCH(s, (k_multidot<NVC, false>), kDotBlocks, kBlock, 0, N, Vb, ldv, w,             \
+                s->dots_part, v0, gate);                                                       \
+    break;
+    switch (cnt) {
+      DP_MD(1) DP_MD(2) DP_MD(3) DP_MD(4) DP_MD(5) DP_MD(6) DP_MD(7) DP_MD(8)
+    }
+#undef DP_MD
   }
-  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, nv, s->dots, s->H, s->m, j, mode);
+  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, nv, s->dots, s->H, s->m, j, mode,
+            s->scal);
   return DP_OK;
 }
 
 // ||x|| into s->scal[slot] (device) via the dot machinery
 static int norm_into(Sim *s, const double *x, double *dst) {
   long long N = 2LL * s->A.n;
-  DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, x, 0LL, 1, x, s->dots_part, 0);
-  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, dst, s->H, s->m, 0, 0);
+  DP_LAUNCH(s, (k_multidot<1, false>), kDotBlocks, kBlock, 0, N, x, 0LL, x, s->dots_part, 0,
+            (const double *)nullptr);
+  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, dst, s->H, s->m, 0, 0, s->scal);
   return DP_OK;
 }
 
 __global__ void k_sqrt_inplace(double *v) { v[0] = sqrt(v[0]); }
 
-// One Arnoldi step of FGMRES for column j: z_j = M v_j, w = A z_j, two
-// passes of classical Gram-Schmidt, h_{j+1,j} = ||w||, v_{j+1} = w / h, the
-// Givens rotations, and |g_{j+1}| into scal[3].
+// One Arnoldi step of FGMRES for column j: z_j = M v_j, w = A z_j, then
+// classical Gram-Schmidt against v_0..v_j with the DGKS test: the second
+// pass runs only when the first cancelled more than half of ||w||^2, and
+// h_{j+1,j} = ||w - V h|| comes from w.w - h.h, so each pass reads the basis
+// twice (dots, projection) and the projection writes v_{j+1} normalised.
+// Then the Givens rotations, and |g_{j+1}| into scal[3].
 static int arnoldi_step(Sim *s, int j) {
   int m = s->m;
   long long N = 2LL * s->A.n;
   int gridN = (int)std::min<long long>(nblk(N), kDotBlocks * 4);
   double *vj = s->V + (long long)j * N, *zj = s->Z + (long long)j * N;
+  double *vnext = s->V + (long long)(j + 1) * N;
   DP_TRY(cpr_apply(s, vj, zj));
   DP_TRY(bsr_spmv(s, zj, s->w));
-  for (int pass = 0; pass < 2; ++pass) {          // classical Gram-Schmidt, twice
-    DP_TRY(dots(s, s->V, N, j + 1, s->w, 1, j));
-    DP_LAUNCH(s, k_multi_axpy, gridN, kBlock, 0, N, s->V, N, j + 1, s->dots, -1.0, s->w);
-  }
-  DP_LAUNCH(s, k_multidot, kDotBlocks, kBlock, 0, N, s->w, 0LL, 1, s->w, s->dots_part, 0);
-  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, s->scal + 2, s->H, m, j, 2);
-  DP_LAUNCH(s, k_scale, nblk(N), kBlock, 0, N, s->w, s->scal + 2, 1, s->V + (long long)(j + 1) * N);
+  DP_TRY(dots(s, s->V, N, j + 1, s->w, 3, j));
+  DP_LAUNCH(s, k_project, gridN, kBlock, 0, N, s->V, N, j + 1, s->dots, s->w, vnext, s->scal, 0);
+  DP_TRY(dots(s, s->V, N, j + 1, s->w, 4, j, s->scal + 4));
+  DP_LAUNCH(s, k_project, gridN, kBlock, 0, N, s->V, N, j + 1, s->dots, s->w, vnext, s->scal, 1);
   DP_LAUNCH(s, k_givens, 1, 32, 0, s->H, s->cs, s->sn, s->g, m, j, s->scal + 3);
   return DP_OK;
 }

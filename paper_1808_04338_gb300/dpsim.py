@@ -59,7 +59,8 @@ class dp_options(C.Structure):
                 ("gmres_restart", C.c_int32), ("gmres_maxit", C.c_int32),
                 ("amg_theta", C.c_double), ("amg_coarse_max", C.c_int32),
                 ("amg_max_levels", C.c_int32), ("precond", C.c_int32),
-                ("ds_max", C.c_double), ("precision", C.c_int32), ("use_graphs", C.c_int32)]
+                ("ds_max", C.c_double), ("precision", C.c_int32), ("use_graphs", C.c_int32),
+                ("amg_gs_levels", C.c_int32), ("cluster_rows", C.c_int32)]
 
 
 class dp_stats(C.Structure):
@@ -72,7 +73,9 @@ class dp_stats(C.Structure):
 def options(mode: str = "parity", **kw) -> dp_options:
     """'parity': fixed eta 1e-10, Newton tolerance 1e-10 (agreement with an
     independent FP64 evaluation far inside 1e-8); 'report': third forcing
-    term (gamma 0.9, beta 2) in [1e-4, 0.1], Newton tolerance 1e-6."""
+    term (gamma 0.9, beta 2) in [1e-4, 0.1], Newton tolerance 1e-6, and
+    l1-Jacobi instead of multicolour Gauss-Seidel on the AMG levels below
+    the finest."""
     o = dp_options()
     o.newton_max = 25
     o.newton_atol = 1e-13
@@ -85,11 +88,13 @@ def options(mode: str = "parity", **kw) -> dp_options:
     o.ds_max = 0.2
     o.precision = 0
     o.use_graphs = 1
+    o.amg_gs_levels = 30
     o.eta_gamma, o.eta_beta, o.eta_min, o.eta_max = 0.9, 2.0, 1e-4, 0.1
     if mode == "parity":
         o.eta_mode, o.eta_fixed, o.newton_tol = 0, 1e-10, 1e-10
     else:
         o.eta_mode, o.eta_fixed, o.newton_tol = 3, 1e-4, 1e-6
+        o.amg_gs_levels = 1
     for k, v in kw.items():
         setattr(o, k, v)
     return o

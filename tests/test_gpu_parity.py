@@ -119,14 +119,15 @@ def dense_from_bsr(rowptr, col, val):
     return A
 
 
-@pytest.mark.parametrize("precond", [1, 2])
-def test_newton_update_parity(precond):
+@pytest.mark.parametrize("precond,gs_levels", [(1, 30), (2, 30), (2, 0)])
+def test_newton_update_parity(precond, gs_levels):
     """One linear solve at eta = 1e-12 on both sides: the GPU update's true
     residual (dense J from the oracle) is at the tolerance, it agrees with
     the oracle's update as closely as the conditioning of J (~1e12) allows,
     and both take (nearly) the same number of FGMRES iterations."""
     prob = di.tiny()
-    g, o = pair(prob, precond=precond, eta_fixed=1e-12, gmres_maxit=1000)
+    g, o = pair(prob, precond=precond, eta_fixed=1e-12, gmres_maxit=1000,
+                amg_gs_levels=gs_levels)
     st = interior(prob, 3)
     for s in (g, o):
         s.set_iterate(*st)
@@ -142,6 +143,31 @@ def test_newton_update_parity(precond):
     assert np.abs(yg[0:2 * nc:2] - yo[0:2 * nc:2]).max() <= 1e-6 * np.abs(yo[0:2 * nc:2]).max()
     assert np.abs(yg[1:2 * nc:2] - yo[1:2 * nc:2]).max() <= 1e-6
     assert abs(stg.linear_iters - sto.linear_iters) <= 2
+
+
+@pytest.mark.parametrize("gs_levels,graphs,cluster_rows",
+                         [(30, 1, 0), (30, 0, 0), (1, 1, 0), (1, 0, 0), (0, 1, 0),
+                          (1, 1, 20000), (0, 1, 20000), (30, 1, -1)])
+def test_preconditioner_residual_after_five_iterations(gs_levels, graphs, cluster_rows):
+    """The CPR-FPF preconditioner itself, on the 200k-cell layered problem
+    (five AMG levels; with graphs and a cluster threshold the coarse ones run
+    in the cluster kernel): five FGMRES iterations from zero on both sides
+    leave the same relative residual, whichever smoother each level uses
+    (Gauss-Seidel on all levels, l1-Jacobi below the finest, l1-Jacobi
+    everywhere) and wherever the coarse levels run."""
+    prob = di.layered()
+    g, o = pair(prob, "parity", eta_fixed=1e-14, gmres_maxit=5, amg_gs_levels=gs_levels)
+    g.close()
+    g = gpu().Sim(prob, gpu().options("parity", eta_fixed=1e-14, gmres_maxit=5,
+                                      amg_gs_levels=gs_levels, use_graphs=graphs,
+                                      cluster_rows=cluster_rows))
+    for s in (g, o):
+        s.assemble(prob.dt)
+    rcg, stg = g.solve_step()
+    rco, sto = o.solve_step()
+    assert stg.linear_iters == sto.linear_iters == 5
+    assert 0 < sto.lin_relres < 0.5
+    assert abs(stg.lin_relres - sto.lin_relres) <= 1e-6 * sto.lin_relres
 
 
 def test_unpreconditioned_gmres_single_location():

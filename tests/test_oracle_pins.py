@@ -369,6 +369,50 @@ def test_amg_two_level_cycle_matches_independent_two_grid():
     np.testing.assert_allclose(m.vcycle(b), x, rtol=1e-10, atol=1e-12 * np.abs(x).max())
 
 
+def test_amg_two_level_l1_jacobi_matches_independent_two_grid():
+    """The same two-grid cycle with l1-Jacobi smoothing (Baker, Falgout,
+    Kolev and Yang 2011): one sweep from zero before the coarse correction,
+    one after, each x += (b - A x) / sum_j |a_ij| over all rows at once."""
+    A = poisson3d(12).tocsr()
+    n = A.shape[0]
+    m = O.OracleAMG(A.indptr, A.indices, A.data, coarse_max=400, gs_levels=0)
+    levels = m.levels()
+    assert len(levels) == 2
+    agg, na = levels[0]["agg"], levels[0]["nagg"]
+    T = sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, na))
+    D = A.diagonal()
+    P = (T - (2.0 / 3.0) * sp.diags(1.0 / D) @ A @ T).tocsr()
+    Ac = (P.T @ A @ P).toarray()
+    l1 = np.asarray(abs(A).sum(axis=1)).ravel()
+    b = np.random.default_rng(5).normal(size=n)
+    x = b / l1
+    x = x + P @ np.linalg.solve(Ac, P.T @ (b - A @ x))
+    x = x + (b - A @ x) / l1
+    np.testing.assert_allclose(m.vcycle(b), x, rtol=1e-10, atol=1e-12 * np.abs(x).max())
+
+
+def test_amg_l1_jacobi_cycle_is_symmetric_and_contracts():
+    """With l1-Jacobi below the finest level the V-cycle is still a symmetric
+    operator (the same sweep before and after each coarse correction) and
+    still contracts the energy norm of the error on 3D Poisson."""
+    A = poisson3d(14)
+    m = O.OracleAMG(A.indptr, A.indices, A.data, coarse_max=64, gs_levels=1)
+    assert len(m.levels()) >= 3
+    rng = np.random.default_rng(2)
+    u, v = rng.normal(size=A.shape[0]), rng.normal(size=A.shape[0])
+    a, b = u @ m.vcycle(v), v @ m.vcycle(u)
+    assert abs(a - b) < 1e-12 * abs(a)
+    m0 = O.OracleAMG(A.indptr, A.indices, A.data, coarse_max=64, gs_levels=0)
+    a, b = u @ m0.vcycle(v), v @ m0.vcycle(u)
+    assert abs(a - b) < 1e-12 * abs(a)
+    e = rng.normal(size=A.shape[0])
+    for _ in range(15):
+        e2 = e - m0.vcycle(A @ e)
+        q = math.sqrt((e2 @ (A @ e2)) / (e @ (A @ e)))
+        e = e2
+    assert q < 0.8
+
+
 def test_amg_aggregates_partition_and_mis2_distance():
     """Aggregates partition the strongly connected nodes, every aggregate is
     connected in the strength graph, and the MIS(2) roots (one per aggregate)
