@@ -40,6 +40,20 @@ def workload(args):
     return di.field8m(args.nx, args.ny, args.nz)
 
 
+def over_ranks(dist, device, elapsed, units):
+    """Whole-job numbers over the ranks of a replica run: the slowest rank's
+    elapsed time (max) and the units that all ranks processed (sum).  No-op
+    on one process (dist None)."""
+    if dist is None:
+        return float(elapsed), float(units)
+    import torch
+    mx = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx.item()), float(sm.item())
+
+
 def spmv_bytes(nb, nnzb):
     """Algorithmic bytes of one y = A x launch (FP64 2x2 BSR): values,
     column indices, row pointers, x and y read/written once."""
@@ -394,20 +408,19 @@ def main():
         torch.cuda.synchronize()
         if clocks:
             clocks.__exit__()
-        ms = e0.elapsed_time(e1)
+        ms, all_solves = over_ranks(dist, dev, e0.elapsed_time(e1), n_solves)
         if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         solve_ms.sort()
-        return {"ms": ms, "solves": n_solves, "its": n_its, "launches": sim.launch_count() - l0,
+        return {"ms": ms, "solves": n_solves, "all_solves": all_solves, "its": n_its,
+                "launches": sim.launch_count() - l0,
                 "median": solve_ms[len(solve_ms) // 2] if solve_ms else None,
                 "p90": solve_ms[min(len(solve_ms) - 1, int(0.9 * len(solve_ms)))] if solve_ms else None}
 
     clk = Clocks(local)
     main = measure(sim, opts, args.steps, args.warmup, clk)
     ms, n_solves, n_its, launches = main["ms"], main["solves"], main["its"], main["launches"]
+    all_solves = main["all_solves"]
     med, p90 = main["median"], main["p90"]
 
     # the dominant kernel timed with CUDA events on the simulation stream over
@@ -438,11 +451,7 @@ def main():
         e2e_solves += st.newton_iters
         sim.get_state_ptr(op.data_ptr(), osw.data_ptr(), ob.data_ptr())
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s, e2e_all = over_ranks(dist, dev, time.perf_counter() - t0, e2e_solves)
     nbytes_state = 8 * (2 * prob.n_cells + prob.n_wells)  # per timestep of e2e
 
     fp64 = None
@@ -452,13 +461,13 @@ def main():
             sim64 = dpsim.Sim(prob, o64, stream=stream)
         r = measure(sim64, o64, max(2, args.steps // 2), args.warmup)
         sim64.close()
-        fp64 = {"value": world * r["solves"] / (r["ms"] / 1000.0), "unit": UNIT,
+        fp64 = {"value": r["all_solves"] / (r["ms"] / 1000.0), "unit": UNIT,
                 "solve_ms_median": r["median"], "solve_ms_p90": r["p90"],
                 "fgmres_iters_per_solve": r["its"] / max(r["solves"], 1),
                 "note": "the same timestep with FP64 ILU(0) and AMG"}
 
     if rank == 0:
-        value = world * n_solves / (ms / 1000.0)
+        value = all_solves / (ms / 1000.0)
         peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
         peak = peaks.get("hbm_gbs", 6800.0)
         ach = spmv_bytes(sim.nb, sim.nnzb) / (k_ms / max(k_n, 1) / 1000.0) / 1e9 if k_n else None
@@ -485,7 +494,7 @@ def main():
                          "avg_launch_ms": (k_ms / k_n) if k_n else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
             "cpu_baseline": cpu,
-            "e2e": {"value": world * e2e_solves / e2e_s if e2e_steps else None, "unit": UNIT,
+            "e2e": {"value": e2e_all / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state},
             "fp64_path": fp64,
             "gpu_launches": launches,
