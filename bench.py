@@ -290,13 +290,15 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(args):
+def config_dict(args, nnzb=None):
     return {"workload": f"dual-porosity oil-water, {args.nx}x{args.ny}x{args.nz} grid, "
                         f"{2 * args.nx * args.ny * args.nz} cells, "
                         f"{4 * args.nx * args.ny * args.nz + 50} unknowns, 25 wells, "
                         f"lognormal perm (sd 2), first 5-day Newton step",
             "grid": [args.nx, args.ny, args.nz], "precision": args.precision,
-            "precond": "CPR-FPF", "l2": "inputs larger than L2 (Jacobian 636 MB)",
+            "precond": "CPR-FPF",
+            "l2": f"inputs larger than L2 (Jacobian {32 * nnzb / 1e6:.0f} MB)" if nnzb else
+                  "inputs larger than L2",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -483,7 +485,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == 0 else "f64 (f32 preconditioner)",
-            "data": "synthetic", "config": config_dict(args),
+            "data": "synthetic", "config": config_dict(args, sim.nnzb),
             "newton_solves_per_step": n_solves / args.steps,
             "fgmres_iters_per_solve": n_its / max(n_solves, 1),
             "solve_ms_median": med, "solve_ms_p90": p90,
