@@ -60,6 +60,23 @@ def spmv_bytes(nb, nnzb):
     return 32 * nnzb + 4 * nnzb + 4 * (nb + 1) + 16 * nb + 16 * nb
 
 
+def sweep_bytes(nb, nnzb):
+    """Algorithmic bytes of one full sweep (all colours) of the FP32 ILU(0)
+    forward and backward solves and of one level-0 Gauss-Seidel sweep.  The
+    pattern is structurally symmetric, so L and U hold (nnzb - nb)/2 blocks
+    each.  Forward: per L block 16 B of values + 4 B column; per row the row
+    pointer, pivot position and permutation (12 B), the FP64 right-hand side
+    (16 B), the FP32 result written (8 B) and its neighbours' values read
+    once (8 B).  Backward: per U block 20 B; per row 12 B of indices, the
+    inverted pivot block (16 B), z read, gathered and written (24 B).
+    Gauss-Seidel (FP32 pressure values): per entry 4 B value + 4 B column;
+    per row the row pointer and permutation (8 B), 1/a_ii, b, x read and
+    written, x gathered (20 B)."""
+    half = (nnzb - nb) // 2
+    return {"k_ilu_fwd": 20 * half + 44 * nb, "k_ilu_bwd": 20 * half + 52 * nb,
+            "k_gs_lu": 8 * nnzb + 28 * nb}
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -433,6 +450,21 @@ def main():
         timestep(sim, opts)
     k_ms, k_n = sim.kernel_timing(reset=True)
     sim.time_kernel(None)
+    # the ILU(0) and Gauss-Seidel sweeps the same way, one kernel per timestep;
+    # one sweep = one launch per colour
+    ncol = sim.colours()[1]
+    sweeps = {}
+    for name, nbytes in sweep_bytes(sim.nb, sim.nnzb).items():
+        sim.time_kernel(name)
+        sim.kernel_timing(reset=True)
+        timestep(sim, opts)
+        t_ms, t_n = sim.kernel_timing(reset=True)
+        sim.time_kernel(None)
+        if t_n:
+            n_sweeps = t_n / ncol
+            sweeps[name] = {"achieved_gbs": nbytes * n_sweeps / (t_ms / 1000.0) / 1e9,
+                            "bytes_per_sweep": nbytes, "ms_per_sweep": t_ms / n_sweeps,
+                            "launches": t_n}
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     hp = torch.from_numpy(prob.p0).pin_memory()
@@ -495,6 +527,7 @@ def main():
                          "launches_timed": k_n,
                          "avg_launch_ms": (k_ms / k_n) if k_n else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+            "sweeps": {k: dict(v, frac=v["achieved_gbs"] / peak) for k, v in sweeps.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_all / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state},

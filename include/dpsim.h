@@ -219,8 +219,9 @@ int sim_footprint(dp_sim *s, uint64_t *current, uint64_t *peak);
  * resident (state, operator, ILU(0) factors, AMG hierarchy) on its own
  * stream.  Admission is by device footprint: a request whose realisation is
  * not resident is admitted when its estimated footprint (the largest bytes
- * per block row measured so far, times its block rows; 4096 B per row before
- * any measurement) fits in hbm_budget after evicting idle resident
+ * per block row measured so far, times its block rows; a guess of 4096 B per
+ * row before any measurement, under which an over-budget realisation waits
+ * until nothing else runs and is then served alone) fits in hbm_budget after evicting idle resident
  * realisations, least recently used first; an evicted realisation's state
  * goes back to its host copy, and the realisation is rebuilt (operator
  * pattern and AMG set-up) when next served.  Requests are taken in arrival
@@ -232,7 +233,7 @@ typedef struct dp_server dp_server;
 
 typedef struct dp_srv_result {
   int32_t status;       /* sim_advance's return code; DP_ENOMEM if the realisation
-                           can never fit in the budget */
+                           cannot fit in the budget by the measured estimate */
   int32_t realisation;  /* id from srv_add */
   int32_t loaded;       /* 1 if the realisation was (re)built for this request */
   int32_t evicted;      /* realisations evicted to admit it */

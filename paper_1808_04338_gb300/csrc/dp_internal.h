@@ -223,7 +223,12 @@ struct Sim {
   double *lu_val = nullptr;
   float *lu_valf = nullptr;
   int *upd_ptr = nullptr, *upd_e2 = nullptr, *upd_q = nullptr;   // IKJ update lists
+  // split layout of the factor: L blocks, inverted pivots, U blocks
+  int lu_nL = 0;
+  int *lu_Lptr = nullptr, *lu_Uptr = nullptr, *lu_dst = nullptr, *lu_colp = nullptr;
+  double *ilu_zp = nullptr;       // colour-order work vector (2 nb values of the sweep type)
   std::vector<int> lu_cstart;
+  std::vector<int> lu_cmaxlen;   // longest row (blocks) of each colour
   // AMG hierarchy (level 0 shares the block pattern)
   std::vector<Level> lev;
   bool amg_ready = false;
@@ -254,7 +259,6 @@ struct Sim {
   double *h_res = nullptr;                           // pinned host scalars
   int dot_blocks = 0;
   double *z1 = nullptr, *r1 = nullptr, *rp = nullptr, *xp = nullptr;
-  float *zf = nullptr;                               // FP32 ILU vector (precision 1)
   // CUDA graphs of the FGMRES iterations j = 0..m-1 (captured on first use)
   std::vector<cudaGraphExec_t> graph;
   std::vector<long long> graph_launches;

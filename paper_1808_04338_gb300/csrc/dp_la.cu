@@ -20,6 +20,39 @@ namespace dp {
 // matrix rows, then wells): pair q processes storage row q, whose blocks are
 // contiguous with those of pair q+1, and writes natural row row_of_pair(q).
 
+// The well rows (the last n - nc storage rows, one block per perforation,
+// tens of blocks each) go to block 0, a warp per row, so that their long
+// rows start first instead of trailing the launch.
+template <int MODE>
+__device__ __forceinline__ void spmv_well_rows(int n, int nc, const int *__restrict__ rowptr,
+                                               const int *__restrict__ col,
+                                               const double *__restrict__ val,
+                                               const double *__restrict__ x,
+                                               const double *__restrict__ b,
+                                               double *__restrict__ y) {
+  int lane = threadIdx.x & 31;
+  const double2 *v2 = reinterpret_cast<const double2 *>(val);
+  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  for (int row = nc + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
+      double2 a = __ldg(v2 + 2 * (size_t)e), c = __ldg(v2 + 2 * (size_t)e + 1);
+      double2 xj = __ldg(x2 + __ldg(col + e));
+      s0 = fma(a.x, xj.x, fma(a.y, xj.y, s0));
+      s1 = fma(c.x, xj.x, fma(c.y, xj.y, s1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+      y[2 * (size_t)row] = MODE == 0 ? s0 : b[2 * (size_t)row] - s0;
+      y[2 * (size_t)row + 1] = MODE == 0 ? s1 : b[2 * (size_t)row + 1] - s1;
+    }
+  }
+}
+
 template <int MODE>  // MODE 0: y = A x; 1: y = b - A x
 __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
                                                      const int *__restrict__ rowptr,
@@ -28,9 +61,13 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
                                                      const double *__restrict__ x,
                                                      const double *__restrict__ b,
                                                      double *__restrict__ y) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0) {
+    spmv_well_rows<MODE>(n, nc, rowptr, col, val, x, b, y);
+    return;
+  }
+  int t = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
   int comp = t & 1, q = t >> 1;
-  if (q >= n) return;
+  if (q >= nc) return;
   int row = row_of_pair(q, nL, nc);
   int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
   const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
@@ -57,8 +94,23 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
                                                        const double *__restrict__ x,
                                                        const double *__restrict__ b,
                                                        double *__restrict__ rp) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
+  if (blockIdx.x == 0) {   // the well rows, a warp per row (as in k_bsr_spmv)
+    int lane = threadIdx.x & 31;
+    const double2 *x2 = reinterpret_cast<const double2 *>(x);
+    for (int row = nc + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+      double s = 0.0;
+      for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
+        double2 xj = __ldg(x2 + __ldg(col + e));
+        s = fma(__ldg(a00 + e), xj.x, fma(__ldg(a01 + e), xj.y, s));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) rp[row] = b[2 * (size_t)row] - s;
+    }
+    return;
+  }
+  int t = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
   int row = row_of_pair(t, nL, nc);
   int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
@@ -73,13 +125,13 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
 }
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
-  DP_LAUNCH(s, k_bsr_spmv<0>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
+  DP_LAUNCH(s, k_bsr_spmv<0>, 1 + nblk(2LL * s->ph.nc), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
             s->srowptr, s->scol, s->sval, x, nullptr, y);
   return DP_OK;
 }
 
 int bsr_residual(Sim *s, const double *b, const double *x, double *r) {
-  DP_LAUNCH(s, k_bsr_spmv<1>, nblk(2LL * s->A.n), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
+  DP_LAUNCH(s, k_bsr_spmv<1>, 1 + nblk(2LL * s->ph.nc), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
             s->srowptr, s->scol, s->sval, x, b, r);
   return DP_OK;
 }
@@ -166,11 +218,23 @@ __global__ void k_ilu_upd(int n, int fill, const int *iperm, const int *lu_rowpt
   }
 }
 
+// Storage of the factor ("split layout"): the L blocks of all rows first
+// (row r's at Lptr[r]..Lptr[r+1]), then the inverted pivot block of every
+// row (at nL + r), then the U blocks (at nL + n + Uptr[r]..); every block's
+// column as its permuted position (colp), so that the sweeps work on a
+// vector kept in colour order: a colour's rows, their pivots and their
+// results are contiguous, and with the greedy colouring of this pattern each
+// location has one row per colour, so the neighbours a row gathers sit
+// compactly in the earlier colours' segments.
+
 // IKJ block ILU(0) of the rows [r0, r1) of one colour, in precision T: all
-// their L blocks refer to rows of earlier colours, which are final.
+// their L blocks refer to rows of earlier colours, which are final.  The
+// loops run over the row's entries e in factor order (lu_rowptr, lu_dpos);
+// dst[e] is the entry's block in the split layout and the update lists hold
+// split-layout positions.
 template <typename T>
-__global__ void k_ilu_factor(int r0, int r1, const int *iperm, const int *lu_rowptr,
-                             const int *lu_col, const int *lu_src, const int *lu_dpos,
+__global__ void k_ilu_factor(int r0, int r1, int nL, const int *lu_rowptr, const int *lu_dpos,
+                             const int *dst, const int *colp, const int *lu_src,
                              const int *upd_ptr, const int *upd_e2, const int *upd_q,
                              const double *aval, T *lu) {
   int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,14 +242,15 @@ __global__ void k_ilu_factor(int r0, int r1, const int *iperm, const int *lu_row
   int s0 = lu_rowptr[r], s1 = lu_rowptr[r + 1], dp = lu_dpos[r];
   for (int e = s0; e < s1; ++e) {
     const double *src = aval + 4 * (size_t)lu_src[e];
-    T *dst = lu + 4 * (size_t)e;
-    dst[0] = T(src[0]); dst[1] = T(src[1]); dst[2] = T(src[2]); dst[3] = T(src[3]);
+    T *d = lu + 4 * (size_t)dst[e];
+    d[0] = T(src[0]); d[1] = T(src[1]); d[2] = T(src[2]); d[3] = T(src[3]);
   }
   for (int e = s0; e < dp; ++e) {
-    int rk = iperm[lu_col[e]];
+    int k = dst[e];
+    int rk = colp[k];
     T lik[4];
-    mul2<T>(lu + 4 * (size_t)e, lu + 4 * (size_t)lu_dpos[rk], lik);   // A_ik U_kk^-1
-    T *le = lu + 4 * (size_t)e;
+    mul2<T>(lu + 4 * (size_t)k, lu + 4 * ((size_t)nL + rk), lik);   // A_ik U_kk^-1
+    T *le = lu + 4 * (size_t)k;
     le[0] = lik[0]; le[1] = lik[1]; le[2] = lik[2]; le[3] = lik[3];
     for (int p = upd_ptr[e]; p < upd_ptr[e + 1]; ++p) {
       T u[4];
@@ -194,70 +259,194 @@ __global__ void k_ilu_factor(int r0, int r1, const int *iperm, const int *lu_row
       aij[0] -= u[0]; aij[1] -= u[1]; aij[2] -= u[2]; aij[3] -= u[3];
     }
   }
-  inv2<T>(lu + 4 * (size_t)dp);
+  inv2<T>(lu + 4 * ((size_t)nL + r));
 }
 
 // Forward sweep of one colour, two lanes per row (one per component):
-// z_i = r_i - sum_{L} L_ik z_k (unit lower triangle).  Factor and z in T, the
-// right-hand side in TR.
+// zp_r = r_{perm[r]} - sum_{L} L_rk zp_k (unit lower triangle), zp in colour
+// order; the right-hand side (natural order) in TR.
 template <typename T, typename TR>
 __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *__restrict__ perm,
-                                                    const int *__restrict__ lu_rowptr,
-                                                    const int *__restrict__ lu_col,
-                                                    const int *__restrict__ lu_dpos,
+                                                    const int *__restrict__ Lptr,
+                                                    const int *__restrict__ colp,
                                                     const T *__restrict__ lu,
-                                                    const TR *__restrict__ rhs, T *z) {
+                                                    const TR *__restrict__ rhs, T *zp) {
   using T2 = typename V2<T>::t;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = r0 + (t >> 1), comp = t & 1;
   if (r >= r1) return;
   int i = __ldg(perm + r);
   const T2 *v2 = reinterpret_cast<const T2 *>(lu) + comp;
-  const T2 *z2 = reinterpret_cast<const T2 *>(z);
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
   T s = T(0);
-  int ea = __ldg(lu_rowptr + r), eb = __ldg(lu_dpos + r);
+  int ea = __ldg(Lptr + r), eb = __ldg(Lptr + r + 1);
 #pragma unroll 4
   for (int e = ea; e < eb; ++e) {
     T2 a = __ldg(v2 + 2 * (size_t)e);
-    T2 xk = z2[__ldg(lu_col + e)];
+    T2 xk = z2[__ldg(colp + e)];
     s = fma(a.x, xk.x, s);
     s = fma(a.y, xk.y, s);
   }
-  z[2 * (size_t)i + comp] = T(rhs[2 * (size_t)i + comp]) - s;
+  zp[2 * (size_t)r + comp] = T(rhs[2 * (size_t)i + comp]) - s;
 }
 
-// Backward sweep of one colour: z_i = U_ii^-1 (z_i - sum_{U} U_ij z_j).  The
-// two lanes of a row exchange their partial results for the 2x2 product.
+// Backward sweep of one colour: zp_r = D_r (zp_r - sum_{U} U_rj zp_j) with
+// D_r the inverted pivot.  The two lanes of a row exchange their partial
+// results for the 2x2 product.
+// The factor, its indices and the permutation are streamed evict-first
+// (ld.global.cs).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_ilu_bwd(int r0, int r1, const int *__restrict__ perm,
-                                                    const int *__restrict__ lu_rowptr,
-                                                    const int *__restrict__ lu_col,
-                                                    const int *__restrict__ lu_dpos,
-                                                    const T *__restrict__ lu, T *z) {
+__global__ void __launch_bounds__(kBlock) k_ilu_bwd(int r0, int r1, int nL, int n,
+                                                    const int *__restrict__ Uptr,
+                                                    const int *__restrict__ colp,
+                                                    const T *__restrict__ lu, T *zp) {
   using T2 = typename V2<T>::t;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = r0 + (t >> 1), comp = t & 1;
   bool valid = r < r1;                  // no early exit: the pair shuffles
-  int i = valid ? __ldg(perm + r) : 0;
   const T2 *v2 = reinterpret_cast<const T2 *>(lu);
-  const T2 *z2 = reinterpret_cast<const T2 *>(z);
-  int dp = valid ? __ldg(lu_dpos + r) : 0, eb = valid ? __ldg(lu_rowptr + r + 1) : 0;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  size_t ub = (size_t)nL + n;
+  int ea = valid ? __ldcs(Uptr + r) : 0, eb = valid ? __ldcs(Uptr + r + 1) : 0;
   T s = T(0);
 #pragma unroll 4
-  for (int e = dp + 1; e < eb; ++e) {
-    T2 a = __ldg(v2 + 2 * (size_t)e + comp);
-    T2 xj = z2[__ldg(lu_col + e)];
+  for (int e = ea; e < eb; ++e) {
+    T2 a = __ldcs(v2 + 2 * (ub + e) + comp);
+    T2 xj = z2[__ldcs(colp + ub + e)];
     s = fma(a.x, xj.x, s);
     s = fma(a.y, xj.y, s);
   }
-  T yi = valid ? z[2 * (size_t)i + comp] - s : T(0);
+  T yi = valid ? zp[2 * (size_t)r + comp] - s : T(0);
   T yo = __shfl_xor_sync(0xffffffffu, yi, 1);
   if (valid) {
     T y0 = comp == 0 ? yi : yo, y1 = comp == 0 ? yo : yi;
-    T2 d = __ldg(v2 + 2 * (size_t)dp + comp);
-    z[2 * (size_t)i + comp] = fma(d.x, y0, d.y * y1);
+    T2 d = __ldcs(v2 + 2 * ((size_t)nL + r) + comp);
+    zp[2 * (size_t)r + comp] = fma(d.x, y0, d.y * y1);
   }
 }
+
+// Warp-per-row variants of the sweeps for colours with long rows (the well
+// rows, one entry per perforation): the lanes split the row's blocks and
+// the partial sums meet in shuffles, instead of one thread walking a row of
+// tens of blocks.
+template <typename T> struct V4;
+template <> struct V4<double> {
+  static __device__ __forceinline__ void load(const double *p, double *o) {
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p)),
+            b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+};
+template <> struct V4<float> {
+  static __device__ __forceinline__ void load(const float *p, float *o) {
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, typename TR>
+__global__ void __launch_bounds__(kBlock) k_ilu_fwd_w(int r0, int r1, const int *__restrict__ perm,
+                                                      const int *__restrict__ Lptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ lu,
+                                                      const TR *__restrict__ rhs, T *zp) {
+  int r = r0 + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (r >= r1) return;   // whole warps
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  T s0 = T(0), s1 = T(0);
+  for (int e = __ldg(Lptr + r) + lane, eb = __ldg(Lptr + r + 1); e < eb; e += 32) {
+    T a[4];
+    V4<T>::load(lu + 4 * (size_t)e, a);
+    T2 xk = z2[__ldg(colp + e)];
+    s0 = fma(a[0], xk.x, fma(a[1], xk.y, s0));
+    s1 = fma(a[2], xk.x, fma(a[3], xk.y, s1));
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  if (lane == 0) {
+    int i = __ldg(perm + r);
+    zp[2 * (size_t)r] = T(rhs[2 * (size_t)i]) - s0;
+    zp[2 * (size_t)r + 1] = T(rhs[2 * (size_t)i + 1]) - s1;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_ilu_bwd_w(int r0, int r1, int nL, int n,
+                                                      const int *__restrict__ Uptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ lu, T *zp) {
+  int r = r0 + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (r >= r1) return;
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  size_t ub = (size_t)nL + n;
+  T s0 = T(0), s1 = T(0);
+  for (int e = __ldg(Uptr + r) + lane, eb = __ldg(Uptr + r + 1); e < eb; e += 32) {
+    T a[4];
+    V4<T>::load(lu + 4 * (ub + e), a);
+    T2 xj = z2[__ldg(colp + ub + e)];
+    s0 = fma(a[0], xj.x, fma(a[1], xj.y, s0));
+    s1 = fma(a[2], xj.x, fma(a[3], xj.y, s1));
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  if (lane == 0) {
+    T y0 = zp[2 * (size_t)r] - s0, y1 = zp[2 * (size_t)r + 1] - s1;
+    T d[4];
+    V4<T>::load(lu + 4 * ((size_t)nL + r), d);
+    zp[2 * (size_t)r] = fma(d[0], y0, d[1] * y1);
+    zp[2 * (size_t)r + 1] = fma(d[2], y0, d[3] * y1);
+  }
+}
+
+// Split-layout position of each factor entry, and the permuted column of
+// each split-layout block.
+__global__ void k_ilu_split(int n, int nL, const int *iperm, const int *lu_rowptr,
+                            const int *lu_col, const int *lu_dpos, const int *Lptr,
+                            const int *Uptr, int *dst, int *colp) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int s0 = lu_rowptr[r], dp = lu_dpos[r], s1 = lu_rowptr[r + 1];
+  for (int e = s0; e < s1; ++e) {
+    int d = e < dp ? Lptr[r] + (e - s0) : (e == dp ? nL + r : nL + n + Uptr[r] + (e - dp - 1));
+    dst[e] = d;
+    colp[d] = iperm[lu_col[e]];
+  }
+}
+
+__global__ void k_remap(long long n, const int *map, int *v) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = map[v[i]];
+}
+
+__global__ void k_lu_lens(int n, const int *lu_rowptr, const int *lu_dpos, int *nl, int *nu) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  nl[r] = lu_dpos[r] - lu_rowptr[r];
+  nu[r] = lu_rowptr[r + 1] - lu_dpos[r] - 1;
+}
+
+// longest row of each colour (blocks), for choosing the sweep variant
+__global__ void k_colour_maxlen(int n, const int *cstart_dev, int ncolour, const int *rowptr,
+                                int *out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int c = 0;
+  while (c + 1 < ncolour && r >= cstart_dev[c + 1]) ++c;
+  atomicMax(out + c, rowptr[r + 1] - rowptr[r]);
+}
+
+constexpr int kLongRow = 24;   // colours with a row longer than this use a warp per row
 
 int ilu_setup(Sim *s) {
   int n = s->A.n;
@@ -283,6 +472,20 @@ int ilu_setup(Sim *s) {
   DP_TRY(scan_i32(s, len, s->lu_rowptr, n, &nnz));
   DP_LAUNCH(s, k_lu_pattern, nblk(n), kBlock, 0, n, s->perm, s->iperm, s->A.rowptr, s->A.col,
             s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos);
+  {
+    int nc = s->ncolour;
+    int *dev = (int *)dalloc(s, (size_t)(2 * nc + 2) * 4);
+    if (!dev) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+    DP_CUDA(s, cudaMemcpyAsync(dev, s->lu_cstart.data(), (size_t)(nc + 1) * 4,
+                               cudaMemcpyHostToDevice, s->stream));
+    DP_CUDA(s, cudaMemsetAsync(dev + nc + 1, 0, (size_t)nc * 4, s->stream));
+    DP_LAUNCH(s, k_colour_maxlen, nblk(n), kBlock, 0, n, dev, nc, s->lu_rowptr, dev + nc + 1);
+    s->lu_cmaxlen.assign(nc, 0);
+    DP_CUDA(s, cudaMemcpyAsync(s->lu_cmaxlen.data(), dev + nc + 1, (size_t)nc * 4,
+                               cudaMemcpyDeviceToHost, s->stream));
+    DP_CUDA(s, cudaStreamSynchronize(s->stream));
+    dfree(s, dev);
+  }
   // update lists of the factorisation
   int *cnt = (int *)dalloc(s, (size_t)nnz * 4);
   s->upd_ptr = (int *)dalloc(s, ((size_t)nnz + 1) * 4);
@@ -297,6 +500,29 @@ int ilu_setup(Sim *s) {
   if (!s->upd_e2 || !s->upd_q) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   DP_LAUNCH(s, k_ilu_upd, nblk(n), kBlock, 0, n, 1, s->iperm, s->lu_rowptr, s->lu_col, s->lu_dpos,
             s->upd_ptr, cnt, s->upd_e2, s->upd_q);
+  // split layout: L and U row pointers, each entry's block, permuted columns
+  int *nu = cnt;   // reused: n <= nnz
+  s->lu_Lptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
+  s->lu_Uptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
+  s->lu_dst = (int *)dalloc(s, (size_t)nnz * 4);
+  s->lu_colp = (int *)dalloc(s, (size_t)nnz * 4);
+  s->ilu_zp = (double *)dalloc(s, (size_t)2 * n * 8);
+  if (!s->lu_Lptr || !s->lu_Uptr || !s->lu_dst || !s->lu_colp || !s->ilu_zp) {
+    s->fail(DP_ENOMEM, "allocation failed");
+    return DP_ENOMEM;
+  }
+  DP_LAUNCH(s, k_lu_lens, nblk(n), kBlock, 0, n, s->lu_rowptr, s->lu_dpos, len, nu);
+  int nL = 0, nU = 0;
+  DP_TRY(scan_i32(s, len, s->lu_Lptr, n, &nL));
+  DP_TRY(scan_i32(s, nu, s->lu_Uptr, n, &nU));
+  if (nL + nU + n != nnz) { s->fail(DP_EINVAL, "ILU(0) pattern without a pivot per row"); return DP_EINVAL; }
+  s->lu_nL = nL;
+  DP_LAUNCH(s, k_ilu_split, nblk(n), kBlock, 0, n, nL, s->iperm, s->lu_rowptr, s->lu_col,
+            s->lu_dpos, s->lu_Lptr, s->lu_Uptr, s->lu_dst, s->lu_colp);
+  if (npairs > 0) {
+    DP_LAUNCH(s, k_remap, nblk(npairs), kBlock, 0, (long long)npairs, s->lu_dst, s->upd_e2);
+    DP_LAUNCH(s, k_remap, nblk(npairs), kBlock, 0, (long long)npairs, s->lu_dst, s->upd_q);
+  }
   DP_CUDA(s, cudaGetLastError());
   dfree(s, cnt);
   dfree(s, len);
@@ -309,37 +535,72 @@ int ilu_factor(Sim *s) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
     if (f32)
-      DP_LAUNCH(s, k_ilu_factor<float>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->iperm,
-                s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos, s->upd_ptr, s->upd_e2, s->upd_q,
-                s->A.val, s->lu_valf);
+      DP_LAUNCH(s, k_ilu_factor<float>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->lu_nL,
+                s->lu_rowptr, s->lu_dpos, s->lu_dst, s->lu_colp, s->lu_src, s->upd_ptr, s->upd_e2,
+                s->upd_q, s->A.val, s->lu_valf);
     else
-      DP_LAUNCH(s, k_ilu_factor<double>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->iperm,
-                s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos, s->upd_ptr, s->upd_e2, s->upd_q,
-                s->A.val, s->lu_val);
+      DP_LAUNCH(s, k_ilu_factor<double>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->lu_nL,
+                s->lu_rowptr, s->lu_dpos, s->lu_dst, s->lu_colp, s->lu_src, s->upd_ptr, s->upd_e2,
+                s->upd_q, s->A.val, s->lu_val);
   }
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
 
-// z = (LU)^-1 r with the factor in T; r in TR.
+// (LU)^-1 r with the factor in T and r (natural order) in TR; the result
+// is left in the colour-order work vector s->ilu_zp, from which the caller
+// gathers it (ilu_result) while converting or accumulating.
 template <typename T, typename TR>
-static int ilu_apply_t(Sim *s, const T *lu, const TR *r, T *z) {
+static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
+  int n = s->A.n, nL = s->lu_nL;
+  T *zp = reinterpret_cast<T *>(s->ilu_zp);
   for (int c = 0; c < s->ncolour; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
-    if (r1 > r0)
+    if (r1 <= r0) continue;
+    if (s->lu_cmaxlen[c] > kLongRow)
+      DP_LAUNCH(s, (k_ilu_fwd_w<T, TR>), nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
+                s->lu_Lptr, s->lu_colp, lu, r, zp);
+    else
       DP_LAUNCH(s, (k_ilu_fwd<T, TR>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
-                s->lu_rowptr, s->lu_col, s->lu_dpos, lu, r, z);
+                s->lu_Lptr, s->lu_colp, lu, r, zp);
   }
   for (int c = s->ncolour - 1; c >= 0; --c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
-    if (r1 > r0)
-      DP_LAUNCH(s, k_ilu_bwd<T>, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
-                s->lu_rowptr, s->lu_col, s->lu_dpos, lu, z);
+    if (r1 <= r0) continue;
+    if (s->lu_cmaxlen[c] > kLongRow)
+      DP_LAUNCH(s, k_ilu_bwd_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL, n,
+                s->lu_Uptr, s->lu_colp, lu, zp);
+    else
+      DP_LAUNCH(s, k_ilu_bwd<T>, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, nL, n, s->lu_Uptr,
+                s->lu_colp, lu, zp);
   }
   return DP_OK;
 }
 
-int ilu_apply(Sim *s, const double *r, double *z) { return ilu_apply_t<double, double>(s, s->lu_val, r, z); }
+// out_i = base_i + zp_{iperm[i]} (base may be NULL: out_i = zp_{iperm[i]}),
+// natural order, FP64; two lanes per block row.
+template <typename T>
+__global__ void k_ilu_result(int n, const int *__restrict__ iperm, const T *__restrict__ zp,
+                             const double *__restrict__ base, double *__restrict__ out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2LL * n) return;
+  int i = (int)(t >> 1), comp = (int)(t & 1);
+  double v = double(zp[2 * (size_t)__ldg(iperm + i) + comp]);
+  out[t] = base ? base[t] + v : v;
+}
+
+template <typename T>
+static int ilu_result(Sim *s, const double *base, double *out) {
+  int n = s->A.n;
+  DP_LAUNCH(s, k_ilu_result<T>, nblk(2LL * n), kBlock, 0, n, s->iperm,
+            reinterpret_cast<const T *>(s->ilu_zp), base, out);
+  return DP_OK;
+}
+
+int ilu_apply(Sim *s, const double *r, double *z) {
+  DP_TRY((ilu_apply_t<double, double>(s, s->lu_val, r)));
+  return ilu_result<double>(s, nullptr, z);
+}
 
 // ---------------------------------------------------------------- AMG cycle
 
@@ -716,6 +977,8 @@ static int jacobi_post(Sim *s, Level &L, const T *b, T *x, T *r) {
 // rows q of a colour are contiguous in the ILU(0) pattern (row q is natural
 // row perm[q], entries lu_col[e] with values pv[e]), so a sweep streams the
 // operator once instead of touching every row's sectors for every colour.
+// Operator data read once per sweep is loaded evict-first (ld.global.cs) so
+// that the vectors stay in L2 between colours.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gs_lu(int r0, int r1, const int *__restrict__ perm,
                                                   const int *__restrict__ lu_rowptr,
@@ -725,10 +988,40 @@ __global__ void __launch_bounds__(kBlock) k_gs_lu(int r0, int r1, const int *__r
                                                   const T *__restrict__ b, T *x) {
   int q = r0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= r1) return;
-  int i = __ldg(perm + q);
-  T s = row_dot<1, T>(__ldg(lu_rowptr + q), __ldg(lu_rowptr + q + 1), 0, lu_col, pv, x);
+  int i = __ldcs(perm + q);
+  int e = __ldcs(lu_rowptr + q), e1 = __ldcs(lu_rowptr + q + 1);
+  T s0 = T(0), s1 = T(0);
+  for (; e + 1 < e1; e += 2) {
+    int c0 = __ldcs(lu_col + e), c1 = __ldcs(lu_col + e + 1);
+    T v0 = __ldcs(pv + e), v1 = __ldcs(pv + e + 1);
+    s0 = fma(v0, x[c0], s0);
+    s1 = fma(v1, x[c1], s1);
+  }
+  if (e < e1) s0 = fma(__ldcs(pv + e), x[__ldcs(lu_col + e)], s0);
+  T s = s0 + s1;
   T di = dinv[i];
   if (di != T(0)) x[i] = fma(b[i] - s, di, x[i]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_lu_w(int r0, int r1, const int *__restrict__ perm,
+                                                    const int *__restrict__ lu_rowptr,
+                                                    const int *__restrict__ lu_col,
+                                                    const T *__restrict__ pv,
+                                                    const T *__restrict__ dinv,
+                                                    const T *__restrict__ b, T *x) {
+  int q = r0 + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (q >= r1) return;   // whole warps
+  T s = T(0);
+  for (int e = __ldg(lu_rowptr + q) + lane, e1 = __ldg(lu_rowptr + q + 1); e < e1; e += 32)
+    s = fma(__ldg(pv + e), x[__ldg(lu_col + e)], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    int i = __ldg(perm + q);
+    T di = dinv[i];
+    if (di != T(0)) x[i] = fma(b[i] - s, di, x[i]);
+  }
 }
 
 template <typename T>
@@ -774,7 +1067,11 @@ static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
     for (int t = 0; t < L.ncolour; ++t) {
       int c = forward ? t : L.ncolour - 1 - t;
       int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
-      if (r1 > r0)
+      if (r1 <= r0) continue;
+      if (s->lu_cmaxlen[c] > kLongRow)
+        DP_LAUNCH(s, k_gs_lu_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
+                  s->lu_rowptr, s->lu_col, pv, LV<T>::dinv(L), b, x);
+      else
         DP_LAUNCH(s, k_gs_lu<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->perm, s->lu_rowptr,
                   s->lu_col, pv, LV<T>::dinv(L), b, x);
     }
@@ -847,21 +1144,12 @@ __global__ void k_inject_add(int n, const T *xp, double *z) {
   if (i < n) z[2 * i] += double(xp[i]);
 }
 
-template <typename T>
-__global__ void k_axpy1(long long n, const T *x, double *y) {  // y += x
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] += double(x[i]);
-}
 
 __global__ void k_to_f32(long long n, const double *x, float *y) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = float(x[i]);
 }
 
-__global__ void k_to_f64(long long n, const float *x, double *y) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = double(x[i]);
-}
 
 int cpr_apply(Sim *s, const double *r, double *z) {
   int nb = s->A.n;
@@ -874,34 +1162,30 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   if (!f32) {
     if (s->opt.precond == 1) return ilu_apply(s, r, z);
     DP_TRY(ilu_apply(s, r, s->z1));
-    DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr, s->scol,
-              s->sa00, s->sa01, s->z1, r, s->rp);
+    DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->ph.nc), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr,
+              s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
     DP_TRY(vcycle(s, 0, s->rp, s->xp));
     DP_LAUNCH(s, k_inject_add<double>, nblk(nb), kBlock, 0, nb, s->xp, s->z1);
     DP_TRY(bsr_residual(s, r, s->z1, s->r1));
-    DP_TRY(ilu_apply(s, s->r1, z));
-    DP_LAUNCH(s, k_axpy1<double>, nblk(N), kBlock, 0, N, s->z1, z);
-    return DP_OK;
+    DP_TRY((ilu_apply_t<double, double>(s, s->lu_val, s->r1)));
+    return ilu_result<double>(s, s->z1, z);           // z = z2 + F (r - A z2)
   }
   // FP32 factor, FP32 V-cycle; the stage residuals stay in FP64
   if (s->opt.precond == 1) {
-    DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r, s->zf)));
-    DP_LAUNCH(s, k_to_f64, nblk(N), kBlock, 0, N, s->zf, z);
-    return DP_OK;
+    DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
+    return ilu_result<float>(s, nullptr, z);
   }
   Level &L0 = s->lev[0];
-  DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r, s->zf)));
-  DP_LAUNCH(s, k_to_f64, nblk(N), kBlock, 0, N, s->zf, s->z1);
-  DP_LAUNCH(s, k_bsr_presid, nblk(nb), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr, s->scol,
-            s->sa00, s->sa01, s->z1, r, s->rp);
+  DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
+  DP_TRY(ilu_result<float>(s, nullptr, s->z1));
+  DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->ph.nc), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr,
+            s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
   DP_LAUNCH(s, k_to_f32, nblk(nb), kBlock, 0, (long long)nb, s->rp, L0.bf);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
   DP_LAUNCH(s, k_inject_add<float>, nblk(nb), kBlock, 0, nb, L0.xf, s->z1);
   DP_TRY(bsr_residual(s, r, s->z1, s->r1));
-  DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, s->r1, s->zf)));
-  DP_CUDA(s, cudaMemcpyAsync(z, s->z1, N * 8, cudaMemcpyDeviceToDevice, s->stream));
-  DP_LAUNCH(s, k_axpy1<float>, nblk(N), kBlock, 0, N, s->zf, z);
-  return DP_OK;
+  DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, s->r1)));
+  return ilu_result<float>(s, s->z1, z);              // z = z2 + F (r - A z2)
 }
 
 // ---------------------------------------------------------------- FGMRES
@@ -1296,9 +1580,8 @@ int la_alloc(Sim *s) {
   s->r1 = (double *)dalloc(s, (size_t)N * 8);
   s->rp = (double *)dalloc(s, (size_t)s->A.n * 8);
   s->xp = (double *)dalloc(s, (size_t)s->A.n * 8);
-  s->zf = (float *)dalloc(s, (size_t)N * 4);
   if (!s->V || !s->Z || !s->w || !s->H || !s->cs || !s->sn || !s->g || !s->hy || !s->dots_part ||
-      !s->dots || !s->scal || !s->z1 || !s->r1 || !s->rp || !s->xp || !s->zf) {
+      !s->dots || !s->scal || !s->z1 || !s->r1 || !s->rp || !s->xp) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }

@@ -84,7 +84,14 @@ bool dp_server::admissible(const Request &q, std::vector<int> &victims, bool &ne
   if (r.busy) return false;
   if (r.sim) return true;
   uint64_t need = estimate(r);
-  if (need > budget) { never = true; return true; }
+  if (need > budget) {
+    // refused only on a measured estimate; before any measurement the guess
+    // may be pessimistic, so the request waits until nothing else holds
+    // device memory and then runs alone (and its footprint is measured)
+    if (bytes_per_row > 0.0) { never = true; return true; }
+    if (running > 0) return false;
+    need = budget;
+  }
   uint64_t have = resident_bytes;
   if (have + need <= budget) return true;
   std::vector<int> idle;

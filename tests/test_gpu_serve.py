@@ -67,10 +67,12 @@ def test_resident_requests_equal_alone():
 
 def test_evictions_stay_within_budget_and_tolerance():
     ref, peaks = alone("parity")
-    budget = int(2.3 * max(peaks))     # room for about two realisations
+    budget = int(1.5 * max(peaks))     # the largest realisation and a small one at most
     res, states, info = serve("parity", 3, budget)
-    assert info.evictions > 0
-    assert info.peak_resident_bytes <= budget
+    detail = (peaks, budget, info.evictions, info.loads, info.peak_resident_bytes,
+              info.bytes_per_row)
+    assert info.evictions > 0, detail
+    assert info.peak_resident_bytes <= budget, detail
     for k in range(len(MEMBERS)):
         assert [r.status for r in res[k]] == [0] * len(DTS)
         p, sw, bhp = states[k]
@@ -81,9 +83,20 @@ def test_evictions_stay_within_budget_and_tolerance():
 
 
 def test_oversized_realisation_is_refused():
-    srv = gpu().Server(2, 1 << 20, gpu().options("report"))
-    rid = srv.add(di.ensemble_member(0))
-    r = srv.wait(srv.submit(rid, di.DAY))
-    assert r.status == gpu().DP_ENOMEM
-    assert srv.info().resident == 0
+    """Once a realisation has been measured, one whose estimated footprint
+    exceeds the budget gets DP_ENOMEM without being loaded."""
+    import torch
+    small = di.ensemble_member(0)
+    s = gpu().Sim(small, gpu().options("report"), stream=torch.cuda.Stream())
+    s.advance(small.dt)
+    peak = s.footprint()[1]
+    s.close()
+    srv = gpu().Server(2, int(1.5 * peak), gpu().options("report"))
+    a = srv.add(small)
+    b = srv.add(di.ensemble_member(40))   # about 30 times the rows
+    assert srv.wait(srv.submit(a, di.DAY)).status == 0
+    r = srv.wait(srv.submit(b, di.DAY))
+    assert r.status == gpu().DP_ENOMEM and r.loaded == 0
+    info = srv.info()
+    assert info.resident == 1 and info.loads == 1
     srv.close()
