@@ -116,6 +116,10 @@ typedef struct {
                             use_graphs); < 0: never; 0: the library default,
                             20000 rows when one of those levels uses
                             Gauss-Seidel, else never */
+  int32_t amg_refresh;   /* 0: the prolongators and coarse operators are recomputed
+                            every Newton iteration; 1: only at the first Newton
+                            iteration of a timestep (level 0, the pressure block,
+                            always takes the current values) */
 } dp_options;
 
 typedef struct {

@@ -679,9 +679,12 @@ static int amg_setup(og_amg *m, const og_csr *A0) {
   return 0;
 }
 
-/* Numeric refresh with the integer structure kept (values of level 0 new). */
-static void amg_refresh(og_amg *m, const double *val0) {
+/* Numeric refresh with the integer structure kept (values of level 0 new);
+ * with coarse = 0 only level 0 takes the new values and the transfer and
+ * coarse operators of the last refresh stay. */
+static void amg_refresh(og_amg *m, const double *val0, int coarse) {
   memcpy(m->lev[0].A.val, val0, (size_t)m->lev[0].A.nnz * sizeof(double));
+  if (!coarse) return;
   for (int l = 0; l + 1 < m->nlev; ++l) {
     og_level *L = &m->lev[l];
     csr_free(&L->P); csr_free(&L->R);
@@ -1544,7 +1547,7 @@ int oracle_solve_step(void *h, og_stats *st) {
   if (s->o.precond >= 1) ilu_factor(&s->ilu, &s->J);
   if (s->o.precond == 2) {
     if (!s->amg_ready) { amg_setup(&s->amg, &s->Ap); s->amg_ready = 1; }
-    else amg_refresh(&s->amg, s->Ap.val);
+    else amg_refresh(&s->amg, s->Ap.val, s->o.amg_refresh == 0 || s->newton_iter == 0);
   }
   og_cpr c; memset(&c, 0, sizeof(c));
   c.A = &s->J; c.ilu = &s->ilu; c.amg = &s->amg; c.mode = s->o.precond;

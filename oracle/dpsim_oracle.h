@@ -43,6 +43,9 @@ typedef struct {
   double ds_max;
   int32_t amg_gs_levels;  /* levels 0..amg_gs_levels-1 smoothed by multicolour
                              Gauss-Seidel, coarser levels by l1-Jacobi */
+  int32_t amg_refresh;    /* 0: P, R and the coarse operators recomputed every
+                             Newton iteration; 1: only at the first Newton
+                             iteration of a timestep (level 0 always current) */
 } og_options;
 typedef struct {
   int32_t newton_iters, linear_iters, converged, amg_levels;

@@ -157,7 +157,7 @@ int coarse_factor(Sim *s);
 int cpr_apply(Sim *s, const double *r, double *z);
 int fgmres(Sim *s, double tol, int *iters, double *relres);
 int la_alloc(Sim *s);
-int mixed_refresh(Sim *s);
+int mixed_refresh(Sim *s, bool coarse);
 int l0_refresh(Sim *s);
 int lanes_for(double mean_len);
 void graphs_free(Sim *s);

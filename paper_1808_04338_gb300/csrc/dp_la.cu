@@ -1594,9 +1594,16 @@ __global__ void k_to_f32_i(long long n, const double *x, float *y) {
 }
 
 // FP32 copies of the AMG operators, transfer operators and inverse
-// diagonals (precision 1), refreshed with the FP64 values.
-int mixed_refresh(Sim *s) {
+// diagonals (precision 1), refreshed with the FP64 values: every level, or
+// (coarse = false) the level-0 operator and scaling only.
+int mixed_refresh(Sim *s, bool coarse) {
   for (size_t l = 0; l < s->lev.size(); ++l) {
+    if (!coarse) {
+      Level &L = s->lev[0];
+      DP_LAUNCH(s, k_to_f32_i, nblk(L.nnz), kBlock, 0, (long long)L.nnz, L.val, L.valf);
+      DP_LAUNCH(s, k_to_f32_i, nblk(L.n), kBlock, 0, (long long)L.n, L.dinv, L.dinvf);
+      break;
+    }
     Level &L = s->lev[l];
     DP_LAUNCH(s, k_to_f32_i, nblk(L.nnz), kBlock, 0, (long long)L.nnz, L.val, L.valf);
     DP_LAUNCH(s, k_to_f32_i, nblk(L.n), kBlock, 0, (long long)L.n, L.dinv, L.dinvf);

@@ -108,7 +108,8 @@ using namespace dp;
 static bool bad_opts(const dp_options *o) {
   return !o || o->gmres_restart < 1 || o->gmres_maxit < 1 || o->newton_max < 0 ||
          o->amg_coarse_max < 1 || o->amg_max_levels < 1 || o->precond < 0 || o->precond > 2 ||
-         o->precision < 0 || o->precision > 1 || !(o->ds_max > 0.0) || o->amg_gs_levels < 0;
+         o->precision < 0 || o->precision > 1 || !(o->ds_max > 0.0) || o->amg_gs_levels < 0 ||
+         o->amg_refresh < 0 || o->amg_refresh > 1;
 }
 
 extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_fluid *fluid,
@@ -329,11 +330,13 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   s->decoupled = true;
   if (s->opt.precond >= 1) DP_TRY(ilu_factor(s));
   if (s->opt.precond == 2) {
+    bool coarse = !s->amg_ready || s->opt.amg_refresh == 0 || s->newton_iter == 0;
     if (!s->amg_ready) DP_TRY(amg_setup(s));
-    else DP_TRY(amg_refresh(s));
-    if (s->opt.precision == 1) DP_TRY(mixed_refresh(s));
+    else if (coarse) DP_TRY(amg_refresh(s));
+    else DP_TRY(level_dinv(s, s->lev[0]));   // level 0 only: its values are s->ap
+    if (s->opt.precision == 1) DP_TRY(mixed_refresh(s, coarse));
     DP_TRY(l0_refresh(s));
-    DP_TRY(cluster_refresh(s));
+    if (coarse) DP_TRY(cluster_refresh(s));
   }
   cudaEventRecord(e1, s->stream);
   int it = 0;

@@ -231,13 +231,28 @@ def test_layered_200k_first_step_parity():
         assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
 
 
-def test_layered_200k_timestep_parity():
+@pytest.mark.parametrize("amg_refresh", [0, 1])
+def test_layered_200k_timestep_parity(amg_refresh):
+    """One 5-day timestep of the 200k-cell grid; with amg_refresh = 1 both
+    sides keep the coarse AMG values of the timestep's first Newton
+    iteration for the later ones."""
     prob = di.layered()
-    g, o = pair(prob, "parity")
+    g, o = pair(prob, "parity", amg_refresh=amg_refresh)
     rcg, stg = g.advance(prob.dt)
     rco, sto = o.advance(prob.dt)
     assert rcg == rco == 0
+    assert stg.newton_iters == sto.newton_iters > 1
     state_close(g, o, prob)
+
+
+def test_tiny_steps_with_timestep_amg_refresh():
+    prob = di.tiny()
+    g, o = pair(prob, "parity", amg_refresh=1)
+    for step in range(prob.nsteps):
+        rcg, _ = g.advance(prob.dt)
+        rco, _ = o.advance(prob.dt)
+        assert rcg == rco == 0, step
+        state_close(g, o, prob)
 
 
 @pytest.mark.parametrize("precond", [1, 2])
