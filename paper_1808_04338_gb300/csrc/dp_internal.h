@@ -133,6 +133,7 @@ int phys_save_old(Sim *s);
 int phys_assemble(Sim *s);
 int phys_norms(Sim *s);
 int phys_decouple_extract(Sim *s);
+int phys_decoupled_natural(Sim *s, double *out);
 int phys_update(Sim *s);
 
 // dp_amg.cu (integer setup and bit-exact smoothed-aggregation numerics)
@@ -227,6 +228,10 @@ struct Sim {
   int lu_nL = 0;
   int *lu_Lptr = nullptr, *lu_Uptr = nullptr, *lu_dst = nullptr, *lu_colp = nullptr;
   double *ilu_zp = nullptr;       // colour-order work vector (2 nb values of the sweep type)
+  // maps of the decoupling's entry-parallel writes: natural row of each
+  // entry, its block in the factor's split layout, its factor-order position
+  int *erow = nullptr, *ilupos = nullptr, *l0pos = nullptr;
+  double *fct = nullptr;          // a01 / a11 of each cell row's diagonal block
   std::vector<int> lu_cstart;
   std::vector<int> lu_cmaxlen;   // longest row (blocks) of each colour
   // AMG hierarchy (level 0 shares the block pattern)

@@ -229,22 +229,17 @@ __global__ void k_ilu_upd(int n, int fill, const int *iperm, const int *lu_rowpt
 
 // IKJ block ILU(0) of the rows [r0, r1) of one colour, in precision T: all
 // their L blocks refer to rows of earlier colours, which are final.  The
-// loops run over the row's entries e in factor order (lu_rowptr, lu_dpos);
+// decoupling has already written the rows' values into the split layout.
+// The loops run over the row's entries e in factor order (lu_rowptr, lu_dpos);
 // dst[e] is the entry's block in the split layout and the update lists hold
 // split-layout positions.
 template <typename T>
 __global__ void k_ilu_factor(int r0, int r1, int nL, const int *lu_rowptr, const int *lu_dpos,
-                             const int *dst, const int *colp, const int *lu_src,
-                             const int *upd_ptr, const int *upd_e2, const int *upd_q,
-                             const double *aval, T *lu) {
+                             const int *dst, const int *colp, const int *upd_ptr,
+                             const int *upd_e2, const int *upd_q, T *lu) {
   int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= r1) return;
-  int s0 = lu_rowptr[r], s1 = lu_rowptr[r + 1], dp = lu_dpos[r];
-  for (int e = s0; e < s1; ++e) {
-    const double *src = aval + 4 * (size_t)lu_src[e];
-    T *d = lu + 4 * (size_t)dst[e];
-    d[0] = T(src[0]); d[1] = T(src[1]); d[2] = T(src[2]); d[3] = T(src[3]);
-  }
+  int s0 = lu_rowptr[r], dp = lu_dpos[r];
   for (int e = s0; e < dp; ++e) {
     int k = dst[e];
     int rk = colp[k];
@@ -424,6 +419,19 @@ __global__ void k_ilu_split(int n, int nL, const int *iperm, const int *lu_rowpt
   }
 }
 
+// For natural entry e: its row, its block in the split layout and its
+// factor-order position (inverse of lu_src).
+__global__ void k_entry_maps(int n, const int *rowptr, const int *lu_rowptr, const int *lu_src,
+                             const int *dst, int *erow, int *ilupos, int *l0pos) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) erow[e] = r;
+  for (int f = lu_rowptr[r]; f < lu_rowptr[r + 1]; ++f) {
+    ilupos[lu_src[f]] = dst[f];
+    l0pos[lu_src[f]] = f;
+  }
+}
+
 __global__ void k_remap(long long n, const int *map, int *v) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = map[v[i]];
@@ -523,6 +531,17 @@ int ilu_setup(Sim *s) {
     DP_LAUNCH(s, k_remap, nblk(npairs), kBlock, 0, (long long)npairs, s->lu_dst, s->upd_e2);
     DP_LAUNCH(s, k_remap, nblk(npairs), kBlock, 0, (long long)npairs, s->lu_dst, s->upd_q);
   }
+  // maps for the decoupling's writes
+  s->erow = (int *)dalloc(s, (size_t)nnz * 4);
+  s->ilupos = (int *)dalloc(s, (size_t)nnz * 4);
+  s->l0pos = (int *)dalloc(s, (size_t)nnz * 4);
+  s->fct = (double *)dalloc(s, (size_t)n * 8);
+  if (!s->erow || !s->ilupos || !s->l0pos || !s->fct) {
+    s->fail(DP_ENOMEM, "allocation failed");
+    return DP_ENOMEM;
+  }
+  DP_LAUNCH(s, k_entry_maps, nblk(n), kBlock, 0, n, s->A.rowptr, s->lu_rowptr, s->lu_src,
+            s->lu_dst, s->erow, s->ilupos, s->l0pos);
   DP_CUDA(s, cudaGetLastError());
   dfree(s, cnt);
   dfree(s, len);
@@ -536,12 +555,12 @@ int ilu_factor(Sim *s) {
     if (r1 <= r0) continue;
     if (f32)
       DP_LAUNCH(s, k_ilu_factor<float>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->lu_nL,
-                s->lu_rowptr, s->lu_dpos, s->lu_dst, s->lu_colp, s->lu_src, s->upd_ptr, s->upd_e2,
-                s->upd_q, s->A.val, s->lu_valf);
+                s->lu_rowptr, s->lu_dpos, s->lu_dst, s->lu_colp, s->upd_ptr, s->upd_e2, s->upd_q,
+                s->lu_valf);
     else
       DP_LAUNCH(s, k_ilu_factor<double>, nblk(r1 - r0, 128), 128, 0, r0, r1, s->lu_nL,
-                s->lu_rowptr, s->lu_dpos, s->lu_dst, s->lu_colp, s->lu_src, s->upd_ptr, s->upd_e2,
-                s->upd_q, s->A.val, s->lu_val);
+                s->lu_rowptr, s->lu_dpos, s->lu_dst, s->lu_colp, s->upd_ptr, s->upd_e2, s->upd_q,
+                s->lu_val);
   }
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
@@ -1031,9 +1050,10 @@ __global__ void k_gather_vals(long long n, const int *__restrict__ src, const do
   if (e < n) out[e] = T(v[__ldg(src + e)]);
 }
 
-// The colour-ordered level-0 values, refreshed with the level's values
-// every Newton step (used when level 0 is smoothed by Gauss-Seidel: its
-// colouring is the ILU(0) colouring, same pattern and same algorithm).
+// The colour-ordered level-0 values (used when level 0 is smoothed by
+// Gauss-Seidel: its colouring is the ILU(0) colouring, same pattern and same
+// algorithm): gathered here when first needed, then written by the
+// decoupling every Newton step.
 int l0_refresh(Sim *s) {
   if (s->lev.empty() || s->opt.precond != 2) return DP_OK;
   Level &L = s->lev[0];
@@ -1046,6 +1066,8 @@ int l0_refresh(Sim *s) {
     else s->l0_pv = (double *)dalloc(s, nnz * 8);
     if (!s->l0_pvf && !s->l0_pv) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
     s->l0_lu = true;
+  } else {
+    return DP_OK;   // later Newton steps: the decoupling writes the copy
   }
   if (s->l0_pvf)
     DP_LAUNCH(s, k_gather_vals<float>, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->lu_src, L.val,

@@ -666,59 +666,104 @@ int phys_norms(Sim *s) {
 // oil row, D_i^-1 = [[1, -a01/a11], [0, 1]], applied to the whole row and to
 // b = -R; well rows unchanged.  The pressure block takes entry (0,0) of
 // every decoupled block.
-// The decoupled rows are also written, in the storage order of the Krylov
-// operator's copy, to sval (whole blocks) and sa00 / sa01 (pressure rows).
+//
+// Two passes: one thread per row takes a01/a11 (one division per row) and
+// the right-hand side; then one thread per entry, in natural order
+// (coalesced reads of the Jacobian), writes the decoupled block wherever it
+// is consumed: the pressure block ap (natural order), the storage-order copy
+// of the Krylov operator (sval, and sa00/sa01 for the pressure residual),
+// the ILU(0) factor's starting values in its split layout and precision,
+// and the colour-ordered level-0 copy of the Gauss-Seidel sweeps.  The
+// Jacobian itself is left as assembled.
+__global__ void __launch_bounds__(kBlock) k_decouple_rows(int nb, int nc, const int *diag,
+                                                          const double *val, const double *R,
+                                                          double *fct, double *bh) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  double b0 = -R[2 * i], b1 = -R[2 * i + 1];
+  if (i < nc) {
+    const double *dg = val + 4 * (size_t)diag[i];
+    double a01 = dg[1], a11 = dg[3];
+    double f = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
+    fct[i] = f;
+    bh[2 * i] = b0 - (f * b1);
+  } else {
+    bh[2 * i] = b0;
+  }
+  bh[2 * i + 1] = b1;
+}
+
 struct DecArgs {
-  int nb, nc, nL;
-  const int *rowptr, *diag, *srowptr;
-  double *val, *bh, *ap, *sval, *sa00, *sa01;
-  const double *R;
+  long long nnz;
+  int nc, nL;
+  const int *erow, *rowptr, *srowptr, *ilupos, *l0pos;
+  const double *val, *fct;
+  double *ap, *sval, *sa00, *sa01;
+  void *lu;         // split-layout factor values (float or double), or null
+  void *l0;         // colour-ordered level-0 pressure values, or null
 };
 
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.nb) return;
-  int i = row_of_pair(t, a.nL, a.nc);     // consecutive threads: consecutive storage rows
-  double b0 = -a.R[2 * i], b1 = -a.R[2 * i + 1];
-  int e0 = a.rowptr[i], e1 = a.rowptr[i + 1], sb = a.srowptr[t] - e0;
-  double fct = 0.0;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.nnz) return;
+  int i = __ldg(a.erow + e);
+  const double2 *v2 = reinterpret_cast<const double2 *>(a.val) + 2 * e;
+  double2 u = v2[0], w = v2[1];
+  double n0 = u.x, n1 = u.y, n2 = w.x, n3 = w.y;
   if (i < a.nc) {
-    const double *dg = a.val + 4 * (size_t)a.diag[i];
-    double a01 = dg[1], a11 = dg[3];
-    fct = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
+    double f = a.fct[i];
+    n0 = n0 - (f * n2);
+    n1 = n1 - (f * n3);
   }
-  for (int e = e0; e < e1; ++e) {
-    double *v = a.val + 4 * (size_t)e;
-    double n0 = v[0], n1 = v[1], n2 = v[2], n3 = v[3];
-    if (i < a.nc) {
-      n0 = n0 - (fct * n2);
-      n1 = n1 - (fct * n3);
-      v[0] = n0; v[1] = n1;
-    }
-    a.ap[e] = n0;
-    size_t q = (size_t)(sb + e);
-    double2 *sv = reinterpret_cast<double2 *>(a.sval) + 2 * q;
-    sv[0] = make_double2(n0, n1);
-    sv[1] = make_double2(n2, n3);
-    a.sa00[q] = n0;
-    a.sa01[q] = n1;
+  a.ap[e] = n0;
+  int si = storage_row(i, a.nL, a.nc);
+  size_t q = (size_t)(__ldg(a.srowptr + si) + (int)(e - __ldg(a.rowptr + i)));
+  double2 *sv = reinterpret_cast<double2 *>(a.sval) + 2 * q;
+  sv[0] = make_double2(n0, n1);
+  sv[1] = make_double2(n2, n3);
+  a.sa00[q] = n0;
+  a.sa01[q] = n1;
+  if (a.lu) {
+    T *d = reinterpret_cast<T *>(a.lu) + 4 * (size_t)__ldg(a.ilupos + e);
+    d[0] = T(n0); d[1] = T(n1); d[2] = T(n2); d[3] = T(n3);
   }
-  if (i < a.nc) {
-    a.bh[2 * i] = b0 - (fct * b1);
-    a.bh[2 * i + 1] = b1;
-  } else {
-    a.bh[2 * i] = b0;
-    a.bh[2 * i + 1] = b1;
-  }
+  if (a.l0) reinterpret_cast<T *>(a.l0)[__ldg(a.l0pos + e)] = T(n0);
 }
 
 int phys_decouple_extract(Sim *s) {
+  DP_LAUNCH(s, k_decouple_rows, nblk(s->ph.nb), kBlock, 0, s->ph.nb, s->ph.nc, s->A.diag,
+            s->A.val, s->R, s->fct, s->bh);
   DecArgs a;
-  a.nb = s->ph.nb; a.nc = s->ph.nc; a.nL = s->ph.nL;
-  a.rowptr = s->A.rowptr; a.diag = s->A.diag; a.srowptr = s->srowptr;
-  a.val = s->A.val; a.bh = s->bh; a.ap = s->ap; a.sval = s->sval; a.sa00 = s->sa00;
-  a.sa01 = s->sa01; a.R = s->R;
-  DP_LAUNCH(s, k_decouple, nblk(s->ph.nb), kBlock, 0, a);
+  a.nnz = s->A.nnz; a.nc = s->ph.nc; a.nL = s->ph.nL;
+  a.erow = s->erow; a.rowptr = s->A.rowptr; a.srowptr = s->srowptr;
+  a.ilupos = s->ilupos; a.l0pos = s->l0pos;
+  a.val = s->A.val; a.fct = s->fct;
+  a.ap = s->ap; a.sval = s->sval; a.sa00 = s->sa00; a.sa01 = s->sa01;
+  bool f32 = s->opt.precision == 1;
+  a.lu = s->opt.precond >= 1 ? (f32 ? (void *)s->lu_valf : (void *)s->lu_val) : nullptr;
+  a.l0 = s->l0_lu ? (f32 ? (void *)s->l0_pvf : (void *)s->l0_pv) : nullptr;
+  if (f32) DP_LAUNCH(s, k_decouple<float>, nblk(s->A.nnz), kBlock, 0, a);
+  else DP_LAUNCH(s, k_decouple<double>, nblk(s->A.nnz), kBlock, 0, a);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// The decoupled matrix in natural order, from its storage-order copy (test
+// access: the Jacobian itself stays as assembled).
+__global__ void k_natural_from_storage(long long nnz, int nc, int nL, const int *erow,
+                                       const int *rowptr, const int *srowptr, const double *sval,
+                                       double *out) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  int i = erow[e];
+  size_t q = (size_t)(srowptr[storage_row(i, nL, nc)] + (int)(e - rowptr[i]));
+  for (int k = 0; k < 4; ++k) out[4 * e + k] = sval[4 * q + k];
+}
+
+int phys_decoupled_natural(Sim *s, double *out) {
+  DP_LAUNCH(s, k_natural_from_storage, nblk(s->A.nnz), kBlock, 0, (long long)s->A.nnz, s->ph.nc,
+            s->ph.nL, s->erow, s->A.rowptr, s->srowptr, s->sval, out);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }

@@ -469,8 +469,17 @@ extern "C" int sim_get_update(dp_sim *s, double *y) {
 extern "C" int sim_get_decoupled(dp_sim *s, double *val, double *rhs) {
   if (!s) return DP_EINVAL;
   if (!s->decoupled) { s->fail(DP_EINVAL, "no decoupled system yet"); return DP_EINVAL; }
-  if (val)
-    DP_CUDA(s, cudaMemcpyAsync(val, s->A.val, (size_t)s->A.nnz * 32, cudaMemcpyDefault, s->stream));
+  if (val) {
+    double *tmp = (double *)dalloc(s, (size_t)s->A.nnz * 32);
+    if (!tmp) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+    int rc = phys_decoupled_natural(s, tmp);
+    if (rc == DP_OK &&
+        cudaMemcpyAsync(val, tmp, (size_t)s->A.nnz * 32, cudaMemcpyDefault, s->stream) != cudaSuccess)
+      rc = DP_ECUDA;
+    cudaStreamSynchronize(s->stream);
+    dfree(s, tmp);
+    if (rc != DP_OK) { s->fail(rc, "sim_get_decoupled"); return rc; }
+  }
   if (rhs) DP_CUDA(s, cudaMemcpyAsync(rhs, s->bh, (size_t)s->A.n * 16, cudaMemcpyDefault, s->stream));
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
   return check(s);
