@@ -313,6 +313,7 @@ def config_dict(args, nnzb=None):
                         f"{4 * args.nx * args.ny * args.nz + 50} unknowns, 25 wells, "
                         f"lognormal perm (sd 2), first 5-day Newton step",
             "grid": [args.nx, args.ny, args.nz], "precision": args.precision,
+            "decouple": args.decouple, "eta_mode": args.eta_mode,
             "precond": "CPR-FPF",
             "l2": f"inputs larger than L2 (Jacobian {32 * nnzb / 1e6:.0f} MB)" if nnzb else
                   "inputs larger than L2",
@@ -336,6 +337,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cluster-rows", type=int, default=0,
                     help="AMG levels up to this many rows run in one cluster launch (0: default)")
+    ap.add_argument("--decouple", type=int, default=0,
+                    help="0: the paper's modified Gauss-Jordan step; 1: ABF; 2: True-IMPES")
+    ap.add_argument("--eta-mode", type=int, default=2,
+                    help="forcing term of Algorithm 1: 1, 2 or 3 (Section 3.1), 0: fixed")
     ap.add_argument("--threads", type=int, default=16,
                     help="ensemble mode: host threads driving realisations concurrently")
     ap.add_argument("--mode", default="bench", choices=["bench", "newton2", "ensemble", "serve"],
@@ -365,7 +370,8 @@ def main():
     if args.mode == "serve":
         return run_serve(args)
     prob = workload(args)
-    opts = dpsim.options("report", precision=args.precision, cluster_rows=args.cluster_rows)
+    opts = dpsim.options("report", precision=args.precision, cluster_rows=args.cluster_rows,
+                         decouple=args.decouple, eta_mode=args.eta_mode)
     if args.mode == "newton2":
         sim = dpsim.Sim(prob, opts)
         out = {}
@@ -490,7 +496,8 @@ def main():
 
     fp64 = None
     if args.precision != 0 and not args.no_fp64_path:
-        o64 = dpsim.options("report", precision=0, cluster_rows=args.cluster_rows)
+        o64 = dpsim.options("report", precision=0, cluster_rows=args.cluster_rows,
+                            decouple=args.decouple, eta_mode=args.eta_mode)
         with torch.cuda.stream(stream):
             sim64 = dpsim.Sim(prob, o64, stream=stream)
         r = measure(sim64, o64, max(2, args.steps // 2), args.warmup)

@@ -120,6 +120,15 @@ typedef struct {
                             every Newton iteration; 1: only at the first Newton
                             iteration of a timestep (level 0, the pressure block,
                             always takes the current values) */
+  int32_t decouple;      /* D of Eq. "decoupled-eq", per cell block row (well rows
+                            unchanged): 0 the modified Gauss-Jordan step, read as
+                            the elimination of the pressure row's saturation
+                            coefficient by the water row of the diagonal block,
+                            D_i^-1 = [[1, -a01/a11], [0, 1]] (the per-cell
+                            Quasi-IMPES form); 1 ABF, D_i = the diagonal block;
+                            2 True-IMPES, D_i^-1 = [[1, -c01/c11], [0, 1]] with c
+                            the sums of block column i over all rows (Section 3.2
+                            names Quasi-IMPES and ABF beside its own choice) */
 } dp_options;
 
 typedef struct {

@@ -63,7 +63,8 @@ class og_options(C.Structure):
                 ("gmres_maxit", C.c_int32), ("amg_theta", C.c_double),
                 ("amg_coarse_max", C.c_int32), ("amg_max_levels", C.c_int32),
                 ("precond", C.c_int32), ("ds_max", C.c_double),
-                ("amg_gs_levels", C.c_int32), ("amg_refresh", C.c_int32)]
+                ("amg_gs_levels", C.c_int32), ("amg_refresh", C.c_int32),
+                ("decouple", C.c_int32)]
 
 
 class og_stats(C.Structure):
@@ -76,9 +77,10 @@ class og_stats(C.Structure):
 def options(mode: str = "parity", **kw) -> og_options:
     """Solver options.  'parity': fixed eta 1e-10 and Newton tolerance 1e-10
     so that two correct implementations agree far inside 1e-8.  'report':
-    the third forcing term (gamma 0.9, beta 2), Newton tolerance 1e-6,
-    l1-Jacobi instead of multicolour Gauss-Seidel on the AMG levels below
-    the finest, and the coarse AMG values refreshed once per timestep."""
+    the second forcing term of Section 3.1 clipped to [1e-4, 0.1], Newton
+    tolerance 1e-6, l1-Jacobi instead of multicolour Gauss-Seidel on the AMG
+    levels below the finest, and the coarse AMG values refreshed once per
+    timestep."""
     o = og_options()
     o.newton_max = 25
     o.newton_atol = 1e-13
@@ -94,7 +96,7 @@ def options(mode: str = "parity", **kw) -> og_options:
     if mode == "parity":
         o.eta_mode, o.eta_fixed, o.newton_tol = 0, 1e-10, 1e-10
     else:
-        o.eta_mode, o.eta_fixed, o.newton_tol = 3, 1e-4, 1e-6
+        o.eta_mode, o.eta_fixed, o.newton_tol = 2, 1e-4, 1e-6
         o.amg_gs_levels = 1
         o.amg_refresh = 1
     for k, v in kw.items():

@@ -1476,14 +1476,61 @@ int oracle_well_index(void *h, double *wi) {
  * diagonal block is the pivot that removes the saturation coefficient from
  * the oil row, D_i^-1 = [[1, -a01/a11], [0, 1]], applied to the whole block
  * row and to the right-hand side b = -R.  Well rows are left as they are. */
+/* Decoupling D^-1 A x = D^-1 b (Section 3.2, Eq. "decoupled-eq") per cell
+ * block row; well rows unchanged.  decouple 0: the modified Gauss-Jordan step
+ * of the paper read as the elimination of the pressure row's saturation
+ * coefficient by the water row of the diagonal block, D_i^-1 = [[1, -w_i],
+ * [0, 1]] with w_i = a01/a11 (the per-cell Quasi-IMPES form); 1: ABF
+ * (alternate block factorisation), D_i = the diagonal block; 2: True-IMPES,
+ * w_i = c01/c11 from the sums of block column i over all rows (taken before
+ * any row changes, rows in increasing order). */
 static void decouple(og_sim *s) {
   og_bsr *J = &s->J;
+  int mode = s->o.decouple;
+  double *w = NULL;
+  if (mode == 2) {
+    double *c01 = (double *)zalloc((size_t)s->nc, sizeof(double));
+    double *c11 = (double *)zalloc((size_t)s->nc, sizeof(double));
+    for (int k = 0; k < s->nb; ++k)
+      for (int e = J->rowptr[k]; e < J->rowptr[k + 1]; ++e) {
+        int j = J->col[e];
+        if (j >= s->nc) continue;
+        const double *a = J->val + 4 * (size_t)e;
+        c01[j] = c01[j] + a[1];
+        c11[j] = c11[j] + a[3];
+      }
+    w = (double *)zalloc((size_t)s->nc, sizeof(double));
+    for (int j = 0; j < s->nc; ++j) w[j] = fabs(c11[j]) < 1e-300 ? 0.0 : c01[j] / c11[j];
+    free(c01);
+    free(c11);
+  }
   for (int i = 0; i < s->nb; ++i) {
     double b0 = -s->R[2 * i], b1 = -s->R[2 * i + 1];
     if (i >= s->nc) { s->bh[2 * i] = b0; s->bh[2 * i + 1] = b1; continue; }
     const double *dg = J->val + 4 * (size_t)J->diag[i];
-    double a01 = dg[1], a11 = dg[3];
-    double fct = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
+    if (mode == 1) {
+      double d00 = dg[0], d01 = dg[1], d10 = dg[2], d11 = dg[3];
+      double det = (d00 * d11) - (d01 * d10);
+      if (fabs(det) < 1e-300) { s->bh[2 * i] = b0; s->bh[2 * i + 1] = b1; continue; }
+      double i00 = d11 / det, i01 = (-d01) / det, i10 = (-d10) / det, i11 = d00 / det;
+      for (int e = J->rowptr[i]; e < J->rowptr[i + 1]; ++e) {
+        double *a = J->val + 4 * (size_t)e;
+        double v0 = a[0], v1 = a[1], v2 = a[2], v3 = a[3];
+        a[0] = (i00 * v0) + (i01 * v2);
+        a[1] = (i00 * v1) + (i01 * v3);
+        a[2] = (i10 * v0) + (i11 * v2);
+        a[3] = (i10 * v1) + (i11 * v3);
+      }
+      s->bh[2 * i] = (i00 * b0) + (i01 * b1);
+      s->bh[2 * i + 1] = (i10 * b0) + (i11 * b1);
+      continue;
+    }
+    double fct;
+    if (mode == 2) fct = w[i];
+    else {
+      double a01 = dg[1], a11 = dg[3];
+      fct = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
+    }
     for (int e = J->rowptr[i]; e < J->rowptr[i + 1]; ++e) {
       double *a = J->val + 4 * (size_t)e;
       a[0] = a[0] - (fct * a[2]);
@@ -1492,6 +1539,7 @@ static void decouple(og_sim *s) {
     s->bh[2 * i] = b0 - (fct * b1);
     s->bh[2 * i + 1] = b1;
   }
+  free(w);
 }
 
 int oracle_get_decoupled(void *h, double *val, double *rhs) {

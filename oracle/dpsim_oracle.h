@@ -46,6 +46,11 @@ typedef struct {
   int32_t amg_refresh;    /* 0: P, R and the coarse operators recomputed every
                              Newton iteration; 1: only at the first Newton
                              iteration of a timestep (level 0 always current) */
+  int32_t decouple;       /* 0: the paper's modified Gauss-Jordan step (per cell,
+                             eliminate the pressure row's saturation coefficient
+                             with the diagonal block; the Quasi-IMPES form);
+                             1: ABF, the inverse of the diagonal block; 2: True-
+                             IMPES, weights from the block-column sums */
 } og_options;
 typedef struct {
   int32_t newton_iters, linear_iters, converged, amg_levels;

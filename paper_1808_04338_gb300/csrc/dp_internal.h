@@ -231,7 +231,8 @@ struct Sim {
   // maps of the decoupling's entry-parallel writes: natural row of each
   // entry, its block in the factor's split layout, its factor-order position
   int *erow = nullptr, *ilupos = nullptr, *l0pos = nullptr;
-  double *fct = nullptr;          // a01 / a11 of each cell row's diagonal block
+  double *fct = nullptr;          // per cell row: the weight w_i, or D_i^-1 (4 values, ABF)
+  int *btpos = nullptr;           // transpose position of each block entry (True-IMPES)
   std::vector<int> lu_cstart;
   std::vector<int> lu_cmaxlen;   // longest row (blocks) of each colour
   // AMG hierarchy (level 0 shares the block pattern)

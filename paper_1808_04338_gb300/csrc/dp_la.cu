@@ -432,6 +432,22 @@ __global__ void k_entry_maps(int n, const int *rowptr, const int *lu_rowptr, con
   }
 }
 
+// Position of entry (j, i) for every entry (i, j) of the structurally
+// symmetric block pattern (columns sorted within rows).
+__global__ void k_block_tpos(int n, const int *rowptr, const int *col, int *tpos) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    int j = col[e], lo = rowptr[j], hi = rowptr[j + 1], t = -1;
+    while (lo < hi) {
+      int m = (lo + hi) >> 1, c = col[m];
+      if (c == i) { t = m; break; }
+      if (c < i) lo = m + 1; else hi = m;
+    }
+    tpos[e] = t;
+  }
+}
+
 __global__ void k_remap(long long n, const int *map, int *v) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = map[v[i]];
@@ -535,13 +551,15 @@ int ilu_setup(Sim *s) {
   s->erow = (int *)dalloc(s, (size_t)nnz * 4);
   s->ilupos = (int *)dalloc(s, (size_t)nnz * 4);
   s->l0pos = (int *)dalloc(s, (size_t)nnz * 4);
-  s->fct = (double *)dalloc(s, (size_t)n * 8);
-  if (!s->erow || !s->ilupos || !s->l0pos || !s->fct) {
+  s->fct = (double *)dalloc(s, (size_t)n * 32);
+  s->btpos = (int *)dalloc(s, (size_t)nnz * 4);
+  if (!s->erow || !s->ilupos || !s->l0pos || !s->fct || !s->btpos) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
   DP_LAUNCH(s, k_entry_maps, nblk(n), kBlock, 0, n, s->A.rowptr, s->lu_rowptr, s->lu_src,
             s->lu_dst, s->erow, s->ilupos, s->l0pos);
+  DP_LAUNCH(s, k_block_tpos, nblk(n), kBlock, 0, n, s->A.rowptr, s->A.col, s->btpos);
   DP_CUDA(s, cudaGetLastError());
   dfree(s, cnt);
   dfree(s, len);

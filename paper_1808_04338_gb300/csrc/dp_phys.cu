@@ -661,41 +661,74 @@ int phys_norms(Sim *s) {
 }
 
 // ---------------------------------------------------------------- decoupling
-// One Gauss-Jordan step per cell block row (Eq. "decoupled-eq"): the water
-// row of the diagonal block eliminates the saturation coefficient of the
-// oil row, D_i^-1 = [[1, -a01/a11], [0, 1]], applied to the whole row and to
-// b = -R; well rows unchanged.  The pressure block takes entry (0,0) of
-// every decoupled block.
+// Per cell block row (Eq. "decoupled-eq"), well rows unchanged; the pressure
+// block takes entry (0,0) of every decoupled block.  Mode 0: the paper's
+// modified Gauss-Jordan step, read as the elimination of the pressure row's
+// saturation coefficient by the water row of the diagonal block, D_i^-1 =
+// [[1, -a01/a11], [0, 1]] (the per-cell Quasi-IMPES form); mode 1: ABF,
+// D_i^-1 = the inverse of the diagonal block; mode 2: True-IMPES, the weight
+// c01/c11 from the sums of block column i over all rows, in increasing row
+// order (read through the transpose positions of row i's entries).
 //
-// Two passes: one thread per row takes a01/a11 (one division per row) and
-// the right-hand side; then one thread per entry, in natural order
-// (coalesced reads of the Jacobian), writes the decoupled block wherever it
-// is consumed: the pressure block ap (natural order), the storage-order copy
-// of the Krylov operator (sval, and sa00/sa01 for the pressure residual),
-// the ILU(0) factor's starting values in its split layout and precision,
-// and the colour-ordered level-0 copy of the Gauss-Seidel sweeps.  The
-// Jacobian itself is left as assembled.
-__global__ void __launch_bounds__(kBlock) k_decouple_rows(int nb, int nc, const int *diag,
-                                                          const double *val, const double *R,
-                                                          double *fct, double *bh) {
+// Two passes: one thread per row takes the row's weight or inverse (the
+// divisions once per row) and the right-hand side; then one thread per
+// entry, in natural order (coalesced reads of the Jacobian), writes the
+// decoupled block wherever it is consumed: the pressure block ap (natural
+// order), the storage-order copy of the Krylov operator (sval, and
+// sa00/sa01 for the pressure residual), the ILU(0) factor's starting values
+// in its split layout and precision, and the colour-ordered level-0 copy of
+// the Gauss-Seidel sweeps.  The Jacobian itself is left as assembled.
+__global__ void __launch_bounds__(kBlock) k_decouple_rows(int nb, int nc, int mode,
+                                                          const int *rowptr, const int *diag,
+                                                          const int *tpos, const double *val,
+                                                          const double *R, double *fct,
+                                                          double *bh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   double b0 = -R[2 * i], b1 = -R[2 * i + 1];
-  if (i < nc) {
-    const double *dg = val + 4 * (size_t)diag[i];
-    double a01 = dg[1], a11 = dg[3];
-    double f = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
-    fct[i] = f;
-    bh[2 * i] = b0 - (f * b1);
-  } else {
+  if (i >= nc) {
     bh[2 * i] = b0;
+    bh[2 * i + 1] = b1;
+    return;
   }
+  const double *dg = val + 4 * (size_t)diag[i];
+  if (mode == 1) {
+    double d00 = dg[0], d01 = dg[1], d10 = dg[2], d11 = dg[3];
+    double det = (d00 * d11) - (d01 * d10);
+    double *f = fct + 4 * (size_t)i;
+    if (fabs(det) < 1e-300) {
+      f[0] = 1.0; f[1] = 0.0; f[2] = 0.0; f[3] = 1.0;   // row left as it is
+      bh[2 * i] = b0;
+      bh[2 * i + 1] = b1;
+      return;
+    }
+    double i00 = d11 / det, i01 = (-d01) / det, i10 = (-d10) / det, i11 = d00 / det;
+    f[0] = i00; f[1] = i01; f[2] = i10; f[3] = i11;
+    bh[2 * i] = (i00 * b0) + (i01 * b1);
+    bh[2 * i + 1] = (i10 * b0) + (i11 * b1);
+    return;
+  }
+  double w;
+  if (mode == 2) {
+    double c01 = 0.0, c11 = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const double *a = val + 4 * (size_t)tpos[e];
+      c01 = c01 + a[1];
+      c11 = c11 + a[3];
+    }
+    w = fabs(c11) < 1e-300 ? 0.0 : c01 / c11;
+  } else {
+    double a01 = dg[1], a11 = dg[3];
+    w = fabs(a11) < 1e-300 ? 0.0 : a01 / a11;
+  }
+  fct[i] = w;
+  bh[2 * i] = b0 - (w * b1);
   bh[2 * i + 1] = b1;
 }
 
 struct DecArgs {
   long long nnz;
-  int nc, nL;
+  int nc, nL, mode;
   const int *erow, *rowptr, *srowptr, *ilupos, *l0pos;
   const double *val, *fct;
   double *ap, *sval, *sa00, *sa01;
@@ -712,9 +745,22 @@ __global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
   double2 u = v2[0], w = v2[1];
   double n0 = u.x, n1 = u.y, n2 = w.x, n3 = w.y;
   if (i < a.nc) {
-    double f = a.fct[i];
-    n0 = n0 - (f * n2);
-    n1 = n1 - (f * n3);
+    if (a.mode == 1) {
+      const double *f = a.fct + 4 * (size_t)i;
+      double i00 = f[0], i01 = f[1], i10 = f[2], i11 = f[3];
+      bool keep = i00 == 1.0 && i01 == 0.0 && i10 == 0.0 && i11 == 1.0;   // singular pivot
+      double v0 = n0, v1 = n1, v2 = n2, v3 = n3;
+      if (!keep) {
+        n0 = (i00 * v0) + (i01 * v2);
+        n1 = (i00 * v1) + (i01 * v3);
+        n2 = (i10 * v0) + (i11 * v2);
+        n3 = (i10 * v1) + (i11 * v3);
+      }
+    } else {
+      double f = a.fct[i];
+      n0 = n0 - (f * n2);
+      n1 = n1 - (f * n3);
+    }
   }
   a.ap[e] = n0;
   int si = storage_row(i, a.nL, a.nc);
@@ -732,10 +778,11 @@ __global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
 }
 
 int phys_decouple_extract(Sim *s) {
-  DP_LAUNCH(s, k_decouple_rows, nblk(s->ph.nb), kBlock, 0, s->ph.nb, s->ph.nc, s->A.diag,
-            s->A.val, s->R, s->fct, s->bh);
+  int mode = s->opt.decouple;
+  DP_LAUNCH(s, k_decouple_rows, nblk(s->ph.nb), kBlock, 0, s->ph.nb, s->ph.nc, mode, s->A.rowptr,
+            s->A.diag, s->btpos, s->A.val, s->R, s->fct, s->bh);
   DecArgs a;
-  a.nnz = s->A.nnz; a.nc = s->ph.nc; a.nL = s->ph.nL;
+  a.nnz = s->A.nnz; a.nc = s->ph.nc; a.nL = s->ph.nL; a.mode = mode;
   a.erow = s->erow; a.rowptr = s->A.rowptr; a.srowptr = s->srowptr;
   a.ilupos = s->ilupos; a.l0pos = s->l0pos;
   a.val = s->A.val; a.fct = s->fct;

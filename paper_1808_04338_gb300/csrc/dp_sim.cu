@@ -109,7 +109,7 @@ static bool bad_opts(const dp_options *o) {
   return !o || o->gmres_restart < 1 || o->gmres_maxit < 1 || o->newton_max < 0 ||
          o->amg_coarse_max < 1 || o->amg_max_levels < 1 || o->precond < 0 || o->precond > 2 ||
          o->precision < 0 || o->precision > 1 || !(o->ds_max > 0.0) || o->amg_gs_levels < 0 ||
-         o->amg_refresh < 0 || o->amg_refresh > 1;
+         o->amg_refresh < 0 || o->amg_refresh > 1 || o->decouple < 0 || o->decouple > 2;
 }
 
 extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_fluid *fluid,

@@ -86,9 +86,12 @@ def test_jacobian_residual_bit_exact(make):
     np.testing.assert_array_equal(g.well_index(), o.well_index())
 
 
-def test_decoupling_colours_and_amg_setup_bit_exact():
+@pytest.mark.parametrize("decouple", [0, 1, 2])
+def test_decoupling_colours_and_amg_setup_bit_exact(decouple):
+    """The decoupled system (the paper's step, ABF, True-IMPES), the
+    colouring and the AMG set-up built on its pressure block, bit for bit."""
     prob = di.tiny()
-    g, o = pair(prob)
+    g, o = pair(prob, decouple=decouple)
     g.assemble(prob.dt)
     o.assemble(prob.dt)
     g.solve_step()
@@ -119,15 +122,16 @@ def dense_from_bsr(rowptr, col, val):
     return A
 
 
-@pytest.mark.parametrize("precond,gs_levels", [(1, 30), (2, 30), (2, 0)])
-def test_newton_update_parity(precond, gs_levels):
+@pytest.mark.parametrize("precond,gs_levels,decouple", [(1, 30, 0), (2, 30, 0), (2, 0, 0),
+                                                        (2, 30, 1), (2, 30, 2)])
+def test_newton_update_parity(precond, gs_levels, decouple):
     """One linear solve at eta = 1e-12 on both sides: the GPU update's true
     residual (dense J from the oracle) is at the tolerance, it agrees with
     the oracle's update as closely as the conditioning of J (~1e12) allows,
     and both take (nearly) the same number of FGMRES iterations."""
     prob = di.tiny()
     g, o = pair(prob, precond=precond, eta_fixed=1e-12, gmres_maxit=1000,
-                amg_gs_levels=gs_levels)
+                amg_gs_levels=gs_levels, decouple=decouple)
     st = interior(prob, 3)
     for s in (g, o):
         s.set_iterate(*st)
@@ -245,9 +249,12 @@ def test_layered_200k_timestep_parity(amg_refresh):
     state_close(g, o, prob)
 
 
-def test_tiny_steps_with_timestep_amg_refresh():
+@pytest.mark.parametrize("kw", [dict(amg_refresh=1), dict(decouple=1), dict(decouple=2)])
+def test_tiny_steps_option_variants(kw):
+    """Ten tiny timesteps against the oracle with the coarse AMG values kept
+    for a timestep, and with the ABF and True-IMPES decouplings."""
     prob = di.tiny()
-    g, o = pair(prob, "parity", amg_refresh=1)
+    g, o = pair(prob, "parity", **kw)
     for step in range(prob.nsteps):
         rcg, _ = g.advance(prob.dt)
         rco, _ = o.advance(prob.dt)

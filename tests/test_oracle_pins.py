@@ -92,6 +92,65 @@ def test_decoupling_removes_saturation_coefficient_and_keeps_solution():
     assert np.linalg.norm(y1 - y0) <= 1e-9 * np.linalg.norm(y0)
 
 
+def _decoupled(mode):
+    prob = small_problem(3, 2, 2)
+    s = O.OracleSim(prob, O.options("parity", decouple=mode))
+    s.set_iterate(*random_interior_state(prob))
+    s.assemble(prob.dt)
+    rowptr, col, val, res = s.jacobian()
+    s.solve_step()
+    dval, rhs = s.decoupled()
+    return prob, rowptr, col, val, res, dval, rhs
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_decoupling_variants_keep_solution(mode):
+    """ABF and True-IMPES (Section 3.2 names them beside the paper's own
+    choice) multiply each cell row by an invertible 2x2 block: the decoupled
+    system has the solution of J y = b, and well rows are unchanged."""
+    prob, rowptr, col, val, res, dval, rhs = _decoupled(mode)
+    nc = prob.n_cells
+    y1 = np.linalg.solve(dense_from_bsr(rowptr, col, dval), rhs)
+    y0 = np.linalg.solve(dense_from_bsr(rowptr, col, val), -res)
+    assert np.linalg.norm(y1 - y0) <= 1e-9 * np.linalg.norm(y0)
+    np.testing.assert_array_equal(dval[rowptr[nc]:], val[rowptr[nc]:])
+    np.testing.assert_array_equal(rhs[2 * nc:], -res[2 * nc:])
+
+
+def test_abf_makes_diagonal_blocks_identity():
+    """ABF: D_i is the diagonal block itself, so every decoupled diagonal
+    block is the identity up to rounding, i.e. within a small multiple of
+    the componentwise bound |A_ii^-1| |A_ii| (the block's columns differ in
+    scale by many orders in SI units, so the error is not small absolutely)."""
+    prob, rowptr, col, val, res, dval, rhs = _decoupled(1)
+    for i in range(prob.n_cells):
+        e = rowptr[i] + list(col[rowptr[i]:rowptr[i + 1]]).index(i)
+        bound = 1e-13 * (np.abs(np.linalg.inv(val[e])) @ np.abs(val[e]))
+        assert np.all(np.abs(dval[e] - np.eye(2)) <= bound), (i, dval[e])
+
+
+def test_true_impes_weight_cancels_the_saturation_column_sum():
+    """True-IMPES: the weight w_i of cell i's pressure row makes the
+    saturation coefficients of (oil - w_i water) in block column i sum to
+    zero over all rows.  w_i is read back from the decoupled diagonal block
+    (its (0,0) entry is a00 - w_i a10) and checked on the original J."""
+    prob, rowptr, col, val, res, dval, rhs = _decoupled(2)
+    nc = prob.n_cells
+    A = dense_from_bsr(rowptr, col, val)
+    checked = 0
+    for i in range(nc):
+        e = rowptr[i] + list(col[rowptr[i]:rowptr[i + 1]]).index(i)
+        a00, a10 = val[e, 0, 0], val[e, 1, 0]
+        if abs(a10) < 1e-8 * abs(a00):
+            continue
+        w = (a00 - dval[e, 0, 0]) / a10
+        c01 = sum(A[2 * k, 2 * i + 1] for k in range(len(rowptr) - 1))
+        c11 = sum(A[2 * k + 1, 2 * i + 1] for k in range(len(rowptr) - 1))
+        assert abs(c01 - w * c11) <= 1e-6 * (abs(c01) + abs(w * c11))
+        checked += 1
+    assert checked > nc // 2
+
+
 # ------------------------------------------------------------------- Jacobian
 
 @pytest.mark.parametrize("g", [0.0, 9.80665])
