@@ -193,6 +193,14 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     dts = [p.dt for p in members]
 
+    tuned = 0
+    if args.autotune:
+        for s, (p, sw, b) in zip(sims, x0):
+            s.set_state_device(p, sw, b)
+        dpsim.advance_many(sims, dts, threads=args.threads)
+        for s in sims:
+            tuned += sum(1 for l in s.autotune(10).splitlines() if "->" in l)
+
     def step(threads):
         for s, (p, sw, b) in zip(sims, x0):
             s.set_state_device(p, sw, b)
@@ -235,6 +243,7 @@ def run_ensemble(args):
             "one_at_a_time": {"value": 64 * args.steps / one["sec"], "unit": "realisation timesteps/s",
                               "ms_per_step": 1000 * one["sec"] / args.steps,
                               "newton_solves_per_s": one["solves"] / one["sec"]},
+            "autotune_decisions": tuned if args.autotune else None,
             "gpu_launches": many["launches"], "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     for s in sims:
@@ -341,6 +350,9 @@ def main():
                     help="0: the paper's modified Gauss-Jordan step; 1: ABF; 2: True-IMPES")
     ap.add_argument("--eta-mode", type=int, default=2,
                     help="forcing term of Algorithm 1: 1, 2 or 3 (Section 3.1), 0: fixed")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the AMG level kernels' launch shapes after the first warm-up "
+                         "timestep and keep the fastest (sim_autotune)")
     ap.add_argument("--threads", type=int, default=16,
                     help="ensemble mode: host threads driving realisations concurrently")
     ap.add_argument("--mode", default="bench", choices=["bench", "newton2", "ensemble", "serve"],
@@ -442,6 +454,14 @@ def main():
                 "median": solve_ms[len(solve_ms) // 2] if solve_ms else None,
                 "p90": solve_ms[min(len(solve_ms) - 1, int(0.9 * len(solve_ms)))] if solve_ms else None}
 
+    tuned = None
+    if args.autotune:
+        timestep(sim, opts)
+        rep = sim.autotune(20)
+        lines = [l for l in rep.splitlines() if "->" in l]
+        tuned = {"decisions": len(lines),
+                 "changed": sum(1 for l in lines if l.split("lanes ")[1].split(" ->")[0]
+                                != l.split("-> ")[1].split(" ")[0])}
     clk = Clocks(local)
     main = measure(sim, opts, args.steps, args.warmup, clk)
     ms, n_solves, n_its, launches = main["ms"], main["solves"], main["its"], main["launches"]
@@ -540,6 +560,7 @@ def main():
                     "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state},
             "fp64_path": fp64,
             "gpu_launches": launches,
+            "autotune": tuned,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -216,6 +216,19 @@ int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t t
 int dp_stream_create(void **stream);
 int dp_stream_destroy(void *stream);
 
+/* Autotuning of launch shapes (no counterpart in the paper): for every AMG
+ * level, times each lanes-per-row variant (1..32) of the kernel of its
+ * smoother's level operator, of the prolongation and of the restriction,
+ * `reps` launches each with CUDA events on the simulation stream, on the
+ * level's own work vectors, and keeps the fastest; the Arnoldi steps' CUDA
+ * graphs are captured again on the next solve.  Colourings, aggregates and
+ * operators do not change, but the summation order of those kernels does,
+ * so results differ from the untuned schedule at rounding level (and a
+ * schedule picked by timing can differ between runs).  Needs the AMG
+ * hierarchy: call after one sim_solve_step or sim_advance with precond 2.
+ * `report` (may be NULL) receives one text line per decision. */
+int sim_autotune(dp_sim *sim, int32_t reps, char *report, int32_t report_len);
+
 /* Device bytes the realisation holds through its allocator now, and the
  * most it has held at once (both may be NULL).  Host only, no CUDA call. */
 int sim_footprint(dp_sim *s, uint64_t *current, uint64_t *peak);

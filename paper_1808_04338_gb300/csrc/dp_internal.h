@@ -162,6 +162,7 @@ int mixed_refresh(Sim *s, bool coarse);
 int l0_refresh(Sim *s);
 int lanes_for(double mean_len);
 void graphs_free(Sim *s);
+int autotune(Sim *s, int reps, std::string &report);
 
 // dp_cycle.cu (the coarse levels of the V-cycle in one cluster launch)
 constexpr int kClusterMaxRows = 20000;   // default of dp_options.cluster_rows

@@ -2,6 +2,8 @@
 // ILU(0) in colour order, the AMG V-cycle with multicolour Gauss-Seidel, the
 // dense coarsest solve, the CPR-FPF preconditioner and flexible GMRES.
 #include <algorithm>
+#include <cstdio>
+#include <string>
 #include <cmath>
 #include <cstring>
 
@@ -1174,6 +1176,100 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x) {
 }
 
 int vcycle(Sim *s, int l, const double *b, double *x) { return vcycle_t<double>(s, l, b, x); }
+
+// ---------------------------------------------------------------- autotuning
+// Lanes per row of the AMG level kernels, chosen by timing: for every level,
+// the level-operator kernel of its smoother (l1-Jacobi sweep, else the
+// residual, which shares the Gauss-Seidel colour kernels' lane count), the
+// prolongation and the restriction, each launched `reps` times per candidate
+// with CUDA events on the simulation stream on the level's own work vectors.
+// Colourings, aggregates and operators are not touched.
+template <typename F>
+static int time_launches(Sim *s, int reps, F launch, float *ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  DP_CUDA(s, cudaEventCreate(&a));
+  DP_CUDA(s, cudaEventCreate(&b));
+  int rc = launch();   // warm-up
+  if (rc == DP_OK) {
+    cudaEventRecord(a, s->stream);
+    for (int k = 0; k < reps && rc == DP_OK; ++k) rc = launch();
+    cudaEventRecord(b, s->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) rc = DP_ECUDA;
+    else cudaEventElapsedTime(ms, a, b);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc == DP_ECUDA) s->fail(DP_ECUDA, "autotune timing");
+  return rc;
+}
+
+template <typename T>
+static int tune_level(Sim *s, int l, int reps, std::string &rep) {
+  static const int cand[] = {1, 2, 4, 8, 16, 32};
+  Level &L = s->lev[l];
+  bool last = l + 1 == (int)s->lev.size();
+  if (L.n == 0) return DP_OK;
+  T *x = LV<T>::x(L), *b = LV<T>::b(L), *r = LV<T>::r(L);
+  auto pick = [&](const char *what, int &field, auto launch_g) -> int {
+    int old = field, best = old;
+    float best_ms = 1e30f;
+    char buf[160];
+    std::string line;
+    for (int g : cand) {
+      float ms = 0.f;
+      auto one = [&]() { return launch_g(g); };
+      DP_TRY(time_launches(s, reps, one, &ms));
+      std::snprintf(buf, sizeof buf, " %d:%.1f", g, 1000.f * ms / reps);
+      line += buf;
+      if (ms < best_ms) { best_ms = ms; best = g; }
+    }
+    field = best;
+    std::snprintf(buf, sizeof buf, "level %d %s lanes %d -> %d (us per launch:%s)\n", l, what, old,
+                  best, line.c_str());
+    rep += buf;
+    return DP_OK;
+  };
+  // level operator
+  auto op = [&](int g) -> int {
+    long long thr = (long long)L.n * g;
+    if (L.l1) {
+      DP_SWITCH_G(g, DP_LAUNCH(s, (k_jacobi_sweep<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
+                               L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
+    } else {
+      DP_SWITCH_G(g, DP_LAUNCH(s, (k_csr_resid<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
+                               L.col, LV<T>::val(L), b, x, r));
+    }
+    return DP_OK;
+  };
+  DP_TRY(pick(L.l1 ? "l1-Jacobi sweep" : "residual", L.G, op));
+  if (last) return DP_OK;
+  Level &N = s->lev[l + 1];
+  T *nx = LV<T>::x(N), *nb = LV<T>::b(N);
+  auto prol = [&](int g) -> int {
+    return csr_mv<T>(s, L.n, g, L.p_rowptr, L.p_col, LV<T>::pval(L), nx, r, 0);
+  };
+  auto restr = [&](int g) -> int {
+    return csr_mv<T>(s, N.n, g, L.r_rowptr, L.r_col, LV<T>::rval(L), r, nb, 0);
+  };
+  DP_TRY(pick("prolongation", L.p_G, prol));
+  DP_TRY(pick("restriction", L.r_G, restr));
+  return DP_OK;
+}
+
+int autotune(Sim *s, int reps, std::string &rep) {
+  if (!s->amg_ready || s->opt.precond != 2) {
+    s->fail(DP_EINVAL, "autotune needs the AMG hierarchy (one CPR-FPF solve first)");
+    return DP_EINVAL;
+  }
+  reps = std::max(1, std::min(reps, 1000));
+  for (int l = 0; l < (int)s->lev.size(); ++l) {
+    if (s->opt.precision == 1) DP_TRY(tune_level<float>(s, l, reps, rep));
+    else DP_TRY(tune_level<double>(s, l, reps, rep));
+  }
+  DP_CUDA(s, cudaStreamSynchronize(s->stream));
+  graphs_free(s);   // the Arnoldi steps are captured again with the new launch shapes
+  return DP_OK;
+}
 
 // ---------------------------------------------------------------- CPR-FPF
 // z1 = F r;  z2 = z1 + P V(R (r - A z1));  z = z2 + F (r - A z2)

@@ -419,6 +419,18 @@ extern "C" int dp_stream_destroy(void *stream) {
   return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? DP_OK : DP_ECUDA;
 }
 
+extern "C" int sim_autotune(dp_sim *s, int32_t reps, char *report, int32_t report_len) {
+  if (!s || reps < 1 || (report && report_len < 1)) return DP_EINVAL;
+  std::string rep;
+  DP_TRY(autotune(s, reps, rep));
+  if (report) {
+    size_t n = std::min(rep.size(), (size_t)report_len - 1);
+    std::memcpy(report, rep.data(), n);
+    report[n] = 0;
+  }
+  return DP_OK;
+}
+
 extern "C" int sim_footprint(dp_sim *s, uint64_t *current, uint64_t *peak) {
   if (!s) return DP_EINVAL;
   if (current) *current = s->cur_bytes;

@@ -141,6 +141,7 @@ def load():
     L.sim_last_error.restype = C.c_char_p
     L.sim_advance_many.argtypes = [P, I, P, I, P, P]
     L.sim_footprint.argtypes = [P, P, P]
+    L.sim_autotune.argtypes = [P, I, C.c_char_p, I]
     L.dp_stream_create.argtypes = [P]
     L.dp_stream_destroy.argtypes = [P]
     L.srv_create.argtypes = [I, C.c_uint64, P, P]
@@ -462,6 +463,13 @@ class Sim:
         c = np.zeros(self.nb, np.int32)
         n = self._check(load().sim_get_colours(self.h, _p(c)), "sim_get_colours")
         return c, n
+
+    def autotune(self, reps: int = 20) -> str:
+        """Time the AMG level kernels' launch shapes and keep the fastest;
+        returns the decisions as text."""
+        buf = C.create_string_buffer(16384)
+        self._check(load().sim_autotune(self.h, int(reps), buf, len(buf)), "sim_autotune")
+        return buf.value.decode()
 
     def footprint(self):
         cur, peak = C.c_uint64(), C.c_uint64()

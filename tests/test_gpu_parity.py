@@ -285,3 +285,19 @@ def test_mixed_precision_layered_timestep():
     assert rcg == rco == 0
     state_close(g, o, prob)
     assert stg.linear_iters <= 2 * sto.linear_iters
+
+
+def test_autotune_keeps_parity():
+    """The autotuner changes launch shapes only: after it, the next timestep
+    still matches the oracle; before any hierarchy exists it refuses."""
+    prob = di.layered()
+    g, o = pair(prob, "parity", newton_tol=1e-9)   # the second step stalls near 1e-10 on both sides
+    with pytest.raises(RuntimeError):
+        g.autotune(2)
+    assert g.advance(prob.dt)[0] == 0 and o.advance(prob.dt)[0] == 0
+    rep = g.autotune(3)
+    assert "level 0" in rep and "prolongation" in rep and "restriction" in rep
+    rcg, _ = g.advance(di.DAY)
+    rco, _ = o.advance(di.DAY)
+    assert rcg == 0 and rco == 0
+    state_close(g, o, prob)
