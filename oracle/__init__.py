@@ -64,7 +64,7 @@ class og_options(C.Structure):
                 ("amg_coarse_max", C.c_int32), ("amg_max_levels", C.c_int32),
                 ("precond", C.c_int32), ("ds_max", C.c_double),
                 ("amg_gs_levels", C.c_int32), ("amg_refresh", C.c_int32),
-                ("decouple", C.c_int32)]
+                ("decouple", C.c_int32), ("schur", C.c_int32)]
 
 
 class og_stats(C.Structure):
@@ -119,6 +119,7 @@ def lib():
         for name in ("oracle_set_state", "oracle_set_iterate", "oracle_get_state"):
             getattr(L, name).argtypes = [P, P, P, P]
         L.oracle_sizes.argtypes = [P, P, P]
+        L.oracle_solver_sizes.argtypes = [P, P, P]
         L.oracle_assemble.argtypes = [P, D]
         L.oracle_get_jacobian.argtypes = [P, P, P, P, P]
         L.oracle_get_norms.argtypes = [P, P]
@@ -185,6 +186,8 @@ class OracleSim:
         nb, nnz = C.c_int32(), C.c_int32()
         L.oracle_sizes(h, C.byref(nb), C.byref(nnz))
         self.nb, self.nnzb = nb.value, nnz.value
+        L.oracle_solver_sizes(h, C.byref(nb), C.byref(nnz))
+        self.snb, self.snnzb = nb.value, nnz.value      # the system the solver sees
         self.nc = prob.n_cells
         self.nw = nw
         self.set_state(prob.p0, prob.sw0, prob.bhp0)
@@ -239,12 +242,12 @@ class OracleSim:
         return y
 
     def decoupled(self):
-        val = np.zeros((self.nnzb, 2, 2)); rhs = np.zeros(2 * self.nb)
+        val = np.zeros((self.snnzb, 2, 2)); rhs = np.zeros(2 * self.snb)
         lib().oracle_get_decoupled(self.h, _p(val), _p(rhs))
         return val, rhs
 
     def colours(self):
-        c = np.zeros(self.nb, np.int32)
+        c = np.zeros(self.snb, np.int32)
         ncol = lib().oracle_get_colours(self.h, _p(c))
         return c, ncol
 

@@ -992,7 +992,13 @@ typedef struct {
   double *kf, *km, *phi_f, *phi_m;
   int nwells; og_well *wells;
   int nL, nc, nb;
-  og_bsr J;          /* Jacobian, natural order; decoupled in place by solve */
+  og_bsr J;          /* Jacobian, natural order; decoupled in place by solve (full system) */
+  og_bsr K;          /* with schur: the fracture-and-well system, decoupled in place */
+  double *RK;        /* with schur: its residual [2 (nL + nwells)] */
+  double *yk;        /* with schur: its update */
+  int *kmap;         /* with schur: entry of J each entry of K copies (-1: S_ff) */
+  int *pos_fm, *pos_mf; /* with schur: blocks (f, m) and (m, f) of each location */
+  double *Minv;      /* with schur: inverted (m, m) block of each location */
   double *R;         /* residual [2 nb] */
   double *p, *sw, *bhp, *pn, *swn, *bhpn;
   double *Mn;        /* accumulation at the old time level [2 nc] */
@@ -1292,6 +1298,121 @@ static void save_old(og_sim *s) {
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* Exact elimination of the matrix continuum (schur = 1).  A matrix cell m
+ * of location loc couples only to itself and its fracture cell f (Section 2:
+ * the matrix exchanges fluid with its own fracture only), so from
+ *   A_mm y_m + A_mf y_f = -R_m
+ * y_m = A_mm^-1 (-R_m - A_mf y_f), and the fracture row becomes
+ *   (A_ff - A_fm A_mm^-1 A_mf) y_f + sum_j A_fj y_j = -(R_f - A_fm A_mm^-1 R_m).
+ * The fracture-and-well system K keeps the fracture rows (row loc) and the
+ * well rows (row nL + w); its blocks are those of J except the fracture
+ * diagonal blocks, which take S_ff. */
+
+static const og_bsr *solver_op(const og_sim *s) { return s->o.schur ? &s->K : &s->J; }
+
+static int kcol(const og_sim *s, int c) {        /* column of J -> column of K, -1: dropped */
+  if (c >= s->nc) return s->nL + (c - s->nc);
+  return (c & 1) ? -1 : c >> 1;
+}
+
+static void schur_pattern(og_sim *s) {
+  og_bsr *J = &s->J, *K = &s->K;
+  int nk = s->nL + s->nwells;
+  K->n = nk;
+  K->rowptr = (int *)zalloc((size_t)nk + 1, sizeof(int));
+  int cnt = 0;
+  for (int r = 0; r < nk; ++r) {
+    int jr = r < s->nL ? 2 * r : s->nc + (r - s->nL);
+    K->rowptr[r] = cnt;
+    for (int e = J->rowptr[jr]; e < J->rowptr[jr + 1]; ++e) if (kcol(s, J->col[e]) >= 0) ++cnt;
+  }
+  K->rowptr[nk] = cnt;
+  K->nnz = cnt;
+  K->col = (int *)zalloc((size_t)cnt, sizeof(int));
+  K->diag = (int *)zalloc((size_t)nk, sizeof(int));
+  K->val = (double *)zalloc(4 * (size_t)cnt, sizeof(double));
+  s->kmap = (int *)zalloc((size_t)cnt, sizeof(int));
+  for (int r = 0; r < nk; ++r) {
+    int jr = r < s->nL ? 2 * r : s->nc + (r - s->nL), k = K->rowptr[r];
+    for (int e = J->rowptr[jr]; e < J->rowptr[jr + 1]; ++e) {
+      int c = kcol(s, J->col[e]);
+      if (c < 0) continue;
+      K->col[k] = c;
+      s->kmap[k] = (r < s->nL && c == r) ? -1 : e;
+      if (c == r) K->diag[r] = k;
+      ++k;
+    }
+  }
+  s->pos_fm = (int *)zalloc((size_t)s->nL, sizeof(int));
+  s->pos_mf = (int *)zalloc((size_t)s->nL, sizeof(int));
+  for (int loc = 0; loc < s->nL; ++loc) {
+    int f = 2 * loc, m = f + 1;
+    s->pos_fm[loc] = find_col(J->col, J->rowptr[f], J->rowptr[f + 1], m);
+    s->pos_mf[loc] = find_col(J->col, J->rowptr[m], J->rowptr[m + 1], f);
+  }
+  s->Minv = (double *)zalloc(4 * (size_t)s->nL, sizeof(double));
+  s->RK = (double *)zalloc(2 * (size_t)nk, sizeof(double));
+  s->yk = (double *)zalloc(2 * (size_t)nk, sizeof(double));
+}
+
+static void schur_reduce(og_sim *s) {
+  og_bsr *J = &s->J, *K = &s->K;
+  for (int k = 0; k < K->nnz; ++k)
+    if (s->kmap[k] >= 0) memcpy(K->val + 4 * (size_t)k, J->val + 4 * (size_t)s->kmap[k], 32);
+  for (int w = 0; w < s->nwells; ++w) {
+    s->RK[2 * (s->nL + w)] = s->R[2 * (s->nc + w)];
+    s->RK[2 * (s->nL + w) + 1] = s->R[2 * (s->nc + w) + 1];
+  }
+  for (int loc = 0; loc < s->nL; ++loc) {
+    int f = 2 * loc, m = f + 1;
+    const double *amm = J->val + 4 * (size_t)J->diag[m];
+    const double *amf = J->val + 4 * (size_t)s->pos_mf[loc];
+    const double *afm = J->val + 4 * (size_t)s->pos_fm[loc];
+    const double *aff = J->val + 4 * (size_t)J->diag[f];
+    double det = (amm[0] * amm[3]) - (amm[1] * amm[2]);
+    double *mi = s->Minv + 4 * (size_t)loc;
+    if (fabs(det) < 1e-300) { mi[0] = 0.0; mi[1] = 0.0; mi[2] = 0.0; mi[3] = 0.0; }
+    else {
+      mi[0] = amm[3] / det; mi[1] = (-amm[1]) / det;
+      mi[2] = (-amm[2]) / det; mi[3] = amm[0] / det;
+    }
+    double x00 = (afm[0] * mi[0]) + (afm[1] * mi[2]);
+    double x01 = (afm[0] * mi[1]) + (afm[1] * mi[3]);
+    double x10 = (afm[2] * mi[0]) + (afm[3] * mi[2]);
+    double x11 = (afm[2] * mi[1]) + (afm[3] * mi[3]);
+    double *sk = K->val + 4 * (size_t)K->diag[loc];
+    sk[0] = aff[0] - ((x00 * amf[0]) + (x01 * amf[2]));
+    sk[1] = aff[1] - ((x00 * amf[1]) + (x01 * amf[3]));
+    sk[2] = aff[2] - ((x10 * amf[0]) + (x11 * amf[2]));
+    sk[3] = aff[3] - ((x10 * amf[1]) + (x11 * amf[3]));
+    double rm0 = s->R[2 * m], rm1 = s->R[2 * m + 1];
+    s->RK[2 * loc] = s->R[2 * f] - ((x00 * rm0) + (x01 * rm1));
+    s->RK[2 * loc + 1] = s->R[2 * f + 1] - ((x10 * rm0) + (x11 * rm1));
+  }
+}
+
+/* y of the full system from the fracture-and-well update yk. */
+static void schur_back(og_sim *s) {
+  const og_bsr *J = &s->J;
+  for (int w = 0; w < s->nwells; ++w) {
+    s->y[2 * (s->nc + w)] = s->yk[2 * (s->nL + w)];
+    s->y[2 * (s->nc + w) + 1] = s->yk[2 * (s->nL + w) + 1];
+  }
+  for (int loc = 0; loc < s->nL; ++loc) {
+    int f = 2 * loc, m = f + 1;
+    double yf0 = s->yk[2 * loc], yf1 = s->yk[2 * loc + 1];
+    const double *amf = J->val + 4 * (size_t)s->pos_mf[loc];
+    const double *mi = s->Minv + 4 * (size_t)loc;
+    double t0 = (-s->R[2 * m]) - ((amf[0] * yf0) + (amf[1] * yf1));
+    double t1 = (-s->R[2 * m + 1]) - ((amf[2] * yf0) + (amf[3] * yf1));
+    s->y[2 * f] = yf0;
+    s->y[2 * f + 1] = yf1;
+    s->y[2 * m] = (mi[0] * t0) + (mi[1] * t1);
+    s->y[2 * m + 1] = (mi[2] * t0) + (mi[3] * t1);
+  }
+}
+
 int oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
                   const og_well *w, int32_t nwells, const og_options *o, void **out) {
   if (!g || !r || !f || !o || !out || g->nx < 1 || g->ny < 1 || g->nz < 1 || nwells < 0)
@@ -1384,12 +1505,14 @@ int oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
   s->Mn = (double *)zalloc(2 * (size_t)s->nc, sizeof(double));
   s->y = (double *)zalloc(2 * (size_t)s->nb, sizeof(double));
   s->bh = (double *)zalloc(2 * (size_t)s->nb, sizeof(double));
-  s->colour = (int *)zalloc((size_t)s->nb, sizeof(int));
-  s->ncolour = greedy_colour(s->nb, J->rowptr, J->col, s->colour);
-  ilu_setup(&s->ilu, J, s->colour);
-  s->Ap.n = s->nb; s->Ap.ncol = s->nb; s->Ap.nnz = J->nnz;
-  s->Ap.rowptr = J->rowptr; s->Ap.col = J->col;
-  s->Ap.val = (double *)zalloc((size_t)J->nnz, sizeof(double));
+  if (o->schur) schur_pattern(s);
+  const og_bsr *A = solver_op(s);
+  s->colour = (int *)zalloc((size_t)A->n, sizeof(int));
+  s->ncolour = greedy_colour(A->n, A->rowptr, A->col, s->colour);
+  ilu_setup(&s->ilu, A, s->colour);
+  s->Ap.n = A->n; s->Ap.ncol = A->n; s->Ap.nnz = A->nnz;
+  s->Ap.rowptr = A->rowptr; s->Ap.col = A->col;
+  s->Ap.val = (double *)zalloc((size_t)A->nnz, sizeof(double));
   s->amg.theta = o->amg_theta; s->amg.coarse_max = o->amg_coarse_max;
   s->amg.smoother = o->amg_gs_levels;
   s->amg.max_levels = o->amg_max_levels > 30 ? 30 : o->amg_max_levels;
@@ -1405,6 +1528,10 @@ void oracle_destroy(void *h) {
   free(s->J.rowptr); free(s->J.col); free(s->J.diag); free(s->J.val);
   free(s->R); free(s->p); free(s->sw); free(s->bhp); free(s->pn); free(s->swn); free(s->bhpn);
   free(s->Mn); free(s->y); free(s->bh); free(s->colour); free(s->Ap.val);
+  if (s->o.schur) {
+    free(s->K.rowptr); free(s->K.col); free(s->K.diag); free(s->K.val);
+    free(s->RK); free(s->yk); free(s->kmap); free(s->pos_fm); free(s->pos_mf); free(s->Minv);
+  }
   ilu_free(&s->ilu);
   amg_free(&s->amg);
   free(s);
@@ -1413,6 +1540,13 @@ void oracle_destroy(void *h) {
 int oracle_sizes(void *h, int32_t *nb, int32_t *nnzb) {
   og_sim *s = (og_sim *)h;
   *nb = s->nb; *nnzb = s->J.nnz;
+  return 0;
+}
+
+int oracle_solver_sizes(void *h, int32_t *nb, int32_t *nnzb) {
+  og_sim *s = (og_sim *)h;
+  const og_bsr *A = solver_op(s);
+  *nb = A->n; *nnzb = A->nnz;
   return 0;
 }
 
@@ -1485,28 +1619,30 @@ int oracle_well_index(void *h, double *wi) {
  * w_i = c01/c11 from the sums of block column i over all rows (taken before
  * any row changes, rows in increasing order). */
 static void decouple(og_sim *s) {
-  og_bsr *J = &s->J;
+  og_bsr *J = s->o.schur ? &s->K : &s->J;              /* the system the solver sees */
+  const double *R = s->o.schur ? s->RK : s->R;
+  int nb = J->n, ncell = s->o.schur ? s->nL : s->nc;    /* rows below ncell are cell rows */
   int mode = s->o.decouple;
   double *w = NULL;
   if (mode == 2) {
-    double *c01 = (double *)zalloc((size_t)s->nc, sizeof(double));
-    double *c11 = (double *)zalloc((size_t)s->nc, sizeof(double));
-    for (int k = 0; k < s->nb; ++k)
+    double *c01 = (double *)zalloc((size_t)ncell, sizeof(double));
+    double *c11 = (double *)zalloc((size_t)ncell, sizeof(double));
+    for (int k = 0; k < nb; ++k)
       for (int e = J->rowptr[k]; e < J->rowptr[k + 1]; ++e) {
         int j = J->col[e];
-        if (j >= s->nc) continue;
+        if (j >= ncell) continue;
         const double *a = J->val + 4 * (size_t)e;
         c01[j] = c01[j] + a[1];
         c11[j] = c11[j] + a[3];
       }
-    w = (double *)zalloc((size_t)s->nc, sizeof(double));
-    for (int j = 0; j < s->nc; ++j) w[j] = fabs(c11[j]) < 1e-300 ? 0.0 : c01[j] / c11[j];
+    w = (double *)zalloc((size_t)ncell, sizeof(double));
+    for (int j = 0; j < ncell; ++j) w[j] = fabs(c11[j]) < 1e-300 ? 0.0 : c01[j] / c11[j];
     free(c01);
     free(c11);
   }
-  for (int i = 0; i < s->nb; ++i) {
-    double b0 = -s->R[2 * i], b1 = -s->R[2 * i + 1];
-    if (i >= s->nc) { s->bh[2 * i] = b0; s->bh[2 * i + 1] = b1; continue; }
+  for (int i = 0; i < nb; ++i) {
+    double b0 = -R[2 * i], b1 = -R[2 * i + 1];
+    if (i >= ncell) { s->bh[2 * i] = b0; s->bh[2 * i + 1] = b1; continue; }
     const double *dg = J->val + 4 * (size_t)J->diag[i];
     if (mode == 1) {
       double d00 = dg[0], d01 = dg[1], d10 = dg[2], d11 = dg[3];
@@ -1544,14 +1680,15 @@ static void decouple(og_sim *s) {
 
 int oracle_get_decoupled(void *h, double *val, double *rhs) {
   og_sim *s = (og_sim *)h;
-  if (val) memcpy(val, s->J.val, sizeof(double) * 4 * (size_t)s->J.nnz);
-  if (rhs) memcpy(rhs, s->bh, sizeof(double) * 2 * (size_t)s->nb);
+  const og_bsr *A = solver_op(s);
+  if (val) memcpy(val, A->val, sizeof(double) * 4 * (size_t)A->nnz);
+  if (rhs) memcpy(rhs, s->bh, sizeof(double) * 2 * (size_t)A->n);
   return 0;
 }
 
 int oracle_get_colours(void *h, int32_t *colour) {
   og_sim *s = (og_sim *)h;
-  memcpy(colour, s->colour, sizeof(int) * (size_t)s->nb);
+  memcpy(colour, s->colour, sizeof(int) * (size_t)solver_op(s)->n);
   return s->ncolour;
 }
 
@@ -1590,24 +1727,28 @@ static double forcing(og_sim *s, double res) {
 int oracle_solve_step(void *h, og_stats *st) {
   og_sim *s = (og_sim *)h;
   double eta = forcing(s, s->norms[0]);
+  if (s->o.schur) schur_reduce(s);
+  og_bsr *A = s->o.schur ? &s->K : &s->J;
   decouple(s);
-  for (int e = 0; e < s->J.nnz; ++e) s->Ap.val[e] = s->J.val[4 * (size_t)e];
-  if (s->o.precond >= 1) ilu_factor(&s->ilu, &s->J);
+  for (int e = 0; e < A->nnz; ++e) s->Ap.val[e] = A->val[4 * (size_t)e];
+  if (s->o.precond >= 1) ilu_factor(&s->ilu, A);
   if (s->o.precond == 2) {
     if (!s->amg_ready) { amg_setup(&s->amg, &s->Ap); s->amg_ready = 1; }
     else amg_refresh(&s->amg, s->Ap.val, s->o.amg_refresh == 0 || s->newton_iter == 0);
   }
   og_cpr c; memset(&c, 0, sizeof(c));
-  c.A = &s->J; c.ilu = &s->ilu; c.amg = &s->amg; c.mode = s->o.precond;
-  int n2 = 2 * s->nb;
+  c.A = A; c.ilu = &s->ilu; c.amg = &s->amg; c.mode = s->o.precond;
+  int n2 = 2 * A->n;
   c.r1 = (double *)zalloc((size_t)n2, sizeof(double));
   c.z1 = (double *)zalloc((size_t)n2, sizeof(double));
-  c.rp = (double *)zalloc((size_t)s->nb, sizeof(double));
-  c.xp = (double *)zalloc((size_t)s->nb, sizeof(double));
+  c.rp = (double *)zalloc((size_t)A->n, sizeof(double));
+  c.xp = (double *)zalloc((size_t)A->n, sizeof(double));
   int it = 0; double rr = 0.0;
-  int rc = fgmres(n2, op_bsr, &s->J, s->o.precond ? op_cpr : NULL, &c, s->bh, s->y,
+  double *ys = s->o.schur ? s->yk : s->y;
+  int rc = fgmres(n2, op_bsr, A, s->o.precond ? op_cpr : NULL, &c, s->bh, ys,
                   s->o.gmres_restart, s->o.gmres_maxit, eta, &it, &rr);
   free(c.r1); free(c.z1); free(c.rp); free(c.xp);
+  if (s->o.schur) schur_back(s);
   for (int cc = 0; cc < s->nc; ++cc) {
     s->p[cc] += s->y[2 * cc];
     double ds = s->y[2 * cc + 1];

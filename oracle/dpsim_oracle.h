@@ -51,6 +51,9 @@ typedef struct {
                              with the diagonal block; the Quasi-IMPES form);
                              1: ABF, the inverse of the diagonal block; 2: True-
                              IMPES, weights from the block-column sums */
+  int32_t schur;          /* 1: eliminate every matrix cell exactly (its 2x2 block
+                             couples only to its own fracture cell) and solve the
+                             fracture-and-well system; 0: the full system */
 } og_options;
 typedef struct {
   int32_t newton_iters, linear_iters, converged, amg_levels;
@@ -62,6 +65,9 @@ int  oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
                    void **out);
 void oracle_destroy(void *h);
 int  oracle_sizes(void *h, int32_t *nb, int32_t *nnzb);
+/* block rows and blocks of the system the linear solver sees (the full one,
+ * or the fracture-and-well one with schur = 1) */
+int  oracle_solver_sizes(void *h, int32_t *nb, int32_t *nnzb);
 int  oracle_set_state(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_set_iterate(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_get_state(void *h, double *p, double *sw, double *bhp);

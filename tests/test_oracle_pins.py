@@ -46,14 +46,20 @@ def random_interior_state(prob, seed=3):
 
 # ---------------------------------------------------------------- linear solve
 
-@pytest.mark.parametrize("make", [lambda: small_problem(3, 3, 2), di.tiny])
-def test_cpr_fgmres_matches_dense_lu(make):
+@pytest.mark.parametrize("make,schur", [(lambda: small_problem(3, 3, 2), 0), (di.tiny, 0),
+                                        (lambda: small_problem(3, 3, 2), 1), (di.tiny, 1)])
+def test_cpr_fgmres_matches_dense_lu(make, schur):
     """The FGMRES/CPR-FPF Newton update solves J y = -R (Algorithm 1, step 5,
     eta = 1e-12): its true residual, formed with a dense copy of J, is at the
     tolerance, and it equals the dense LU solution to the accuracy that the
-    conditioning of J (about 1e12 in SI units) allows."""
+    conditioning of J (about 1e12 in SI units) allows.  With schur = 1 the
+    solver sees only the fracture and well rows (the matrix cells eliminated
+    exactly) and the matrix part of y comes from back-substitution: the
+    update must still be the dense solution of the full system."""
     prob = make()
-    s = O.OracleSim(prob, O.options("parity", eta_fixed=1e-12))
+    s = O.OracleSim(prob, O.options("parity", eta_fixed=1e-12, schur=schur))
+    if schur:
+        assert s.snb == prob.n_cells // 2 + prob.n_wells
     p, sw, bhp = random_interior_state(prob)
     s.set_iterate(p, sw, bhp)
     s.assemble(prob.dt)
