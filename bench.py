@@ -184,7 +184,7 @@ def run_ensemble(args):
     import dp_inputs as di
     from paper_1808_04338_gb300 import dpsim
     members = [di.ensemble_member(r) for r in range(64)]
-    opts = dpsim.options("report", precision=args.precision)
+    opts = dpsim.options("report", precision=args.precision, schur=args.schur)
     sims, x0, streams = [], [], []
     for prob in members:
         streams.append(dpsim.OwnedStream())
@@ -237,7 +237,8 @@ def run_ensemble(args):
             "higher_is_better": True, "dtype": "f64" if args.precision == 0 else "f64 (f32 preconditioner)",
             "data": "synthetic",
             "config": {"workload": f"64 realisations, 20x20x5 to 80x80x20 locations, {cells} cells",
-                       "threads": args.threads, "precision": args.precision},
+                       "threads": args.threads, "precision": args.precision,
+                       "schur": args.schur},
             "newton_solves_per_s": many["solves"] / many["sec"],
             "fgmres_iters_per_solve": many["its"] / max(many["solves"], 1),
             "one_at_a_time": {"value": 64 * args.steps / one["sec"], "unit": "realisation timesteps/s",
@@ -269,7 +270,8 @@ def run_serve(args):
     budget = 160 << 30
 
     def once(workers, precision):
-        srv = dpsim.Server(workers, budget, dpsim.options("report", precision=precision))
+        srv = dpsim.Server(workers, budget, dpsim.options("report", precision=precision,
+                                                          schur=args.schur))
         ids = [srv.add(p) for p in members]
         for t in [srv.submit(ids[r], di.DAY) for r in sorted(set(real.tolist()))]:
             if srv.wait(t).status != 0:
@@ -309,7 +311,8 @@ def run_serve(args):
             "data": "synthetic",
             "config": {"workload": f"512 requests, Poisson 200/s, 128 realisations "
                                    f"({cells} cells), dt 1-10 days, budget 160 GB",
-                       "workers": args.threads, "precision": args.precision},
+                       "workers": args.threads, "precision": args.precision,
+                       "schur": args.schur},
             "served": served,
             "plain_fp64_one_worker": plain,
             "gpu_launches": served["launches"], "clocks": clk.summary()}
@@ -322,7 +325,7 @@ def config_dict(args, nnzb=None):
                         f"{4 * args.nx * args.ny * args.nz + 50} unknowns, 25 wells, "
                         f"lognormal perm (sd 2), first 5-day Newton step",
             "grid": [args.nx, args.ny, args.nz], "precision": args.precision,
-            "decouple": args.decouple, "eta_mode": args.eta_mode,
+            "decouple": args.decouple, "eta_mode": args.eta_mode, "schur": args.schur,
             "precond": "CPR-FPF",
             "l2": f"inputs larger than L2 (Jacobian {32 * nnzb / 1e6:.0f} MB)" if nnzb else
                   "inputs larger than L2",
@@ -341,6 +344,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1,
                     help="0: FP64 everywhere; 1: FP32 ILU(0)/AMG inside FP64 FGMRES")
     ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--no-schur-path", action="store_true")
     ap.add_argument("--sample-div", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -350,6 +354,9 @@ def main():
                     help="0: the paper's modified Gauss-Jordan step; 1: ABF; 2: True-IMPES")
     ap.add_argument("--eta-mode", type=int, default=2,
                     help="forcing term of Algorithm 1: 1, 2 or 3 (Section 3.1), 0: fixed")
+    ap.add_argument("--schur", type=int, default=0,
+                    help="1: eliminate the matrix cells exactly and solve the fracture-and-well "
+                         "system")
     ap.add_argument("--autotune", action="store_true",
                     help="time the AMG level kernels' launch shapes after the first warm-up "
                          "timestep and keep the fastest (sim_autotune)")
@@ -383,7 +390,7 @@ def main():
         return run_serve(args)
     prob = workload(args)
     opts = dpsim.options("report", precision=args.precision, cluster_rows=args.cluster_rows,
-                         decouple=args.decouple, eta_mode=args.eta_mode)
+                         decouple=args.decouple, eta_mode=args.eta_mode, schur=args.schur)
     if args.mode == "newton2":
         sim = dpsim.Sim(prob, opts)
         out = {}
@@ -480,7 +487,7 @@ def main():
     # one sweep = one launch per colour
     ncol = sim.colours()[1]
     sweeps = {}
-    for name, nbytes in sweep_bytes(sim.nb, sim.nnzb).items():
+    for name, nbytes in sweep_bytes(sim.snb, sim.snnzb).items():
         sim.time_kernel(name)
         sim.kernel_timing(reset=True)
         timestep(sim, opts)
@@ -514,10 +521,25 @@ def main():
     e2e_s, e2e_all = over_ranks(dist, dev, time.perf_counter() - t0, e2e_solves)
     nbytes_state = 8 * (2 * prob.n_cells + prob.n_wells)  # per timestep of e2e
 
+    schur = None
+    if args.schur == 0 and not args.no_schur_path:
+        osch = dpsim.options("report", precision=args.precision, cluster_rows=args.cluster_rows,
+                             decouple=args.decouple, eta_mode=args.eta_mode, schur=1)
+        with torch.cuda.stream(stream):
+            simsch = dpsim.Sim(prob, osch, stream=stream)
+        r = measure(simsch, osch, max(2, args.steps // 2), args.warmup)
+        simsch.close()
+        schur = {"value": r["all_solves"] / (r["ms"] / 1000.0), "unit": UNIT,
+                 "solve_ms_median": r["median"], "solve_ms_p90": r["p90"],
+                 "fgmres_iters_per_solve": r["its"] / max(r["solves"], 1),
+                 "ms_per_step": r["ms"] / max(2, args.steps // 2),
+                 "note": "the same timestep with the matrix cells eliminated exactly before "
+                         "the solve (CPR-FPF on the fracture-and-well system, 4M unknowns)"}
+
     fp64 = None
     if args.precision != 0 and not args.no_fp64_path:
         o64 = dpsim.options("report", precision=0, cluster_rows=args.cluster_rows,
-                            decouple=args.decouple, eta_mode=args.eta_mode)
+                            decouple=args.decouple, eta_mode=args.eta_mode, schur=args.schur)
         with torch.cuda.stream(stream):
             sim64 = dpsim.Sim(prob, o64, stream=stream)
         r = measure(sim64, o64, max(2, args.steps // 2), args.warmup)
@@ -531,7 +553,7 @@ def main():
         value = all_solves / (ms / 1000.0)
         peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
         peak = peaks.get("hbm_gbs", 6800.0)
-        ach = spmv_bytes(sim.nb, sim.nnzb) / (k_ms / max(k_n, 1) / 1000.0) / 1e9 if k_n else None
+        ach = spmv_bytes(sim.snb, sim.snnzb) / (k_ms / max(k_n, 1) / 1000.0) / 1e9 if k_n else None
         cpu = None
         if not args.no_cpu_baseline:
             try:
@@ -559,6 +581,7 @@ def main():
             "e2e": {"value": e2e_all / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state},
             "fp64_path": fp64,
+            "schur_path": schur,
             "gpu_launches": launches,
             "autotune": tuned,
             "clocks": clk.summary(),

@@ -129,6 +129,12 @@ typedef struct {
                             2 True-IMPES, D_i^-1 = [[1, -c01/c11], [0, 1]] with c
                             the sums of block column i over all rows (Section 3.2
                             names Quasi-IMPES and ABF beside its own choice) */
+  int32_t schur;         /* 1: eliminate every matrix cell exactly before the solve (a
+                            matrix cell couples only to its own fracture cell, Section
+                            2), y_m = A_mm^-1 (-R_m - A_mf y_f); the decoupling, ILU(0),
+                            AMG and FGMRES work on the fracture-and-well system with
+                            S_ff = A_ff - A_fm A_mm^-1 A_mf (half the unknowns); 0: the
+                            full system */
 } dp_options;
 
 typedef struct {
@@ -215,6 +221,11 @@ int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t t
  * need as many distinct streams to overlap).  No counterpart in the paper. */
 int dp_stream_create(void **stream);
 int dp_stream_destroy(void *stream);
+
+/* Block rows and blocks of the system the linear solver works on: the full
+ * one, or the fracture-and-well one with the Schur option (the sizes of
+ * sim_get_decoupled's arrays and sim_get_colours' array). */
+int sim_solver_sizes(dp_sim *sim, int32_t *nb, int32_t *nnzb);
 
 /* Autotuning of launch shapes (no counterpart in the paper): for every AMG
  * level, times each lanes-per-row variant (1..32) of the kernel of its

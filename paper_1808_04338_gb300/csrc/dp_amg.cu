@@ -675,10 +675,10 @@ int amg_setup(Sim *s) {
   s->lev.clear();
   s->lev.reserve(32);
   Level L0;
-  L0.n = s->ph.nb;
-  L0.nnz = s->A.nnz;
-  L0.rowptr = s->A.rowptr;
-  L0.col = s->A.col;
+  L0.n = s->K.n;
+  L0.nnz = s->K.nnz;
+  L0.rowptr = s->K.rowptr;
+  L0.col = s->K.col;
   L0.val = s->ap;
   L0.l1 = o.amg_gs_levels <= 0;
   L0.dinv = (double *)dalloc(s, (size_t)L0.n * 8);

@@ -134,6 +134,9 @@ int phys_assemble(Sim *s);
 int phys_norms(Sim *s);
 int phys_decouple_extract(Sim *s);
 int phys_decoupled_natural(Sim *s, double *out);
+int phys_solver_view(Sim *s);     // K and the solver view, after phys_build_pattern
+int phys_schur_reduce(Sim *s);    // K's values and residual from A and R (Schur option)
+int phys_schur_back(Sim *s);      // the full update y from K's update
 int phys_update(Sim *s);
 
 // dp_amg.cu (integer setup and bit-exact smoothed-aggregation numerics)
@@ -232,6 +235,18 @@ struct Sim {
   // maps of the decoupling's entry-parallel writes: natural row of each
   // entry, its block in the factor's split layout, its factor-order position
   int *erow = nullptr, *ilupos = nullptr, *l0pos = nullptr;
+  // The system the linear solver sees: K is the assembled Jacobian A (full
+  // system), or with the Schur option the fracture-and-well system whose
+  // rows are the fracture cells (row loc) and the wells (row nL + w).  Its
+  // storage-order copy maps storage row q to row row_of_pair(q, sv_sL,
+  // sv_sc); rows below sv_cells are cell rows (decoupled), rows from
+  // sv_long0 on are the long well rows.
+  Bsr K;
+  int sv_sL = 0, sv_sc = 0, sv_cells = 0, sv_long0 = 0;
+  double *Rk = nullptr;           // residual of K's rows (R itself for the full system)
+  double *yk = nullptr;           // update of K's rows (y itself for the full system)
+  int *kmap = nullptr, *pos_fm = nullptr, *pos_mf = nullptr;   // Schur: entry maps
+  double *Minv = nullptr;         // Schur: inverted matrix-cell block of each location
   double *fct = nullptr;          // per cell row: the weight w_i, or D_i^-1 (4 values, ABF)
   int *btpos = nullptr;           // transpose position of each block entry (True-IMPES)
   std::vector<int> lu_cstart;

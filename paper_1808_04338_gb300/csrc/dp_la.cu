@@ -22,9 +22,10 @@ namespace dp {
 // matrix rows, then wells): pair q processes storage row q, whose blocks are
 // contiguous with those of pair q+1, and writes natural row row_of_pair(q).
 
-// The well rows (the last n - nc storage rows, one block per perforation,
-// tens of blocks each) go to block 0, a warp per row, so that their long
-// rows start first instead of trailing the launch.
+// The well rows (storage rows nlong..n-1, one block per perforation, tens of
+// blocks each; their storage row is their row) go to block 0, a warp per
+// row, so that their long rows start first instead of trailing the launch.
+// Storage row q < nlong is row row_of_pair(q, nL, nc).
 template <int MODE>
 __device__ __forceinline__ void spmv_well_rows(int n, int nc, const int *__restrict__ rowptr,
                                                const int *__restrict__ col,
@@ -56,7 +57,7 @@ __device__ __forceinline__ void spmv_well_rows(int n, int nc, const int *__restr
 }
 
 template <int MODE>  // MODE 0: y = A x; 1: y = b - A x
-__global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
+__global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc, int nlong,
                                                      const int *__restrict__ rowptr,
                                                      const int *__restrict__ col,
                                                      const double *__restrict__ val,
@@ -64,12 +65,12 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
                                                      const double *__restrict__ b,
                                                      double *__restrict__ y) {
   if (blockIdx.x == 0) {
-    spmv_well_rows<MODE>(n, nc, rowptr, col, val, x, b, y);
+    spmv_well_rows<MODE>(n, nlong, rowptr, col, val, x, b, y);
     return;
   }
   int t = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
   int comp = t & 1, q = t >> 1;
-  if (q >= nc) return;
+  if (q >= nlong) return;
   int row = row_of_pair(q, nL, nc);
   int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
   const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc,
 // Pressure component of b - A x: rp_i = b_{i,0} - sum_j (a00 x_j0 + a01 x_j1),
 // from the contiguous copies of the (0,0) and (0,1) entries that the
 // decoupling writes (the 2x2 blocks would be read half-used).
-__global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
+__global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, int nlong,
                                                        const int *__restrict__ rowptr,
                                                        const int *__restrict__ col,
                                                        const double *__restrict__ a00,
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
   if (blockIdx.x == 0) {   // the well rows, a warp per row (as in k_bsr_spmv)
     int lane = threadIdx.x & 31;
     const double2 *x2 = reinterpret_cast<const double2 *>(x);
-    for (int row = nc + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+    for (int row = nlong + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
       double s = 0.0;
       for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
         double2 xj = __ldg(x2 + __ldg(col + e));
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
     return;
   }
   int t = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
-  if (t >= nc) return;
+  if (t >= nlong) return;
   int row = row_of_pair(t, nL, nc);
   int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
   const double2 *x2 = reinterpret_cast<const double2 *>(x);
@@ -127,13 +128,15 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc,
 }
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
-  DP_LAUNCH(s, k_bsr_spmv<0>, 1 + nblk(2LL * s->ph.nc), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
+  DP_LAUNCH(s, k_bsr_spmv<0>, 1 + nblk(2LL * s->sv_long0), kBlock, 0, s->K.n, s->sv_sL, s->sv_sc,
+            s->sv_long0,
             s->srowptr, s->scol, s->sval, x, nullptr, y);
   return DP_OK;
 }
 
 int bsr_residual(Sim *s, const double *b, const double *x, double *r) {
-  DP_LAUNCH(s, k_bsr_spmv<1>, 1 + nblk(2LL * s->ph.nc), kBlock, 0, s->A.n, s->ph.nL, s->ph.nc,
+  DP_LAUNCH(s, k_bsr_spmv<1>, 1 + nblk(2LL * s->sv_long0), kBlock, 0, s->K.n, s->sv_sL, s->sv_sc,
+            s->sv_long0,
             s->srowptr, s->scol, s->sval, x, b, r);
   return DP_OK;
 }
@@ -475,28 +478,28 @@ __global__ void k_colour_maxlen(int n, const int *cstart_dev, int ncolour, const
 constexpr int kLongRow = 24;   // colours with a row longer than this use a warp per row
 
 int ilu_setup(Sim *s) {
-  int n = s->A.n;
+  int n = s->K.n;
   s->colour = (int *)dalloc(s, (size_t)n * 4);
   s->perm = (int *)dalloc(s, (size_t)n * 4);
   s->iperm = (int *)dalloc(s, (size_t)n * 4);
   s->lu_rowptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
   s->lu_dpos = (int *)dalloc(s, (size_t)n * 4);
-  s->lu_col = (int *)dalloc(s, (size_t)s->A.nnz * 4);
-  s->lu_src = (int *)dalloc(s, (size_t)s->A.nnz * 4);
-  s->lu_val = (double *)dalloc(s, (size_t)s->A.nnz * 32);
-  s->lu_valf = (float *)dalloc(s, (size_t)s->A.nnz * 16);
+  s->lu_col = (int *)dalloc(s, (size_t)s->K.nnz * 4);
+  s->lu_src = (int *)dalloc(s, (size_t)s->K.nnz * 4);
+  s->lu_val = (double *)dalloc(s, (size_t)s->K.nnz * 32);
+  s->lu_valf = (float *)dalloc(s, (size_t)s->K.nnz * 16);
   int *len = (int *)dalloc(s, (size_t)n * 4);
   if (!s->colour || !s->perm || !s->iperm || !s->lu_rowptr || !s->lu_dpos || !s->lu_col ||
       !s->lu_src || !s->lu_val || !s->lu_valf || !len) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
-  DP_TRY(greedy_colour(s, n, s->A.rowptr, s->A.col, s->colour, &s->ncolour));
+  DP_TRY(greedy_colour(s, n, s->K.rowptr, s->K.col, s->colour, &s->ncolour));
   DP_TRY(colour_lists(s, n, s->colour, s->ncolour, s->perm, s->lu_cstart, s->iperm));
-  DP_LAUNCH(s, k_perm_len, nblk(n), kBlock, 0, n, s->perm, s->A.rowptr, len);
+  DP_LAUNCH(s, k_perm_len, nblk(n), kBlock, 0, n, s->perm, s->K.rowptr, len);
   int nnz = 0;
   DP_TRY(scan_i32(s, len, s->lu_rowptr, n, &nnz));
-  DP_LAUNCH(s, k_lu_pattern, nblk(n), kBlock, 0, n, s->perm, s->iperm, s->A.rowptr, s->A.col,
+  DP_LAUNCH(s, k_lu_pattern, nblk(n), kBlock, 0, n, s->perm, s->iperm, s->K.rowptr, s->K.col,
             s->lu_rowptr, s->lu_col, s->lu_src, s->lu_dpos);
   {
     int nc = s->ncolour;
@@ -559,9 +562,9 @@ int ilu_setup(Sim *s) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
-  DP_LAUNCH(s, k_entry_maps, nblk(n), kBlock, 0, n, s->A.rowptr, s->lu_rowptr, s->lu_src,
+  DP_LAUNCH(s, k_entry_maps, nblk(n), kBlock, 0, n, s->K.rowptr, s->lu_rowptr, s->lu_src,
             s->lu_dst, s->erow, s->ilupos, s->l0pos);
-  DP_LAUNCH(s, k_block_tpos, nblk(n), kBlock, 0, n, s->A.rowptr, s->A.col, s->btpos);
+  DP_LAUNCH(s, k_block_tpos, nblk(n), kBlock, 0, n, s->K.rowptr, s->K.col, s->btpos);
   DP_CUDA(s, cudaGetLastError());
   dfree(s, cnt);
   dfree(s, len);
@@ -591,7 +594,7 @@ int ilu_factor(Sim *s) {
 // gathers it (ilu_result) while converting or accumulating.
 template <typename T, typename TR>
 static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
-  int n = s->A.n, nL = s->lu_nL;
+  int n = s->K.n, nL = s->lu_nL;
   T *zp = reinterpret_cast<T *>(s->ilu_zp);
   for (int c = 0; c < s->ncolour; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
@@ -630,7 +633,7 @@ __global__ void k_ilu_result(int n, const int *__restrict__ iperm, const T *__re
 
 template <typename T>
 static int ilu_result(Sim *s, const double *base, double *out) {
-  int n = s->A.n;
+  int n = s->K.n;
   DP_LAUNCH(s, k_ilu_result<T>, nblk(2LL * n), kBlock, 0, n, s->iperm,
             reinterpret_cast<const T *>(s->ilu_zp), base, out);
   return DP_OK;
@@ -1078,7 +1081,7 @@ int l0_refresh(Sim *s) {
   if (s->lev.empty() || s->opt.precond != 2) return DP_OK;
   Level &L = s->lev[0];
   if (!s->l0_lu) {
-    if (L.l1 || L.ncolour != s->ncolour || L.rowptr != s->A.rowptr) return DP_OK;
+    if (L.l1 || L.ncolour != s->ncolour || L.rowptr != s->K.rowptr) return DP_OK;
     for (int c = 0; c <= L.ncolour; ++c)
       if (L.cstart[c] != s->lu_cstart[c]) return DP_OK;
     size_t nnz = (size_t)std::max(L.nnz, 1);
@@ -1288,7 +1291,7 @@ __global__ void k_to_f32(long long n, const double *x, float *y) {
 
 
 int cpr_apply(Sim *s, const double *r, double *z) {
-  int nb = s->A.n;
+  int nb = s->K.n;
   long long N = 2LL * nb;
   bool f32 = s->opt.precision == 1;
   if (s->opt.precond == 0) {
@@ -1298,8 +1301,8 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   if (!f32) {
     if (s->opt.precond == 1) return ilu_apply(s, r, z);
     DP_TRY(ilu_apply(s, r, s->z1));
-    DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->ph.nc), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr,
-              s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
+    DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
+              s->sv_long0, s->srowptr, s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
     DP_TRY(vcycle(s, 0, s->rp, s->xp));
     DP_LAUNCH(s, k_inject_add<double>, nblk(nb), kBlock, 0, nb, s->xp, s->z1);
     DP_TRY(bsr_residual(s, r, s->z1, s->r1));
@@ -1314,8 +1317,8 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   Level &L0 = s->lev[0];
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
   DP_TRY(ilu_result<float>(s, nullptr, s->z1));
-  DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->ph.nc), kBlock, 0, nb, s->ph.nL, s->ph.nc, s->srowptr,
-            s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
+  DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
+            s->sv_long0, s->srowptr, s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
   DP_LAUNCH(s, k_to_f32, nblk(nb), kBlock, 0, (long long)nb, s->rp, L0.bf);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
   DP_LAUNCH(s, k_inject_add<float>, nblk(nb), kBlock, 0, nb, L0.xf, s->z1);
@@ -1546,7 +1549,7 @@ __global__ void k_init_g(double *g, int m, const double *beta) {
 // `gate` as for k_multidot.
 static int dots(Sim *s, const double *V, long long ldv, int nv, const double *w, int mode, int j,
                 const double *gate = nullptr) {
-  long long N = 2LL * s->A.n;
+  long long N = 2LL * s->K.n;
   for (int v0 = 0; v0 < nv; v0 += kDotVec) {
     int cnt = std::min(kDotVec, nv - v0);
     const double *Vb = V + (long long)v0 * ldv;
@@ -1571,7 +1574,7 @@ static int dots(Sim *s, const double *V, long long ldv, int nv, const double *w,
 
 // ||x|| into s->scal[slot] (device) via the dot machinery
 static int norm_into(Sim *s, const double *x, double *dst) {
-  long long N = 2LL * s->A.n;
+  long long N = 2LL * s->K.n;
   DP_LAUNCH(s, (k_multidot<1, false>), kDotBlocks, kBlock, 0, N, x, 0LL, x, s->dots_part, 0,
             (const double *)nullptr);
   DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, dst, s->H, s->m, 0, 0, s->scal);
@@ -1588,7 +1591,7 @@ __global__ void k_sqrt_inplace(double *v) { v[0] = sqrt(v[0]); }
 // Then the Givens rotations, and |g_{j+1}| into scal[3].
 static int arnoldi_step(Sim *s, int j) {
   int m = s->m;
-  long long N = 2LL * s->A.n;
+  long long N = 2LL * s->K.n;
   int gridN = (int)std::min<long long>(nblk(N), kDotBlocks * 4);
   double *vj = s->V + (long long)j * N, *zj = s->Z + (long long)j * N;
   double *vnext = s->V + (long long)(j + 1) * N;
@@ -1647,9 +1650,9 @@ static int arnoldi_step_graph(Sim *s, int j) {
 
 int fgmres(Sim *s, double tol, int *iters, double *relres) {
   int m = s->m, maxit = s->opt.gmres_maxit;
-  long long N = 2LL * s->A.n;
+  long long N = 2LL * s->K.n;
   bool use_graph = s->opt.use_graphs && s->timing.kernel_id < 0;
-  double *x = s->y;
+  double *x = s->yk;
   DP_CUDA(s, cudaMemsetAsync(x, 0, N * 8, s->stream));
   DP_TRY(norm_into(s, s->bh, s->scal + 0));
   DP_LAUNCH(s, k_sqrt_inplace, 1, 1, 0, s->scal + 0);
@@ -1700,7 +1703,7 @@ int fgmres(Sim *s, double tol, int *iters, double *relres) {
 int la_alloc(Sim *s) {
   int m = std::max(1, std::min(s->opt.gmres_restart, 30));
   s->m = m;
-  long long N = 2LL * s->A.n;
+  long long N = 2LL * s->K.n;
   s->V = (double *)dalloc(s, (size_t)(m + 1) * N * 8);
   s->Z = (double *)dalloc(s, (size_t)m * N * 8);
   s->w = (double *)dalloc(s, (size_t)N * 8);
@@ -1714,8 +1717,8 @@ int la_alloc(Sim *s) {
   s->scal = (double *)dalloc(s, 8 * 8);
   s->z1 = (double *)dalloc(s, (size_t)N * 8);
   s->r1 = (double *)dalloc(s, (size_t)N * 8);
-  s->rp = (double *)dalloc(s, (size_t)s->A.n * 8);
-  s->xp = (double *)dalloc(s, (size_t)s->A.n * 8);
+  s->rp = (double *)dalloc(s, (size_t)s->K.n * 8);
+  s->xp = (double *)dalloc(s, (size_t)s->K.n * 8);
   if (!s->V || !s->Z || !s->w || !s->H || !s->cs || !s->sn || !s->g || !s->hy || !s->dots_part ||
       !s->dots || !s->scal || !s->z1 || !s->r1 || !s->rp || !s->xp) {
     s->fail(DP_ENOMEM, "allocation failed");

@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(kBlock) k_decouple_rows(int nb, int nc, int mo
 
 struct DecArgs {
   long long nnz;
-  int nc, nL, mode;
+  int nc, sL, sc, mode;   // rows below nc are cell rows; storage mapping (sL, sc)
   const int *erow, *rowptr, *srowptr, *ilupos, *l0pos;
   const double *val, *fct;
   double *ap, *sval, *sa00, *sa01;
@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
     }
   }
   a.ap[e] = n0;
-  int si = storage_row(i, a.nL, a.nc);
+  int si = storage_row(i, a.sL, a.sc);
   size_t q = (size_t)(__ldg(a.srowptr + si) + (int)(e - __ldg(a.rowptr + i)));
   double2 *sv = reinterpret_cast<double2 *>(a.sval) + 2 * q;
   sv[0] = make_double2(n0, n1);
@@ -779,19 +779,20 @@ __global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
 
 int phys_decouple_extract(Sim *s) {
   int mode = s->opt.decouple;
-  DP_LAUNCH(s, k_decouple_rows, nblk(s->ph.nb), kBlock, 0, s->ph.nb, s->ph.nc, mode, s->A.rowptr,
-            s->A.diag, s->btpos, s->A.val, s->R, s->fct, s->bh);
+  const Bsr &K = s->K;
+  DP_LAUNCH(s, k_decouple_rows, nblk(K.n), kBlock, 0, K.n, s->sv_cells, mode, K.rowptr, K.diag,
+            s->btpos, K.val, s->Rk, s->fct, s->bh);
   DecArgs a;
-  a.nnz = s->A.nnz; a.nc = s->ph.nc; a.nL = s->ph.nL; a.mode = mode;
-  a.erow = s->erow; a.rowptr = s->A.rowptr; a.srowptr = s->srowptr;
+  a.nnz = K.nnz; a.nc = s->sv_cells; a.sL = s->sv_sL; a.sc = s->sv_sc; a.mode = mode;
+  a.erow = s->erow; a.rowptr = K.rowptr; a.srowptr = s->srowptr;
   a.ilupos = s->ilupos; a.l0pos = s->l0pos;
-  a.val = s->A.val; a.fct = s->fct;
+  a.val = K.val; a.fct = s->fct;
   a.ap = s->ap; a.sval = s->sval; a.sa00 = s->sa00; a.sa01 = s->sa01;
   bool f32 = s->opt.precision == 1;
   a.lu = s->opt.precond >= 1 ? (f32 ? (void *)s->lu_valf : (void *)s->lu_val) : nullptr;
   a.l0 = s->l0_lu ? (f32 ? (void *)s->l0_pvf : (void *)s->l0_pv) : nullptr;
-  if (f32) DP_LAUNCH(s, k_decouple<float>, nblk(s->A.nnz), kBlock, 0, a);
-  else DP_LAUNCH(s, k_decouple<double>, nblk(s->A.nnz), kBlock, 0, a);
+  if (f32) DP_LAUNCH(s, k_decouple<float>, nblk(K.nnz), kBlock, 0, a);
+  else DP_LAUNCH(s, k_decouple<double>, nblk(K.nnz), kBlock, 0, a);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
@@ -809,8 +810,191 @@ __global__ void k_natural_from_storage(long long nnz, int nc, int nL, const int 
 }
 
 int phys_decoupled_natural(Sim *s, double *out) {
-  DP_LAUNCH(s, k_natural_from_storage, nblk(s->A.nnz), kBlock, 0, (long long)s->A.nnz, s->ph.nc,
-            s->ph.nL, s->erow, s->A.rowptr, s->srowptr, s->sval, out);
+  DP_LAUNCH(s, k_natural_from_storage, nblk(s->K.nnz), kBlock, 0, (long long)s->K.nnz, s->sv_sc,
+            s->sv_sL, s->erow, s->K.rowptr, s->srowptr, s->sval, out);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------- Schur option
+// Exact elimination of the matrix continuum: a matrix cell m of location loc
+// couples only to itself and to its fracture cell f, so y_m = A_mm^-1 (-R_m
+// - A_mf y_f), and the fracture row takes S_ff = A_ff - A_fm A_mm^-1 A_mf and
+// the residual R_f - A_fm A_mm^-1 R_m.  K keeps the fracture rows (row loc)
+// and the well rows (row nL + w); its other blocks are copies of A's.  The
+// formulas are evaluated as written, in the order the oracle uses.
+
+__device__ __forceinline__ int kcol(int c, int nL, int nc) {   // -1: a matrix column, dropped
+  return c >= nc ? nL + (c - nc) : ((c & 1) ? -1 : c >> 1);
+}
+
+__global__ void k_schur_len(int nk, int nL, int nc, const int *rowptr, const int *col, int *len) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nk) return;
+  int jr = r < nL ? 2 * r : nc + (r - nL), c = 0;
+  for (int e = rowptr[jr]; e < rowptr[jr + 1]; ++e) c += kcol(col[e], nL, nc) >= 0;
+  len[r] = c;
+}
+
+__global__ void k_schur_fill(int nk, int nL, int nc, const int *rowptr, const int *col,
+                             const int *krowptr, int *kcolv, int *kdiag, int *kmap) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nk) return;
+  int jr = r < nL ? 2 * r : nc + (r - nL), k = krowptr[r];
+  for (int e = rowptr[jr]; e < rowptr[jr + 1]; ++e) {
+    int c = kcol(col[e], nL, nc);
+    if (c < 0) continue;
+    kcolv[k] = c;
+    kmap[k] = (r < nL && c == r) ? -1 : e;
+    if (c == r) kdiag[r] = k;
+    ++k;
+  }
+}
+
+__device__ __forceinline__ int find_col_in(const int *col, int lo, int hi, int c) {
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (col[m] == c) return m;
+    if (col[m] < c) lo = m + 1; else hi = m;
+  }
+  return -1;
+}
+
+__global__ void k_schur_pos(int nL, const int *rowptr, const int *col, int *pos_fm, int *pos_mf) {
+  int loc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= nL) return;
+  int f = 2 * loc, m = f + 1;
+  pos_fm[loc] = find_col_in(col, rowptr[f], rowptr[f + 1], m);
+  pos_mf[loc] = find_col_in(col, rowptr[m], rowptr[m + 1], f);
+}
+
+__global__ void k_schur_copy(long long nnzk, const int *kmap, const double *val, double *kval) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnzk) return;
+  int e = kmap[k];
+  if (e < 0) return;
+  const double2 *src = reinterpret_cast<const double2 *>(val) + 2 * (size_t)e;
+  double2 *dst = reinterpret_cast<double2 *>(kval) + 2 * k;
+  dst[0] = src[0];
+  dst[1] = src[1];
+}
+
+__global__ void k_schur_loc(int nL, int nc, int nw, const int *diag, const int *pos_fm,
+                            const int *pos_mf, const int *kdiag, const double *val,
+                            const double *R, double *kval, double *RK, double *Minv) {
+  int loc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc < nw) {
+    RK[2 * (nL + loc)] = R[2 * (nc + loc)];
+    RK[2 * (nL + loc) + 1] = R[2 * (nc + loc) + 1];
+  }
+  if (loc >= nL) return;
+  int f = 2 * loc, m = f + 1;
+  const double *amm = val + 4 * (size_t)diag[m];
+  const double *amf = val + 4 * (size_t)pos_mf[loc];
+  const double *afm = val + 4 * (size_t)pos_fm[loc];
+  const double *aff = val + 4 * (size_t)diag[f];
+  double det = (amm[0] * amm[3]) - (amm[1] * amm[2]);
+  double m0, m1, m2, m3;
+  if (fabs(det) < 1e-300) { m0 = 0.0; m1 = 0.0; m2 = 0.0; m3 = 0.0; }
+  else { m0 = amm[3] / det; m1 = (-amm[1]) / det; m2 = (-amm[2]) / det; m3 = amm[0] / det; }
+  double *mi = Minv + 4 * (size_t)loc;
+  mi[0] = m0; mi[1] = m1; mi[2] = m2; mi[3] = m3;
+  double x00 = (afm[0] * m0) + (afm[1] * m2);
+  double x01 = (afm[0] * m1) + (afm[1] * m3);
+  double x10 = (afm[2] * m0) + (afm[3] * m2);
+  double x11 = (afm[2] * m1) + (afm[3] * m3);
+  double *sk = kval + 4 * (size_t)kdiag[loc];
+  sk[0] = aff[0] - ((x00 * amf[0]) + (x01 * amf[2]));
+  sk[1] = aff[1] - ((x00 * amf[1]) + (x01 * amf[3]));
+  sk[2] = aff[2] - ((x10 * amf[0]) + (x11 * amf[2]));
+  sk[3] = aff[3] - ((x10 * amf[1]) + (x11 * amf[3]));
+  double rm0 = R[2 * m], rm1 = R[2 * m + 1];
+  RK[2 * loc] = R[2 * f] - ((x00 * rm0) + (x01 * rm1));
+  RK[2 * loc + 1] = R[2 * f + 1] - ((x10 * rm0) + (x11 * rm1));
+}
+
+__global__ void k_schur_back(int nL, int nc, int nw, const int *pos_mf, const double *val,
+                             const double *Minv, const double *R, const double *yk, double *y) {
+  int loc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc < nw) {
+    y[2 * (nc + loc)] = yk[2 * (nL + loc)];
+    y[2 * (nc + loc) + 1] = yk[2 * (nL + loc) + 1];
+  }
+  if (loc >= nL) return;
+  int f = 2 * loc, m = f + 1;
+  double yf0 = yk[2 * loc], yf1 = yk[2 * loc + 1];
+  const double *amf = val + 4 * (size_t)pos_mf[loc];
+  const double *mi = Minv + 4 * (size_t)loc;
+  double t0 = (-R[2 * m]) - ((amf[0] * yf0) + (amf[1] * yf1));
+  double t1 = (-R[2 * m + 1]) - ((amf[2] * yf0) + (amf[3] * yf1));
+  y[2 * f] = yf0;
+  y[2 * f + 1] = yf1;
+  y[2 * m] = (mi[0] * t0) + (mi[1] * t1);
+  y[2 * m + 1] = (mi[2] * t0) + (mi[3] * t1);
+}
+
+int phys_solver_view(Sim *s) {
+  Phys &P = s->ph;
+  if (!s->opt.schur) {
+    s->K = s->A;
+    s->sv_sL = P.nL; s->sv_sc = P.nc; s->sv_cells = P.nc; s->sv_long0 = P.nc;
+    s->Rk = s->R;
+    s->yk = s->y;
+    return DP_OK;
+  }
+  Bsr &K = s->K;
+  int nk = P.nL + P.nw;
+  K.n = nk;
+  K.rowptr = (int *)dalloc(s, ((size_t)nk + 1) * 4);
+  K.diag = (int *)dalloc(s, (size_t)nk * 4);
+  int *len = (int *)dalloc(s, (size_t)nk * 4);
+  if (!K.rowptr || !K.diag || !len) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  DP_LAUNCH(s, k_schur_len, nblk(nk), kBlock, 0, nk, P.nL, P.nc, s->A.rowptr, s->A.col, len);
+  int nnz = 0;
+  DP_TRY(scan_i32(s, len, K.rowptr, nk, &nnz));
+  K.nnz = nnz;
+  K.col = (int *)dalloc(s, (size_t)nnz * 4);
+  K.val = (double *)dalloc(s, (size_t)nnz * 32);
+  s->kmap = (int *)dalloc(s, (size_t)nnz * 4);
+  s->pos_fm = (int *)dalloc(s, (size_t)P.nL * 4);
+  s->pos_mf = (int *)dalloc(s, (size_t)P.nL * 4);
+  s->Minv = (double *)dalloc(s, (size_t)P.nL * 32);
+  s->Rk = (double *)dalloc(s, (size_t)nk * 16);
+  s->yk = (double *)dalloc(s, (size_t)nk * 16);
+  if (!K.col || !K.val || !s->kmap || !s->pos_fm || !s->pos_mf || !s->Minv || !s->Rk || !s->yk) {
+    s->fail(DP_ENOMEM, "allocation failed");
+    return DP_ENOMEM;
+  }
+  DP_LAUNCH(s, k_schur_fill, nblk(nk), kBlock, 0, nk, P.nL, P.nc, s->A.rowptr, s->A.col, K.rowptr,
+            K.col, K.diag, s->kmap);
+  DP_LAUNCH(s, k_schur_pos, nblk(P.nL), kBlock, 0, P.nL, s->A.rowptr, s->A.col, s->pos_fm,
+            s->pos_mf);
+  dfree(s, len);
+  // K's rows are already grouped (fracture rows, then wells): its storage
+  // order is its natural order
+  dfree(s, s->srowptr);
+  dfree(s, s->scol);
+  s->srowptr = K.rowptr;
+  s->scol = K.col;
+  s->sv_sL = 0; s->sv_sc = 0; s->sv_cells = P.nL; s->sv_long0 = P.nL;
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+int phys_schur_reduce(Sim *s) {
+  Phys &P = s->ph;
+  DP_LAUNCH(s, k_schur_copy, nblk(s->K.nnz), kBlock, 0, (long long)s->K.nnz, s->kmap, s->A.val,
+            s->K.val);
+  DP_LAUNCH(s, k_schur_loc, nblk(std::max(P.nL, P.nw)), kBlock, 0, P.nL, P.nc, P.nw, s->A.diag,
+            s->pos_fm, s->pos_mf, s->K.diag, s->A.val, s->R, s->K.val, s->Rk, s->Minv);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+int phys_schur_back(Sim *s) {
+  Phys &P = s->ph;
+  DP_LAUNCH(s, k_schur_back, nblk(std::max(P.nL, P.nw)), kBlock, 0, P.nL, P.nc, P.nw, s->pos_mf,
+            s->A.val, s->Minv, s->R, s->yk, s->y);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }

@@ -109,7 +109,8 @@ static bool bad_opts(const dp_options *o) {
   return !o || o->gmres_restart < 1 || o->gmres_maxit < 1 || o->newton_max < 0 ||
          o->amg_coarse_max < 1 || o->amg_max_levels < 1 || o->precond < 0 || o->precond > 2 ||
          o->precision < 0 || o->precision > 1 || !(o->ds_max > 0.0) || o->amg_gs_levels < 0 ||
-         o->amg_refresh < 0 || o->amg_refresh > 1 || o->decouple < 0 || o->decouple > 2;
+         o->amg_refresh < 0 || o->amg_refresh > 1 || o->decouple < 0 || o->decouple > 2 ||
+         o->schur < 0 || o->schur > 1;
 }
 
 extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_fluid *fluid,
@@ -203,6 +204,7 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   cudaMemsetAsync(s->p, 0, nc8, st); cudaMemsetAsync(s->sw, 0, nc8, st);
   cudaMemsetAsync(s->bhp, 0, nw8, st); cudaMemsetAsync(s->Mn, 0, 2 * nc8, st);
   cudaMemsetAsync(s->y, 0, nb16, st);
+  if ((rc = phys_solver_view(s))) return fail(rc);
   if ((rc = ilu_setup(s))) return fail(rc);
   if ((rc = la_alloc(s))) return fail(rc);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(DP_ECUDA);
@@ -326,6 +328,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
   cudaEventRecord(e0, s->stream);
+  if (s->opt.schur) DP_TRY(phys_schur_reduce(s));
   DP_TRY(phys_decouple_extract(s));
   s->decoupled = true;
   if (s->opt.precond >= 1) DP_TRY(ilu_factor(s));
@@ -343,6 +346,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   double rr = 0.0;
   int rc = fgmres(s, eta, &it, &rr);
   if (rc != DP_OK && rc != DP_ELINEAR) return rc;
+  if (s->opt.schur) DP_TRY(phys_schur_back(s));
   DP_TRY(phys_update(s));
   cudaEventRecord(e2, s->stream);
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -419,6 +423,13 @@ extern "C" int dp_stream_destroy(void *stream) {
   return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? DP_OK : DP_ECUDA;
 }
 
+extern "C" int sim_solver_sizes(dp_sim *s, int32_t *nb, int32_t *nnzb) {
+  if (!s) return DP_EINVAL;
+  if (nb) *nb = s->K.n;
+  if (nnzb) *nnzb = s->K.nnz;
+  return DP_OK;
+}
+
 extern "C" int sim_autotune(dp_sim *s, int32_t reps, char *report, int32_t report_len) {
   if (!s || reps < 1 || (report && report_len < 1)) return DP_EINVAL;
   std::string rep;
@@ -482,24 +493,24 @@ extern "C" int sim_get_decoupled(dp_sim *s, double *val, double *rhs) {
   if (!s) return DP_EINVAL;
   if (!s->decoupled) { s->fail(DP_EINVAL, "no decoupled system yet"); return DP_EINVAL; }
   if (val) {
-    double *tmp = (double *)dalloc(s, (size_t)s->A.nnz * 32);
+    double *tmp = (double *)dalloc(s, (size_t)s->K.nnz * 32);
     if (!tmp) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
     int rc = phys_decoupled_natural(s, tmp);
     if (rc == DP_OK &&
-        cudaMemcpyAsync(val, tmp, (size_t)s->A.nnz * 32, cudaMemcpyDefault, s->stream) != cudaSuccess)
+        cudaMemcpyAsync(val, tmp, (size_t)s->K.nnz * 32, cudaMemcpyDefault, s->stream) != cudaSuccess)
       rc = DP_ECUDA;
     cudaStreamSynchronize(s->stream);
     dfree(s, tmp);
     if (rc != DP_OK) { s->fail(rc, "sim_get_decoupled"); return rc; }
   }
-  if (rhs) DP_CUDA(s, cudaMemcpyAsync(rhs, s->bh, (size_t)s->A.n * 16, cudaMemcpyDefault, s->stream));
+  if (rhs) DP_CUDA(s, cudaMemcpyAsync(rhs, s->bh, (size_t)s->K.n * 16, cudaMemcpyDefault, s->stream));
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
   return check(s);
 }
 
 extern "C" int sim_get_colours(dp_sim *s, int32_t *colour) {
   if (!s || !colour) return DP_EINVAL;
-  DP_CUDA(s, cudaMemcpyAsync(colour, s->colour, (size_t)s->A.n * 4, cudaMemcpyDefault, s->stream));
+  DP_CUDA(s, cudaMemcpyAsync(colour, s->colour, (size_t)s->K.n * 4, cudaMemcpyDefault, s->stream));
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
   DP_TRY(check(s));
   return s->ncolour;

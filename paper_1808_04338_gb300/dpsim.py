@@ -61,7 +61,7 @@ class dp_options(C.Structure):
                 ("amg_max_levels", C.c_int32), ("precond", C.c_int32),
                 ("ds_max", C.c_double), ("precision", C.c_int32), ("use_graphs", C.c_int32),
                 ("amg_gs_levels", C.c_int32), ("cluster_rows", C.c_int32),
-                ("amg_refresh", C.c_int32), ("decouple", C.c_int32)]
+                ("amg_refresh", C.c_int32), ("decouple", C.c_int32), ("schur", C.c_int32)]
 
 
 class dp_stats(C.Structure):
@@ -142,6 +142,7 @@ def load():
     L.sim_advance_many.argtypes = [P, I, P, I, P, P]
     L.sim_footprint.argtypes = [P, P, P]
     L.sim_autotune.argtypes = [P, I, C.c_char_p, I]
+    L.sim_solver_sizes.argtypes = [P, P, P]
     L.dp_stream_create.argtypes = [P]
     L.dp_stream_destroy.argtypes = [P]
     L.srv_create.argtypes = [I, C.c_uint64, P, P]
@@ -372,6 +373,8 @@ class Sim:
         nb, nnz, nc, nwl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         L.sim_sizes(h, C.byref(nb), C.byref(nnz), C.byref(nc), C.byref(nwl))
         self.nb, self.nnzb, self.nc, self.nw = nb.value, nnz.value, nc.value, nwl.value
+        L.sim_solver_sizes(h, C.byref(nb), C.byref(nnz))
+        self.snb, self.snnzb = nb.value, nnz.value     # the system the solver sees
         if prob.p0 is not None:
             self.set_state(prob.p0, prob.sw0, prob.bhp0)
 
@@ -455,12 +458,12 @@ class Sim:
         return y
 
     def decoupled(self):
-        val = np.zeros((self.nnzb, 2, 2)); rhs = np.zeros(2 * self.nb)
+        val = np.zeros((self.snnzb, 2, 2)); rhs = np.zeros(2 * self.snb)
         self._check(load().sim_get_decoupled(self.h, _p(val), _p(rhs)), "sim_get_decoupled")
         return val, rhs
 
     def colours(self):
-        c = np.zeros(self.nb, np.int32)
+        c = np.zeros(self.snb, np.int32)
         n = self._check(load().sim_get_colours(self.h, _p(c)), "sim_get_colours")
         return c, n
 

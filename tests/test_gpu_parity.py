@@ -86,12 +86,15 @@ def test_jacobian_residual_bit_exact(make):
     np.testing.assert_array_equal(g.well_index(), o.well_index())
 
 
-@pytest.mark.parametrize("decouple", [0, 1, 2])
-def test_decoupling_colours_and_amg_setup_bit_exact(decouple):
-    """The decoupled system (the paper's step, ABF, True-IMPES), the
-    colouring and the AMG set-up built on its pressure block, bit for bit."""
+@pytest.mark.parametrize("decouple,schur", [(0, 0), (1, 0), (2, 0), (0, 1), (2, 1)])
+def test_decoupling_colours_and_amg_setup_bit_exact(decouple, schur):
+    """The decoupled system (the paper's step, ABF, True-IMPES; the full
+    system or the fracture-and-well system left by eliminating the matrix
+    cells), the colouring and the AMG set-up built on its pressure block,
+    bit for bit."""
     prob = di.tiny()
-    g, o = pair(prob, decouple=decouple)
+    g, o = pair(prob, decouple=decouple, schur=schur)
+    assert (g.snb, g.snnzb) == (o.snb, o.snnzb)
     g.assemble(prob.dt)
     o.assemble(prob.dt)
     g.solve_step()
@@ -122,16 +125,18 @@ def dense_from_bsr(rowptr, col, val):
     return A
 
 
-@pytest.mark.parametrize("precond,gs_levels,decouple", [(1, 30, 0), (2, 30, 0), (2, 0, 0),
-                                                        (2, 30, 1), (2, 30, 2)])
-def test_newton_update_parity(precond, gs_levels, decouple):
+@pytest.mark.parametrize("precond,gs_levels,decouple,schur", [(1, 30, 0, 0), (2, 30, 0, 0),
+                                                               (2, 0, 0, 0), (2, 30, 1, 0),
+                                                               (2, 30, 2, 0), (2, 30, 0, 1),
+                                                               (1, 30, 0, 1)])
+def test_newton_update_parity(precond, gs_levels, decouple, schur):
     """One linear solve at eta = 1e-12 on both sides: the GPU update's true
     residual (dense J from the oracle) is at the tolerance, it agrees with
     the oracle's update as closely as the conditioning of J (~1e12) allows,
     and both take (nearly) the same number of FGMRES iterations."""
     prob = di.tiny()
     g, o = pair(prob, precond=precond, eta_fixed=1e-12, gmres_maxit=1000,
-                amg_gs_levels=gs_levels, decouple=decouple)
+                amg_gs_levels=gs_levels, decouple=decouple, schur=schur)
     st = interior(prob, 3)
     for s in (g, o):
         s.set_iterate(*st)
@@ -235,13 +240,13 @@ def test_layered_200k_first_step_parity():
         assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
 
 
-@pytest.mark.parametrize("amg_refresh", [0, 1])
-def test_layered_200k_timestep_parity(amg_refresh):
+@pytest.mark.parametrize("amg_refresh,schur", [(0, 0), (1, 0), (0, 1)])
+def test_layered_200k_timestep_parity(amg_refresh, schur):
     """One 5-day timestep of the 200k-cell grid; with amg_refresh = 1 both
     sides keep the coarse AMG values of the timestep's first Newton
     iteration for the later ones."""
     prob = di.layered()
-    g, o = pair(prob, "parity", amg_refresh=amg_refresh)
+    g, o = pair(prob, "parity", amg_refresh=amg_refresh, schur=schur)
     rcg, stg = g.advance(prob.dt)
     rco, sto = o.advance(prob.dt)
     assert rcg == rco == 0
@@ -249,12 +254,16 @@ def test_layered_200k_timestep_parity(amg_refresh):
     state_close(g, o, prob)
 
 
-@pytest.mark.parametrize("kw", [dict(amg_refresh=1), dict(decouple=1), dict(decouple=2)])
+@pytest.mark.parametrize("kw", [dict(amg_refresh=1), dict(decouple=1), dict(decouple=2),
+                                dict(schur=1), dict(schur=1, precision=1)])
 def test_tiny_steps_option_variants(kw):
-    """Ten tiny timesteps against the oracle with the coarse AMG values kept
-    for a timestep, and with the ABF and True-IMPES decouplings."""
+    """Ten tiny timesteps against the FP64 oracle with the coarse AMG values
+    kept for a timestep, with the ABF and True-IMPES decouplings, and with the
+    matrix cells eliminated (FP64 and FP32 preconditioner)."""
     prob = di.tiny()
-    g, o = pair(prob, "parity", **kw)
+    okw = {k: v for k, v in kw.items() if k != "precision"}
+    g = gpu().Sim(prob, gpu().options("parity", **kw))
+    o = O.OracleSim(prob, O.options("parity", **okw))
     for step in range(prob.nsteps):
         rcg, _ = g.advance(prob.dt)
         rco, _ = o.advance(prob.dt)
