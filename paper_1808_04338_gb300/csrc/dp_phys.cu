@@ -58,14 +58,25 @@ __device__ __forceinline__ void accumulation(const Phys &P, double sw, const Pro
 }
 
 // Mass flux a -> b (a < b) per phase with upstream mobility (Section 2:
-// Darcy flux with potential Phi = p - rho g z, upstream weighting).
+// Darcy flux with potential Phi = p - rho g z, upstream weighting).  GRAV =
+// false is the same evaluation for gdz = 0: the gravity terms are then exact
+// zeros (x - (y * 0) == x for the finite values here, and p_a - p_b is never
+// -0), so the result is identical bit for bit.
+template <bool GRAV>
 __device__ __forceinline__ void flux(double T, double gdz, double pa, double pb, const Props &qa,
                                      const Props &qb, double F[2], double dFa[4], double dFb[4]) {
 #pragma unroll
   for (int al = 0; al < 2; ++al) {
-    double dpot = (pa - pb) - ((0.5 * (qa.rho[al] + qb.rho[al])) * gdz);
-    double ddpa = 1.0 - ((0.5 * qa.drho[al]) * gdz);
-    double ddpb = -1.0 - ((0.5 * qb.drho[al]) * gdz);
+    double dpot, ddpa, ddpb;
+    if (GRAV) {
+      dpot = (pa - pb) - ((0.5 * (qa.rho[al] + qb.rho[al])) * gdz);
+      ddpa = 1.0 - ((0.5 * qa.drho[al]) * gdz);
+      ddpb = -1.0 - ((0.5 * qb.drho[al]) * gdz);
+    } else {
+      dpot = pa - pb;
+      ddpa = 1.0;
+      ddpb = -1.0;
+    }
     double mob, mpa, msa, mpb, msb;
     if (dpot >= 0.0) {
       mob = qa.rho[al] * qa.lam[al];
@@ -410,6 +421,7 @@ struct AsmArgs {
 // one kind and equal length.  Cell rows: accumulation, then the connections
 // in increasing column order (fluxes, then perforations); well rows: the
 // rate or pressure constraint.
+template <bool GRAV>
 __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const Phys &P = a.P;
@@ -431,8 +443,8 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
     double r1 = (M[1] - a.Mn[2 * r + 1]) * a.inv_dt;
     double d0 = dM[0] * a.inv_dt, d1 = dM[1] * a.inv_dt;
     double d2 = dM[2] * a.inv_dt, d3 = dM[3] * a.inv_dt;
-    int ir, jr, kr;
-    loc_ijk(P, r >> 1, ir, jr, kr);
+    int ir = 0, jr = 0, kr = 0;
+    if (GRAV) loc_ijk(P, r >> 1, ir, jr, kr);
     for (int e = e0; e < e1; ++e) {
       int d = a.col[e];
       if (d == r) continue;
@@ -442,22 +454,25 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
         double pd = a.p[d];
         Props qd;
         load_props(P, a.phi_f, a.phi_m, a.pr, d, qd);
-        double dzab;
-        if ((r >> 1) == (d >> 1)) dzab = 0.0;
-        else {
-          int id, jd, kd;
-          loc_ijk(P, d >> 1, id, jd, kd);
-          dzab = r < d ? depth(P, kr) - depth(P, kd) : depth(P, kd) - depth(P, kr);
+        double gdz = 0.0;
+        if (GRAV) {
+          double dzab;
+          if ((r >> 1) == (d >> 1)) dzab = 0.0;
+          else {
+            int id, jd, kd;
+            loc_ijk(P, d >> 1, id, jd, kd);
+            dzab = r < d ? depth(P, kr) - depth(P, kd) : depth(P, kd) - depth(P, kr);
+          }
+          gdz = P.g * dzab;
         }
-        double gdz = P.g * dzab;
         double F[2], dFa[4], dFb[4];
         if (r < d) {
-          flux(T, gdz, pc, pd, qc, qd, F, dFa, dFb);
+          flux<GRAV>(T, gdz, pc, pd, qc, qd, F, dFa, dFb);
           r0 = r0 + F[0]; r1 = r1 + F[1];
           d0 = d0 + dFa[0]; d1 = d1 + dFa[1]; d2 = d2 + dFa[2]; d3 = d3 + dFa[3];
           off[0] = dFb[0]; off[1] = dFb[1]; off[2] = dFb[2]; off[3] = dFb[3];
         } else {
-          flux(T, gdz, pd, pc, qd, qc, F, dFa, dFb);
+          flux<GRAV>(T, gdz, pd, pc, qd, qc, F, dFa, dFb);
           r0 = r0 + (-F[0]); r1 = r1 + (-F[1]);
           d0 = d0 + (-dFb[0]); d1 = d1 + (-dFb[1]); d2 = d2 + (-dFb[2]); d3 = d3 + (-dFb[3]);
           off[0] = -dFa[0]; off[1] = -dFa[1]; off[2] = -dFa[2]; off[3] = -dFa[3];
@@ -545,7 +560,8 @@ int phys_assemble(Sim *s) {
   a.well_kind = s->well_kind; a.well_target = s->well_target;
   a.val = s->A.val; a.R = s->R;
   a.inv_dt = s->inv_dt;
-  DP_LAUNCH(s, k_assemble, nblk(s->ph.nb), kBlock, 0, a);
+  if (s->ph.g != 0.0) DP_LAUNCH(s, k_assemble<true>, nblk(s->ph.nb), kBlock, 0, a);
+  else DP_LAUNCH(s, k_assemble<false>, nblk(s->ph.nb), kBlock, 0, a);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }
