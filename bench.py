@@ -33,6 +33,9 @@ METRIC = "CPR-FPF Newton-step solve time & HBM GB/s at 8M unknowns; served p99 l
 UNIT = "Newton-step solves/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TIMED_KERNEL = "k_bsr_spmv<0>"
+# DRAM bytes (read + written) per launch of TIMED_KERNEL on the 200x200x50 field, from the
+# ncu capture summarised in profiles/bsr_spmv_field200x200x50_dram.md (this kernel version)
+TIMED_TRAFFIC = {(200, 200, 50, 0): 972267264 + 112484096}
 
 
 def workload(args):
@@ -572,7 +575,8 @@ def main():
             "solve_ms_median": med, "solve_ms_p90": p90,
             "roofline": {"bound": "hbm", "kernel": "bsr_spmv (FP64 2x2 BSR, y = A x)",
                          "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": (ach / peak) if ach else None, "traffic": None,
+                         "frac": (ach / peak) if ach else None,
+                         "traffic": TIMED_TRAFFIC.get((args.nx, args.ny, args.nz, args.schur)),
                          "launches_timed": k_n,
                          "avg_launch_ms": (k_ms / k_n) if k_n else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
