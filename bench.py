@@ -487,17 +487,17 @@ def main():
     k_ms, k_n = sim.kernel_timing(reset=True)
     sim.time_kernel(None)
     # the ILU(0) and Gauss-Seidel sweeps the same way, one kernel per timestep;
-    # one sweep = one launch per colour
-    ncol = sim.colours()[1]
+    # every FGMRES iteration applies the ILU(0) twice (both CPR-FPF stages) and
+    # one V-cycle (one forward and one backward level-0 sweep)
     sweeps = {}
     for name, nbytes in sweep_bytes(sim.snb, sim.snnzb).items():
         sim.time_kernel(name)
         sim.kernel_timing(reset=True)
-        timestep(sim, opts)
+        _, its = timestep(sim, opts)
         t_ms, t_n = sim.kernel_timing(reset=True)
         sim.time_kernel(None)
-        if t_n:
-            n_sweeps = t_n / ncol
+        if t_n and its:
+            n_sweeps = 2 * its
             sweeps[name] = {"achieved_gbs": nbytes * n_sweeps / (t_ms / 1000.0) / 1e9,
                             "bytes_per_sweep": nbytes, "ms_per_sweep": t_ms / n_sweeps,
                             "launches": t_n}

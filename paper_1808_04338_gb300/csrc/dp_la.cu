@@ -351,8 +351,11 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-template <typename T, typename TR>
-__global__ void __launch_bounds__(kBlock) k_ilu_fwd_w(int r0, int r1, const int *__restrict__ perm,
+// PIVOT: the colour is the last one (no U blocks), so the backward sweep's
+// first step for it, z_r = D_r (y_r - 0), follows at once in the same launch.
+template <typename T, typename TR, bool PIVOT>
+__global__ void __launch_bounds__(kBlock) k_ilu_fwd_w(int r0, int r1, int nL,
+                                                      const int *__restrict__ perm,
                                                       const int *__restrict__ Lptr,
                                                       const int *__restrict__ colp,
                                                       const T *__restrict__ lu,
@@ -374,8 +377,18 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd_w(int r0, int r1, const int 
   s1 = warp_sum(s1);
   if (lane == 0) {
     int i = __ldg(perm + r);
-    zp[2 * (size_t)r] = T(rhs[2 * (size_t)i]) - s0;
-    zp[2 * (size_t)r + 1] = T(rhs[2 * (size_t)i + 1]) - s1;
+    T y0 = T(rhs[2 * (size_t)i]) - s0, y1 = T(rhs[2 * (size_t)i + 1]) - s1;
+    if (PIVOT) {
+      y0 = y0 - T(0);   // the backward sweep's y - (sum over no U blocks)
+      y1 = y1 - T(0);
+      T d[4];
+      V4<T>::load(lu + 4 * ((size_t)nL + r), d);
+      zp[2 * (size_t)r] = fma(d[0], y0, d[1] * y1);
+      zp[2 * (size_t)r + 1] = fma(d[2], y0, d[3] * y1);
+    } else {
+      zp[2 * (size_t)r] = y0;
+      zp[2 * (size_t)r + 1] = y1;
+    }
   }
 }
 
@@ -594,21 +607,29 @@ int ilu_factor(Sim *s) {
 // gathers it (ilu_result) while converting or accumulating.
 template <typename T, typename TR>
 static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
-  int n = s->K.n, nL = s->lu_nL;
+  int n = s->K.n, nL = s->lu_nL, nc = s->ncolour;
   T *zp = reinterpret_cast<T *>(s->ilu_zp);
-  for (int c = 0; c < s->ncolour; ++c) {
+  // the last colour is solved forward and its pivots applied in one launch:
+  // its rows have no U blocks, so that is also the backward sweep's first step
+  int last = nc - 1;
+  while (last >= 0 && s->lu_cstart[last + 1] <= s->lu_cstart[last]) --last;
+  for (int c = 0; c < nc; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
-    if (s->lu_cmaxlen[c] > kLongRow)
-      DP_LAUNCH(s, (k_ilu_fwd_w<T, TR>), nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
-                s->lu_Lptr, s->lu_colp, lu, r, zp);
+    if (c == last && s->lu_cmaxlen[c] > kLongRow)
+      DP_LAUNCH(s, (k_ilu_fwd_w<T, TR, true>), nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL,
+                s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp);
+    else if (s->lu_cmaxlen[c] > kLongRow)
+      DP_LAUNCH(s, (k_ilu_fwd_w<T, TR, false>), nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL,
+                s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp);
     else
       DP_LAUNCH(s, (k_ilu_fwd<T, TR>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
                 s->lu_Lptr, s->lu_colp, lu, r, zp);
   }
-  for (int c = s->ncolour - 1; c >= 0; --c) {
+  for (int c = nc - 1; c >= 0; --c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
+    if (c == last && s->lu_cmaxlen[c] > kLongRow) continue;   // done with the forward launch
     if (s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, k_ilu_bwd_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL, n,
                 s->lu_Uptr, s->lu_colp, lu, zp);
