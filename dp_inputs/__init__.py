@@ -36,6 +36,7 @@ RHO_W_REF = 999.55
 
 WELL_RATE_INJ = 0
 WELL_BHP = 1
+WELL_OIL_RATE = 2
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _STREAM = np.uint64(0xD1B54A32D192ED03)
@@ -63,14 +64,16 @@ def normals(seed: int, stream: int, n: int) -> np.ndarray:
 
 @dataclass
 class Well:
-    kind: int            # WELL_RATE_INJ or WELL_BHP
+    kind: int            # WELL_RATE_INJ, WELL_BHP or WELL_OIL_RATE
     i: int
     j: int
     k_top: int
     k_bot: int
-    target: float        # m^3/s (rate) or Pa (BHP)
+    target: float        # m^3/s (injector rate), Pa (BHP) or kg/s of oil (producer rate)
     rw: float = 0.25 * FT
     skin: float = 0.0
+    limit: float = 0.0   # BHP limit of a rate-controlled well (Pa), 0: none
+    wi: float = 0.0      # given well index (m^3), 0: Peaceman
 
 
 @dataclass
@@ -142,7 +145,7 @@ def _base(name, nx, ny, nz, kf_md, km_md, phi_f, phi_m, sigma, wells, seed,
         swc=0.2, sor=0.2, g=g, wells=wells,
         p0=np.full(2 * n, p0), sw0=np.full(2 * n, sw0),
         dt=dt_days * DAY, nsteps=nsteps)
-    prob.bhp0 = np.array([p0 if w.kind == WELL_RATE_INJ else w.target
+    prob.bhp0 = np.array([w.target if w.kind == WELL_BHP else p0
                           for w in wells], dtype=np.float64)
     prob.seed = seed
     return prob
@@ -271,3 +274,55 @@ def request_stream(n_requests: int = 512, rate_per_s: float = 200.0, n_real: int
     dts = np.array([1.0, 2.0, 5.0, 10.0])[
         np.minimum((splitmix64_uniform(seed, 2, k) * 4).astype(np.int64), 3)]
     return arrivals, real, dts
+
+
+LBM_FT3 = 16.01846337       # kg/m^3 per lbm/ft^3
+
+
+def paper_example(which: int, days: float = 1.0, nsteps: int = 10) -> Problem:
+    """The setups of the paper's Examples 1 (10x10x1) and 2 (10x10x3), Section
+    4: field units converted to SI, oil density at the reference pressure
+    from the stock-tank density and the formation volume factor (58.0 lbm/ft^3
+    / 1.036), rock and oil compressibility about 15 psi, gravity with depth,
+    fracture and matrix initial states, a water injector with a given well
+    index and a maximum BHP, two oil-rate producers with a minimum BHP.
+    Not given by the paper, read here: water viscosity 1 cP and
+    compressibility 3e-6/psi; Corey curves with no residual saturations;
+    transfer through the Kazemi shape factor of the grid block, with the
+    matrix's vertical permeability folded into sigma (k_m = k_m,x)."""
+    if which == 1:
+        nz, kmz, pm0, pf0, q_inj, q_oil = 1, 10.0, 2000.0, 1980.0, 500.0, 300.0
+        inj, prods, h = (4, 0), [(0, 9), (9, 9)], 102.04
+    else:
+        nz, kmz, pm0, pf0, q_inj, q_oil = 3, 100.0, 800.0, 500.0, 200.0, 500.0
+        inj, prods, h = (4, 4), [(0, 0), (9, 9)], 102.0
+    nx = ny = 10
+    n = nx * ny * nz
+    dx = dy = h * FT
+    dz = 100.0 * FT
+    kmx = 100.0
+    sigma = 4.0 * (1.0 / dx ** 2 + 1.0 / dy ** 2 + (kmz / kmx) / dz ** 2)
+    rho_o_std = 58.0 * LBM_FT3
+    wells = [Well(WELL_RATE_INJ, inj[0], inj[1], 0, 0, q_inj * BBL_DAY, limit=5.0e4 * PSI,
+                  wi=200.0 * BBL_DAY * CP / PSI)]
+    for (i, j) in prods:
+        wells.append(Well(WELL_OIL_RATE, i, j, 0, 0, q_oil * BBL_DAY * rho_o_std,
+                          rw=0.25 * FT, limit=15.0 * PSI))
+    p0 = np.empty(2 * n)
+    p0[0::2], p0[1::2] = pf0 * PSI, pm0 * PSI
+    sw0 = np.empty(2 * n)
+    sw0[0::2], sw0[1::2] = 0.01, 0.08
+    prob = Problem(
+        name=f"example{which}", nx=nx, ny=ny, nz=nz, dx=dx, dy=dy, dz=dz,
+        top_depth=2000.0 * FT - 0.5 * dz,
+        kf=np.full(n, 395.85 * MD), km=np.full(n, kmx * MD),
+        phi_f=np.full(n, 0.039585), phi_m=np.full(n, 0.1392),
+        sigma=sigma, c_rock=3e-6 / PSI, p_ref_rock=15.0 * PSI,
+        mu_o=40.0 * CP, mu_w=1.0 * CP, c_o=1.313e-5 / PSI, c_w=3e-6 / PSI,
+        rho_o_ref=rho_o_std / 1.036, rho_w_ref=62.4 * LBM_FT3, p_ref=15.0 * PSI,
+        swc=0.0, sor=0.0, g=9.80665, wells=wells, p0=p0, sw0=sw0,
+        dt=days * DAY, nsteps=nsteps)
+    prob.bhp0 = np.array([pf0 * PSI] * len(wells))
+    prob.seed = 0
+    return prob
+

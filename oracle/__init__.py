@@ -51,7 +51,8 @@ class og_fluid(C.Structure):
 class og_well(C.Structure):
     _fields_ = [("kind", C.c_int32), ("i", C.c_int32), ("j", C.c_int32),
                 ("k_top", C.c_int32), ("k_bot", C.c_int32),
-                ("target", C.c_double), ("rw", C.c_double), ("skin", C.c_double)]
+                ("target", C.c_double), ("rw", C.c_double), ("skin", C.c_double),
+                ("limit", C.c_double), ("wi", C.c_double)]
 
 
 class og_options(C.Structure):
@@ -120,6 +121,7 @@ def lib():
             getattr(L, name).argtypes = [P, P, P, P]
         L.oracle_sizes.argtypes = [P, P, P]
         L.oracle_solver_sizes.argtypes = [P, P, P]
+        L.oracle_well_controls.argtypes = [P, P, P]
         L.oracle_assemble.argtypes = [P, D]
         L.oracle_get_jacobian.argtypes = [P, P, P, P, P]
         L.oracle_get_norms.argtypes = [P, P]
@@ -176,7 +178,8 @@ class OracleSim:
         nw = len(prob.wells)
         W = (og_well * max(nw, 1))()
         for q, w in enumerate(prob.wells):
-            W[q] = og_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin)
+            W[q] = og_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin,
+                           w.limit, w.wi)
         h = C.c_void_p()
         rc = L.oracle_create(C.byref(g), C.byref(r), C.byref(f), W, nw,
                              C.byref(self.opts), C.byref(h))
@@ -245,6 +248,11 @@ class OracleSim:
         val = np.zeros((self.snnzb, 2, 2)); rhs = np.zeros(2 * self.snb)
         lib().oracle_get_decoupled(self.h, _p(val), _p(rhs))
         return val, rhs
+
+    def well_controls(self):
+        k = np.zeros(max(self.nw, 1), np.int32); t = np.zeros(max(self.nw, 1))
+        lib().oracle_well_controls(self.h, _p(k), _p(t))
+        return k[:self.nw], t[:self.nw]
 
     def colours(self):
         c = np.zeros(self.snb, np.int32)

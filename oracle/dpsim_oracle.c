@@ -991,6 +991,7 @@ typedef struct {
   double sigma, c_rock, p_ref_rock;
   double *kf, *km, *phi_f, *phi_m;
   int nwells; og_well *wells;
+  int *ctl_kind; double *ctl_target;   /* the wells' own controls (restored each timestep) */
   int nL, nc, nb;
   og_bsr J;          /* Jacobian, natural order; decoupled in place by solve (full system) */
   og_bsr K;          /* with schur: the fracture-and-well system, decoupled in place */
@@ -1236,6 +1237,25 @@ static void assemble(og_sim *s) {
       }
       s->R[2 * row] = acc - s->wells[w].target;
       dg[0] = accd;
+    } else if (s->wells[w].kind == 2) {
+      /* oil-rate producer: the oil mass leaving through the perforations
+       * (-sum of the perforation rates into the cells) equals the target */
+      double acc = 0.0, accd = 0.0;
+      for (int e = J->rowptr[row]; e < J->rowptr[row + 1]; ++e) {
+        int c = J->col[e];
+        if (c == row) continue;
+        int t = perf_of(s, c, w);
+        og_props q;
+        props(s, c, s->p[c], s->sw[c], &q);
+        double Q[2], dq[4], dqb[2];
+        perf_rate(2, s->perf[t].wi, s->p[c], pb, &q, Q, dq, dqb);
+        acc = acc + Q[0];
+        accd = accd + dqb[0];
+        double *off = J->val + 4 * (size_t)e;
+        off[0] = dq[0]; off[1] = dq[1]; off[2] = 0.0; off[3] = 0.0;
+      }
+      s->R[2 * row] = acc + s->wells[w].target;
+      dg[0] = accd;
     } else {
       s->R[2 * row] = pb - s->wells[w].target;
       dg[0] = 1.0;
@@ -1434,12 +1454,16 @@ int oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
   memcpy(s->phi_m, r->phi_m, sizeof(double) * (size_t)s->nL);
   s->wells = (og_well *)zalloc((size_t)nwells, sizeof(og_well));
   if (nwells) memcpy(s->wells, w, sizeof(og_well) * (size_t)nwells);
+  s->ctl_kind = (int *)zalloc((size_t)nwells, sizeof(int));
+  s->ctl_target = (double *)zalloc((size_t)nwells, sizeof(double));
+  for (int q = 0; q < nwells; ++q) { s->ctl_kind[q] = w[q].kind; s->ctl_target[q] = w[q].target; }
   /* perforations: fracture cells of every layer k_top..k_bot */
   s->nperf = 0;
   for (int q = 0; q < nwells; ++q) {
     const og_well *W = &w[q];
     if (W->i < 0 || W->i >= g->nx || W->j < 0 || W->j >= g->ny || W->k_top < 0 ||
-        W->k_bot >= g->nz || W->k_top > W->k_bot || W->rw <= 0.0) { oracle_destroy(s); return OG_EINVAL; }
+        W->k_bot >= g->nz || W->k_top > W->k_bot || W->rw <= 0.0 || W->kind < 0 || W->kind > 2 ||
+        W->limit < 0.0 || W->wi < 0.0) { oracle_destroy(s); return OG_EINVAL; }
     s->nperf += W->k_bot - W->k_top + 1;
   }
   s->perf = (og_perf *)zalloc((size_t)s->nperf, sizeof(og_perf));
@@ -1450,7 +1474,8 @@ int oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
       int loc = W->i + g->nx * (W->j + g->ny * k);
       s->perf[t].cell = 2 * loc;
       s->perf[t].well = q;
-      s->perf[t].wi = well_index(s->kf[loc], s->kf[loc], g->dx, g->dy, g->dz, W->rw, W->skin);
+      s->perf[t].wi = W->wi > 0.0 ? W->wi
+                                  : well_index(s->kf[loc], s->kf[loc], g->dx, g->dy, g->dz, W->rw, W->skin);
       ++t;
     }
   }
@@ -1525,6 +1550,7 @@ void oracle_destroy(void *h) {
   og_sim *s = (og_sim *)h;
   if (!s) return;
   free(s->kf); free(s->km); free(s->phi_f); free(s->phi_m); free(s->wells); free(s->perf);
+  free(s->ctl_kind); free(s->ctl_target);
   free(s->J.rowptr); free(s->J.col); free(s->J.diag); free(s->J.val);
   free(s->R); free(s->p); free(s->sw); free(s->bhp); free(s->pn); free(s->swn); free(s->bhpn);
   free(s->Mn); free(s->y); free(s->bh); free(s->colour); free(s->Ap.val);
@@ -1541,6 +1567,12 @@ int oracle_sizes(void *h, int32_t *nb, int32_t *nnzb) {
   og_sim *s = (og_sim *)h;
   *nb = s->nb; *nnzb = s->J.nnz;
   return 0;
+}
+
+int oracle_well_controls(void *h, int32_t *kind, double *target) {
+  og_sim *s = (og_sim *)h;
+  for (int w = 0; w < s->nwells; ++w) { kind[w] = s->wells[w].kind; target[w] = s->wells[w].target; }
+  return s->nwells;
 }
 
 int oracle_solver_sizes(void *h, int32_t *nb, int32_t *nnzb) {
@@ -1779,8 +1811,31 @@ int oracle_get_update(void *h, double *y) {
 /* One backward-Euler timestep by Algorithm 1: assemble; stop when
  * ||R~|| <= tol ||R~_0|| or ||R~||_inf <= atol; otherwise solve and update.
  * On failure the state of the old time level is restored. */
+/* Well controls (the examples' wells have rate targets and BHP limits): a
+ * timestep starts with every well on its own control; after a Newton update
+ * an injector whose BHP exceeds its limit, or an oil-rate producer whose BHP
+ * falls below its limit, switches to BHP control at the limit for the rest
+ * of the timestep.  Returns the number of wells switched. */
+static int switch_controls(og_sim *s) {
+  int n = 0;
+  for (int w = 0; w < s->nwells; ++w) {
+    og_well *W = &s->wells[w];
+    if (W->limit <= 0.0) continue;
+    if ((W->kind == 0 && s->bhp[w] > W->limit) || (W->kind == 2 && s->bhp[w] < W->limit)) {
+      W->kind = 1;
+      W->target = W->limit;
+      ++n;
+    }
+  }
+  return n;
+}
+
 int oracle_advance(void *h, double dt, og_stats *st) {
   og_sim *s = (og_sim *)h;
+  for (int w = 0; w < s->nwells; ++w) {
+    s->wells[w].kind = s->ctl_kind[w];
+    s->wells[w].target = s->ctl_target[w];
+  }
   save_old(s);
   s->newton_iter = 0;
   s->prev_res = 0.0; s->prev_linres = 0.0;
@@ -1795,6 +1850,7 @@ int oracle_advance(void *h, double dt, og_stats *st) {
     og_stats ls; memset(&ls, 0, sizeof(ls));
     oracle_solve_step(h, &ls);
     lin += ls.linear_iters;
+    switch_controls(s);
   }
   if (st) {
     st->newton_iters = s->newton_iter; st->linear_iters = lin; st->converged = conv;

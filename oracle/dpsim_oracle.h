@@ -30,8 +30,12 @@ typedef struct {
   double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
 } og_fluid;
 typedef struct {
-  int32_t kind, i, j, k_top, k_bot;  /* kind 0: water rate injector, 1: BHP */
-  double target, rw, skin;
+  int32_t kind, i, j, k_top, k_bot;  /* kind 0: water rate injector, 1: BHP, 2: oil-rate
+                                        producer */
+  double target, rw, skin;   /* target: m^3/s (kind 0), Pa (kind 1), oil kg/s (kind 2) */
+  double limit;              /* kinds 0 and 2: BHP limit (Pa; 0 none): an injector above
+                                it, or a producer below it, switches to BHP control */
+  double wi;                 /* > 0: well index of every perforation (m^3), else Peaceman */
 } og_well;
 typedef struct {
   double newton_tol, newton_atol; int32_t newton_max;
@@ -68,6 +72,8 @@ int  oracle_sizes(void *h, int32_t *nb, int32_t *nnzb);
 /* block rows and blocks of the system the linear solver sees (the full one,
  * or the fracture-and-well one with schur = 1) */
 int  oracle_solver_sizes(void *h, int32_t *nb, int32_t *nnzb);
+/* the wells' current controls (kind, target) after the last timestep */
+int  oracle_well_controls(void *h, int32_t *kind, double *target);
 int  oracle_set_state(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_set_iterate(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_get_state(void *h, double *p, double *sw, double *bhp);

@@ -159,11 +159,15 @@ def test_true_impes_weight_cancels_the_saturation_column_sum():
 
 # ------------------------------------------------------------------- Jacobian
 
-@pytest.mark.parametrize("g", [0.0, 9.80665])
-def test_jacobian_matches_finite_differences(g):
+@pytest.mark.parametrize("make", [lambda: small_problem(3, 2, 2, g=0.0),
+                                  lambda: small_problem(3, 2, 2, g=9.80665),
+                                  lambda: di.paper_example(1), lambda: di.paper_example(2)])
+def test_jacobian_matches_finite_differences(make):
     """Analytic J equals central differences of the residual R (Section 3:
-    Newton needs the exact Jacobian of F), columnwise, rel 1e-5."""
-    prob = small_problem(3, 2, 2, g=g)
+    Newton needs the exact Jacobian of F), columnwise, rel 1e-5; also for
+    the setups of the paper's examples (oil-rate producer rows, a given well
+    index, rock compressibility, three layers under gravity)."""
+    prob = make()
     s = O.OracleSim(prob)
     p, sw, bhp = random_interior_state(prob)
     s.set_iterate(p, sw, bhp)
@@ -192,11 +196,12 @@ def test_jacobian_matches_finite_differences(g):
 
 # --------------------------------------------------------------- conservation
 
-def test_mass_balance_every_newton_iterate():
+@pytest.mark.parametrize("make", [di.tiny, lambda: di.paper_example(2)])
+def test_mass_balance_every_newton_iterate(make):
     """Summing the cell residuals cancels every internal flux (each flux
     enters two rows with opposite signs): sum_c R_a = dM_a/dt - W_a to round
     off, for both phases, at every Newton iterate of a timestep."""
-    prob = di.tiny()
+    prob = make()
     s = O.OracleSim(prob, O.options("report"))
     for it in range(4):
         s.assemble(prob.dt)
@@ -222,6 +227,39 @@ def test_mass_conserved_over_a_converged_timestep():
     for a in range(2):
         dm, w = nr[4 + a], nr[6 + a] * prob.dt
         assert abs(dm - w) <= 1e-8 * max(abs(w), abs(dm), 1e-3)
+
+
+def test_oil_rate_producer_meets_its_target_or_switches_at_its_limit():
+    """Example 2: while every producer is on oil-rate control the oil leaving
+    the reservoir (the well term of the oil balance, summed over perforations
+    apart from the well rows) equals the sum of the targets; once a producer's
+    BHP would fall below its minimum it is on BHP control with the BHP exactly
+    at that limit, and the field then produces less oil than the targets."""
+    prob = di.paper_example(2, days=5.0)
+    s = O.OracleSim(prob, O.options("report"))
+    q_total = sum(w.target for w in prob.wells if w.kind == di.WELL_OIL_RATE)
+    assert q_total > 0.0
+    switched = False
+    for step in range(12):
+        rc, st = s.advance(prob.dt)
+        assert rc == 0
+        kinds, targets = s.well_controls()
+        p, sw, bhp = s.get_state()
+        s.assemble(prob.dt)
+        w_oil = s.norms()[6]
+        for w, W in enumerate(prob.wells):
+            if W.kind != di.WELL_OIL_RATE:
+                continue
+            if kinds[w] == di.WELL_OIL_RATE:
+                assert bhp[w] >= W.limit
+            else:
+                assert kinds[w] == di.WELL_BHP and targets[w] == W.limit and bhp[w] == W.limit
+                switched = True
+        if switched:
+            assert -w_oil < q_total * (1.0 - 1e-6)
+            break
+        assert abs(w_oil + q_total) <= 1e-6 * q_total
+    assert switched
 
 
 # ----------------------------------------------------------- closed forms
