@@ -75,12 +75,20 @@ typedef struct {
 /* Vertical well perforating the fracture cells of column (i, j), layers
  * k_top..k_bot (Section 2, perforation rate and well index).  kind
  * DP_WELL_RATE_INJ: water injector at a reservoir-volume rate target (m^3/s);
- * DP_WELL_BHP: producer at a bottom-hole pressure target (Pa).  rw: wellbore
- * radius (m); skin: skin factor. */
-typedef enum { DP_WELL_RATE_INJ = 0, DP_WELL_BHP = 1 } dp_well_kind;
+ * DP_WELL_BHP: well at a bottom-hole pressure target (Pa);
+ * DP_WELL_OIL_RATE: producer at an oil mass-rate target (kg/s, the oil
+ * leaving through its perforations; Section 5's producers).  rw: wellbore
+ * radius (m); skin: skin factor.  limit (Pa, 0: none; kinds 0 and 2): a
+ * maximum BHP for an injector, a minimum BHP for an oil-rate producer; after
+ * each Newton update of sim_advance a well past its limit switches to BHP
+ * control at the limit for the rest of that timestep (each timestep starts on
+ * the well's own control).  wi (m^3): > 0 gives every perforation this well
+ * index, 0 takes Peaceman's from kf, dx, dy, dz, rw and skin. */
+typedef enum { DP_WELL_RATE_INJ = 0, DP_WELL_BHP = 1, DP_WELL_OIL_RATE = 2 } dp_well_kind;
 typedef struct {
   int32_t kind, i, j, k_top, k_bot;
   double target, rw, skin;
+  double limit, wi;
 } dp_well;
 
 /* Device memory provider.  alloc returns device memory usable on `stream`
@@ -317,6 +325,11 @@ int sim_get_update(dp_sim *sim, double *y);
 int sim_get_decoupled(dp_sim *sim, double *val, double *rhs);
 int sim_get_colours(dp_sim *sim, int32_t *colour);
 int sim_well_index(dp_sim *sim, double *wi);
+/* The wells' current controls: kind[nwells] and target[nwells] (host
+ * arrays; synchronises).  After sim_advance they show the controls the
+ * timestep ended on (a switched well: DP_WELL_BHP at its limit).
+ * DP_EINVAL: sim NULL, or kind/target NULL with nwells > 0. */
+int sim_well_controls(dp_sim *sim, int32_t *kind, double *target);
 
 /* AMG hierarchy of the pressure stage after the first sim_solve_step:
  * level sizes (returns the number of levels) and level arrays (CSR of the

@@ -130,6 +130,7 @@ inline int nblk(long long n, int b = kBlock) {
 // oracle's bit for bit)
 int phys_build_pattern(Sim *s);
 int phys_save_old(Sim *s);
+int phys_well_controls(Sim *s, bool restore);
 int phys_assemble(Sim *s);
 int phys_norms(Sim *s);
 int phys_decouple_extract(Sim *s);
@@ -202,8 +203,11 @@ struct Sim {
   double *kf = nullptr, *km = nullptr, *phi_f = nullptr, *phi_m = nullptr;
   int *perf_cell = nullptr, *perf_well = nullptr;   // sorted by (cell, well)
   double *perf_wi = nullptr;
-  int *well_kind = nullptr;
-  double *well_target = nullptr;
+  int *well_kind = nullptr;                          // current controls (switched by
+  double *well_target = nullptr;                     //   sim_advance)
+  int *well_ctl_kind = nullptr;                      // the wells' own controls
+  double *well_ctl_target = nullptr, *well_limit = nullptr;
+  bool well_limits = false;                          // some well has a BHP limit
   std::vector<double> wi_host;                       // per perforation, well order
   Bsr A;                                             // Jacobian, decoupled in place
   double *trans = nullptr;                           // per entry: T or WI

@@ -277,7 +277,7 @@ int phys_build_pattern(Sim *s) {
     pw_start[w] = q;
     for (int k = W.k_top; k <= W.k_bot; ++k, ++q) {
       pw_cell[q] = 2 * locs[q];
-      pw_wi[q] = well_index_host(kfp[q], kfp[q], P.dx, P.dy, P.dz, W.rw, W.skin);
+      pw_wi[q] = W.wi > 0.0 ? W.wi : well_index_host(kfp[q], kfp[q], P.dx, P.dy, P.dz, W.rw, W.skin);
       s->wi_host[q] = pw_wi[q];
     }
   }
@@ -512,6 +512,24 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
     }
     a.R[2 * r] = acc - a.well_target[w];
     dg[0] = accd;
+  } else if (a.well_kind[w] == 2) {
+    // oil-rate producer: the perforation oil rates into the cells sum to
+    // minus the target (the oil leaving the reservoir equals the target)
+    double acc = 0.0, accd = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      int c = a.col[e];
+      if (c == r) continue;
+      Props q;
+      load_props(P, a.phi_f, a.phi_m, a.pr, c, q);
+      double Q[2], dq[4], dqb[2];
+      perf_rate(2, a.trans[e], a.p[c], pb, q, Q, dq, dqb);
+      acc = acc + Q[0];
+      accd = accd + dqb[0];
+      double *off = a.val + 4 * (size_t)e;
+      off[0] = dq[0]; off[1] = dq[1]; off[2] = 0.0; off[3] = 0.0;
+    }
+    a.R[2 * r] = acc + a.well_target[w];
+    dg[0] = accd;
   } else {
     for (int e = e0; e < e1; ++e) {
       if (a.col[e] == r) continue;
@@ -546,6 +564,36 @@ int phys_save_old(Sim *s) {
   int n = std::max(P.nc, P.nw);
   DP_LAUNCH(s, k_save_old, nblk(n), kBlock, 0, P, s->phi_f, s->phi_m, s->p, s->sw, s->bhp, s->pn,
             s->swn, s->bhpn, s->Mn);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// Well controls.  restore: every well back on its own control (start of a
+// timestep).  Otherwise, after a Newton update: an injector above its BHP
+// limit, or an oil-rate producer below it, goes on BHP control at the limit.
+__global__ void k_well_controls(int nw, int restore, const int *ctl_kind, const double *ctl_target,
+                                const double *limit, const double *bhp, int *kind, double *target) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nw) return;
+  if (restore) {
+    kind[w] = ctl_kind[w];
+    target[w] = ctl_target[w];
+    return;
+  }
+  double lim = limit[w];
+  if (lim <= 0.0) return;
+  int k = kind[w];
+  if ((k == 0 && bhp[w] > lim) || (k == 2 && bhp[w] < lim)) {
+    kind[w] = 1;
+    target[w] = lim;
+  }
+}
+
+int phys_well_controls(Sim *s, bool restore) {
+  if (s->ph.nw == 0) return DP_OK;
+  DP_LAUNCH(s, k_well_controls, nblk(s->ph.nw), kBlock, 0, s->ph.nw, restore ? 1 : 0,
+            s->well_ctl_kind, s->well_ctl_target, s->well_limit, s->bhp, s->well_kind,
+            s->well_target);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }

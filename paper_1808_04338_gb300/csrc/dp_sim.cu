@@ -128,8 +128,9 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   if (!rock->kf || !rock->km || !rock->phi_f || !rock->phi_m) return DP_EINVAL;
   for (int w = 0; w < nwells; ++w) {
     const dp_well &W = wells[w];
-    if (W.kind < 0 || W.kind > 1 || W.i < 0 || W.i >= grid->nx || W.j < 0 || W.j >= grid->ny ||
-        W.k_top < 0 || W.k_bot >= grid->nz || W.k_top > W.k_bot || !(W.rw > 0.0))
+    if (W.kind < 0 || W.kind > 2 || W.i < 0 || W.i >= grid->nx || W.j < 0 || W.j >= grid->ny ||
+        W.k_top < 0 || W.k_bot >= grid->nz || W.k_top > W.k_bot || !(W.rw > 0.0) ||
+        !(W.limit >= 0.0) || !(W.wi >= 0.0) || !std::isfinite(W.limit) || !std::isfinite(W.wi))
       return DP_EINVAL;
   }
   dp_sim *s = new (std::nothrow) dp_sim();
@@ -159,10 +160,14 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   s->phi_m = (double *)dalloc(s, nl8);
   s->well_kind = (int *)dalloc(s, (size_t)std::max(nwells, 1) * 4);
   s->well_target = (double *)dalloc(s, (size_t)std::max(nwells, 1) * 8);
+  s->well_ctl_kind = (int *)dalloc(s, (size_t)std::max(nwells, 1) * 4);
+  s->well_ctl_target = (double *)dalloc(s, (size_t)std::max(nwells, 1) * 8);
+  s->well_limit = (double *)dalloc(s, (size_t)std::max(nwells, 1) * 8);
   s->counter = (int *)dalloc(s, 64);
   s->omega = (double *)dalloc(s, 8);
   s->rho_bits = (unsigned long long *)dalloc(s, 8);
   if (!s->kf || !s->km || !s->phi_f || !s->phi_m || !s->well_kind || !s->well_target ||
+      !s->well_ctl_kind || !s->well_ctl_target || !s->well_limit ||
       !s->counter || !s->omega || !s->rho_bits)
     return fail(DP_ENOMEM);
   if (cudaMallocHost(&s->h_counter, 64) != cudaSuccess ||
@@ -175,11 +180,21 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
       cudaMemcpyAsync(s->phi_m, rock->phi_m, nl8, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return fail(DP_ECUDA);
   std::vector<int> kinds(std::max(nwells, 1), 0);
-  std::vector<double> targets(std::max(nwells, 1), 0.0);
-  for (int w = 0; w < nwells; ++w) { kinds[w] = wells[w].kind; targets[w] = wells[w].target; }
+  std::vector<double> targets(std::max(nwells, 1), 0.0), limits(std::max(nwells, 1), 0.0);
+  for (int w = 0; w < nwells; ++w) {
+    kinds[w] = wells[w].kind; targets[w] = wells[w].target;
+    limits[w] = wells[w].kind == DP_WELL_BHP ? 0.0 : wells[w].limit;
+    if (limits[w] > 0.0) s->well_limits = true;
+  }
   if (cudaMemcpyAsync(s->well_kind, kinds.data(), kinds.size() * 4, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       cudaMemcpyAsync(s->well_target, targets.data(), targets.size() * 8, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
+      cudaMemcpyAsync(s->well_ctl_kind, kinds.data(), kinds.size() * 4, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
+      cudaMemcpyAsync(s->well_ctl_target, targets.data(), targets.size() * 8,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->well_limit, limits.data(), limits.size() * 8, cudaMemcpyHostToDevice,
                       st) != cudaSuccess ||
       cudaMemsetAsync(s->counter, 0, 64, st) != cudaSuccess)
     return fail(DP_ECUDA);
@@ -369,6 +384,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
 
 extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
   if (!s || !(dt > 0.0)) return DP_EINVAL;
+  if (s->well_limits) DP_TRY(phys_well_controls(s, true));
   DP_TRY(phys_save_old(s));
   new_timestep(s);
   int lin = 0;
@@ -387,6 +403,7 @@ extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
     lin += ls.linear_iters;
     ms_setup += ls.ms_setup;
     ms_solve += ls.ms_solve;
+    if (s->well_limits) DP_TRY(phys_well_controls(s, false));
   }
   dp_stats &L = s->last;
   L.newton_iters = s->newton_iter; L.linear_iters = lin; L.converged = conv;
@@ -504,6 +521,16 @@ extern "C" int sim_get_decoupled(dp_sim *s, double *val, double *rhs) {
     if (rc != DP_OK) { s->fail(rc, "sim_get_decoupled"); return rc; }
   }
   if (rhs) DP_CUDA(s, cudaMemcpyAsync(rhs, s->bh, (size_t)s->K.n * 16, cudaMemcpyDefault, s->stream));
+  DP_CUDA(s, cudaStreamSynchronize(s->stream));
+  return check(s);
+}
+
+extern "C" int sim_well_controls(dp_sim *s, int32_t *kind, double *target) {
+  if (!s || (s->ph.nw > 0 && (!kind || !target))) return DP_EINVAL;
+  if (s->ph.nw == 0) return DP_OK;
+  DP_CUDA(s, cudaMemcpyAsync(kind, s->well_kind, (size_t)s->ph.nw * 4, cudaMemcpyDefault, s->stream));
+  DP_CUDA(s, cudaMemcpyAsync(target, s->well_target, (size_t)s->ph.nw * 8, cudaMemcpyDefault,
+                             s->stream));
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
   return check(s);
 }

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdpsim.so")
 
 DP_OK, DP_EINVAL, DP_ENOMEM, DP_ECUDA, DP_ELINEAR, DP_ENEWTON, DP_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-WELL_RATE_INJ, WELL_BHP = 0, 1
+WELL_RATE_INJ, WELL_BHP, WELL_OIL_RATE = 0, 1, 2
 
 
 class dp_grid(C.Structure):
@@ -40,7 +40,8 @@ class dp_fluid(C.Structure):
 class dp_well(C.Structure):
     _fields_ = [("kind", C.c_int32), ("i", C.c_int32), ("j", C.c_int32),
                 ("k_top", C.c_int32), ("k_bot", C.c_int32), ("target", C.c_double),
-                ("rw", C.c_double), ("skin", C.c_double)]
+                ("rw", C.c_double), ("skin", C.c_double), ("limit", C.c_double),
+                ("wi", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -131,6 +132,7 @@ def load():
     L.sim_get_decoupled.argtypes = [P, P, P]
     L.sim_get_colours.argtypes = [P, P]
     L.sim_well_index.argtypes = [P, P]
+    L.sim_well_controls.argtypes = [P, P, P]
     L.sim_amg_level_info.argtypes = [P, I, P, P, P]
     L.sim_amg_level_arrays.argtypes = [P, I, P, P, P, P, P]
     L.sim_time_kernel.argtypes = [P, C.c_char_p]
@@ -250,7 +252,8 @@ def _inputs(prob):
     nw = len(prob.wells)
     W = (dp_well * max(nw, 1))()
     for q, w in enumerate(prob.wells):
-        W[q] = dp_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin)
+        W[q] = dp_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin, w.limit,
+                       w.wi)
     return g, r, f, W, nw, keep
 
 
@@ -361,7 +364,8 @@ class Sim:
         nw = len(prob.wells)
         W = (dp_well * max(nw, 1))()
         for q, w in enumerate(prob.wells):
-            W[q] = dp_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin)
+            W[q] = dp_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin, w.limit,
+                       w.wi)
         self._alloc = TorchAllocator(torch.cuda.current_device()) if use_torch_alloc else None
         h = C.c_void_p()
         rc = L.sim_create(C.byref(g), C.byref(r), C.byref(f), W, nw, C.byref(self.opts),
@@ -483,6 +487,12 @@ class Sim:
         wi = np.zeros(sum(w.k_bot - w.k_top + 1 for w in self.prob.wells) + 1)
         n = self._check(load().sim_well_index(self.h, _p(wi)), "sim_well_index")
         return wi[:n]
+
+    def well_controls(self):
+        """The wells' current (kind, target), as sim_well_controls."""
+        k = np.zeros(max(self.nw, 1), np.int32); t = np.zeros(max(self.nw, 1))
+        self._check(load().sim_well_controls(self.h, _p(k), _p(t)), "sim_well_controls")
+        return k[:self.nw], t[:self.nw]
 
     def amg_levels(self):
         L = load()

@@ -63,6 +63,16 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert L.srv_create(2, 0, ctypes.byref(o), ctypes.byref(srv)) == dpsim.DP_EINVAL
     assert L.srv_submit(None, 0, 1.0, None) == dpsim.DP_EINVAL
     assert L.sim_advance_many(None, 2, None, 0, None, None) == dpsim.DP_EINVAL
+    assert L.sim_well_controls(None, None, None) == dpsim.DP_EINVAL
+    # wells: unknown control kind, negative limit, negative well index
+    import dataclasses
+    import dp_inputs as di
+    prob = di.paper_example(2)
+    for bad in (dict(kind=3), dict(limit=-1.0), dict(wi=-1.0), dict(limit=float("nan"))):
+        wells = [dataclasses.replace(prob.wells[0], **bad)] + list(prob.wells[1:])
+        g, r, f, W, nw, keep = dpsim._inputs(dataclasses.replace(prob, wells=wells))
+        assert L.sim_create(ctypes.byref(g), ctypes.byref(r), ctypes.byref(f), W, nw,
+                            ctypes.byref(o), None, None, ctypes.byref(out)) == dpsim.DP_EINVAL, bad
 
 
 def test_oracle_is_not_linked_into_the_library(lib):

@@ -65,7 +65,8 @@ def interior(prob, seed=7):
 
 @pytest.mark.parametrize("make", [di.tiny, lambda: small(7, 5, 3), lambda: small(1, 1, 1, wells="bhp"),
                                   lambda: small(9, 1, 1), lambda: small(4, 3, 2, wells="none"),
-                                  lambda: small(3, 4, 5, g=9.80665)])
+                                  lambda: small(3, 4, 5, g=9.80665),
+                                  lambda: di.paper_example(1), lambda: di.paper_example(2)])
 def test_jacobian_residual_bit_exact(make):
     prob = make()
     g, o = pair(prob)
@@ -217,6 +218,30 @@ def test_edge_case_steps(make):
         rco, _ = o.advance(prob.dt)
         assert rcg == rco == 0
         state_close(g, o, prob)
+
+
+@pytest.mark.parametrize("example,days,nsteps", [(1, 5.0, 8), (2, 5.0, 6)])
+def test_paper_example_timesteps_and_well_switching(example, days, nsteps):
+    """The setups of the paper's two examples (oil-rate producers with a
+    minimum BHP, an injector with a given well index and a maximum BHP,
+    three layers under gravity in the second): every timestep's state and
+    the controls it ended on match the oracle; in the second example both
+    producers reach their minimum BHP and go on BHP control."""
+    prob = di.paper_example(example, days=days)
+    g, o = pair(prob)
+    switched = False
+    for step in range(nsteps):
+        rcg, stg = g.advance(prob.dt)
+        rco, sto = o.advance(prob.dt)
+        assert rcg == rco == 0, step
+        assert stg.newton_iters == sto.newton_iters, step
+        state_close(g, o, prob)
+        kg, tg = g.well_controls()
+        ko, to = o.well_controls()
+        np.testing.assert_array_equal(kg, ko)
+        np.testing.assert_array_equal(tg, to)
+        switched = switched or bool((kg == di.WELL_BHP).any())
+    assert switched == (example == 2)
 
 
 def test_layered_200k_first_step_parity():
