@@ -330,6 +330,13 @@ int sim_well_index(dp_sim *sim, double *wi);
  * timestep ended on (a switched well: DP_WELL_BHP at its limit).
  * DP_EINVAL: sim NULL, or kind/target NULL with nwells > 0. */
 int sim_well_controls(dp_sim *sim, int32_t *kind, double *target);
+/* Per well, the oil and water mass rates (kg/s, positive into the
+ * reservoir: an injector's water rate is > 0, a producer's rates are <= 0)
+ * summed over its perforations at the current state with the controls in
+ * force (Section 2, perforation rate).  q_oil[nwells], q_water[nwells]: host
+ * or device arrays; synchronises.  DP_EINVAL: sim NULL, or an array NULL
+ * with nwells > 0. */
+int sim_well_rates(dp_sim *sim, double *q_oil, double *q_water);
 
 /* AMG hierarchy of the pressure stage after the first sim_solve_step:
  * level sizes (returns the number of levels) and level arrays (CSR of the

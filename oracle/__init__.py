@@ -122,6 +122,7 @@ def lib():
         L.oracle_sizes.argtypes = [P, P, P]
         L.oracle_solver_sizes.argtypes = [P, P, P]
         L.oracle_well_controls.argtypes = [P, P, P]
+        L.oracle_well_rates.argtypes = [P, P, P]
         L.oracle_assemble.argtypes = [P, D]
         L.oracle_get_jacobian.argtypes = [P, P, P, P, P]
         L.oracle_get_norms.argtypes = [P, P]
@@ -253,6 +254,12 @@ class OracleSim:
         k = np.zeros(max(self.nw, 1), np.int32); t = np.zeros(max(self.nw, 1))
         lib().oracle_well_controls(self.h, _p(k), _p(t))
         return k[:self.nw], t[:self.nw]
+
+    def well_rates(self):
+        """Per well (oil, water) mass rates, kg/s, positive into the reservoir."""
+        qo = np.zeros(max(self.nw, 1)); qw = np.zeros(max(self.nw, 1))
+        lib().oracle_well_rates(self.h, _p(qo), _p(qw))
+        return qo[:self.nw], qw[:self.nw]
 
     def colours(self):
         c = np.zeros(self.snb, np.int32)

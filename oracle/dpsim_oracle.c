@@ -1575,6 +1575,29 @@ int oracle_well_controls(void *h, int32_t *kind, double *target) {
   return s->nwells;
 }
 
+/* The perforation rates of Section 2 (WI rho_alpha lambda_alpha (p_b - p)
+ * for a producer, WI rho_w lambda_t (p_b - p) for a water injector), summed
+ * per well over its perforations from the top layer down. */
+int oracle_well_rates(void *h, double *q_oil, double *q_water) {
+  og_sim *s = (og_sim *)h;
+  for (int w = 0; w < s->nwells; ++w) {
+    double qo = 0.0, qw = 0.0;
+    for (int t = 0; t < s->nperf; ++t) {
+      if (s->perf[t].well != w) continue;
+      int c = s->perf[t].cell;
+      og_props q;
+      props(s, c, s->p[c], s->sw[c], &q);
+      double Q[2], dq[4], dqb[2];
+      perf_rate(s->wells[w].kind, s->perf[t].wi, s->p[c], s->bhp[w], &q, Q, dq, dqb);
+      qo = qo + Q[0];
+      qw = qw + Q[1];
+    }
+    q_oil[w] = qo;
+    q_water[w] = qw;
+  }
+  return s->nwells;
+}
+
 int oracle_solver_sizes(void *h, int32_t *nb, int32_t *nnzb) {
   og_sim *s = (og_sim *)h;
   const og_bsr *A = solver_op(s);

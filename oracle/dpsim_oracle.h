@@ -74,6 +74,9 @@ int  oracle_sizes(void *h, int32_t *nb, int32_t *nnzb);
 int  oracle_solver_sizes(void *h, int32_t *nb, int32_t *nnzb);
 /* the wells' current controls (kind, target) after the last timestep */
 int  oracle_well_controls(void *h, int32_t *kind, double *target);
+/* per well, the oil and water mass rates (kg/s, positive into the reservoir)
+ * summed over its perforations at the current state and controls */
+int  oracle_well_rates(void *h, double *q_oil, double *q_water);
 int  oracle_set_state(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_set_iterate(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_get_state(void *h, double *p, double *sw, double *bhp);

@@ -131,6 +131,7 @@ inline int nblk(long long n, int b = kBlock) {
 int phys_build_pattern(Sim *s);
 int phys_save_old(Sim *s);
 int phys_well_controls(Sim *s, bool restore);
+int phys_well_rates(Sim *s, double *q);   // device q[2 nw]: oil rates, then water rates
 int phys_assemble(Sim *s);
 int phys_norms(Sim *s);
 int phys_decouple_extract(Sim *s);

@@ -568,6 +568,40 @@ int phys_save_old(Sim *s) {
   return DP_OK;
 }
 
+// Per well, the oil and water mass rates into the reservoir summed over its
+// perforations (Section 2's perforation rates).  One thread per well; the
+// perforations are sorted by (cell, well), so a well's own perforations come
+// in increasing cell order, from the top layer down.
+__global__ void k_well_rates(Phys P, const double *phi_f, const double *phi_m, const double *p,
+                             const double *sw, const double *bhp, const int *perf_cell,
+                             const int *perf_well, const double *perf_wi, int np,
+                             const int *well_kind, double *q_oil, double *q_water) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= P.nw) return;
+  double qo = 0.0, qw = 0.0;
+  for (int t = 0; t < np; ++t) {
+    if (perf_well[t] != w) continue;
+    int c = perf_cell[t];
+    Props q;
+    props(P, phi_f, phi_m, c, p[c], sw[c], q);
+    double Q[2], dq[4], dqb[2];
+    perf_rate(well_kind[w], perf_wi[t], p[c], bhp[w], q, Q, dq, dqb);
+    qo = qo + Q[0];
+    qw = qw + Q[1];
+  }
+  q_oil[w] = qo;
+  q_water[w] = qw;
+}
+
+int phys_well_rates(Sim *s, double *q) {
+  if (s->ph.nw == 0) return DP_OK;
+  DP_LAUNCH(s, k_well_rates, nblk(s->ph.nw), kBlock, 0, s->ph, s->phi_f, s->phi_m, s->p, s->sw,
+            s->bhp, s->perf_cell, s->perf_well, s->perf_wi, s->nperf, s->well_kind, q,
+            q + s->ph.nw);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
 // Well controls.  restore: every well back on its own control (start of a
 // timestep).  Otherwise, after a Newton update: an injector above its BHP
 // limit, or an oil-rate producer below it, goes on BHP control at the limit.

@@ -535,6 +535,23 @@ extern "C" int sim_well_controls(dp_sim *s, int32_t *kind, double *target) {
   return check(s);
 }
 
+extern "C" int sim_well_rates(dp_sim *s, double *q_oil, double *q_water) {
+  if (!s || (s->ph.nw > 0 && (!q_oil || !q_water))) return DP_EINVAL;
+  if (s->ph.nw == 0) return DP_OK;
+  size_t nw8 = (size_t)s->ph.nw * 8;
+  double *q = (double *)dalloc(s, 2 * nw8);
+  if (!q) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  int rc = phys_well_rates(s, q);
+  if (rc == DP_OK &&
+      (cudaMemcpyAsync(q_oil, q, nw8, cudaMemcpyDefault, s->stream) != cudaSuccess ||
+       cudaMemcpyAsync(q_water, q + s->ph.nw, nw8, cudaMemcpyDefault, s->stream) != cudaSuccess))
+    rc = DP_ECUDA;
+  cudaStreamSynchronize(s->stream);
+  dfree(s, q);
+  if (rc != DP_OK) { s->fail(rc, "sim_well_rates"); return rc; }
+  return check(s);
+}
+
 extern "C" int sim_get_colours(dp_sim *s, int32_t *colour) {
   if (!s || !colour) return DP_EINVAL;
   DP_CUDA(s, cudaMemcpyAsync(colour, s->colour, (size_t)s->K.n * 4, cudaMemcpyDefault, s->stream));

@@ -133,6 +133,7 @@ def load():
     L.sim_get_colours.argtypes = [P, P]
     L.sim_well_index.argtypes = [P, P]
     L.sim_well_controls.argtypes = [P, P, P]
+    L.sim_well_rates.argtypes = [P, P, P]
     L.sim_amg_level_info.argtypes = [P, I, P, P, P]
     L.sim_amg_level_arrays.argtypes = [P, I, P, P, P, P, P]
     L.sim_time_kernel.argtypes = [P, C.c_char_p]
@@ -493,6 +494,13 @@ class Sim:
         k = np.zeros(max(self.nw, 1), np.int32); t = np.zeros(max(self.nw, 1))
         self._check(load().sim_well_controls(self.h, _p(k), _p(t)), "sim_well_controls")
         return k[:self.nw], t[:self.nw]
+
+    def well_rates(self):
+        """Per well (oil, water) mass rates, kg/s, positive into the reservoir
+        (sim_well_rates)."""
+        qo = np.zeros(max(self.nw, 1)); qw = np.zeros(max(self.nw, 1))
+        self._check(load().sim_well_rates(self.h, _p(qo), _p(qw)), "sim_well_rates")
+        return qo[:self.nw], qw[:self.nw]
 
     def amg_levels(self):
         L = load()

@@ -244,6 +244,52 @@ def test_paper_example_timesteps_and_well_switching(example, days, nsteps):
     assert switched == (example == 2)
 
 
+def schedule(total_days, dt_max_days):
+    """Timesteps of 1, 2, 4, ... days up to dt_max, the last one ending the period."""
+    t, dt, out = 0.0, 1.0, []
+    while t < total_days - 1e-9:
+        h = min(dt, total_days - t)
+        out.append(h)
+        t += h
+        dt = min(2.0 * dt, dt_max_days)
+    return out
+
+
+@pytest.mark.parametrize("example,total_days", [(1, 800.0), (2, 1600.0)])
+def test_paper_example_full_period(example, total_days):
+    """The paper's simulation periods (800 and 1600 days) in 20-day steps:
+    after every timestep the controls are equal, the states match, and the
+    per-well oil and water rates match the oracle's; every producer ends on
+    BHP control at its minimum, having produced its target before."""
+    prob = di.paper_example(example)
+    g, o = pair(prob)
+    seen_rate = np.zeros(len(prob.wells), bool)
+    for step, days in enumerate(schedule(total_days, 20.0)):
+        rcg, _ = g.advance(days * di.DAY)
+        rco, _ = o.advance(days * di.DAY)
+        assert rcg == rco == 0, step
+        state_close(g, o, prob)
+        kg, tg = g.well_controls()
+        ko, to = o.well_controls()
+        np.testing.assert_array_equal(kg, ko)
+        np.testing.assert_array_equal(tg, to)
+        qg, qo = np.concatenate(g.well_rates()), np.concatenate(o.well_rates())
+        assert np.abs(qg - qo).max() <= 1e-6 * np.abs(qo).max(), step
+        seen_rate |= kg == di.WELL_OIL_RATE
+    assert (kg[1:] == di.WELL_BHP).all() and seen_rate[1:].all()
+
+
+def test_well_rates_bit_exact_at_the_same_state():
+    prob = di.paper_example(2)
+    g, o = pair(prob)
+    for state in (None, interior(prob, seed=3)):
+        if state is not None:
+            g.set_state(*state)
+            o.set_state(*state)
+        for a, b in zip(g.well_rates(), o.well_rates()):
+            assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
 def test_layered_200k_first_step_parity():
     """100x100x10 (200k cells): bit-exact assembly and AMG setup, then one
     timestep of Newton in report mode on both sides."""

@@ -246,14 +246,23 @@ def test_oil_rate_producer_meets_its_target_or_switches_at_its_limit():
         kinds, targets = s.well_controls()
         p, sw, bhp = s.get_state()
         s.assemble(prob.dt)
-        w_oil = s.norms()[6]
+        nr = s.norms()
+        w_oil = nr[6]
+        q_oil, q_wat = s.well_rates()
+        # the per-well rates add up to the well terms of the phase balances
+        assert abs(q_oil.sum() - nr[6]) <= 1e-12 * np.abs(q_oil).sum()
+        assert abs(q_wat.sum() - nr[7]) <= 1e-12 * np.abs(q_wat).sum()
+        assert q_wat[0] > 0.0 and q_oil[0] == 0.0          # the injector injects water only
         for w, W in enumerate(prob.wells):
             if W.kind != di.WELL_OIL_RATE:
                 continue
+            assert q_oil[w] < 0.0 and q_wat[w] <= 0.0
             if kinds[w] == di.WELL_OIL_RATE:
                 assert bhp[w] >= W.limit
+                assert abs(-q_oil[w] - W.target) <= 1e-6 * W.target
             else:
                 assert kinds[w] == di.WELL_BHP and targets[w] == W.limit and bhp[w] == W.limit
+                assert -q_oil[w] < W.target
                 switched = True
         if switched:
             assert -w_oil < q_total * (1.0 - 1e-6)
