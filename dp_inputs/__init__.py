@@ -110,6 +110,21 @@ class Problem:
     bhp0: np.ndarray | None = None
     dt: float = DAY
     nsteps: int = 1
+    # capillary pressure p_cow(s_w) per continuum: None, or an (n, 2) array of
+    # (s_w, p_cow in Pa) points with s_w strictly ascending
+    pc_f: np.ndarray | None = None
+    pc_m: np.ndarray | None = None
+
+    def pc_tables(self):
+        """(n, contiguous float64 table) of the fracture and matrix curves."""
+        out = []
+        for t in (self.pc_f, self.pc_m):
+            if t is None:
+                out.append((0, np.zeros(2)))
+            else:
+                a = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1, 2))
+                out.append((a.shape[0], a.reshape(-1)))
+        return out
 
     @property
     def n_loc(self) -> int:

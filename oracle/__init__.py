@@ -45,7 +45,7 @@ class og_rock(C.Structure):
 class og_fluid(C.Structure):
     _fields_ = [(n, C.c_double) for n in
                 ("mu_o", "mu_w", "c_o", "c_w", "rho_o_ref", "rho_w_ref", "p_ref",
-                 "swc", "sor", "g")]
+                 "swc", "sor", "g")] + [("pc_n", C.c_int32 * 2), ("pc_table", C.c_void_p * 2)]
 
 
 class og_well(C.Structure):
@@ -123,6 +123,8 @@ def lib():
         L.oracle_solver_sizes.argtypes = [P, P, P]
         L.oracle_well_controls.argtypes = [P, P, P]
         L.oracle_well_rates.argtypes = [P, P, P]
+        L.oracle_cap_pressure.argtypes = [C.c_int32, P, C.c_double, P, P]
+        L.oracle_cap_pressure.restype = None
         L.oracle_assemble.argtypes = [P, D]
         L.oracle_get_jacobian.argtypes = [P, P, P, P, P]
         L.oracle_get_norms.argtypes = [P, P]
@@ -176,6 +178,10 @@ class OracleSim:
                     prob.p_ref_rock)
         f = og_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref,
                      prob.rho_w_ref, prob.p_ref, prob.swc, prob.sor, prob.g)
+        for k, (n, tab) in enumerate(prob.pc_tables()):
+            self._keep.append(tab)
+            f.pc_n[k] = n
+            f.pc_table[k] = tab.ctypes.data
         nw = len(prob.wells)
         W = (og_well * max(nw, 1))()
         for q, w in enumerate(prob.wells):
@@ -336,6 +342,14 @@ class OracleAMG:
             if lev >= nl:
                 break
         return out
+
+
+def cap_pressure(table, sw):
+    """p_cow(s_w) and its slope from an (n, 2) table of (s_w, p_cow) points."""
+    t = np.ascontiguousarray(np.asarray(table, np.float64).reshape(-1, 2))
+    pc, dpc = C.c_double(), C.c_double()
+    lib().oracle_cap_pressure(t.shape[0], _p(t), float(sw), C.byref(pc), C.byref(dpc))
+    return pc.value, dpc.value
 
 
 def greedy_colour(rowptr, col):

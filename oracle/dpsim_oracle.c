@@ -992,6 +992,7 @@ typedef struct {
   double *kf, *km, *phi_f, *phi_m;
   int nwells; og_well *wells;
   int *ctl_kind; double *ctl_target;   /* the wells' own controls (restored each timestep) */
+  int cap; double *pc_own[2];          /* some p_cow table given; the tables (copies) */
   int nL, nc, nb;
   og_bsr J;          /* Jacobian, natural order; decoupled in place by solve (full system) */
   og_bsr K;          /* with schur: the fracture-and-well system, decoupled in place */
@@ -1064,7 +1065,23 @@ static double conn_trans(const og_sim *s, int a, int b, double *dzab) {
  * derivatives. */
 typedef struct {
   double rho[2], drho[2], phi, dphi, lam[2], dlam[2];
+  double pc, dpc;              /* p_cow(s_w) of the cell's continuum and d/ds_w */
 } og_props;
+
+/* Capillary pressure p_cow(s_w) (Section 2: p_w = p_o - p_cow(s_w)) from a
+ * table of (s_w, p_cow) pairs: linear between neighbouring points, constant
+ * (zero slope) below the first and above the last; no table: zero. */
+static void cap_pressure(int n, const double *t, double sw, double *pc, double *dpc) {
+  if (n == 0) { *pc = 0.0; *dpc = 0.0; return; }
+  if (sw <= t[0]) { *pc = t[1]; *dpc = 0.0; return; }
+  if (sw >= t[2 * (n - 1)]) { *pc = t[2 * n - 1]; *dpc = 0.0; return; }
+  int k = 0;
+  while (sw >= t[2 * (k + 1)]) ++k;      /* t[2k] <= sw < t[2k + 2] */
+  double ds = t[2 * k + 2] - t[2 * k];
+  double dp = t[2 * k + 3] - t[2 * k + 1];
+  *dpc = dp / ds;
+  *pc = t[2 * k + 1] + dp * ((sw - t[2 * k]) / ds);
+}
 
 static void props(const og_sim *s, int c, double p, double sw, og_props *q) {
   int loc = c / 2;
@@ -1087,6 +1104,8 @@ static void props(const og_sim *s, int c, double p, double sw, og_props *q) {
   q->dlam[1] = ((2.0 * S) * dS) * inv_mu_w;
   q->lam[0] = (so * so) * inv_mu_o;
   q->dlam[0] = (-((2.0 * so) * dS)) * inv_mu_o;
+  int k = c % 2;
+  cap_pressure(s->f.pc_n[k], s->f.pc_table[k], sw, &q->pc, &q->dpc);
 }
 
 /* Mass of each phase in a cell, V phi rho s, and its derivatives. */
@@ -1105,14 +1124,18 @@ static void accumulation(const og_sim *s, int c, double sw, const og_props *q,
 }
 
 /* Mass flux from a to b (a < b) of each phase, F = T (rho lambda)_up dPhi
- * with dPhi = p_a - p_b - rho_avg g (z_a - z_b); upstream a when dPhi >= 0.
+ * with dPhi = p_alpha,a - p_alpha,b - rho_avg g (z_a - z_b), the phase
+ * pressures p_o = p and p_w = p - p_cow(s_w); upstream a when dPhi >= 0.
  * dFa, dFb: derivatives with respect to (p, sw) of a and of b, laid out as
  * [phase][variable]. */
 static void flux(double T, double gdz, double pa, double pb,
-                 const og_props *qa, const og_props *qb,
+                 const og_props *qa, const og_props *qb, int cap,
                  double F[2], double dFa[4], double dFb[4]) {
   for (int al = 0; al < 2; ++al) {
-    double dpot = (pa - pb) - ((0.5 * (qa->rho[al] + qb->rho[al])) * gdz);
+    int capw = cap && al == 1;                  /* water with a p_cow table */
+    double ppa = capw ? pa - qa->pc : pa;       /* phase pressures */
+    double ppb = capw ? pb - qb->pc : pb;
+    double dpot = (ppa - ppb) - ((0.5 * (qa->rho[al] + qb->rho[al])) * gdz);
     double ddpa = 1.0 - ((0.5 * qa->drho[al]) * gdz);
     double ddpb = -1.0 - ((0.5 * qb->drho[al]) * gdz);
     double mob, mpa, msa, mpb, msb;
@@ -1127,9 +1150,14 @@ static void flux(double T, double gdz, double pa, double pb,
     }
     F[al] = (T * mob) * dpot;
     dFa[2 * al + 0] = T * ((mpa * dpot) + (mob * ddpa));
-    dFa[2 * al + 1] = T * (msa * dpot);
     dFb[2 * al + 0] = T * ((mpb * dpot) + (mob * ddpb));
-    dFb[2 * al + 1] = T * (msb * dpot);
+    if (capw) {   /* dPhi_w/ds_w,a = -p_cow'(s_w,a), dPhi_w/ds_w,b = +p_cow'(s_w,b) */
+      dFa[2 * al + 1] = T * ((msa * dpot) - (mob * qa->dpc));
+      dFb[2 * al + 1] = T * ((msb * dpot) + (mob * qb->dpc));
+    } else {
+      dFa[2 * al + 1] = T * (msa * dpot);
+      dFb[2 * al + 1] = T * (msb * dpot);
+    }
   }
 }
 
@@ -1193,12 +1221,12 @@ static void assemble(og_sim *s) {
         double T = conn_trans(s, a, b, &dzab);
         double gdz = s->f.g * dzab;
         if (c < d) {
-          flux(T, gdz, s->p[c], s->p[d], &qc, &qd, F, dFa, dFb);
+          flux(T, gdz, s->p[c], s->p[d], &qc, &qd, s->cap, F, dFa, dFb);
           r0 = r0 + F[0]; r1 = r1 + F[1];
           d0 = d0 + dFa[0]; d1 = d1 + dFa[1]; d2 = d2 + dFa[2]; d3 = d3 + dFa[3];
           off[0] = dFb[0]; off[1] = dFb[1]; off[2] = dFb[2]; off[3] = dFb[3];
         } else {
-          flux(T, gdz, s->p[d], s->p[c], &qd, &qc, F, dFa, dFb);
+          flux(T, gdz, s->p[d], s->p[c], &qd, &qc, s->cap, F, dFa, dFb);
           r0 = r0 + (-F[0]); r1 = r1 + (-F[1]);
           d0 = d0 + (-dFb[0]); d1 = d1 + (-dFb[1]); d2 = d2 + (-dFb[2]); d3 = d3 + (-dFb[3]);
           off[0] = -dFa[0]; off[1] = -dFa[1]; off[2] = -dFa[2]; off[3] = -dFa[3];
@@ -1437,8 +1465,21 @@ int oracle_create(const og_grid *g, const og_rock *r, const og_fluid *f,
                   const og_well *w, int32_t nwells, const og_options *o, void **out) {
   if (!g || !r || !f || !o || !out || g->nx < 1 || g->ny < 1 || g->nz < 1 || nwells < 0)
     return OG_EINVAL;
+  for (int k = 0; k < 2; ++k) {
+    if (f->pc_n[k] < 0 || f->pc_n[k] > 256 || (f->pc_n[k] > 0 && !f->pc_table[k])) return OG_EINVAL;
+    for (int i = 0; i < f->pc_n[k]; ++i) {
+      if (!isfinite(f->pc_table[k][2 * i]) || !isfinite(f->pc_table[k][2 * i + 1])) return OG_EINVAL;
+      if (i > 0 && !(f->pc_table[k][2 * i] > f->pc_table[k][2 * i - 2])) return OG_EINVAL;
+    }
+  }
   og_sim *s = (og_sim *)zalloc(1, sizeof(og_sim));
   s->g = *g; s->f = *f; s->o = *o;
+  for (int k = 0; k < 2; ++k) {
+    s->pc_own[k] = (double *)zalloc((size_t)(2 * f->pc_n[k] + 1), sizeof(double));
+    if (f->pc_n[k]) memcpy(s->pc_own[k], f->pc_table[k], sizeof(double) * 2 * (size_t)f->pc_n[k]);
+    s->f.pc_table[k] = s->pc_own[k];
+    if (f->pc_n[k]) s->cap = 1;
+  }
   s->sigma = r->sigma; s->c_rock = r->c_rock; s->p_ref_rock = r->p_ref;
   s->nL = g->nx * g->ny * g->nz;
   s->nc = 2 * s->nL;
@@ -1550,7 +1591,7 @@ void oracle_destroy(void *h) {
   og_sim *s = (og_sim *)h;
   if (!s) return;
   free(s->kf); free(s->km); free(s->phi_f); free(s->phi_m); free(s->wells); free(s->perf);
-  free(s->ctl_kind); free(s->ctl_target);
+  free(s->ctl_kind); free(s->ctl_target); free(s->pc_own[0]); free(s->pc_own[1]);
   free(s->J.rowptr); free(s->J.col); free(s->J.diag); free(s->J.val);
   free(s->R); free(s->p); free(s->sw); free(s->bhp); free(s->pn); free(s->swn); free(s->bhpn);
   free(s->Mn); free(s->y); free(s->bh); free(s->colour); free(s->Ap.val);
@@ -1596,6 +1637,10 @@ int oracle_well_rates(void *h, double *q_oil, double *q_water) {
     q_water[w] = qw;
   }
   return s->nwells;
+}
+
+void oracle_cap_pressure(int32_t n, const double *table, double sw, double *pc, double *dpc) {
+  cap_pressure(n, table, sw, pc, dpc);
 }
 
 int oracle_solver_sizes(void *h, int32_t *nb, int32_t *nnzb) {

@@ -28,6 +28,10 @@ typedef struct {
 } og_rock;
 typedef struct {
   double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
+  int32_t pc_n[2];            /* points of the p_cow(s_w) tables: [0] fracture, [1] matrix;
+                                 0: p_cow = 0 in that continuum */
+  const double *pc_table[2];  /* pc_n[k] pairs (s_w, p_cow in Pa), s_w strictly ascending;
+                                 linear between points, constant outside (copied) */
 } og_fluid;
 typedef struct {
   int32_t kind, i, j, k_top, k_bot;  /* kind 0: water rate injector, 1: BHP, 2: oil-rate
@@ -77,6 +81,8 @@ int  oracle_well_controls(void *h, int32_t *kind, double *target);
 /* per well, the oil and water mass rates (kg/s, positive into the reservoir)
  * summed over its perforations at the current state and controls */
 int  oracle_well_rates(void *h, double *q_oil, double *q_water);
+/* p_cow(s_w) and its slope from a table of n (s_w, p_cow) pairs */
+void oracle_cap_pressure(int32_t n, const double *table, double sw, double *pc, double *dpc);
 int  oracle_set_state(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_set_iterate(void *h, const double *p, const double *sw, const double *bhp);
 int  oracle_get_state(void *h, double *p, double *sw, double *bhp);

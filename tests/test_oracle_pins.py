@@ -35,6 +35,17 @@ def small_problem(nx=3, ny=3, nz=2, seed=1, g=0.0):
                     0.08, wells, seed, dt_days=1.0, nsteps=1, g=g)
 
 
+# capillary pressure curves (s_w, p_cow in Pa): a weak one for the fracture, a
+# strong one for the matrix
+PC_F = np.array([[0.2, 2.0e4], [0.5, 5.0e3], [0.8, 0.0]])
+PC_M = np.array([[0.2, 5.0e5], [0.35, 2.0e5], [0.5, 8.0e4], [0.65, 2.0e4], [0.8, 0.0]])
+
+
+def with_pc(prob, pc_f=PC_F, pc_m=PC_M):
+    prob.pc_f, prob.pc_m = pc_f, pc_m
+    return prob
+
+
 def random_interior_state(prob, seed=3):
     rng = np.random.default_rng(seed)
     nc = prob.n_cells
@@ -161,12 +172,14 @@ def test_true_impes_weight_cancels_the_saturation_column_sum():
 
 @pytest.mark.parametrize("make", [lambda: small_problem(3, 2, 2, g=0.0),
                                   lambda: small_problem(3, 2, 2, g=9.80665),
-                                  lambda: di.paper_example(1), lambda: di.paper_example(2)])
+                                  lambda: di.paper_example(1), lambda: di.paper_example(2),
+                                  lambda: with_pc(small_problem(3, 2, 2, g=9.80665))])
 def test_jacobian_matches_finite_differences(make):
     """Analytic J equals central differences of the residual R (Section 3:
     Newton needs the exact Jacobian of F), columnwise, rel 1e-5; also for
     the setups of the paper's examples (oil-rate producer rows, a given well
-    index, rock compressibility, three layers under gravity)."""
+    index, rock compressibility, three layers under gravity) and with
+    capillary pressure curves in both continua."""
     prob = make()
     s = O.OracleSim(prob)
     p, sw, bhp = random_interior_state(prob)
@@ -332,6 +345,117 @@ def test_hydrostatic_column_is_at_rest():
     s.assemble(prob.dt)
     bad = s.jacobian()[3]
     assert np.abs(res).max() <= 1e-10 * np.abs(bad).max()
+
+
+# ------------------------------------------------------- capillary pressure
+
+def test_cap_pressure_table_is_linear_interpolation():
+    """p_cow between table points is the straight line through them (numpy's
+    interp), constant outside the table, with the segment's slope as its
+    derivative (zero outside)."""
+    for tab in (PC_F, PC_M, np.array([[0.4, 1.0e5]])):
+        xs = np.concatenate([np.linspace(0.0, 1.0, 101), tab[:, 0],
+                             0.5 * (tab[1:, 0] + tab[:-1, 0])])
+        for x in xs:
+            pc, dpc = O.cap_pressure(tab, x)
+            ref = np.interp(x, tab[:, 0], tab[:, 1])
+            assert abs(pc - ref) <= 1e-9 * max(abs(tab[:, 1]).max(), 1.0), x
+            if x <= tab[0, 0] or x >= tab[-1, 0]:     # at the end points: zero slope
+                assert dpc == 0.0
+            else:
+                k = np.searchsorted(tab[:, 0], x, side="right") - 1
+                slope = (tab[k + 1, 1] - tab[k, 1]) / (tab[k + 1, 0] - tab[k, 0])
+                assert abs(dpc - slope) <= 1e-12 * abs(slope)
+
+
+def test_zero_capillary_tables_change_nothing():
+    """Tables of zero capillary pressure give the residual and Jacobian of
+    the model without capillary pressure."""
+    zero = np.array([[0.1, 0.0], [0.9, 0.0]])
+    out = []
+    for pc in (None, zero):
+        prob = small_problem(3, 2, 2, g=9.80665)
+        prob.pc_f = prob.pc_m = pc
+        s = O.OracleSim(prob)
+        s.set_iterate(*random_interior_state(prob))
+        s.assemble(prob.dt)
+        out.append(s.jacobian())
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+
+
+def _column_equilibrium(prob, pc_top):
+    """A column at capillary-gravity equilibrium (Section 2 constraints):
+    the oil potential p - rho_o g z and the water potential
+    p - p_cow - rho_w g z are the same in every cell, with the discrete
+    densities of the flux (the mean of the two cells' densities).  Oil
+    pressure layer by layer from the top (densities linear in p, so each step
+    is a linear equation); p_cow from the water balance; saturations from the
+    inverse of each continuum's curve (so p_cow,f = p_cow,m in a location)."""
+    nz, gdz = prob.nz, prob.g * prob.dz
+    rho_o = lambda p: prob.rho_o_ref * (1.0 + prob.c_o * (p - prob.p_ref))
+    rho_w = lambda p: prob.rho_w_ref * (1.0 + prob.c_w * (p - prob.p_ref))
+    p = np.empty(nz); pc = np.empty(nz)
+    p[0], pc[0] = 2.0e7, pc_top
+    for k in range(nz - 1):
+        a = 0.5 * prob.rho_o_ref * prob.c_o * gdz
+        rhs = p[k] + 0.5 * gdz * (rho_o(p[k]) + prob.rho_o_ref * (1.0 - prob.c_o * prob.p_ref))
+        p[k + 1] = rhs / (1.0 - a)
+        pc[k + 1] = pc[k] + (0.5 * (rho_o(p[k]) + rho_o(p[k + 1]))
+                             - 0.5 * (rho_w(p[k]) + rho_w(p[k + 1]))) * gdz
+    inv = lambda tab, v: np.interp(v, tab[::-1, 1], tab[::-1, 0])   # decreasing curves
+    sw = np.empty(2 * nz)
+    sw[0::2], sw[1::2] = inv(prob.pc_f, pc), inv(prob.pc_m, pc)
+    return np.repeat(p, 2), sw
+
+
+def test_capillary_gravity_column_is_at_rest():
+    """A column with different fracture and matrix curves at capillary-gravity
+    equilibrium has zero flux residual in every cell and phase (water is
+    wetter at depth, and the matrix holds more water than its fracture); the
+    same column with p_cow left out of the water potential is far from
+    rest."""
+    nz = 8
+    prob = with_pc(small_problem(1, 1, nz, g=9.80665))
+    prob.wells = []
+    prob.bhp0 = np.zeros(0)
+    prob.dz = 2.0            # p_cow changes by ~4 kPa a layer: inside both curves
+    p, sw = _column_equilibrium(prob, pc_top=1.5e4)
+    assert (np.diff(sw[0::2]) > 0).all() and (sw[1::2] > sw[0::2]).all()
+    s = O.OracleSim(prob)
+    s.set_state(p, sw, np.zeros(0))
+    s.assemble(prob.dt)
+    res = s.jacobian()[3]
+    prob0 = small_problem(1, 1, nz, g=9.80665)
+    prob0.wells, prob0.bhp0, prob0.dz = [], np.zeros(0), prob.dz
+    s0 = O.OracleSim(prob0)
+    s0.set_state(p, sw, np.zeros(0))
+    s0.assemble(prob0.dt)
+    bad = s0.jacobian()[3]
+    assert np.abs(bad[1::2]).max() > 0.0
+    assert np.abs(res).max() <= 1e-8 * np.abs(bad).max()
+
+
+def test_capillary_imbibition_into_the_matrix():
+    """Equal oil pressures in a location, a wet fracture and a dry matrix with
+    a strong curve: the water potential of the matrix is p_cow(s_m) lower, so
+    water moves from the fracture into the matrix, oil does not move, and the
+    transfer is proportional to the capillary pressure difference."""
+    prob = small_problem(1, 1, 1)
+    prob.wells = []
+    prob.bhp0 = np.zeros(0)
+    out = []
+    for scale in (1.0, 2.0):
+        prob.pc_f = None
+        prob.pc_m = PC_M * np.array([1.0, scale])
+        s = O.OracleSim(prob)
+        s.set_state(np.array([3.0e7, 3.0e7]), np.array([0.7, 0.3]), np.zeros(0))
+        s.assemble(prob.dt)
+        res = s.jacobian()[3]
+        assert res[0] == 0.0 and res[2] == 0.0           # no oil transfer
+        assert res[1] > 0.0 and res[3] == -res[1]        # water leaves f, enters m
+        out.append(res[1])
+    assert abs(out[1] - 2.0 * out[0]) <= 1e-12 * out[1]
 
 
 def test_transfer_and_flux_relax_towards_equilibrium():
