@@ -67,9 +67,18 @@ typedef struct {
 /* Fluids (Section 2): viscosities (Pa s), compressibilities (1/Pa) of the
  * linear densities rho = rho_ref (1 + c (p - p_ref)), Corey end points
  * s_wc, s_or (krw = S^2, kro = (1-S)^2 of the normalised saturation), and
- * the gravitational acceleration g (m/s^2). */
+ * the gravitational acceleration g (m/s^2).
+ * Capillary pressure (Section 2 constraints, p_w = p_o - p_cow(s_w)):
+ * pc_n[k] points (0..256) of the table of continuum k (0 fracture, 1 matrix),
+ * pc_table[k] -> pc_n[k] pairs (s_w, p_cow in Pa) with s_w strictly
+ * ascending, read once by sim_create (host memory).  p_cow is linear
+ * between points and constant outside; with no table it is zero.  It enters
+ * the water potential of the fluxes and of the fracture-matrix transfer;
+ * densities and perforation rates use the oil pressure p. */
 typedef struct {
   double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
+  int32_t pc_n[2];
+  const double *pc_table[2];
 } dp_fluid;
 
 /* Vertical well perforating the fracture cells of column (i, j), layers

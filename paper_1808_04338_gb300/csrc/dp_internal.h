@@ -41,6 +41,8 @@ struct Phys {
   double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
   double inv_span, inv_mu_o, inv_mu_w;
   double sigma, c_rock, p_ref_rock;
+  int pc_n[2];                    // capillary tables: points per continuum
+  const double *pc_tab[2];        //   device (s_w, p_cow) pairs, or null
 };
 
 // 2x2-block sparse row matrix (device pointers), natural row order.

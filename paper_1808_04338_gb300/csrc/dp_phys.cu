@@ -20,7 +20,24 @@ namespace dp {
 // permeabilities of the normalised saturation, mobilities and derivatives.
 struct Props {
   double rho[2], drho[2], phi, dphi, lam[2], dlam[2];
+  double pc, dpc;   // capillary pressure and slope (set only where a table is given)
 };
+
+// Capillary pressure p_cow(s_w) (Section 2: p_w = p_o - p_cow(s_w)) from a
+// table of n (s_w, p_cow) pairs: the line through the two points around s_w,
+// constant with zero slope at and beyond the end points; zero with no table.
+__device__ __forceinline__ void cap_pressure(int n, const double *t, double sw, double &pc,
+                                             double &dpc) {
+  if (n == 0) { pc = 0.0; dpc = 0.0; return; }
+  if (sw <= t[0]) { pc = t[1]; dpc = 0.0; return; }
+  if (sw >= t[2 * (n - 1)]) { pc = t[2 * n - 1]; dpc = 0.0; return; }
+  int k = 0;
+  while (sw >= t[2 * (k + 1)]) ++k;      // t[2k] <= sw < t[2k + 2]
+  double ds = t[2 * k + 2] - t[2 * k];
+  double dp = t[2 * k + 3] - t[2 * k + 1];
+  dpc = dp / ds;
+  pc = t[2 * k + 1] + dp * ((sw - t[2 * k]) / ds);
+}
 
 __device__ __forceinline__ void props(const Phys &P, const double *phi_f, const double *phi_m,
                                       int c, double p, double sw, Props &q) {
@@ -62,18 +79,23 @@ __device__ __forceinline__ void accumulation(const Phys &P, double sw, const Pro
 // false is the same evaluation for gdz = 0: the gravity terms are then exact
 // zeros (x - (y * 0) == x for the finite values here, and p_a - p_b is never
 // -0), so the result is identical bit for bit.
-template <bool GRAV>
+// CAP: the water potential carries -p_cow(s_w) of each side (phase pressure
+// p_w = p - p_cow), which adds -/+ p_cow' to the saturation derivatives.
+template <bool GRAV, bool CAP>
 __device__ __forceinline__ void flux(double T, double gdz, double pa, double pb, const Props &qa,
                                      const Props &qb, double F[2], double dFa[4], double dFb[4]) {
 #pragma unroll
   for (int al = 0; al < 2; ++al) {
+    const bool capw = CAP && al == 1;
+    double ppa = capw ? pa - qa.pc : pa;
+    double ppb = capw ? pb - qb.pc : pb;
     double dpot, ddpa, ddpb;
     if (GRAV) {
-      dpot = (pa - pb) - ((0.5 * (qa.rho[al] + qb.rho[al])) * gdz);
+      dpot = (ppa - ppb) - ((0.5 * (qa.rho[al] + qb.rho[al])) * gdz);
       ddpa = 1.0 - ((0.5 * qa.drho[al]) * gdz);
       ddpb = -1.0 - ((0.5 * qb.drho[al]) * gdz);
     } else {
-      dpot = pa - pb;
+      dpot = ppa - ppb;
       ddpa = 1.0;
       ddpb = -1.0;
     }
@@ -91,9 +113,14 @@ __device__ __forceinline__ void flux(double T, double gdz, double pa, double pb,
     }
     F[al] = (T * mob) * dpot;
     dFa[2 * al + 0] = T * ((mpa * dpot) + (mob * ddpa));
-    dFa[2 * al + 1] = T * (msa * dpot);
     dFb[2 * al + 0] = T * ((mpb * dpot) + (mob * ddpb));
-    dFb[2 * al + 1] = T * (msb * dpot);
+    if (capw) {
+      dFa[2 * al + 1] = T * ((msa * dpot) - (mob * qa.dpc));
+      dFb[2 * al + 1] = T * ((msb * dpot) + (mob * qb.dpc));
+    } else {
+      dFa[2 * al + 1] = T * (msa * dpot);
+      dFb[2 * al + 1] = T * (msb * dpot);
+    }
   }
 }
 
@@ -421,7 +448,7 @@ struct AsmArgs {
 // one kind and equal length.  Cell rows: accumulation, then the connections
 // in increasing column order (fluxes, then perforations); well rows: the
 // rate or pressure constraint.
-template <bool GRAV>
+template <bool GRAV, bool CAP>
 __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const Phys &P = a.P;
@@ -435,6 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
     double pc = a.p[r], swc = a.sw[r];
     Props qc;
     load_props(P, a.phi_f, a.phi_m, a.pr, r, qc);
+    if (CAP) cap_pressure(P.pc_n[r & 1], P.pc_tab[r & 1], swc, qc.pc, qc.dpc);
     double M[2], dM[4];
     accumulation(P, swc, qc, M, dM);
     a.Macc[2 * r] = M[0];
@@ -454,6 +482,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
         double pd = a.p[d];
         Props qd;
         load_props(P, a.phi_f, a.phi_m, a.pr, d, qd);
+        if (CAP) cap_pressure(P.pc_n[d & 1], P.pc_tab[d & 1], a.sw[d], qd.pc, qd.dpc);
         double gdz = 0.0;
         if (GRAV) {
           double dzab;
@@ -467,12 +496,12 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
         }
         double F[2], dFa[4], dFb[4];
         if (r < d) {
-          flux<GRAV>(T, gdz, pc, pd, qc, qd, F, dFa, dFb);
+          flux<GRAV, CAP>(T, gdz, pc, pd, qc, qd, F, dFa, dFb);
           r0 = r0 + F[0]; r1 = r1 + F[1];
           d0 = d0 + dFa[0]; d1 = d1 + dFa[1]; d2 = d2 + dFa[2]; d3 = d3 + dFa[3];
           off[0] = dFb[0]; off[1] = dFb[1]; off[2] = dFb[2]; off[3] = dFb[3];
         } else {
-          flux<GRAV>(T, gdz, pd, pc, qd, qc, F, dFa, dFb);
+          flux<GRAV, CAP>(T, gdz, pd, pc, qd, qc, F, dFa, dFb);
           r0 = r0 + (-F[0]); r1 = r1 + (-F[1]);
           d0 = d0 + (-dFb[0]); d1 = d1 + (-dFb[1]); d2 = d2 + (-dFb[2]); d3 = d3 + (-dFb[3]);
           off[0] = -dFa[0]; off[1] = -dFa[1]; off[2] = -dFa[2]; off[3] = -dFa[3];
@@ -642,8 +671,11 @@ int phys_assemble(Sim *s) {
   a.well_kind = s->well_kind; a.well_target = s->well_target;
   a.val = s->A.val; a.R = s->R;
   a.inv_dt = s->inv_dt;
-  if (s->ph.g != 0.0) DP_LAUNCH(s, k_assemble<true>, nblk(s->ph.nb), kBlock, 0, a);
-  else DP_LAUNCH(s, k_assemble<false>, nblk(s->ph.nb), kBlock, 0, a);
+  bool grav = s->ph.g != 0.0, cap = s->ph.pc_n[0] > 0 || s->ph.pc_n[1] > 0;
+  void (*k_assemble_sel)(AsmArgs) =
+      cap ? (grav ? k_assemble<true, true> : k_assemble<false, true>)
+          : (grav ? k_assemble<true, false> : k_assemble<false, false>);
+  DP_LAUNCH(s, k_assemble_sel, nblk(s->ph.nb), kBlock, 0, a);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }

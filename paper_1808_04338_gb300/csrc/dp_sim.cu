@@ -133,6 +133,15 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
         !(W.limit >= 0.0) || !(W.wi >= 0.0) || !std::isfinite(W.limit) || !std::isfinite(W.wi))
       return DP_EINVAL;
   }
+  for (int k = 0; k < 2; ++k) {
+    int n = fluid->pc_n[k];
+    if (n < 0 || n > 256 || (n > 0 && !fluid->pc_table[k])) return DP_EINVAL;
+    for (int i = 0; i < n; ++i) {
+      const double *t = fluid->pc_table[k];
+      if (!std::isfinite(t[2 * i]) || !std::isfinite(t[2 * i + 1])) return DP_EINVAL;
+      if (i > 0 && !(t[2 * i] > t[2 * i - 2])) return DP_EINVAL;
+    }
+  }
   dp_sim *s = new (std::nothrow) dp_sim();
   if (!s) return DP_ENOMEM;
   s->opt = *opts;
@@ -153,6 +162,18 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   P.inv_mu_w = 1.0 / fluid->mu_w;
   P.sigma = rock->sigma; P.c_rock = rock->c_rock; P.p_ref_rock = rock->p_ref;
   auto fail = [&](int rc) { sim_destroy(s); return rc; };
+  for (int k = 0; k < 2; ++k) {
+    P.pc_n[k] = fluid->pc_n[k];
+    P.pc_tab[k] = nullptr;
+    if (P.pc_n[k] == 0) continue;
+    size_t bytes = (size_t)P.pc_n[k] * 16;
+    double *t = (double *)dalloc(s, bytes);
+    if (!t) return fail(DP_ENOMEM);
+    if (cudaMemcpyAsync(t, fluid->pc_table[k], bytes, cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
+      return fail(DP_ECUDA);
+    P.pc_tab[k] = t;
+  }
   size_t nl8 = (size_t)P.nL * 8;
   s->kf = (double *)dalloc(s, nl8);
   s->km = (double *)dalloc(s, nl8);

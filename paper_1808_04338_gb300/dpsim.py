@@ -34,7 +34,18 @@ class dp_rock(C.Structure):
 class dp_fluid(C.Structure):
     _fields_ = [(n, C.c_double) for n in
                 ("mu_o", "mu_w", "c_o", "c_w", "rho_o_ref", "rho_w_ref", "p_ref", "swc",
-                 "sor", "g")]
+                 "sor", "g")] + [("pc_n", C.c_int32 * 2), ("pc_table", C.c_void_p * 2)]
+
+
+def _fluid(prob, keep):
+    """dp_fluid of a Problem; its capillary tables are appended to keep."""
+    f = dp_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref, prob.rho_w_ref,
+                 prob.p_ref, prob.swc, prob.sor, prob.g)
+    for k, (n, tab) in enumerate(prob.pc_tables()):
+        keep.append(tab)
+        f.pc_n[k] = n
+        f.pc_table[k] = tab.ctypes.data
+    return f
 
 
 class dp_well(C.Structure):
@@ -174,8 +185,8 @@ def residual_norms_noalloc(prob, phi_f, phi_m, well_kind, well_target, res, dt, 
     """Scaled residual 2-norm and max-norm into out2 (device tensors in, no
     allocation by the library); returns (rc, message)."""
     g = dp_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.top_depth)
-    f = dp_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref, prob.rho_w_ref,
-                 prob.p_ref, prob.swc, prob.sor, prob.g)
+    keep = []
+    f = _fluid(prob, keep)
     buf = C.create_string_buffer(256)
 
     def ptr(t):
@@ -248,8 +259,7 @@ def _inputs(prob):
     g = dp_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.top_depth)
     keep = [_f64(prob.kf), _f64(prob.km), _f64(prob.phi_f), _f64(prob.phi_m)]
     r = dp_rock(*[a.ctypes.data for a in keep], prob.sigma, prob.c_rock, prob.p_ref_rock)
-    f = dp_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref, prob.rho_w_ref,
-                 prob.p_ref, prob.swc, prob.sor, prob.g)
+    f = _fluid(prob, keep)
     nw = len(prob.wells)
     W = (dp_well * max(nw, 1))()
     for q, w in enumerate(prob.wells):
@@ -357,16 +367,7 @@ class Sim:
         self.prob = prob
         self.opts = opts if opts is not None else options("parity")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        g = dp_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.top_depth)
-        keep = [_f64(prob.kf), _f64(prob.km), _f64(prob.phi_f), _f64(prob.phi_m)]
-        r = dp_rock(*[a.ctypes.data for a in keep], prob.sigma, prob.c_rock, prob.p_ref_rock)
-        f = dp_fluid(prob.mu_o, prob.mu_w, prob.c_o, prob.c_w, prob.rho_o_ref, prob.rho_w_ref,
-                     prob.p_ref, prob.swc, prob.sor, prob.g)
-        nw = len(prob.wells)
-        W = (dp_well * max(nw, 1))()
-        for q, w in enumerate(prob.wells):
-            W[q] = dp_well(w.kind, w.i, w.j, w.k_top, w.k_bot, w.target, w.rw, w.skin, w.limit,
-                       w.wi)
+        g, r, f, W, nw, keep = _inputs(prob)
         self._alloc = TorchAllocator(torch.cuda.current_device()) if use_torch_alloc else None
         h = C.c_void_p()
         rc = L.sim_create(C.byref(g), C.byref(r), C.byref(f), W, nw, C.byref(self.opts),

@@ -74,6 +74,17 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
         g, r, f, W, nw, keep = dpsim._inputs(dataclasses.replace(prob, wells=wells))
         assert L.sim_create(ctypes.byref(g), ctypes.byref(r), ctypes.byref(f), W, nw,
                             ctypes.byref(o), None, None, ctypes.byref(out)) == dpsim.DP_EINVAL, bad
+    # capillary tables: s_w not strictly ascending, a NaN, too many points, no array
+    import numpy as np
+    for tab in (np.array([[0.2, 1e5], [0.2, 0.0]]), np.array([[0.2, np.nan], [0.5, 0.0]]),
+                np.column_stack([np.linspace(0, 1, 257), np.zeros(257)])):
+        g, r, f, W, nw, keep = dpsim._inputs(dataclasses.replace(prob, pc_m=tab))
+        assert L.sim_create(ctypes.byref(g), ctypes.byref(r), ctypes.byref(f), W, nw,
+                            ctypes.byref(o), None, None, ctypes.byref(out)) == dpsim.DP_EINVAL
+    g, r, f, W, nw, keep = dpsim._inputs(prob)
+    f.pc_n[0] = 3
+    assert L.sim_create(ctypes.byref(g), ctypes.byref(r), ctypes.byref(f), W, nw,
+                        ctypes.byref(o), None, None, ctypes.byref(out)) == dpsim.DP_EINVAL
 
 
 def test_oracle_is_not_linked_into_the_library(lib):

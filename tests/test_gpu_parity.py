@@ -37,6 +37,17 @@ def small(nx, ny, nz, seed=1, wells="two", g=0.0):
                     seed, dt_days=1.0, nsteps=2, g=g)
 
 
+# capillary pressure curves (s_w, p_cow in Pa): weak in the fracture, strong
+# in the matrix
+PC_F = np.array([[0.2, 2.0e4], [0.5, 5.0e3], [0.8, 0.0]])
+PC_M = np.array([[0.2, 5.0e5], [0.35, 2.0e5], [0.5, 8.0e4], [0.65, 2.0e4], [0.8, 0.0]])
+
+
+def with_pc(prob, pc_f=PC_F, pc_m=PC_M):
+    prob.pc_f, prob.pc_m = pc_f, pc_m
+    return prob
+
+
 def pair(prob, mode="parity", **kw):
     return gpu().Sim(prob, gpu().options(mode, **kw)), O.OracleSim(prob, O.options(mode, **kw))
 
@@ -66,7 +77,10 @@ def interior(prob, seed=7):
 @pytest.mark.parametrize("make", [di.tiny, lambda: small(7, 5, 3), lambda: small(1, 1, 1, wells="bhp"),
                                   lambda: small(9, 1, 1), lambda: small(4, 3, 2, wells="none"),
                                   lambda: small(3, 4, 5, g=9.80665),
-                                  lambda: di.paper_example(1), lambda: di.paper_example(2)])
+                                  lambda: di.paper_example(1), lambda: di.paper_example(2),
+                                  lambda: with_pc(small(7, 5, 3)),
+                                  lambda: with_pc(small(3, 4, 5, g=9.80665)),
+                                  lambda: with_pc(small(3, 4, 5, g=9.80665), pc_f=None)])
 def test_jacobian_residual_bit_exact(make):
     prob = make()
     g, o = pair(prob)
@@ -323,6 +337,19 @@ def test_layered_200k_timestep_parity(amg_refresh, schur):
     assert rcg == rco == 0
     assert stg.newton_iters == sto.newton_iters > 1
     state_close(g, o, prob)
+
+
+@pytest.mark.parametrize("schur", [0, 1])
+def test_capillary_pressure_tiny_steps(schur):
+    """Ten timesteps with capillary pressure curves in both continua (the
+    matrix imbibes water from the fracture): states match the oracle's."""
+    prob = with_pc(di.tiny())
+    g, o = pair(prob, schur=schur)
+    for step in range(prob.nsteps):
+        rcg, _ = g.advance(prob.dt)
+        rco, _ = o.advance(prob.dt)
+        assert rcg == rco == 0, step
+        state_close(g, o, prob)
 
 
 @pytest.mark.parametrize("kw", [dict(amg_refresh=1), dict(decouple=1), dict(decouple=2),
