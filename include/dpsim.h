@@ -86,7 +86,7 @@ typedef struct {
  * DP_WELL_RATE_INJ: water injector at a reservoir-volume rate target (m^3/s);
  * DP_WELL_BHP: well at a bottom-hole pressure target (Pa);
  * DP_WELL_OIL_RATE: producer at an oil mass-rate target (kg/s, the oil
- * leaving through its perforations; Section 5's producers).  rw: wellbore
+ * leaving through its perforations; the producers of Section 4's examples).  rw: wellbore
  * radius (m); skin: skin factor.  limit (Pa, 0: none; kinds 0 and 2): a
  * maximum BHP for an injector, a minimum BHP for an oil-rate producer; after
  * each Newton update of sim_advance a well past its limit switches to BHP
