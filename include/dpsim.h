@@ -152,6 +152,11 @@ typedef struct {
                             AMG and FGMRES work on the fracture-and-well system with
                             S_ff = A_ff - A_fm A_mm^-1 A_mf (half the unknowns); 0: the
                             full system */
+  double reorth;         /* classical Gram-Schmidt of FGMRES's Arnoldi step: a second
+                            pass when ||w - V h||^2 < reorth ||w||^2 after the first
+                            (the test of Daniel, Gragg, Kaufman and Stewart; 0.5 its
+                            usual constant, >= 1: always two passes, 0: one pass);
+                            finite, >= 0 */
 } dp_options;
 
 typedef struct {

@@ -818,7 +818,7 @@ void oracle_amg_destroy(void *amg) {
 typedef void (*op_fn)(void *ctx, const double *x, double *y);
 
 static int fgmres(int n, op_fn A, void *actx, op_fn M, void *mctx,
-                  const double *b, double *x, int m, int maxit, double tol,
+                  const double *b, double *x, int m, int maxit, double tol, double reorth,
                   int *iters, double *relres) {
   double *V = (double *)zalloc((size_t)(m + 1) * n, sizeof(double));
   double *Z = (double *)zalloc((size_t)m * n, sizeof(double));
@@ -849,15 +849,19 @@ static int fgmres(int n, op_fn A, void *actx, op_fn M, void *mctx,
       double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
       if (M) M(mctx, vj, zj); else memcpy(zj, vj, sizeof(double) * (size_t)n);
       A(actx, zj, w);
-      for (int pass = 0; pass < 2; ++pass) {            /* CGS2 */
+      double wn = nrm2(w, n), hn = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {            /* classical Gram-Schmidt */
         for (int i = 0; i <= j; ++i) h[i] = dot(V + (size_t)i * n, w, n);
         for (int i = 0; i <= j; ++i) {
           const double *vi = V + (size_t)i * n;
           for (int q = 0; q < n; ++q) w[q] -= h[i] * vi[q];
           H[(size_t)i * m + j] += h[i];
         }
+        hn = nrm2(w, n);
+        /* a second pass only after cancellation (Daniel, Gragg, Kaufman and
+         * Stewart's test): ||w - V h||^2 < reorth ||w||^2; reorth >= 1: always */
+        if (!(reorth >= 1.0 || hn * hn < reorth * (wn * wn))) break;
       }
-      double hn = nrm2(w, n);
       H[(size_t)(j + 1) * m + j] = hn;
       if (hn != 0.0) {
         double *v1 = V + (size_t)(j + 1) * n;
@@ -950,10 +954,10 @@ int oracle_fgmres_bsr(int32_t n, const int32_t *rowptr, const int32_t *col,
     ilu_factor(&f, &A);
     free(colour);
     c.A = &A; c.ilu = &f; c.mode = 1;
-    rc = fgmres(2 * n, op_bsr, &A, op_cpr, &c, b, x, restart, maxit, tol, &it, &rr);
+    rc = fgmres(2 * n, op_bsr, &A, op_cpr, &c, b, x, restart, maxit, tol, 1.0, &it, &rr);
     ilu_free(&f);
   } else {
-    rc = fgmres(2 * n, op_bsr, &A, NULL, NULL, b, x, restart, maxit, tol, &it, &rr);
+    rc = fgmres(2 * n, op_bsr, &A, NULL, NULL, b, x, restart, maxit, tol, 1.0, &it, &rr);
   }
   *iters = it; *relres = rr;
   return rc;
@@ -970,7 +974,7 @@ int oracle_fgmres_amg(int32_t n, const int32_t *rowptr, const int32_t *col,
   og_amg *m = NULL;
   oracle_amg_create(n, rowptr, col, val, theta, coarse_max, 20, (void **)&m);
   int it = 0; double rr = 0.0;
-  int rc = fgmres(n, op_csr, &A, op_amg, m, b, x, restart, maxit, tol, &it, &rr);
+  int rc = fgmres(n, op_csr, &A, op_amg, m, b, x, restart, maxit, tol, 1.0, &it, &rr);
   oracle_amg_destroy(m);
   *iters = it; *relres = rr;
   return rc;
@@ -1846,7 +1850,7 @@ int oracle_solve_step(void *h, og_stats *st) {
   int it = 0; double rr = 0.0;
   double *ys = s->o.schur ? s->yk : s->y;
   int rc = fgmres(n2, op_bsr, A, s->o.precond ? op_cpr : NULL, &c, s->bh, ys,
-                  s->o.gmres_restart, s->o.gmres_maxit, eta, &it, &rr);
+                  s->o.gmres_restart, s->o.gmres_maxit, eta, s->o.reorth, &it, &rr);
   free(c.r1); free(c.z1); free(c.rp); free(c.xp);
   if (s->o.schur) schur_back(s);
   for (int cc = 0; cc < s->nc; ++cc) {

@@ -62,6 +62,9 @@ typedef struct {
   int32_t schur;          /* 1: eliminate every matrix cell exactly (its 2x2 block
                              couples only to its own fracture cell) and solve the
                              fracture-and-well system; 0: the full system */
+  double reorth;          /* Gram-Schmidt in FGMRES: a second classical pass when
+                             ||w - V h||^2 < reorth ||w||^2 after the first (0.5:
+                             the DGKS test; 0: one pass; 1: always two) */
 } og_options;
 typedef struct {
   int32_t newton_iters, linear_iters, converged, amg_levels;

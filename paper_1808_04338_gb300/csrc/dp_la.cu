@@ -1427,14 +1427,15 @@ __global__ void __launch_bounds__(kBlock, kDotBlocks / 152) k_multidot(long long
 // Modes 3 and 4 are the two passes of classical Gram-Schmidt with the DGKS
 // test (Daniel, Gragg, Kaufman and Stewart 1976): both add the projections
 // into H[:, j] and take ||w - V h||^2 = w.w - h.h (slot 31 holds w.w).
-// Mode 3 sets scal[4] = 1 when that is below half of w.w (cancellation: a
-// second pass is needed), else stores beta = h_{j+1,j} in H and scal[2].
+// Mode 3 sets scal[4] = 1 when that is below reorth * w.w (cancellation: a
+// second pass is needed; reorth >= 1: always), else stores beta = h_{j+1,j}
+// in H and scal[2].
 // Mode 4 runs only when scal[4] = 1 and stores beta.
 // 256 threads: lane k of group g sums the partials of blocks g, g+8, ...;
 // the eight group sums are then added in group order.
 __global__ void __launch_bounds__(256) k_dot_final(const double *part, int nblocks, int nv,
                                                    double *dots, double *H, int m, int j,
-                                                   int mode, double *scal) {
+                                                   int mode, double *scal, double reorth) {
   if (mode == 4 && scal[4] == 0.0) return;
   __shared__ double sh[8][32];
   int k = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -1463,7 +1464,7 @@ __global__ void __launch_bounds__(256) k_dot_final(const double *part, int nbloc
   double ww = __shfl_sync(0xffffffffu, v, 31);
   if (k != 0) return;
   double b2 = ww - hh;
-  if (mode == 3 && b2 < 0.5 * ww) { scal[4] = 1.0; return; }
+  if (mode == 3 && (reorth >= 1.0 || b2 < reorth * ww)) { scal[4] = 1.0; return; }
   double beta = sqrt(b2 > 0.0 ? b2 : 0.0);
   if (mode == 3) scal[4] = 0.0;
   H[(size_t)(j + 1) * m + j] = beta;
@@ -1589,7 +1590,7 @@ static int dots(Sim *s, const double *V, long long ldv, int nv, const double *w,
 #undef DP_MD
   }
   DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, nv, s->dots, s->H, s->m, j, mode,
-            s->scal);
+            s->scal, s->opt.reorth);
   return DP_OK;
 }
 
@@ -1598,7 +1599,8 @@ static int norm_into(Sim *s, const double *x, double *dst) {
   long long N = 2LL * s->K.n;
   DP_LAUNCH(s, (k_multidot<1, false>), kDotBlocks, kBlock, 0, N, x, 0LL, x, s->dots_part, 0,
             (const double *)nullptr);
-  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, dst, s->H, s->m, 0, 0, s->scal);
+  DP_LAUNCH(s, k_dot_final, 1, 256, 0, s->dots_part, kDotBlocks, 1, dst, s->H, s->m, 0, 0, s->scal,
+            0.0);
   return DP_OK;
 }
 
@@ -1606,7 +1608,7 @@ __global__ void k_sqrt_inplace(double *v) { v[0] = sqrt(v[0]); }
 
 // One Arnoldi step of FGMRES for column j: z_j = M v_j, w = A z_j, then
 // classical Gram-Schmidt against v_0..v_j with the DGKS test: the second
-// pass runs only when the first cancelled more than half of ||w||^2, and
+// pass runs only when the first left less than reorth ||w||^2, and
 // h_{j+1,j} = ||w - V h|| comes from w.w - h.h, so each pass reads the basis
 // twice (dots, projection) and the projection writes v_{j+1} normalised.
 // Then the Givens rotations, and |g_{j+1}| into scal[3].

@@ -110,7 +110,7 @@ static bool bad_opts(const dp_options *o) {
          o->amg_coarse_max < 1 || o->amg_max_levels < 1 || o->precond < 0 || o->precond > 2 ||
          o->precision < 0 || o->precision > 1 || !(o->ds_max > 0.0) || o->amg_gs_levels < 0 ||
          o->amg_refresh < 0 || o->amg_refresh > 1 || o->decouple < 0 || o->decouple > 2 ||
-         o->schur < 0 || o->schur > 1;
+         o->schur < 0 || o->schur > 1 || !(o->reorth >= 0.0) || !std::isfinite(o->reorth);
 }
 
 extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_fluid *fluid,

@@ -73,7 +73,8 @@ class dp_options(C.Structure):
                 ("amg_max_levels", C.c_int32), ("precond", C.c_int32),
                 ("ds_max", C.c_double), ("precision", C.c_int32), ("use_graphs", C.c_int32),
                 ("amg_gs_levels", C.c_int32), ("cluster_rows", C.c_int32),
-                ("amg_refresh", C.c_int32), ("decouple", C.c_int32), ("schur", C.c_int32)]
+                ("amg_refresh", C.c_int32), ("decouple", C.c_int32), ("schur", C.c_int32),
+                ("reorth", C.c_double)]
 
 
 class dp_stats(C.Structure):
@@ -88,7 +89,9 @@ def options(mode: str = "parity", **kw) -> dp_options:
     independent FP64 evaluation far inside 1e-8); 'report': the second
     forcing term of Section 3.1 clipped to [1e-4, 0.1], Newton tolerance
     1e-6, l1-Jacobi instead of multicolour Gauss-Seidel on the AMG levels
-    below the finest, and the coarse AMG values refreshed once per timestep."""
+    below the finest, the coarse AMG values refreshed once per timestep, and a
+    second Gram-Schmidt pass only after near-total cancellation (reorth 1e-10;
+    parity mode: 0.5)."""
     o = dp_options()
     o.newton_max = 25
     o.newton_atol = 1e-13
@@ -102,6 +105,7 @@ def options(mode: str = "parity", **kw) -> dp_options:
     o.precision = 0
     o.use_graphs = 1
     o.amg_gs_levels = 30
+    o.reorth = 0.5
     o.eta_gamma, o.eta_beta, o.eta_min, o.eta_max = 0.9, 2.0, 1e-4, 0.1
     if mode == "parity":
         o.eta_mode, o.eta_fixed, o.newton_tol = 0, 1e-10, 1e-10
@@ -109,6 +113,7 @@ def options(mode: str = "parity", **kw) -> dp_options:
         o.eta_mode, o.eta_fixed, o.newton_tol = 2, 1e-4, 1e-6
         o.amg_gs_levels = 1
         o.amg_refresh = 1
+        o.reorth = 1e-10
     for k, v in kw.items():
         setattr(o, k, v)
     return o

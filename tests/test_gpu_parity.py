@@ -353,11 +353,13 @@ def test_capillary_pressure_tiny_steps(schur):
 
 
 @pytest.mark.parametrize("kw", [dict(amg_refresh=1), dict(decouple=1), dict(decouple=2),
-                                dict(schur=1), dict(schur=1, precision=1)])
+                                dict(schur=1), dict(schur=1, precision=1), dict(reorth=0.0),
+                                dict(reorth=1.0)])
 def test_tiny_steps_option_variants(kw):
     """Ten tiny timesteps against the FP64 oracle with the coarse AMG values
-    kept for a timestep, with the ABF and True-IMPES decouplings, and with the
-    matrix cells eliminated (FP64 and FP32 preconditioner)."""
+    kept for a timestep, with the ABF and True-IMPES decouplings, with the
+    matrix cells eliminated (FP64 and FP32 preconditioner), and with one or
+    always two Gram-Schmidt passes."""
     prob = di.tiny()
     okw = {k: v for k, v in kw.items() if k != "precision"}
     g = gpu().Sim(prob, gpu().options("parity", **kw))

@@ -88,6 +88,28 @@ def test_cpr_fgmres_matches_dense_lu(make, schur):
     assert np.abs(d[2 * nc::2]).max() <= 1e-5 * np.abs(y_ref[2 * nc::2]).max()
 
 
+@pytest.mark.parametrize("reorth", [0.0, 1.0])
+def test_gram_schmidt_passes_keep_the_solution(reorth):
+    """One classical Gram-Schmidt pass (reorth 0) or always two (reorth 1)
+    in FGMRES's Arnoldi step: the update still solves J y = -R to the
+    tolerance (its true residual, formed with a dense J) and equals the dense
+    LU solution."""
+    prob = small_problem(3, 3, 2)
+    s = O.OracleSim(prob, O.options("parity", eta_fixed=1e-12, reorth=reorth))
+    p, sw, bhp = random_interior_state(prob)
+    s.set_iterate(p, sw, bhp)
+    s.assemble(prob.dt)
+    rowptr, col, val, res = s.jacobian()
+    J = dense_from_bsr(rowptr, col, val)
+    y_ref = np.linalg.solve(J, -res)
+    rc, st = s.solve_step()
+    assert rc == 0 and st.converged
+    y = s.update()
+    assert np.linalg.norm(J @ y + res) <= 20 * 1e-12 * np.linalg.norm(res)
+    nc = prob.n_cells
+    assert np.abs((y - y_ref)[0:2 * nc:2]).max() <= 1e-6 * np.abs(y_ref[0:2 * nc:2]).max()
+
+
 def test_decoupling_removes_saturation_coefficient_and_keeps_solution():
     """Eq. "decoupled-eq": D^-1 J has a zero (0,1) entry in every cell's
     diagonal block (up to rounding), leaves the water rows unchanged, and
