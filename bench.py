@@ -35,7 +35,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TIMED_KERNEL = "k_bsr_spmv<0>"
 # DRAM bytes (read + written) per launch of TIMED_KERNEL on the 200x200x50 field, from the
 # ncu capture summarised in profiles/bsr_spmv_field200x200x50_dram.md (this kernel version)
-TIMED_TRAFFIC = {(200, 200, 50, 0): 972267264 + 112484096}
+TIMED_TRAFFIC = {(200, 200, 50, 0): 795957760 + 56835072}
 
 
 def workload(args):

@@ -112,14 +112,25 @@ struct LaunchScope {
     name<<<(grid), (block), (smem), (sim)->stream>>>(__VA_ARGS__);      \
   } while (0)
 
-// Storage order of the Krylov operator's copy: the fracture rows (cells 2q)
-// first, then the matrix rows (2q+1), then the well rows, so that a warp
-// streams rows of one kind and length from contiguous memory.
+// Storage order of the Krylov operator's copy: locations in chunks of
+// kChunk; storage rows 2 kChunk c .. of chunk c hold its fracture rows (cells
+// 2 loc), then its matrix rows (2 loc + 1); the well rows follow.  A warp
+// streams rows of one kind and length from contiguous memory, and the
+// storage rows of a chunk are, as a set, the natural rows 2 kChunk c .. of
+// the same chunk, so a CTA of one chunk writes its outputs contiguously.
+// nL = 0 (no matrix rows in the operator) gives the identity.
+constexpr int kChunk = 64;
 __host__ __device__ __forceinline__ int row_of_pair(int q, int nL, int nc) {
-  return q < nL ? 2 * q : (q < nc ? 2 * (q - nL) + 1 : q);
+  if (q >= nc) return q;
+  int c = q / (2 * kChunk), w = q - 2 * kChunk * c;
+  int k = nL - kChunk * c < kChunk ? nL - kChunk * c : kChunk;   // locations of chunk c
+  return w < k ? 2 * (kChunk * c + w) : 2 * (kChunk * c + w - k) + 1;
 }
 __host__ __device__ __forceinline__ int storage_row(int i, int nL, int nc) {
-  return i < nc ? ((i & 1) ? nL + (i >> 1) : (i >> 1)) : i;
+  if (i >= nc) return i;
+  int loc = i >> 1, c = loc / kChunk, w = loc - kChunk * c;
+  int k = nL - kChunk * c < kChunk ? nL - kChunk * c : kChunk;
+  return 2 * kChunk * c + ((i & 1) ? k + w : w);
 }
 
 inline int nblk(long long n, int b = kBlock) {

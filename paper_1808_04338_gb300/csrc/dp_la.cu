@@ -18,9 +18,13 @@ namespace dp {
 // pair) and accumulates its own output with FMAs, so no FP64 reduction
 // across lanes is needed.  A warp covers 16 block rows.
 //
-// The operator is read from its storage-order copy (fracture rows, then
-// matrix rows, then wells): pair q processes storage row q, whose blocks are
-// contiguous with those of pair q+1, and writes natural row row_of_pair(q).
+// The operator is read from its storage-order copy (chunks of fracture rows
+// then matrix rows, then wells): pair q processes storage row q, whose
+// blocks are contiguous with those of pair q+1.  A CTA takes 128 storage
+// rows, which are, as a set, the natural rows q0..q0+127; the results meet
+// in shared memory at their natural position and leave in one coalesced
+// write (a direct store to natural row row_of_pair(q) would write half
+// sectors: the fracture and matrix rows of a location are 16 bytes apart).
 
 // The well rows (storage rows nlong..n-1, one block per perforation, tens of
 // blocks each; their storage row is their row) go to block 0, a warp per
@@ -68,22 +72,30 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc, int 
     spmv_well_rows<MODE>(n, nlong, rowptr, col, val, x, b, y);
     return;
   }
-  int t = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
-  int comp = t & 1, q = t >> 1;
-  if (q >= nlong) return;
-  int row = row_of_pair(q, nL, nc);
-  int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
-  const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
-  const double2 *x2 = reinterpret_cast<const double2 *>(x);
-  double s = 0.0;
+  __shared__ double sh[kBlock];
+  int q0 = (blockIdx.x - 1) * (kBlock / 2);
+  int comp = threadIdx.x & 1, q = q0 + (threadIdx.x >> 1);
+  if (q < nlong) {
+    int row = row_of_pair(q, nL, nc);
+    int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
+    const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
+    const double2 *x2 = reinterpret_cast<const double2 *>(x);
+    double s = 0.0;
 #pragma unroll 4
-  for (int e = e0; e < e1; ++e) {
-    double2 a = __ldg(v2 + 2 * (size_t)e);
-    double2 xj = __ldg(x2 + __ldg(col + e));
-    s = fma(a.x, xj.x, s);
-    s = fma(a.y, xj.y, s);
+    for (int e = e0; e < e1; ++e) {
+      double2 a = __ldg(v2 + 2 * (size_t)e);
+      double2 xj = __ldg(x2 + __ldg(col + e));
+      s = fma(a.x, xj.x, s);
+      s = fma(a.y, xj.y, s);
+    }
+    sh[2 * (row - q0) + comp] = s;
   }
-  y[2 * (size_t)row + comp] = MODE == 0 ? s : b[2 * (size_t)row + comp] - s;
+  __syncthreads();
+  int cnt = nlong - q0 < kBlock / 2 ? nlong - q0 : kBlock / 2;
+  if ((int)threadIdx.x < 2 * cnt) {
+    size_t k = 2 * (size_t)q0 + threadIdx.x;
+    y[k] = MODE == 0 ? sh[threadIdx.x] : b[k] - sh[threadIdx.x];
+  }
 }
 
 // Pressure component of b - A x: rp_i = b_{i,0} - sum_j (a00 x_j0 + a01 x_j1),
@@ -112,19 +124,25 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
     }
     return;
   }
-  int t = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
-  if (t >= nlong) return;
-  int row = row_of_pair(t, nL, nc);
-  int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
-  const double2 *x2 = reinterpret_cast<const double2 *>(x);
-  double s = 0.0;
+  // a CTA takes storage rows q0..q0+255 (two chunks: the natural rows
+  // q0..q0+255 as a set) and writes rp through shared memory, coalesced
+  __shared__ double sh[kBlock];
+  int q0 = (blockIdx.x - 1) * kBlock, t = q0 + threadIdx.x;
+  if (t < nlong) {
+    int row = row_of_pair(t, nL, nc);
+    int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
+    const double2 *x2 = reinterpret_cast<const double2 *>(x);
+    double s = 0.0;
 #pragma unroll 4
-  for (int e = e0; e < e1; ++e) {
-    double2 xj = __ldg(x2 + __ldg(col + e));
-    s = fma(__ldg(a00 + e), xj.x, s);
-    s = fma(__ldg(a01 + e), xj.y, s);
+    for (int e = e0; e < e1; ++e) {
+      double2 xj = __ldg(x2 + __ldg(col + e));
+      s = fma(__ldg(a00 + e), xj.x, s);
+      s = fma(__ldg(a01 + e), xj.y, s);
+    }
+    sh[row - q0] = s;
   }
-  rp[row] = b[2 * (size_t)row] - s;
+  __syncthreads();
+  if (t < nlong) rp[t] = b[2 * (size_t)t] - sh[threadIdx.x];
 }
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
