@@ -1706,17 +1706,24 @@ int fgmres(Sim *s, double tol, int *iters, double *relres) {
   if (bnorm == 0.0) { conv = true; res = 0.0; }
   int gridN = (int)std::min<long long>(nblk(N), kDotBlocks * 4);
   while (!conv && total < maxit) {
-    DP_TRY(bsr_residual(s, s->bh, x, s->V));
-    DP_TRY(norm_into(s, s->V, s->scal + 1));
-    DP_LAUNCH(s, k_sqrt_inplace, 1, 1, 0, s->scal + 1);
-    DP_CUDA(s, cudaMemcpyAsync(s->h_res + 1, s->scal + 1, 8, cudaMemcpyDeviceToHost, s->stream));
-    DP_CUDA(s, cudaStreamSynchronize(s->stream));
-    double beta = s->h_res[1];
+    // v_0 = r / ||r||.  The first cycle starts from x = 0, where r = b - A 0
+    // = b exactly and ||r|| = ||b|| is already in scal[0]: no product.
+    const double *beta_dev = s->scal + 0;
+    double beta = bnorm;
+    if (total > 0) {
+      DP_TRY(bsr_residual(s, s->bh, x, s->V));
+      DP_TRY(norm_into(s, s->V, s->scal + 1));
+      DP_LAUNCH(s, k_sqrt_inplace, 1, 1, 0, s->scal + 1);
+      DP_CUDA(s, cudaMemcpyAsync(s->h_res + 1, s->scal + 1, 8, cudaMemcpyDeviceToHost, s->stream));
+      DP_CUDA(s, cudaStreamSynchronize(s->stream));
+      beta = s->h_res[1];
+      beta_dev = s->scal + 1;
+    }
     res = beta;
     if (beta <= tol * bnorm) { conv = true; break; }
-    DP_LAUNCH(s, k_scale, nblk(N), kBlock, 0, N, s->V, s->scal + 1, 1, s->V);
+    DP_LAUNCH(s, k_scale, nblk(N), kBlock, 0, N, total > 0 ? s->V : s->bh, beta_dev, 1, s->V);
     DP_CUDA(s, cudaMemsetAsync(s->H, 0, (size_t)(m + 1) * m * 8, s->stream));
-    DP_LAUNCH(s, k_init_g, 1, 64, 0, s->g, m, s->scal + 1);
+    DP_LAUNCH(s, k_init_g, 1, 64, 0, s->g, m, beta_dev);
     int jend = 0;
     for (int j = 0; j < m && total < maxit; ++j) {
       if (use_graph) DP_TRY(arnoldi_step_graph(s, j));
