@@ -147,6 +147,7 @@ int phys_well_controls(Sim *s, bool restore);
 int phys_well_rates(Sim *s, double *q);   // device q[2 nw]: oil rates, then water rates
 int phys_assemble(Sim *s);
 int phys_norms(Sim *s);
+int phys_norm_weights(Sim *s);    // s->norm_w, once the porosities are on the device
 int phys_decouple_extract(Sim *s);
 int phys_decoupled_natural(Sim *s, double *out);
 int phys_solver_view(Sim *s);     // K and the solver view, after phys_build_pattern
@@ -233,6 +234,7 @@ struct Sim {
   double *Macc = nullptr;                            // phase masses at the iterate, 2 x nc
   double dt = 1.0, inv_dt = 1.0;
   double *norm_part = nullptr;                       // reduction partials
+  double *norm_w = nullptr;                          // 1/(rho_ref phi_ref V), 2 x nc
   double *norm_out = nullptr;                        // 8 doubles
   double *h_norms = nullptr;                         // pinned host copy
   int norm_blocks = 0;

@@ -195,6 +195,29 @@ template <typename T> struct V2;
 template <> struct V2<double> { using t = double2; };
 template <> struct V2<float> { using t = float2; };
 
+// A 2x2 block (row-major, 16-byte aligned) loaded or stored with vector
+// accesses (coherent: the factorisation reads blocks that it also writes).
+template <typename T> struct Blk;
+template <> struct Blk<float> {
+  static __device__ __forceinline__ void load(const float *p, float *o) {
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  static __device__ __forceinline__ void store(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Blk<double> {
+  static __device__ __forceinline__ void load(const double *p, double *o) {
+    double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  static __device__ __forceinline__ void store(double *p, const double *v) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ void mul2(const T *a, const T *b, T *o) {
   T t0 = a[0] * b[0] + a[1] * b[2];
@@ -259,25 +282,35 @@ __global__ void k_ilu_upd(int n, int fill, const int *iperm, const int *lu_rowpt
 template <typename T>
 __global__ void k_ilu_factor(int r0, int r1, int nL, const int *lu_rowptr, const int *lu_dpos,
                              const int *dst, const int *colp, const int *upd_ptr,
-                             const int *upd_e2, const int *upd_q, T *lu) {
+                             const int *__restrict__ upd_e2, const int *__restrict__ upd_q,
+                             T *lu) {
   int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= r1) return;
-  int s0 = lu_rowptr[r], dp = lu_dpos[r];
+  // every block moves as one 16-byte (FP32) or two 16-byte (FP64) accesses;
+  // the index arrays are read-only
+  int s0 = __ldg(lu_rowptr + r), dp = __ldg(lu_dpos + r);
   for (int e = s0; e < dp; ++e) {
-    int k = dst[e];
-    int rk = colp[k];
-    T lik[4];
-    mul2<T>(lu + 4 * (size_t)k, lu + 4 * ((size_t)nL + rk), lik);   // A_ik U_kk^-1
-    T *le = lu + 4 * (size_t)k;
-    le[0] = lik[0]; le[1] = lik[1]; le[2] = lik[2]; le[3] = lik[3];
-    for (int p = upd_ptr[e]; p < upd_ptr[e + 1]; ++p) {
-      T u[4];
-      mul2<T>(lik, lu + 4 * (size_t)upd_q[p], u);
-      T *aij = lu + 4 * (size_t)upd_e2[p];
-      aij[0] -= u[0]; aij[1] -= u[1]; aij[2] -= u[2]; aij[3] -= u[3];
+    int k = __ldg(dst + e);
+    int rk = __ldg(colp + k);
+    T a[4], piv[4], lik[4];
+    Blk<T>::load(lu + 4 * (size_t)k, a);
+    Blk<T>::load(lu + 4 * ((size_t)nL + rk), piv);
+    mul2<T>(a, piv, lik);                                            // A_ik U_kk^-1
+    Blk<T>::store(lu + 4 * (size_t)k, lik);
+    for (int p = __ldg(upd_ptr + e), p1 = __ldg(upd_ptr + e + 1); p < p1; ++p) {
+      T ukj[4], u[4], c[4];
+      Blk<T>::load(lu + 4 * (size_t)__ldg(upd_q + p), ukj);
+      mul2<T>(lik, ukj, u);
+      T *aij = lu + 4 * (size_t)__ldg(upd_e2 + p);
+      Blk<T>::load(aij, c);
+      c[0] -= u[0]; c[1] -= u[1]; c[2] -= u[2]; c[3] -= u[3];
+      Blk<T>::store(aij, c);
     }
   }
-  inv2<T>(lu + 4 * ((size_t)nL + r));
+  T d[4];
+  Blk<T>::load(lu + 4 * ((size_t)nL + r), d);
+  inv2<T>(d);
+  Blk<T>::store(lu + 4 * ((size_t)nL + r), d);
 }
 
 // Forward sweep of one colour, two lanes per row (one per component):

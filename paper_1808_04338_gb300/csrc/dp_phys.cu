@@ -696,8 +696,26 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *phi_f,
-                                                       const double *phi_m, const double *R,
+// The cell rows' weights of the scaled residual, 1 / (rho_ref phi_ref V) per
+// cell and phase, formed once (an FP64 division per entry is a long
+// instruction sequence on this GPU; the norms then multiply).
+__global__ void k_norm_weights(Phys P, const double *phi_f, const double *phi_m, double *w) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.nc) return;
+  int loc = c >> 1;
+  double phi_ref = (c & 1) == 0 ? phi_f[loc] : phi_m[loc];
+  w[2 * c] = 1.0 / ((P.rho_o_ref * phi_ref) * P.V);
+  w[2 * c + 1] = 1.0 / ((P.rho_w_ref * phi_ref) * P.V);
+}
+
+int phys_norm_weights(Sim *s) {
+  DP_LAUNCH(s, k_norm_weights, nblk(s->ph.nc), kBlock, 0, s->ph, s->phi_f, s->phi_m, s->norm_w);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+__global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *__restrict__ w,
+                                                       const double *R,
                                                        const double *Macc, const double *Mn,
                                                        const int *well_kind,
                                                        const double *well_target, double dt,
@@ -705,12 +723,9 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *phi
   double v[7] = {0, 0, 0, 0, 0, 0, 0};  // s2, max, sro, srw, dmo, dmw, unused
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.nb; r += gridDim.x * blockDim.x) {
     if (r < P.nc) {
-      int loc = r >> 1;
-      double phi_ref = (r & 1) == 0 ? phi_f[loc] : phi_m[loc];
 #pragma unroll
       for (int al = 0; al < 2; ++al) {
-        double rref = al == 0 ? P.rho_o_ref : P.rho_w_ref;
-        double x = (R[2 * r + al] * dt) / ((rref * phi_ref) * P.V);
+        double x = (R[2 * r + al] * dt) * w[2 * r + al];
         v[0] += x * x;
         v[1] = fmax(v[1], fabs(x));
       }
@@ -781,7 +796,7 @@ __global__ void __launch_bounds__(kBlock) k_norms_final(Phys P, const double *ph
 
 int phys_norms(Sim *s) {
   Phys &P = s->ph;
-  DP_LAUNCH(s, k_norms_part, s->norm_blocks, kBlock, 0, P, s->phi_f, s->phi_m, s->R, s->Macc,
+  DP_LAUNCH(s, k_norms_part, s->norm_blocks, kBlock, 0, P, s->norm_w, s->R, s->Macc,
             s->Mn, s->well_kind, s->well_target, s->dt, s->norm_part);
   DP_LAUNCH(s, k_norms_final, 1, kBlock, 0, P, s->phi_f, s->phi_m, s->p, s->sw, s->bhp, s->perf_cell,
             s->perf_well, s->perf_wi, s->nperf, s->well_kind, s->norm_part, s->norm_blocks,

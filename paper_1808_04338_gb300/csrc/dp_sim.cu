@@ -234,9 +234,11 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   s->norm_blocks = std::min(nblk(P.nb), 1024);
   s->norm_part = (double *)dalloc(s, (size_t)s->norm_blocks * 64);
   s->norm_out = (double *)dalloc(s, 64);
+  s->norm_w = (double *)dalloc(s, 2 * nc8);
   if (!s->p || !s->sw || !s->bhp || !s->pn || !s->swn || !s->bhpn || !s->Mn || !s->R || !s->bh ||
-      !s->y || !s->norm_part || !s->norm_out || !s->pr || !s->Macc)
+      !s->y || !s->norm_part || !s->norm_out || !s->norm_w || !s->pr || !s->Macc)
     return fail(DP_ENOMEM);
+  if ((rc = phys_norm_weights(s))) return fail(rc);
   cudaMemsetAsync(s->p, 0, nc8, st); cudaMemsetAsync(s->sw, 0, nc8, st);
   cudaMemsetAsync(s->bhp, 0, nw8, st); cudaMemsetAsync(s->Mn, 0, 2 * nc8, st);
   cudaMemsetAsync(s->y, 0, nb16, st);
