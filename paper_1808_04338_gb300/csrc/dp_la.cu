@@ -786,19 +786,24 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restr
   int i = t / G, lane = t % G;
   bool valid = i < n;
   int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
-  T s0 = T(0), s1 = T(0);
+  // four independent accumulators, as in row_dot
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   int e = e0 + lane;
-  for (; e + G < e1; e += 2 * G) {
-    int c0 = __ldg(col + e), c1 = __ldg(col + e + G);
-    T v0 = __ldg(val + e), v1 = __ldg(val + e + G);
+  for (; e + 3 * G < e1; e += 4 * G) {
+    int c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
+        c3 = __ldg(col + e + 3 * G);
+    T v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G),
+      v3 = __ldg(val + e + 3 * G);
     s0 = fma(v0, __ldg(b + c0) * __ldg(d + c0), s0);
     s1 = fma(v1, __ldg(b + c1) * __ldg(d + c1), s1);
+    s2 = fma(v2, __ldg(b + c2) * __ldg(d + c2), s2);
+    s3 = fma(v3, __ldg(b + c3) * __ldg(d + c3), s3);
   }
-  if (e < e1) {
+  for (; e < e1; e += G) {
     int c0 = __ldg(col + e);
     s0 = fma(__ldg(val + e), __ldg(b + c0) * __ldg(d + c0), s0);
   }
-  T s = s0 + s1;
+  T s = (s0 + s1) + (s2 + s3);
   if (G > 1) s = group_sum<G, T>(s);
   if (valid && lane == 0) {
     T bi = b[i];
@@ -1104,14 +1109,25 @@ __global__ void __launch_bounds__(kBlock) k_gs_lu(int r0, int r1, const int *__r
   if (q >= r1) return;
   int i = __ldcs(perm + q);
   int e = __ldcs(lu_rowptr + q), e1 = __ldcs(lu_rowptr + q + 1);
-  T s0 = T(0), s1 = T(0);
-  for (; e + 1 < e1; e += 2) {
-    int c0 = __ldcs(lu_col + e), c1 = __ldcs(lu_col + e + 1);
-    T v0 = __ldcs(pv + e), v1 = __ldcs(pv + e + 1);
-    s0 = fma(v0, x[c0], s0);
-    s1 = fma(v1, x[c1], s1);
+  // the row's first eight entries (a cell row's whole stencil) in one batch
+  // of predicated loads, then their eight gathers of x, so that a thread waits
+  // for two memory round trips instead of one pair per two entries
+  constexpr int kB = 8;
+  int c[kB];
+  T v[kB];
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    bool in = e + k < e1;
+    c[k] = in ? __ldcs(lu_col + e + k) : 0;
+    v[k] = in ? __ldcs(pv + e + k) : T(0);
   }
-  if (e < e1) s0 = fma(__ldcs(pv + e), x[__ldcs(lu_col + e)], s0);
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int k = 0; k < kB; k += 2) {
+    if (e + k < e1) s0 = fma(v[k], x[c[k]], s0);
+    if (e + k + 1 < e1) s1 = fma(v[k + 1], x[c[k + 1]], s1);
+  }
+  for (e += kB; e < e1; ++e) s0 = fma(__ldcs(pv + e), x[__ldcs(lu_col + e)], s0);
   T s = s0 + s1;
   T di = dinv[i];
   if (di != T(0)) x[i] = fma(b[i] - s, di, x[i]);
