@@ -161,11 +161,58 @@ def oracle_sample(args, budget_s=25.0):
                       f"by the unknown ratio {scale:g} to 8M unknowns; single-threaded C"}
 
 
+def _oracle_worker(nx, ny, nz, nsteps, barrier, out):
+    """One process of the all-core oracle sample: set up, wait for the
+    others, then time nsteps Newton steps of its own copy of the slice."""
+    import dp_inputs as di
+    import oracle as O
+    prob = di.field8m(nx, ny, nz)
+    s = O.OracleSim(prob, O.options("report"))
+    s.assemble(prob.dt)
+    s.solve_step()
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        s.set_state(prob.p0, prob.sw0, prob.bhp0)
+        s.assemble(prob.dt)
+        s.solve_step()
+    out.put(time.perf_counter() - t0)
+
+
+def oracle_sample_all_cores(args, nsteps=2):
+    """The same oracle on every host core at once: one process per core
+    (started with spawn), each running nsteps Newton steps of its own copy of
+    the slice that oracle_sample times; throughput = steps of all processes /
+    the slowest process's time, scaled to the full problem like
+    oracle_sample.  The oracle itself is single-threaded C, unchanged."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    nz = max(1, args.nz // args.sample_div)
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(args.nx, args.ny, nz, nsteps, barrier, out))
+             for _ in range(cores)]
+    for p in procs:
+        p.start()
+    times = [out.get(timeout=900) for _ in procs]
+    for p in procs:
+        p.join()
+    scale = (2 * args.nx * args.ny * args.nz) / (2 * args.nx * args.ny * nz)
+    return {"value": cores * nsteps / (max(times) * scale), "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{cores} processes, each {nsteps} Newton steps of its own "
+                      f"{args.nx}x{args.ny}x{nz} grid after its set-up, started together; "
+                      f"steps of all processes / the slowest process's time, scaled by "
+                      f"{scale:g} to 8M unknowns"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = oracle_sample(args)
+    # the oracle on every host core (one process per core), and on one core
+    cb = oracle_sample_all_cores(args)
+    cb["single_core"] = oracle_sample(args)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True,
@@ -564,6 +611,10 @@ def main():
             except Exception as e:  # report, do not fail the bench
                 cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                        "sample": f"failed: {e}"}
+            try:
+                cpu["all_cores"] = oracle_sample_all_cores(args)
+            except Exception as e:
+                cpu["all_cores"] = {"value": None, "sample": f"failed: {e}"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

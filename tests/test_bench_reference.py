@@ -1,0 +1,21 @@
+"""The bench's reference arm (the oracle on the host cores) runs without a GPU
+and prints one JSON line in the bench contract's form."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_its_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--nx", "12", "--ny",
+                          "12", "--nz", "4", "--sample-div", "1", "--steps", "1", "--warmup", "1"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0.0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] == line["value"] and cb["single_core"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["warmup"] >= 3
