@@ -279,6 +279,8 @@ struct Sim {
   // pressure rows (entries (0,0) and (0,1) of every block) as separate arrays
   int *srowptr = nullptr, *scol = nullptr;
   double *sval = nullptr, *sa00 = nullptr, *sa01 = nullptr;
+  float *svalf = nullptr;   // precision 1: FP32 copy of sval (CPR stage residuals)
+  float *spf = nullptr;     //   and the (a00, a01) pair of every block, FP32
   double *coarse_lu = nullptr;
   double *coarse_inv = nullptr;
   // level-0 pressure values in the colour order of the ILU(0) pattern (the

@@ -145,6 +145,118 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
   if (t < nlong) rp[t] = b[2 * (size_t)t] - sh[threadIdx.x];
 }
 
+// Residuals inside the CPR preconditioner with the FP32 preconditioner
+// (precision 1), from an FP32 copy of the decoupled operator: the stage
+// residuals feed the FP32 ILU(0) and the FP32 V-cycle only, so products in
+// FP32 (the vectors read in FP64 and rounded) change nothing that the
+// preconditioner's own rounding does not already, and take the stage
+// residuals off GB300's FP64 pipe.  FGMRES itself (its Arnoldi products,
+// restart residuals and orthogonalisation) stays in FP64; a flexible method
+// takes any preconditioner.
+//
+// r = b - A x: the layout and work split of k_bsr_spmv (a CTA of 128
+// storage rows writing its natural rows through shared memory), FP32 values
+// (16-byte blocks: the lane of component c reads that row as a float2).
+__global__ void __launch_bounds__(kBlock) k_bsr_resid_f32(int n, int nL, int nc, int nlong,
+                                                         const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         const float *__restrict__ valf,
+                                                         const double *__restrict__ x,
+                                                         const double *__restrict__ b,
+                                                         double *__restrict__ y) {
+  const float2 *v2 = reinterpret_cast<const float2 *>(valf);
+  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  if (blockIdx.x == 0) {   // the well rows, a warp per row
+    int lane = threadIdx.x & 31;
+    for (int row = nlong + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+      float s0 = 0.f, s1 = 0.f;
+      for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
+        float2 a = __ldg(v2 + 2 * (size_t)e), c = __ldg(v2 + 2 * (size_t)e + 1);
+        double2 xd = __ldg(x2 + __ldg(col + e));
+        float xa = float(xd.x), xb = float(xd.y);
+        s0 = fmaf(a.x, xa, fmaf(a.y, xb, s0));
+        s1 = fmaf(c.x, xa, fmaf(c.y, xb, s1));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (lane == 0) {
+        y[2 * (size_t)row] = b[2 * (size_t)row] - double(s0);
+        y[2 * (size_t)row + 1] = b[2 * (size_t)row + 1] - double(s1);
+      }
+    }
+    return;
+  }
+  __shared__ float sh[kBlock];
+  int q0 = (blockIdx.x - 1) * (kBlock / 2);
+  int comp = threadIdx.x & 1, q = q0 + (threadIdx.x >> 1);
+  if (q < nlong) {
+    int row = row_of_pair(q, nL, nc);
+    int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
+    float s = 0.f;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+      float2 a = __ldg(v2 + 2 * (size_t)e + comp);
+      double2 xd = __ldg(x2 + __ldg(col + e));
+      s = fmaf(a.x, float(xd.x), s);
+      s = fmaf(a.y, float(xd.y), s);
+    }
+    sh[2 * (row - q0) + comp] = s;
+  }
+  __syncthreads();
+  int cnt = nlong - q0 < kBlock / 2 ? nlong - q0 : kBlock / 2;
+  if ((int)threadIdx.x < 2 * cnt) {
+    size_t k = 2 * (size_t)q0 + threadIdx.x;
+    y[k] = b[k] - double(sh[threadIdx.x]);
+  }
+}
+
+// The pressure rows of b - A x from the FP32 (a00, a01) pairs, written in
+// FP32 straight into the V-cycle's level-0 right-hand side (natural order).
+__global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc, int nlong,
+                                                          const int *__restrict__ rowptr,
+                                                          const int *__restrict__ col,
+                                                          const float2 *__restrict__ pf,
+                                                          const double *__restrict__ x,
+                                                          const double *__restrict__ b,
+                                                          float *__restrict__ rp) {
+  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  if (blockIdx.x == 0) {
+    int lane = threadIdx.x & 31;
+    for (int row = nlong + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+      float s = 0.f;
+      for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
+        double2 xd = __ldg(x2 + __ldg(col + e));
+        float2 a = __ldg(pf + e);
+        s = fmaf(a.x, float(xd.x), fmaf(a.y, float(xd.y), s));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) rp[row] = float(b[2 * (size_t)row] - double(s));
+    }
+    return;
+  }
+  __shared__ float sh[kBlock];
+  int q0 = (blockIdx.x - 1) * kBlock, t = q0 + threadIdx.x;
+  if (t < nlong) {
+    int row = row_of_pair(t, nL, nc);
+    int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
+    float s = 0.f;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+      double2 xd = __ldg(x2 + __ldg(col + e));
+      float2 a = __ldg(pf + e);
+      s = fmaf(a.x, float(xd.x), s);
+      s = fmaf(a.y, float(xd.y), s);
+    }
+    sh[row - q0] = s;
+  }
+  __syncthreads();
+  if (t < nlong) rp[t] = float(b[2 * (size_t)t] - double(sh[threadIdx.x]));
+}
+
 int bsr_spmv(Sim *s, const double *x, double *y) {
   DP_LAUNCH(s, k_bsr_spmv<0>, 1 + nblk(2LL * s->sv_long0), kBlock, 0, s->K.n, s->sv_sL, s->sv_sc,
             s->sv_long0,
@@ -1397,20 +1509,22 @@ int cpr_apply(Sim *s, const double *r, double *z) {
     DP_TRY((ilu_apply_t<double, double>(s, s->lu_val, s->r1)));
     return ilu_result<double>(s, s->z1, z);           // z = z2 + F (r - A z2)
   }
-  // FP32 factor, FP32 V-cycle; the stage residuals stay in FP64
+  // FP32 factor, FP32 V-cycle, FP32 stage residuals
   if (s->opt.precond == 1) {
     DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
     return ilu_result<float>(s, nullptr, z);
   }
+  // the stage residuals from the FP32 copy of the operator
   Level &L0 = s->lev[0];
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
   DP_TRY(ilu_result<float>(s, nullptr, s->z1));
-  DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
-            s->sv_long0, s->srowptr, s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
-  DP_LAUNCH(s, k_to_f32, nblk(nb), kBlock, 0, (long long)nb, s->rp, L0.bf);
+  DP_LAUNCH(s, k_bsr_presid_f32, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
+            s->sv_long0, s->srowptr, s->scol, reinterpret_cast<const float2 *>(s->spf), s->z1,
+            r, L0.bf);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
   DP_LAUNCH(s, k_inject_add<float>, nblk(nb), kBlock, 0, nb, L0.xf, s->z1);
-  DP_TRY(bsr_residual(s, r, s->z1, s->r1));
+  DP_LAUNCH(s, k_bsr_resid_f32, 1 + nblk(2LL * s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
+            s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1, r, s->r1);
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, s->r1)));
   return ilu_result<float>(s, s->z1, z);              // z = z2 + F (r - A z2)
 }

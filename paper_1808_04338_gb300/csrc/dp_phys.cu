@@ -365,12 +365,18 @@ int phys_build_pattern(Sim *s) {
   s->trans = (double *)dalloc(s, (size_t)nnz * 8);
   s->ap = (double *)dalloc(s, (size_t)nnz * 8);
   s->sval = (double *)dalloc(s, (size_t)nnz * 32);
-  s->sa00 = (double *)dalloc(s, (size_t)nnz * 8);
-  s->sa01 = (double *)dalloc(s, (size_t)nnz * 8);
+  if (s->opt.precision == 1) {   // the preconditioner's residuals in FP32
+    s->svalf = (float *)dalloc(s, (size_t)nnz * 16);
+    s->spf = (float *)dalloc(s, (size_t)nnz * 8);
+    if (!s->svalf || !s->spf) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  } else {
+    s->sa00 = (double *)dalloc(s, (size_t)nnz * 8);
+    s->sa01 = (double *)dalloc(s, (size_t)nnz * 8);
+    if (!s->sa00 || !s->sa01) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  }
   s->scol = (int *)dalloc(s, (size_t)nnz * 4);
   s->srowptr = (int *)dalloc(s, ((size_t)P.nb + 1) * 4);
-  if (!s->A.col || !s->A.val || !s->trans || !s->ap || !s->sval || !s->sa00 || !s->sa01 ||
-      !s->scol || !s->srowptr) {
+  if (!s->A.col || !s->A.val || !s->trans || !s->ap || !s->sval || !s->scol || !s->srowptr) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
@@ -877,6 +883,7 @@ struct DecArgs {
   const int *erow, *rowptr, *srowptr, *ilupos, *l0pos;
   const double *val, *fct;
   double *ap, *sval, *sa00, *sa01;
+  float *svalf, *spf;   // FP32 copies for the preconditioner's residuals, or null
   void *lu;         // split-layout factor values (float or double), or null
   void *l0;         // colour-ordered level-0 pressure values, or null
 };
@@ -913,8 +920,14 @@ __global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
   double2 *sv = reinterpret_cast<double2 *>(a.sval) + 2 * q;
   sv[0] = make_double2(n0, n1);
   sv[1] = make_double2(n2, n3);
-  a.sa00[q] = n0;
-  a.sa01[q] = n1;
+  if (a.sa00) {
+    a.sa00[q] = n0;
+    a.sa01[q] = n1;
+  }
+  if (a.svalf) {
+    reinterpret_cast<float4 *>(a.svalf)[q] = make_float4(float(n0), float(n1), float(n2), float(n3));
+    reinterpret_cast<float2 *>(a.spf)[q] = make_float2(float(n0), float(n1));
+  }
   if (a.lu) {
     T *d = reinterpret_cast<T *>(a.lu) + 4 * (size_t)__ldg(a.ilupos + e);
     d[0] = T(n0); d[1] = T(n1); d[2] = T(n2); d[3] = T(n3);
@@ -933,6 +946,7 @@ int phys_decouple_extract(Sim *s) {
   a.ilupos = s->ilupos; a.l0pos = s->l0pos;
   a.val = K.val; a.fct = s->fct;
   a.ap = s->ap; a.sval = s->sval; a.sa00 = s->sa00; a.sa01 = s->sa01;
+  a.svalf = s->svalf; a.spf = s->spf;
   bool f32 = s->opt.precision == 1;
   a.lu = s->opt.precond >= 1 ? (f32 ? (void *)s->lu_valf : (void *)s->lu_val) : nullptr;
   a.l0 = s->l0_lu ? (f32 ? (void *)s->l0_pvf : (void *)s->l0_pv) : nullptr;
