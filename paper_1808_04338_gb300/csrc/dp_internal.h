@@ -281,6 +281,7 @@ struct Sim {
   double *sval = nullptr, *sa00 = nullptr, *sa01 = nullptr;
   float *svalf = nullptr;   // precision 1: FP32 copy of sval (CPR stage residuals)
   float *spf = nullptr;     //   and the (a00, a01) pair of every block, FP32
+  float *z1f = nullptr, *r1f = nullptr;   // FP32 stage vectors of the CPR preconditioner
   double *coarse_lu = nullptr;
   double *coarse_inv = nullptr;
   // level-0 pressure values in the colour order of the ILU(0) pattern (the

@@ -161,21 +161,20 @@ __global__ void __launch_bounds__(kBlock) k_bsr_resid_f32(int n, int nL, int nc,
                                                          const int *__restrict__ rowptr,
                                                          const int *__restrict__ col,
                                                          const float *__restrict__ valf,
-                                                         const double *__restrict__ x,
+                                                         const float *__restrict__ x,
                                                          const double *__restrict__ b,
-                                                         double *__restrict__ y) {
+                                                         float *__restrict__ y) {
   const float2 *v2 = reinterpret_cast<const float2 *>(valf);
-  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  const float2 *x2 = reinterpret_cast<const float2 *>(x);
   if (blockIdx.x == 0) {   // the well rows, a warp per row
     int lane = threadIdx.x & 31;
     for (int row = nlong + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
       float s0 = 0.f, s1 = 0.f;
       for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
         float2 a = __ldg(v2 + 2 * (size_t)e), c = __ldg(v2 + 2 * (size_t)e + 1);
-        double2 xd = __ldg(x2 + __ldg(col + e));
-        float xa = float(xd.x), xb = float(xd.y);
-        s0 = fmaf(a.x, xa, fmaf(a.y, xb, s0));
-        s1 = fmaf(c.x, xa, fmaf(c.y, xb, s1));
+        float2 xj = __ldg(x2 + __ldg(col + e));
+        s0 = fmaf(a.x, xj.x, fmaf(a.y, xj.y, s0));
+        s1 = fmaf(c.x, xj.x, fmaf(c.y, xj.y, s1));
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -183,8 +182,8 @@ __global__ void __launch_bounds__(kBlock) k_bsr_resid_f32(int n, int nL, int nc,
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       }
       if (lane == 0) {
-        y[2 * (size_t)row] = b[2 * (size_t)row] - double(s0);
-        y[2 * (size_t)row + 1] = b[2 * (size_t)row + 1] - double(s1);
+        y[2 * (size_t)row] = float(b[2 * (size_t)row]) - s0;
+        y[2 * (size_t)row + 1] = float(b[2 * (size_t)row + 1]) - s1;
       }
     }
     return;
@@ -199,9 +198,9 @@ __global__ void __launch_bounds__(kBlock) k_bsr_resid_f32(int n, int nL, int nc,
 #pragma unroll 4
     for (int e = e0; e < e1; ++e) {
       float2 a = __ldg(v2 + 2 * (size_t)e + comp);
-      double2 xd = __ldg(x2 + __ldg(col + e));
-      s = fmaf(a.x, float(xd.x), s);
-      s = fmaf(a.y, float(xd.y), s);
+      float2 xj = __ldg(x2 + __ldg(col + e));
+      s = fmaf(a.x, xj.x, s);
+      s = fmaf(a.y, xj.y, s);
     }
     sh[2 * (row - q0) + comp] = s;
   }
@@ -209,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_resid_f32(int n, int nL, int nc,
   int cnt = nlong - q0 < kBlock / 2 ? nlong - q0 : kBlock / 2;
   if ((int)threadIdx.x < 2 * cnt) {
     size_t k = 2 * (size_t)q0 + threadIdx.x;
-    y[k] = b[k] - double(sh[threadIdx.x]);
+    y[k] = float(b[k]) - sh[threadIdx.x];
   }
 }
 
@@ -219,22 +218,22 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc
                                                           const int *__restrict__ rowptr,
                                                           const int *__restrict__ col,
                                                           const float2 *__restrict__ pf,
-                                                          const double *__restrict__ x,
+                                                          const float *__restrict__ x,
                                                           const double *__restrict__ b,
                                                           float *__restrict__ rp) {
-  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  const float2 *x2 = reinterpret_cast<const float2 *>(x);
   if (blockIdx.x == 0) {
     int lane = threadIdx.x & 31;
     for (int row = nlong + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
       float s = 0.f;
       for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
-        double2 xd = __ldg(x2 + __ldg(col + e));
+        float2 xj = __ldg(x2 + __ldg(col + e));
         float2 a = __ldg(pf + e);
-        s = fmaf(a.x, float(xd.x), fmaf(a.y, float(xd.y), s));
+        s = fmaf(a.x, xj.x, fmaf(a.y, xj.y, s));
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) rp[row] = float(b[2 * (size_t)row] - double(s));
+      if (lane == 0) rp[row] = float(b[2 * (size_t)row]) - s;
     }
     return;
   }
@@ -246,15 +245,15 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc
     float s = 0.f;
 #pragma unroll 4
     for (int e = e0; e < e1; ++e) {
-      double2 xd = __ldg(x2 + __ldg(col + e));
+      float2 xj = __ldg(x2 + __ldg(col + e));
       float2 a = __ldg(pf + e);
-      s = fmaf(a.x, float(xd.x), s);
-      s = fmaf(a.y, float(xd.y), s);
+      s = fmaf(a.x, xj.x, s);
+      s = fmaf(a.y, xj.y, s);
     }
     sh[row - q0] = s;
   }
   __syncthreads();
-  if (t < nlong) rp[t] = float(b[2 * (size_t)t] - double(sh[threadIdx.x]));
+  if (t < nlong) rp[t] = float(b[2 * (size_t)t]) - sh[threadIdx.x];
 }
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
@@ -807,19 +806,22 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
 // natural order, FP64; two lanes per block row.
 template <typename T>
 __global__ void k_ilu_result(int n, const int *__restrict__ iperm, const T *__restrict__ zp,
-                             const double *__restrict__ base, double *__restrict__ out) {
+                             const double *__restrict__ base, double *__restrict__ out,
+                             T *__restrict__ outT) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2LL * n) return;
   int i = (int)(t >> 1), comp = (int)(t & 1);
-  double v = double(zp[2 * (size_t)__ldg(iperm + i) + comp]);
+  T z = zp[2 * (size_t)__ldg(iperm + i) + comp];
+  double v = double(z);
   out[t] = base ? base[t] + v : v;
+  if (outT) outT[t] = z;   // the result also in the sweep's precision (no base)
 }
 
 template <typename T>
-static int ilu_result(Sim *s, const double *base, double *out) {
+static int ilu_result(Sim *s, const double *base, double *out, T *outT = nullptr) {
   int n = s->K.n;
   DP_LAUNCH(s, k_ilu_result<T>, nblk(2LL * n), kBlock, 0, n, s->iperm,
-            reinterpret_cast<const T *>(s->ilu_zp), base, out);
+            reinterpret_cast<const T *>(s->ilu_zp), base, out, outT);
   return DP_OK;
 }
 
@@ -1483,6 +1485,17 @@ __global__ void k_inject_add(int n, const T *xp, double *z) {
   if (i < n) z[2 * i] += double(xp[i]);
 }
 
+// The same injection applied to an FP64 vector and to its FP32 copy (the
+// copy updated in FP32: no conversions on the FP64 pipe).
+__global__ void k_inject_add2(int n, const float *xp, double *z, float *zf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    float e = xp[i];
+    z[2 * i] += double(e);
+    zf[2 * i] += e;
+  }
+}
+
 
 __global__ void k_to_f32(long long n, const double *x, float *y) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1515,17 +1528,18 @@ int cpr_apply(Sim *s, const double *r, double *z) {
     return ilu_result<float>(s, nullptr, z);
   }
   // the stage residuals from the FP32 copy of the operator
+  // (z1 and z2 also kept in FP32 for the residuals' gathers; r - A z2 in FP32)
   Level &L0 = s->lev[0];
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
-  DP_TRY(ilu_result<float>(s, nullptr, s->z1));
+  DP_TRY(ilu_result<float>(s, nullptr, s->z1, s->z1f));
   DP_LAUNCH(s, k_bsr_presid_f32, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
-            s->sv_long0, s->srowptr, s->scol, reinterpret_cast<const float2 *>(s->spf), s->z1,
+            s->sv_long0, s->srowptr, s->scol, reinterpret_cast<const float2 *>(s->spf), s->z1f,
             r, L0.bf);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
-  DP_LAUNCH(s, k_inject_add<float>, nblk(nb), kBlock, 0, nb, L0.xf, s->z1);
+  DP_LAUNCH(s, k_inject_add2, nblk(nb), kBlock, 0, nb, L0.xf, s->z1, s->z1f);
   DP_LAUNCH(s, k_bsr_resid_f32, 1 + nblk(2LL * s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
-            s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1, r, s->r1);
-  DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, s->r1)));
+            s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1f, r, s->r1f);
+  DP_TRY((ilu_apply_t<float, float>(s, s->lu_valf, s->r1f)));
   return ilu_result<float>(s, s->z1, z);              // z = z2 + F (r - A z2)
 }
 
@@ -1928,6 +1942,11 @@ int la_alloc(Sim *s) {
   s->scal = (double *)dalloc(s, 8 * 8);
   s->z1 = (double *)dalloc(s, (size_t)N * 8);
   s->r1 = (double *)dalloc(s, (size_t)N * 8);
+  if (s->opt.precision == 1) {
+    s->z1f = (float *)dalloc(s, (size_t)N * 4);
+    s->r1f = (float *)dalloc(s, (size_t)N * 4);
+    if (!s->z1f || !s->r1f) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  }
   s->rp = (double *)dalloc(s, (size_t)s->K.n * 8);
   s->xp = (double *)dalloc(s, (size_t)s->K.n * 8);
   if (!s->V || !s->Z || !s->w || !s->H || !s->cs || !s->sn || !s->g || !s->hy || !s->dots_part ||
