@@ -72,12 +72,12 @@ def sweep_bytes(nb, nnzb):
     (16 B), the FP32 result written (8 B) and its neighbours' values read
     once (8 B).  Backward: per U block 20 B; per row 12 B of indices, the
     inverted pivot block (16 B), z read, gathered and written (24 B).
-    Gauss-Seidel (FP32 pressure values): per entry 4 B value + 4 B column;
-    per row the row pointer and permutation (8 B), 1/a_ii, b, x read and
-    written, x gathered (20 B)."""
+    Gauss-Seidel (FP32 pressure values, level 0 in the colour order of the
+    ILU(0)): per entry 4 B value + 4 B column; per row the row pointer, 1/a_ii,
+    b, x read and written, x gathered (24 B)."""
     half = (nnzb - nb) // 2
     return {"k_ilu_fwd": 20 * half + 44 * nb, "k_ilu_bwd": 20 * half + 52 * nb,
-            "k_gs_lu": 8 * nnzb + 28 * nb}
+            "k_gs_c": 8 * nnzb + 24 * nb}
 
 
 class Clocks:

@@ -178,7 +178,7 @@ int cpr_apply(Sim *s, const double *r, double *z);
 int fgmres(Sim *s, double tol, int *iters, double *relres);
 int la_alloc(Sim *s);
 int mixed_refresh(Sim *s, bool coarse);
-int l0_refresh(Sim *s);
+int l0_refresh(Sim *s, bool coarse);
 int lanes_for(double mean_len);
 void graphs_free(Sim *s);
 int autotune(Sim *s, int reps, std::string &report);
@@ -286,6 +286,17 @@ struct Sim {
   double *coarse_inv = nullptr;
   // level-0 pressure values in the colour order of the ILU(0) pattern (the
   // same greedy colouring), for contiguous Gauss-Seidel colour sweeps
+  // Level 0 in colour order: when its Gauss-Seidel runs on the ILU(0)
+  // colouring (l0_lu), the level's vectors are kept in that colour order, so
+  // that the sweeps, the residual and the transfers stream them contiguously
+  // (natural order would read each at stride 2: one location's fracture and
+  // matrix rows fall in different colours).
+  bool l0c = false;
+  int *l0_colp = nullptr;                                 // colour position of each column
+  int *r0_colp = nullptr;                                 // R0's columns, colour positions
+  int *p0c_rowptr = nullptr, *p0c_col = nullptr, *p0c_src = nullptr;  // P0, rows in colour order
+  double *p0c_val = nullptr, *dinv_c = nullptr;
+  float *p0c_valf = nullptr, *dinv_cf = nullptr;
   bool l0_lu = false;
   double *l0_pv = nullptr;
   float *l0_pvf = nullptr;   // inverse from the LU factors (n <= kInverseMax), row-major

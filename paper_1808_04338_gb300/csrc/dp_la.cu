@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
                                                        const double *__restrict__ a01,
                                                        const double *__restrict__ x,
                                                        const double *__restrict__ b,
-                                                       double *__restrict__ rp) {
+                                                       double *__restrict__ rp,
+                                                       const int *__restrict__ omap) {
   if (blockIdx.x == 0) {   // the well rows, a warp per row (as in k_bsr_spmv)
     int lane = threadIdx.x & 31;
     const double2 *x2 = reinterpret_cast<const double2 *>(x);
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) rp[row] = b[2 * (size_t)row] - s;
+      if (lane == 0) rp[omap ? omap[row] : row] = b[2 * (size_t)row] - s;
     }
     return;
   }
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
     sh[row - q0] = s;
   }
   __syncthreads();
-  if (t < nlong) rp[t] = b[2 * (size_t)t] - sh[threadIdx.x];
+  if (t < nlong) rp[omap ? __ldg(omap + t) : t] = b[2 * (size_t)t] - sh[threadIdx.x];
 }
 
 // Residuals inside the CPR preconditioner with the FP32 preconditioner
@@ -220,7 +221,8 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc
                                                           const float2 *__restrict__ pf,
                                                           const float *__restrict__ x,
                                                           const double *__restrict__ b,
-                                                          float *__restrict__ rp) {
+                                                          float *__restrict__ rp,
+                                                          const int *__restrict__ omap) {
   const float2 *x2 = reinterpret_cast<const float2 *>(x);
   if (blockIdx.x == 0) {
     int lane = threadIdx.x & 31;
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) rp[row] = float(b[2 * (size_t)row]) - s;
+      if (lane == 0) rp[omap ? omap[row] : row] = float(b[2 * (size_t)row]) - s;
     }
     return;
   }
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc
     sh[row - q0] = s;
   }
   __syncthreads();
-  if (t < nlong) rp[t] = float(b[2 * (size_t)t]) - sh[threadIdx.x];
+  if (t < nlong) rp[omap ? __ldg(omap + t) : t] = float(b[2 * (size_t)t]) - sh[threadIdx.x];
 }
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
@@ -1278,10 +1280,64 @@ __global__ void k_gather_vals(long long n, const int *__restrict__ src, const do
 // The colour-ordered level-0 values (used when level 0 is smoothed by
 // Gauss-Seidel: its colouring is the ILU(0) colouring, same pattern and same
 // algorithm): gathered here when first needed, then written by the
-// decoupling every Newton step.
-int l0_refresh(Sim *s) {
+// decoupling every Newton step.  With them, level 0 runs in colour order
+// (Sim::l0c): the colour positions of the copy's columns and of R0's columns
+// and P0 with its rows in colour order are built once; 1/a_ii in colour order
+// every Newton step, P0's values whenever the coarse values are refreshed.
+__global__ void k_perm_rows(int n, const int *perm, const int *rowptr, const int *col,
+                            const int *prow, int *pcol, int *psrc) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  int i = perm[q], e0 = rowptr[i], m = rowptr[i + 1] - e0, d0 = prow[q];
+  for (int k = 0; k < m; ++k) { pcol[d0 + k] = col[e0 + k]; psrc[d0 + k] = e0 + k; }
+}
+
+__global__ void k_map_copy(long long n, const int *map, const int *in, int *out) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = map[in[e]];
+}
+
+static int l0c_setup(Sim *s) {
+  Level &L = s->lev[0];
+  int n = L.n;
+  s->l0_colp = (int *)dalloc(s, (size_t)std::max(L.nnz, 1) * 4);
+  s->r0_colp = (int *)dalloc(s, (size_t)std::max(L.r_nnz, 1) * 4);
+  s->p0c_rowptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
+  s->p0c_col = (int *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
+  s->p0c_src = (int *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
+  int *len = (int *)dalloc(s, (size_t)n * 4);
+  bool f32 = s->opt.precision == 1;
+  if (f32) {
+    s->p0c_valf = (float *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
+    s->dinv_cf = (float *)dalloc(s, (size_t)n * 4);
+  } else {
+    s->p0c_val = (double *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 8);
+    s->dinv_c = (double *)dalloc(s, (size_t)n * 8);
+  }
+  if (!s->l0_colp || !s->r0_colp || !s->p0c_rowptr || !s->p0c_col || !s->p0c_src || !len ||
+      (f32 ? (!s->p0c_valf || !s->dinv_cf) : (!s->p0c_val || !s->dinv_c))) {
+    s->fail(DP_ENOMEM, "allocation failed");
+    return DP_ENOMEM;
+  }
+  DP_LAUNCH(s, k_map_copy, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->iperm, s->lu_col,
+            s->l0_colp);
+  DP_LAUNCH(s, k_map_copy, nblk(L.r_nnz), kBlock, 0, (long long)L.r_nnz, s->iperm, L.r_col,
+            s->r0_colp);
+  DP_LAUNCH(s, k_perm_len, nblk(n), kBlock, 0, n, s->perm, L.p_rowptr, len);
+  int pn = 0;
+  DP_TRY(scan_i32(s, len, s->p0c_rowptr, n, &pn));
+  DP_LAUNCH(s, k_perm_rows, nblk(n), kBlock, 0, n, s->perm, L.p_rowptr, L.p_col, s->p0c_rowptr,
+            s->p0c_col, s->p0c_src);
+  DP_CUDA(s, cudaGetLastError());
+  dfree(s, len);
+  s->l0c = true;
+  return DP_OK;
+}
+
+int l0_refresh(Sim *s, bool coarse) {
   if (s->lev.empty() || s->opt.precond != 2) return DP_OK;
   Level &L = s->lev[0];
+  bool first = false;
   if (!s->l0_lu) {
     if (L.l1 || L.ncolour != s->ncolour || L.rowptr != s->K.rowptr) return DP_OK;
     for (int c = 0; c <= L.ncolour; ++c)
@@ -1291,16 +1347,192 @@ int l0_refresh(Sim *s) {
     else s->l0_pv = (double *)dalloc(s, nnz * 8);
     if (!s->l0_pvf && !s->l0_pv) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
     s->l0_lu = true;
-  } else {
-    return DP_OK;   // later Newton steps: the decoupling writes the copy
+    first = true;
+    // later Newton steps: the decoupling writes the copy
+    if (s->l0_pvf)
+      DP_LAUNCH(s, k_gather_vals<float>, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->lu_src,
+                L.val, s->l0_pvf);
+    else
+      DP_LAUNCH(s, k_gather_vals<double>, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->lu_src,
+                L.val, s->l0_pv);
+    if (s->lev.size() > 1) DP_TRY(l0c_setup(s));
   }
-  if (s->l0_pvf)
-    DP_LAUNCH(s, k_gather_vals<float>, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->lu_src, L.val,
-              s->l0_pvf);
-  else
-    DP_LAUNCH(s, k_gather_vals<double>, nblk(L.nnz), kBlock, 0, (long long)L.nnz, s->lu_src, L.val,
-              s->l0_pv);
+  if (s->l0c) {
+    if (s->dinv_cf)
+      DP_LAUNCH(s, k_gather_vals<float>, nblk(L.n), kBlock, 0, (long long)L.n, s->perm, L.dinv,
+                s->dinv_cf);
+    else
+      DP_LAUNCH(s, k_gather_vals<double>, nblk(L.n), kBlock, 0, (long long)L.n, s->perm, L.dinv,
+                s->dinv_c);
+    if (coarse || first) {
+      if (s->p0c_valf)
+        DP_LAUNCH(s, k_gather_vals<float>, nblk(L.p_nnz), kBlock, 0, (long long)L.p_nnz,
+                  s->p0c_src, L.p_val, s->p0c_valf);
+      else
+        DP_LAUNCH(s, k_gather_vals<double>, nblk(L.p_nnz), kBlock, 0, (long long)L.p_nnz,
+                  s->p0c_src, L.p_val, s->p0c_val);
+    }
+  }
   DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
+// Level 0 in colour order (Sim::l0c): row q of the colour copy is the q-th
+// row of the ILU(0) ordering, its columns are colour positions (colp), and
+// b, x, 1/a_ii and the residual are colour-ordered vectors, so every access
+// but the column gathers is contiguous.  The same row formulas as k_gs_lu.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_c(int r0, int r1, const int *__restrict__ rowptr,
+                                                 const int *__restrict__ colp,
+                                                 const T *__restrict__ pv,
+                                                 const T *__restrict__ dinv,
+                                                 const T *__restrict__ b, T *x) {
+  int q = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= r1) return;
+  int e = __ldcs(rowptr + q), e1 = __ldcs(rowptr + q + 1);
+  constexpr int kB = 8;
+  int c[kB];
+  T v[kB];
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    bool in = e + k < e1;
+    c[k] = in ? __ldcs(colp + e + k) : 0;
+    v[k] = in ? __ldcs(pv + e + k) : T(0);
+  }
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int k = 0; k < kB; k += 2) {
+    if (e + k < e1) s0 = fma(v[k], x[c[k]], s0);
+    if (e + k + 1 < e1) s1 = fma(v[k + 1], x[c[k + 1]], s1);
+  }
+  for (e += kB; e < e1; ++e) s0 = fma(__ldcs(pv + e), x[__ldcs(colp + e)], s0);
+  T s = s0 + s1;
+  T di = dinv[q];
+  if (di != T(0)) x[q] = fma(b[q] - s, di, x[q]);
+}
+
+// A warp per (long) row: RESID = false, one colour of Gauss-Seidel;
+// RESID = true, r = b - A x for those rows.
+template <typename T, bool RESID>
+__device__ __forceinline__ void row_c_w(int r0, int r1, const int *__restrict__ rowptr,
+                                        const int *__restrict__ colp, const T *__restrict__ pv,
+                                        const T *__restrict__ dinv, const T *__restrict__ b,
+                                        T *x, T *r) {
+  int q = r0 + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (q >= r1) return;   // whole warps
+  T s = T(0);
+  for (int e = __ldg(rowptr + q) + lane, e1 = __ldg(rowptr + q + 1); e < e1; e += 32)
+    s = fma(__ldg(pv + e), x[__ldg(colp + e)], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (RESID) {
+      r[q] = b[q] - s;
+    } else {
+      T di = dinv[q];
+      if (di != T(0)) x[q] = fma(b[q] - s, di, x[q]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_c_w(int r0, int r1, const int *__restrict__ rowptr,
+                                                   const int *__restrict__ colp,
+                                                   const T *__restrict__ pv,
+                                                   const T *__restrict__ dinv,
+                                                   const T *__restrict__ b, T *x) {
+  row_c_w<T, false>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_resid_c_w(int r0, int r1, const int *__restrict__ rowptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ pv,
+                                                      const T *__restrict__ b, T *x, T *r) {
+  row_c_w<T, true>(r0, r1, rowptr, colp, pv, nullptr, b, x, r);
+}
+
+// r = b - A x over the rows [r0, r1) of the colour copy, a thread per row.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_resid_c(int r0, int r1, const int *__restrict__ rowptr,
+                                                    const int *__restrict__ colp,
+                                                    const T *__restrict__ pv,
+                                                    const T *__restrict__ b,
+                                                    const T *__restrict__ x, T *__restrict__ r) {
+  int q = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= r1) return;
+  int e = __ldcs(rowptr + q), e1 = __ldcs(rowptr + q + 1);
+  constexpr int kB = 8;
+  int c[kB];
+  T v[kB];
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    bool in = e + k < e1;
+    c[k] = in ? __ldcs(colp + e + k) : 0;
+    v[k] = in ? __ldcs(pv + e + k) : T(0);
+  }
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int k = 0; k < kB; k += 2) {
+    if (e + k < e1) s0 = fma(v[k], __ldg(x + c[k]), s0);
+    if (e + k + 1 < e1) s1 = fma(v[k + 1], __ldg(x + c[k + 1]), s1);
+  }
+  for (e += kB; e < e1; ++e) s0 = fma(__ldcs(pv + e), __ldg(x + __ldcs(colp + e)), s0);
+  r[q] = b[q] - (s0 + s1);
+}
+
+template <typename T> struct L0C;
+template <> struct L0C<double> {
+  static const double *pv(const Sim *s) { return s->l0_pv; }
+  static const double *dinv(const Sim *s) { return s->dinv_c; }
+  static const double *pval(const Sim *s) { return s->p0c_val; }
+};
+template <> struct L0C<float> {
+  static const float *pv(const Sim *s) { return s->l0_pvf; }
+  static const float *dinv(const Sim *s) { return s->dinv_cf; }
+  static const float *pval(const Sim *s) { return s->p0c_valf; }
+};
+
+// level 0 runs in colour order (see Sim::l0c): not when the hierarchy has one
+// level or the cluster cycle takes level 0 itself
+static bool l0c_on(const Sim *s) { return s->l0c && s->lev.size() > 1 && s->cl_level != 0; }
+
+template <typename T>
+static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward) {
+  int nc = s->ncolour;
+  for (int t = 0; t < nc; ++t) {
+    int c = forward ? t : nc - 1 - t;
+    int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
+    if (r1 <= r0) continue;
+    if (s->lu_cmaxlen[c] > kLongRow)
+      DP_LAUNCH(s, k_gs_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
+                s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
+    else
+      DP_LAUNCH(s, k_gs_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+                L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
+  }
+  return DP_OK;
+}
+
+template <typename T>
+static int resid_c(Sim *s, const T *b, const T *x, T *r) {
+  int nc = s->ncolour, c = 0;
+  while (c < nc) {   // runs of short-row colours in one launch, long-row colours a warp per row
+    int r0 = s->lu_cstart[c];
+    bool lng = s->lu_cmaxlen[c] > kLongRow;
+    int c1 = c + 1;
+    while (c1 < nc && (s->lu_cmaxlen[c1] > kLongRow) == lng) ++c1;
+    int r1 = s->lu_cstart[c1];
+    if (r1 > r0) {
+      if (lng)
+        DP_LAUNCH(s, k_resid_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
+                  s->l0_colp, L0C<T>::pv(s), b, (T *)x, r);
+      else
+        DP_LAUNCH(s, k_resid_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+                  L0C<T>::pv(s), b, x, r);
+    }
+    c = c1;
+  }
   return DP_OK;
 }
 
@@ -1343,6 +1575,17 @@ static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
 template <typename T>
 static int vcycle_t(Sim *s, int l, const T *b, T *x) {
   if (l == s->cl_level) return coarse_cycle<T>(s, l, b, x);
+  if (l == 0 && l0c_on(s)) {   // b and x in colour order
+    Level &L = s->lev[0], &N = s->lev[1];
+    T *r = LV<T>::r(L), *nb = LV<T>::b(N), *nx = LV<T>::x(N);
+    DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), s->stream));
+    DP_TRY(gs_sweep_c<T>(s, b, x, true));
+    DP_TRY(resid_c<T>(s, b, x, r));
+    DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, s->r0_colp, LV<T>::rval(L), r, nb, 0));
+    DP_TRY(vcycle_t<T>(s, 1, nb, nx));
+    DP_TRY(csr_mv<T>(s, L.n, L.p_G, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x, 1));
+    return gs_sweep_c<T>(s, b, x, false);
+  }
   Level &L = s->lev[l];
   int n = L.n;
   if (l == (int)s->lev.size() - 1) {
@@ -1480,17 +1723,17 @@ int autotune(Sim *s, int reps, std::string &rep) {
 // z1 = F r;  z2 = z1 + P V(R (r - A z1));  z = z2 + F (r - A z2)
 
 template <typename T>
-__global__ void k_inject_add(int n, const T *xp, double *z) {
+__global__ void k_inject_add(int n, const T *xp, double *z, const int *imap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) z[2 * i] += double(xp[i]);
+  if (i < n) z[2 * i] += double(xp[imap ? __ldg(imap + i) : i]);
 }
 
 // The same injection applied to an FP64 vector and to its FP32 copy (the
 // copy updated in FP32: no conversions on the FP64 pipe).
-__global__ void k_inject_add2(int n, const float *xp, double *z, float *zf) {
+__global__ void k_inject_add2(int n, const float *xp, double *z, float *zf, const int *imap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
-    float e = xp[i];
+    float e = xp[imap ? __ldg(imap + i) : i];
     z[2 * i] += double(e);
     zf[2 * i] += e;
   }
@@ -1514,10 +1757,11 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   if (!f32) {
     if (s->opt.precond == 1) return ilu_apply(s, r, z);
     DP_TRY(ilu_apply(s, r, s->z1));
+    const int *m = l0c_on(s) ? s->iperm : nullptr;   // level-0 vectors in colour order
     DP_LAUNCH(s, k_bsr_presid, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
-              s->sv_long0, s->srowptr, s->scol, s->sa00, s->sa01, s->z1, r, s->rp);
+              s->sv_long0, s->srowptr, s->scol, s->sa00, s->sa01, s->z1, r, s->rp, m);
     DP_TRY(vcycle(s, 0, s->rp, s->xp));
-    DP_LAUNCH(s, k_inject_add<double>, nblk(nb), kBlock, 0, nb, s->xp, s->z1);
+    DP_LAUNCH(s, k_inject_add<double>, nblk(nb), kBlock, 0, nb, s->xp, s->z1, m);
     DP_TRY(bsr_residual(s, r, s->z1, s->r1));
     DP_TRY((ilu_apply_t<double, double>(s, s->lu_val, s->r1)));
     return ilu_result<double>(s, s->z1, z);           // z = z2 + F (r - A z2)
@@ -1532,11 +1776,12 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   Level &L0 = s->lev[0];
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
   DP_TRY(ilu_result<float>(s, nullptr, s->z1, s->z1f));
+  const int *m = l0c_on(s) ? s->iperm : nullptr;     // level-0 vectors in colour order
   DP_LAUNCH(s, k_bsr_presid_f32, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
             s->sv_long0, s->srowptr, s->scol, reinterpret_cast<const float2 *>(s->spf), s->z1f,
-            r, L0.bf);
+            r, L0.bf, m);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
-  DP_LAUNCH(s, k_inject_add2, nblk(nb), kBlock, 0, nb, L0.xf, s->z1, s->z1f);
+  DP_LAUNCH(s, k_inject_add2, nblk(nb), kBlock, 0, nb, L0.xf, s->z1, s->z1f, m);
   DP_LAUNCH(s, k_bsr_resid_f32, 1 + nblk(2LL * s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
             s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1f, r, s->r1f);
   DP_TRY((ilu_apply_t<float, float>(s, s->lu_valf, s->r1f)));
@@ -1968,9 +2213,13 @@ __global__ void k_to_f32_i(long long n, const double *x, float *y) {
 int mixed_refresh(Sim *s, bool coarse) {
   for (size_t l = 0; l < s->lev.size(); ++l) {
     if (!coarse) {
+      // level 0 only; in colour order its FP32 values and 1/a_ii come from the
+      // decoupling and from l0_refresh instead
       Level &L = s->lev[0];
-      DP_LAUNCH(s, k_to_f32_i, nblk(L.nnz), kBlock, 0, (long long)L.nnz, L.val, L.valf);
-      DP_LAUNCH(s, k_to_f32_i, nblk(L.n), kBlock, 0, (long long)L.n, L.dinv, L.dinvf);
+      if (!s->l0c) {
+        DP_LAUNCH(s, k_to_f32_i, nblk(L.nnz), kBlock, 0, (long long)L.nnz, L.val, L.valf);
+        DP_LAUNCH(s, k_to_f32_i, nblk(L.n), kBlock, 0, (long long)L.n, L.dinv, L.dinvf);
+      }
       break;
     }
     Level &L = s->lev[l];

@@ -376,7 +376,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
     else if (coarse) DP_TRY(amg_refresh(s));
     else DP_TRY(level_dinv(s, s->lev[0]));   // level 0 only: its values are s->ap
     if (s->opt.precision == 1) DP_TRY(mixed_refresh(s, coarse));
-    DP_TRY(l0_refresh(s));
+    DP_TRY(l0_refresh(s, coarse));
     if (coarse) DP_TRY(cluster_refresh(s));
   }
   cudaEventRecord(e1, s->stream);
