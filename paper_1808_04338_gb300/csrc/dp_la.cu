@@ -806,23 +806,53 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
 
 // out_i = base_i + zp_{iperm[i]} (base may be NULL: out_i = zp_{iperm[i]}),
 // natural order, FP64; two lanes per block row.
+// out_i = base_i + zp_{iperm[i]} (base may be NULL), natural order, FP64,
+// and optionally the result in T.  A thread takes kRes rows (i, i + S, ...,
+// S the thread count), all their index loads first, then all their gathers:
+// with one row per thread the launch is a chain of dependent loads per
+// thread and stays far below the bandwidth.
+constexpr int kRes = 4;
 template <typename T>
-__global__ void k_ilu_result(int n, const int *__restrict__ iperm, const T *__restrict__ zp,
-                             const double *__restrict__ base, double *__restrict__ out,
-                             T *__restrict__ outT) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2LL * n) return;
-  int i = (int)(t >> 1), comp = (int)(t & 1);
-  T z = zp[2 * (size_t)__ldg(iperm + i) + comp];
-  double v = double(z);
-  out[t] = base ? base[t] + v : v;
-  if (outT) outT[t] = z;   // the result also in the sweep's precision (no base)
+__global__ void __launch_bounds__(kBlock) k_ilu_result(int n, const int *__restrict__ iperm,
+                                                       const T *__restrict__ zp,
+                                                       const double *__restrict__ base,
+                                                       double *__restrict__ out,
+                                                       T *__restrict__ outT) {
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  int S = gridDim.x * blockDim.x;
+  int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  int p[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int i = i0 + k * S;
+    p[k] = i < n ? __ldg(iperm + i) : 0;
+  }
+  T2 z[kRes];
+  double2 bs[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int i = i0 + k * S;
+    if (i < n) {
+      z[k] = z2[p[k]];
+      bs[k] = base ? reinterpret_cast<const double2 *>(base)[i] : make_double2(0.0, 0.0);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int i = i0 + k * S;
+    if (i >= n) continue;
+    double v0 = double(z[k].x), v1 = double(z[k].y);
+    reinterpret_cast<double2 *>(out)[i] =
+        base ? make_double2(bs[k].x + v0, bs[k].y + v1) : make_double2(v0, v1);
+    if (outT) reinterpret_cast<T2 *>(outT)[i] = z[k];
+  }
 }
 
 template <typename T>
 static int ilu_result(Sim *s, const double *base, double *out, T *outT = nullptr) {
   int n = s->K.n;
-  DP_LAUNCH(s, k_ilu_result<T>, nblk(2LL * n), kBlock, 0, n, s->iperm,
+  DP_LAUNCH(s, k_ilu_result<T>, nblk((n + kRes - 1) / kRes), kBlock, 0, n, s->iperm,
             reinterpret_cast<const T *>(s->ilu_zp), base, out, outT);
   return DP_OK;
 }
