@@ -454,6 +454,34 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *_
   zp[2 * (size_t)r + comp] = T(rhs[2 * (size_t)i + comp]) - s;
 }
 
+constexpr int kRes = 4;   // rows per thread of the gather-style kernels
+
+// Forward sweep of the first colour, whose rows have no L blocks: zp_r =
+// r_{perm[r]}, a copy.  A thread takes kRes rows (r, r + S, ...) with their
+// permutation loads, then their right-hand-side loads, issued together.
+template <typename T, typename TR>
+__global__ void __launch_bounds__(kBlock) k_ilu_fwd_copy(int r0, int r1, const int *__restrict__ perm,
+                                                     const TR *__restrict__ rhs, T *zp) {
+  using T2 = typename V2<T>::t;
+  using R2 = typename V2<TR>::t;
+  int S = gridDim.x * blockDim.x;
+  int q0 = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  int p[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) p[k] = q0 + k * S < r1 ? __ldcs(perm + q0 + k * S) : 0;
+  R2 v[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k)
+    if (q0 + k * S < r1) v[k] = reinterpret_cast<const R2 *>(rhs)[p[k]];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    T2 o;
+    o.x = T(v[k].x);
+    o.y = T(v[k].y);
+    if (q0 + k * S < r1) reinterpret_cast<T2 *>(zp)[q0 + k * S] = o;
+  }
+}
+
 // Backward sweep of one colour: zp_r = D_r (zp_r - sum_{U} U_rj zp_j) with
 // D_r the inverted pivot.  The two lanes of a row exchange their partial
 // results for the 2x2 product.
@@ -777,6 +805,8 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
   // its rows have no U blocks, so that is also the backward sweep's first step
   int last = nc - 1;
   while (last >= 0 && s->lu_cstart[last + 1] <= s->lu_cstart[last]) --last;
+  int first = 0;
+  while (first < nc && s->lu_cstart[first + 1] <= s->lu_cstart[first]) ++first;
   for (int c = 0; c < nc; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
@@ -786,6 +816,9 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
     else if (s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, (k_ilu_fwd_w<T, TR, false>), nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL,
                 s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp);
+    else if (c == first)   // no L blocks
+      DP_LAUNCH(s, (k_ilu_fwd_copy<T, TR>), nblk((r1 - r0 + kRes - 1) / kRes), kBlock, 0, r0, r1,
+                s->perm, r, zp);
     else
       DP_LAUNCH(s, (k_ilu_fwd<T, TR>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
                 s->lu_Lptr, s->lu_colp, lu, r, zp);
@@ -811,7 +844,6 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
 // S the thread count), all their index loads first, then all their gathers:
 // with one row per thread the launch is a chain of dependent loads per
 // thread and stays far below the bandwidth.
-constexpr int kRes = 4;
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_ilu_result(int n, const int *__restrict__ iperm,
                                                        const T *__restrict__ zp,
