@@ -482,6 +482,57 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd_copy(int r0, int r1, const i
   }
 }
 
+// Backward sweep of a colour whose rows have at most one U block (the
+// colour before the well rows: only perforated cells couple forward): a
+// thread per row, kRes rows per thread, each row's pivot block and y loaded
+// with its U pointers before the (rare) U gathers.  The arithmetic of
+// k_ilu_bwd, both components in one thread.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_ilu_bwd_r(int r0, int r1, int nL, int n,
+                                                      const int *__restrict__ Uptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ lu, T *zp) {
+  using T2 = typename V2<T>::t;
+  T2 *z2 = reinterpret_cast<T2 *>(zp);
+  size_t ub = (size_t)nL + n;
+  int S = gridDim.x * blockDim.x;
+  int q0 = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  int ea[kRes], eb[kRes];
+  T d[kRes][4];
+  T2 y[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int q = q0 + k * S;
+    bool ok = q < r1;
+    ea[k] = ok ? __ldcs(Uptr + q) : 0;
+    eb[k] = ok ? __ldcs(Uptr + q + 1) : 0;
+    if (ok) {
+      Blk<T>::load(lu + 4 * ((size_t)nL + q), d[k]);
+      y[k] = z2[q];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int q = q0 + k * S;
+    if (q >= r1) continue;
+    T s0 = T(0), s1 = T(0);
+    for (int e = ea[k]; e < eb[k]; ++e) {
+      T a[4];
+      Blk<T>::load(lu + 4 * (ub + e), a);
+      T2 xj = z2[__ldcs(colp + ub + e)];
+      s0 = fma(a[0], xj.x, s0);
+      s0 = fma(a[1], xj.y, s0);
+      s1 = fma(a[2], xj.x, s1);
+      s1 = fma(a[3], xj.y, s1);
+    }
+    T y0 = y[k].x - s0, y1 = y[k].y - s1;
+    T2 o;
+    o.x = fma(d[k][0], y0, d[k][1] * y1);
+    o.y = fma(d[k][2], y0, d[k][3] * y1);
+    z2[q] = o;
+  }
+}
+
 // Backward sweep of one colour: zp_r = D_r (zp_r - sum_{U} U_rj zp_j) with
 // D_r the inverted pivot.  The two lanes of a row exchange their partial
 // results for the 2x2 product.
@@ -751,6 +802,20 @@ int ilu_setup(Sim *s) {
   DP_TRY(scan_i32(s, nu, s->lu_Uptr, n, &nU));
   if (nL + nU + n != nnz) { s->fail(DP_EINVAL, "ILU(0) pattern without a pivot per row"); return DP_EINVAL; }
   s->lu_nL = nL;
+  {   // longest U part of a row, per colour (the backward sweep's variant)
+    int nc = s->ncolour;
+    int *dev = (int *)dalloc(s, (size_t)(2 * nc + 2) * 4);
+    if (!dev) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+    DP_CUDA(s, cudaMemcpyAsync(dev, s->lu_cstart.data(), (size_t)(nc + 1) * 4,
+                               cudaMemcpyHostToDevice, s->stream));
+    DP_CUDA(s, cudaMemsetAsync(dev + nc + 1, 0, (size_t)nc * 4, s->stream));
+    DP_LAUNCH(s, k_colour_maxlen, nblk(n), kBlock, 0, n, dev, nc, s->lu_Uptr, dev + nc + 1);
+    s->lu_cmaxu.assign(nc, 0);
+    DP_CUDA(s, cudaMemcpyAsync(s->lu_cmaxu.data(), dev + nc + 1, (size_t)nc * 4,
+                               cudaMemcpyDeviceToHost, s->stream));
+    DP_CUDA(s, cudaStreamSynchronize(s->stream));
+    dfree(s, dev);
+  }
   DP_LAUNCH(s, k_ilu_split, nblk(n), kBlock, 0, n, nL, s->iperm, s->lu_rowptr, s->lu_col,
             s->lu_dpos, s->lu_Lptr, s->lu_Uptr, s->lu_dst, s->lu_colp);
   if (npairs > 0) {
@@ -829,6 +894,9 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
     if (c == last && s->lu_cmaxlen[c] > kLongRow) continue;   // done with the forward launch
     if (s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, k_ilu_bwd_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL, n,
+                s->lu_Uptr, s->lu_colp, lu, zp);
+    else if (s->lu_cmaxu[c] <= 1)
+      DP_LAUNCH(s, k_ilu_bwd_r<T>, nblk((r1 - r0 + kRes - 1) / kRes), kBlock, 0, r0, r1, nL, n,
                 s->lu_Uptr, s->lu_colp, lu, zp);
     else
       DP_LAUNCH(s, k_ilu_bwd<T>, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, nL, n, s->lu_Uptr,
