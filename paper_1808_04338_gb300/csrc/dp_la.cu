@@ -1541,6 +1541,18 @@ __global__ void __launch_bounds__(kBlock) k_gs_c(int r0, int r1, const int *__re
   if (di != T(0)) x[q] = fma(b[q] - s, di, x[q]);
 }
 
+// The first colour of a Gauss-Seidel sweep that starts from x = 0: every
+// x_j a row reads is still zero, so the row formula reduces to
+// x_i = fma(b_i, 1/a_ii, 0) (the same value bit for bit: the sum is +0).
+template <typename T>
+__global__ void k_gs_c_first(int r0, int r1, const T *__restrict__ dinv, const T *__restrict__ b,
+                             T *__restrict__ x) {
+  int q = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= r1) return;
+  T di = dinv[q];
+  x[q] = di != T(0) ? fma(b[q] - T(0), di, T(0)) : T(0);
+}
+
 // A warp per (long) row: RESID = false, one colour of Gauss-Seidel;
 // RESID = true, r = b - A x for those rows.
 template <typename T, bool RESID>
@@ -1627,13 +1639,21 @@ template <> struct L0C<float> {
 // level or the cluster cycle takes level 0 itself
 static bool l0c_on(const Sim *s) { return s->l0c && s->lev.size() > 1 && s->cl_level != 0; }
 
+// from_zero: x = 0 on entry (the pre-smoothing), so the first colour is the
+// reduced formula of k_gs_c_first
 template <typename T>
-static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward) {
+static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false) {
   int nc = s->ncolour;
+  bool first = from_zero;
   for (int t = 0; t < nc; ++t) {
     int c = forward ? t : nc - 1 - t;
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
+    if (first) {
+      first = false;
+      DP_LAUNCH(s, k_gs_c_first<T>, nblk(r1 - r0), kBlock, 0, r0, r1, L0C<T>::dinv(s), b, x);
+      continue;
+    }
     if (s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, k_gs_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
                 s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
@@ -1709,7 +1729,7 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x) {
     Level &L = s->lev[0], &N = s->lev[1];
     T *r = LV<T>::r(L), *nb = LV<T>::b(N), *nx = LV<T>::x(N);
     DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), s->stream));
-    DP_TRY(gs_sweep_c<T>(s, b, x, true));
+    DP_TRY(gs_sweep_c<T>(s, b, x, true, true));
     DP_TRY(resid_c<T>(s, b, x, r));
     DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, s->r0_colp, LV<T>::rval(L), r, nb, 0));
     DP_TRY(vcycle_t<T>(s, 1, nb, nx));
