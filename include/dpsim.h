@@ -223,6 +223,23 @@ int sim_solve_step(dp_sim *sim, dp_stats *stats);
  * failure the old state is restored and DP_ENEWTON returned. */
 int sim_advance(dp_sim *sim, double dt, dp_stats *stats);
 
+/* A simulation period [0, t_end] (seconds) by sim_advance timesteps, as the
+ * paper's examples run theirs (800 and 1600 days): dt0 first; after a
+ * converged step the next is min(2 h, dt_max) (h the step just taken); a step
+ * whose Newton iteration fails is retried at h / 2 (a cut); the last step
+ * ends at t_end.  Returns DP_OK at t_end; DP_ENEWTON when a retry would fall
+ * below dt_min or after max_steps accepted steps (the state is that of the
+ * last accepted step, stats->t its time); other codes as sim_advance.
+ * DP_EINVAL: sim NULL, t_end, dt0 or dt_min not > 0, dt_max < dt0, or
+ * max_steps < 1.  stats (may be NULL): accepted steps, cuts, Newton and
+ * FGMRES iterations summed over the accepted steps, the time reached. */
+typedef struct {
+  int32_t steps, cuts, newton_iters, linear_iters;
+  double t;
+} dp_run_stats;
+int sim_run(dp_sim *sim, double t_end, double dt0, double dt_max, double dt_min,
+            int32_t max_steps, dp_run_stats *stats);
+
 /* Batched timesteps of many realisations (no counterpart in the paper,
  * which advances one grid on many processors; here many independent grids
  * share one GPU).  Advances sims[k] by dt[k] for k < n, like sim_advance,

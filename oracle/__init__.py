@@ -68,6 +68,11 @@ class og_options(C.Structure):
                 ("decouple", C.c_int32), ("schur", C.c_int32), ("reorth", C.c_double)]
 
 
+class og_run_stats(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("cuts", C.c_int32), ("newton_iters", C.c_int32),
+                ("linear_iters", C.c_int32), ("t", C.c_double)]
+
+
 class og_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int32), ("linear_iters", C.c_int32),
                 ("converged", C.c_int32), ("amg_levels", C.c_int32),
@@ -128,6 +133,8 @@ def lib():
         L.oracle_well_rates.argtypes = [P, P, P]
         L.oracle_cap_pressure.argtypes = [C.c_int32, P, C.c_double, P, P]
         L.oracle_cap_pressure.restype = None
+        L.oracle_run.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                 C.POINTER(og_run_stats)]
         L.oracle_assemble.argtypes = [P, D]
         L.oracle_get_jacobian.argtypes = [P, P, P, P, P]
         L.oracle_get_norms.argtypes = [P, P]
@@ -247,6 +254,13 @@ class OracleSim:
     def advance(self, dt):
         st = og_stats()
         rc = lib().oracle_advance(self.h, float(dt), C.byref(st))
+        return rc, st
+
+    def run(self, t_end, dt0, dt_max, dt_min, max_steps=100000):
+        """oracle_run: (rc, og_run_stats) of the period [0, t_end] (seconds)."""
+        st = og_run_stats()
+        rc = lib().oracle_run(self.h, float(t_end), float(dt0), float(dt_max), float(dt_min),
+                              int(max_steps), C.byref(st))
         return rc, st
 
     def update(self):

@@ -1936,3 +1936,39 @@ int oracle_advance(void *h, double dt, og_stats *st) {
   }
   return OG_OK;
 }
+
+/* The time loop of a whole simulation period (the paper's examples run 800
+ * and 1600 days): halve a step whose Newton iteration fails, double after a
+ * converged one up to dt_max, end exactly at t_end. */
+int oracle_run(void *h, double t_end, double dt0, double dt_max, double dt_min,
+               int32_t max_steps, og_run_stats *st) {
+  og_run_stats r;
+  memset(&r, 0, sizeof(r));
+  if (!h || !(t_end > 0.0) || !(dt0 > 0.0) || !(dt_max >= dt0) || !(dt_min > 0.0) ||
+      max_steps < 1)
+    return OG_EINVAL;
+  double t = 0.0, dt = dt0;
+  int rc = OG_OK;
+  while (t_end - t > 1e-9 * t_end) {
+    if (r.steps >= max_steps) { rc = OG_ENEWTON; break; }
+    double hstep = dt < t_end - t ? dt : t_end - t;
+    og_stats a;
+    memset(&a, 0, sizeof(a));
+    int rc1 = oracle_advance(h, hstep, &a);
+    if (rc1 == OG_ENEWTON) {
+      r.cuts += 1;
+      dt = 0.5 * hstep;
+      if (dt < dt_min) { rc = OG_ENEWTON; break; }
+      continue;
+    }
+    if (rc1 != OG_OK) { rc = rc1; break; }
+    t = t + hstep;
+    r.steps += 1;
+    r.newton_iters += a.newton_iters;
+    r.linear_iters += a.linear_iters;
+    dt = 2.0 * hstep < dt_max ? 2.0 * hstep : dt_max;
+  }
+  r.t = t;
+  if (st) *st = r;
+  return rc;
+}

@@ -94,6 +94,17 @@ int  oracle_get_jacobian(void *h, int32_t *rowptr, int32_t *col, double *val, do
 int  oracle_get_norms(void *h, double *out8);
 int  oracle_solve_step(void *h, og_stats *st);
 int  oracle_advance(void *h, double dt, og_stats *st);
+/* A simulation period [0, t_end] by timesteps of oracle_advance: dt0 first;
+ * after a converged step the next is min(2 h, dt_max) (h the step taken);
+ * a step whose Newton iteration fails is retried at h / 2 (a cut), and the
+ * run stops with OG_ENEWTON once that would fall below dt_min or after
+ * max_steps accepted steps; the last step ends at t_end. */
+typedef struct {
+  int32_t steps, cuts, newton_iters, linear_iters;
+  double t;                 /* time reached (s) */
+} og_run_stats;
+int  oracle_run(void *h, double t_end, double dt0, double dt_max, double dt_min,
+                int32_t max_steps, og_run_stats *st);
 int  oracle_get_update(void *h, double *y);
 int  oracle_get_decoupled(void *h, double *val, double *rhs);
 int  oracle_get_colours(void *h, int32_t *colour);

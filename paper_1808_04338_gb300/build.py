@@ -69,8 +69,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-Xlinker", "-z,defs", *objs, "-o",
-             tmp])
+        run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-Xlinker", "-z,defs", *objs, "-ldl",
+             "-o", tmp])
         os.replace(tmp, LIB)
     return LIB
 

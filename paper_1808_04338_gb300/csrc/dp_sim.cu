@@ -10,11 +10,20 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dp_internal.h"
 
 struct dp_sim : dp::Sim {};
 
 namespace dp {
+
+// NVTX range around a stage of the solve (visible in Nsight timelines; a
+// no-op unless a tool is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 // ---------------------------------------------------------------- memory
 static void *default_alloc(size_t bytes, void *stream, void *) {
@@ -325,6 +334,7 @@ extern "C" int sim_get_state(dp_sim *s, double *p, double *sw, double *bhp) {
 }
 
 extern "C" int sim_assemble(dp_sim *s, double dt) {
+  Range range("assemble");
   if (!s || !(dt > 0.0)) return DP_EINVAL;
   s->dt = dt;
   s->inv_dt = 1.0 / dt;
@@ -366,11 +376,18 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
   cudaEventRecord(e0, s->stream);
-  if (s->opt.schur) DP_TRY(phys_schur_reduce(s));
-  DP_TRY(phys_decouple_extract(s));
+  {
+    Range range("decouple");
+    if (s->opt.schur) DP_TRY(phys_schur_reduce(s));
+    DP_TRY(phys_decouple_extract(s));
+  }
   s->decoupled = true;
-  if (s->opt.precond >= 1) DP_TRY(ilu_factor(s));
+  if (s->opt.precond >= 1) {
+    Range range("ilu_factor");
+    DP_TRY(ilu_factor(s));
+  }
   if (s->opt.precond == 2) {
+    Range range("amg");
     bool coarse = !s->amg_ready || s->opt.amg_refresh == 0 || s->newton_iter == 0;
     if (!s->amg_ready) DP_TRY(amg_setup(s));
     else if (coarse) DP_TRY(amg_refresh(s));
@@ -382,7 +399,11 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   cudaEventRecord(e1, s->stream);
   int it = 0;
   double rr = 0.0;
-  int rc = fgmres(s, eta, &it, &rr);
+  int rc;
+  {
+    Range range("fgmres");
+    rc = fgmres(s, eta, &it, &rr);
+  }
   if (rc != DP_OK && rc != DP_ELINEAR) return rc;
   if (s->opt.schur) DP_TRY(phys_schur_back(s));
   DP_TRY(phys_update(s));
@@ -407,6 +428,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
 
 extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
   if (!s || !(dt > 0.0)) return DP_EINVAL;
+  Range range("timestep");
   if (s->well_limits) DP_TRY(phys_well_controls(s, true));
   DP_TRY(phys_save_old(s));
   new_timestep(s);
@@ -445,6 +467,38 @@ extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
     return DP_ENEWTON;
   }
   return check(s);
+}
+
+extern "C" int sim_run(dp_sim *s, double t_end, double dt0, double dt_max, double dt_min,
+                       int32_t max_steps, dp_run_stats *st) {
+  dp_run_stats r{};
+  if (!s || !(t_end > 0.0) || !(dt0 > 0.0) || !(dt_max >= dt0) || !(dt_min > 0.0) ||
+      max_steps < 1)
+    return DP_EINVAL;
+  double t = 0.0, dt = dt0;
+  int rc = DP_OK;
+  while (t_end - t > 1e-9 * t_end) {
+    if (r.steps >= max_steps) { rc = DP_ENEWTON; break; }
+    double h = dt < t_end - t ? dt : t_end - t;
+    dp_stats a{};
+    int rc1 = sim_advance(s, h, &a);
+    if (rc1 == DP_ENEWTON) {   // rolled back by sim_advance: retry at half the step
+      r.cuts += 1;
+      dt = 0.5 * h;
+      if (dt < dt_min) { rc = DP_ENEWTON; break; }
+      continue;
+    }
+    if (rc1 != DP_OK) { rc = rc1; break; }
+    t = t + h;
+    r.steps += 1;
+    r.newton_iters += a.newton_iters;
+    r.linear_iters += a.linear_iters;
+    dt = 2.0 * h < dt_max ? 2.0 * h : dt_max;
+  }
+  r.t = t;
+  if (st) *st = r;
+  if (rc == DP_ENEWTON) s->fail(DP_ENEWTON, "sim_run: timestep below dt_min or step limit");
+  return rc;
 }
 
 extern "C" int dp_stream_create(void **stream) {

@@ -144,6 +144,7 @@ def load():
     L.sim_get_norms.argtypes = [P, P]
     L.sim_solve_step.argtypes = [P, C.POINTER(dp_stats)]
     L.sim_advance.argtypes = [P, D, C.POINTER(dp_stats)]
+    L.sim_run.argtypes = [P, D, D, D, D, I, C.POINTER(dp_run_stats)]
     L.sim_get_update.argtypes = [P, P]
     L.sim_get_decoupled.argtypes = [P, P, P]
     L.sim_get_colours.argtypes = [P, P]
@@ -242,6 +243,11 @@ def advance_many(sims, dts, threads=0):
     rc = load().sim_advance_many(C.cast(H, C.c_void_p), n, C.cast(D, C.c_void_p), int(threads),
                                  C.cast(st, C.c_void_p), C.cast(rs, C.c_void_p))
     return rc, [st[k] for k in range(n)], [rs[k] for k in range(n)]
+
+
+class dp_run_stats(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("cuts", C.c_int32), ("newton_iters", C.c_int32),
+                ("linear_iters", C.c_int32), ("t", C.c_double)]
 
 
 class dp_srv_result(C.Structure):
@@ -461,6 +467,15 @@ class Sim:
         rc = load().sim_advance(self.h, float(dt), C.byref(st))
         if rc < 0 and rc not in (DP_ENEWTON, DP_ELINEAR):
             self._check(rc, "sim_advance")
+        return rc, st
+
+    def run(self, t_end, dt0, dt_max, dt_min, max_steps=100000):
+        """sim_run: (rc, dp_run_stats) of the period [0, t_end] (seconds)."""
+        st = dp_run_stats()
+        rc = load().sim_run(self.h, float(t_end), float(dt0), float(dt_max), float(dt_min),
+                            int(max_steps), C.byref(st))
+        if rc < 0 and rc != DP_ENEWTON:
+            self._check(rc, "sim_run")
         return rc, st
 
     def update(self):

@@ -65,6 +65,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert L.sim_advance_many(None, 2, None, 0, None, None) == dpsim.DP_EINVAL
     assert L.sim_well_controls(None, None, None) == dpsim.DP_EINVAL
     assert L.sim_well_rates(None, None, None) == dpsim.DP_EINVAL
+    assert L.sim_run(None, 1.0, 1.0, 1.0, 0.1, 10, None) == dpsim.DP_EINVAL
     # wells: unknown control kind, negative limit, negative well index
     import dataclasses
     import dp_inputs as di

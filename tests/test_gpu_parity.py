@@ -410,3 +410,57 @@ def test_autotune_keeps_parity():
     rco, _ = o.advance(di.DAY)
     assert rcg == 0 and rco == 0
     state_close(g, o, prob)
+
+
+def test_run_matches_the_oracle_over_example_1():
+    """sim_run over Example 1's 800 days (steps doubling from 1 day up to 20)
+    against oracle_run: the same accepted steps and cuts, the same end time,
+    the final state within the parity tolerances."""
+    prob = di.paper_example(1)
+    g, o = pair(prob)
+    args = (800 * di.DAY, 1 * di.DAY, 20 * di.DAY, 0.01 * di.DAY)
+    rcg, sg = g.run(*args)
+    rco, so = o.run(*args)
+    assert rcg == rco == 0
+    assert (sg.steps, sg.cuts) == (so.steps, so.cuts) and sg.t == so.t
+    assert abs(sg.newton_iters - so.newton_iters) <= 0.02 * so.newton_iters
+    state_close(g, o, prob)
+
+
+def _gpu_python_run(s, t_end, dt0, dt_max, dt_min):
+    t, dt, steps, cuts = 0.0, dt0, 0, 0
+    while t_end - t > 1e-9 * t_end:
+        h = min(dt, t_end - t)
+        rc, st = s.advance(h)
+        if rc == gpu().DP_ENEWTON:
+            cuts += 1
+            dt = 0.5 * h
+            if dt < dt_min:
+                return rc, t, steps, cuts
+            continue
+        assert rc == 0
+        t += h
+        steps += 1
+        dt = min(2.0 * h, dt_max)
+    return 0, t, steps, cuts
+
+
+def test_run_cuts_follow_the_rule_on_the_gpu():
+    """With at most four Newton iterations per step some of Example 2's steps
+    fail and are halved; sim_run reaches the same counts and the same state as
+    the rule restated with sim_advance calls (the GPU path is deterministic)."""
+    day = di.DAY
+    res = []
+    for how in ("run", "python"):
+        prob = di.paper_example(2)
+        s = gpu().Sim(prob, gpu().options("report", newton_max=4))
+        if how == "run":
+            rc, st = s.run(200 * day, 10 * day, 80 * day, 0.01 * day)
+            res.append(((rc, st.t, st.steps, st.cuts), s.get_state()))
+        else:
+            res.append((_gpu_python_run(s, 200 * day, 10 * day, 80 * day, 0.01 * day),
+                        s.get_state()))
+    (ca, sa), (cb, sb) = res
+    assert ca == cb and ca[0] == 0 and ca[3] > 0
+    for a, b in zip(sa, sb):
+        np.testing.assert_array_equal(a, b)

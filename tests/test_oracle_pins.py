@@ -775,3 +775,65 @@ def test_parity_mode_tiny_ten_steps_runs():
     p, sw, bhp = s.get_state()
     assert np.all(sw >= 0.2 - 1e-9) and np.all(sw <= 0.8 + 1e-9)
     assert bhp[0] > bhp[1]
+
+
+# ------------------------------------------------------------ time loop
+
+def _python_run(s, t_end, dt0, dt_max, dt_min, max_steps=100000):
+    """The time-loop rule restated step by step with advance calls."""
+    t, dt, steps, cuts, newton = 0.0, dt0, 0, 0, 0
+    while t_end - t > 1e-9 * t_end:
+        if steps >= max_steps:
+            return -5, t, steps, cuts, newton
+        h = min(dt, t_end - t)
+        rc, st = s.advance(h)
+        if rc == -5:
+            cuts += 1
+            dt = 0.5 * h
+            if dt < dt_min:
+                return -5, t, steps, cuts, newton
+            continue
+        assert rc == 0
+        t += h
+        steps += 1
+        newton += st.newton_iters
+        dt = min(2.0 * h, dt_max)
+    return 0, t, steps, cuts, newton
+
+
+@pytest.mark.parametrize("newton_max", [25, 4])
+def test_time_loop_follows_its_rule(newton_max):
+    """oracle_run over Example 2's first 200 days (steps doubling from 10 days
+    up to 80; with at most four Newton iterations per step some steps fail and
+    are halved) reaches the same time, step and cut counts and the same state,
+    bit for bit, as the rule restated with single timesteps."""
+    day = di.DAY
+    out = []
+    for how in ("run", "python"):
+        prob = di.paper_example(2)
+        s = O.OracleSim(prob, O.options("report", newton_max=newton_max))
+        if how == "run":
+            rc, st = s.run(200 * day, 10 * day, 80 * day, 0.01 * day)
+            res = (rc, st.t, st.steps, st.cuts, st.newton_iters)
+        else:
+            res = _python_run(s, 200 * day, 10 * day, 80 * day, 0.01 * day)
+        out.append((res, s.get_state()))
+    (ra, sa), (rb, sb) = out
+    assert ra == rb and ra[0] == 0 and abs(ra[1] - 200 * day) <= 1e-9 * 200 * day
+    if newton_max == 4:
+        assert ra[3] > 0          # some steps were cut
+    for a, b in zip(sa, sb):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_time_loop_gives_up_below_the_smallest_step():
+    """A step that keeps failing is halved until the next try would fall below
+    dt_min; the run then returns the Newton failure, with the state of the last
+    accepted step (here the initial state) restored."""
+    prob = di.paper_example(2)
+    s = O.OracleSim(prob, O.options("report", newton_max=1))
+    p0 = s.get_state()
+    rc, st = s.run(100 * di.DAY, 50 * di.DAY, 50 * di.DAY, 10 * di.DAY)
+    assert rc == -5 and st.steps == 0 and st.cuts >= 1 and st.t == 0.0
+    for a, b in zip(s.get_state(), p0):
+        np.testing.assert_array_equal(a, b)
