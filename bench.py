@@ -374,6 +374,51 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_period(args):
+    """A whole simulation period: Example 1's physics (Section 4) on the
+    --nx x --ny x --nz grid (500x500x50 is Example 3's size), 800 days by
+    sim_run (steps from 1 day doubling up to 20, halved when Newton fails),
+    reported in the units of the paper's Table for Example 3: time steps,
+    Newton and linear iterations, running time.  The time is the wall clock
+    of the whole run on the device (set-up of the realisation excluded)."""
+    import torch
+    import dp_inputs as di
+    from paper_1808_04338_gb300 import dpsim
+    prob = di.paper_example(1, grid=(args.nx, args.ny, args.nz))
+    opts = dpsim.options("report", precision=args.precision, schur=args.schur)
+    sim = dpsim.Sim(prob, opts)
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    clk.__enter__()
+    t0 = time.perf_counter()
+    rc, st = sim.run(800 * di.DAY, 1 * di.DAY, 20 * di.DAY, 0.001 * di.DAY)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk.__exit__()
+    kinds, _ = sim.well_controls()
+    q_oil, q_wat = sim.well_rates()
+    line = {"metric": "whole-period run (800 days) of Example 1's physics", "value": wall,
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "rc": rc,
+            "time_steps": st.steps, "cuts": st.cuts, "newton_iters": st.newton_iters,
+            "linear_iters": st.linear_iters, "days": st.t / di.DAY,
+            "newton_solves_per_s": st.newton_iters / wall,
+            "s_per_newton_iter": wall / max(st.newton_iters, 1),
+            "dtype": "f64" if args.precision == 0 else "f64 (f32 preconditioner)",
+            "data": "synthetic",
+            "config": {"workload": f"Example 1's physics on {args.nx}x{args.ny}x{args.nz} "
+                                   f"({prob.n_cells} cells, {prob.n_unknowns} unknowns), "
+                                   f"wells at the same relative cells, 800 days",
+                       "precision": args.precision, "schur": args.schur},
+            "final_well_controls": [int(k) for k in kinds],
+            "final_oil_rates_stb_day": [float(-q / (58.0 * di.LBM_FT3) / di.BBL_DAY)
+                                        for q in q_oil],
+            "paper_example3_64_ranks": {"time_steps": 68, "newton_iters": 267,
+                                        "linear_iters": 623, "running_time_s": 2531.91},
+            "gpu_launches": sim.launch_count(), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    sim.close()
+
+
 def config_dict(args, nnzb=None):
     return {"workload": f"dual-porosity oil-water, {args.nx}x{args.ny}x{args.nz} grid, "
                         f"{2 * args.nx * args.ny * args.nz} cells, "
@@ -417,7 +462,8 @@ def main():
                          "timestep and keep the fastest (sim_autotune)")
     ap.add_argument("--threads", type=int, default=16,
                     help="ensemble mode: host threads driving realisations concurrently")
-    ap.add_argument("--mode", default="bench", choices=["bench", "newton2", "ensemble", "serve"],
+    ap.add_argument("--mode", default="bench",
+                    choices=["bench", "newton2", "ensemble", "serve", "period"],
                     help="newton2: create the realisation, run the first Newton solve of the "
                          "first step (AMG set-up) and the second one, print their timings "
                          "(a short run for profilers)")
@@ -443,6 +489,8 @@ def main():
         return run_ensemble(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "period":
+        return run_period(args)
     prob = workload(args)
     opts = dpsim.options("report", precision=args.precision, cluster_rows=args.cluster_rows,
                          decouple=args.decouple, eta_mode=args.eta_mode, schur=args.schur)

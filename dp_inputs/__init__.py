@@ -294,7 +294,7 @@ def request_stream(n_requests: int = 512, rate_per_s: float = 200.0, n_real: int
 LBM_FT3 = 16.01846337       # kg/m^3 per lbm/ft^3
 
 
-def paper_example(which: int, days: float = 1.0, nsteps: int = 10) -> Problem:
+def paper_example(which: int, days: float = 1.0, nsteps: int = 10, grid=None) -> Problem:
     """The setups of the paper's Examples 1 (10x10x1) and 2 (10x10x3), Section
     4: field units converted to SI, oil density at the reference pressure
     from the stock-tank density and the formation volume factor (58.0 lbm/ft^3
@@ -304,7 +304,11 @@ def paper_example(which: int, days: float = 1.0, nsteps: int = 10) -> Problem:
     Not given by the paper, read here: water viscosity 1 cP and
     compressibility 3e-6/psi; Corey curves with no residual saturations;
     transfer through the Kazemi shape factor of the grid block, with the
-    matrix's vertical permeability folded into sigma (k_m = k_m,x)."""
+    matrix's vertical permeability folded into sigma (k_m = k_m,x).
+    grid = (nx, ny, nz) gives the same example on another grid (Example 3 is
+    Example 1 at 500x500x50): the same cells and rates, the wells in the
+    cells at the same relative positions, perforating the top layer as the
+    paper's cells [i j 1] do."""
     if which == 1:
         nz, kmz, pm0, pf0, q_inj, q_oil = 1, 10.0, 2000.0, 1980.0, 500.0, 300.0
         inj, prods, h = (4, 0), [(0, 9), (9, 9)], 102.04
@@ -312,6 +316,11 @@ def paper_example(which: int, days: float = 1.0, nsteps: int = 10) -> Problem:
         nz, kmz, pm0, pf0, q_inj, q_oil = 3, 100.0, 800.0, 500.0, 200.0, 500.0
         inj, prods, h = (4, 4), [(0, 0), (9, 9)], 102.0
     nx = ny = 10
+    if grid is not None:
+        gx, gy, nz = grid
+        inj = ((2 * inj[0] + 1) * gx // 20, (2 * inj[1] + 1) * gy // 20)
+        prods = [((2 * i + 1) * gx // 20, (2 * j + 1) * gy // 20) for (i, j) in prods]
+        nx, ny = gx, gy
     n = nx * ny * nz
     dx = dy = h * FT
     dz = 100.0 * FT
@@ -328,7 +337,8 @@ def paper_example(which: int, days: float = 1.0, nsteps: int = 10) -> Problem:
     sw0 = np.empty(2 * n)
     sw0[0::2], sw0[1::2] = 0.01, 0.08
     prob = Problem(
-        name=f"example{which}", nx=nx, ny=ny, nz=nz, dx=dx, dy=dy, dz=dz,
+        name=f"example{which}" + (f"_{nx}x{ny}x{nz}" if grid is not None else ""),
+        nx=nx, ny=ny, nz=nz, dx=dx, dy=dy, dz=dz,
         top_depth=2000.0 * FT - 0.5 * dz,
         kf=np.full(n, 395.85 * MD), km=np.full(n, kmx * MD),
         phi_f=np.full(n, 0.039585), phi_m=np.full(n, 0.1392),
