@@ -271,7 +271,6 @@ struct Sim {
   int *btpos = nullptr;           // transpose position of each block entry (True-IMPES)
   std::vector<int> lu_cstart;
   std::vector<int> lu_cmaxlen;   // longest row (blocks) of each colour
-  std::vector<int> lu_cmaxu;     // longest U part of a row, per colour
   // AMG hierarchy (level 0 shares the block pattern)
   std::vector<Level> lev;
   bool amg_ready = false;

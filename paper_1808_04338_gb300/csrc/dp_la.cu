@@ -482,11 +482,12 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd_copy(int r0, int r1, const i
   }
 }
 
-// Backward sweep of a colour whose rows have at most one U block (the
-// colour before the well rows: only perforated cells couple forward): a
-// thread per row, kRes rows per thread, each row's pivot block and y loaded
-// with its U pointers before the (rare) U gathers.  The arithmetic of
-// k_ilu_bwd, both components in one thread.
+// Backward sweep of one colour (short rows): zp_r = D_r (zp_r - sum_{U}
+// U_rj zp_j) with D_r the inverted pivot; a thread per row, kRes rows per
+// thread, each row's pivot block and y loaded with its U pointers before the
+// U gathers (a two-lanes-per-row version, one output component a lane, was
+// 2% slower on the cell colours and 2.3 times slower on the colour before
+// the wells, whose rows have at most one U block).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_ilu_bwd_r(int r0, int r1, int nL, int n,
                                                       const int *__restrict__ Uptr,
@@ -530,41 +531,6 @@ __global__ void __launch_bounds__(kBlock) k_ilu_bwd_r(int r0, int r1, int nL, in
     o.x = fma(d[k][0], y0, d[k][1] * y1);
     o.y = fma(d[k][2], y0, d[k][3] * y1);
     z2[q] = o;
-  }
-}
-
-// Backward sweep of one colour: zp_r = D_r (zp_r - sum_{U} U_rj zp_j) with
-// D_r the inverted pivot.  The two lanes of a row exchange their partial
-// results for the 2x2 product.
-// The factor, its indices and the permutation are streamed evict-first
-// (ld.global.cs).
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_ilu_bwd(int r0, int r1, int nL, int n,
-                                                    const int *__restrict__ Uptr,
-                                                    const int *__restrict__ colp,
-                                                    const T *__restrict__ lu, T *zp) {
-  using T2 = typename V2<T>::t;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = r0 + (t >> 1), comp = t & 1;
-  bool valid = r < r1;                  // no early exit: the pair shuffles
-  const T2 *v2 = reinterpret_cast<const T2 *>(lu);
-  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
-  size_t ub = (size_t)nL + n;
-  int ea = valid ? __ldcs(Uptr + r) : 0, eb = valid ? __ldcs(Uptr + r + 1) : 0;
-  T s = T(0);
-#pragma unroll 4
-  for (int e = ea; e < eb; ++e) {
-    T2 a = __ldcs(v2 + 2 * (ub + e) + comp);
-    T2 xj = z2[__ldcs(colp + ub + e)];
-    s = fma(a.x, xj.x, s);
-    s = fma(a.y, xj.y, s);
-  }
-  T yi = valid ? zp[2 * (size_t)r + comp] - s : T(0);
-  T yo = __shfl_xor_sync(0xffffffffu, yi, 1);
-  if (valid) {
-    T y0 = comp == 0 ? yi : yo, y1 = comp == 0 ? yo : yi;
-    T2 d = __ldcs(v2 + 2 * ((size_t)nL + r) + comp);
-    zp[2 * (size_t)r + comp] = fma(d.x, y0, d.y * y1);
   }
 }
 
@@ -802,20 +768,6 @@ int ilu_setup(Sim *s) {
   DP_TRY(scan_i32(s, nu, s->lu_Uptr, n, &nU));
   if (nL + nU + n != nnz) { s->fail(DP_EINVAL, "ILU(0) pattern without a pivot per row"); return DP_EINVAL; }
   s->lu_nL = nL;
-  {   // longest U part of a row, per colour (the backward sweep's variant)
-    int nc = s->ncolour;
-    int *dev = (int *)dalloc(s, (size_t)(2 * nc + 2) * 4);
-    if (!dev) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
-    DP_CUDA(s, cudaMemcpyAsync(dev, s->lu_cstart.data(), (size_t)(nc + 1) * 4,
-                               cudaMemcpyHostToDevice, s->stream));
-    DP_CUDA(s, cudaMemsetAsync(dev + nc + 1, 0, (size_t)nc * 4, s->stream));
-    DP_LAUNCH(s, k_colour_maxlen, nblk(n), kBlock, 0, n, dev, nc, s->lu_Uptr, dev + nc + 1);
-    s->lu_cmaxu.assign(nc, 0);
-    DP_CUDA(s, cudaMemcpyAsync(s->lu_cmaxu.data(), dev + nc + 1, (size_t)nc * 4,
-                               cudaMemcpyDeviceToHost, s->stream));
-    DP_CUDA(s, cudaStreamSynchronize(s->stream));
-    dfree(s, dev);
-  }
   DP_LAUNCH(s, k_ilu_split, nblk(n), kBlock, 0, n, nL, s->iperm, s->lu_rowptr, s->lu_col,
             s->lu_dpos, s->lu_Lptr, s->lu_Uptr, s->lu_dst, s->lu_colp);
   if (npairs > 0) {
@@ -895,12 +847,9 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
     if (s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, k_ilu_bwd_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL, n,
                 s->lu_Uptr, s->lu_colp, lu, zp);
-    else if (s->lu_cmaxu[c] <= 1)
+    else
       DP_LAUNCH(s, k_ilu_bwd_r<T>, nblk((r1 - r0 + kRes - 1) / kRes), kBlock, 0, r0, r1, nL, n,
                 s->lu_Uptr, s->lu_colp, lu, zp);
-    else
-      DP_LAUNCH(s, k_ilu_bwd<T>, nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, nL, n, s->lu_Uptr,
-                s->lu_colp, lu, zp);
   }
   return DP_OK;
 }
