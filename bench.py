@@ -185,13 +185,13 @@ def _oracle_worker(nx, ny, nz, nsteps, barrier, out):
 
 
 def oracle_sample_all_cores(args, nsteps=2):
-    """The same oracle on every host core at once: one process per core
-    (started with spawn), each running nsteps Newton steps of its own copy of
-    the slice that oracle_sample times; throughput = steps of all processes /
+    """The same oracle on every host core at once (at most 64): one process
+    per core (started with spawn), each running nsteps Newton steps of its own
+    copy of the slice that oracle_sample times; throughput = steps of all processes /
     the slowest process's time, scaled to the full problem like
     oracle_sample.  The oracle itself is single-threaded C, unchanged."""
     import multiprocessing as mp
-    cores = os.cpu_count() or 1
+    cores = min(os.cpu_count() or 1, 64)   # bounded: one process (and one slice copy) a core
     nz = max(1, args.nz // args.sample_div)
     ctx = mp.get_context("spawn")
     barrier, out = ctx.Barrier(cores), ctx.Queue()
