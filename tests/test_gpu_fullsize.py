@@ -1,0 +1,64 @@
+"""GPU against the oracle at the bench's size and launch configuration: the
+200x200x50 field (4M cells, 8M unknowns), report options with the FP32
+preconditioner, as bench.py times it.
+
+At this size the oracle still assembles in seconds, so the Jacobian and
+residual are compared whole, bit for bit.  The solve is checked through
+properties that hold at any size: the update's true residual on the
+decoupled system (formed on the host in FP64) is FGMRES's reported relative
+residual, within the forcing term; and the state a GPU timestep converges to
+satisfies the oracle's own residual to the Newton tolerance, with its mass
+balance closed.
+"""
+import numpy as np
+import pytest
+
+import dp_inputs as di
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bench_size_assembly_solve_and_timestep():
+    import scipy.sparse as sp
+    from paper_1808_04338_gb300 import dpsim
+    prob = di.field8m(200, 200, 50)
+    g = dpsim.Sim(prob, dpsim.options("report", precision=1))
+    o = O.OracleSim(prob, O.options("report"))
+    assert g.nb == o.nb == 4000025
+
+    # Jacobian and residual at the initial iterate, all 19.9M blocks
+    g.assemble(prob.dt)
+    o.assemble(prob.dt)
+    rg, cg, vg, resg = g.jacobian()
+    ro, co, vo, reso = o.jacobian()
+    np.testing.assert_array_equal(rg, ro)
+    np.testing.assert_array_equal(cg, co)
+    assert np.array_equal(vg.view(np.uint64), vo.view(np.uint64))
+    assert np.array_equal(resg.view(np.uint64), reso.view(np.uint64))
+    del vo, vg
+    nr0 = o.norms()
+
+    # one Newton solve: the true residual of the decoupled system
+    rc, st = g.solve_step()
+    assert rc == 0 and st.converged
+    y = g.update()
+    dval, rhs = g.decoupled()
+    n2 = 2 * g.nb
+    A = sp.bsr_matrix((dval, cg, rg), shape=(n2, n2))
+    rel = np.linalg.norm(rhs - A @ y) / np.linalg.norm(rhs)
+    assert abs(rel - st.lin_relres) <= 1e-6 and rel <= st.eta * (1 + 1e-6)
+    del A, dval
+
+    # a whole timestep: the oracle's residual at the GPU's converged state
+    g.set_state(prob.p0, prob.sw0, prob.bhp0)
+    rc, st = g.advance(prob.dt)
+    assert rc == 0 and st.converged and st.newton_iters > 1
+    o.set_iterate(*g.get_state())
+    o.assemble(prob.dt)
+    nr = o.norms()
+    opts = O.options("report")
+    assert nr[0] <= opts.newton_tol * nr0[0] * (1 + 1e-9) or nr[1] <= opts.newton_atol
+    for a in range(2):   # mass change = dt x well inflow, to the Newton tolerance
+        dm, w = nr[4 + a], nr[6 + a] * prob.dt
+        assert abs(dm - w) <= 1e-3 * max(abs(dm), abs(w))
