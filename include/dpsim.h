@@ -111,8 +111,10 @@ typedef struct {
 /* Solver options.  eta_mode 0: fixed forcing term eta_fixed; 1-3: the three
  * forcing terms of Section 3.1, clipped to [eta_min, eta_max].  precond:
  * 0 none, 1 block ILU(0) only, 2 CPR-FPF.  precision: 0 FP64 everywhere;
- * 1 ILU(0) factors and AMG levels stored and applied in FP32 inside FP64
- * FGMRES.  amg_gs_levels: AMG levels 0..amg_gs_levels-1 are smoothed by
+ * 1 the preconditioner in FP32 inside FP64 FGMRES: ILU(0) factors, AMG
+ * levels and the CPR stage residuals (from an FP32 copy of the decoupled
+ * operator); the Arnoldi products, restart residuals and orthogonalisation
+ * stay FP64.  amg_gs_levels: AMG levels 0..amg_gs_levels-1 are smoothed by
  * multicolour Gauss-Seidel (forward colour order before the coarse
  * correction, reverse after), the coarser ones by one l1-Jacobi sweep
  * before and after, x += (b - A x) / sum_j |a_ij| (Baker, Falgout, Kolev and
