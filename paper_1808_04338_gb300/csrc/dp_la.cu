@@ -866,7 +866,9 @@ __global__ void __launch_bounds__(kBlock) k_ilu_result(int n, const int *__restr
                                                        const T *__restrict__ zp,
                                                        const double *__restrict__ base,
                                                        double *__restrict__ out,
-                                                       T *__restrict__ outT) {
+                                                       T *__restrict__ outT,
+                                                       const float *__restrict__ inj,
+                                                       int inj_perm) {
   using T2 = typename V2<T>::t;
   const T2 *z2 = reinterpret_cast<const T2 *>(zp);
   int S = gridDim.x * blockDim.x;
@@ -885,6 +887,8 @@ __global__ void __launch_bounds__(kBlock) k_ilu_result(int n, const int *__restr
     if (i < n) {
       z[k] = z2[p[k]];
       bs[k] = base ? reinterpret_cast<const double2 *>(base)[i] : make_double2(0.0, 0.0);
+      // the coarse correction injected into the base's pressure component
+      if (inj) bs[k].x = bs[k].x + double(__ldg(inj + (inj_perm ? p[k] : i)));
     }
   }
 #pragma unroll
@@ -898,11 +902,15 @@ __global__ void __launch_bounds__(kBlock) k_ilu_result(int n, const int *__restr
   }
 }
 
+// out = base + result; with inj, out = (base + inj injected) + result, inj
+// (a level-0 vector, natural or, with inj_perm, colour order) added to the
+// base's pressure component first.
 template <typename T>
-static int ilu_result(Sim *s, const double *base, double *out, T *outT = nullptr) {
+static int ilu_result(Sim *s, const double *base, double *out, T *outT = nullptr,
+                      const float *inj = nullptr, int inj_perm = 0) {
   int n = s->K.n;
   DP_LAUNCH(s, k_ilu_result<T>, nblk((n + kRes - 1) / kRes), kBlock, 0, n, s->iperm,
-            reinterpret_cast<const T *>(s->ilu_zp), base, out, outT);
+            reinterpret_cast<const T *>(s->ilu_zp), base, out, outT, inj, inj_perm);
   return DP_OK;
 }
 
@@ -1827,15 +1835,12 @@ __global__ void k_inject_add(int n, const T *xp, double *z, const int *imap) {
   if (i < n) z[2 * i] += double(xp[imap ? __ldg(imap + i) : i]);
 }
 
-// The same injection applied to an FP64 vector and to its FP32 copy (the
-// copy updated in FP32: no conversions on the FP64 pipe).
-__global__ void k_inject_add2(int n, const float *xp, double *z, float *zf, const int *imap) {
+// The injection into the FP32 copy of z1 only (updated in FP32: no
+// conversions on the FP64 pipe); the FP64 z1 takes the same correction in
+// the final result gather (ilu_result's inj).
+__global__ void k_inject_f32(int n, const float *xp, float *zf, const int *imap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    float e = xp[imap ? __ldg(imap + i) : i];
-    z[2 * i] += double(e);
-    zf[2 * i] += e;
-  }
+  if (i < n) zf[2 * i] += xp[imap ? __ldg(imap + i) : i];
 }
 
 
@@ -1880,11 +1885,12 @@ int cpr_apply(Sim *s, const double *r, double *z) {
             s->sv_long0, s->srowptr, s->scol, reinterpret_cast<const float2 *>(s->spf), s->z1f,
             r, L0.bf, m);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
-  DP_LAUNCH(s, k_inject_add2, nblk(nb), kBlock, 0, nb, L0.xf, s->z1, s->z1f, m);
+  DP_LAUNCH(s, k_inject_f32, nblk(nb), kBlock, 0, nb, L0.xf, s->z1f, m);
   DP_LAUNCH(s, k_bsr_resid_f32, 1 + nblk(2LL * s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
             s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1f, r, s->r1f);
   DP_TRY((ilu_apply_t<float, float>(s, s->lu_valf, s->r1f)));
-  return ilu_result<float>(s, s->z1, z);              // z = z2 + F (r - A z2)
+  // z = z2 + F (r - A z2), z2 = z1 + P e formed here
+  return ilu_result<float>(s, s->z1, z, nullptr, L0.xf, m ? 1 : 0);
 }
 
 // ---------------------------------------------------------------- FGMRES
