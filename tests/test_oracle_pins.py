@@ -58,7 +58,9 @@ def random_interior_state(prob, seed=3):
 # ---------------------------------------------------------------- linear solve
 
 @pytest.mark.parametrize("make,schur", [(lambda: small_problem(3, 3, 2), 0), (di.tiny, 0),
-                                        (lambda: small_problem(3, 3, 2), 1), (di.tiny, 1)])
+                                        (lambda: small_problem(3, 3, 2), 1), (di.tiny, 1),
+                                        (lambda: with_pc(small_problem(3, 3, 2, g=9.80665)), 1),
+                                        (lambda: di.paper_example(2), 0)])
 def test_cpr_fgmres_matches_dense_lu(make, schur):
     """The FGMRES/CPR-FPF Newton update solves J y = -R (Algorithm 1, step 5,
     eta = 1e-12): its true residual, formed with a dense copy of J, is at the
