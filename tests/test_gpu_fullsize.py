@@ -2,8 +2,9 @@
 200x200x50 field (4M cells, 8M unknowns), report options with the FP32
 preconditioner, as bench.py times it.
 
-At this size the oracle still assembles in seconds, so the Jacobian and
-residual are compared whole, bit for bit.  The solve is checked through
+At this size the oracle still assembles and sets up in seconds, so the
+Jacobian and residual, the decoupled system, the colourings and the AMG
+hierarchy are compared whole, bit for bit.  The solve is checked through
 properties that hold at any size: the update's true residual on the
 decoupled system (formed on the host in FP64) is FGMRES's reported relative
 residual, within the forcing term; and the state a GPU timestep converges to
@@ -62,3 +63,33 @@ def test_bench_size_assembly_solve_and_timestep():
     for a in range(2):   # mass change = dt x well inflow, to the Newton tolerance
         dm, w = nr[4 + a], nr[6 + a] * prob.dt
         assert abs(dm - w) <= 1e-3 * max(abs(dm), abs(w))
+
+
+def test_bench_size_decoupling_colours_and_amg_setup_bit_exact():
+    """At the bench's size, after the first Newton solve's set-up: the
+    decoupled matrix and right-hand side, the ILU(0) colouring, and every AMG
+    level's aggregates, colouring and operator values are those of the oracle,
+    bit for bit (the oracle runs one FGMRES iteration: its set-up is what is
+    compared)."""
+    from paper_1808_04338_gb300 import dpsim
+    prob = di.field8m(200, 200, 50)
+    g = dpsim.Sim(prob, dpsim.options("report", precision=1))
+    o = O.OracleSim(prob, O.options("report", gmres_maxit=1))
+    g.assemble(prob.dt)
+    o.assemble(prob.dt)
+    g.solve_step()
+    o.solve_step()
+    gv, gr = g.decoupled()
+    ov, orr = o.decoupled()
+    assert np.array_equal(gv.view(np.uint64), ov.view(np.uint64))
+    assert np.array_equal(gr.view(np.uint64), orr.view(np.uint64))
+    del gv, ov
+    (gc, gn), (oc, on) = g.colours(), o.colours()
+    assert gn == on
+    np.testing.assert_array_equal(gc, oc)
+    Lg, Lo = g.amg_levels(), o.amg_levels()
+    assert len(Lg) == len(Lo) > 2
+    for a, b in zip(Lg, Lo):
+        np.testing.assert_array_equal(a["agg"], b["agg"])
+        np.testing.assert_array_equal(a["colour"], b["colour"])
+        assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
