@@ -14,7 +14,8 @@ OUT = os.path.join(ROOT, "paper_1808_04338_gb300", "_build")
 
 def _layouts(header, structs):
     """{name: (size, {field: offset})} from the C compiler."""
-    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{header}"', "int main(void) {"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>",
+             f'#include "{os.path.basename(header)}"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("S {name} %zu\\n", sizeof({name}));')
         for f in cls._fields_:
