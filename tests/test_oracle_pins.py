@@ -839,3 +839,13 @@ def test_time_loop_gives_up_below_the_smallest_step():
     assert rc == -5 and st.steps == 0 and st.cuts >= 1 and st.t == 0.0
     for a, b in zip(s.get_state(), p0):
         np.testing.assert_array_equal(a, b)
+
+
+def test_time_loop_stops_at_its_step_limit():
+    """After max_steps accepted steps the run stops short of t_end with the
+    Newton-failure code and reports the time and steps it reached."""
+    prob = di.paper_example(1)
+    s = O.OracleSim(prob, O.options("report"))
+    rc, st = s.run(100 * di.DAY, 1 * di.DAY, 20 * di.DAY, 0.01 * di.DAY, max_steps=3)
+    assert rc == -5 and st.steps == 3 and st.cuts == 0
+    assert abs(st.t - 7 * di.DAY) <= 1e-9 * di.DAY        # 1 + 2 + 4 days
