@@ -109,7 +109,12 @@ typedef struct {
 } dp_allocator;
 
 /* Solver options.  eta_mode 0: fixed forcing term eta_fixed; 1-3: the three
- * forcing terms of Section 3.1, clipped to [eta_min, eta_max].  precond:
+ * forcing terms of Section 3.1, clipped to [eta_min, eta_max] (eta_max on a
+ * timestep's first Newton iteration).  With b = -R and the previous solve's
+ * linear residual r = b - J y (J as assembled), every norm taken in the
+ * scaled norm of Algorithm 1's ||b|| (sim_get_norms out[0]): 1 is
+ * ||b(x^l) - r^{l-1}|| / ||b(x^{l-1})||, 2 is (||b(x^l)|| - ||r^{l-1}||) /
+ * ||b(x^{l-1})||, 3 is eta_gamma (||b(x^l)|| / ||b(x^{l-1})||)^eta_beta.  precond:
  * 0 none, 1 block ILU(0) only, 2 CPR-FPF.  precision: 0 FP64 everywhere;
  * 1 the preconditioner in FP32 inside FP64 FGMRES: ILU(0) factors, AMG
  * levels and the CPR stage residuals (from an FP32 copy of the decoupled
@@ -218,18 +223,21 @@ int sim_get_norms(dp_sim *sim, double *out8);
  * (Eq. "decoupled-eq"), pressure extraction, block ILU(0), AMG setup (first
  * call) or value refresh, CPR-FPF preconditioned FGMRES to the forcing term
  * eta, and the update x += y (saturation change limited to +-ds_max, s_w
- * kept in [0, 1]).  Synchronises; fills *stats when not NULL. */
+ * kept in [0, 1]).  Synchronises; fills *stats when not NULL.  DP_ELINEAR:
+ * FGMRES did not reach eta within gmres_maxit iterations; no update is made
+ * (the state is unchanged; call sim_assemble before solving again). */
 int sim_solve_step(dp_sim *sim, dp_stats *stats);
 
-/* One backward-Euler timestep of length dt by Algorithm 1.  On Newton
- * failure the old state is restored and DP_ENEWTON returned. */
+/* One backward-Euler timestep of length dt by Algorithm 1.  On failure the
+ * old state is restored and DP_ENEWTON (Newton did not converge within
+ * newton_max iterations) or DP_ELINEAR (a linear solve failed) returned. */
 int sim_advance(dp_sim *sim, double dt, dp_stats *stats);
 
 /* A simulation period [0, t_end] (seconds) by sim_advance timesteps, as the
  * paper's examples run theirs (800 and 1600 days): dt0 first; after a
  * converged step the next is min(2 h, dt_max) (h the step just taken); a step
- * whose Newton iteration fails is retried at h / 2 (a cut); the last step
- * ends at t_end.  Returns DP_OK at t_end; DP_ENEWTON when a retry would fall
+ * whose Newton iteration or linear solve fails is retried at h / 2 (a cut);
+ * the last step ends at t_end.  Returns DP_OK at t_end; DP_ENEWTON when a retry would fall
  * below dt_min or after max_steps accepted steps (the state is that of the
  * last accepted step, stats->t its time); other codes as sim_advance.
  * DP_EINVAL: sim NULL, t_end, dt0 or dt_min not > 0, dt_max < dt0, or
@@ -420,8 +428,10 @@ const char *sim_last_error(const dp_sim *sim);
  * clearing between calls, but calls that overlap on the GPU (on different
  * streams, or from different threads) share that array and race: order
  * them on one stream.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  No cudaMalloc, cudaFree or
+ * device address (cudaGetSymbolAddress) with that device current and keeps
+ * it for the life of the process; make that first call before any stream
+ * capture.  A program that resets the device (cudaDeviceReset) invalidates
+ * the kept address and must not call this entry point after the reset.  No cudaMalloc, cudaFree or
  * allocating library routine is called.  Returns DP_OK, DP_EINVAL or
  * DP_ECUDA. */
 int dp_residual_norms_noalloc(const dp_grid *grid, const dp_fluid *fluid, const double *phi_f,

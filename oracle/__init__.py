@@ -19,15 +19,36 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 OG_OK, OG_EINVAL, OG_ENOMEM, OG_ELINEAR, OG_ENEWTON = 0, -1, -2, -4, -5
 
 
+def _compile(src: str, out: str) -> None:
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
+           "-fno-fast-math", "-fPIC", "-shared", "-I", _HERE, src, "-o", out + ".tmp", "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(out + ".tmp", out)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, IEEE double)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "dpsim_oracle.h"))):
-        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
-               "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
-        subprocess.check_call(cmd)
-        os.replace(_LIB + ".tmp", _LIB)
+        _compile(_SRC, _LIB)
     return _LIB
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def build_variant(text: str, directory: str, name: str = "variant") -> str:
+    """Compile a modified copy of the oracle's source (tests that plant a
+    mistake and check that a pin catches it) into `directory`; returns the
+    library path.  The oracle itself is not touched."""
+    src = os.path.join(directory, name + ".c")
+    with open(src, "w") as f:
+        f.write(text)
+    out = os.path.join(directory, "lib" + name + ".so")
+    _compile(src, out)
+    return out
 
 
 class og_grid(C.Structure):
@@ -114,53 +135,82 @@ def options(mode: str = "parity", **kw) -> og_options:
 
 
 _lib = None
+_override = None
 
 
 def lib():
+    """The oracle library in use: the built oracle, or a variant installed by
+    ``use_library``."""
     global _lib
+    if _override is not None:
+        return _override
     if _lib is None:
-        L = C.CDLL(build())
-        P, I, D = C.c_void_p, C.c_int32, C.c_double
-        L.oracle_create.argtypes = [C.POINTER(og_grid), C.POINTER(og_rock), C.POINTER(og_fluid),
-                                    C.POINTER(og_well), I, C.POINTER(og_options), C.POINTER(P)]
-        L.oracle_destroy.argtypes = [P]
-        L.oracle_destroy.restype = None
-        for name in ("oracle_set_state", "oracle_set_iterate", "oracle_get_state"):
-            getattr(L, name).argtypes = [P, P, P, P]
-        L.oracle_sizes.argtypes = [P, P, P]
-        L.oracle_solver_sizes.argtypes = [P, P, P]
-        L.oracle_well_controls.argtypes = [P, P, P]
-        L.oracle_well_rates.argtypes = [P, P, P]
-        L.oracle_cap_pressure.argtypes = [C.c_int32, P, C.c_double, P, P]
-        L.oracle_cap_pressure.restype = None
-        L.oracle_run.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
-                                 C.POINTER(og_run_stats)]
-        L.oracle_assemble.argtypes = [P, D]
-        L.oracle_get_jacobian.argtypes = [P, P, P, P, P]
-        L.oracle_get_norms.argtypes = [P, P]
-        L.oracle_solve_step.argtypes = [P, C.POINTER(og_stats)]
-        L.oracle_advance.argtypes = [P, D, C.POINTER(og_stats)]
-        L.oracle_get_update.argtypes = [P, P]
-        L.oracle_get_decoupled.argtypes = [P, P, P]
-        L.oracle_get_colours.argtypes = [P, P]
-        L.oracle_amg_level_info.argtypes = [P, I, P, P, P]
-        L.oracle_amg_level_arrays.argtypes = [P, I, P, P, P, P, P]
-        L.oracle_well_index.argtypes = [P, P]
-        L.oracle_greedy_colour.argtypes = [I, P, P, P]
-        L.oracle_ilu0_solve.argtypes = [I, P, P, P, P, P, P]
-        L.oracle_amg_create.argtypes = [I, P, P, P, D, I, I, C.POINTER(P)]
-        L.oracle_amg_vcycle.argtypes = [P, P, P]
-        L.oracle_amg_set_smoother.argtypes = [P, I]
-        L.oracle_amg_info.argtypes = [P, I, P, P, P]
-        L.oracle_amg_arrays.argtypes = [P, I, P, P, P, P, P]
-        L.oracle_amg_destroy.argtypes = [P]
-        L.oracle_amg_destroy.restype = None
-        L.oracle_fgmres_bsr.argtypes = [I, P, P, P, P, P, I, I, I, D, P, P]
-        L.oracle_fgmres_amg.argtypes = [I, P, P, P, P, P, D, I, I, I, D, P, P]
-        L.oracle_hash32.argtypes = [C.c_uint32]
-        L.oracle_hash32.restype = C.c_uint32
-        _lib = L
+        _lib = load_library(build())
     return _lib
+
+
+class use_library:
+    """Context manager: objects created inside it use the library at `path`
+    (a variant from ``build_variant``)."""
+
+    def __init__(self, path: str):
+        self.L = load_library(path)
+
+    def __enter__(self):
+        global _override
+        self._prev, _override = _override, self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _override
+        _override = self._prev
+        return False
+
+
+def load_library(path: str):
+    """The library at `path` with the argument types of every entry point."""
+    L = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int32, C.c_double
+    L.oracle_create.argtypes = [C.POINTER(og_grid), C.POINTER(og_rock), C.POINTER(og_fluid),
+                                C.POINTER(og_well), I, C.POINTER(og_options), C.POINTER(P)]
+    L.oracle_destroy.argtypes = [P]
+    L.oracle_destroy.restype = None
+    for name in ("oracle_set_state", "oracle_set_iterate", "oracle_get_state"):
+        getattr(L, name).argtypes = [P, P, P, P]
+    L.oracle_sizes.argtypes = [P, P, P]
+    L.oracle_solver_sizes.argtypes = [P, P, P]
+    L.oracle_well_controls.argtypes = [P, P, P]
+    L.oracle_well_rates.argtypes = [P, P, P]
+    L.oracle_cap_pressure.argtypes = [C.c_int32, P, C.c_double, P, P]
+    L.oracle_cap_pressure.restype = None
+    L.oracle_run.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                             C.POINTER(og_run_stats)]
+    L.oracle_assemble.argtypes = [P, D]
+    L.oracle_get_jacobian.argtypes = [P, P, P, P, P]
+    L.oracle_get_norms.argtypes = [P, P]
+    L.oracle_solve_step.argtypes = [P, C.POINTER(og_stats)]
+    L.oracle_advance.argtypes = [P, D, C.POINTER(og_stats)]
+    L.oracle_get_update.argtypes = [P, P]
+    L.oracle_get_decoupled.argtypes = [P, P, P]
+    L.oracle_get_colours.argtypes = [P, P]
+    L.oracle_amg_level_info.argtypes = [P, I, P, P, P]
+    L.oracle_amg_level_arrays.argtypes = [P, I, P, P, P, P, P]
+    L.oracle_well_index.argtypes = [P, P]
+    L.oracle_greedy_colour.argtypes = [I, P, P, P]
+    L.oracle_ilu0_solve.argtypes = [I, P, P, P, P, P, P]
+    L.oracle_amg_create.argtypes = [I, P, P, P, D, I, I, C.POINTER(P)]
+    L.oracle_amg_vcycle.argtypes = [P, P, P]
+    L.oracle_amg_set_smoother.argtypes = [P, I]
+    L.oracle_amg_info.argtypes = [P, I, P, P, P]
+    L.oracle_amg_arrays.argtypes = [P, I, P, P, P, P, P]
+    L.oracle_amg_destroy.argtypes = [P]
+    L.oracle_amg_destroy.restype = None
+    L.oracle_fgmres_bsr.argtypes = [I, P, P, P, P, P, I, I, I, D, P, P]
+    L.oracle_fgmres_amg.argtypes = [I, P, P, P, P, P, D, I, I, I, D, P, P]
+    L.oracle_hash32.argtypes = [C.c_uint32]
+    L.oracle_hash32.restype = C.c_uint32
+    L.oracle_mis2.argtypes = [I, P, P, P, D, P]
+    return L
 
 
 def _p(a):
@@ -179,7 +229,7 @@ class OracleSim:
     """One realisation in the oracle.  ``prob`` is a ``dp_inputs.Problem``."""
 
     def __init__(self, prob, opts: og_options | None = None):
-        L = lib()
+        L = self._L = lib()
         self.prob = prob
         self.opts = opts if opts is not None else options("parity")
         g = og_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.top_depth)
@@ -213,90 +263,90 @@ class OracleSim:
         self.set_state(prob.p0, prob.sw0, prob.bhp0)
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
-            _lib.oracle_destroy(self.h)
+        if getattr(self, "h", None):
+            self._L.oracle_destroy(self.h)
             self.h = None
 
     def set_state(self, p, sw, bhp):
         p, sw, bhp = _f64(p), _f64(sw), _f64(bhp if len(bhp) else np.zeros(1))
-        lib().oracle_set_state(self.h, _p(p), _p(sw), _p(bhp))
+        self._L.oracle_set_state(self.h, _p(p), _p(sw), _p(bhp))
 
     def set_iterate(self, p, sw, bhp):
         p, sw, bhp = _f64(p), _f64(sw), _f64(bhp if len(bhp) else np.zeros(1))
-        lib().oracle_set_iterate(self.h, _p(p), _p(sw), _p(bhp))
+        self._L.oracle_set_iterate(self.h, _p(p), _p(sw), _p(bhp))
 
     def get_state(self):
         p = np.zeros(self.nc); sw = np.zeros(self.nc); bhp = np.zeros(max(self.nw, 1))
-        lib().oracle_get_state(self.h, _p(p), _p(sw), _p(bhp))
+        self._L.oracle_get_state(self.h, _p(p), _p(sw), _p(bhp))
         return p, sw, bhp[:self.nw]
 
     def assemble(self, dt):
-        rc = lib().oracle_assemble(self.h, float(dt))
+        rc = self._L.oracle_assemble(self.h, float(dt))
         if rc:
             raise ValueError(f"oracle_assemble failed ({rc})")
 
     def jacobian(self):
         rowptr = np.zeros(self.nb + 1, np.int32); col = np.zeros(self.nnzb, np.int32)
         val = np.zeros((self.nnzb, 2, 2)); res = np.zeros(2 * self.nb)
-        lib().oracle_get_jacobian(self.h, _p(rowptr), _p(col), _p(val), _p(res))
+        self._L.oracle_get_jacobian(self.h, _p(rowptr), _p(col), _p(val), _p(res))
         return rowptr, col, val, res
 
     def norms(self):
         out = np.zeros(8)
-        lib().oracle_get_norms(self.h, _p(out))
+        self._L.oracle_get_norms(self.h, _p(out))
         return out
 
     def solve_step(self):
         st = og_stats()
-        rc = lib().oracle_solve_step(self.h, C.byref(st))
+        rc = self._L.oracle_solve_step(self.h, C.byref(st))
         return rc, st
 
     def advance(self, dt):
         st = og_stats()
-        rc = lib().oracle_advance(self.h, float(dt), C.byref(st))
+        rc = self._L.oracle_advance(self.h, float(dt), C.byref(st))
         return rc, st
 
     def run(self, t_end, dt0, dt_max, dt_min, max_steps=100000):
         """oracle_run: (rc, og_run_stats) of the period [0, t_end] (seconds)."""
         st = og_run_stats()
-        rc = lib().oracle_run(self.h, float(t_end), float(dt0), float(dt_max), float(dt_min),
+        rc = self._L.oracle_run(self.h, float(t_end), float(dt0), float(dt_max), float(dt_min),
                               int(max_steps), C.byref(st))
         return rc, st
 
     def update(self):
         y = np.zeros(2 * self.nb)
-        lib().oracle_get_update(self.h, _p(y))
+        self._L.oracle_get_update(self.h, _p(y))
         return y
 
     def decoupled(self):
         val = np.zeros((self.snnzb, 2, 2)); rhs = np.zeros(2 * self.snb)
-        lib().oracle_get_decoupled(self.h, _p(val), _p(rhs))
+        self._L.oracle_get_decoupled(self.h, _p(val), _p(rhs))
         return val, rhs
 
     def well_controls(self):
         k = np.zeros(max(self.nw, 1), np.int32); t = np.zeros(max(self.nw, 1))
-        lib().oracle_well_controls(self.h, _p(k), _p(t))
+        self._L.oracle_well_controls(self.h, _p(k), _p(t))
         return k[:self.nw], t[:self.nw]
 
     def well_rates(self):
         """Per well (oil, water) mass rates, kg/s, positive into the reservoir."""
         qo = np.zeros(max(self.nw, 1)); qw = np.zeros(max(self.nw, 1))
-        lib().oracle_well_rates(self.h, _p(qo), _p(qw))
+        self._L.oracle_well_rates(self.h, _p(qo), _p(qw))
         return qo[:self.nw], qw[:self.nw]
 
     def colours(self):
         c = np.zeros(self.snb, np.int32)
-        ncol = lib().oracle_get_colours(self.h, _p(c))
+        ncol = self._L.oracle_get_colours(self.h, _p(c))
         return c, ncol
 
     def well_index(self):
         wi = np.zeros(sum(w.k_bot - w.k_top + 1 for w in self.prob.wells) + 1)
-        n = lib().oracle_well_index(self.h, _p(wi))
+        n = self._L.oracle_well_index(self.h, _p(wi))
         return wi[:n]
 
     def amg_levels(self):
         """Per level: dict(n, nnz, nagg, rowptr, col, val, agg, colour)."""
-        L = lib()
+        L = self._L
         out = []
         lev = 0
         while True:
@@ -324,20 +374,21 @@ class OracleAMG:
                  gs_levels=30):
         self._a = (_i32(rowptr), _i32(col), _f64(val))
         self.n = len(rowptr) - 1
+        self._L = lib()
         h = C.c_void_p()
-        lib().oracle_amg_create(self.n, *[_p(a) for a in self._a], float(theta),
+        self._L.oracle_amg_create(self.n, *[_p(a) for a in self._a], float(theta),
                                 int(coarse_max), int(max_levels), C.byref(h))
         self.h = h
-        lib().oracle_amg_set_smoother(self.h, int(gs_levels))
+        self._L.oracle_amg_set_smoother(self.h, int(gs_levels))
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
-            _lib.oracle_amg_destroy(self.h)
+        if getattr(self, "h", None):
+            self._L.oracle_amg_destroy(self.h)
             self.h = None
 
     def vcycle(self, b):
         b = _f64(b); x = np.zeros(self.n)
-        lib().oracle_amg_vcycle(self.h, _p(b), _p(x))
+        self._L.oracle_amg_vcycle(self.h, _p(b), _p(x))
         return x
 
     def levels(self):
@@ -345,14 +396,14 @@ class OracleAMG:
         lev = 0
         while True:
             n, nnz, nagg = C.c_int32(), C.c_int32(), C.c_int32()
-            nl = lib().oracle_amg_info(self.h, lev, C.byref(n), C.byref(nnz), C.byref(nagg))
+            nl = self._L.oracle_amg_info(self.h, lev, C.byref(n), C.byref(nnz), C.byref(nagg))
             if nl < 0:
                 break
             d = dict(n=n.value, nnz=nnz.value, nagg=nagg.value,
                      rowptr=np.zeros(n.value + 1, np.int32), col=np.zeros(nnz.value, np.int32),
                      val=np.zeros(nnz.value), agg=np.zeros(n.value, np.int32),
                      colour=np.zeros(n.value, np.int32))
-            lib().oracle_amg_arrays(self.h, lev, _p(d["rowptr"]), _p(d["col"]), _p(d["val"]),
+            self._L.oracle_amg_arrays(self.h, lev, _p(d["rowptr"]), _p(d["col"]), _p(d["val"]),
                                     _p(d["agg"]), _p(d["colour"]))
             out.append(d)
             lev += 1
@@ -408,3 +459,13 @@ def fgmres_amg(rowptr, col, val, b, theta=0.08, coarse_max=128, restart=30, maxi
 
 def hash32(i: int) -> int:
     return lib().oracle_hash32(i)
+
+
+def mis2(rowptr, col, val, theta=0.08):
+    """MIS(2) of the strength graph of a scalar CSR matrix: (state, roots),
+    state 2 for a root and 0 otherwise."""
+    rowptr, col, val = _i32(rowptr), _i32(col), _f64(val)
+    n = len(rowptr) - 1
+    st = np.zeros(n, np.int32)
+    roots = lib().oracle_mis2(n, _p(rowptr), _p(col), _p(val), float(theta), _p(st))
+    return st, roots

@@ -407,6 +407,18 @@ static void mis2(const og_csr *A, const unsigned char *s, int *state) {
   free(t0); free(t1);
 }
 
+int oracle_mis2(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                double theta, int32_t *state) {
+  if (n < 1 || !rowptr || !col || !val || !state) return OG_EINVAL;
+  og_csr A = {n, n, rowptr[n], (int *)rowptr, (int *)col, (double *)val};
+  unsigned char *s = strength(&A, theta);
+  mis2(&A, s, state);
+  free(s);
+  int roots = 0;
+  for (int i = 0; i < n; ++i) roots += state[i] == 2;
+  return roots;
+}
+
 /* Aggregates: roots numbered in index order; a distance-1 node joins the
  * strongly connected root with the largest (hash, index); a distance-2 node
  * joins the aggregate of its strongly connected, already assigned neighbour
@@ -1016,8 +1028,15 @@ typedef struct {
   og_csr Ap;
   double *y, *bh;    /* Newton update and decoupled right-hand side */
   double norms[8];
-  double prev_res, prev_linres;
+  double prev_res;
   int newton_iter;
+  /* forcing terms 1-2 of Section 3.1 need the linear residual of the last
+   * solve: lq = R + J y with J as assembled (Ja keeps J's assembled values
+   * when the full system is decoupled in place), and its scaled norms at the
+   * next assembly: lin_norms[0] = ||R~(lq)||_2, lin_norms[1] = ||R~(R - lq)||_2 */
+  double *Ja, *lq;
+  int have_lq;
+  double lin_norms[2];
 } og_sim;
 
 /* Peaceman's effective radius for a vertical well (Section 2, the first
@@ -1298,10 +1317,14 @@ static void assemble(og_sim *s) {
 }
 
 /* Scaled residual norms (Algorithm 1's ||b||) and mass-balance sums.
- * Cell rows scaled by dt / (rho_ref phi_ref V), well rows by the target. */
+ * Cell rows scaled by dt / (rho_ref phi_ref V), well rows by the target.
+ * With a linear residual lq of the last solve (forcing terms 1-2), its
+ * scaled 2-norm and that of R - lq, in the same scaling. */
 static void norms(og_sim *s) {
   double V = (s->g.dx * s->g.dy) * s->g.dz;
   double s2 = 0.0, sinf = 0.0, sro = 0.0, srw = 0.0, dmo = 0.0, dmw = 0.0, wo = 0.0, ww = 0.0;
+  double lq2 = 0.0, ld2 = 0.0;
+  int lin = s->have_lq && (s->o.eta_mode == 1 || s->o.eta_mode == 2);
   for (int c = 0; c < s->nc; ++c) {
     int loc = c / 2;
     double phi_ref = (c % 2 == 0) ? s->phi_f[loc] : s->phi_m[loc];
@@ -1310,6 +1333,12 @@ static void norms(og_sim *s) {
       double v = (s->R[2 * c + al] * s->dt) / ((rref * phi_ref) * V);
       s2 += v * v;
       if (fabs(v) > sinf) sinf = fabs(v);
+      if (lin) {
+        double a = (s->lq[2 * c + al] * s->dt) / ((rref * phi_ref) * V);
+        double d = ((s->R[2 * c + al] - s->lq[2 * c + al]) * s->dt) / ((rref * phi_ref) * V);
+        lq2 += a * a;
+        ld2 += d * d;
+      }
     }
     sro += s->R[2 * c]; srw += s->R[2 * c + 1];
     og_props q;
@@ -1328,10 +1357,17 @@ static void norms(og_sim *s) {
   }
   for (int w = 0; w < s->nwells; ++w) {
     double sc = s->wells[w].kind == 0 ? fmax(s->wells[w].target, 1e-12) : s->wells[w].target;
-    double v = s->R[2 * (s->nc + w)] / sc;
+    int row = 2 * (s->nc + w);
+    double v = s->R[row] / sc;
     s2 += v * v;
     if (fabs(v) > sinf) sinf = fabs(v);
+    if (lin) {
+      double a = s->lq[row] / sc, d = (s->R[row] - s->lq[row]) / sc;
+      lq2 += a * a;
+      ld2 += d * d;
+    }
   }
+  s->lin_norms[0] = sqrt(lq2); s->lin_norms[1] = sqrt(ld2);
   s->norms[0] = sqrt(s2); s->norms[1] = sinf;
   s->norms[2] = sro; s->norms[3] = srw;
   s->norms[4] = dmo; s->norms[5] = dmw; s->norms[6] = wo; s->norms[7] = ww;
@@ -1597,6 +1633,7 @@ void oracle_destroy(void *h) {
   free(s->kf); free(s->km); free(s->phi_f); free(s->phi_m); free(s->wells); free(s->perf);
   free(s->ctl_kind); free(s->ctl_target); free(s->pc_own[0]); free(s->pc_own[1]);
   free(s->J.rowptr); free(s->J.col); free(s->J.diag); free(s->J.val);
+  free(s->Ja); free(s->lq);
   free(s->R); free(s->p); free(s->sw); free(s->bhp); free(s->pn); free(s->swn); free(s->bhpn);
   free(s->Mn); free(s->y); free(s->bh); free(s->colour); free(s->Ap.val);
   if (s->o.schur) {
@@ -1667,7 +1704,7 @@ int oracle_set_state(void *h, const double *p, const double *sw, const double *b
   oracle_set_iterate(h, p, sw, bhp);
   save_old(s);
   s->newton_iter = 0;            /* a new old time level starts a new timestep */
-  s->prev_res = 0.0; s->prev_linres = 0.0;
+  s->prev_res = 0.0; s->have_lq = 0;
   return 0;
 }
 
@@ -1811,26 +1848,54 @@ int oracle_amg_level_arrays(void *h, int32_t level, int32_t *rowptr, int32_t *co
 
 /* Forcing term eta_l of Algorithm 1 (Section 3.1).  Choice 0 is a fixed
  * eta; choices 1-3 are the three formulas given, clipped to
- * [eta_min, eta_max]; the first Newton iteration uses eta_max. */
+ * [eta_min, eta_max]; the first Newton iteration uses eta_max.  With the
+ * right-hand side b = -R and the linear residual r^{l-1} = b(x^{l-1}) -
+ * A y^{l-1} = -lq of the previous solve, in the scaled norm of ||b||:
+ *   1: ||b(x^l) - r^{l-1}|| / ||b(x^{l-1})|| = ||R~(R - lq)|| / prev_res,
+ *   2: (||b(x^l)|| - ||r^{l-1}||) / ||b(x^{l-1})|| = (res - ||R~(lq)||) / prev_res,
+ *   3: gamma (||b(x^l)|| / ||b(x^{l-1})||)^beta. */
 static double forcing(og_sim *s, double res) {
   const og_options *o = &s->o;
   if (o->eta_mode == 0) return o->eta_fixed;
   if (s->newton_iter == 0 || s->prev_res <= 0.0) return o->eta_max;
   double eta;
-  if (o->eta_mode == 1) eta = fabs(res - s->prev_linres) / s->prev_res;
-  else if (o->eta_mode == 2) eta = (res - s->prev_linres) / s->prev_res;
+  if (o->eta_mode == 1) eta = s->lin_norms[1] / s->prev_res;
+  else if (o->eta_mode == 2) eta = (res - s->lin_norms[0]) / s->prev_res;
   else eta = o->eta_gamma * pow(res / s->prev_res, o->eta_beta);
   if (eta < o->eta_min) eta = o->eta_min;
   if (eta > o->eta_max) eta = o->eta_max;
   return eta;
 }
 
+/* lq = R + J y over the full system, J as assembled (the linear residual of
+ * the Newton equation J y = -R, up to its sign). */
+static void linear_residual(og_sim *s) {
+  const double *jv = s->o.schur ? s->J.val : s->Ja;
+  for (int i = 0; i < s->nb; ++i) {
+    double a0 = s->R[2 * i], a1 = s->R[2 * i + 1];
+    for (int e = s->J.rowptr[i]; e < s->J.rowptr[i + 1]; ++e) {
+      const double *b = jv + 4 * (size_t)e;
+      int j = s->J.col[e];
+      a0 += b[0] * s->y[2 * j] + b[1] * s->y[2 * j + 1];
+      a1 += b[2] * s->y[2 * j] + b[3] * s->y[2 * j + 1];
+    }
+    s->lq[2 * i] = a0; s->lq[2 * i + 1] = a1;
+  }
+}
+
 /* One linear solve of Algorithm 1 at the assembled iterate, and the update
  * x <- x + y with the saturation change limited to +-ds_max and sw kept in
- * [0, 1]. */
+ * [0, 1].  When FGMRES does not reach its tolerance no update is made (the
+ * state and the Newton counters stay as they were) and OG_ELINEAR is
+ * returned. */
 int oracle_solve_step(void *h, og_stats *st) {
   og_sim *s = (og_sim *)h;
   double eta = forcing(s, s->norms[0]);
+  int lin = s->o.eta_mode == 1 || s->o.eta_mode == 2;
+  if (lin && !s->o.schur) {
+    if (!s->Ja) s->Ja = (double *)zalloc(4 * (size_t)s->J.nnz, sizeof(double));
+    memcpy(s->Ja, s->J.val, sizeof(double) * 4 * (size_t)s->J.nnz);
+  }
   if (s->o.schur) schur_reduce(s);
   og_bsr *A = s->o.schur ? &s->K : &s->J;
   decouple(s);
@@ -1852,7 +1917,17 @@ int oracle_solve_step(void *h, og_stats *st) {
   int rc = fgmres(n2, op_bsr, A, s->o.precond ? op_cpr : NULL, &c, s->bh, ys,
                   s->o.gmres_restart, s->o.gmres_maxit, eta, s->o.reorth, &it, &rr);
   free(c.r1); free(c.z1); free(c.rp); free(c.xp);
+  if (st) {
+    st->linear_iters = it; st->lin_relres = rr; st->eta = eta;
+    st->amg_levels = s->amg.nlev; st->converged = rc == 0;
+  }
+  if (rc != 0) return OG_ELINEAR;
   if (s->o.schur) schur_back(s);
+  if (lin) {
+    if (!s->lq) s->lq = (double *)zalloc(2 * (size_t)s->nb, sizeof(double));
+    linear_residual(s);
+    s->have_lq = 1;
+  }
   for (int cc = 0; cc < s->nc; ++cc) {
     s->p[cc] += s->y[2 * cc];
     double ds = s->y[2 * cc + 1];
@@ -1865,13 +1940,8 @@ int oracle_solve_step(void *h, og_stats *st) {
   }
   for (int w = 0; w < s->nwells; ++w) s->bhp[w] += s->y[2 * (s->nc + w)];
   s->prev_res = s->norms[0];
-  s->prev_linres = rr * s->norms[0];
   s->newton_iter++;
-  if (st) {
-    st->linear_iters = it; st->lin_relres = rr; st->eta = eta;
-    st->amg_levels = s->amg.nlev; st->converged = rc == 0;
-  }
-  return rc == 0 ? OG_OK : OG_ELINEAR;
+  return OG_OK;
 }
 
 int oracle_get_update(void *h, double *y) {
@@ -1880,9 +1950,6 @@ int oracle_get_update(void *h, double *y) {
   return 0;
 }
 
-/* One backward-Euler timestep by Algorithm 1: assemble; stop when
- * ||R~|| <= tol ||R~_0|| or ||R~||_inf <= atol; otherwise solve and update.
- * On failure the state of the old time level is restored. */
 /* Well controls (the examples' wells have rate targets and BHP limits): a
  * timestep starts with every well on its own control; after a Newton update
  * an injector whose BHP exceeds its limit, or an oil-rate producer whose BHP
@@ -1902,6 +1969,11 @@ static int switch_controls(og_sim *s) {
   return n;
 }
 
+/* One backward-Euler timestep by Algorithm 1: assemble; stop when
+ * ||R~|| <= tol ||R~_0|| or ||R~||_inf <= atol; otherwise solve and update.
+ * On failure the state of the old time level is restored: OG_ENEWTON when
+ * Newton did not converge, OG_ELINEAR when a linear solve did not reach its
+ * forcing term. */
 int oracle_advance(void *h, double dt, og_stats *st) {
   og_sim *s = (og_sim *)h;
   for (int w = 0; w < s->nwells; ++w) {
@@ -1910,8 +1982,8 @@ int oracle_advance(void *h, double dt, og_stats *st) {
   }
   save_old(s);
   s->newton_iter = 0;
-  s->prev_res = 0.0; s->prev_linres = 0.0;
-  int lin = 0, conv = 0;
+  s->prev_res = 0.0; s->have_lq = 0;
+  int lin = 0, conv = 0, lin_fail = 0;
   double res0 = 0.0, res = 0.0;
   for (int l = 0; l <= s->o.newton_max; ++l) {
     oracle_assemble(h, dt);
@@ -1920,7 +1992,7 @@ int oracle_advance(void *h, double dt, og_stats *st) {
     if (res <= s->o.newton_tol * res0 || s->norms[1] <= s->o.newton_atol) { conv = 1; break; }
     if (l == s->o.newton_max) break;
     og_stats ls; memset(&ls, 0, sizeof(ls));
-    oracle_solve_step(h, &ls);
+    if (oracle_solve_step(h, &ls) != OG_OK) { lin += ls.linear_iters; lin_fail = 1; break; }
     lin += ls.linear_iters;
     switch_controls(s);
   }
@@ -1932,7 +2004,7 @@ int oracle_advance(void *h, double dt, og_stats *st) {
     memcpy(s->p, s->pn, sizeof(double) * (size_t)s->nc);
     memcpy(s->sw, s->swn, sizeof(double) * (size_t)s->nc);
     memcpy(s->bhp, s->bhpn, sizeof(double) * (size_t)s->nwells);
-    return OG_ENEWTON;
+    return lin_fail ? OG_ELINEAR : OG_ENEWTON;
   }
   return OG_OK;
 }
@@ -1955,7 +2027,7 @@ int oracle_run(void *h, double t_end, double dt0, double dt_max, double dt_min,
     og_stats a;
     memset(&a, 0, sizeof(a));
     int rc1 = oracle_advance(h, hstep, &a);
-    if (rc1 == OG_ENEWTON) {
+    if (rc1 == OG_ENEWTON || rc1 == OG_ELINEAR) {
       r.cuts += 1;
       dt = 0.5 * hstep;
       if (dt < dt_min) { rc = OG_ENEWTON; break; }

@@ -92,13 +92,16 @@ int  oracle_get_state(void *h, double *p, double *sw, double *bhp);
 int  oracle_assemble(void *h, double dt);
 int  oracle_get_jacobian(void *h, int32_t *rowptr, int32_t *col, double *val, double *res);
 int  oracle_get_norms(void *h, double *out8);
+/* one linear solve and update; -4 (no update made) when FGMRES does not
+ * reach the forcing term */
 int  oracle_solve_step(void *h, og_stats *st);
+/* one timestep; -5 (Newton) or -4 (a linear solve) with the old state back */
 int  oracle_advance(void *h, double dt, og_stats *st);
 /* A simulation period [0, t_end] by timesteps of oracle_advance: dt0 first;
  * after a converged step the next is min(2 h, dt_max) (h the step taken);
- * a step whose Newton iteration fails is retried at h / 2 (a cut), and the
- * run stops with OG_ENEWTON once that would fall below dt_min or after
- * max_steps accepted steps; the last step ends at t_end. */
+ * a step whose Newton iteration or linear solve fails is retried at h / 2 (a
+ * cut), and the run stops with OG_ENEWTON once that would fall below dt_min
+ * or after max_steps accepted steps; the last step ends at t_end. */
 typedef struct {
   int32_t steps, cuts, newton_iters, linear_iters;
   double t;                 /* time reached (s) */
@@ -119,6 +122,11 @@ int  oracle_greedy_colour(int32_t n, const int32_t *rowptr, const int32_t *col,
 int  oracle_ilu0_solve(int32_t n, const int32_t *rowptr, const int32_t *col,
                        const double *val, const int32_t *colour,
                        const double *b, double *x);
+/* strength graph (max(|a_ij|, |a_ji|) >= theta sqrt(|a_ii a_jj|)) of a CSR
+ * matrix with sorted rows and its MIS(2): state[i] = 2 for a root, 0
+ * otherwise; returns the number of roots */
+int  oracle_mis2(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                 double theta, int32_t *state);
 int  oracle_amg_create(int32_t n, const int32_t *rowptr, const int32_t *col,
                        const double *val, double theta, int32_t coarse_max,
                        int32_t max_levels, void **out);

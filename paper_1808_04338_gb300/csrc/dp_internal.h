@@ -172,6 +172,7 @@ int ilu_factor(Sim *s);
 int ilu_apply(Sim *s, const double *r, double *z);
 int bsr_spmv(Sim *s, const double *x, double *y);                 // y = A x
 int bsr_residual(Sim *s, const double *b, const double *x, double *r);  // r = b - A x
+int lin_residual(Sim *s);          // s->lq = R + A y, A the assembled Jacobian
 int vcycle(Sim *s, int level, const double *b, double *x);
 int coarse_factor(Sim *s);
 int cpr_apply(Sim *s, const double *r, double *z);
@@ -235,7 +236,7 @@ struct Sim {
   double dt = 1.0, inv_dt = 1.0;
   double *norm_part = nullptr;                       // reduction partials
   double *norm_w = nullptr;                          // 1/(rho_ref phi_ref V), 2 x nc
-  double *norm_out = nullptr;                        // 8 doubles
+  double *norm_out = nullptr;                        // 10 doubles (phys_norms)
   double *h_norms = nullptr;                         // pinned host copy
   int norm_blocks = 0;
   bool assembled = false, decoupled = false;
@@ -320,13 +321,19 @@ struct Sim {
   std::vector<long long> graph_launches;
   cudaStream_t cap_stream = nullptr;
   // Newton bookkeeping
-  double prev_res = 0.0, prev_linres = 0.0;
+  double prev_res = 0.0;
   int newton_iter = 0;
-  double last_norms[8] = {0};
+  double last_norms[10] = {0};
+  // forcing terms 1-2 (Section 3.1): the linear residual lq = R + A y of the
+  // last solve (A as assembled), valid from the second Newton iteration on
+  double *lq = nullptr;
+  bool have_lq = false;
   dp_stats last{};
 
+  // Records a failure's message; a CUDA failure also marks the realisation
+  // unusable (every later call returns DP_ECUDA), other codes do not.
   void fail(int code, const std::string &m) {
-    if (err.code == DP_OK) { err.code = code; err.msg = m; }
+    if (code == DP_ECUDA && err.code != DP_ECUDA) { err.code = code; err.msg = m; }
     last_error = m;
   }
 };

@@ -98,6 +98,38 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc, int 
   }
 }
 
+// lq = R + A y over every block row of the Jacobian as assembled (natural
+// order): the linear residual of the Newton equation A y = -R, whose scaled
+// norms the forcing terms 1 and 2 of Section 3.1 take.  Two lanes per block
+// row, one per component (as in k_bsr_spmv), writing natural order directly.
+__global__ void __launch_bounds__(kBlock) k_lin_residual(int n, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         const double *__restrict__ val,
+                                                         const double *__restrict__ R,
+                                                         const double *__restrict__ y,
+                                                         double *__restrict__ lq) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(t >> 1), comp = (int)(t & 1);
+  if (i >= n) return;
+  const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
+  const double2 *y2 = reinterpret_cast<const double2 *>(y);
+  double a = R[2 * (size_t)i + comp];
+  for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) {
+    double2 b = __ldg(v2 + 2 * (size_t)e);
+    double2 x = __ldg(y2 + __ldg(col + e));
+    a = fma(b.x, x.x, fma(b.y, x.y, a));
+  }
+  lq[2 * (size_t)i + comp] = a;
+}
+
+int lin_residual(Sim *s) {
+  const Bsr &A = s->A;
+  DP_LAUNCH(s, k_lin_residual, nblk(2LL * A.n), kBlock, 0, A.n, A.rowptr, A.col, A.val, s->R,
+            s->y, s->lq);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
 // Pressure component of b - A x: rp_i = b_{i,0} - sum_j (a00 x_j0 + a01 x_j1),
 // from the contiguous copies of the (0,0) and (0,1) entries that the
 // decoupling writes (the 2x2 blocks would be read half-used).

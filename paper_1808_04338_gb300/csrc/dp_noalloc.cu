@@ -27,6 +27,9 @@ constexpr int kMaxDevices = 64;
 // Partial sums of the blocks: [block][0] sum of squares, [block][1] maximum.
 static __device__ __align__(256) double g_partials[kMaxBlocks * 2];
 
+// Device address of g_partials per device, looked up on the first call with
+// that device current and kept until the process exits (a device reset
+// invalidates it; the header tells callers not to call after one).
 std::mutex g_lock;
 double *g_addr[kMaxDevices] = {nullptr};
 

@@ -720,13 +720,17 @@ int phys_norm_weights(Sim *s) {
   return DP_OK;
 }
 
+// With lq (the linear residual of the last solve; null when the forcing term
+// does not use it) also the squared scaled norms of lq and of R - lq, in the
+// scaling of the residual norm.
 __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *__restrict__ w,
                                                        const double *R,
                                                        const double *Macc, const double *Mn,
                                                        const int *well_kind,
                                                        const double *well_target, double dt,
+                                                       const double *__restrict__ lq,
                                                        double *part) {
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};  // s2, max, sro, srw, dmo, dmw, unused
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // s2, max, sro, srw, dmo, dmw, |lq|^2, |R-lq|^2
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.nb; r += gridDim.x * blockDim.x) {
     if (r < P.nc) {
 #pragma unroll
@@ -734,6 +738,12 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *__r
         double x = (R[2 * r + al] * dt) * w[2 * r + al];
         v[0] += x * x;
         v[1] = fmax(v[1], fabs(x));
+        if (lq) {
+          double a = (lq[2 * r + al] * dt) * w[2 * r + al];
+          double d = ((R[2 * r + al] - lq[2 * r + al]) * dt) * w[2 * r + al];
+          v[6] += a * a;
+          v[7] += d * d;
+        }
       }
       v[2] += R[2 * r];
       v[3] += R[2 * r + 1];
@@ -745,19 +755,24 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *__r
       double x = R[2 * r] / sc;
       v[0] += x * x;
       v[1] = fmax(v[1], fabs(x));
+      if (lq) {
+        double a = lq[2 * r] / sc, d = (R[2 * r] - lq[2 * r]) / sc;
+        v[6] += a * a;
+        v[7] += d * d;
+      }
     }
   }
-  __shared__ double sh[kBlock / 32][7];
+  __shared__ double sh[kBlock / 32][8];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < 8; ++k) {
     double t = k == 1 ? warp_max(v[k]) : warp_sum(v[k]);
     if (lane == 0) sh[wid][k] = t;
   }
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < 8) {
     int k = threadIdx.x;
-    double t = k == 1 ? 0.0 : 0.0;
+    double t = 0.0;
     for (int q = 0; q < kBlock / 32; ++q) t = k == 1 ? fmax(t, sh[q][k]) : t + sh[q][k];
     part[blockIdx.x * 8 + k] = t;
   }
@@ -771,9 +786,12 @@ __global__ void __launch_bounds__(kBlock) k_norms_final(Phys P, const double *ph
                                                         const double *perf_wi, int np,
                                                         const int *well_kind, const double *part,
                                                         int nparts, double *out) {
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+  double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
     for (int k = 0; k < 6; ++k) v[k] = k == 1 ? fmax(v[k], part[b * 8 + k]) : v[k] + part[b * 8 + k];
+    v[8] += part[b * 8 + 6];
+    v[9] += part[b * 8 + 7];
+  }
   for (int t = threadIdx.x; t < np; t += blockDim.x) {
     int c = perf_cell[t], w = perf_well[t];
     Props q;
@@ -783,27 +801,30 @@ __global__ void __launch_bounds__(kBlock) k_norms_final(Phys P, const double *ph
     v[6] += Q[0];
     v[7] += Q[1];
   }
-  __shared__ double sh[kBlock / 32][8];
+  __shared__ double sh[kBlock / 32][10];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < 10; ++k) {
     double t = k == 1 ? warp_max(v[k]) : warp_sum(v[k]);
     if (lane == 0) sh[wid][k] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double o[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int q = 0; q < kBlock / 32; ++q)
-      for (int k = 0; k < 8; ++k) o[k] = k == 1 ? fmax(o[k], sh[q][k]) : o[k] + sh[q][k];
+      for (int k = 0; k < 10; ++k) o[k] = k == 1 ? fmax(o[k], sh[q][k]) : o[k] + sh[q][k];
     out[0] = sqrt(o[0]);
     for (int k = 1; k < 8; ++k) out[k] = o[k];
+    out[8] = sqrt(o[8]);   // ||R~(lq)||_2
+    out[9] = sqrt(o[9]);   // ||R~(R - lq)||_2
   }
 }
 
 int phys_norms(Sim *s) {
   Phys &P = s->ph;
+  bool lin = s->have_lq && (s->opt.eta_mode == 1 || s->opt.eta_mode == 2);
   DP_LAUNCH(s, k_norms_part, s->norm_blocks, kBlock, 0, P, s->norm_w, s->R, s->Macc,
-            s->Mn, s->well_kind, s->well_target, s->dt, s->norm_part);
+            s->Mn, s->well_kind, s->well_target, s->dt, lin ? s->lq : nullptr, s->norm_part);
   DP_LAUNCH(s, k_norms_final, 1, kBlock, 0, P, s->phi_f, s->phi_m, s->p, s->sw, s->bhp, s->perf_cell,
             s->perf_well, s->perf_wi, s->nperf, s->well_kind, s->norm_part, s->norm_blocks,
             s->norm_out);

@@ -92,21 +92,25 @@ static int check(Sim *s) {
 
 // Forcing term of Algorithm 1 (Section 3.1): fixed, or one of the three
 // formulas clipped to [eta_min, eta_max]; eta_max on the first iteration.
+// With b = -R and the previous solve's linear residual r^{l-1} = -lq
+// (lq = R + A y), in the scaled norm of ||b||: 1 takes ||b(x^l) - r^{l-1}||
+// = ||R~(R - lq)|| (last_norms[9]), 2 takes ||r^{l-1}|| = ||R~(lq)||
+// (last_norms[8]), 3 the ratio of residual norms alone.
 static double forcing(Sim *s, double res) {
   const dp_options &o = s->opt;
   if (o.eta_mode == 0) return o.eta_fixed;
   if (s->newton_iter == 0 || s->prev_res <= 0.0) return o.eta_max;
   double eta;
-  if (o.eta_mode == 1) eta = std::fabs(res - s->prev_linres) / s->prev_res;
-  else if (o.eta_mode == 2) eta = (res - s->prev_linres) / s->prev_res;
+  if (o.eta_mode == 1) eta = s->last_norms[9] / s->prev_res;
+  else if (o.eta_mode == 2) eta = (res - s->last_norms[8]) / s->prev_res;
   else eta = o.eta_gamma * std::pow(res / s->prev_res, o.eta_beta);
   return std::min(std::max(eta, o.eta_min), o.eta_max);
 }
 
 static int read_norms(Sim *s) {
-  DP_CUDA(s, cudaMemcpyAsync(s->h_norms, s->norm_out, 64, cudaMemcpyDeviceToHost, s->stream));
+  DP_CUDA(s, cudaMemcpyAsync(s->h_norms, s->norm_out, 80, cudaMemcpyDeviceToHost, s->stream));
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
-  std::memcpy(s->last_norms, s->h_norms, 64);
+  std::memcpy(s->last_norms, s->h_norms, 80);
   return DP_OK;
 }
 
@@ -201,7 +205,7 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
       !s->counter || !s->omega || !s->rho_bits)
     return fail(DP_ENOMEM);
   if (cudaMallocHost(&s->h_counter, 64) != cudaSuccess ||
-      cudaMallocHost(&s->h_res, 64) != cudaSuccess || cudaMallocHost(&s->h_norms, 64) != cudaSuccess)
+      cudaMallocHost(&s->h_res, 64) != cudaSuccess || cudaMallocHost(&s->h_norms, 128) != cudaSuccess)
     return fail(DP_ECUDA);
   cudaStream_t st = s->stream;
   if (cudaMemcpyAsync(s->kf, rock->kf, nl8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -242,7 +246,7 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   s->Macc = (double *)dalloc(s, 2 * nc8);
   s->norm_blocks = std::min(nblk(P.nb), 1024);
   s->norm_part = (double *)dalloc(s, (size_t)s->norm_blocks * 64);
-  s->norm_out = (double *)dalloc(s, 64);
+  s->norm_out = (double *)dalloc(s, 80);
   s->norm_w = (double *)dalloc(s, 2 * nc8);
   if (!s->p || !s->sw || !s->bhp || !s->pn || !s->swn || !s->bhpn || !s->Mn || !s->R || !s->bh ||
       !s->y || !s->norm_part || !s->norm_out || !s->norm_w || !s->pr || !s->Macc)
@@ -300,7 +304,7 @@ static int copy_state(dp_sim *s, const double *p, const double *sw, const double
 static void new_timestep(Sim *s) {
   s->newton_iter = 0;
   s->prev_res = 0.0;
-  s->prev_linres = 0.0;
+  s->have_lq = false;
 }
 
 extern "C" int sim_set_state(dp_sim *s, const double *p, const double *sw, const double *bhp) {
@@ -404,26 +408,40 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
     Range range("fgmres");
     rc = fgmres(s, eta, &it, &rr);
   }
-  if (rc != DP_OK && rc != DP_ELINEAR) return rc;
-  if (s->opt.schur) DP_TRY(phys_schur_back(s));
-  DP_TRY(phys_update(s));
+  if (rc == DP_OK) {   // a failed linear solve makes no update
+    if (s->opt.schur) rc = phys_schur_back(s);
+    bool lin = s->opt.eta_mode == 1 || s->opt.eta_mode == 2;
+    if (rc == DP_OK && lin) {
+      if (!s->lq) s->lq = (double *)dalloc(s, (size_t)s->ph.nb * 16);
+      rc = s->lq ? lin_residual(s) : DP_ENOMEM;
+      if (rc == DP_ENOMEM) s->fail(DP_ENOMEM, "allocation of the linear residual failed");
+    }
+    if (rc == DP_OK) rc = phys_update(s);
+  }
   cudaEventRecord(e2, s->stream);
-  DP_CUDA(s, cudaStreamSynchronize(s->stream));
+  cudaError_t se = cudaStreamSynchronize(s->stream);
   float ms1 = 0.f, ms2 = 0.f;
   cudaEventElapsedTime(&ms1, e0, e1);
   cudaEventElapsedTime(&ms2, e1, e2);
   cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
-  s->prev_res = s->last_norms[0];
-  s->prev_linres = rr * s->last_norms[0];
-  s->newton_iter++;
+  DP_CUDA(s, se);
+  if (rc != DP_OK && rc != DP_ELINEAR) return rc;
   s->assembled = false;
   dp_stats &L = s->last;
   L.linear_iters = it; L.lin_relres = rr; L.eta = eta;
   L.amg_levels = (int)s->lev.size(); L.converged = rc == DP_OK;
   L.ms_setup = ms1; L.ms_solve = ms2;
   if (st) *st = L;
+  if (rc == DP_ELINEAR) {
+    s->fail(DP_ELINEAR, "FGMRES did not reach the forcing term; no update was made");
+    DP_TRY(check(s));
+    return DP_ELINEAR;
+  }
+  s->prev_res = s->last_norms[0];
+  s->have_lq = s->opt.eta_mode == 1 || s->opt.eta_mode == 2;
+  s->newton_iter++;
   DP_TRY(check(s));
-  return rc;
+  return DP_OK;
 }
 
 extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
@@ -433,7 +451,7 @@ extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
   DP_TRY(phys_save_old(s));
   new_timestep(s);
   int lin = 0;
-  bool conv = false;
+  bool conv = false, lin_fail = false;
   double res0 = 0.0, res = 0.0, ms_setup = 0.0, ms_solve = 0.0;
   for (int l = 0; l <= s->opt.newton_max; ++l) {
     DP_TRY(sim_assemble(s, dt));
@@ -442,12 +460,13 @@ extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
     if (l == 0) res0 = res;
     if (res <= s->opt.newton_tol * res0 || s->last_norms[1] <= s->opt.newton_atol) { conv = true; break; }
     if (l == s->opt.newton_max) break;
-    dp_stats ls;
+    dp_stats ls{};
     int rc = sim_solve_step(s, &ls);
     if (rc != DP_OK && rc != DP_ELINEAR) return rc;
     lin += ls.linear_iters;
     ms_setup += ls.ms_setup;
     ms_solve += ls.ms_solve;
+    if (rc == DP_ELINEAR) { lin_fail = true; break; }
     if (s->well_limits) DP_TRY(phys_well_controls(s, false));
   }
   dp_stats &L = s->last;
@@ -463,6 +482,10 @@ extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
       DP_CUDA(s, cudaMemcpyAsync(s->bhp, s->bhpn, (size_t)s->ph.nw * 8, cudaMemcpyDeviceToDevice,
                                  s->stream));
     DP_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (lin_fail) {
+      s->fail(DP_ELINEAR, "a linear solve did not reach its forcing term; the old state is restored");
+      return DP_ELINEAR;
+    }
     s->fail(DP_ENEWTON, "Newton did not converge");
     return DP_ENEWTON;
   }
@@ -482,7 +505,7 @@ extern "C" int sim_run(dp_sim *s, double t_end, double dt0, double dt_max, doubl
     double h = dt < t_end - t ? dt : t_end - t;
     dp_stats a{};
     int rc1 = sim_advance(s, h, &a);
-    if (rc1 == DP_ENEWTON) {   // rolled back by sim_advance: retry at half the step
+    if (rc1 == DP_ENEWTON || rc1 == DP_ELINEAR) {   // rolled back: retry at half the step
       r.cuts += 1;
       dt = 0.5 * h;
       if (dt < dt_min) { rc = DP_ENEWTON; break; }

@@ -39,8 +39,10 @@ def test_noalloc_norms_match_sim_get_norms_twice(make):
         assert rc == 0, msg
         torch.cuda.synchronize()
         got = out.cpu().numpy()
+        # the two paths scale by a division and by a product with a
+        # precomputed reciprocal: entries may differ in the last bit
         np.testing.assert_allclose(got[0], expect[0], rtol=1e-12)
-        assert got[1] == expect[1]
+        np.testing.assert_allclose(got[1], expect[1], rtol=1e-15)
     sim.close()
 
 
