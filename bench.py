@@ -85,6 +85,26 @@ def sweep_bytes(nb, nnzb, c0_rows, c0_nnz):
             "k_gs_c": (pre + post) // 2}
 
 
+def assembly_bytes(nb, nnzb, nc):
+    """Algorithmic bytes of one assembly (k_props then k_assemble), every
+    array read or written once.  k_props: p, s_w and the reference porosity
+    of every cell read, its seven properties (rho_o, rho_w, lambda_o,
+    lambda_w and their derivatives, phi) written: 80 B per cell.
+    k_assemble: per block the column, the transmissibility or well index and
+    the 2x2 FP64 block written (44 B); per cell p, the seven properties and
+    the reference porosity read once, the old masses read and the new ones
+    written (104 B); per block row its row pointer, diagonal position and
+    the two residual entries (24 B)."""
+    return {"k_props": 80 * nc, "k_assemble": 44 * nnzb + 104 * nc + 24 * nb}
+
+
+def state_error(a, b):
+    """Max |dp| / max |p| and max |ds_w| between two states."""
+    import numpy as np
+    return {"dp_rel": float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()),
+            "dsw_abs": float(np.abs(a[1] - b[1]).max())}
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -134,48 +154,56 @@ class Clocks:
                 "samples": len(self.samples)}
 
 
-def oracle_sample(args, budget_s=25.0):
-    """The CPU oracle, as it stands, on a bounded sample of the workload: the
-    same field recipe with nz reduced by --sample-div so that a Newton step
-    fits the time budget; the rate is scaled to the full 8M-unknown problem
-    by the ratio of unknowns."""
-    import numpy as np
-    import dp_inputs as di
+def _oracle_steps(prob, budget_s, max_steps, min_steps=1):
+    """Set up the oracle on `prob` (its first Newton step, which builds the
+    colouring and the AMG hierarchy, untimed), then time whole Newton steps
+    of the first timestep (assembly and solve_step from x^n) until the
+    budget or max_steps is reached.  Returns (oracle sim, step times)."""
     import oracle as O
-    nz = max(1, args.nz // args.sample_div)
-    prob = di.field8m(args.nx, args.ny, nz)
     s = O.OracleSim(prob, O.options("report"))
     s.assemble(prob.dt)
-    s.solve_step()                      # integer set-up on the first Newton step
-    p0, sw0, b0 = prob.p0, prob.sw0, prob.bhp0
+    s.solve_step()
     times = []
     t_start = time.perf_counter()
-    while True:
-        s.set_state(p0, sw0, b0)
+    while len(times) < max_steps:
+        s.set_state(prob.p0, prob.sw0, prob.bhp0)
         t0 = time.perf_counter()
         s.assemble(prob.dt)
         s.solve_step()
         times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > budget_s or len(times) >= 3:
+        if len(times) >= min_steps and time.perf_counter() - t_start > budget_s:
             break
+    return s, times
+
+
+def oracle_sample(args, budget_s=20.0, keep=None):
+    """The CPU oracle, as it stands, on the bench's own workload (the whole
+    grid, no scaling): median time of up to three Newton steps after the
+    untimed set-up step.  `keep` (a list) receives the oracle realisation
+    for the precision-error check."""
+    import dp_inputs as di
+    prob = di.field8m(args.nx, args.ny, args.nz)
+    s, times = _oracle_steps(prob, budget_s, 3)
+    if keep is not None:
+        keep.append(s)
     t = statistics.median(times)
-    scale = (2 * args.nx * args.ny * args.nz) / (2 * args.nx * args.ny * nz)
-    return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one Newton step of the {args.nx}x{args.ny}x{nz} grid "
-                      f"({prob.n_unknowns} unknowns), median of {len(times)}, rate scaled "
-                      f"by the unknown ratio {scale:g} to 8M unknowns; single-threaded C"}
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one Newton step (assembly, decoupling, ILU(0), AMG refresh, FGMRES to the "
+                      f"forcing term) of the whole {args.nx}x{args.ny}x{args.nz} grid "
+                      f"({prob.n_unknowns} unknowns), median of {len(times)} after an untimed "
+                      f"set-up step; single-threaded C, no scaling"}
 
 
 def _oracle_worker(nx, ny, nz, nsteps, barrier, out):
     """One process of the all-core oracle sample: set up, wait for the
-    others, then time nsteps Newton steps of its own copy of the slice."""
+    others, then time nsteps Newton steps of its own copy of the grid."""
     import dp_inputs as di
     import oracle as O
     prob = di.field8m(nx, ny, nz)
     s = O.OracleSim(prob, O.options("report"))
     s.assemble(prob.dt)
     s.solve_step()
-    barrier.wait(timeout=600)
+    barrier.wait(timeout=1200)
     t0 = time.perf_counter()
     for _ in range(nsteps):
         s.set_state(prob.p0, prob.sw0, prob.bhp0)
@@ -184,42 +212,62 @@ def _oracle_worker(nx, ny, nz, nsteps, barrier, out):
     out.put(time.perf_counter() - t0)
 
 
+def _host_mem_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
 def oracle_sample_all_cores(args, nsteps=2):
-    """The same oracle on every host core at once (at most 64): one process
-    per core (started with spawn), each running nsteps Newton steps of its own
-    copy of the slice that oracle_sample times; throughput = steps of all processes /
-    the slowest process's time, scaled to the full problem like
-    oracle_sample.  The oracle itself is single-threaded C, unchanged."""
+    """The same oracle on every host core at once: one process per core
+    (started with spawn), each running nsteps Newton steps of its own copy of
+    the whole grid after its set-up; throughput = steps of all processes /
+    the slowest process's time.  The number of processes is bounded by the
+    host memory available (about 700 bytes per unknown each, half the free
+    memory at most) and by 64; `cores` reports how many ran.  The oracle
+    itself is single-threaded C, unchanged."""
     import multiprocessing as mp
-    cores = min(os.cpu_count() or 1, 64)   # bounded: one process (and one slice copy) a core
-    nz = max(1, args.nz // args.sample_div)
+    unknowns = 4 * args.nx * args.ny * args.nz + 50
+    mem = _host_mem_bytes()
+    cores = min(os.cpu_count() or 1, 64)
+    if mem:
+        cores = max(1, min(cores, int(0.5 * mem // (700 * unknowns))))
     ctx = mp.get_context("spawn")
     barrier, out = ctx.Barrier(cores), ctx.Queue()
-    procs = [ctx.Process(target=_oracle_worker, args=(args.nx, args.ny, nz, nsteps, barrier, out))
+    procs = [ctx.Process(target=_oracle_worker,
+                         args=(args.nx, args.ny, args.nz, nsteps, barrier, out))
              for _ in range(cores)]
     for p in procs:
         p.start()
-    times = [out.get(timeout=900) for _ in procs]
+    times = [out.get(timeout=1800) for _ in procs]
     for p in procs:
         p.join()
-    scale = (2 * args.nx * args.ny * args.nz) / (2 * args.nx * args.ny * nz)
-    return {"value": cores * nsteps / (max(times) * scale), "unit": UNIT, "cores": cores,
-            "kind": "oracle",
-            "sample": f"{cores} processes, each {nsteps} Newton steps of its own "
-                      f"{args.nx}x{args.ny}x{nz} grid after its set-up, started together; "
-                      f"steps of all processes / the slowest process's time, scaled by "
-                      f"{scale:g} to 8M unknowns"}
+    return {"value": cores * nsteps / max(times), "unit": UNIT, "cores": cores,
+            "kind": "oracle", "steps_per_process": nsteps,
+            "sample": f"{cores} processes (of {os.cpu_count()} host cores), each {nsteps} Newton "
+                      f"steps of its own copy of the whole {args.nx}x{args.ny}x{args.nz} grid "
+                      f"after its set-up step, started together; steps of all processes / the "
+                      f"slowest process's time; no scaling"}
 
 
 def run_reference(args):
+    """The reference arm: the oracle on every host core, and on one core,
+    on the bench's own workload.  `steps` and `warmup` report what was
+    timed: Newton steps per process, after one untimed set-up step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # the oracle on every host core (one process per core), and on one core
-    cb = oracle_sample_all_cores(args)
+    nsteps = 2
+    cb = oracle_sample_all_cores(args, nsteps)
     cb["single_core"] = oracle_sample(args)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": args.gpus, "steps": nsteps, "warmup": 1,
+            "steps_requested": args.steps, "warmup_requested": args.warmup,
             "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args), "cpu_baseline": cb,
@@ -308,27 +356,32 @@ def run_ensemble(args):
         st.close()
 
 
-def serve_stream(workers, precision, schur):
+def serve_stream(workers, precision, schur, budget_gb=160, warm=False):
     """One served stream: 512 timestep requests with Poisson arrivals (mean
     200/s) over 128 realisations of about 10k to 1M cells, served by the
-    library's request server under a 160 GB device budget.  Every requested
-    realisation is made resident first by one untimed 1-day request; the
-    stream then arrives in real time.  Latency = result ready - arrival on
-    the server's clock."""
+    library's request server under a device budget of budget_gb.  Cold (the
+    default): nothing is resident when the stream starts, so a realisation's
+    first request includes building it (pattern, AMG set-up), and requests
+    wait for admission and evictions as the budget dictates.  warm: every
+    requested realisation is first made resident by one untimed 1-day
+    request.  The stream arrives in real time; latency = result ready -
+    arrival on the server's clock."""
     import numpy as np
     import torch
     import dp_inputs as di
     from paper_1808_04338_gb300 import dpsim
     members = [di.served_member(r) for r in range(128)]
     arrivals, real, dts = di.request_stream()
-    budget = 160 << 30
+    budget = int(budget_gb) << 30
     srv = dpsim.Server(workers, budget, dpsim.options("report", precision=precision,
                                                       schur=schur))
     ids = [srv.add(p) for p in members]
-    for t in [srv.submit(ids[r], di.DAY) for r in sorted(set(real.tolist()))]:
-        if srv.wait(t).status != 0:
-            raise RuntimeError("warm-up request failed")
+    if warm:
+        for t in [srv.submit(ids[r], di.DAY) for r in sorted(set(real.tolist()))]:
+            if srv.wait(t).status != 0:
+                raise RuntimeError("warm-up request failed")
     torch.cuda.synchronize()
+    e0 = srv.info().evictions
     l0 = srv.info().launches
     t0 = time.perf_counter()
     tickets = []
@@ -343,29 +396,37 @@ def serve_stream(workers, precision, schur):
     lat = np.array([x.t_done_ms - x.t_submit_ms for x in res])
     span = (max(x.t_done_ms for x in res) - min(x.t_submit_ms for x in res)) / 1000.0
     newton = sum(x.stats.newton_iters for x in res)
+    loads = sum(x.loaded for x in res)
     return {"solves_per_s": len(res) / span, "newton_solves_per_s": newton / span,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "makespan_s": span, "failed": int(sum(x.status != 0 for x in res)),
-            "newton_per_request": newton / len(res),
-            "resident_gb": info.peak_resident_bytes / 1e9, "evictions": info.evictions,
-            "launches": info.launches - l0}
+            "newton_per_request": newton / len(res), "workers": workers,
+            "precision": precision, "budget_gb": budget_gb, "warm": warm,
+            "requests_with_build": int(loads),
+            "resident_gb": info.peak_resident_bytes / 1e9,
+            "evictions": int(info.evictions - e0), "launches": info.launches - l0}
+
+
+def serve_variants(workers, precision, schur):
+    """The served stream cold at 160 GB (the headline), warm at 160 GB, cold
+    under a 40 GB budget that forces evictions, and the plain FP64 path cold
+    at 160 GB with the same number of workers."""
+    return {"cold": serve_stream(workers, precision, schur),
+            "warm": serve_stream(workers, precision, schur, warm=True),
+            "evicting_40gb": serve_stream(workers, precision, schur, budget_gb=40),
+            "fp64_same_workers": serve_stream(workers, 0, schur)}
 
 
 def run_serve(args):
-    """The served stream (serve_stream), run twice: `--threads` workers with
-    the FP32 preconditioner, and one worker with the plain FP64 path."""
+    """The served stream (serve_variants) with `--threads` workers."""
     import torch
     import dp_inputs as di
     members = [di.served_member(r) for r in range(128)]
-
-    def once(workers, precision):
-        return serve_stream(workers, precision, args.schur)
-
     clk = Clocks(torch.cuda.current_device())
     clk.__enter__()
-    served = once(args.threads, args.precision)
+    v = serve_variants(args.threads, args.precision, args.schur)
     clk.__exit__()
-    plain = once(1, 0)
+    served = v["cold"]
     cells = sum(p.n_cells for p in members)
     line = {"metric": "served timestep-solve stream: p50/p99 latency and throughput",
             "value": served["solves_per_s"], "unit": "timestep solves/s", "n_gpus": 1,
@@ -373,11 +434,10 @@ def run_serve(args):
             "dtype": "f64" if args.precision == 0 else "f64 (f32 preconditioner)",
             "data": "synthetic",
             "config": {"workload": f"512 requests, Poisson 200/s, 128 realisations "
-                                   f"({cells} cells), dt 1-10 days, budget 160 GB",
+                                   f"({cells} cells), dt 1-10 days, budget 160 GB, cold start",
                        "workers": args.threads, "precision": args.precision,
                        "schur": args.schur},
-            "served": served,
-            "plain_fp64_one_worker": plain,
+            "variants": v,
             "gpu_launches": served["launches"], "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -453,7 +513,6 @@ def main():
                     help="0: FP64 everywhere; 1: FP32 ILU(0)/AMG inside FP64 FGMRES")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-schur-path", action="store_true")
-    ap.add_argument("--sample-div", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true",
@@ -584,6 +643,8 @@ def main():
                                 != l.split("-> ")[1].split(" ")[0])}
     clk = Clocks(local)
     main = measure(sim, opts, args.steps, args.warmup, clk)
+    timestep(sim, opts)
+    states = {"headline": sim.get_state()}   # the converged first timestep of each variant
     ms, n_solves, n_its, launches = main["ms"], main["solves"], main["its"], main["launches"]
     all_solves = main["all_solves"]
     med, p90 = main["median"], main["p90"]
@@ -608,6 +669,18 @@ def main():
         c0_rows, c0_nnz = int(c0.sum()), int(lens[c0].sum())
     else:
         c0_rows, c0_nnz = 0, 0
+    # the assembly kernels the same way (one launch each per Newton iteration)
+    assembly = {}
+    for name, nbytes in assembly_bytes(sim.nb, sim.nnzb, sim.nc).items():
+        sim.time_kernel(name)
+        sim.kernel_timing(reset=True)
+        timestep(sim, opts)
+        t_ms, t_n = sim.kernel_timing(reset=True)
+        sim.time_kernel(None)
+        if t_n:
+            assembly[name] = {"achieved_gbs": nbytes * t_n / (t_ms / 1000.0) / 1e9,
+                              "bytes_per_launch": nbytes, "ms_per_launch": t_ms / t_n,
+                              "launches": t_n}
     for name, nbytes in sweep_bytes(sim.snb, sim.snnzb, c0_rows, c0_nnz).items():
         sim.time_kernel(name)
         sim.kernel_timing(reset=True)
@@ -649,6 +722,8 @@ def main():
         with torch.cuda.stream(stream):
             simsch = dpsim.Sim(prob, osch, stream=stream)
         r = measure(simsch, osch, max(2, args.steps // 2), args.warmup)
+        timestep(simsch, osch)
+        states["schur_path"] = simsch.get_state()
         simsch.close()
         schur = {"value": r["all_solves"] / (r["ms"] / 1000.0), "unit": UNIT,
                  "solve_ms_median": r["median"], "solve_ms_p90": r["p90"],
@@ -664,6 +739,8 @@ def main():
         with torch.cuda.stream(stream):
             sim64 = dpsim.Sim(prob, o64, stream=stream)
         r = measure(sim64, o64, max(2, args.steps // 2), args.warmup)
+        timestep(sim64, o64)
+        states["fp64_path"] = sim64.get_state()
         sim64.close()
         fp64 = {"value": r["all_solves"] / (r["ms"] / 1000.0), "unit": UNIT,
                 "solve_ms_median": r["median"], "solve_ms_p90": r["p90"],
@@ -676,12 +753,37 @@ def main():
         peak = peaks.get("hbm_gbs", 6800.0)
         ach = spmv_bytes(sim.snb, sim.snnzb) / (k_ms / max(k_n, 1) / 1000.0) / 1e9 if k_n else None
         cpu = None
+        errors = None
         if not args.no_cpu_baseline:
+            keep = []
             try:
-                cpu = oracle_sample(args)
+                cpu = oracle_sample(args, keep=keep)
             except Exception as e:  # report, do not fail the bench
                 cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                        "sample": f"failed: {e}"}
+            # each variant's converged first timestep against the FP64 oracle: the
+            # oracle's scaled residual there relative to its residual at x^n (the
+            # Newton tolerance is 1e-6), its mass balance, and the state's
+            # distance from the plain FP64 GPU path's
+            if keep:
+                o = keep[0]
+                o.set_state(prob.p0, prob.sw0, prob.bhp0)
+                o.assemble(prob.dt)
+                r0 = o.norms()[0]
+                errors = {"newton_tol": opts.newton_tol}
+                for k, x in states.items():
+                    o.set_iterate(*x)
+                    o.assemble(prob.dt)
+                    nr = o.norms()
+                    e = {"oracle_residual_ratio": float(nr[0] / r0),
+                         "oracle_mass_balance_rel": float(max(
+                             abs(nr[4 + a] - nr[6 + a] * prob.dt) /
+                             max(abs(nr[4 + a]), abs(nr[6 + a] * prob.dt)) for a in range(2)))}
+                    if k != "fp64_path" and "fp64_path" in states:
+                        e["vs_fp64_path"] = state_error(x, states["fp64_path"])
+                    errors[k] = e
+                keep.clear()
+                del o
             try:
                 cpu["all_cores"] = oracle_sample_all_cores(args)
             except Exception as e:
@@ -703,6 +805,8 @@ def main():
                          "avg_launch_ms": (k_ms / k_n) if k_n else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
             "sweeps": {k: dict(v, frac=v["achieved_gbs"] / peak) for k, v in sweeps.items()},
+            "assembly": {k: dict(v, frac=v["achieved_gbs"] / peak) for k, v in assembly.items()},
+            "errors_vs_oracle": errors,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_all / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state},
@@ -719,12 +823,19 @@ def main():
         if not args.no_serve and world == 1:
             torch.cuda.synchronize()
             try:
-                sv = serve_stream(args.threads, args.precision, args.schur)
-                line["served"] = {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
-                                  "solves_per_s": sv["solves_per_s"],
-                                  "workload": "512 timestep requests, Poisson 200/s, 128 "
-                                              "realisations of 10k-1M cells, 16 workers",
-                                  "failed": sv["failed"], "gpu_launches": sv["launches"]}
+                v = serve_variants(args.threads, args.precision, args.schur)
+                sv = v["cold"]
+                keys = ("p50_ms", "p99_ms", "solves_per_s", "evictions", "requests_with_build",
+                        "failed", "workers", "precision", "budget_gb")
+                line["served"] = dict(
+                    {k: sv[k] for k in keys},
+                    workload=f"512 timestep requests, Poisson 200/s, 128 realisations of "
+                             f"10k-1M cells, {args.threads} workers, cold start (first "
+                             f"request of a realisation builds it)",
+                    gpu_launches=sv["launches"],
+                    warm={k: v["warm"][k] for k in keys},
+                    evicting_40gb={k: v["evicting_40gb"][k] for k in keys},
+                    fp64_same_workers={k: v["fp64_same_workers"][k] for k in keys})
             except Exception as e:  # report, do not fail the bench
                 line["served"] = {"p50_ms": None, "p99_ms": None, "error": str(e)}
         print(json.dumps(line), flush=True)

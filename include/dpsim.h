@@ -32,7 +32,7 @@
  *     return host results synchronise that stream before returning.
  *   - Return value: DP_OK (0) or a negative DP_E* code; sim_last_error()
  *     gives a message.  A failed call leaves the dp_sim usable unless it
- *     returned DP_ECUDA.
+ *     returned DP_ECUDA or DP_ENOMEM.
  */
 #ifndef DPSIM_H
 #define DPSIM_H
@@ -45,7 +45,8 @@ extern "C" {
 
 #define DP_OK 0
 #define DP_EINVAL (-1)   /* bad argument or size */
-#define DP_ENOMEM (-2)   /* the allocator returned NULL */
+#define DP_ENOMEM (-2)   /* the allocator returned NULL; the dp_sim must be destroyed
+                            (sim_destroy then returns every block it holds) */
 #define DP_ECUDA (-3)    /* a CUDA call failed; the dp_sim must be destroyed */
 #define DP_ELINEAR (-4)  /* FGMRES did not reach its tolerance */
 #define DP_ENEWTON (-5)  /* Newton did not converge; the old state is restored */

@@ -106,8 +106,12 @@ struct LaunchScope {
   LaunchScope(Sim *s, const char *name);
   ~LaunchScope();
 };
+// After an allocation has failed nothing more is launched for the
+// realisation (its calls return DP_ENOMEM until it is destroyed), so no
+// kernel can be handed a buffer that was never obtained.
 #define DP_LAUNCH(sim, name, grid, block, smem, ...)                    \
   do {                                                                  \
+    if ((sim)->alloc_failed) break;                                     \
     ::dp::LaunchScope ls__((sim), #name);                               \
     name<<<(grid), (block), (smem), (sim)->stream>>>(__VA_ARGS__);      \
   } while (0)
@@ -210,6 +214,7 @@ struct Sim {
   bool own_alloc = true;
   std::vector<std::pair<void *, size_t>> blocks;
   size_t cur_bytes = 0, peak_bytes = 0;   // device bytes held through the allocator
+  bool alloc_failed = false;              // the allocator returned NULL once (sticky)
   Err err;
   Timing timing;
   int64_t launches = 0;

@@ -43,6 +43,9 @@ void *dalloc(Sim *s, size_t bytes) {
     s->blocks.push_back({p, bytes});
     s->cur_bytes += bytes;
     s->peak_bytes = std::max(s->peak_bytes, s->cur_bytes);
+  } else {
+    s->alloc_failed = true;
+    s->last_error = "the device allocator returned NULL";
   }
   return p;
 }
@@ -84,10 +87,18 @@ LaunchScope::~LaunchScope() {
   t.launches += 1;
 }
 
+// A realisation whose allocator failed, or that met a CUDA failure, does no
+// further work.
+static int unusable(Sim *s) {
+  if (s->err.code == DP_ECUDA) return DP_ECUDA;
+  return s->alloc_failed ? DP_ENOMEM : DP_OK;
+}
+
 static int check(Sim *s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { s->fail(DP_ECUDA, cudaGetErrorString(e)); return DP_ECUDA; }
-  return s->err.code == DP_ECUDA ? DP_ECUDA : DP_OK;
+  if (s->err.code == DP_ECUDA) return DP_ECUDA;
+  return s->alloc_failed ? DP_ENOMEM : DP_OK;
 }
 
 // Forcing term of Algorithm 1 (Section 3.1): fixed, or one of the three
@@ -340,6 +351,7 @@ extern "C" int sim_get_state(dp_sim *s, double *p, double *sw, double *bhp) {
 extern "C" int sim_assemble(dp_sim *s, double dt) {
   Range range("assemble");
   if (!s || !(dt > 0.0)) return DP_EINVAL;
+  DP_TRY(unusable(s));
   s->dt = dt;
   s->inv_dt = 1.0 / dt;
   DP_TRY(phys_assemble(s));
@@ -374,6 +386,7 @@ extern "C" int sim_get_norms(dp_sim *s, double *out8) {
 
 extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   if (!s) return DP_EINVAL;
+  DP_TRY(unusable(s));
   if (!s->assembled) { s->fail(DP_EINVAL, "sim_solve_step before sim_assemble"); return DP_EINVAL; }
   DP_TRY(read_norms(s));
   double eta = forcing(s, s->last_norms[0]);
@@ -446,6 +459,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
 
 extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
   if (!s || !(dt > 0.0)) return DP_EINVAL;
+  DP_TRY(unusable(s));
   Range range("timestep");
   if (s->well_limits) DP_TRY(phys_well_controls(s, true));
   DP_TRY(phys_save_old(s));

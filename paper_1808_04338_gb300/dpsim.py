@@ -370,7 +370,11 @@ class TorchAllocator:
 class Sim:
     """One realisation on the GPU.  ``prob`` is a ``dp_inputs.Problem``."""
 
-    def __init__(self, prob, opts: dp_options | None = None, stream=None, use_torch_alloc=True):
+    def __init__(self, prob, opts: dp_options | None = None, stream=None, use_torch_alloc=True,
+                 allocator=None):
+        """allocator: an object with a ``struct`` dp_allocator (default: torch's
+        caching allocator; None with use_torch_alloc False: the library's own).
+        A failed sim_create raises RuntimeError with the code in ``self.create_rc``."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("dpsim needs a CUDA device")
@@ -379,11 +383,15 @@ class Sim:
         self.opts = opts if opts is not None else options("parity")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         g, r, f, W, nw, keep = _inputs(prob)
-        self._alloc = TorchAllocator(torch.cuda.current_device()) if use_torch_alloc else None
+        if allocator is not None:
+            self._alloc = allocator
+        else:
+            self._alloc = TorchAllocator(torch.cuda.current_device()) if use_torch_alloc else None
         h = C.c_void_p()
         rc = L.sim_create(C.byref(g), C.byref(r), C.byref(f), W, nw, C.byref(self.opts),
                           C.byref(self._alloc.struct) if self._alloc else None,
                           C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        self.create_rc = rc
         if rc != 0:
             raise RuntimeError(f"sim_create failed ({rc})")
         self.h = h

@@ -93,3 +93,45 @@ def test_bench_size_decoupling_colours_and_amg_setup_bit_exact():
         np.testing.assert_array_equal(a["agg"], b["agg"])
         np.testing.assert_array_equal(a["colour"], b["colour"])
         assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
+
+
+def test_example3_size_assembly_and_setup_bit_exact():
+    """Section 4, Example 3's size: the bench's field recipe on 500x500x50
+    (25M cells, 50M unknowns, 124.6M blocks: every index of the 4 x 124.6M
+    block values is beyond the range of the 200x200x50 tests), the bench's
+    options.  The Jacobian and residual, the decoupled system, the ILU(0)
+    colouring and every AMG level are the oracle's, bit for bit.  The oracle
+    takes a fixed forcing term (only its set-up is compared); host arrays
+    are held one pair at a time."""
+    from paper_1808_04338_gb300 import dpsim
+    prob = di.field8m(500, 500, 50)
+    g = dpsim.Sim(prob, dpsim.options("report", precision=1))
+    o = O.OracleSim(prob, O.options("report", eta_mode=0, eta_fixed=0.1, gmres_maxit=1))
+    assert g.nb == o.nb == 25000025 and g.nnzb == o.nnzb > 124_000_000
+    g.assemble(prob.dt)
+    o.assemble(prob.dt)
+    rg, cg, vg, resg = g.jacobian()
+    ro, co, vo, reso = o.jacobian()
+    np.testing.assert_array_equal(rg, ro)
+    np.testing.assert_array_equal(cg, co)
+    assert np.array_equal(vg.view(np.uint64), vo.view(np.uint64))
+    assert np.array_equal(resg.view(np.uint64), reso.view(np.uint64))
+    del rg, cg, vg, resg, ro, co, vo, reso
+    g.solve_step()
+    o.solve_step()
+    gv, gr = g.decoupled()
+    ov, orr = o.decoupled()
+    assert np.array_equal(gv.view(np.uint64), ov.view(np.uint64))
+    assert np.array_equal(gr.view(np.uint64), orr.view(np.uint64))
+    del gv, ov, gr, orr
+    (gc, gn), (oc, on) = g.colours(), o.colours()
+    assert gn == on
+    np.testing.assert_array_equal(gc, oc)
+    del gc, oc
+    Lg, Lo = g.amg_levels(), o.amg_levels()
+    assert len(Lg) == len(Lo) > 2
+    for a, b in zip(Lg, Lo):
+        assert (a["n"], a["nnz"], a["nagg"]) == (b["n"], b["nnz"], b["nagg"])
+        for k in ("rowptr", "col", "agg", "colour"):
+            np.testing.assert_array_equal(a[k], b[k])
+        assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))

@@ -432,7 +432,7 @@ def _gpu_python_run(s, t_end, dt0, dt_max, dt_min):
     while t_end - t > 1e-9 * t_end:
         h = min(dt, t_end - t)
         rc, st = s.advance(h)
-        if rc == gpu().DP_ENEWTON:
+        if rc in (gpu().DP_ENEWTON, gpu().DP_ELINEAR):
             cuts += 1
             dt = 0.5 * h
             if dt < dt_min:
