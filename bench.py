@@ -510,9 +510,11 @@ def main():
     ap.add_argument("--ny", type=int, default=200)
     ap.add_argument("--nz", type=int, default=50)
     ap.add_argument("--precision", type=int, default=1,
-                    help="0: FP64 everywhere; 1: FP32 ILU(0)/AMG inside FP64 FGMRES")
+                    help="0: FP64 everywhere; 1: FP32 ILU(0)/AMG inside FP64 FGMRES; 2: as 1 "
+                         "with the AMG levels >= 1 stored in BF16")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-schur-path", action="store_true")
+    ap.add_argument("--no-bf16-path", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true",
@@ -732,6 +734,23 @@ def main():
                  "note": "the same timestep with the matrix cells eliminated exactly before "
                          "the solve (CPR-FPF on the fracture-and-well system, 4M unknowns)"}
 
+    bf16 = None
+    if args.precision == 1 and not args.no_bf16_path:
+        obf = dpsim.options("report", precision=2, cluster_rows=args.cluster_rows,
+                            decouple=args.decouple, eta_mode=args.eta_mode, schur=args.schur)
+        with torch.cuda.stream(stream):
+            simbf = dpsim.Sim(prob, obf, stream=stream)
+        r = measure(simbf, obf, max(2, args.steps // 2), args.warmup)
+        timestep(simbf, obf)
+        states["bf16_coarse_path"] = simbf.get_state()
+        simbf.close()
+        bf16 = {"value": r["all_solves"] / (r["ms"] / 1000.0), "unit": UNIT,
+                "solve_ms_median": r["median"], "solve_ms_p90": r["p90"],
+                "fgmres_iters_per_solve": r["its"] / max(r["solves"], 1),
+                "ms_per_step": r["ms"] / max(2, args.steps // 2),
+                "note": "the same timestep with the AMG levels >= 1 stored in BF16 "
+                        "(precision 2; FP32 arithmetic, FP64 FGMRES)"}
+
     fp64 = None
     if args.precision != 0 and not args.no_fp64_path:
         o64 = dpsim.options("report", precision=0, cluster_rows=args.cluster_rows,
@@ -811,6 +830,7 @@ def main():
             "e2e": {"value": e2e_all / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes_state, "d2h_bytes_per_step": nbytes_state},
             "fp64_path": fp64,
+            "bf16_coarse_path": bf16,
             "schur_path": schur,
             "gpu_launches": launches,
             "autotune": tuned,

@@ -120,7 +120,10 @@ typedef struct {
  * 1 the preconditioner in FP32 inside FP64 FGMRES: ILU(0) factors, AMG
  * levels and the CPR stage residuals (from an FP32 copy of the decoupled
  * operator); the Arnoldi products, restart residuals and orthogonalisation
- * stay FP64.  amg_gs_levels: AMG levels 0..amg_gs_levels-1 are smoothed by
+ * stay FP64; 2 as 1, with the operator, prolongation and restriction values
+ * of the AMG levels >= 1 (not the coarsest, solved by its FP64 inverse)
+ * stored in BF16 and widened to FP32 as they are read (levels run inside the
+ * cluster kernel keep FP32 values).  amg_gs_levels: AMG levels 0..amg_gs_levels-1 are smoothed by
  * multicolour Gauss-Seidel (forward colour order before the coarse
  * correction, reverse after), the coarser ones by one l1-Jacobi sweep
  * before and after, x += (b - A x) / sum_j |a_ij| (Baker, Falgout, Kolev and

@@ -819,7 +819,7 @@ void amg_free(Sim *s) {
                     L.r_val, L.r_valf, L.ap_rowptr, L.ap_col, L.ap_val, L.x, L.b, L.r,
                     L.xf, L.bf, L.rf, L.valf, L.dinv, L.dinvf, L.ap_off, L.ap_pos, L.rap_off,
                     L.cstart_dev, L.ell_col, L.ell_src, L.ell_off, L.ell_K, L.ell_val,
-                    L.ell_valf,
+                    L.ell_valf, L.valh, L.p_valh, L.r_valh,
                     L.rap_pos};
     for (void *p : ptrs) if (p) dfree(s, p);
     if (l > 0) { dfree(s, L.rowptr); dfree(s, L.col); dfree(s, L.val); }

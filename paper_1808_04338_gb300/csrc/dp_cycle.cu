@@ -478,7 +478,7 @@ static int ell_build(Sim *s, Level &L) {
 // after the hierarchy's values and their FP32 copies are refreshed).
 int cluster_refresh(Sim *s) {
   if (s->cl_level < 0) return DP_OK;
-  bool f32 = s->opt.precision == 1;
+  bool f32 = s->opt.precision >= 1;
   for (int l = s->cl_level; l < (int)s->lev.size(); ++l) {
     Level &L = s->lev[l];
     if (!L.ell_src) continue;

@@ -1,5 +1,6 @@
 // Internal declarations of the dpsim CUDA library (not part of the C ABI).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -78,6 +79,9 @@ struct Level {
   int *r_rowptr = nullptr, *r_col = nullptr, *r_src = nullptr;
   double *r_val = nullptr;
   float *r_valf = nullptr;
+  // precision 2, levels >= 1: BF16 copies of the operator, P and R values
+  // (stored in BF16, computed in FP32)
+  __nv_bfloat16 *valh = nullptr, *p_valh = nullptr, *r_valh = nullptr;
   int *ap_rowptr = nullptr, *ap_col = nullptr;
   double *ap_val = nullptr;
   bool l1 = false;                        // l1-Jacobi smoothing (dinv = 1 / sum_j |a_ij|)

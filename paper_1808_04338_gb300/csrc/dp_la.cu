@@ -6,6 +6,7 @@
 #include <string>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "dp_internal.h"
 
@@ -826,7 +827,7 @@ int ilu_setup(Sim *s) {
 }
 
 int ilu_factor(Sim *s) {
-  bool f32 = s->opt.precision == 1;
+  bool f32 = s->opt.precision >= 1;
   for (int c = 0; c < s->ncolour; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
@@ -963,36 +964,45 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// A stored value as the compute type T: the value itself, or (BF16 storage
+// of the coarse levels, precision 2) its FP32 widening.
+template <typename T, typename TV>
+__device__ __forceinline__ T ldv(const TV *p) { return T(__ldg(p)); }
+template <>
+__device__ __forceinline__ float ldv<float, __nv_bfloat16>(const __nv_bfloat16 *p) {
+  return __bfloat162float(__ldg(p));
+}
+
 // Row dot product sum_e val[e] x[col[e]] over the lane's entries e0+lane,
 // e0+lane+G, ...: four independent accumulators keep four loads in flight
 // per lane, so a long row is not one serial chain of dependent loads.
-template <int G, typename T>
+template <int G, typename T, typename TV = T>
 __device__ __forceinline__ T row_dot(int e0, int e1, int lane, const int *__restrict__ col,
-                                     const T *__restrict__ val, const T *__restrict__ x) {
+                                     const TV *__restrict__ val, const T *__restrict__ x) {
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   int e = e0 + lane;
   for (; e + 3 * G < e1; e += 4 * G) {
     int c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
         c3 = __ldg(col + e + 3 * G);
-    T v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G),
-      v3 = __ldg(val + e + 3 * G);
+    T v0 = ldv<T>(val + e), v1 = ldv<T>(val + e + G), v2 = ldv<T>(val + e + 2 * G),
+      v3 = ldv<T>(val + e + 3 * G);
     s0 = fma(v0, x[c0], s0);
     s1 = fma(v1, x[c1], s1);
     s2 = fma(v2, x[c2], s2);
     s3 = fma(v3, x[c3], s3);
   }
-  for (; e < e1; e += G) s0 = fma(__ldg(val + e), x[__ldg(col + e)], s0);
+  for (; e < e1; e += G) s0 = fma(ldv<T>(val + e), x[__ldg(col + e)], s0);
   return (s0 + s1) + (s2 + s3);
 }
 
 // One colour of Gauss-Seidel: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii,
 // evaluated as x_i + (b_i - (A x)_i) / a_ii with 1/a_ii precomputed per level
 // (0 where a_ii = 0: the row is left as is).
-template <int G, typename T>
+template <int G, typename T, typename TV = T>
 __global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int *__restrict__ clist,
                                                       const int *__restrict__ rowptr,
                                                       const int *__restrict__ col,
-                                                      const T *__restrict__ val,
+                                                      const TV *__restrict__ val,
                                                       const T *__restrict__ dinv,
                                                       const T *__restrict__ b, T *x) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1000,7 +1010,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int 
   bool valid = q < r1;
   int i = valid ? clist[q] : 0;
   int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
-  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  T s = row_dot<G, T, TV>(e0, e1, lane, col, val, x);
   if (G > 1) s = group_sum<G, T>(s);
   if (valid && lane == 0) {
     T di = dinv[i];
@@ -1010,10 +1020,10 @@ __global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int 
 
 // l1-Jacobi pre-smoothing from x = 0 fused with the residual: x_i = b_i d_i
 // and r_i = b_i - sum_j a_ij b_j d_j (d = 1 / sum_j |a_ij|, 0 for an empty row).
-template <int G, typename T>
+template <int G, typename T, typename TV = T>
 __global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restrict__ rowptr,
                                                        const int *__restrict__ col,
-                                                       const T *__restrict__ val,
+                                                       const TV *__restrict__ val,
                                                        const T *__restrict__ d,
                                                        const T *__restrict__ b, T *__restrict__ x,
                                                        T *__restrict__ r) {
@@ -1027,8 +1037,8 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restr
   for (; e + 3 * G < e1; e += 4 * G) {
     int c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
         c3 = __ldg(col + e + 3 * G);
-    T v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G),
-      v3 = __ldg(val + e + 3 * G);
+    T v0 = ldv<T>(val + e), v1 = ldv<T>(val + e + G), v2 = ldv<T>(val + e + 2 * G),
+      v3 = ldv<T>(val + e + 3 * G);
     s0 = fma(v0, __ldg(b + c0) * __ldg(d + c0), s0);
     s1 = fma(v1, __ldg(b + c1) * __ldg(d + c1), s1);
     s2 = fma(v2, __ldg(b + c2) * __ldg(d + c2), s2);
@@ -1036,7 +1046,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restr
   }
   for (; e < e1; e += G) {
     int c0 = __ldg(col + e);
-    s0 = fma(__ldg(val + e), __ldg(b + c0) * __ldg(d + c0), s0);
+    s0 = fma(ldv<T>(val + e), __ldg(b + c0) * __ldg(d + c0), s0);
   }
   T s = (s0 + s1) + (s2 + s3);
   if (G > 1) s = group_sum<G, T>(s);
@@ -1049,10 +1059,10 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restr
 
 // One l1-Jacobi sweep: t_i = x_i + (b_i - (A x)_i) d_i for every row from
 // the old x (t must not alias x).
-template <int G, typename T>
+template <int G, typename T, typename TV = T>
 __global__ void __launch_bounds__(kBlock) k_jacobi_sweep(int n, const int *__restrict__ rowptr,
                                                          const int *__restrict__ col,
-                                                         const T *__restrict__ val,
+                                                         const TV *__restrict__ val,
                                                          const T *__restrict__ d,
                                                          const T *__restrict__ b,
                                                          const T *__restrict__ x,
@@ -1061,39 +1071,39 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_sweep(int n, const int *__res
   int i = t / G, lane = t % G;
   bool valid = i < n;
   int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
-  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  T s = row_dot<G, T, TV>(e0, e1, lane, col, val, x);
   if (G > 1) s = group_sum<G, T>(s);
   if (valid && lane == 0) tout[i] = fma(b[i] - s, d[i], x[i]);
 }
 
 // r = b - A x
-template <int G, typename T>
+template <int G, typename T, typename TV = T>
 __global__ void __launch_bounds__(kBlock) k_csr_resid(int n, const int *__restrict__ rowptr,
                                                       const int *__restrict__ col,
-                                                      const T *__restrict__ val,
+                                                      const TV *__restrict__ val,
                                                       const T *__restrict__ b,
                                                       const T *__restrict__ x, T *__restrict__ r) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int i = t / G, lane = t % G;
   bool valid = i < n;
   int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
-  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  T s = row_dot<G, T, TV>(e0, e1, lane, col, val, x);
   if (G > 1) s = group_sum<G, T>(s);
   if (valid && lane == 0) r[i] = b[i] - s;
 }
 
 // y = A x (add = 0) or y += A x (add = 1)
-template <int G, typename T>
+template <int G, typename T, typename TV = T>
 __global__ void __launch_bounds__(kBlock) k_csr_mv(int n, const int *__restrict__ rowptr,
                                                    const int *__restrict__ col,
-                                                   const T *__restrict__ val,
+                                                   const TV *__restrict__ val,
                                                    const T *__restrict__ x, T *__restrict__ y,
                                                    int add) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int i = t / G, lane = t % G;
   bool valid = i < n;
   int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
-  T s = row_dot<G, T>(e0, e1, lane, col, val, x);
+  T s = row_dot<G, T, TV>(e0, e1, lane, col, val, x);
   if (G > 1) s = group_sum<G, T>(s);
   if (valid && lane == 0) y[i] = add ? y[i] + s : s;
 }
@@ -1139,9 +1149,23 @@ template <> struct LV<float> {
   static float *r(const Level &L) { return L.rf; }
 };
 
+// In the FP32 cycle a level whose values also have a BF16 copy (precision 2,
+// levels >= 1) is read from that copy.
+template <typename T>
+static bool use_bf16(const __nv_bfloat16 *h) {
+  return std::is_same<T, float>::value && h != nullptr;
+}
+
 template <typename T>
 static int csr_resid(Sim *s, const Level &L, const T *b, const T *x, T *r) {
   long long thr = (long long)L.n * L.G;
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_bf16<T>(L.valh)) {
+      DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_csr_resid<GG, float, __nv_bfloat16>), nblk(thr), kBlock, 0,
+                                 L.n, L.rowptr, L.col, L.valh, b, x, r));
+      return DP_OK;
+    }
+  }
   DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_csr_resid<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr, L.col,
                              LV<T>::val(L), b, x, r));
   return DP_OK;
@@ -1154,6 +1178,21 @@ static int csr_mv(Sim *s, int n, int G, const int *rowptr, const int *col, const
   DP_SWITCH_G(G, DP_LAUNCH(s, (k_csr_mv<GG, T>), nblk(thr), kBlock, 0, n, rowptr, col, val, x, y,
                            add));
   return DP_OK;
+}
+
+// A transfer operator (P or R) of a level, from its BF16 copy when it has one.
+template <typename T>
+static int transfer_mv(Sim *s, int n, int G, const int *rowptr, const int *col, const T *val,
+                       const __nv_bfloat16 *valh, const T *x, T *y, int add) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_bf16<T>(valh)) {
+      long long thr = (long long)n * G;
+      DP_SWITCH_G(G, DP_LAUNCH(s, (k_csr_mv<GG, float, __nv_bfloat16>), nblk(thr), kBlock, 0, n,
+                               rowptr, col, valh, x, y, add));
+      return DP_OK;
+    }
+  }
+  return csr_mv<T>(s, n, G, rowptr, col, val, x, y, add);
 }
 
 // coarsest level: dense copy, LU with partial pivoting, solve (one block)
@@ -1313,6 +1352,13 @@ int coarse_factor(Sim *s) {
 template <typename T>
 static int jacobi_pre(Sim *s, Level &L, const T *b, T *x, T *r) {
   long long thr = (long long)L.n * L.G;
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_bf16<T>(L.valh)) {
+      DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_pre<GG, float, __nv_bfloat16>), nblk(thr), kBlock, 0,
+                                 L.n, L.rowptr, L.col, L.valh, L.dinvf, b, x, r));
+      return DP_OK;
+    }
+  }
   DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_pre<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
                              L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
   return DP_OK;
@@ -1321,8 +1367,17 @@ static int jacobi_pre(Sim *s, Level &L, const T *b, T *x, T *r) {
 template <typename T>
 static int jacobi_post(Sim *s, Level &L, const T *b, T *x, T *r) {
   long long thr = (long long)L.n * L.G;
-  DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_sweep<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
-                             L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
+  bool done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_bf16<T>(L.valh)) {
+      DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_sweep<GG, float, __nv_bfloat16>), nblk(thr), kBlock,
+                                 0, L.n, L.rowptr, L.col, L.valh, L.dinvf, b, x, r));
+      done = true;
+    }
+  }
+  if (!done)
+    DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_sweep<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
+                               L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
   DP_CUDA(s, cudaMemcpyAsync(x, r, (size_t)L.n * sizeof(T), cudaMemcpyDeviceToDevice, s->stream));
   return DP_OK;
 }
@@ -1425,7 +1480,7 @@ static int l0c_setup(Sim *s) {
   s->p0c_col = (int *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
   s->p0c_src = (int *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
   int *len = (int *)dalloc(s, (size_t)n * 4);
-  bool f32 = s->opt.precision == 1;
+  bool f32 = s->opt.precision >= 1;
   if (f32) {
     s->p0c_valf = (float *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
     s->dinv_cf = (float *)dalloc(s, (size_t)n * 4);
@@ -1462,7 +1517,7 @@ int l0_refresh(Sim *s, bool coarse) {
     for (int c = 0; c <= L.ncolour; ++c)
       if (L.cstart[c] != s->lu_cstart[c]) return DP_OK;
     size_t nnz = (size_t)std::max(L.nnz, 1);
-    if (s->opt.precision == 1) s->l0_pvf = (float *)dalloc(s, nnz * 4);
+    if (s->opt.precision >= 1) s->l0_pvf = (float *)dalloc(s, nnz * 4);
     else s->l0_pv = (double *)dalloc(s, nnz * 8);
     if (!s->l0_pvf && !s->l0_pv) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
     s->l0_lu = true;
@@ -1700,8 +1755,17 @@ static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
     int r0 = L.cstart[c], r1 = L.cstart[c + 1];
     if (r1 > r0) {
       long long thr = (long long)(r1 - r0) * L.G;
-      DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_gs_colour<GG, T>), nblk(thr), kBlock, 0, r0, r1, L.clist,
-                                 L.rowptr, L.col, LV<T>::val(L), LV<T>::dinv(L), b, x));
+      bool done = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (use_bf16<T>(L.valh)) {
+          DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_gs_colour<GG, float, __nv_bfloat16>), nblk(thr), kBlock,
+                                     0, r0, r1, L.clist, L.rowptr, L.col, L.valh, L.dinvf, b, x));
+          done = true;
+        }
+      }
+      if (!done)
+        DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_gs_colour<GG, T>), nblk(thr), kBlock, 0, r0, r1, L.clist,
+                                   L.rowptr, L.col, LV<T>::val(L), LV<T>::dinv(L), b, x));
     }
   }
   return DP_OK;
@@ -1754,9 +1818,9 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x) {
     DP_TRY(gs_sweep<T>(s, L, b, x, true));
     DP_TRY(csr_resid<T>(s, L, b, x, r));
   }
-  DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, L.r_col, LV<T>::rval(L), r, nb, 0));
+  DP_TRY(transfer_mv<T>(s, N.n, L.r_G, L.r_rowptr, L.r_col, LV<T>::rval(L), L.r_valh, r, nb, 0));
   DP_TRY(vcycle_t<T>(s, l + 1, nb, nx));
-  DP_TRY(csr_mv<T>(s, n, L.p_G, L.p_rowptr, L.p_col, LV<T>::pval(L), nx, x, 1));
+  DP_TRY(transfer_mv<T>(s, n, L.p_G, L.p_rowptr, L.p_col, LV<T>::pval(L), L.p_valh, nx, x, 1));
   if (L.l1) DP_TRY(jacobi_post<T>(s, L, b, x, r));
   else DP_TRY(gs_sweep<T>(s, L, b, x, false));
   return DP_OK;
@@ -1850,7 +1914,7 @@ int autotune(Sim *s, int reps, std::string &rep) {
   }
   reps = std::max(1, std::min(reps, 1000));
   for (int l = 0; l < (int)s->lev.size(); ++l) {
-    if (s->opt.precision == 1) DP_TRY(tune_level<float>(s, l, reps, rep));
+    if (s->opt.precision >= 1) DP_TRY(tune_level<float>(s, l, reps, rep));
     else DP_TRY(tune_level<double>(s, l, reps, rep));
   }
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -1885,7 +1949,7 @@ __global__ void k_to_f32(long long n, const double *x, float *y) {
 int cpr_apply(Sim *s, const double *r, double *z) {
   int nb = s->K.n;
   long long N = 2LL * nb;
-  bool f32 = s->opt.precision == 1;
+  bool f32 = s->opt.precision >= 1;
   if (s->opt.precond == 0) {
     DP_CUDA(s, cudaMemcpyAsync(z, r, N * 8, cudaMemcpyDeviceToDevice, s->stream));
     return DP_OK;
@@ -2324,7 +2388,7 @@ int la_alloc(Sim *s) {
   s->scal = (double *)dalloc(s, 8 * 8);
   s->z1 = (double *)dalloc(s, (size_t)N * 8);
   s->r1 = (double *)dalloc(s, (size_t)N * 8);
-  if (s->opt.precision == 1) {
+  if (s->opt.precision >= 1) {
     s->z1f = (float *)dalloc(s, (size_t)N * 4);
     s->r1f = (float *)dalloc(s, (size_t)N * 4);
     if (!s->z1f || !s->r1f) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
@@ -2344,9 +2408,29 @@ __global__ void k_to_f32_i(long long n, const double *x, float *y) {
   if (i < n) y[i] = float(x[i]);
 }
 
+__global__ void k_to_bf16(long long n, const double *x, __nv_bfloat16 *y) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __double2bfloat16(x[i]);
+}
+
+// BF16 copy of n FP64 values into *dst (allocated on first use).
+static int to_bf16(Sim *s, long long n, const double *src, __nv_bfloat16 **dst) {
+  if (n <= 0) return DP_OK;
+  if (!*dst) {
+    *dst = (__nv_bfloat16 *)dalloc(s, (size_t)n * 2);
+    if (!*dst) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  }
+  DP_LAUNCH(s, k_to_bf16, nblk(n), kBlock, 0, n, src, *dst);
+  return DP_OK;
+}
+
 // FP32 copies of the AMG operators, transfer operators and inverse
-// diagonals (precision 1), refreshed with the FP64 values: every level, or
-// (coarse = false) the level-0 operator and scaling only.
+// diagonals (precisions 1 and 2), refreshed with the FP64 values: every
+// level, or (coarse = false) the level-0 operator and scaling only.  With
+// precision 2 the operators of levels >= 1 below the coarsest, and their
+// prolongation and restriction, also get BF16 copies, which the FP32 cycle
+// reads instead (values rounded to 8 significant bits; the scalings 1/a_ii
+// and every vector stay FP32, the arithmetic FP32).
 int mixed_refresh(Sim *s, bool coarse) {
   for (size_t l = 0; l < s->lev.size(); ++l) {
     if (!coarse) {
@@ -2362,9 +2446,15 @@ int mixed_refresh(Sim *s, bool coarse) {
     Level &L = s->lev[l];
     DP_LAUNCH(s, k_to_f32_i, nblk(L.nnz), kBlock, 0, (long long)L.nnz, L.val, L.valf);
     DP_LAUNCH(s, k_to_f32_i, nblk(L.n), kBlock, 0, (long long)L.n, L.dinv, L.dinvf);
-    if (l + 1 < s->lev.size()) {
+    bool last = l + 1 == s->lev.size();
+    if (!last) {
       DP_LAUNCH(s, k_to_f32_i, nblk(L.p_nnz), kBlock, 0, (long long)L.p_nnz, L.p_val, L.p_valf);
       DP_LAUNCH(s, k_to_f32_i, nblk(L.r_nnz), kBlock, 0, (long long)L.r_nnz, L.r_val, L.r_valf);
+    }
+    if (s->opt.precision == 2 && l >= 1 && !last) {
+      DP_TRY(to_bf16(s, L.nnz, L.val, &L.valh));
+      DP_TRY(to_bf16(s, L.p_nnz, L.p_val, &L.p_valh));
+      DP_TRY(to_bf16(s, L.r_nnz, L.r_val, &L.r_valh));
     }
   }
   DP_CUDA(s, cudaGetLastError());

@@ -365,7 +365,7 @@ int phys_build_pattern(Sim *s) {
   s->trans = (double *)dalloc(s, (size_t)nnz * 8);
   s->ap = (double *)dalloc(s, (size_t)nnz * 8);
   s->sval = (double *)dalloc(s, (size_t)nnz * 32);
-  if (s->opt.precision == 1) {   // the preconditioner's residuals in FP32
+  if (s->opt.precision >= 1) {   // the preconditioner's residuals in FP32
     s->svalf = (float *)dalloc(s, (size_t)nnz * 16);
     s->spf = (float *)dalloc(s, (size_t)nnz * 8);
     if (!s->svalf || !s->spf) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
@@ -968,7 +968,7 @@ int phys_decouple_extract(Sim *s) {
   a.val = K.val; a.fct = s->fct;
   a.ap = s->ap; a.sval = s->sval; a.sa00 = s->sa00; a.sa01 = s->sa01;
   a.svalf = s->svalf; a.spf = s->spf;
-  bool f32 = s->opt.precision == 1;
+  bool f32 = s->opt.precision >= 1;
   a.lu = s->opt.precond >= 1 ? (f32 ? (void *)s->lu_valf : (void *)s->lu_val) : nullptr;
   a.l0 = s->l0_lu ? (f32 ? (void *)s->l0_pvf : (void *)s->l0_pv) : nullptr;
   if (f32) DP_LAUNCH(s, k_decouple<float>, nblk(K.nnz), kBlock, 0, a);

@@ -132,7 +132,7 @@ using namespace dp;
 static bool bad_opts(const dp_options *o) {
   return !o || o->gmres_restart < 1 || o->gmres_maxit < 1 || o->newton_max < 0 ||
          o->amg_coarse_max < 1 || o->amg_max_levels < 1 || o->precond < 0 || o->precond > 2 ||
-         o->precision < 0 || o->precision > 1 || !(o->ds_max > 0.0) || o->amg_gs_levels < 0 ||
+         o->precision < 0 || o->precision > 2 || !(o->ds_max > 0.0) || o->amg_gs_levels < 0 ||
          o->amg_refresh < 0 || o->amg_refresh > 1 || o->decouple < 0 || o->decouple > 2 ||
          o->schur < 0 || o->schur > 1 || !(o->reorth >= 0.0) || !std::isfinite(o->reorth);
 }
@@ -409,7 +409,7 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
     if (!s->amg_ready) DP_TRY(amg_setup(s));
     else if (coarse) DP_TRY(amg_refresh(s));
     else DP_TRY(level_dinv(s, s->lev[0]));   // level 0 only: its values are s->ap
-    if (s->opt.precision == 1) DP_TRY(mixed_refresh(s, coarse));
+    if (s->opt.precision >= 1) DP_TRY(mixed_refresh(s, coarse));
     DP_TRY(l0_refresh(s, coarse));
     if (coarse) DP_TRY(cluster_refresh(s));
   }

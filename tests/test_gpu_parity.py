@@ -371,12 +371,14 @@ def test_tiny_steps_option_variants(kw):
         state_close(g, o, prob)
 
 
-@pytest.mark.parametrize("precond", [1, 2])
-def test_mixed_precision_preconditioner_tiny_steps(precond):
-    """FP32 ILU(0) and AMG inside FP64 FGMRES: the Newton states still match
-    the FP64 oracle to the parity tolerance (FGMRES wins the accuracy back)."""
+@pytest.mark.parametrize("precond,precision", [(1, 1), (2, 1), (2, 2)])
+def test_mixed_precision_preconditioner_tiny_steps(precond, precision):
+    """FP32 ILU(0) and AMG inside FP64 FGMRES (precision 2: the coarse AMG
+    levels stored in BF16): the Newton states still match the FP64 oracle to
+    the parity tolerance (FGMRES wins the accuracy back)."""
     prob = di.tiny()
-    g = gpu().Sim(prob, gpu().options("parity", precision=1, precond=precond, gmres_maxit=600))
+    g = gpu().Sim(prob, gpu().options("parity", precision=precision, precond=precond,
+                                      gmres_maxit=600))
     o = O.OracleSim(prob, O.options("parity", precond=precond, gmres_maxit=600))
     for step in range(4):
         rcg, stg = g.advance(prob.dt)
@@ -385,9 +387,10 @@ def test_mixed_precision_preconditioner_tiny_steps(precond):
         state_close(g, o, prob)
 
 
-def test_mixed_precision_layered_timestep():
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_layered_timestep(precision):
     prob = di.layered()
-    g = gpu().Sim(prob, gpu().options("parity", precision=1))
+    g = gpu().Sim(prob, gpu().options("parity", precision=precision))
     o = O.OracleSim(prob, O.options("parity"))
     rcg, stg = g.advance(prob.dt)
     rco, sto = o.advance(prob.dt)

@@ -55,7 +55,9 @@ def test_forcing_terms_tiny_steps(mode):
         g.assemble(prob.dt)
         o.assemble(prob.dt)
         ng, no = g.norms(), o.norms()
-        np.testing.assert_allclose(ng[:2], no[:2], rtol=1e-12)
+        # the same state at l = 0; after that the two updates differ at the
+        # rounding of their FGMRES runs (solved to eta ~ 1e-1 .. 1e-4)
+        np.testing.assert_allclose(ng[:2], no[:2], rtol=1e-12 if l == 0 else 1e-6)
         res0 = no[0] if l == 0 else res0
         if no[0] <= opts.newton_tol * res0 or no[1] <= opts.newton_atol:
             break
