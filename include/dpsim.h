@@ -269,6 +269,36 @@ int sim_run(dp_sim *sim, double t_end, double dt0, double dt_max, double dt_min,
 int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t threads,
                      dp_stats *stats, int32_t *status);
 
+/* Batched timesteps in lockstep (no counterpart in the paper; the batched
+ * engine of many uneven-size realisations on one GPU).  A batch groups n
+ * realisations created with the FP32 preconditioner (precision 1 or 2),
+ * CPR-FPF (precond 2), l1-Jacobi below AMG level 0 (amg_gs_levels <= 1) and
+ * equal gmres_restart and gmres_maxit; the realisations must outlive the
+ * batch and must not be used by other calls while batch_advance runs.
+ * batch_advance does one timestep of each realisation k by dt[k] (Algorithm
+ * 1, as sim_advance): every Newton iteration assembles and sets up each
+ * realisation still iterating, then runs their FGMRES iterations together:
+ * every phase of the Arnoldi step (the ILU(0) sweeps of each colour, the
+ * CPR stage residuals, each level of the V-cycle, the operator product, the
+ * Gram-Schmidt passes, the Givens rotations) is one launch over a work list
+ * of (realisation, block) tiles, in which each realisation runs the blocks
+ * of its own launch; realisations that have converged drop out through a
+ * device flag.  Each realisation's result is that of sim_advance on it
+ * alone, bit for bit, whatever the other members of the batch.  All work
+ * runs on `stream` (a cudaStream_t; NULL: the default stream), with the
+ * realisations' own streams synchronised first.  stats[k], status[k] (may
+ * be NULL) as sim_advance's; returns DP_OK when all succeeded, else the
+ * first failing code.  batch_create returns DP_EINVAL for an unsupported or
+ * repeated realisation; its device memory comes from the first
+ * realisation's allocator. */
+typedef struct dp_batch dp_batch;
+int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_batch **out);
+int batch_advance(dp_batch *batch, const double *dt, dp_stats *stats, int32_t *status);
+void batch_destroy(dp_batch *batch);
+const char *batch_last_error(const dp_batch *batch);
+/* kernel launches of the batch and its realisations since their creation */
+int64_t batch_launch_count(const dp_batch *batch);
+
 /* A non-blocking CUDA stream owned by the caller until dp_stream_destroy:
  * for callers whose framework hands out pooled streams (many realisations
  * need as many distinct streams to overlap).  No counterpart in the paper. */

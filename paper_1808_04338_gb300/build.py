@@ -28,6 +28,7 @@ UNITS = {
     "dp_noalloc.cu": [],
     "dp_cycle.cu": [],
     "dp_serve.cu": [],
+    "dp_batch.cu": [],
 }
 
 
@@ -48,7 +49,8 @@ def _stale(obj, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, "dp_internal.h"), os.path.join(ROOT, "include", "dpsim.h")]
+    headers = [os.path.join(CSRC, "dp_internal.h"), os.path.join(CSRC, "dp_kernels.cuh"),
+               os.path.join(ROOT, "include", "dpsim.h")]
     jobs = []
     objs = []
     for src, extra in UNITS.items():

@@ -163,6 +163,16 @@ int phys_schur_reduce(Sim *s);    // K's values and residual from A and R (Schur
 int phys_schur_back(Sim *s);      // the full update y from K's update
 int phys_update(Sim *s);
 
+// dp_sim.cu: the parts of a Newton step that the batched driver shares with
+// sim_solve_step and sim_advance
+int solve_prepare(Sim *s, double *eta, bool norms_current = false);
+int solve_update(Sim *s, int rc);
+int solve_finish(Sim *s, int rc, int it, double rr, double eta, float ms_setup, float ms_solve,
+                 dp_stats *st);
+void new_timestep(Sim *s);
+int timestep_begin(Sim *s);
+int timestep_restore(Sim *s);
+
 // dp_amg.cu (integer setup and bit-exact smoothed-aggregation numerics)
 int scan_i32(Sim *s, const int *in, int *out, int n, int *total);  // out[n] = total
 int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour,
@@ -348,3 +358,6 @@ struct Sim {
 };
 
 }  // namespace dp
+
+// The opaque handle of the C ABI is the library's realisation.
+struct dp_sim : dp::Sim {};

@@ -1,0 +1,885 @@
+// Kernel bodies of the Krylov loop and the preconditioner, shared by the
+// per-realisation launches (dp_la.cu) and the batched launches over many
+// realisations (dp_batch.cu).  Each body takes the block index and the grid
+// size of the launch it stands for (bx, gx) in place of blockIdx.x and
+// gridDim.x: a batched launch runs, for every realisation, exactly the
+// blocks its own launch would run, so each realisation's results are the
+// same bit for bit whether it is solved alone or in a batch.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "dp_internal.h"
+
+namespace dp {
+
+constexpr int kLongRow = 24;   // colours with a row longer than this use a warp per row
+
+// The well rows (storage rows nlong..n-1, one block per perforation, tens of
+// blocks each; their storage row is their row) go to block 0, a warp per
+// row, so that their long rows start first instead of trailing the launch.
+// Storage row q < nlong is row row_of_pair(q, nL, nc).
+template <int MODE>
+__device__ __forceinline__ void spmv_well_rows(int n, int nc, const int *__restrict__ rowptr,
+                                               const int *__restrict__ col,
+                                               const double *__restrict__ val,
+                                               const double *__restrict__ x,
+                                               const double *__restrict__ b,
+                                               double *__restrict__ y) {
+  int lane = threadIdx.x & 31;
+  const double2 *v2 = reinterpret_cast<const double2 *>(val);
+  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  for (int row = nc + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
+      double2 a = __ldg(v2 + 2 * (size_t)e), c = __ldg(v2 + 2 * (size_t)e + 1);
+      double2 xj = __ldg(x2 + __ldg(col + e));
+      s0 = fma(a.x, xj.x, fma(a.y, xj.y, s0));
+      s1 = fma(c.x, xj.x, fma(c.y, xj.y, s1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+      y[2 * (size_t)row] = MODE == 0 ? s0 : b[2 * (size_t)row] - s0;
+      y[2 * (size_t)row + 1] = MODE == 0 ? s1 : b[2 * (size_t)row + 1] - s1;
+    }
+  }
+}
+
+// Two-component vector type of a value type (16-byte double2 or 8-byte
+// float2 loads of one row of a 2x2 block).
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+
+// A 2x2 block (row-major, 16-byte aligned) loaded or stored with vector
+// accesses (coherent: the factorisation reads blocks that it also writes).
+template <typename T> struct Blk;
+template <> struct Blk<float> {
+  static __device__ __forceinline__ void load(const float *p, float *o) {
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  static __device__ __forceinline__ void store(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Blk<double> {
+  static __device__ __forceinline__ void load(const double *p, double *o) {
+    double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  static __device__ __forceinline__ void store(double *p, const double *v) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+constexpr int kRes = 4;   // rows per thread of the gather-style kernels
+
+// Warp-per-row variants of the sweeps for colours with long rows (the well
+// rows, one entry per perforation): the lanes split the row's blocks and
+// the partial sums meet in shuffles, instead of one thread walking a row of
+// tens of blocks.
+template <typename T> struct V4;
+template <> struct V4<double> {
+  static __device__ __forceinline__ void load(const double *p, double *o) {
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p)),
+            b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+};
+template <> struct V4<float> {
+  static __device__ __forceinline__ void load(const float *p, float *o) {
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Scalar CSR kernels of the AMG levels in precision T: G lanes per row (G
+// chosen per level from its mean row length), partial sums combined with
+// shuffles inside the group; every lane reaches the shuffles (no early exit).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+// A stored value as the compute type T: the value itself, or (BF16 storage
+// of the coarse levels, precision 2) its FP32 widening.
+template <typename T, typename TV>
+__device__ __forceinline__ T ldv(const TV *p) { return T(__ldg(p)); }
+template <>
+__device__ __forceinline__ float ldv<float, __nv_bfloat16>(const __nv_bfloat16 *p) {
+  return __bfloat162float(__ldg(p));
+}
+
+// Row dot product sum_e val[e] x[col[e]] over the lane's entries e0+lane,
+// e0+lane+G, ...: four independent accumulators keep four loads in flight
+// per lane, so a long row is not one serial chain of dependent loads.
+template <int G, typename T, typename TV = T>
+__device__ __forceinline__ T row_dot(int e0, int e1, int lane, const int *__restrict__ col,
+                                     const TV *__restrict__ val, const T *__restrict__ x) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int e = e0 + lane;
+  for (; e + 3 * G < e1; e += 4 * G) {
+    int c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
+        c3 = __ldg(col + e + 3 * G);
+    T v0 = ldv<T>(val + e), v1 = ldv<T>(val + e + G), v2 = ldv<T>(val + e + 2 * G),
+      v3 = ldv<T>(val + e + 3 * G);
+    s0 = fma(v0, x[c0], s0);
+    s1 = fma(v1, x[c1], s1);
+    s2 = fma(v2, x[c2], s2);
+    s3 = fma(v3, x[c3], s3);
+  }
+  for (; e < e1; e += G) s0 = fma(ldv<T>(val + e), x[__ldg(col + e)], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// A warp per (long) row: RESID = false, one colour of Gauss-Seidel;
+// RESID = true, r = b - A x for those rows.
+template <typename T, bool RESID>
+__device__ __forceinline__ void row_c_w(int bx, int r0, int r1, const int *__restrict__ rowptr,
+                                        const int *__restrict__ colp, const T *__restrict__ pv,
+                                        const T *__restrict__ dinv, const T *__restrict__ b,
+                                        T *x, T *r) {
+  int q = r0 + (int)((bx * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (q >= r1) return;   // whole warps
+  T s = T(0);
+  for (int e = __ldg(rowptr + q) + lane, e1 = __ldg(rowptr + q + 1); e < e1; e += 32)
+    s = fma(__ldg(pv + e), x[__ldg(colp + e)], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (RESID) {
+      r[q] = b[q] - s;
+    } else {
+      T di = dinv[q];
+      if (di != T(0)) x[q] = fma(b[q] - s, di, x[q]);
+    }
+  }
+}
+
+// Deterministic reductions: a grid of dot_blocks(N) blocks writes one
+// partial per vector, a single warp sums the partials in block order.
+constexpr int kDotBlocks = 608;   // 4 x 152 SMs
+constexpr int kDotVec = 8;        // vectors per pass
+
+// Blocks of a dot-product launch over N doubles: one per 512 double2
+// elements (each thread takes two a trip), at least one, at most kDotBlocks.
+// A realisation's reductions depend on its own N only.
+inline int dot_blocks(long long N) {
+  long long b = (N / 2 + 2LL * kBlock - 1) / (2LL * kBlock);
+  return (int)(b < 1 ? 1 : (b > kDotBlocks ? kDotBlocks : b));
+}
+
+template <int MODE>  // MODE 0: y = A x; 1: y = b - A x
+__device__ __forceinline__ void k_bsr_spmv_b(int bx, int gx, int n, int nL, int nc, int nlong,
+                                                     const int *__restrict__ rowptr,
+                                                     const int *__restrict__ col,
+                                                     const double *__restrict__ val,
+                                                     const double *__restrict__ x,
+                                                     const double *__restrict__ b,
+                                                     double *__restrict__ y) {
+  if (bx == 0) {
+    spmv_well_rows<MODE>(n, nlong, rowptr, col, val, x, b, y);
+    return;
+  }
+  __shared__ double sh[kBlock];
+  int q0 = (bx - 1) * (kBlock / 2);
+  int comp = threadIdx.x & 1, q = q0 + (threadIdx.x >> 1);
+  if (q < nlong) {
+    int row = row_of_pair(q, nL, nc);
+    int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
+    const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
+    const double2 *x2 = reinterpret_cast<const double2 *>(x);
+    double s = 0.0;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+      double2 a = __ldg(v2 + 2 * (size_t)e);
+      double2 xj = __ldg(x2 + __ldg(col + e));
+      s = fma(a.x, xj.x, s);
+      s = fma(a.y, xj.y, s);
+    }
+    sh[2 * (row - q0) + comp] = s;
+  }
+  __syncthreads();
+  int cnt = nlong - q0 < kBlock / 2 ? nlong - q0 : kBlock / 2;
+  if ((int)threadIdx.x < 2 * cnt) {
+    size_t k = 2 * (size_t)q0 + threadIdx.x;
+    y[k] = MODE == 0 ? sh[threadIdx.x] : b[k] - sh[threadIdx.x];
+  }
+}
+
+__device__ __forceinline__ void k_bsr_resid_f32_b(int bx, int gx, int n, int nL, int nc, int nlong,
+                                                         const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         const float *__restrict__ valf,
+                                                         const float *__restrict__ x,
+                                                         const double *__restrict__ b,
+                                                         float *__restrict__ y) {
+  const float2 *v2 = reinterpret_cast<const float2 *>(valf);
+  const float2 *x2 = reinterpret_cast<const float2 *>(x);
+  if (bx == 0) {   // the well rows, a warp per row
+    int lane = threadIdx.x & 31;
+    for (int row = nlong + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+      float s0 = 0.f, s1 = 0.f;
+      for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
+        float2 a = __ldg(v2 + 2 * (size_t)e), c = __ldg(v2 + 2 * (size_t)e + 1);
+        float2 xj = __ldg(x2 + __ldg(col + e));
+        s0 = fmaf(a.x, xj.x, fmaf(a.y, xj.y, s0));
+        s1 = fmaf(c.x, xj.x, fmaf(c.y, xj.y, s1));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (lane == 0) {
+        y[2 * (size_t)row] = float(b[2 * (size_t)row]) - s0;
+        y[2 * (size_t)row + 1] = float(b[2 * (size_t)row + 1]) - s1;
+      }
+    }
+    return;
+  }
+  __shared__ float sh[kBlock];
+  int q0 = (bx - 1) * (kBlock / 2);
+  int comp = threadIdx.x & 1, q = q0 + (threadIdx.x >> 1);
+  if (q < nlong) {
+    int row = row_of_pair(q, nL, nc);
+    int e0 = __ldg(rowptr + q), e1 = __ldg(rowptr + q + 1);
+    float s = 0.f;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+      float2 a = __ldg(v2 + 2 * (size_t)e + comp);
+      float2 xj = __ldg(x2 + __ldg(col + e));
+      s = fmaf(a.x, xj.x, s);
+      s = fmaf(a.y, xj.y, s);
+    }
+    sh[2 * (row - q0) + comp] = s;
+  }
+  __syncthreads();
+  int cnt = nlong - q0 < kBlock / 2 ? nlong - q0 : kBlock / 2;
+  if ((int)threadIdx.x < 2 * cnt) {
+    size_t k = 2 * (size_t)q0 + threadIdx.x;
+    y[k] = float(b[k]) - sh[threadIdx.x];
+  }
+}
+
+__device__ __forceinline__ void k_bsr_presid_f32_b(int bx, int gx, int n, int nL, int nc, int nlong,
+                                                          const int *__restrict__ rowptr,
+                                                          const int *__restrict__ col,
+                                                          const float2 *__restrict__ pf,
+                                                          const float *__restrict__ x,
+                                                          const double *__restrict__ b,
+                                                          float *__restrict__ rp,
+                                                          const int *__restrict__ omap) {
+  const float2 *x2 = reinterpret_cast<const float2 *>(x);
+  if (bx == 0) {
+    int lane = threadIdx.x & 31;
+    for (int row = nlong + (threadIdx.x >> 5); row < n; row += blockDim.x >> 5) {
+      float s = 0.f;
+      for (int e = __ldg(rowptr + row) + lane, e1 = __ldg(rowptr + row + 1); e < e1; e += 32) {
+        float2 xj = __ldg(x2 + __ldg(col + e));
+        float2 a = __ldg(pf + e);
+        s = fmaf(a.x, xj.x, fmaf(a.y, xj.y, s));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) rp[omap ? omap[row] : row] = float(b[2 * (size_t)row]) - s;
+    }
+    return;
+  }
+  __shared__ float sh[kBlock];
+  int q0 = (bx - 1) * kBlock, t = q0 + threadIdx.x;
+  if (t < nlong) {
+    int row = row_of_pair(t, nL, nc);
+    int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
+    float s = 0.f;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+      float2 xj = __ldg(x2 + __ldg(col + e));
+      float2 a = __ldg(pf + e);
+      s = fmaf(a.x, xj.x, s);
+      s = fmaf(a.y, xj.y, s);
+    }
+    sh[row - q0] = s;
+  }
+  __syncthreads();
+  if (t < nlong) rp[omap ? __ldg(omap + t) : t] = float(b[2 * (size_t)t]) - sh[threadIdx.x];
+}
+
+template <typename T, typename TR>
+__device__ __forceinline__ void k_ilu_fwd_b(int bx, int gx, int r0, int r1, const int *__restrict__ perm,
+                                                    const int *__restrict__ Lptr,
+                                                    const int *__restrict__ colp,
+                                                    const T *__restrict__ lu,
+                                                    const TR *__restrict__ rhs, T *zp) {
+  using T2 = typename V2<T>::t;
+  int t = bx * blockDim.x + threadIdx.x;
+  int r = r0 + (t >> 1), comp = t & 1;
+  if (r >= r1) return;
+  int i = __ldg(perm + r);
+  const T2 *v2 = reinterpret_cast<const T2 *>(lu) + comp;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  T s = T(0);
+  int ea = __ldg(Lptr + r), eb = __ldg(Lptr + r + 1);
+#pragma unroll 4
+  for (int e = ea; e < eb; ++e) {
+    T2 a = __ldg(v2 + 2 * (size_t)e);
+    T2 xk = z2[__ldg(colp + e)];
+    s = fma(a.x, xk.x, s);
+    s = fma(a.y, xk.y, s);
+  }
+  zp[2 * (size_t)r + comp] = T(rhs[2 * (size_t)i + comp]) - s;
+}
+
+template <typename T, typename TR>
+__device__ __forceinline__ void k_ilu_fwd_copy_b(int bx, int gx, int r0, int r1, const int *__restrict__ perm,
+                                                     const TR *__restrict__ rhs, T *zp) {
+  using T2 = typename V2<T>::t;
+  using R2 = typename V2<TR>::t;
+  int S = gx * blockDim.x;
+  int q0 = r0 + bx * blockDim.x + threadIdx.x;
+  int p[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) p[k] = q0 + k * S < r1 ? __ldcs(perm + q0 + k * S) : 0;
+  R2 v[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k)
+    if (q0 + k * S < r1) v[k] = reinterpret_cast<const R2 *>(rhs)[p[k]];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    T2 o;
+    o.x = T(v[k].x);
+    o.y = T(v[k].y);
+    if (q0 + k * S < r1) reinterpret_cast<T2 *>(zp)[q0 + k * S] = o;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void k_ilu_bwd_r_b(int bx, int gx, int r0, int r1, int nL, int n,
+                                                      const int *__restrict__ Uptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ lu, T *zp) {
+  using T2 = typename V2<T>::t;
+  T2 *z2 = reinterpret_cast<T2 *>(zp);
+  size_t ub = (size_t)nL + n;
+  int S = gx * blockDim.x;
+  int q0 = r0 + bx * blockDim.x + threadIdx.x;
+  int ea[kRes], eb[kRes];
+  T d[kRes][4];
+  T2 y[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int q = q0 + k * S;
+    bool ok = q < r1;
+    ea[k] = ok ? __ldcs(Uptr + q) : 0;
+    eb[k] = ok ? __ldcs(Uptr + q + 1) : 0;
+    if (ok) {
+      Blk<T>::load(lu + 4 * ((size_t)nL + q), d[k]);
+      y[k] = z2[q];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int q = q0 + k * S;
+    if (q >= r1) continue;
+    T s0 = T(0), s1 = T(0);
+    for (int e = ea[k]; e < eb[k]; ++e) {
+      T a[4];
+      Blk<T>::load(lu + 4 * (ub + e), a);
+      T2 xj = z2[__ldcs(colp + ub + e)];
+      s0 = fma(a[0], xj.x, s0);
+      s0 = fma(a[1], xj.y, s0);
+      s1 = fma(a[2], xj.x, s1);
+      s1 = fma(a[3], xj.y, s1);
+    }
+    T y0 = y[k].x - s0, y1 = y[k].y - s1;
+    T2 o;
+    o.x = fma(d[k][0], y0, d[k][1] * y1);
+    o.y = fma(d[k][2], y0, d[k][3] * y1);
+    z2[q] = o;
+  }
+}
+
+template <typename T, typename TR, bool PIVOT>
+__device__ __forceinline__ void k_ilu_fwd_w_b(int bx, int gx, int r0, int r1, int nL,
+                                                      const int *__restrict__ perm,
+                                                      const int *__restrict__ Lptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ lu,
+                                                      const TR *__restrict__ rhs, T *zp) {
+  int r = r0 + (int)((bx * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (r >= r1) return;   // whole warps
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  T s0 = T(0), s1 = T(0);
+  for (int e = __ldg(Lptr + r) + lane, eb = __ldg(Lptr + r + 1); e < eb; e += 32) {
+    T a[4];
+    V4<T>::load(lu + 4 * (size_t)e, a);
+    T2 xk = z2[__ldg(colp + e)];
+    s0 = fma(a[0], xk.x, fma(a[1], xk.y, s0));
+    s1 = fma(a[2], xk.x, fma(a[3], xk.y, s1));
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  if (lane == 0) {
+    int i = __ldg(perm + r);
+    T y0 = T(rhs[2 * (size_t)i]) - s0, y1 = T(rhs[2 * (size_t)i + 1]) - s1;
+    if (PIVOT) {
+      y0 = y0 - T(0);   // the backward sweep's y - (sum over no U blocks)
+      y1 = y1 - T(0);
+      T d[4];
+      V4<T>::load(lu + 4 * ((size_t)nL + r), d);
+      zp[2 * (size_t)r] = fma(d[0], y0, d[1] * y1);
+      zp[2 * (size_t)r + 1] = fma(d[2], y0, d[3] * y1);
+    } else {
+      zp[2 * (size_t)r] = y0;
+      zp[2 * (size_t)r + 1] = y1;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void k_ilu_bwd_w_b(int bx, int gx, int r0, int r1, int nL, int n,
+                                                      const int *__restrict__ Uptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ lu, T *zp) {
+  int r = r0 + (int)((bx * (long long)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (r >= r1) return;
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  size_t ub = (size_t)nL + n;
+  T s0 = T(0), s1 = T(0);
+  for (int e = __ldg(Uptr + r) + lane, eb = __ldg(Uptr + r + 1); e < eb; e += 32) {
+    T a[4];
+    V4<T>::load(lu + 4 * (ub + e), a);
+    T2 xj = z2[__ldg(colp + ub + e)];
+    s0 = fma(a[0], xj.x, fma(a[1], xj.y, s0));
+    s1 = fma(a[2], xj.x, fma(a[3], xj.y, s1));
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  if (lane == 0) {
+    T y0 = zp[2 * (size_t)r] - s0, y1 = zp[2 * (size_t)r + 1] - s1;
+    T d[4];
+    V4<T>::load(lu + 4 * ((size_t)nL + r), d);
+    zp[2 * (size_t)r] = fma(d[0], y0, d[1] * y1);
+    zp[2 * (size_t)r + 1] = fma(d[2], y0, d[3] * y1);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void k_ilu_result_b(int bx, int gx, int n, const int *__restrict__ iperm,
+                                                       const T *__restrict__ zp,
+                                                       const double *__restrict__ base,
+                                                       double *__restrict__ out,
+                                                       T *__restrict__ outT,
+                                                       const float *__restrict__ inj,
+                                                       int inj_perm) {
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  int S = gx * blockDim.x;
+  int i0 = bx * blockDim.x + threadIdx.x;
+  int p[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int i = i0 + k * S;
+    p[k] = i < n ? __ldg(iperm + i) : 0;
+  }
+  T2 z[kRes];
+  double2 bs[kRes];
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int i = i0 + k * S;
+    if (i < n) {
+      z[k] = z2[p[k]];
+      bs[k] = base ? reinterpret_cast<const double2 *>(base)[i] : make_double2(0.0, 0.0);
+      // the coarse correction injected into the base's pressure component
+      if (inj) bs[k].x = bs[k].x + double(__ldg(inj + (inj_perm ? p[k] : i)));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRes; ++k) {
+    int i = i0 + k * S;
+    if (i >= n) continue;
+    double v0 = double(z[k].x), v1 = double(z[k].y);
+    reinterpret_cast<double2 *>(out)[i] =
+        base ? make_double2(bs[k].x + v0, bs[k].y + v1) : make_double2(v0, v1);
+    if (outT) reinterpret_cast<T2 *>(outT)[i] = z[k];
+  }
+}
+
+template <int G, typename T, typename TV = T>
+__device__ __forceinline__ void k_jacobi_pre_b(int bx, int gx, int n, const int *__restrict__ rowptr,
+                                                       const int *__restrict__ col,
+                                                       const TV *__restrict__ val,
+                                                       const T *__restrict__ d,
+                                                       const T *__restrict__ b, T *__restrict__ x,
+                                                       T *__restrict__ r) {
+  int t = bx * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  // four independent accumulators, as in row_dot
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int e = e0 + lane;
+  for (; e + 3 * G < e1; e += 4 * G) {
+    int c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
+        c3 = __ldg(col + e + 3 * G);
+    T v0 = ldv<T>(val + e), v1 = ldv<T>(val + e + G), v2 = ldv<T>(val + e + 2 * G),
+      v3 = ldv<T>(val + e + 3 * G);
+    s0 = fma(v0, __ldg(b + c0) * __ldg(d + c0), s0);
+    s1 = fma(v1, __ldg(b + c1) * __ldg(d + c1), s1);
+    s2 = fma(v2, __ldg(b + c2) * __ldg(d + c2), s2);
+    s3 = fma(v3, __ldg(b + c3) * __ldg(d + c3), s3);
+  }
+  for (; e < e1; e += G) {
+    int c0 = __ldg(col + e);
+    s0 = fma(ldv<T>(val + e), __ldg(b + c0) * __ldg(d + c0), s0);
+  }
+  T s = (s0 + s1) + (s2 + s3);
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) {
+    T bi = b[i];
+    x[i] = bi * d[i];
+    r[i] = bi - s;
+  }
+}
+
+template <int G, typename T, typename TV = T>
+__device__ __forceinline__ void k_jacobi_sweep_b(int bx, int gx, int n, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         const TV *__restrict__ val,
+                                                         const T *__restrict__ d,
+                                                         const T *__restrict__ b,
+                                                         const T *__restrict__ x,
+                                                         T *__restrict__ tout) {
+  int t = bx * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  T s = row_dot<G, T, TV>(e0, e1, lane, col, val, x);
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) tout[i] = fma(b[i] - s, d[i], x[i]);
+}
+
+template <int G, typename T, typename TV = T>
+__device__ __forceinline__ void k_csr_mv_b(int bx, int gx, int n, const int *__restrict__ rowptr,
+                                                   const int *__restrict__ col,
+                                                   const TV *__restrict__ val,
+                                                   const T *__restrict__ x, T *__restrict__ y,
+                                                   int add) {
+  int t = bx * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  T s = row_dot<G, T, TV>(e0, e1, lane, col, val, x);
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) y[i] = add ? y[i] + s : s;
+}
+
+template <typename T>
+__device__ __forceinline__ void k_dense_mv_b(int bx, int gx, int n, const double *__restrict__ inv, const T *__restrict__ b,
+                           T *__restrict__ x) {
+  int w = (bx * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n) return;   // whole warps leave together
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s = fma(inv[(size_t)w * n + j], double(b[j]), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[w] = T(s);
+}
+
+template <typename T>
+__device__ __forceinline__ void k_gs_c_b(int bx, int gx, int r0, int r1, const int *__restrict__ rowptr,
+                                                 const int *__restrict__ colp,
+                                                 const T *__restrict__ pv,
+                                                 const T *__restrict__ dinv,
+                                                 const T *__restrict__ b, T *x) {
+  int q = r0 + bx * blockDim.x + threadIdx.x;
+  if (q >= r1) return;
+  int e = __ldcs(rowptr + q), e1 = __ldcs(rowptr + q + 1);
+  constexpr int kB = 8;
+  int c[kB];
+  T v[kB];
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    bool in = e + k < e1;
+    c[k] = in ? __ldcs(colp + e + k) : 0;
+    v[k] = in ? __ldcs(pv + e + k) : T(0);
+  }
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int k = 0; k < kB; k += 2) {
+    if (e + k < e1) s0 = fma(v[k], x[c[k]], s0);
+    if (e + k + 1 < e1) s1 = fma(v[k + 1], x[c[k + 1]], s1);
+  }
+  for (e += kB; e < e1; ++e) s0 = fma(__ldcs(pv + e), x[__ldcs(colp + e)], s0);
+  T s = s0 + s1;
+  T di = dinv[q];
+  if (di != T(0)) x[q] = fma(b[q] - s, di, x[q]);
+}
+
+template <typename T>
+__device__ __forceinline__ void k_gs_c_first_b(int bx, int gx, int r0, int r1, const T *__restrict__ dinv, const T *__restrict__ b,
+                             T *__restrict__ x) {
+  int q = r0 + bx * blockDim.x + threadIdx.x;
+  if (q >= r1) return;
+  T di = dinv[q];
+  x[q] = di != T(0) ? fma(b[q] - T(0), di, T(0)) : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void k_gs_c_w_b(int bx, int gx, int r0, int r1, const int *__restrict__ rowptr,
+                                                   const int *__restrict__ colp,
+                                                   const T *__restrict__ pv,
+                                                   const T *__restrict__ dinv,
+                                                   const T *__restrict__ b, T *x) {
+  row_c_w<T, false>(bx, r0, r1, rowptr, colp, pv, dinv, b, x, nullptr);
+}
+
+template <typename T>
+__device__ __forceinline__ void k_resid_c_w_b(int bx, int gx, int r0, int r1, const int *__restrict__ rowptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ pv,
+                                                      const T *__restrict__ b, T *x, T *r) {
+  row_c_w<T, true>(bx, r0, r1, rowptr, colp, pv, nullptr, b, x, r);
+}
+
+template <typename T>
+__device__ __forceinline__ void k_resid_c_b(int bx, int gx, int r0, int r1, const int *__restrict__ rowptr,
+                                                    const int *__restrict__ colp,
+                                                    const T *__restrict__ pv,
+                                                    const T *__restrict__ b,
+                                                    const T *__restrict__ x, T *__restrict__ r) {
+  int q = r0 + bx * blockDim.x + threadIdx.x;
+  if (q >= r1) return;
+  int e = __ldcs(rowptr + q), e1 = __ldcs(rowptr + q + 1);
+  constexpr int kB = 8;
+  int c[kB];
+  T v[kB];
+#pragma unroll
+  for (int k = 0; k < kB; ++k) {
+    bool in = e + k < e1;
+    c[k] = in ? __ldcs(colp + e + k) : 0;
+    v[k] = in ? __ldcs(pv + e + k) : T(0);
+  }
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int k = 0; k < kB; k += 2) {
+    if (e + k < e1) s0 = fma(v[k], __ldg(x + c[k]), s0);
+    if (e + k + 1 < e1) s1 = fma(v[k + 1], __ldg(x + c[k + 1]), s1);
+  }
+  for (e += kB; e < e1; ++e) s0 = fma(__ldcs(pv + e), __ldg(x + __ldcs(colp + e)), s0);
+  r[q] = b[q] - (s0 + s1);
+}
+
+__device__ __forceinline__ void k_inject_f32_b(int bx, int gx, int n, const float *xp, float *zf, const int *imap) {
+  int i = bx * blockDim.x + threadIdx.x;
+  if (i < n) zf[2 * i] += xp[imap ? __ldg(imap + i) : i];
+}
+
+template <int NV, bool SELF>
+__device__ __forceinline__ void k_multidot_b(int bx, int gx, long long N, const double *__restrict__ V,
+                                                     long long ldv,
+                                                     const double *__restrict__ w,
+                                                     double *__restrict__ part, int part_off,
+                                                     const double *__restrict__ gate) {
+  if (gate && *gate == 0.0) return;
+  double acc[NV];
+  double accw = 0.0;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  const long long N2 = N >> 1;   // double2 elements
+  const double2 *w2 = reinterpret_cast<const double2 *>(w);
+  const long long stride = (long long)gx * blockDim.x;
+  long long i = (long long)bx * blockDim.x + threadIdx.x;
+  for (; i + stride < N2; i += 2 * stride) {
+    double2 wa = __ldg(w2 + i), wb = __ldg(w2 + i + stride);
+    double2 va[NV], vb[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double2 *v2 = reinterpret_cast<const double2 *>(V + k * ldv);
+      va[k] = __ldg(v2 + i);
+      vb[k] = __ldg(v2 + i + stride);
+    }
+    if (SELF) {
+      accw = fma(wa.x, wa.x, accw); accw = fma(wa.y, wa.y, accw);
+      accw = fma(wb.x, wb.x, accw); accw = fma(wb.y, wb.y, accw);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      acc[k] = fma(va[k].x, wa.x, acc[k]); acc[k] = fma(va[k].y, wa.y, acc[k]);
+      acc[k] = fma(vb[k].x, wb.x, acc[k]); acc[k] = fma(vb[k].y, wb.y, acc[k]);
+    }
+  }
+  if (i < N2) {
+    double2 wa = __ldg(w2 + i);
+    if (SELF) { accw = fma(wa.x, wa.x, accw); accw = fma(wa.y, wa.y, accw); }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double2 va = __ldg(reinterpret_cast<const double2 *>(V + k * ldv) + i);
+      acc[k] = fma(va.x, wa.x, acc[k]); acc[k] = fma(va.y, wa.y, acc[k]);
+    }
+  }
+  constexpr int NS = NV + (SELF ? 1 : 0);
+  __shared__ double sh[kBlock / 32][kDotVec + 1];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    double v = k < NV ? acc[k] : accw;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    int k = threadIdx.x;
+    double v = 0.0;
+    for (int q = 0; q < kBlock / 32; ++q) v += sh[q][k];
+    part[(size_t)bx * 32 + (k == NV ? 31 : part_off + k)] = v;
+  }
+}
+
+__device__ __forceinline__ void k_dot_final_b(int bx, int gx, const double *part, int nblocks, int nv,
+                                                   double *dots, double *H, int m, int j,
+                                                   int mode, double *scal, double reorth) {
+  if (mode == 4 && scal[4] == 0.0) return;
+  __shared__ double sh[8][32];
+  int k = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  bool self = mode >= 3;
+  bool active = k < nv || (self && k == 31);
+  double v = 0.0;
+  if (active)
+    for (int b = grp; b < nblocks; b += 8) v += part[(size_t)b * 32 + k];
+  sh[grp][k] = v;
+  __syncthreads();
+  if (grp != 0) return;
+  v = 0.0;
+  for (int q = 0; q < 8; ++q) v += sh[q][k];
+  if (mode == 2) {
+    if (k == 0) { v = sqrt(v); dots[0] = v; H[(size_t)(j + 1) * m + j] = v; }
+    return;
+  }
+  if (k < nv) {
+    dots[k] = v;
+    if (mode != 0) H[(size_t)k * m + j] += v;
+  }
+  if (!self) return;
+  double hh = k < nv ? v * v : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+  double ww = __shfl_sync(0xffffffffu, v, 31);
+  if (k != 0) return;
+  double b2 = ww - hh;
+  if (mode == 3 && (reorth >= 1.0 || b2 < reorth * ww)) { scal[4] = 1.0; return; }
+  double beta = sqrt(b2 > 0.0 ? b2 : 0.0);
+  if (mode == 3) scal[4] = 0.0;
+  H[(size_t)(j + 1) * m + j] = beta;
+  scal[2] = beta;
+}
+
+__device__ __forceinline__ void k_project_b(int bx, int gx, long long N, const double *__restrict__ V,
+                                                    long long ldv, int nv,
+                                                    const double *__restrict__ c,
+                                                    double *__restrict__ w,
+                                                    double *__restrict__ out,
+                                                    const double *__restrict__ scal, int pass) {
+  __shared__ double cs[32];
+  __shared__ double rb;
+  __shared__ int fin;
+  if (threadIdx.x == 0) {
+    bool again = scal[4] != 0.0;
+    fin = pass == 0 ? (again ? 0 : 1) : (again ? 1 : -1);
+    double b = scal[2];
+    rb = b != 0.0 ? 1.0 / b : 0.0;
+  }
+  if (threadIdx.x < nv) cs[threadIdx.x] = -c[threadIdx.x];
+  __syncthreads();
+  if (fin < 0) return;
+  for (long long i = (long long)bx * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gx * blockDim.x) {
+    double acc = w[i];
+    for (int k = 0; k < nv; ++k) acc = fma(cs[k], V[k * ldv + i], acc);
+    if (fin) out[i] = acc * rb;
+    else w[i] = acc;
+  }
+}
+
+__device__ __forceinline__ void k_multi_axpy_b(int bx, int gx, long long N, const double *__restrict__ V,
+                                                       long long ldv, int nv,
+                                                       const double *__restrict__ c, double sign,
+                                                       double *__restrict__ w) {
+  __shared__ double cs[32];
+  if (threadIdx.x < nv) cs[threadIdx.x] = sign * c[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)bx * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gx * blockDim.x) {
+    double acc = w[i];
+    for (int k = 0; k < nv; ++k) acc += cs[k] * V[k * ldv + i];
+    w[i] = acc;
+  }
+}
+
+__device__ __forceinline__ void k_scale_b(int bx, int gx, long long N, const double *x, const double *alpha, int invert, double *y) {
+  __shared__ double sa;
+  if (threadIdx.x == 0) {
+    double a = *alpha;
+    sa = invert ? (a != 0.0 ? 1.0 / a : 0.0) : a;
+  }
+  __syncthreads();
+  long long i = (long long)bx * blockDim.x + threadIdx.x;
+  if (i < N) y[i] = x[i] * sa;
+}
+
+__device__ __forceinline__ void k_givens_b(int bx, int gx, double *H, double *cs, double *sn, double *g, int m, int j,
+                         double *res_out) {
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < j; ++i) {
+    double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+    H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+    H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+  }
+  double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+  double r = sqrt(a * a + c * c);
+  if (r == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+  else { cs[j] = a / r; sn[j] = c / r; }
+  H[(size_t)j * m + j] = r;
+  H[(size_t)(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  *res_out = fabs(g[j + 1]);
+}
+
+__device__ __forceinline__ void k_backsub_b(int bx, int gx, const double *H, const double *g, int m, int jend, double *y) {
+  if (threadIdx.x != 0) return;
+  for (int i = jend - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int k = i + 1; k < jend; ++k) s -= H[(size_t)i * m + k] * y[k];
+    double d = H[(size_t)i * m + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+__device__ __forceinline__ void k_init_g_b(int bx, int gx, double *g, int m, const double *beta) {
+  int i = threadIdx.x;
+  if (i <= m) g[i] = i == 0 ? *beta : 0.0;
+}
+
+__device__ __forceinline__ void k_sqrt_inplace_b(int bx, int gx, double *v) { v[0] = sqrt(v[0]); }
+
+}  // namespace dp

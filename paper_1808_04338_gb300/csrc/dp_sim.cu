@@ -14,7 +14,6 @@
 
 #include "dp_internal.h"
 
-struct dp_sim : dp::Sim {};
 
 namespace dp {
 
@@ -310,13 +309,37 @@ static int copy_state(dp_sim *s, const double *p, const double *sw, const double
   return DP_OK;
 }
 
+namespace dp {
+
 // A new old time level starts a new timestep of Algorithm 1: the Newton
 // counters that the forcing terms use start again.
-static void new_timestep(Sim *s) {
+void new_timestep(Sim *s) {
   s->newton_iter = 0;
   s->prev_res = 0.0;
   s->have_lq = false;
 }
+
+// The start of a timestep: the wells back on their own controls, x^n saved,
+// the Newton counters reset.
+int timestep_begin(Sim *s) {
+  if (s->well_limits) DP_TRY(phys_well_controls(s, true));
+  DP_TRY(phys_save_old(s));
+  new_timestep(s);
+  return DP_OK;
+}
+
+// The old time level copied back into the iterate (a failed timestep).
+int timestep_restore(Sim *s) {
+  size_t nc8 = (size_t)s->ph.nc * 8;
+  DP_CUDA(s, cudaMemcpyAsync(s->p, s->pn, nc8, cudaMemcpyDeviceToDevice, s->stream));
+  DP_CUDA(s, cudaMemcpyAsync(s->sw, s->swn, nc8, cudaMemcpyDeviceToDevice, s->stream));
+  if (s->ph.nw)
+    DP_CUDA(s, cudaMemcpyAsync(s->bhp, s->bhpn, (size_t)s->ph.nw * 8, cudaMemcpyDeviceToDevice,
+                               s->stream));
+  return DP_OK;
+}
+
+}  // namespace dp
 
 extern "C" int sim_set_state(dp_sim *s, const double *p, const double *sw, const double *bhp) {
   DP_TRY(copy_state(s, p, sw, bhp, cudaMemcpyDefault));
@@ -384,15 +407,14 @@ extern "C" int sim_get_norms(dp_sim *s, double *out8) {
   return DP_OK;
 }
 
-extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
-  if (!s) return DP_EINVAL;
-  DP_TRY(unusable(s));
-  if (!s->assembled) { s->fail(DP_EINVAL, "sim_solve_step before sim_assemble"); return DP_EINVAL; }
-  DP_TRY(read_norms(s));
-  double eta = forcing(s, s->last_norms[0]);
-  cudaEvent_t e0, e1, e2;
-  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
-  cudaEventRecord(e0, s->stream);
+namespace dp {
+
+// The first part of a linear solve of Algorithm 1 at the assembled iterate:
+// the forcing term, the decoupling (with the Schur option, the reduction
+// first), the ILU(0) factorisation and the AMG set-up or value refresh.
+int solve_prepare(Sim *s, double *eta, bool norms_current) {
+  if (!norms_current) DP_TRY(read_norms(s));
+  *eta = forcing(s, s->last_norms[0]);
   {
     Range range("decouple");
     if (s->opt.schur) DP_TRY(phys_schur_reduce(s));
@@ -413,37 +435,32 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
     DP_TRY(l0_refresh(s, coarse));
     if (coarse) DP_TRY(cluster_refresh(s));
   }
-  cudaEventRecord(e1, s->stream);
-  int it = 0;
-  double rr = 0.0;
-  int rc;
-  {
-    Range range("fgmres");
-    rc = fgmres(s, eta, &it, &rr);
+  return DP_OK;
+}
+
+// After FGMRES returned rc (DP_OK or DP_ELINEAR) with `it` iterations and
+// relative residual rr: the update (none after DP_ELINEAR), the linear
+// residual of the forcing terms 1-2, stream-ordered.
+int solve_update(Sim *s, int rc) {
+  if (rc != DP_OK) return DP_OK;
+  if (s->opt.schur) DP_TRY(phys_schur_back(s));
+  if (s->opt.eta_mode == 1 || s->opt.eta_mode == 2) {
+    if (!s->lq) s->lq = (double *)dalloc(s, (size_t)s->ph.nb * 16);
+    if (!s->lq) { s->fail(DP_ENOMEM, "allocation of the linear residual failed"); return DP_ENOMEM; }
+    DP_TRY(lin_residual(s));
   }
-  if (rc == DP_OK) {   // a failed linear solve makes no update
-    if (s->opt.schur) rc = phys_schur_back(s);
-    bool lin = s->opt.eta_mode == 1 || s->opt.eta_mode == 2;
-    if (rc == DP_OK && lin) {
-      if (!s->lq) s->lq = (double *)dalloc(s, (size_t)s->ph.nb * 16);
-      rc = s->lq ? lin_residual(s) : DP_ENOMEM;
-      if (rc == DP_ENOMEM) s->fail(DP_ENOMEM, "allocation of the linear residual failed");
-    }
-    if (rc == DP_OK) rc = phys_update(s);
-  }
-  cudaEventRecord(e2, s->stream);
-  cudaError_t se = cudaStreamSynchronize(s->stream);
-  float ms1 = 0.f, ms2 = 0.f;
-  cudaEventElapsedTime(&ms1, e0, e1);
-  cudaEventElapsedTime(&ms2, e1, e2);
-  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
-  DP_CUDA(s, se);
-  if (rc != DP_OK && rc != DP_ELINEAR) return rc;
+  return phys_update(s);
+}
+
+// The bookkeeping of a finished solve (after the stream has synchronised):
+// statistics, and on success the Newton counters of the forcing terms.
+int solve_finish(Sim *s, int rc, int it, double rr, double eta, float ms_setup, float ms_solve,
+                 dp_stats *st) {
   s->assembled = false;
   dp_stats &L = s->last;
   L.linear_iters = it; L.lin_relres = rr; L.eta = eta;
   L.amg_levels = (int)s->lev.size(); L.converged = rc == DP_OK;
-  L.ms_setup = ms1; L.ms_solve = ms2;
+  L.ms_setup = ms_setup; L.ms_solve = ms_solve;
   if (st) *st = L;
   if (rc == DP_ELINEAR) {
     s->fail(DP_ELINEAR, "FGMRES did not reach the forcing term; no update was made");
@@ -457,13 +474,44 @@ extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
   return DP_OK;
 }
 
+}  // namespace dp
+
+extern "C" int sim_solve_step(dp_sim *s, dp_stats *st) {
+  if (!s) return DP_EINVAL;
+  DP_TRY(unusable(s));
+  if (!s->assembled) { s->fail(DP_EINVAL, "sim_solve_step before sim_assemble"); return DP_EINVAL; }
+  cudaEvent_t e0, e1, e2;
+  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+  cudaEventRecord(e0, s->stream);
+  double eta = 0.0;
+  int rc = solve_prepare(s, &eta);
+  cudaEventRecord(e1, s->stream);
+  int it = 0;
+  double rr = 0.0;
+  if (rc == DP_OK) {
+    Range range("fgmres");
+    rc = fgmres(s, eta, &it, &rr);
+  }
+  if (rc == DP_OK || rc == DP_ELINEAR) {
+    int ru = solve_update(s, rc);
+    if (ru != DP_OK) rc = ru;
+  }
+  cudaEventRecord(e2, s->stream);
+  cudaError_t se = cudaStreamSynchronize(s->stream);
+  float ms1 = 0.f, ms2 = 0.f;
+  cudaEventElapsedTime(&ms1, e0, e1);
+  cudaEventElapsedTime(&ms2, e1, e2);
+  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+  DP_CUDA(s, se);
+  if (rc != DP_OK && rc != DP_ELINEAR) return rc;
+  return solve_finish(s, rc, it, rr, eta, ms1, ms2, st);
+}
+
 extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
   if (!s || !(dt > 0.0)) return DP_EINVAL;
   DP_TRY(unusable(s));
   Range range("timestep");
-  if (s->well_limits) DP_TRY(phys_well_controls(s, true));
-  DP_TRY(phys_save_old(s));
-  new_timestep(s);
+  DP_TRY(timestep_begin(s));
   int lin = 0;
   bool conv = false, lin_fail = false;
   double res0 = 0.0, res = 0.0, ms_setup = 0.0, ms_solve = 0.0;
@@ -489,12 +537,7 @@ extern "C" int sim_advance(dp_sim *s, double dt, dp_stats *st) {
   L.ms_setup = ms_setup; L.ms_solve = ms_solve;
   if (st) *st = L;
   if (!conv) {
-    size_t nc8 = (size_t)s->ph.nc * 8;
-    DP_CUDA(s, cudaMemcpyAsync(s->p, s->pn, nc8, cudaMemcpyDeviceToDevice, s->stream));
-    DP_CUDA(s, cudaMemcpyAsync(s->sw, s->swn, nc8, cudaMemcpyDeviceToDevice, s->stream));
-    if (s->ph.nw)
-      DP_CUDA(s, cudaMemcpyAsync(s->bhp, s->bhpn, (size_t)s->ph.nw * 8, cudaMemcpyDeviceToDevice,
-                                 s->stream));
+    DP_TRY(timestep_restore(s));
     DP_CUDA(s, cudaStreamSynchronize(s->stream));
     if (lin_fail) {
       s->fail(DP_ELINEAR, "a linear solve did not reach its forcing term; the old state is restored");

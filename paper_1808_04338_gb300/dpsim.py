@@ -172,6 +172,14 @@ def load():
     L.srv_get_state.argtypes = [P, I, P, P, P]
     L.srv_info.argtypes = [P, P]
     L.srv_destroy.argtypes = [P]
+    L.batch_create.argtypes = [P, I, P, P]
+    L.batch_advance.argtypes = [P, P, P, P]
+    L.batch_destroy.argtypes = [P]
+    L.batch_destroy.restype = None
+    L.batch_last_error.argtypes = [P]
+    L.batch_last_error.restype = C.c_char_p
+    L.batch_launch_count.argtypes = [P]
+    L.batch_launch_count.restype = C.c_int64
     L.dp_residual_norms_noalloc.argtypes = [C.POINTER(dp_grid), C.POINTER(dp_fluid), P, P, I, P,
                                             P, P, D, P, P, C.c_char_p, C.c_size_t]
     _lib = L
@@ -243,6 +251,52 @@ def advance_many(sims, dts, threads=0):
     rc = load().sim_advance_many(C.cast(H, C.c_void_p), n, C.cast(D, C.c_void_p), int(threads),
                                  C.cast(st, C.c_void_p), C.cast(rs, C.c_void_p))
     return rc, [st[k] for k in range(n)], [rs[k] for k in range(n)]
+
+
+class Batch:
+    """Realisations advanced in lockstep by one batched engine (batch_* in
+    include/dpsim.h): one launch per phase of each FGMRES iteration over all
+    of them.  The realisations must outlive the batch."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.sims = list(sims)
+        n = len(self.sims)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        H = (C.c_void_p * max(n, 1))(*[s.h.value for s in self.sims])
+        h = C.c_void_p()
+        rc = load().batch_create(C.cast(H, C.c_void_p), n, C.c_void_p(self.stream.cuda_stream),
+                                 C.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"batch_create failed ({rc})")
+        self.h = h
+
+    def advance(self, dts):
+        """One timestep of every realisation; returns (rc, stats, status)."""
+        n = len(self.sims)
+        D = (C.c_double * max(n, 1))(*[float(d) for d in dts])
+        st = (dp_stats * max(n, 1))()
+        rs = (C.c_int32 * max(n, 1))()
+        rc = load().batch_advance(self.h, C.cast(D, C.c_void_p), C.cast(st, C.c_void_p),
+                                  C.cast(rs, C.c_void_p))
+        if rc < 0 and rc not in (DP_ENEWTON, DP_ELINEAR):
+            msg = load().batch_last_error(self.h)
+            raise RuntimeError(f"batch_advance failed ({rc}): {msg.decode() if msg else ''}")
+        return rc, [st[k] for k in range(n)], [rs[k] for k in range(n)]
+
+    def launch_count(self):
+        return load().batch_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class dp_run_stats(C.Structure):

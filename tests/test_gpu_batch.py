@@ -85,3 +85,85 @@ def test_owned_streams_are_distinct():
     assert len({s.h.value for s in ss}) == 40
     for s in ss:
         s.close()
+
+
+def _batch_run(members, opts, steps, owned=True):
+    """Each member advanced `steps` timesteps by one lockstep batch; returns
+    per step [(status, newton, linear, state)] and the batch's launch count."""
+    import torch
+    sims = [gpu().Sim(p, opts, stream=torch.cuda.Stream()) for p in members]
+    b = gpu().Batch(sims)
+    out = []
+    for _ in range(steps):
+        rc, stats, status = b.advance([p.dt for p in members])
+        out.append([(status[k], stats[k].newton_iters, stats[k].linear_iters, s.get_state())
+                    for k, s in enumerate(sims)])
+    n = b.launch_count()
+    b.close()
+    for s in sims:
+        s.close()
+    return out, n
+
+
+def _alone_run(members, opts, steps):
+    import torch
+    out = [[] for _ in range(steps)]
+    for prob in members:
+        s = gpu().Sim(prob, opts, stream=torch.cuda.Stream())
+        for t in range(steps):
+            rc, st = s.advance(prob.dt)
+            out[t].append((rc, st.newton_iters, st.linear_iters, s.get_state()))
+        s.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_batch_equals_alone_bit_for_bit(precision):
+    """The lockstep batch (one launch per phase over all members' tiles)
+    gives every member exactly what sim_advance gives it alone: the same
+    codes, Newton and FGMRES counts and states, bit for bit, over two
+    timesteps (the second reuses the AMG hierarchy); a batch of one gives
+    the same too."""
+    members = [di.ensemble_member(r) for r in (0, 7, 14, 21, 28, 3, 10, 17)]
+    opts = gpu().options("report", precision=precision)
+    alone = _alone_run(members, opts, 2)
+    mix, launches = _batch_run(members, opts, 2)
+    single, _ = _batch_run(members[3:4], opts, 2)
+    for t in range(2):
+        for k, (a, m) in enumerate(zip(alone[t], mix[t])):
+            assert a[0] == m[0] == 0, (t, k)
+            assert a[1:3] == m[1:3], (t, k, a[1:3], m[1:3])
+            for x, y in zip(a[3], m[3]):
+                np.testing.assert_array_equal(x, y)
+        for x, y in zip(single[t][0][3], mix[t][3][3]):
+            np.testing.assert_array_equal(x, y)
+    assert launches > 0
+
+
+def test_batch_fp_states_match_the_oracle():
+    """The batched members in parity mode's tolerances against the FP64
+    oracle after one timestep (FP32 preconditioner, fixed forcing term)."""
+    members = [di.ensemble_member(r) for r in (0, 5)]
+    opts = gpu().options("parity", precision=1, amg_gs_levels=1)
+    mix, _ = _batch_run(members, opts, 1)
+    for k, prob in enumerate(members):
+        o = OracleSim(prob, oracle_options("parity", amg_gs_levels=1))
+        assert o.advance(prob.dt)[0] == 0
+        po, so, bo = o.get_state()
+        pg, sg, bg = mix[0][k][3]
+        assert np.abs(pg - po).max() <= 1e-8 * np.abs(po).max()
+        assert np.abs(sg - so).max() <= 1e-8
+        assert np.abs(bg - bo).max() <= 1e-8 * np.abs(bo).max()
+
+
+def test_batch_rejects_unsupported_members():
+    """FP64 preconditioner or Gauss-Seidel below level 0: not batched."""
+    import ctypes as C
+    prob = di.ensemble_member(0)
+    L = gpu().load()
+    for kw in (dict(precision=0), dict(precision=1, amg_gs_levels=30), dict(precision=1, precond=1)):
+        s = gpu().Sim(prob, gpu().options("report", **kw))
+        H = (C.c_void_p * 1)(s.h.value)
+        h = C.c_void_p()
+        assert L.batch_create(C.cast(H, C.c_void_p), 1, None, C.byref(h)) == gpu().DP_EINVAL, kw
+        s.close()
