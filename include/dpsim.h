@@ -272,9 +272,10 @@ int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t t
 /* Batched timesteps in lockstep (no counterpart in the paper; the batched
  * engine of many uneven-size realisations on one GPU).  A batch groups n
  * realisations created with the FP32 preconditioner (precision 1 or 2),
- * CPR-FPF (precond 2), l1-Jacobi below AMG level 0 (amg_gs_levels <= 1) and
- * equal gmres_restart and gmres_maxit; the realisations must outlive the
- * batch and must not be used by other calls while batch_advance runs.
+ * CPR-FPF (precond 2), l1-Jacobi below AMG level 0 (amg_gs_levels <= 1), the
+ * V-cycle outside the cluster kernel (cluster_rows < 0) and equal
+ * gmres_restart and gmres_maxit; the realisations must not be used by other
+ * calls while batch_advance runs, nor destroyed before it returns.
  * batch_advance does one timestep of each realisation k by dt[k] (Algorithm
  * 1, as sim_advance): every Newton iteration assembles and sets up each
  * realisation still iterating, then runs their FGMRES iterations together:
@@ -289,8 +290,9 @@ int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t t
  * realisations' own streams synchronised first.  stats[k], status[k] (may
  * be NULL) as sim_advance's; returns DP_OK when all succeeded, else the
  * first failing code.  batch_create returns DP_EINVAL for an unsupported or
- * repeated realisation; its device memory comes from the first
- * realisation's allocator. */
+ * repeated realisation.  The batch's own device memory (work lists and
+ * argument records, a few bytes per tile) comes from cudaMalloc;
+ * batch_destroy touches neither the realisations nor the stream. */
 typedef struct dp_batch dp_batch;
 int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_batch **out);
 int batch_advance(dp_batch *batch, const double *dt, dp_stats *stats, int32_t *status);

@@ -389,7 +389,8 @@ struct dp_batch {
   std::vector<cudaStream_t> own_streams;   // each member's stream, restored after a call
   int nm = 0, mres = 30, maxit = 300;
   bool built = false;
-  // device memory (through member 0's allocator)
+  // the batch's own device memory (cudaMalloc: it never touches a member's
+  // allocator, so that it can be released after its members)
   std::vector<void *> blocks;
   // activity masks: the Arnoldi step's, and two for the restart prologue
   unsigned char *act = nullptr, *act_a = nullptr, *act_b = nullptr, *act_all = nullptr;
@@ -417,8 +418,9 @@ struct dp_batch {
 namespace dp {
 
 static void *balloc(dp_batch *b, size_t bytes) {
-  void *p = dalloc(b->m[0], bytes);
-  if (p) b->blocks.push_back(p);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  b->blocks.push_back(p);
   return p;
 }
 
@@ -515,6 +517,8 @@ static const char *unsupported(const Sim *s, const Sim *s0) {
   if (o.precond != 2) return "the batch needs the CPR-FPF preconditioner (precond 2)";
   if (o.precision < 1) return "the batch needs the FP32 preconditioner (precision 1 or 2)";
   if (o.amg_gs_levels > 1) return "the batch needs l1-Jacobi below AMG level 0 (amg_gs_levels <= 1)";
+  if (o.cluster_rows >= 0 && o.use_graphs)
+    return "the batch needs the V-cycle outside the cluster kernel (cluster_rows < 0)";
   if (o.gmres_restart != s0->opt.gmres_restart || o.gmres_maxit != s0->opt.gmres_maxit)
     return "the realisations of a batch need equal gmres_restart and gmres_maxit";
   if (s->amg_ready) {
@@ -642,7 +646,8 @@ static int one_phase(dp_batch *b, std::vector<Phase> *into, Phase *ph, int kind,
 // the whole plan: the Arnoldi step (as cpr_apply and arnoldi_step run it for
 // the FP32 preconditioner) and the pieces of the restart cycle
 static int build_plan(dp_batch *b) {
-  for (void *p : b->blocks) dfree(b->m[0], p);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ECUDA;
+  for (void *p : b->blocks) cudaFree(p);
   b->blocks.clear();
   b->step.clear();
   for (cudaGraphExec_t &g : b->graph)
@@ -1152,11 +1157,9 @@ extern "C" int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_bat
   for (int k = 0; k < n; ++k) b->m.push_back(static_cast<Sim *>(sims[k]));
   b->mres = b->m[0]->m;
   b->maxit = b->m[0]->opt.gmres_maxit;
-  Sim *s0 = b->m[0];
-  b->act_all = (unsigned char *)dalloc(s0, 4 * (size_t)n);
-  b->jend = (int *)dalloc(s0, 4 * (size_t)n);
-  b->gath = (double *)dalloc(s0, 32 * (size_t)n);
-  if (!b->act_all || !b->jend || !b->gath) {
+  if (cudaMalloc(&b->act_all, 4 * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&b->jend, 4 * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&b->gath, 32 * (size_t)n) != cudaSuccess) {
     batch_destroy(b);
     return DP_ENOMEM;
   }
@@ -1174,18 +1177,17 @@ extern "C" int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_bat
   return DP_OK;
 }
 
+// Touches neither the members nor the batch's stream (either may be gone
+// already); cudaFree waits for the device.
 extern "C" void batch_destroy(dp_batch *b) {
   if (!b) return;
-  if (b->stream) cudaStreamSynchronize(b->stream);
   for (cudaGraphExec_t &g : b->graph)
     if (g) cudaGraphExecDestroy(g);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  if (!b->m.empty()) {
-    for (void *p : b->blocks) dfree(b->m[0], p);
-    dfree(b->m[0], b->act_all);
-    dfree(b->m[0], b->jend);
-    dfree(b->m[0], b->gath);
-  }
+  for (void *p : b->blocks) cudaFree(p);
+  if (b->act_all) cudaFree(b->act_all);
+  if (b->jend) cudaFree(b->jend);
+  if (b->gath) cudaFree(b->gath);
   if (b->h_gath) cudaFreeHost(b->h_gath);
   if (b->h_norms) cudaFreeHost(b->h_norms);
   delete b;

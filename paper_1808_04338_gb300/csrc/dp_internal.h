@@ -42,6 +42,7 @@ struct Phys {
   double mu_o, mu_w, c_o, c_w, rho_o_ref, rho_w_ref, p_ref, swc, sor, g;
   double inv_span, inv_mu_o, inv_mu_w;
   double sigma, c_rock, p_ref_rock;
+  double drho_o, drho_w;          // rho_ref c per phase (the density slopes)
   int pc_n[2];                    // capillary tables: points per continuum
   const double *pc_tab[2];        //   device (s_w, p_cow) pairs, or null
 };
@@ -191,6 +192,9 @@ int ilu_apply(Sim *s, const double *r, double *z);
 int bsr_spmv(Sim *s, const double *x, double *y);                 // y = A x
 int bsr_residual(Sim *s, const double *b, const double *x, double *r);  // r = b - A x
 int lin_residual(Sim *s);          // s->lq = R + A y, A the assembled Jacobian
+// tpos[e] = position of entry (j, i) for every entry (i, j) of a structurally
+// symmetric block pattern with sorted rows
+int block_tpos(Sim *s, int n, const int *rowptr, const int *col, int *tpos);
 int vcycle(Sim *s, int level, const double *b, double *x);
 int coarse_factor(Sim *s);
 int cpr_apply(Sim *s, const double *r, double *z);
@@ -250,7 +254,9 @@ struct Sim {
   double *p = nullptr, *sw = nullptr, *bhp = nullptr;
   double *pn = nullptr, *swn = nullptr, *bhpn = nullptr, *Mn = nullptr;
   double *R = nullptr, *bh = nullptr, *y = nullptr;
-  double *pr = nullptr;                              // cell properties, 7 x nc (SoA)
+  double *pr = nullptr;                              // cell properties, 8 x nc (SoA)
+  double *fconn = nullptr;   // per connection (3 faces a location, then its f-m link): F
+  int *atpos = nullptr;      // position of the transposed block of each Jacobian entry
   double *Macc = nullptr;                            // phase masses at the iterate, 2 x nc
   double dt = 1.0, inv_dt = 1.0;
   double *norm_part = nullptr;                       // reduction partials

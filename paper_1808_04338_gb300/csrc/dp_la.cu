@@ -419,6 +419,12 @@ __global__ void k_colour_maxlen(int n, const int *cstart_dev, int ncolour, const
 }
 
 
+int block_tpos(Sim *s, int n, const int *rowptr, const int *col, int *tpos) {
+  DP_LAUNCH(s, k_block_tpos, nblk(n), kBlock, 0, n, rowptr, col, tpos);
+  DP_CUDA(s, cudaGetLastError());
+  return DP_OK;
+}
+
 int ilu_setup(Sim *s) {
   int n = s->K.n;
   s->colour = (int *)dalloc(s, (size_t)n * 4);

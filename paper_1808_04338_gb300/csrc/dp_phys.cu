@@ -376,7 +376,10 @@ int phys_build_pattern(Sim *s) {
   }
   s->scol = (int *)dalloc(s, (size_t)nnz * 4);
   s->srowptr = (int *)dalloc(s, ((size_t)P.nb + 1) * 4);
-  if (!s->A.col || !s->A.val || !s->trans || !s->ap || !s->sval || !s->scol || !s->srowptr) {
+  s->atpos = (int *)dalloc(s, (size_t)nnz * 4);
+  s->fconn = (double *)dalloc(s, (size_t)P.nL * 64);
+  if (!s->A.col || !s->A.val || !s->trans || !s->ap || !s->sval || !s->scol || !s->srowptr ||
+      !s->atpos || !s->fconn) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
@@ -384,6 +387,7 @@ int phys_build_pattern(Sim *s) {
             d_pc_wi, np, d_pw_start, d_pw_cell, d_pw_wi, s->A.rowptr, s->A.col, s->A.diag,
             s->trans);
   DP_CUDA(s, cudaGetLastError());
+  DP_TRY(block_tpos(s, P.nb, s->A.rowptr, s->A.col, s->atpos));
   // the storage-order pattern of the Krylov operator's copy
   DP_LAUNCH(s, k_storage_len, nblk(P.nb), kBlock, 0, P.nb, P.nL, P.nc, s->A.rowptr, len);
   int snnz = 0;
@@ -401,8 +405,8 @@ int phys_build_pattern(Sim *s) {
 // ---------------------------------------------------------------- assembly
 
 // Cell properties stored structure-of-arrays, [k * nc + c]: rho_o, rho_w,
-// lam_o, lam_w, dlam_o, dlam_w, phi.  Evaluated once per cell so that the
-// rows that use a cell as a neighbour read them instead of re-evaluating.
+// lam_o, lam_w, dlam_o, dlam_w, phi, dphi.  Evaluated once per cell so that
+// the connections that use a cell read them instead of re-evaluating.
 
 __global__ void __launch_bounds__(kBlock) k_props(Phys P, const double *phi_f, const double *phi_m,
                                                   const double *p, const double *sw, double *pr) {
@@ -418,9 +422,11 @@ __global__ void __launch_bounds__(kBlock) k_props(Phys P, const double *phi_f, c
   pr[4 * n + c] = q.dlam[0];
   pr[5 * n + c] = q.dlam[1];
   pr[6 * n + c] = q.phi;
+  pr[7 * n + c] = q.dphi;
 }
 
-// The same values as props(): stored fields plus the constant derivatives.
+// The same values as props(): the stored fields, and the density slopes
+// rho_ref c formed once on the host (the same products props() forms).
 __device__ __forceinline__ void load_props(const Phys &P, const double *phi_f, const double *phi_m,
                                            const double *__restrict__ pr, int c, Props &q) {
   size_t n = (size_t)P.nc;
@@ -431,29 +437,101 @@ __device__ __forceinline__ void load_props(const Phys &P, const double *phi_f, c
   q.dlam[0] = pr[4 * n + c];
   q.dlam[1] = pr[5 * n + c];
   q.phi = pr[6 * n + c];
-  q.drho[0] = P.rho_o_ref * P.c_o;
-  q.drho[1] = P.rho_w_ref * P.c_w;
-  int loc = c >> 1;
-  double phi_ref = (c & 1) == 0 ? phi_f[loc] : phi_m[loc];
-  q.dphi = phi_ref * P.c_rock;
+  q.dphi = pr[7 * n + c];
+  q.drho[0] = P.drho_o;
+  q.drho[1] = P.drho_w;
 }
 
 struct AsmArgs {
   Phys P;
-  const int *rowptr, *col, *diag;
+  const int *rowptr, *col, *diag, *tpos;
   const double *trans, *phi_f, *phi_m, *pr;
   const double *p, *sw, *bhp, *Mn;
   const int *well_kind;
   const double *well_target;
   double *val, *R, *Macc;
+  double2 *fconn;
   double inv_dt;
 };
 
-// One thread per block row.  Threads [0, nL) take the fracture rows, [nL, nc)
-// the matrix rows and [nc, nb) the well rows, so that a warp holds rows of
-// one kind and equal length.  Cell rows: accumulation, then the connections
-// in increasing column order (fluxes, then perforations); well rows: the
-// rate or pressure constraint.
+// Connection c of the cell graph: c = 3 loc + axis for the face between
+// location loc and its neighbour along x, y or z (when there is one), c =
+// 3 nL + loc for the fracture-matrix link of loc.  The two cells a < b.
+__device__ __forceinline__ int conn_of(const Phys &P, int r, int d) {
+  int la = min(r, d) >> 1, lb = max(r, d) >> 1;
+  if (la == lb) return 3 * P.nL + la;
+  int diff = lb - la;
+  int axis = (diff == 1 && P.nx > 1) ? 0 : ((diff == P.nx && P.ny > 1) ? 1 : 2);
+  return 3 * la + axis;
+}
+
+__device__ __forceinline__ int find_entry(const int *__restrict__ rowptr,
+                                          const int *__restrict__ col, int r, int d) {
+  for (int e = rowptr[r], e1 = rowptr[r + 1]; e < e1; ++e)
+    if (col[e] == d) return e;
+  return -1;
+}
+
+// Each connection's flux once (face-based): one thread per connection a < b
+// evaluates the flux a -> b with the expressions and operand order of the
+// row-wise evaluation, writes the two off-diagonal blocks, dF/dx_b into row
+// a and -dF/dx_a into row b, and keeps F for the two rows' sums.  (The row
+// of b used to evaluate the same flux again from its side; the values are
+// the same, bit for bit: the same call with the same arguments.)
+template <bool GRAV, bool CAP>
+__global__ void __launch_bounds__(kBlock) k_conn_flux(AsmArgs a) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const Phys &P = a.P;
+  if (c >= 4 * P.nL) return;
+  int la, lb;
+  if (c < 3 * P.nL) {
+    la = c / 3;
+    int axis = c - 3 * la, i, j, k;
+    loc_ijk(P, la, i, j, k);
+    if (axis == 0) { if (i + 1 >= P.nx) return; lb = la + 1; }
+    else if (axis == 1) { if (j + 1 >= P.ny) return; lb = la + P.nx; }
+    else { if (k + 1 >= P.nz) return; lb = la + P.nx * P.ny; }
+  } else {
+    la = lb = c - 3 * P.nL;
+  }
+  int ca = 2 * la, cb = la == lb ? ca + 1 : 2 * lb;
+  int eab = find_entry(a.rowptr, a.col, ca, cb), eba = find_entry(a.rowptr, a.col, cb, ca);
+  if (eab < 0 || eba < 0) return;
+  Props qa, qb;
+  load_props(P, a.phi_f, a.phi_m, a.pr, ca, qa);
+  load_props(P, a.phi_f, a.phi_m, a.pr, cb, qb);
+  if (CAP) {
+    cap_pressure(P.pc_n[ca & 1], P.pc_tab[ca & 1], a.sw[ca], qa.pc, qa.dpc);
+    cap_pressure(P.pc_n[cb & 1], P.pc_tab[cb & 1], a.sw[cb], qb.pc, qb.dpc);
+  }
+  double gdz = 0.0;
+  if (GRAV) {
+    double dzab = 0.0;
+    if (la != lb) {
+      int ia, ja, ka, ib, jb, kb;
+      loc_ijk(P, la, ia, ja, ka);
+      loc_ijk(P, lb, ib, jb, kb);
+      dzab = depth(P, ka) - depth(P, kb);
+    }
+    gdz = P.g * dzab;
+  }
+  double F[2], dFa[4], dFb[4];
+  flux<GRAV, CAP>(a.trans[eab], gdz, a.p[ca], a.p[cb], qa, qb, F, dFa, dFb);
+  double *oab = a.val + 4 * (size_t)eab, *oba = a.val + 4 * (size_t)eba;
+  oab[0] = dFb[0]; oab[1] = dFb[1]; oab[2] = dFb[2]; oab[3] = dFb[3];
+  oba[0] = -dFa[0]; oba[1] = -dFa[1]; oba[2] = -dFa[2]; oba[3] = -dFa[3];
+  a.fconn[c] = make_double2(F[0], F[1]);
+}
+
+// One thread per block row, after k_conn_flux.  Threads [0, nL) take the
+// fracture rows, [nL, nc) the matrix rows and [nc, nb) the well rows, so
+// that a warp holds rows of one kind and equal length.  Cell rows:
+// accumulation, then the connections in increasing column order: a cell
+// neighbour d adds +F (d > r) or -F (d < r) of their connection to the
+// residual and minus the transposed block (d, r) to the diagonal block
+// (that block is -dF/dx_r written by k_conn_flux, so this adds exactly the
+// dF/dx_r the row-wise evaluation added); then the perforations.  Well
+// rows: the rate or pressure constraint.
 template <bool GRAV, bool CAP>
 __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,41 +555,20 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
     double r1 = (M[1] - a.Mn[2 * r + 1]) * a.inv_dt;
     double d0 = dM[0] * a.inv_dt, d1 = dM[1] * a.inv_dt;
     double d2 = dM[2] * a.inv_dt, d3 = dM[3] * a.inv_dt;
-    int ir = 0, jr = 0, kr = 0;
-    if (GRAV) loc_ijk(P, r >> 1, ir, jr, kr);
     for (int e = e0; e < e1; ++e) {
       int d = a.col[e];
       if (d == r) continue;
       double *off = a.val + 4 * (size_t)e;
       double T = a.trans[e];
       if (d < P.nc) {
-        double pd = a.p[d];
-        Props qd;
-        load_props(P, a.phi_f, a.phi_m, a.pr, d, qd);
-        if (CAP) cap_pressure(P.pc_n[d & 1], P.pc_tab[d & 1], a.sw[d], qd.pc, qd.dpc);
-        double gdz = 0.0;
-        if (GRAV) {
-          double dzab;
-          if ((r >> 1) == (d >> 1)) dzab = 0.0;
-          else {
-            int id, jd, kd;
-            loc_ijk(P, d >> 1, id, jd, kd);
-            dzab = r < d ? depth(P, kr) - depth(P, kd) : depth(P, kd) - depth(P, kr);
-          }
-          gdz = P.g * dzab;
-        }
-        double F[2], dFa[4], dFb[4];
-        if (r < d) {
-          flux<GRAV, CAP>(T, gdz, pc, pd, qc, qd, F, dFa, dFb);
-          r0 = r0 + F[0]; r1 = r1 + F[1];
-          d0 = d0 + dFa[0]; d1 = d1 + dFa[1]; d2 = d2 + dFa[2]; d3 = d3 + dFa[3];
-          off[0] = dFb[0]; off[1] = dFb[1]; off[2] = dFb[2]; off[3] = dFb[3];
-        } else {
-          flux<GRAV, CAP>(T, gdz, pd, pc, qd, qc, F, dFa, dFb);
-          r0 = r0 + (-F[0]); r1 = r1 + (-F[1]);
-          d0 = d0 + (-dFb[0]); d1 = d1 + (-dFb[1]); d2 = d2 + (-dFb[2]); d3 = d3 + (-dFb[3]);
-          off[0] = -dFa[0]; off[1] = -dFa[1]; off[2] = -dFa[2]; off[3] = -dFa[3];
-        }
+        double2 F = a.fconn[conn_of(P, r, d)];
+        int te = a.tpos[e];
+        if (te < 0) continue;
+        double2 t01 = *reinterpret_cast<const double2 *>(a.val + 4 * (size_t)te);
+        double2 t23 = *reinterpret_cast<const double2 *>(a.val + 4 * (size_t)te + 2);
+        if (r < d) { r0 = r0 + F.x; r1 = r1 + F.y; }
+        else { r0 = r0 + (-F.x); r1 = r1 + (-F.y); }
+        d0 = d0 + (-t01.x); d1 = d1 + (-t01.y); d2 = d2 + (-t23.x); d3 = d3 + (-t23.y);
       } else {
         int w = d - P.nc;
         double Q[2], dq[4], dqb[2];
@@ -671,16 +728,21 @@ int phys_assemble(Sim *s) {
   DP_LAUNCH(s, k_props, nblk(s->ph.nc), kBlock, 0, s->ph, s->phi_f, s->phi_m, s->p, s->sw, s->pr);
   AsmArgs a;
   a.P = s->ph;
-  a.rowptr = s->A.rowptr; a.col = s->A.col; a.diag = s->A.diag;
+  a.rowptr = s->A.rowptr; a.col = s->A.col; a.diag = s->A.diag; a.tpos = s->atpos;
   a.trans = s->trans; a.phi_f = s->phi_f; a.phi_m = s->phi_m; a.pr = s->pr; a.Macc = s->Macc;
   a.p = s->p; a.sw = s->sw; a.bhp = s->bhp; a.Mn = s->Mn;
   a.well_kind = s->well_kind; a.well_target = s->well_target;
   a.val = s->A.val; a.R = s->R;
+  a.fconn = reinterpret_cast<double2 *>(s->fconn);
   a.inv_dt = s->inv_dt;
   bool grav = s->ph.g != 0.0, cap = s->ph.pc_n[0] > 0 || s->ph.pc_n[1] > 0;
+  void (*k_conn_flux_sel)(AsmArgs) =
+      cap ? (grav ? k_conn_flux<true, true> : k_conn_flux<false, true>)
+          : (grav ? k_conn_flux<true, false> : k_conn_flux<false, false>);
   void (*k_assemble_sel)(AsmArgs) =
       cap ? (grav ? k_assemble<true, true> : k_assemble<false, true>)
           : (grav ? k_assemble<true, false> : k_assemble<false, false>);
+  DP_LAUNCH(s, k_conn_flux_sel, nblk(4LL * s->ph.nL), kBlock, 0, a);
   DP_LAUNCH(s, k_assemble_sel, nblk(s->ph.nb), kBlock, 0, a);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;

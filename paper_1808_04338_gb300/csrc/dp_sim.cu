@@ -184,6 +184,8 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   P.inv_mu_o = 1.0 / fluid->mu_o;
   P.inv_mu_w = 1.0 / fluid->mu_w;
   P.sigma = rock->sigma; P.c_rock = rock->c_rock; P.p_ref_rock = rock->p_ref;
+  P.drho_o = fluid->rho_o_ref * fluid->c_o;   // the products props() forms, once
+  P.drho_w = fluid->rho_w_ref * fluid->c_w;
   auto fail = [&](int rc) { sim_destroy(s); return rc; };
   for (int k = 0; k < 2; ++k) {
     P.pc_n[k] = fluid->pc_n[k];
@@ -252,7 +254,7 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   s->Mn = (double *)dalloc(s, 2 * nc8);
   s->R = (double *)dalloc(s, nb16); s->bh = (double *)dalloc(s, nb16);
   s->y = (double *)dalloc(s, nb16);
-  s->pr = (double *)dalloc(s, 7 * nc8);
+  s->pr = (double *)dalloc(s, 8 * nc8);
   s->Macc = (double *)dalloc(s, 2 * nc8);
   s->norm_blocks = std::min(nblk(P.nb), 1024);
   s->norm_part = (double *)dalloc(s, (size_t)s->norm_blocks * 64);

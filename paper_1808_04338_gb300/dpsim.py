@@ -270,6 +270,8 @@ class Batch:
         if rc != 0:
             raise RuntimeError(f"batch_create failed ({rc})")
         self.h = h
+        for s in self.sims:        # a member closed first closes the batch first
+            s._batches.append(self)
 
     def advance(self, dts):
         """One timestep of every realisation; returns (rc, stats, status)."""
@@ -441,6 +443,7 @@ class Sim:
             self._alloc = allocator
         else:
             self._alloc = TorchAllocator(torch.cuda.current_device()) if use_torch_alloc else None
+        self._batches = []
         h = C.c_void_p()
         rc = L.sim_create(C.byref(g), C.byref(r), C.byref(f), W, nw, C.byref(self.opts),
                           C.byref(self._alloc.struct) if self._alloc else None,
@@ -459,6 +462,8 @@ class Sim:
 
     def close(self):
         if getattr(self, "h", None):
+            for b in getattr(self, "_batches", []):
+                b.close()
             load().sim_destroy(self.h)
             self.h = None
 

@@ -125,7 +125,7 @@ def test_batch_equals_alone_bit_for_bit(precision):
     timesteps (the second reuses the AMG hierarchy); a batch of one gives
     the same too."""
     members = [di.ensemble_member(r) for r in (0, 7, 14, 21, 28, 3, 10, 17)]
-    opts = gpu().options("report", precision=precision)
+    opts = gpu().options("report", precision=precision, cluster_rows=-1)
     alone = _alone_run(members, opts, 2)
     mix, launches = _batch_run(members, opts, 2)
     single, _ = _batch_run(members[3:4], opts, 2)
@@ -144,7 +144,7 @@ def test_batch_fp_states_match_the_oracle():
     """The batched members in parity mode's tolerances against the FP64
     oracle after one timestep (FP32 preconditioner, fixed forcing term)."""
     members = [di.ensemble_member(r) for r in (0, 5)]
-    opts = gpu().options("parity", precision=1, amg_gs_levels=1)
+    opts = gpu().options("parity", precision=1, amg_gs_levels=1, cluster_rows=-1)
     mix, _ = _batch_run(members, opts, 1)
     for k, prob in enumerate(members):
         o = OracleSim(prob, oracle_options("parity", amg_gs_levels=1))
@@ -157,11 +157,13 @@ def test_batch_fp_states_match_the_oracle():
 
 
 def test_batch_rejects_unsupported_members():
-    """FP64 preconditioner or Gauss-Seidel below level 0: not batched."""
+    """FP64 preconditioner, Gauss-Seidel below level 0, ILU(0) alone or the
+    cluster kernel allowed: not batched."""
     import ctypes as C
     prob = di.ensemble_member(0)
     L = gpu().load()
-    for kw in (dict(precision=0), dict(precision=1, amg_gs_levels=30), dict(precision=1, precond=1)):
+    for kw in (dict(precision=0), dict(precision=1, amg_gs_levels=30), dict(precision=1, precond=1),
+               dict(precision=1)):   # the last: the default cluster_rows
         s = gpu().Sim(prob, gpu().options("report", **kw))
         H = (C.c_void_p * 1)(s.h.value)
         h = C.c_void_p()
