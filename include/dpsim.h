@@ -278,16 +278,18 @@ int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t t
  * calls while batch_advance runs, nor destroyed before it returns.
  * batch_advance does one timestep of each realisation k by dt[k] (Algorithm
  * 1, as sim_advance): every Newton iteration assembles and sets up each
- * realisation still iterating, then runs their FGMRES iterations together:
+ * realisation still iterating (up to 16 host threads, each realisation on
+ * the stream it was created with, so these must differ to overlap), then
+ * runs their FGMRES iterations together on `stream`:
  * every phase of the Arnoldi step (the ILU(0) sweeps of each colour, the
  * CPR stage residuals, each level of the V-cycle, the operator product, the
  * Gram-Schmidt passes, the Givens rotations) is one launch over a work list
  * of (realisation, block) tiles, in which each realisation runs the blocks
  * of its own launch; realisations that have converged drop out through a
  * device flag.  Each realisation's result is that of sim_advance on it
- * alone, bit for bit, whatever the other members of the batch.  All work
- * runs on `stream` (a cudaStream_t; NULL: the default stream), with the
- * realisations' own streams synchronised first.  stats[k], status[k] (may
+ * alone, bit for bit, whatever the other members of the batch.  `stream`:
+ * a cudaStream_t (NULL: the default stream); batch_advance returns after
+ * every stream involved has synchronised.  stats[k], status[k] (may
  * be NULL) as sim_advance's; returns DP_OK when all succeeded, else the
  * first failing code.  batch_create returns DP_EINVAL for an unsupported or
  * repeated realisation.  The batch's own device memory (work lists and

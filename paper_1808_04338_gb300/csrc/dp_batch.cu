@@ -1,16 +1,22 @@
 // Batched Newton steps of many realisations (batch_create / batch_advance,
 // include/dpsim.h).  The realisations advance in lockstep: each Newton
-// iteration assembles and sets up every realisation still iterating, then
-// runs their FGMRES iterations together, one launch per phase of the Arnoldi
-// step over a work list of (realisation, block) tiles.  A tile runs the
+// iteration assembles and sets up every realisation still iterating (a pool
+// of host threads, each realisation on its own stream), then runs their
+// FGMRES iterations together on the batch's stream, one launch per phase of
+// the Arnoldi step over a work list of (realisation, block) tiles.  A tile runs the
 // kernel body of dp_kernels.cuh with the block index and grid size of the
 // realisation's own launch, so every realisation computes exactly what it
 // computes alone (sim_advance), whatever else is in the batch.  A device
 // flag per realisation takes the ones that have converged out of the later
 // launches: their tiles return at once.
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "dp_internal.h"
@@ -386,7 +392,6 @@ enum Kind {
 struct dp_batch {
   std::vector<dp::Sim *> m;
   cudaStream_t stream = nullptr;
-  std::vector<cudaStream_t> own_streams;   // each member's stream, restored after a call
   int nm = 0, mres = 30, maxit = 300;
   bool built = false;
   // the batch's own device memory (cudaMalloc: it never touches a member's
@@ -413,6 +418,18 @@ struct dp_batch {
   cudaStream_t cap_stream = nullptr;
   std::string err;
   int64_t launches = 0;
+  // the per-realisation parts (assembly, set-up, update) run on the
+  // realisations' own streams from a pool of host threads
+  std::vector<cudaEvent_t> ev;   // per realisation: its set-up is queued
+  cudaEvent_t solved = nullptr;  // the batched FGMRES is queued
+  int device = 0;
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::function<void(int)> task;
+  int ntask = 0, generation = 0, busy = 0;
+  std::atomic<int> next{0};
+  bool quit = false;
 };
 
 namespace dp {
@@ -1140,6 +1157,48 @@ static int bfail(dp_batch *b, int rc, const std::string &msg) {
   return rc;
 }
 
+// The worker pool: run(fn, n) calls fn(0..n-1) on the workers (each index
+// once) and returns when all are done.
+static void worker_main(dp_batch *b) {
+  cudaSetDevice(b->device);
+  int seen = 0;
+  for (;;) {
+    std::function<void(int)> fn;
+    int n = 0;
+    {
+      std::unique_lock<std::mutex> lk(b->mu);
+      b->cv.wait(lk, [&] { return b->quit || b->generation != seen; });
+      if (b->quit) return;
+      seen = b->generation;
+      fn = b->task;
+      n = b->ntask;
+    }
+    for (;;) {
+      int k = b->next.fetch_add(1);
+      if (k >= n) break;
+      fn(k);
+    }
+    std::lock_guard<std::mutex> lk(b->mu);
+    if (--b->busy == 0) b->done_cv.notify_all();
+  }
+}
+
+static void pool_run(dp_batch *b, int n, const std::function<void(int)> &fn) {
+  if (n <= 0) return;
+  if (b->workers.empty()) {
+    for (int k = 0; k < n; ++k) fn(k);
+    return;
+  }
+  std::unique_lock<std::mutex> lk(b->mu);
+  b->task = fn;
+  b->ntask = n;
+  b->next.store(0);
+  b->busy = (int)b->workers.size();
+  ++b->generation;
+  b->cv.notify_all();
+  b->done_cv.wait(lk, [&] { return b->busy == 0; });
+}
+
 extern "C" int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_batch **out) {
   if (!out) return DP_EINVAL;
   *out = nullptr;
@@ -1168,6 +1227,19 @@ extern "C" int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_bat
   b->act_b = b->act_all + 2 * n;
   b->h_act.assign(3 * (size_t)n, 0);
   b->h_jend.assign(n, 0);
+  cudaGetDevice(&b->device);
+  b->ev.assign(n, nullptr);
+  for (int k = 0; k < n; ++k)
+    if (cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming) != cudaSuccess) {
+      batch_destroy(b);
+      return DP_ECUDA;
+    }
+  if (cudaEventCreateWithFlags(&b->solved, cudaEventDisableTiming) != cudaSuccess) {
+    batch_destroy(b);
+    return DP_ECUDA;
+  }
+  int nw = std::min(n, 16);
+  for (int k = 0; k < nw && n > 1; ++k) b->workers.emplace_back(worker_main, b);
   if (cudaMallocHost(&b->h_gath, 32 * (size_t)n) != cudaSuccess ||
       cudaMallocHost(&b->h_norms, 80 * (size_t)n) != cudaSuccess) {
     batch_destroy(b);
@@ -1181,6 +1253,15 @@ extern "C" int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_bat
 // already); cudaFree waits for the device.
 extern "C" void batch_destroy(dp_batch *b) {
   if (!b) return;
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->quit = true;
+  }
+  b->cv.notify_all();
+  for (std::thread &t : b->workers) t.join();
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->solved) cudaEventDestroy(b->solved);
   for (cudaGraphExec_t &g : b->graph)
     if (g) cudaGraphExecDestroy(g);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -1202,18 +1283,6 @@ extern "C" int64_t batch_launch_count(const dp_batch *b) {
   return n;
 }
 
-// The members' calls of one batch_advance run on the batch's stream.
-struct StreamSwap {
-  dp_batch *b;
-  explicit StreamSwap(dp_batch *bb) : b(bb) {
-    b->own_streams.clear();
-    for (Sim *s : b->m) { b->own_streams.push_back(s->stream); s->stream = b->stream; }
-  }
-  ~StreamSwap() {
-    for (size_t k = 0; k < b->m.size(); ++k) b->m[k]->stream = b->own_streams[k];
-  }
-};
-
 extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int32_t *status) {
   if (!b || !dt) return DP_EINVAL;
   int nm = b->nm;
@@ -1223,33 +1292,33 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
     if (s->err.code == DP_ECUDA) return bfail(b, DP_ECUDA, "a realisation is unusable");
     if (s->alloc_failed) return bfail(b, DP_ENOMEM, "a realisation's allocator failed");
   }
-  // the members' earlier work on their own streams comes first
-  for (Sim *s : b->m)
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bfail(b, DP_ECUDA, "stream");
-  StreamSwap swap(b);
-  std::vector<int> rc(nm, DP_OK), lin(nm, 0), nit(nm, 0);
-  std::vector<char> newton(nm, 1), conv(nm, 0), linfail(nm, 0);
-  std::vector<double> res0(nm, 0.0), res(nm, 0.0);
-  for (int k = 0; k < nm; ++k) {
-    int r = timestep_begin(b->m[k]);
-    if (r != DP_OK) return bfail(b, r, "timestep set-up");
-  }
+  std::vector<int> rc(nm, DP_OK), lin(nm, 0), perr(nm, DP_OK);
+  std::vector<char> newton(nm, 1), conv(nm, 0), linfail(nm, 0), solving(nm, 0), rebuilt(nm, 0);
+  std::vector<double> res0(nm, 0.0), res(nm, 0.0), eta(nm, 0.0);
+  std::vector<std::string> why(nm);
+  std::vector<int> all(nm);
+  for (int k = 0; k < nm; ++k) all[k] = k;
+  pool_run(b, nm, [&](int k) { perr[k] = timestep_begin(b->m[k]); });
+  for (int k = 0; k < nm; ++k)
+    if (perr[k] != DP_OK) return bfail(b, perr[k], "timestep set-up");
   int newton_max = b->m[0]->opt.newton_max;
   for (int l = 0; l <= newton_max; ++l) {
     std::vector<int> iter;
     for (int k = 0; k < nm; ++k) if (newton[k]) iter.push_back(k);
     if (iter.empty()) break;
-    for (int k : iter) {
-      int r = sim_assemble(static_cast<dp_sim *>(b->m[k]), dt[k]);
-      if (r != DP_OK) return bfail(b, r, "assembly");
-      if (cudaMemcpyAsync(b->h_norms + 10 * k, b->m[k]->norm_out, 80, cudaMemcpyDeviceToHost,
-                          b->stream) != cudaSuccess)
-        return bfail(b, DP_ECUDA, "norms");
-    }
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, DP_ECUDA, "norms");
-    std::vector<int> solve;
-    for (int k : iter) {
+    // assembly, convergence test and set-up of each realisation, on its own
+    // stream; the batch's stream then waits for every set-up
+    pool_run(b, (int)iter.size(), [&](int q) {
+      int k = iter[q];
       Sim *s = b->m[k];
+      solving[k] = 0;
+      int r = sim_assemble(static_cast<dp_sim *>(s), dt[k]);
+      if (r == DP_OK &&
+          (cudaMemcpyAsync(b->h_norms + 10 * k, s->norm_out, 80, cudaMemcpyDeviceToHost,
+                           s->stream) != cudaSuccess ||
+           cudaStreamSynchronize(s->stream) != cudaSuccess))
+        r = DP_ECUDA;
+      if (r != DP_OK) { perr[k] = r; return; }
       std::memcpy(s->last_norms, b->h_norms + 10 * k, 80);
       res[k] = s->last_norms[0];
       if (l == 0) res0[k] = res[k];
@@ -1257,25 +1326,31 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
       if (res[k] <= o.newton_tol * res0[k] || s->last_norms[1] <= o.newton_atol) {
         conv[k] = 1;
         newton[k] = 0;
-        continue;
+        return;
       }
-      if (l == o.newton_max) { newton[k] = 0; continue; }
-      solve.push_back(k);
+      if (l == o.newton_max) { newton[k] = 0; return; }
+      bool had = s->amg_ready;
+      r = solve_prepare(s, &eta[k], true);
+      if (r == DP_OK && cudaEventRecord(b->ev[k], s->stream) != cudaSuccess) r = DP_ECUDA;
+      if (r != DP_OK) { perr[k] = r; return; }
+      rebuilt[k] = !had;
+      const char *w = unsupported(s, b->m[0]);
+      if (w) { why[k] = w; perr[k] = DP_EINVAL; return; }
+      solving[k] = 1;
+    });
+    std::vector<int> solve;
+    bool rebuild = !b->built;
+    for (int k : iter) {
+      if (perr[k] != DP_OK) return bfail(b, perr[k], why[k].empty() ? "assembly or set-up" : why[k]);
+      if (solving[k]) {
+        solve.push_back(k);
+        if (rebuilt[k]) rebuild = true;
+        if (cudaStreamWaitEvent(b->stream, b->ev[k], 0) != cudaSuccess)
+          return bfail(b, DP_ECUDA, "event");
+      }
     }
     if (solve.empty()) continue;
-    // set-up of every realisation that solves (its own launches, in order)
-    std::vector<double> eta(nm, 0.0);
-    bool rebuilt = !b->built;
-    for (int k : solve) {
-      Sim *s = b->m[k];
-      bool had = s->amg_ready;
-      int r = solve_prepare(s, &eta[k], true);
-      if (r != DP_OK) return bfail(b, r, "solve set-up");
-      if (!had) rebuilt = true;
-      const char *why = unsupported(s, b->m[0]);
-      if (why) return bfail(b, DP_EINVAL, why);
-    }
-    if (rebuilt) {
+    if (rebuild) {
       int r = build_plan(b);
       if (r != DP_OK) return bfail(b, r, "batch plan");
     }
@@ -1283,24 +1358,24 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
     std::vector<double> frr(nm, 0.0);
     int r = batch_fgmres(b, solve, eta, frc, fit, frr);
     if (r != DP_OK) return bfail(b, r, "batched FGMRES");
-    for (int k : solve) {
+    if (cudaEventRecord(b->solved, b->stream) != cudaSuccess) return bfail(b, DP_ECUDA, "event");
+    // the updates, each on its own stream after the batched FGMRES
+    pool_run(b, (int)solve.size(), [&](int q) {
+      int k = solve[q];
       Sim *s = b->m[k];
-      int ru = solve_update(s, frc[k]);
-      if (ru != DP_OK) return bfail(b, ru, "update");
-    }
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, DP_ECUDA, "update");
-    for (int k : solve) {
-      Sim *s = b->m[k];
+      int ru = cudaStreamWaitEvent(s->stream, b->solved, 0) == cudaSuccess ? DP_OK : DP_ECUDA;
+      if (ru == DP_OK) ru = solve_update(s, frc[k]);
+      if (ru == DP_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) ru = DP_ECUDA;
+      if (ru != DP_OK) { perr[k] = ru; return; }
       dp_stats ls{};
       int rf = solve_finish(s, frc[k], fit[k], frr[k], eta[k], 0.f, 0.f, &ls);
-      if (rf != DP_OK && rf != DP_ELINEAR) return bfail(b, rf, "solve");
+      if (rf != DP_OK && rf != DP_ELINEAR) { perr[k] = rf; return; }
       lin[k] += ls.linear_iters;
-      if (rf == DP_ELINEAR) { linfail[k] = 1; newton[k] = 0; continue; }
-      if (s->well_limits) {
-        int rw = phys_well_controls(s, false);
-        if (rw != DP_OK) return bfail(b, rw, "well controls");
-      }
-    }
+      if (rf == DP_ELINEAR) { linfail[k] = 1; newton[k] = 0; return; }
+      if (s->well_limits) perr[k] = phys_well_controls(s, false);
+    });
+    for (int k : solve)
+      if (perr[k] != DP_OK) return bfail(b, perr[k], "update");
   }
   int first = DP_OK;
   for (int k = 0; k < nm; ++k) {
@@ -1321,6 +1396,8 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
     if (status) status[k] = rc[k];
     if (rc[k] != DP_OK && first == DP_OK) first = rc[k];
   }
+  for (Sim *s : b->m)
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bfail(b, DP_ECUDA, "sync");
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, DP_ECUDA, "sync");
   return first;
 }
