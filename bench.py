@@ -349,6 +349,7 @@ def run_ensemble(args):
             bstep()
         torch.cuda.synchronize()
         l0 = batch.launch_count()
+        p0 = batch.profile()
         t0 = time.perf_counter()
         solves = its = 0
         for _ in range(args.steps):
@@ -357,7 +358,12 @@ def run_ensemble(args):
             its += b
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
-        return {"sec": sec, "solves": solves, "its": its, "launches": batch.launch_count() - l0}
+        p1 = batch.profile()
+        prof = {"ms_setup": p1[0][0] - p0[0][0], "ms_fgmres": p1[0][1] - p0[0][1],
+                "ms_update": p1[0][2] - p0[0][2], "newton_rounds": p1[1][0] - p0[1][0],
+                "cycles": p1[1][1] - p0[1][1], "arnoldi_steps": p1[1][2] - p0[1][2]}
+        return {"sec": sec, "solves": solves, "its": its, "launches": batch.launch_count() - l0,
+                "profile": prof}
 
     clk = Clocks(torch.cuda.current_device())
     one = timed(1)
@@ -387,6 +393,7 @@ def run_ensemble(args):
                               "ms_per_step": 1000 * one["sec"] / args.steps,
                               "newton_solves_per_s": one["solves"] / one["sec"]},
             "autotune_decisions": tuned if args.autotune else None,
+            "batch_profile": bat["profile"],
             "gpu_launches": bat["launches"], "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     for s in sims:

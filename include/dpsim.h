@@ -302,6 +302,11 @@ void batch_destroy(dp_batch *batch);
 const char *batch_last_error(const dp_batch *batch);
 /* kernel launches of the batch and its realisations since their creation */
 int64_t batch_launch_count(const dp_batch *batch);
+/* Where a batch's time goes, since its creation (host wall clock, ms):
+ * ms3[0] the per-realisation assembly, convergence tests and set-up, ms3[1]
+ * the batched FGMRES, ms3[2] the per-realisation updates; counts3: lockstep
+ * Newton rounds, FGMRES cycles, batched Arnoldi steps.  Either may be NULL. */
+int batch_profile(const dp_batch *batch, double *ms3, int64_t *counts3);
 
 /* A non-blocking CUDA stream owned by the caller until dp_stream_destroy:
  * for callers whose framework hands out pooled streams (many realisations

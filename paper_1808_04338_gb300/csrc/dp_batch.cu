@@ -11,6 +11,7 @@
 // launches: their tiles return at once.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <functional>
@@ -430,6 +431,10 @@ struct dp_batch {
   int ntask = 0, generation = 0, busy = 0;
   std::atomic<int> next{0};
   bool quit = false;
+  // host wall time (ms) since creation: the per-realisation parts (assembly
+  // and set-up; update), the batched FGMRES; lockstep counts
+  double ms_setup = 0.0, ms_fgmres = 0.0, ms_update = 0.0;
+  int64_t newton_rounds = 0, arnoldi_steps = 0, cycles = 0;
 };
 
 namespace dp {
@@ -1104,6 +1109,7 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
     DP_TRY(launch(b, b->init_g0, b->act_a, 0));
     DP_TRY(launch(b, b->init_g1, b->act_b, 0));
     for (int k : go) jend[k] = 0;
+    ++b->cycles;
     std::vector<char> in_cycle(nm, 0);
     for (int k : go) in_cycle[k] = 1;
     for (int j = 0; j < b->mres; ++j) {
@@ -1117,6 +1123,7 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
       bool graphs = b->m[0]->opt.use_graphs != 0;
       if (graphs) DP_TRY(run_step_graph(b, j));
       else DP_TRY(run_step(b, j));
+      ++b->arnoldi_steps;
       DP_TRY(fetch_gather(b));
       for (int k = 0; k < nm; ++k) {
         if (!hs[k]) continue;
@@ -1276,6 +1283,13 @@ extern "C" void batch_destroy(dp_batch *b) {
 
 extern "C" const char *batch_last_error(const dp_batch *b) { return b ? b->err.c_str() : ""; }
 
+extern "C" int batch_profile(const dp_batch *b, double *ms3, int64_t *counts3) {
+  if (!b) return DP_EINVAL;
+  if (ms3) { ms3[0] = b->ms_setup; ms3[1] = b->ms_fgmres; ms3[2] = b->ms_update; }
+  if (counts3) { counts3[0] = b->newton_rounds; counts3[1] = b->cycles; counts3[2] = b->arnoldi_steps; }
+  return DP_OK;
+}
+
 extern "C" int64_t batch_launch_count(const dp_batch *b) {
   if (!b) return 0;
   int64_t n = b->launches;
@@ -1308,6 +1322,12 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
     if (iter.empty()) break;
     // assembly, convergence test and set-up of each realisation, on its own
     // stream; the batch's stream then waits for every set-up
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t0) {
+      return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    };
+    auto t0 = clk::now();
+    ++b->newton_rounds;
     pool_run(b, (int)iter.size(), [&](int q) {
       int k = iter[q];
       Sim *s = b->m[k];
@@ -1338,6 +1358,8 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
       if (w) { why[k] = w; perr[k] = DP_EINVAL; return; }
       solving[k] = 1;
     });
+    b->ms_setup += ms_since(t0);
+    t0 = clk::now();
     std::vector<int> solve;
     bool rebuild = !b->built;
     for (int k : iter) {
@@ -1359,6 +1381,8 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
     int r = batch_fgmres(b, solve, eta, frc, fit, frr);
     if (r != DP_OK) return bfail(b, r, "batched FGMRES");
     if (cudaEventRecord(b->solved, b->stream) != cudaSuccess) return bfail(b, DP_ECUDA, "event");
+    b->ms_fgmres += ms_since(t0);
+    t0 = clk::now();
     // the updates, each on its own stream after the batched FGMRES
     pool_run(b, (int)solve.size(), [&](int q) {
       int k = solve[q];
@@ -1376,6 +1400,7 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
     });
     for (int k : solve)
       if (perr[k] != DP_OK) return bfail(b, perr[k], "update");
+    b->ms_update += ms_since(t0);
   }
   int first = DP_OK;
   for (int k = 0; k < nm; ++k) {

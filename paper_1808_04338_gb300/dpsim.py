@@ -180,6 +180,7 @@ def load():
     L.batch_last_error.restype = C.c_char_p
     L.batch_launch_count.argtypes = [P]
     L.batch_launch_count.restype = C.c_int64
+    L.batch_profile.argtypes = [P, P, P]
     L.dp_residual_norms_noalloc.argtypes = [C.POINTER(dp_grid), C.POINTER(dp_fluid), P, P, I, P,
                                             P, P, D, P, P, C.c_char_p, C.c_size_t]
     _lib = L
@@ -288,6 +289,13 @@ class Batch:
 
     def launch_count(self):
         return load().batch_launch_count(self.h)
+
+    def profile(self):
+        """(ms of set-up, batched FGMRES, updates; Newton rounds, cycles, Arnoldi steps)"""
+        ms = (C.c_double * 3)()
+        n = (C.c_int64 * 3)()
+        load().batch_profile(self.h, C.cast(ms, C.c_void_p), C.cast(n, C.c_void_p))
+        return list(ms), list(n)
 
     def close(self):
         if getattr(self, "h", None):
