@@ -285,8 +285,8 @@ int sim_advance_many(dp_sim *const *sims, int32_t n, const double *dt, int32_t t
  * CPR stage residuals, each level of the V-cycle, the operator product, the
  * Gram-Schmidt passes, the Givens rotations) is one launch over a work list
  * of (realisation, block) tiles, in which each realisation runs the blocks
- * of its own launch; realisations that have converged drop out through a
- * device flag.  Each realisation's result is that of sim_advance on it
+ * of its own launch; each launch's list holds only the realisations still
+ * iterating.  At most 256 realisations a batch.  Each realisation's result is that of sim_advance on it
  * alone, bit for bit, whatever the other members of the batch.  `stream`:
  * a cudaStream_t (NULL: the default stream); batch_advance returns after
  * every stream involved has synchronised.  stats[k], status[k] (may

@@ -6,9 +6,10 @@
 // the Arnoldi step over a work list of (realisation, block) tiles.  A tile runs the
 // kernel body of dp_kernels.cuh with the block index and grid size of the
 // realisation's own launch, so every realisation computes exactly what it
-// computes alone (sim_advance), whatever else is in the batch.  A device
-// flag per realisation takes the ones that have converged out of the later
-// launches: their tiles return at once.
+// computes alone (sim_advance), whatever else is in the batch.  Each
+// launch's work list (a segment table passed by value) holds only the
+// realisations still iterating, so a launch costs the work left, not the
+// batch's size.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -27,6 +28,16 @@ namespace dp {
 
 struct Tile {
   int m, bx;   // realisation, block of its own launch
+};
+
+// The realisations of one batched launch, passed by value: the active ones
+// (those a launch covers), and the first block of each in the launch; a
+// block finds its realisation by bisection.  At most kMaxBatch realisations.
+constexpr int kMaxBatch = 256;
+struct Seg {
+  int n;
+  int start[kMaxBatch + 1];
+  short id[kMaxBatch];
 };
 
 // ---------------------------------------------------------------- argument records
@@ -151,15 +162,19 @@ struct AInitG { double *g; int m; const double *beta; };
 struct ASqrt { double *v; };
 struct AGather { const double *scal; double *out; };
 
-#define TILE(A)                        \
-  Tile t = tiles[blockIdx.x];          \
-  if (!act[t.m]) return;               \
+#define TILE(A)                                                   \
+  int lo_ = 0, hi_ = seg.n;                                       \
+  while (hi_ - lo_ > 1) {                                         \
+    int mid_ = (lo_ + hi_) >> 1;                                  \
+    if (seg.start[mid_] <= (int)blockIdx.x) lo_ = mid_;           \
+    else hi_ = mid_;                                              \
+  }                                                               \
+  Tile t{seg.id[lo_], (int)blockIdx.x - seg.start[lo_]};          \
   const A &a = args[t.m];
 
 // ---------------------------------------------------------------- batched kernels
 template <typename TR>
-__global__ void __launch_bounds__(kBlock) kb_ilu_fwd(const ALuF *args, const Tile *tiles,
-                                                     const unsigned char *act, int j) {
+__global__ void __launch_bounds__(kBlock) kb_ilu_fwd(const ALuF *args, const Seg seg, int j) {
   TILE(ALuF)
   const TR *rhs = reinterpret_cast<const TR *>(a.rhs) + (long long)j * a.rjs;
   switch (a.var) {
@@ -175,58 +190,50 @@ __global__ void __launch_bounds__(kBlock) kb_ilu_fwd(const ALuF *args, const Til
   }
 }
 
-__global__ void __launch_bounds__(kBlock) kb_ilu_bwd(const ALuB *args, const Tile *tiles,
-                                                     const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_ilu_bwd(const ALuB *args, const Seg seg, int) {
   TILE(ALuB)
   if (a.var == 0) k_ilu_bwd_r_b<float>(t.bx, a.gx, a.r0, a.r1, a.nL, a.n, a.Uptr, a.colp, a.lu, a.zp);
   else k_ilu_bwd_w_b<float>(t.bx, a.gx, a.r0, a.r1, a.nL, a.n, a.Uptr, a.colp, a.lu, a.zp);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_ilu_result(const ARes *args, const Tile *tiles,
-                                                        const unsigned char *act, int j) {
+__global__ void __launch_bounds__(kBlock) kb_ilu_result(const ARes *args, const Seg seg, int j) {
   TILE(ARes)
   k_ilu_result_b<float>(t.bx, a.gx, a.n, a.iperm, a.zp, a.base, a.out + (long long)j * a.ojs,
                         a.outT, a.inj, a.inj_perm);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_presid(const APres *args, const Tile *tiles,
-                                                    const unsigned char *act, int j) {
+__global__ void __launch_bounds__(kBlock) kb_presid(const APres *args, const Seg seg, int j) {
   TILE(APres)
   k_bsr_presid_f32_b(t.bx, a.gx, a.n, a.nL, a.nc, a.nlong, a.rowptr, a.col, a.pf, a.x,
                      a.b + (long long)j * a.bjs, a.rp, a.omap);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_resid(const AResid *args, const Tile *tiles,
-                                                   const unsigned char *act, int j) {
+__global__ void __launch_bounds__(kBlock) kb_resid(const AResid *args, const Seg seg, int j) {
   TILE(AResid)
   k_bsr_resid_f32_b(t.bx, a.gx, a.n, a.nL, a.nc, a.nlong, a.rowptr, a.col, a.valf, a.x,
                     a.b + (long long)j * a.bjs, a.y);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_fill_f(const AFillF *args, const Tile *tiles,
-                                                    const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_fill_f(const AFillF *args, const Seg seg, int) {
   TILE(AFillF)
   long long i = (long long)t.bx * blockDim.x + threadIdx.x;
   if (i < a.n) a.x[i] = 0.f;
 }
 
-__global__ void __launch_bounds__(kBlock) kb_copy_f(const ACopyF *args, const Tile *tiles,
-                                                    const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_copy_f(const ACopyF *args, const Seg seg, int) {
   TILE(ACopyF)
   long long i = (long long)t.bx * blockDim.x + threadIdx.x;
   if (i < a.n) a.dst[i] = a.src[i];
 }
 
-__global__ void __launch_bounds__(kBlock) kb_gs_c(const AGsC *args, const Tile *tiles,
-                                                  const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_gs_c(const AGsC *args, const Seg seg, int) {
   TILE(AGsC)
   if (a.var == 0) k_gs_c_first_b<float>(t.bx, a.gx, a.r0, a.r1, a.dinv, a.b, a.x);
   else if (a.var == 1) k_gs_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x);
   else k_gs_c_w_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_resid_c(const AResC *args, const Tile *tiles,
-                                                     const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_resid_c(const AResC *args, const Seg seg, int) {
   TILE(AResC)
   if (a.var == 0) k_resid_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.b, a.x, a.r);
   else k_resid_c_w_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.b, a.x, a.r);
@@ -242,8 +249,7 @@ __global__ void __launch_bounds__(kBlock) kb_resid_c(const AResC *args, const Ti
     default: { constexpr int GG = 32; CALL; } break;  \
   }
 
-__global__ void __launch_bounds__(kBlock) kb_csr_mv(const ACsr *args, const Tile *tiles,
-                                                    const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_csr_mv(const ACsr *args, const Seg seg, int) {
   TILE(ACsr)
   if (a.valh)
     KB_SWITCH_G(a.G, (k_csr_mv_b<GG, float, __nv_bfloat16>(t.bx, a.gx, a.n, a.rowptr, a.col,
@@ -253,8 +259,7 @@ __global__ void __launch_bounds__(kBlock) kb_csr_mv(const ACsr *args, const Tile
                                              a.add)))
 }
 
-__global__ void __launch_bounds__(kBlock) kb_jacobi_pre(const AJac *args, const Tile *tiles,
-                                                        const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_jacobi_pre(const AJac *args, const Seg seg, int) {
   TILE(AJac)
   if (a.valh)
     KB_SWITCH_G(a.G, (k_jacobi_pre_b<GG, float, __nv_bfloat16>(t.bx, a.gx, a.n, a.rowptr, a.col,
@@ -264,8 +269,7 @@ __global__ void __launch_bounds__(kBlock) kb_jacobi_pre(const AJac *args, const 
                                                  a.x, a.r)))
 }
 
-__global__ void __launch_bounds__(kBlock) kb_jacobi_sweep(const AJac *args, const Tile *tiles,
-                                                          const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_jacobi_sweep(const AJac *args, const Seg seg, int) {
   TILE(AJac)
   if (a.valh)
     KB_SWITCH_G(a.G, (k_jacobi_sweep_b<GG, float, __nv_bfloat16>(t.bx, a.gx, a.n, a.rowptr, a.col,
@@ -275,21 +279,18 @@ __global__ void __launch_bounds__(kBlock) kb_jacobi_sweep(const AJac *args, cons
                                                    a.b, a.x, a.r)))
 }
 
-__global__ void __launch_bounds__(kBlock) kb_dense_mv(const ADense *args, const Tile *tiles,
-                                                      const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_dense_mv(const ADense *args, const Seg seg, int) {
   TILE(ADense)
   k_dense_mv_b<float>(t.bx, a.gx, a.n, a.inv, a.b, a.x);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_inject(const AInj *args, const Tile *tiles,
-                                                    const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_inject(const AInj *args, const Seg seg, int) {
   TILE(AInj)
   k_inject_f32_b(t.bx, a.gx, a.n, a.xp, a.zf, a.imap);
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBlock) kb_spmv(const ASpmv *args, const Tile *tiles,
-                                                  const unsigned char *act, int j) {
+__global__ void __launch_bounds__(kBlock) kb_spmv(const ASpmv *args, const Seg seg, int j) {
   TILE(ASpmv)
   k_bsr_spmv_b<MODE>(t.bx, a.gx, a.n, a.nL, a.nc, a.nlong, a.rowptr, a.col, a.val,
                      a.x + (long long)j * a.xjs, a.b, a.y);
@@ -298,87 +299,76 @@ __global__ void __launch_bounds__(kBlock) kb_spmv(const ASpmv *args, const Tile 
 // v0: the first vector of this chunk of V
 template <int NV, bool SELF>
 __global__ void __launch_bounds__(kBlock, kDotBlocks / 152) kb_multidot(const ADot *args,
-                                                                        const Tile *tiles,
-                                                                        const unsigned char *act,
+                                                                        const Seg seg,
                                                                         int v0) {
   TILE(ADot)
   k_multidot_b<NV, SELF>(t.bx, a.gx, a.N, a.V + (long long)v0 * a.ldv, a.ldv, a.w, a.part, v0,
                          a.gate);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_dot_final(const ADotF *args, const Tile *tiles,
-                                                       const unsigned char *act, int nv, int j,
+__global__ void __launch_bounds__(kBlock) kb_dot_final(const ADotF *args, const Seg seg, int nv, int j,
                                                        int mode) {
   TILE(ADotF)
   double *dots = mode == 0 ? a.dst : a.dots;
   k_dot_final_b(t.bx, 1, a.part, a.nblocks, nv, dots, a.H, a.m, j, mode, a.scal, a.reorth);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_project(const AProj *args, const Tile *tiles,
-                                                     const unsigned char *act, int j, int pass) {
+__global__ void __launch_bounds__(kBlock) kb_project(const AProj *args, const Seg seg, int j, int pass) {
   TILE(AProj)
   k_project_b(t.bx, a.gx, a.N, a.V, a.ldv, j + 1, a.c, a.w, const_cast<double *>(a.V) + (long long)(j + 1) * a.ldv,
               a.scal, pass);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_givens(const AGiv *args, const Tile *tiles,
-                                                    const unsigned char *act, int j) {
+__global__ void __launch_bounds__(kBlock) kb_givens(const AGiv *args, const Seg seg, int j) {
   TILE(AGiv)
   k_givens_b(t.bx, 1, a.H, a.cs, a.sn, a.g, a.m, j, a.scal + 3);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_backsub(const ABack *args, const Tile *tiles,
-                                                     const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_backsub(const ABack *args, const Seg seg, int) {
   TILE(ABack)
   k_backsub_b(t.bx, 1, a.H, a.g, a.m, a.jend[t.m], a.y);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_multi_axpy(const AAxpy *args, const Tile *tiles,
-                                                        const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_multi_axpy(const AAxpy *args, const Seg seg, int) {
   TILE(AAxpy)
   k_multi_axpy_b(t.bx, a.gx, a.N, a.Z, a.ldv, a.jend[t.m], a.c, 1.0, a.x);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_scale(const AScale *args, const Tile *tiles,
-                                                   const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_scale(const AScale *args, const Seg seg, int) {
   TILE(AScale)
   k_scale_b(t.bx, a.gx, a.N, a.src, a.alpha, 1, a.y);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_fill_d(const AFillD *args, const Tile *tiles,
-                                                    const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_fill_d(const AFillD *args, const Seg seg, int) {
   TILE(AFillD)
   long long i = (long long)t.bx * blockDim.x + threadIdx.x;
   if (i < a.n) a.x[i] = 0.0;
 }
 
-__global__ void __launch_bounds__(kBlock) kb_init_g(const AInitG *args, const Tile *tiles,
-                                                    const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_init_g(const AInitG *args, const Seg seg, int) {
   TILE(AInitG)
   k_init_g_b(t.bx, 1, a.g, a.m, a.beta);
 }
 
-__global__ void __launch_bounds__(kBlock) kb_sqrt(const ASqrt *args, const Tile *tiles,
-                                                  const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_sqrt(const ASqrt *args, const Seg seg, int) {
   TILE(ASqrt)
   if (threadIdx.x == 0) k_sqrt_inplace_b(t.bx, 1, a.v);
 }
 
 // scal[0..3] of every realisation into one array for a single copy to the host
-__global__ void __launch_bounds__(kBlock) kb_gather(const AGather *args, const Tile *tiles,
-                                                    const unsigned char *act, int) {
+__global__ void __launch_bounds__(kBlock) kb_gather(const AGather *args, const Seg seg, int) {
   TILE(AGather)
   if (threadIdx.x < 4) a.out[4 * t.m + threadIdx.x] = a.scal[threadIdx.x];
 }
 
 // ---------------------------------------------------------------- phases
 // A phase: one batched launch; its argument records (one per realisation)
-// and its tiles live in device memory from the batch's set-up.
+// live in device memory from the batch's set-up, its work list is made at
+// each launch from the realisations active then.
 struct Phase {
   int kind = 0;
   void *args = nullptr;
-  Tile *tiles = nullptr;
-  int ntiles = 0;
+  std::vector<int> grid;    // blocks of each realisation's own launch (0: not in it)
   int p0 = 0, p1 = 0;       // kind-specific uniform parameters (a template choice)
 };
 
@@ -399,11 +389,12 @@ struct dp_batch {
   // allocator, so that it can be released after its members)
   std::vector<void *> blocks;
   // activity masks: the Arnoldi step's, and two for the restart prologue
-  unsigned char *act = nullptr, *act_a = nullptr, *act_b = nullptr, *act_all = nullptr;
-  // host copies of the three masks and of jend: pageable, so that each
-  // upload is staged before cudaMemcpyAsync returns and the host may change
-  // them at once
+  // the active realisations of the Arnoldi step (s), of the first cycle's
+  // start (a) and of a restart (b); host arrays from which each launch's
+  // work list is made
   std::vector<unsigned char> h_act;
+  // jend per realisation for the cycle's end (host copy pageable, so that
+  // an upload is staged before cudaMemcpyAsync returns)
   std::vector<int> h_jend;
   int *jend = nullptr;
   double *gath = nullptr, *h_gath = nullptr;   // scal[0..3] of every member
@@ -414,9 +405,6 @@ struct dp_batch {
   dp::Phase rst[4];                     // restart residual, multidot, final (scal[1]), sqrt
   dp::Phase scale_b, scale_r, fill_x, fill_h, init_g0, init_g1;
   dp::Phase backsub, axpy, gather;
-  // CUDA graphs of the Arnoldi steps
-  std::vector<cudaGraphExec_t> graph;
-  cudaStream_t cap_stream = nullptr;
   std::string err;
   int64_t launches = 0;
   // the per-realisation parts (assembly, set-up, update) run on the
@@ -452,27 +440,38 @@ static int add_phase(dp_batch *b, Phase &ph, int kind, const std::vector<A> &arg
   ph.kind = kind;
   ph.p0 = p0;
   ph.p1 = p1;
-  std::vector<Tile> tiles;
-  for (int k = 0; k < b->nm; ++k)
-    for (int x = 0; x < grid[k]; ++x) tiles.push_back({k, x});
-  ph.ntiles = (int)tiles.size();
+  ph.grid = grid;
   ph.args = balloc(b, sizeof(A) * std::max(b->nm, 1));
-  ph.tiles = (Tile *)balloc(b, sizeof(Tile) * std::max<size_t>(tiles.size(), 1));
-  if (!ph.args || !ph.tiles) return DP_ENOMEM;
+  if (!ph.args) return DP_ENOMEM;
   if (cudaMemcpyAsync(ph.args, args.data(), sizeof(A) * b->nm, cudaMemcpyHostToDevice,
-                      b->stream) != cudaSuccess ||
-      (!tiles.empty() && cudaMemcpyAsync(ph.tiles, tiles.data(), sizeof(Tile) * tiles.size(),
-                                         cudaMemcpyHostToDevice, b->stream) != cudaSuccess))
+                      b->stream) != cudaSuccess)
     return DP_ECUDA;
   return DP_OK;
 }
 
+// The work list of a launch: the realisations flagged in `act` (host) that
+// take part in the phase, with their first blocks.  Returns the blocks.
+static int make_seg(dp_batch *b, const Phase &ph, const unsigned char *act, Seg &sg) {
+  sg.n = 0;
+  int total = 0;
+  for (int k = 0; k < b->nm; ++k) {
+    if (!act[k] || ph.grid[k] <= 0) continue;
+    sg.id[sg.n] = (short)k;
+    sg.start[sg.n] = total;
+    total += ph.grid[k];
+    ++sg.n;
+  }
+  sg.start[sg.n] = total;
+  return total;
+}
+
 static int launch(dp_batch *b, const Phase &ph, const unsigned char *act, int j) {
-  if (ph.ntiles == 0) return DP_OK;
-  dim3 g(ph.ntiles), t(kBlock);
+  Seg sg;
+  int nbl = make_seg(b, ph, act, sg);
+  if (nbl == 0) return DP_OK;
+  dim3 g(nbl), t(kBlock);
   cudaStream_t st = b->stream;
-  const Tile *T = ph.tiles;
-#define KB(name, A, ...) name<<<g, t, 0, st>>>(reinterpret_cast<const A *>(ph.args), T, act, __VA_ARGS__)
+#define KB(name, A, ...) name<<<g, t, 0, st>>>(reinterpret_cast<const A *>(ph.args), sg, __VA_ARGS__)
   switch (ph.kind) {
     case K_ILU_FWD_D: KB(kb_ilu_fwd<double>, ALuF, j); break;
     case K_ILU_FWD_F: KB(kb_ilu_fwd<float>, ALuF, j); break;
@@ -522,9 +521,11 @@ static int launch(dp_batch *b, const Phase &ph, const unsigned char *act, int j)
 // parameter, not a record field)
 static int launch_final(dp_batch *b, const Phase &ph, const unsigned char *act, int nv, int j,
                         int mode) {
-  if (ph.ntiles == 0) return DP_OK;
-  kb_dot_final<<<ph.ntiles, kBlock, 0, b->stream>>>(reinterpret_cast<const ADotF *>(ph.args),
-                                                    ph.tiles, act, nv, j, mode);
+  Seg sg;
+  int nbl = make_seg(b, ph, act, sg);
+  if (nbl == 0) return DP_OK;
+  kb_dot_final<<<nbl, kBlock, 0, b->stream>>>(reinterpret_cast<const ADotF *>(ph.args), sg, nv, j,
+                                              mode);
   b->launches += 1;
   return cudaGetLastError() == cudaSuccess ? DP_OK : DP_ECUDA;
 }
@@ -672,8 +673,6 @@ static int build_plan(dp_batch *b) {
   for (void *p : b->blocks) cudaFree(p);
   b->blocks.clear();
   b->step.clear();
-  for (cudaGraphExec_t &g : b->graph)
-    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   int nm = b->nm;
   std::vector<int> one(nm, 1), gridN(nm), gridNb(nm), dotg(nm);
   std::vector<long long> Ns(nm);
@@ -970,12 +969,12 @@ static int build_plan(dp_batch *b) {
   return DP_OK;
 }
 
-// One Arnoldi step for column j over the realisations flagged in b->act:
+// One Arnoldi step for column j over the realisations flagged in act:
 // every phase of cpr_apply and arnoldi_step, then the scalars gathered.
-static int run_step(dp_batch *b, int j) {
+static int run_step(dp_batch *b, int j, const unsigned char *act) {
   size_t ntail = 5;
   size_t nbody = b->step.size() - ntail;
-  for (size_t p = 0; p < nbody; ++p) DP_TRY(launch(b, b->step[p], b->act, j));
+  for (size_t p = 0; p < nbody; ++p) DP_TRY(launch(b, b->step[p], act, j));
   const Phase &pd0 = b->step[nbody], &pd1 = b->step[nbody + 1], &pf = b->step[nbody + 2],
               &pp = b->step[nbody + 3], &pg = b->step[nbody + 4];
   int nv = j + 1;
@@ -986,54 +985,15 @@ static int run_step(dp_batch *b, int j) {
       Phase q = pd;
       q.p0 = std::min(kDotVec, nv - v0);
       q.p1 = v0 == 0 ? 1 : 0;
-      DP_TRY(launch(b, q, b->act, v0));
+      DP_TRY(launch(b, q, act, v0));
     }
-    DP_TRY(launch_final(b, pf, b->act, nv, j, pass == 0 ? 3 : 4));
+    DP_TRY(launch_final(b, pf, act, nv, j, pass == 0 ? 3 : 4));
     Phase q = pp;
     q.p0 = pass;
-    DP_TRY(launch(b, q, b->act, j));
+    DP_TRY(launch(b, q, act, j));
   }
-  DP_TRY(launch(b, pg, b->act, j));
-  DP_TRY(launch(b, b->gather, b->act, 0));
-  return DP_OK;
-}
-
-static int run_step_graph(dp_batch *b, int j) {
-  if ((int)b->graph.size() < b->mres) b->graph.assign(b->mres, nullptr);
-  if (!b->graph[j]) {
-    if (!b->cap_stream && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-      return DP_ECUDA;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ECUDA;
-    cudaStream_t user = b->stream;
-    b->stream = b->cap_stream;
-    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      b->stream = user;
-      return DP_ECUDA;
-    }
-    int64_t l0 = b->launches;
-    int rc = run_step(b, j);
-    cudaGraph_t g = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &g);
-    b->stream = user;
-    b->launches = l0;
-    if (rc != DP_OK || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return DP_ECUDA; }
-    cudaGraphExec_t ex = nullptr;
-    ce = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    if (ce != cudaSuccess) return DP_ECUDA;
-    b->graph[j] = ex;
-  }
-  if (cudaGraphLaunch(b->graph[j], b->stream) != cudaSuccess) return DP_ECUDA;
-  b->launches += 1;
-  return DP_OK;
-}
-
-// upload the three masks (step, a, b) from h_act
-static int put_masks(dp_batch *b) {
-  int nm = b->nm;
-  if (cudaMemcpyAsync(b->act, b->h_act.data(), 3 * (size_t)nm, cudaMemcpyHostToDevice, b->stream) !=
-      cudaSuccess)
-    return DP_ECUDA;
+  DP_TRY(launch(b, pg, act, j));
+  DP_TRY(launch(b, b->gather, act, 0));
   return DP_OK;
 }
 
@@ -1052,18 +1012,18 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
                         std::vector<int> &rc, std::vector<int> &it, std::vector<double> &rr) {
   int nm = b->nm;
   unsigned char *hs = b->h_act.data(), *ha = hs + nm, *hb = hs + 2 * nm;
+  const unsigned char *act = hs, *act_a = ha, *act_b = hb;
   std::vector<int> total(nm, 0), jend(nm, 0);
   std::vector<char> conv(nm, 0), live(nm, 0), stop(nm, 0);
   std::vector<double> bnorm(nm, 0.0), res(nm, 0.0);
   for (int k : in) live[k] = 1;
   // x = 0, ||b|| into scal[0]
   for (int k = 0; k < nm; ++k) hs[k] = live[k], ha[k] = 0, hb[k] = 0;
-  DP_TRY(put_masks(b));
-  DP_TRY(launch(b, b->fill_x, b->act, 0));
-  DP_TRY(launch(b, b->norm_b[0], b->act, 0));
-  DP_TRY(launch_final(b, b->norm_b[1], b->act, 1, 0, 0));
-  DP_TRY(launch(b, b->norm_b[2], b->act, 0));
-  DP_TRY(launch(b, b->gather, b->act, 0));
+  DP_TRY(launch(b, b->fill_x, act, 0));
+  DP_TRY(launch(b, b->norm_b[0], act, 0));
+  DP_TRY(launch_final(b, b->norm_b[1], act, 1, 0, 0));
+  DP_TRY(launch(b, b->norm_b[2], act, 0));
+  DP_TRY(launch(b, b->gather, act, 0));
   DP_TRY(fetch_gather(b));
   for (int k : in) {
     bnorm[k] = b->h_gath[4 * k + 0];
@@ -1085,11 +1045,10 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
     }
     for (int k : cyc) { if (total[k] > 0) { hb[k] = 1; any_r = true; } }
     if (any_r) {
-      DP_TRY(put_masks(b));
-      for (int p = 0; p < 2; ++p) DP_TRY(launch(b, b->rst[p], b->act_b, 0));
-      DP_TRY(launch_final(b, b->rst[2], b->act_b, 1, 0, 0));
-      DP_TRY(launch(b, b->rst[3], b->act_b, 0));
-      DP_TRY(launch(b, b->gather, b->act_b, 0));
+      for (int p = 0; p < 2; ++p) DP_TRY(launch(b, b->rst[p], act_b, 0));
+      DP_TRY(launch_final(b, b->rst[2], act_b, 1, 0, 0));
+      DP_TRY(launch(b, b->rst[3], act_b, 0));
+      DP_TRY(launch(b, b->gather, act_b, 0));
       DP_TRY(fetch_gather(b));
     }
     std::vector<int> go;
@@ -1102,12 +1061,11 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
     if (go.empty()) continue;
     for (int k = 0; k < nm; ++k) { hs[k] = 0; ha[k] = 0; hb[k] = 0; }
     for (int k : go) { if (total[k] > 0) hb[k] = 1; else ha[k] = 1; hs[k] = 1; }
-    DP_TRY(put_masks(b));
-    DP_TRY(launch(b, b->scale_b, b->act_a, 0));
-    DP_TRY(launch(b, b->scale_r, b->act_b, 0));
-    DP_TRY(launch(b, b->fill_h, b->act, 0));
-    DP_TRY(launch(b, b->init_g0, b->act_a, 0));
-    DP_TRY(launch(b, b->init_g1, b->act_b, 0));
+    DP_TRY(launch(b, b->scale_b, act_a, 0));
+    DP_TRY(launch(b, b->scale_r, act_b, 0));
+    DP_TRY(launch(b, b->fill_h, act, 0));
+    DP_TRY(launch(b, b->init_g0, act_a, 0));
+    DP_TRY(launch(b, b->init_g1, act_b, 0));
     for (int k : go) jend[k] = 0;
     ++b->cycles;
     std::vector<char> in_cycle(nm, 0);
@@ -1119,10 +1077,7 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
         any = any || hs[k];
       }
       if (!any) break;
-      DP_TRY(put_masks(b));
-      bool graphs = b->m[0]->opt.use_graphs != 0;
-      if (graphs) DP_TRY(run_step_graph(b, j));
-      else DP_TRY(run_step(b, j));
+      DP_TRY(run_step(b, j, act));
       ++b->arnoldi_steps;
       DP_TRY(fetch_gather(b));
       for (int k = 0; k < nm; ++k) {
@@ -1138,12 +1093,11 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
     // x += Z y for the members of the cycle
     for (int k = 0; k < nm; ++k) { hs[k] = 0; b->h_jend[k] = jend[k]; }
     for (int k : go) hs[k] = 1;
-    DP_TRY(put_masks(b));
     if (cudaMemcpyAsync(b->jend, b->h_jend.data(), 4 * (size_t)nm, cudaMemcpyHostToDevice, b->stream) !=
         cudaSuccess)
       return DP_ECUDA;
-    DP_TRY(launch(b, b->backsub, b->act, 0));
-    DP_TRY(launch(b, b->axpy, b->act, 0));
+    DP_TRY(launch(b, b->backsub, act, 0));
+    DP_TRY(launch(b, b->axpy, act, 0));
     for (int k : go) if (jend[k] == 0) stop[k] = 1;
   }
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ECUDA;
@@ -1223,15 +1177,15 @@ extern "C" int batch_create(dp_sim *const *sims, int32_t n, void *stream, dp_bat
   for (int k = 0; k < n; ++k) b->m.push_back(static_cast<Sim *>(sims[k]));
   b->mres = b->m[0]->m;
   b->maxit = b->m[0]->opt.gmres_maxit;
-  if (cudaMalloc(&b->act_all, 4 * (size_t)n) != cudaSuccess ||
-      cudaMalloc(&b->jend, 4 * (size_t)n) != cudaSuccess ||
+  if (n > kMaxBatch) {
+    delete b;
+    return DP_EINVAL;
+  }
+  if (cudaMalloc(&b->jend, 4 * (size_t)n) != cudaSuccess ||
       cudaMalloc(&b->gath, 32 * (size_t)n) != cudaSuccess) {
     batch_destroy(b);
     return DP_ENOMEM;
   }
-  b->act = b->act_all;
-  b->act_a = b->act_all + n;
-  b->act_b = b->act_all + 2 * n;
   b->h_act.assign(3 * (size_t)n, 0);
   b->h_jend.assign(n, 0);
   cudaGetDevice(&b->device);
@@ -1269,11 +1223,7 @@ extern "C" void batch_destroy(dp_batch *b) {
   for (cudaEvent_t e : b->ev)
     if (e) cudaEventDestroy(e);
   if (b->solved) cudaEventDestroy(b->solved);
-  for (cudaGraphExec_t &g : b->graph)
-    if (g) cudaGraphExecDestroy(g);
-  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (void *p : b->blocks) cudaFree(p);
-  if (b->act_all) cudaFree(b->act_all);
   if (b->jend) cudaFree(b->jend);
   if (b->gath) cudaFree(b->gath);
   if (b->h_gath) cudaFreeHost(b->h_gath);
