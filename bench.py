@@ -574,9 +574,10 @@ def main():
     ap.add_argument("--schur", type=int, default=0,
                     help="1: eliminate the matrix cells exactly and solve the fracture-and-well "
                          "system")
-    ap.add_argument("--autotune", action="store_true",
-                    help="time the AMG level kernels' launch shapes after the first warm-up "
-                         "timestep and keep the fastest (sim_autotune)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the autotuner (sim_autotune: launch shapes of the AMG level "
+                         "kernels and of level 0's colour sweeps, the V-cycle schedule), which "
+                         "otherwise runs after one untimed timestep")
     ap.add_argument("--threads", type=int, default=16,
                     help="ensemble mode: host threads driving realisations concurrently")
     ap.add_argument("--mode", default="bench",
@@ -681,14 +682,21 @@ def main():
                 "median": solve_ms[len(solve_ms) // 2] if solve_ms else None,
                 "p90": solve_ms[min(len(solve_ms) - 1, int(0.9 * len(solve_ms)))] if solve_ms else None}
 
-    tuned = None
-    if args.autotune:
+    def tune(sim, opts):
+        """Launch shapes and the V-cycle schedule chosen by the library's
+        autotuner after one untimed timestep (sim_autotune); returns its
+        decisions."""
         timestep(sim, opts)
         rep = sim.autotune(20)
         lines = [l for l in rep.splitlines() if "->" in l]
-        tuned = {"decisions": len(lines),
-                 "changed": sum(1 for l in lines if l.split("lanes ")[1].split(" ->")[0]
-                                != l.split("-> ")[1].split(" ")[0])}
+
+        def changed(l):
+            a, b = l.split(" -> ")
+            return a.split()[-1] != b.split()[0]
+        return {"decisions": len(lines), "changed": sum(1 for l in lines if changed(l)),
+                "report": [l for l in lines if changed(l)]}
+
+    tuned = tune(sim, opts) if args.autotune else None
     clk = Clocks(local)
     main = measure(sim, opts, args.steps, args.warmup, clk)
     timestep(sim, opts)
@@ -774,6 +782,8 @@ def main():
                              decouple=args.decouple, eta_mode=args.eta_mode, schur=1)
         with torch.cuda.stream(stream):
             simsch = dpsim.Sim(prob, osch, stream=stream)
+        if args.autotune:
+            tune(simsch, osch)
         r = measure(simsch, osch, max(2, args.steps // 2), args.warmup)
         timestep(simsch, osch)
         states["schur_path"] = simsch.get_state()
@@ -791,6 +801,8 @@ def main():
                             decouple=args.decouple, eta_mode=args.eta_mode, schur=args.schur)
         with torch.cuda.stream(stream):
             simbf = dpsim.Sim(prob, obf, stream=stream)
+        if args.autotune:
+            tune(simbf, obf)
         r = measure(simbf, obf, max(2, args.steps // 2), args.warmup)
         timestep(simbf, obf)
         states["bf16_coarse_path"] = simbf.get_state()
@@ -808,6 +820,8 @@ def main():
                             decouple=args.decouple, eta_mode=args.eta_mode, schur=args.schur)
         with torch.cuda.stream(stream):
             sim64 = dpsim.Sim(prob, o64, stream=stream)
+        if args.autotune:
+            tune(sim64, o64)
         r = measure(sim64, o64, max(2, args.steps // 2), args.warmup)
         timestep(sim64, o64)
         states["fp64_path"] = sim64.get_state()

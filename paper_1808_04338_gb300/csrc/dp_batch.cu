@@ -93,15 +93,15 @@ struct AResid {  // b - A x, FP32 copy of the operator
 struct AFillF { int gx; long long n; float *x; };
 struct ACopyF { int gx; long long n; const float *src; float *dst; };
 struct AGsC {   // level-0 Gauss-Seidel colour in colour order
-  int var;      // 0 first colour from zero, 1 thread per row, 2 warp per row
-  int gx, r0, r1;
+  int var;      // 0 first colour from zero, 1 G lanes per row, 2 warp per row
+  int G, gx, r0, r1;
   const int *rowptr, *colp;
   const float *pv, *dinv, *b;
   float *x;
 };
 struct AResC {  // level-0 residual rows in colour order
-  int var;      // 0 thread per row, 1 warp per row
-  int gx, r0, r1;
+  int var;      // 0 G lanes per row, 1 warp per row
+  int G, gx, r0, r1;
   const int *rowptr, *colp;
   const float *pv, *b;
   float *x, *r;
@@ -173,6 +173,16 @@ struct AGather { const double *scal; double *out; };
   const A &a = args[t.m];
 
 // ---------------------------------------------------------------- batched kernels
+#define KB_SWITCH_G(G, CALL)                          \
+  switch (G) {                                        \
+    case 1: { constexpr int GG = 1; CALL; } break;    \
+    case 2: { constexpr int GG = 2; CALL; } break;    \
+    case 4: { constexpr int GG = 4; CALL; } break;    \
+    case 8: { constexpr int GG = 8; CALL; } break;    \
+    case 16: { constexpr int GG = 16; CALL; } break;  \
+    default: { constexpr int GG = 32; CALL; } break;  \
+  }
+
 template <typename TR>
 __global__ void __launch_bounds__(kBlock) kb_ilu_fwd(const ALuF *args, const Seg seg, int j) {
   TILE(ALuF)
@@ -228,26 +238,30 @@ __global__ void __launch_bounds__(kBlock) kb_copy_f(const ACopyF *args, const Se
 
 __global__ void __launch_bounds__(kBlock) kb_gs_c(const AGsC *args, const Seg seg, int) {
   TILE(AGsC)
-  if (a.var == 0) k_gs_c_first_b<float>(t.bx, a.gx, a.r0, a.r1, a.dinv, a.b, a.x);
-  else if (a.var == 1) k_gs_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x);
-  else k_gs_c_w_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x);
+  if (a.var == 0) {
+    k_gs_c_first_b<float>(t.bx, a.gx, a.r0, a.r1, a.dinv, a.b, a.x);
+  } else if (a.var == 1) {
+    if (a.G == 1) k_gs_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x);
+    else
+      KB_SWITCH_G(a.G, (k_gs_cg_b<GG, float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv,
+                                              a.dinv, a.b, a.x)))
+  } else {
+    k_gs_c_w_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x);
+  }
 }
 
 __global__ void __launch_bounds__(kBlock) kb_resid_c(const AResC *args, const Seg seg, int) {
   TILE(AResC)
-  if (a.var == 0) k_resid_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.b, a.x, a.r);
-  else k_resid_c_w_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.b, a.x, a.r);
+  if (a.var == 0) {
+    if (a.G == 1) k_resid_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.b, a.x, a.r);
+    else
+      KB_SWITCH_G(a.G, (k_resid_cg_b<GG, float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv,
+                                                 a.b, a.x, a.r)))
+  } else {
+    k_resid_c_w_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.b, a.x, a.r);
+  }
 }
 
-#define KB_SWITCH_G(G, CALL)                          \
-  switch (G) {                                        \
-    case 1: { constexpr int GG = 1; CALL; } break;    \
-    case 2: { constexpr int GG = 2; CALL; } break;    \
-    case 4: { constexpr int GG = 4; CALL; } break;    \
-    case 8: { constexpr int GG = 8; CALL; } break;    \
-    case 16: { constexpr int GG = 16; CALL; } break;  \
-    default: { constexpr int GG = 32; CALL; } break;  \
-  }
 
 __global__ void __launch_bounds__(kBlock) kb_csr_mv(const ACsr *args, const Seg seg, int) {
   TILE(ACsr)
@@ -385,6 +399,7 @@ struct dp_batch {
   cudaStream_t stream = nullptr;
   int nm = 0, mres = 30, maxit = 300;
   bool built = false;
+  std::vector<int> shapes;   // each member's Sim::shapes when the plan was built
   // the batch's own device memory (cudaMalloc: it never touches a member's
   // allocator, so that it can be released after its members)
   std::vector<void *> blocks;
@@ -593,7 +608,7 @@ static void gs_colours(const Sim *s, bool forward, bool from_zero, std::vector<S
     if (r1 <= r0) continue;
     if (first) { first = false; out.push_back({0, r0, r1, nblk(r1 - r0)}); continue; }
     if (s->lu_cmaxlen[c] > kLongRow) out.push_back({2, r0, r1, nblk(32LL * (r1 - r0))});
-    else out.push_back({1, r0, r1, nblk(r1 - r0)});
+    else out.push_back({1, r0, r1, nblk((long long)(r1 - r0) * s->l0_G)});
   }
 }
 static void resid_runs(const Sim *s, std::vector<Sweep> &out) {
@@ -604,7 +619,9 @@ static void resid_runs(const Sim *s, std::vector<Sweep> &out) {
     int c1 = c + 1;
     while (c1 < nc && (s->lu_cmaxlen[c1] > kLongRow) == lng) ++c1;
     int r1 = s->lu_cstart[c1];
-    if (r1 > r0) out.push_back({lng ? 1 : 0, r0, r1, lng ? nblk(32LL * (r1 - r0)) : nblk(r1 - r0)});
+    if (r1 > r0)
+      out.push_back({lng ? 1 : 0, r0, r1,
+                     lng ? nblk(32LL * (r1 - r0)) : nblk((long long)(r1 - r0) * s->l0_G)});
     c = c1;
   }
 }
@@ -734,8 +751,8 @@ static int build_plan(dp_batch *b) {
       std::vector<Sweep> cs;
       gs_colours(s, forward, from_zero, cs);
       for (auto &w : cs) {
-        AGsC a{w.var, w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf, s->dinv_cf,
-               s->lev[0].bf, s->lev[0].xf};
+        AGsC a{w.var, s->l0_G, w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf,
+               s->dinv_cf, s->lev[0].bf, s->lev[0].xf};
         P[k].push_back({a, w.grid});
       }
       np = std::max(np, P[k].size());
@@ -752,8 +769,8 @@ static int build_plan(dp_batch *b) {
       std::vector<Sweep> rs;
       resid_runs(s, rs);
       for (auto &w : rs) {
-        AResC a{w.var, w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf, s->lev[0].bf,
-                s->lev[0].xf, s->lev[0].rf};
+        AResC a{w.var, s->l0_G, w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf,
+                s->lev[0].bf, s->lev[0].xf, s->lev[0].rf};
         P[k].push_back({a, w.grid});
       }
       np = std::max(np, P[k].size());
@@ -965,6 +982,8 @@ static int build_plan(dp_batch *b) {
   DP_TRY(one_phase(b, nullptr, &b->axpy, K_AXPY, ax, gridN));
   DP_TRY(one_phase(b, nullptr, &b->gather, K_GATHER, ga, one));
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ECUDA;
+  b->shapes.assign(nm, 0);
+  for (int k = 0; k < nm; ++k) b->shapes[k] = b->m[k]->shapes;
   b->built = true;
   return DP_OK;
 }
@@ -1312,6 +1331,7 @@ extern "C" int batch_advance(dp_batch *b, const double *dt, dp_stats *stats, int
     t0 = clk::now();
     std::vector<int> solve;
     bool rebuild = !b->built;
+    for (int k = 0; k < nm && !rebuild; ++k) rebuild = b->shapes[k] != b->m[k]->shapes;
     for (int k : iter) {
       if (perr[k] != DP_OK) return bfail(b, perr[k], why[k].empty() ? "assembly or set-up" : why[k]);
       if (solving[k]) {

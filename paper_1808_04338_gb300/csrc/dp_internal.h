@@ -324,6 +324,8 @@ struct Sim {
   double *p0c_val = nullptr, *dinv_c = nullptr;
   float *p0c_valf = nullptr, *dinv_cf = nullptr;
   bool l0_lu = false;
+  int l0_G = 1;       // lanes per row of the level-0 colour-order sweeps (autotuned; 1: a thread)
+  int shapes = 0;     // bumped whenever launch shapes change (autotune, AMG set-up)
   double *l0_pv = nullptr;
   float *l0_pvf = nullptr;   // inverse from the LU factors (n <= kInverseMax), row-major
   int *coarse_piv = nullptr;

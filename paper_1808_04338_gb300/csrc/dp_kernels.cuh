@@ -660,6 +660,44 @@ __device__ __forceinline__ void k_resid_c_w_b(int bx, int gx, int r0, int r1, co
   row_c_w<T, true>(bx, r0, r1, rowptr, colp, pv, nullptr, b, x, r);
 }
 
+// Level-0 Gauss-Seidel colour and residual rows with G lanes per row (G =
+// 2, 4, 8; the autotuner's choice for short-row colours): the lanes split a
+// row's entries (e0 + lane, e0 + lane + G, ...), so a warp reads the
+// colour's entries as one contiguous stretch and each lane's chain of
+// dependent gathers is G times shorter; the partial sums meet in shuffles.
+template <int G, typename T>
+__device__ __forceinline__ void k_gs_cg_b(int bx, int gx, int r0, int r1,
+                                          const int *__restrict__ rowptr,
+                                          const int *__restrict__ colp,
+                                          const T *__restrict__ pv, const T *__restrict__ dinv,
+                                          const T *__restrict__ b, T *x) {
+  int t = bx * blockDim.x + threadIdx.x;
+  int q = r0 + t / G, lane = t % G;
+  bool valid = q < r1;
+  int e0 = valid ? __ldg(rowptr + q) : 0, e1 = valid ? __ldg(rowptr + q + 1) : 0;
+  T s = row_dot<G, T>(e0, e1, lane, colp, pv, x);
+  s = group_sum<G, T>(s);
+  if (valid && lane == 0) {
+    T di = dinv[q];
+    if (di != T(0)) x[q] = fma(b[q] - s, di, x[q]);
+  }
+}
+
+template <int G, typename T>
+__device__ __forceinline__ void k_resid_cg_b(int bx, int gx, int r0, int r1,
+                                             const int *__restrict__ rowptr,
+                                             const int *__restrict__ colp,
+                                             const T *__restrict__ pv, const T *__restrict__ b,
+                                             const T *x, T *__restrict__ r) {
+  int t = bx * blockDim.x + threadIdx.x;
+  int q = r0 + t / G, lane = t % G;
+  bool valid = q < r1;
+  int e0 = valid ? __ldg(rowptr + q) : 0, e1 = valid ? __ldg(rowptr + q + 1) : 0;
+  T s = row_dot<G, T>(e0, e1, lane, colp, pv, x);
+  s = group_sum<G, T>(s);
+  if (valid && lane == 0) r[q] = b[q] - s;
+}
+
 template <typename T>
 __device__ __forceinline__ void k_resid_c_b(int bx, int gx, int r0, int r1, const int *__restrict__ rowptr,
                                                     const int *__restrict__ colp,

@@ -1179,6 +1179,24 @@ __global__ void __launch_bounds__(kBlock) k_resid_c(int r0, int r1, const int *_
   k_resid_c_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
 }
 
+template <int G, typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_cg(int r0, int r1, const int *__restrict__ rowptr,
+                                                  const int *__restrict__ colp,
+                                                  const T *__restrict__ pv,
+                                                  const T *__restrict__ dinv,
+                                                  const T *__restrict__ b, T *x) {
+  k_gs_cg_b<G, T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x);
+}
+
+template <int G, typename T>
+__global__ void __launch_bounds__(kBlock) k_resid_cg(int r0, int r1, const int *__restrict__ rowptr,
+                                                     const int *__restrict__ colp,
+                                                     const T *__restrict__ pv,
+                                                     const T *__restrict__ b, const T *x,
+                                                     T *__restrict__ r) {
+  k_resid_cg_b<G, T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
+}
+
 template <typename T> struct L0C;
 template <> struct L0C<double> {
   static const double *pv(const Sim *s) { return s->l0_pv; }
@@ -1213,7 +1231,11 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
     if (s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, k_gs_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
                 s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
-    else
+    else if (s->l0_G > 1) {
+      DP_SWITCH_G(s->l0_G, DP_LAUNCH(s, (k_gs_cg<GG, T>), nblk((long long)(r1 - r0) * GG), kBlock,
+                                     0, r0, r1, s->lu_rowptr, s->l0_colp, L0C<T>::pv(s),
+                                     L0C<T>::dinv(s), b, x));
+    } else
       DP_LAUNCH(s, k_gs_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
   }
@@ -1233,7 +1255,11 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
       if (lng)
         DP_LAUNCH(s, k_resid_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
                   s->l0_colp, L0C<T>::pv(s), b, (T *)x, r);
-      else
+      else if (s->l0_G > 1) {
+        DP_SWITCH_G(s->l0_G, DP_LAUNCH(s, (k_resid_cg<GG, T>), nblk((long long)(r1 - r0) * GG),
+                                       kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+                                       L0C<T>::pv(s), b, x, r));
+      } else
         DP_LAUNCH(s, k_resid_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, x, r);
     }
@@ -1419,6 +1445,66 @@ static int tune_level(Sim *s, int l, int reps, std::string &rep) {
   return DP_OK;
 }
 
+// Level 0 in colour order: lanes per row (1, 2, 4, 8) of its short-row
+// Gauss-Seidel colours and residual, timed as one forward sweep and one
+// residual on the level's own vectors.
+template <typename T>
+static int tune_l0(Sim *s, int reps, std::string &rep) {
+  if (!l0c_on(s)) return DP_OK;
+  Level &L = s->lev[0];
+  T *x = LV<T>::x(L), *b = LV<T>::b(L), *r = LV<T>::r(L);
+  static const int cand[] = {1, 2, 4, 8};
+  int old = s->l0_G, best = old;
+  float best_ms = 1e30f;
+  std::string line;
+  char buf[160];
+  for (int g : cand) {
+    s->l0_G = g;
+    float ms = 0.f;
+    auto one = [&]() -> int {
+      DP_TRY(gs_sweep_c<T>(s, b, x, true));
+      return resid_c<T>(s, b, x, r);
+    };
+    int rc = time_launches(s, reps, one, &ms);
+    if (rc != DP_OK) { s->l0_G = old; return rc; }
+    std::snprintf(buf, sizeof buf, " %d:%.1f", g, 1000.f * ms / reps);
+    line += buf;
+    if (ms < best_ms) { best_ms = ms; best = g; }
+  }
+  s->l0_G = best;
+  std::snprintf(buf, sizeof buf, "level 0 colour sweeps and residual lanes %d -> %d (us per sweep+residual:%s)\n",
+                old, best, line.c_str());
+  rep += buf;
+  return DP_OK;
+}
+
+// The schedule of the coarse V-cycle: the levels from cl_level on in one
+// thread-block-cluster launch (a persistent launch with cluster barriers
+// between the colour phases) or one launch per phase; timed as whole
+// V-cycles from level 0 on the level's own vectors.
+template <typename T>
+static int tune_cycle(Sim *s, int reps, std::string &rep) {
+  if (s->cl_level < 0) return DP_OK;
+  Level &L = s->lev[0];
+  T *x = LV<T>::x(L), *b = LV<T>::b(L);
+  int keep = s->cl_level;
+  float ms[2] = {0.f, 0.f};
+  for (int k = 0; k < 2; ++k) {
+    s->cl_level = k == 0 ? keep : -1;
+    auto one = [&]() -> int { return vcycle_t<T>(s, 0, b, x); };
+    int rc = time_launches(s, reps, one, &ms[k]);
+    if (rc != DP_OK) { s->cl_level = keep; return rc; }
+  }
+  s->cl_level = ms[1] < ms[0] ? -1 : keep;
+  char buf[200];
+  std::snprintf(buf, sizeof buf,
+                "V-cycle schedule: cluster launch from level %d %.1f us, per-phase launches %.1f us -> %s\n",
+                keep, 1000.f * ms[0] / reps, 1000.f * ms[1] / reps,
+                s->cl_level < 0 ? "per-phase launches" : "cluster launch");
+  rep += buf;
+  return DP_OK;
+}
+
 int autotune(Sim *s, int reps, std::string &rep) {
   if (!s->amg_ready || s->opt.precond != 2) {
     s->fail(DP_EINVAL, "autotune needs the AMG hierarchy (one CPR-FPF solve first)");
@@ -1429,8 +1515,16 @@ int autotune(Sim *s, int reps, std::string &rep) {
     if (s->opt.precision >= 1) DP_TRY(tune_level<float>(s, l, reps, rep));
     else DP_TRY(tune_level<double>(s, l, reps, rep));
   }
+  if (s->opt.precision >= 1) {
+    DP_TRY(tune_l0<float>(s, reps, rep));
+    DP_TRY(tune_cycle<float>(s, reps, rep));
+  } else {
+    DP_TRY(tune_l0<double>(s, reps, rep));
+    DP_TRY(tune_cycle<double>(s, reps, rep));
+  }
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
   graphs_free(s);   // the Arnoldi steps are captured again with the new launch shapes
+  ++s->shapes;      // and a batch holding this realisation rebuilds its plan
   return DP_OK;
 }
 
