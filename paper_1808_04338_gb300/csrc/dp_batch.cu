@@ -242,6 +242,9 @@ __global__ void __launch_bounds__(kBlock) kb_gs_c(const AGsC *args, const Seg se
     k_gs_c_first_b<float>(t.bx, a.gx, a.r0, a.r1, a.dinv, a.b, a.x);
   } else if (a.var == 1) {
     if (a.G == 1) k_gs_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x);
+    else if (a.G == 0)
+      k_sweep_cs_b<float, false>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.dinv, a.b, a.x,
+                                 nullptr);
     else
       KB_SWITCH_G(a.G, (k_gs_cg_b<GG, float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv,
                                               a.dinv, a.b, a.x)))
@@ -254,6 +257,9 @@ __global__ void __launch_bounds__(kBlock) kb_resid_c(const AResC *args, const Se
   TILE(AResC)
   if (a.var == 0) {
     if (a.G == 1) k_resid_c_b<float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, a.b, a.x, a.r);
+    else if (a.G == 0)
+      k_sweep_cs_b<float, true>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv, nullptr, a.b, a.x,
+                                a.r);
     else
       KB_SWITCH_G(a.G, (k_resid_cg_b<GG, float>(t.bx, a.gx, a.r0, a.r1, a.rowptr, a.colp, a.pv,
                                                  a.b, a.x, a.r)))
@@ -608,7 +614,7 @@ static void gs_colours(const Sim *s, bool forward, bool from_zero, std::vector<S
     if (r1 <= r0) continue;
     if (first) { first = false; out.push_back({0, r0, r1, nblk(r1 - r0)}); continue; }
     if (s->lu_cmaxlen[c] > kLongRow) out.push_back({2, r0, r1, nblk(32LL * (r1 - r0))});
-    else out.push_back({1, r0, r1, nblk((long long)(r1 - r0) * s->l0_G)});
+    else out.push_back({1, r0, r1, nblk((long long)(r1 - r0) * std::max(s->l0_G, 1))});
   }
 }
 static void resid_runs(const Sim *s, std::vector<Sweep> &out) {
@@ -621,7 +627,7 @@ static void resid_runs(const Sim *s, std::vector<Sweep> &out) {
     int r1 = s->lu_cstart[c1];
     if (r1 > r0)
       out.push_back({lng ? 1 : 0, r0, r1,
-                     lng ? nblk(32LL * (r1 - r0)) : nblk((long long)(r1 - r0) * s->l0_G)});
+                     lng ? nblk(32LL * (r1 - r0)) : nblk((long long)(r1 - r0) * std::max(s->l0_G, 1))});
     c = c1;
   }
 }

@@ -683,6 +683,58 @@ __device__ __forceinline__ void k_gs_cg_b(int bx, int gx, int r0, int r1,
   }
 }
 
+// Level-0 Gauss-Seidel colour (RESID false) or residual rows (RESID true)
+// with the CTA's rows staged: a CTA of kBlock threads takes rows q0 ..
+// q0+255 of the colour range, loads their row pointers and then all their
+// entries (columns and values, contiguous in the colour-order copy) into
+// shared memory with coalesced loads, and each thread then gathers x for
+// its own row from there.  Rows of up to kStageLen entries on average (the
+// short-row colours); the result of every row is that of k_gs_c/k_resid_c
+// bit for bit (the same products summed in the same order: entries 1, 3, 5,
+// 7 into one accumulator, all others into the other).
+constexpr int kStageLen = 10;   // entries staged per row on average (smem: 80 B a row)
+template <typename T, bool RESID>
+__device__ __forceinline__ void k_sweep_cs_b(int bx, int gx, int r0, int r1,
+                                             const int *__restrict__ rowptr,
+                                             const int *__restrict__ colp,
+                                             const T *__restrict__ pv, const T *__restrict__ dinv,
+                                             const T *__restrict__ b, T *x, T *r) {
+  __shared__ int srp[kBlock + 1];
+  __shared__ int scol[kBlock * kStageLen];
+  __shared__ T sval[kBlock * kStageLen];
+  int q0 = r0 + bx * kBlock;
+  int nrow = min(kBlock, r1 - q0);
+  for (int i = threadIdx.x; i <= nrow; i += kBlock) srp[i] = __ldcs(rowptr + q0 + i);
+  __syncthreads();
+  int base = srp[0], cnt = srp[nrow] - base;
+  bool staged = cnt <= kBlock * kStageLen;   // else read the row from global memory
+  if (staged)
+    for (int i = threadIdx.x; i < cnt; i += kBlock) {
+      scol[i] = __ldcs(colp + base + i);
+      sval[i] = __ldcs(pv + base + i);
+    }
+  __syncthreads();
+  int t = threadIdx.x;
+  if (t >= nrow) return;
+  int q = q0 + t;
+  int e = srp[t] - base, e1 = srp[t + 1] - base;
+  T s0 = T(0), s1 = T(0);
+  for (int k = 0; e + k < e1; ++k) {
+    int ek = e + k;
+    T v = staged ? sval[ek] : __ldcs(pv + base + ek);
+    int c = staged ? scol[ek] : __ldcs(colp + base + ek);
+    if (k < 8 && (k & 1)) s1 = fma(v, x[c], s1);
+    else s0 = fma(v, x[c], s0);
+  }
+  T sum = s0 + s1;
+  if (RESID) {
+    r[q] = b[q] - sum;
+  } else {
+    T di = dinv[q];
+    if (di != T(0)) x[q] = fma(b[q] - sum, di, x[q]);
+  }
+}
+
 template <int G, typename T>
 __device__ __forceinline__ void k_resid_cg_b(int bx, int gx, int r0, int r1,
                                              const int *__restrict__ rowptr,

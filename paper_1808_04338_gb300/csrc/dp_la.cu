@@ -1197,6 +1197,24 @@ __global__ void __launch_bounds__(kBlock) k_resid_cg(int r0, int r1, const int *
   k_resid_cg_b<G, T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_cs(int r0, int r1, const int *__restrict__ rowptr,
+                                                  const int *__restrict__ colp,
+                                                  const T *__restrict__ pv,
+                                                  const T *__restrict__ dinv,
+                                                  const T *__restrict__ b, T *x) {
+  k_sweep_cs_b<T, false>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x, nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_resid_cs(int r0, int r1, const int *__restrict__ rowptr,
+                                                     const int *__restrict__ colp,
+                                                     const T *__restrict__ pv,
+                                                     const T *__restrict__ b, T *x,
+                                                     T *__restrict__ r) {
+  k_sweep_cs_b<T, true>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, nullptr, b, x, r);
+}
+
 template <typename T> struct L0C;
 template <> struct L0C<double> {
   static const double *pv(const Sim *s) { return s->l0_pv; }
@@ -1235,7 +1253,10 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
       DP_SWITCH_G(s->l0_G, DP_LAUNCH(s, (k_gs_cg<GG, T>), nblk((long long)(r1 - r0) * GG), kBlock,
                                      0, r0, r1, s->lu_rowptr, s->l0_colp, L0C<T>::pv(s),
                                      L0C<T>::dinv(s), b, x));
-    } else
+    } else if (s->l0_G == 0)
+      DP_LAUNCH(s, k_gs_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+                L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
+    else
       DP_LAUNCH(s, k_gs_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
   }
@@ -1259,7 +1280,10 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
         DP_SWITCH_G(s->l0_G, DP_LAUNCH(s, (k_resid_cg<GG, T>), nblk((long long)(r1 - r0) * GG),
                                        kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                                        L0C<T>::pv(s), b, x, r));
-      } else
+      } else if (s->l0_G == 0)
+        DP_LAUNCH(s, k_resid_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+                  L0C<T>::pv(s), b, (T *)x, r);
+      else
         DP_LAUNCH(s, k_resid_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, x, r);
     }
@@ -1445,15 +1469,16 @@ static int tune_level(Sim *s, int l, int reps, std::string &rep) {
   return DP_OK;
 }
 
-// Level 0 in colour order: lanes per row (1, 2, 4, 8) of its short-row
-// Gauss-Seidel colours and residual, timed as one forward sweep and one
-// residual on the level's own vectors.
+// Level 0 in colour order: the kernel of its short-row Gauss-Seidel colours
+// and residual, timed as one forward sweep and one residual on the level's
+// own vectors: a thread per row (1), a CTA's rows staged in shared memory
+// (0), or 2, 4, 8 lanes per row.
 template <typename T>
 static int tune_l0(Sim *s, int reps, std::string &rep) {
   if (!l0c_on(s)) return DP_OK;
   Level &L = s->lev[0];
   T *x = LV<T>::x(L), *b = LV<T>::b(L), *r = LV<T>::r(L);
-  static const int cand[] = {1, 2, 4, 8};
+  static const int cand[] = {1, 0, 2, 4, 8};   // 0: the rows staged in shared memory
   int old = s->l0_G, best = old;
   float best_ms = 1e30f;
   std::string line;
