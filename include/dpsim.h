@@ -321,16 +321,40 @@ int sim_solver_sizes(dp_sim *sim, int32_t *nb, int32_t *nnzb);
 
 /* Autotuning of launch shapes (no counterpart in the paper): for every AMG
  * level, times each lanes-per-row variant (1..32) of the kernel of its
- * smoother's level operator, of the prolongation and of the restriction,
- * `reps` launches each with CUDA events on the simulation stream, on the
- * level's own work vectors, and keeps the fastest; the Arnoldi steps' CUDA
- * graphs are captured again on the next solve.  Colourings, aggregates and
- * operators do not change, but the summation order of those kernels does,
- * so results differ from the untuned schedule at rounding level (and a
- * schedule picked by timing can differ between runs).  Needs the AMG
- * hierarchy: call after one sim_solve_step or sim_advance with precond 2.
- * `report` (may be NULL) receives one text line per decision. */
+ * smoother's level operator, of the prolongation and of the restriction;
+ * for level 0 in colour order, the kernel of its Gauss-Seidel colours and
+ * residual (see sim_set_l0_kernel); and the V-cycle schedule below the
+ * cluster level (one cluster launch or a launch per phase).  Each candidate
+ * runs `reps` times, timed with CUDA events on the simulation stream on the
+ * level's own work vectors, and the fastest is kept; the Arnoldi steps'
+ * CUDA graphs are captured again on the next solve.  Colourings, aggregates
+ * and operators do not change, but the summation order of some of those
+ * kernels does, so results differ from the untuned schedule at rounding
+ * level (and a schedule picked by timing can differ between runs).  Needs
+ * the AMG hierarchy: call after one sim_solve_step or sim_advance with
+ * precond 2.  `report` (may be NULL) receives one text line per decision.
+ * Returns DP_ETIMEOUT (and the realisation must be destroyed) when a timed
+ * kernel's bounded device wait gave up. */
 int sim_autotune(dp_sim *sim, int32_t reps, char *report, int32_t report_len);
+
+/* Sets the kernel of level 0's Gauss-Seidel colours and residual when level
+ * 0 runs in the ILU(0) colour order (what sim_autotune chooses; the default
+ * is 1):
+ *    1  a thread per row;
+ *    0  a CTA's rows and their entries staged in shared memory first;
+ *   -1, -2, -3  a persistent kernel whose producer warp brings tiles of
+ *       256 rows into shared memory with bulk asynchronous copies while the
+ *       other warps compute the previous tile: two stages of up to 8
+ *       entries a row on average (-1), three of 6 (-2), two of 4 (-3); a
+ *       tile with more entries brings its row pointers only.  They need the
+ *       level's arrays at 16-byte boundaries (else they run as 1); their
+ *       waits are bounded, and one that gives up makes the next
+ *       sim_solve_step return DP_ETIMEOUT;
+ *    2, 4, 8  lanes per row (a row's entries split between the lanes).
+ * 1, 0, -1, -2 and -3 sum a row's products in the same order and give the
+ * same results bit for bit; 2, 4 and 8 differ from them at rounding level.
+ * Returns DP_EINVAL for another value.  Takes effect from the next solve. */
+int sim_set_l0_kernel(dp_sim *sim, int32_t variant);
 
 /* Device bytes the realisation holds through its allocator now, and the
  * most it has held at once (both may be NULL).  Host only, no CUDA call. */

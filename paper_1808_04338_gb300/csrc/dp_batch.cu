@@ -605,6 +605,12 @@ static void ilu_sweeps(const Sim *s, std::vector<Sweep> &fwd, std::vector<Sweep>
 
 // level-0 Gauss-Seidel colours (forward, from zero when pre-smoothing) and
 // the residual's runs, as in gs_sweep_c and resid_c
+// Lanes per row of a member's level-0 colour kernels inside the batch: the
+// member's own choice, except that the pipelined persistent kernel (-1; a
+// launch walks one member's tiles) runs as the thread-per-row kernel, whose
+// results are the same bit for bit.
+static int batch_lanes(int l0_G) { return l0_G < 0 ? 1 : l0_G; }
+
 static void gs_colours(const Sim *s, bool forward, bool from_zero, std::vector<Sweep> &out) {
   int nc = s->ncolour;
   bool first = from_zero;
@@ -757,7 +763,7 @@ static int build_plan(dp_batch *b) {
       std::vector<Sweep> cs;
       gs_colours(s, forward, from_zero, cs);
       for (auto &w : cs) {
-        AGsC a{w.var, s->l0_G, w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf,
+        AGsC a{w.var, batch_lanes(s->l0_G), w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf,
                s->dinv_cf, s->lev[0].bf, s->lev[0].xf};
         P[k].push_back({a, w.grid});
       }
@@ -775,7 +781,7 @@ static int build_plan(dp_batch *b) {
       std::vector<Sweep> rs;
       resid_runs(s, rs);
       for (auto &w : rs) {
-        AResC a{w.var, s->l0_G, w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf,
+        AResC a{w.var, batch_lanes(s->l0_G), w.grid, w.r0, w.r1, s->lu_rowptr, s->l0_colp, s->l0_pvf,
                 s->lev[0].bf, s->lev[0].xf, s->lev[0].rf};
         P[k].push_back({a, w.grid});
       }

@@ -171,6 +171,7 @@ int solve_update(Sim *s, int rc);
 int solve_finish(Sim *s, int rc, int it, double rr, double eta, float ms_setup, float ms_solve,
                  dp_stats *st);
 void new_timestep(Sim *s);
+int device_waits(Sim *s);   // DP_ETIMEOUT when a kernel's bounded wait gave up
 int timestep_begin(Sim *s);
 int timestep_restore(Sim *s);
 
@@ -357,10 +358,15 @@ struct Sim {
   bool have_lq = false;
   dp_stats last{};
 
-  // Records a failure's message; a CUDA failure also marks the realisation
-  // unusable (every later call returns DP_ECUDA), other codes do not.
+  // device flag of the bounded waits (set by a kernel whose wait gave up)
+  int *dev_err = nullptr;
+  bool waits_used = false;   // a kernel with bounded waits ran since the flag was read
+
+  // Records a failure's message; a CUDA failure or a device wait that gave
+  // up also marks the realisation unusable (every later call returns that
+  // code), other codes do not.
   void fail(int code, const std::string &m) {
-    if (code == DP_ECUDA && err.code != DP_ECUDA) { err.code = code; err.msg = m; }
+    if ((code == DP_ECUDA || code == DP_ETIMEOUT) && err.code == 0) { err.code = code; err.msg = m; }
     last_error = m;
   }
 };

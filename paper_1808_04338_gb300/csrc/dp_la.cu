@@ -10,6 +10,7 @@
 
 #include "dp_internal.h"
 #include "dp_kernels.cuh"
+#include "dp_tma.cuh"
 
 namespace dp {
 
@@ -430,7 +431,7 @@ int ilu_setup(Sim *s) {
   s->colour = (int *)dalloc(s, (size_t)n * 4);
   s->perm = (int *)dalloc(s, (size_t)n * 4);
   s->iperm = (int *)dalloc(s, (size_t)n * 4);
-  s->lu_rowptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
+  s->lu_rowptr = (int *)dalloc(s, ((size_t)n + 1) * 4 + 16);   // + the bulk copies' overrun
   s->lu_dpos = (int *)dalloc(s, (size_t)n * 4);
   s->lu_col = (int *)dalloc(s, (size_t)s->K.nnz * 4);
   s->lu_src = (int *)dalloc(s, (size_t)s->K.nnz * 4);
@@ -1052,7 +1053,7 @@ __global__ void k_map_copy(long long n, const int *map, const int *in, int *out)
 static int l0c_setup(Sim *s) {
   Level &L = s->lev[0];
   int n = L.n;
-  s->l0_colp = (int *)dalloc(s, (size_t)std::max(L.nnz, 1) * 4);
+  s->l0_colp = (int *)dalloc(s, (size_t)std::max(L.nnz, 1) * 4 + 16);
   s->r0_colp = (int *)dalloc(s, (size_t)std::max(L.r_nnz, 1) * 4);
   s->p0c_rowptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
   s->p0c_col = (int *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
@@ -1095,8 +1096,8 @@ int l0_refresh(Sim *s, bool coarse) {
     for (int c = 0; c <= L.ncolour; ++c)
       if (L.cstart[c] != s->lu_cstart[c]) return DP_OK;
     size_t nnz = (size_t)std::max(L.nnz, 1);
-    if (s->opt.precision >= 1) s->l0_pvf = (float *)dalloc(s, nnz * 4);
-    else s->l0_pv = (double *)dalloc(s, nnz * 8);
+    if (s->opt.precision >= 1) s->l0_pvf = (float *)dalloc(s, nnz * 4 + 16);
+    else s->l0_pv = (double *)dalloc(s, nnz * 8 + 32);
     if (!s->l0_pvf && !s->l0_pv) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
     s->l0_lu = true;
     first = true;
@@ -1215,6 +1216,179 @@ __global__ void __launch_bounds__(kBlock) k_resid_cs(int r0, int r1, const int *
   k_sweep_cs_b<T, true>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, nullptr, b, x, r);
 }
 
+// Level-0 Gauss-Seidel colour (RESID false) or residual rows (RESID true)
+// as a pipelined persistent kernel: each CTA walks tiles of kTT consecutive
+// rows of [r0, r1) (tile blockIdx.x, + gridDim.x, ...).  A producer warp
+// brings a tile's row pointers, columns and values into shared memory with
+// bulk asynchronous copies (S stages, full/empty mbarriers), so the matrix
+// stream of the next tiles is in flight while the kTT consumer threads (a
+// thread per row) gather x for the current one; 1/a_ii and b are read per
+// thread before the wait.  A stage holds CAPR entries a row on average;
+// a tile with more entries brings only its row pointers and its threads
+// read their entries from global memory.  The row's products are summed as
+// in k_gs_c (entries 1, 3, 5, 7 into one accumulator, the others into the
+// second), so every row's result is that kernel's bit for bit.  The copies
+// start at 16-byte boundaries below the tile's first row pointer and entry
+// and read up to three elements past the last one: the row pointer, column
+// and value arrays are allocated with 16 (32 for FP64 values) spare bytes.
+// A bounded wait that gives up sets *err and ends the thread (the producer
+// first lets its copies in flight land, again with a bound).
+constexpr int kTT = 256;
+template <typename T, int CAPR> struct TStage {
+  int rp[kTT + 8];
+  int col[CAPR * kTT];
+  T val[CAPR * kTT];
+};
+
+template <typename T, bool RESID, int S, int CAPR>
+__device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__restrict__ rowptr,
+                                               const int *__restrict__ colp,
+                                               const T *__restrict__ pv,
+                                               const T *__restrict__ dinv,
+                                               const T *__restrict__ b, T *x,
+                                               T *__restrict__ r, int *err) {
+  constexpr int kCap = CAPR * kTT;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  TStage<T, CAPR> *st = reinterpret_cast<TStage<T, CAPR> *>(tma_smem);
+  __shared__ __align__(8) uint64_t full[S], empty[S];
+  int ntile = (r1 - r0 + kTT - 1) / kTT;
+  int mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < S; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kTT);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x >= kTT) {   // the producer warp: one lane issues the copies
+    if (threadIdx.x != kTT) return;
+    int issued = 0;
+    for (int i = 0; i < mine; ++i) {
+      int k = i % S;
+      if (i >= S && !mbar_wait(&empty[k], (i / S - 1) & 1)) {
+        atomicExch(err, 1);
+        break;
+      }
+      int q0 = r0 + ((int)blockIdx.x + i * (int)gridDim.x) * kTT, nrow = min(kTT, r1 - q0);
+      int e0 = __ldg(rowptr + q0), e1 = __ldg(rowptr + q0 + nrow);
+      int aq = q0 & ~3, nrp = (q0 + nrow + 1 - aq + 3) & ~3;
+      int ae = e0 & ~3, ne = (e1 - ae + 3) & ~3;
+      bool fits = ne <= kCap;
+      mbar_arrive_tx(&full[k], (uint32_t)(4 * nrp + (fits ? ne * (4 + (int)sizeof(T)) : 0)));
+      bulk_load(st[k].rp, rowptr + aq, 4u * nrp, &full[k]);
+      if (fits && ne > 0) {
+        bulk_load(st[k].col, colp + ae, 4u * ne, &full[k]);
+        bulk_load(st[k].val, pv + ae, (uint32_t)sizeof(T) * ne, &full[k]);
+      }
+      issued = i + 1;
+    }
+    if (issued < mine)   // gave up: the copies in flight land before the thread ends
+      for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(&full[i % S], (i / S) & 1);
+    return;
+  }
+  int t = threadIdx.x;
+  for (int i = 0; i < mine; ++i) {
+    int k = i % S;
+    int q0 = r0 + ((int)blockIdx.x + i * (int)gridDim.x) * kTT, nrow = min(kTT, r1 - q0);
+    int q = q0 + t;
+    bool in = t < nrow;
+    T bq = T(0), dq = T(0);
+    if (in) {
+      bq = b[q];
+      if (!RESID) dq = dinv[q];
+    }
+    if (!mbar_wait(&full[k], (i / S) & 1)) {
+      atomicExch(err, 1);
+      return;
+    }
+    if (in) {
+      const int *rp = st[k].rp + (q0 & 3);
+      int ae = rp[0] & ~3;
+      bool fits = ((rp[nrow] - ae + 3) & ~3) <= kCap;
+      int e = rp[t], e1 = rp[t + 1];
+      T s0 = T(0), s1 = T(0);
+      for (int j = 0; e + j < e1; ++j) {
+        int ej = e + j;
+        T v = fits ? st[k].val[ej - ae] : __ldcs(pv + ej);
+        int c = fits ? st[k].col[ej - ae] : __ldcs(colp + ej);
+        if (j < 8 && (j & 1)) s1 = fma(v, x[c], s1);
+        else s0 = fma(v, x[c], s0);
+      }
+      T sum = s0 + s1;
+      if (RESID) r[q] = bq - sum;
+      else if (dq != T(0)) x[q] = fma(bq - sum, dq, x[q]);
+    }
+    mbar_arrive(&empty[k]);
+  }
+}
+
+template <typename T, int S, int CAPR>
+__global__ void __launch_bounds__(kTT + 32) k_gs_c_tma(int r0, int r1, const int *__restrict__ rowptr,
+                                                       const int *__restrict__ colp,
+                                                       const T *__restrict__ pv,
+                                                       const T *__restrict__ dinv,
+                                                       const T *__restrict__ b, T *x, int *err) {
+  sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err);
+}
+
+template <typename T, int S, int CAPR>
+__global__ void __launch_bounds__(kTT + 32) k_resid_c_tma(int r0, int r1,
+                                                          const int *__restrict__ rowptr,
+                                                          const int *__restrict__ colp,
+                                                          const T *__restrict__ pv,
+                                                          const T *__restrict__ b, T *x,
+                                                          T *__restrict__ r, int *err) {
+  sweep_tma_body<T, true, S, CAPR>(r0, r1, rowptr, colp, pv, nullptr, b, x, r, err);
+}
+
+// grid of a pipelined kernel: its tiles, at most the CTAs that fit on the
+// GPU at once (queried once per kernel, thread-safe; ID tells the kernels
+// of one signature apart)
+template <int ID, typename K>
+static int tma_grid(K kern, int smem, int rows) {
+  static const int slots = [&]() {
+    int dev = 0, nsm = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kTT + 32, smem);
+    return std::max(n, 1) * std::max(nsm, 1);
+  }();
+  return std::max(1, std::min((rows + kTT - 1) / kTT, slots));
+}
+
+// the pipelined variants: -1 two stages of up to 8 entries a row, -2 three
+// stages of 6, -3 two stages of 4 (level 0's mixed fracture/matrix tiles
+// average about 5, so those bring their row pointers only)
+template <typename T, int S, int CAPR>
+static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x) {
+  constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
+  DP_LAUNCH(s, (k_gs_c_tma<T, S, CAPR>), (tma_grid<16 * S + CAPR>(k_gs_c_tma<T, S, CAPR>, smem, r1 - r0)),
+            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err);
+}
+template <typename T, int S, int CAPR>
+static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *r) {
+  constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
+  DP_LAUNCH(s, (k_resid_c_tma<T, S, CAPR>),
+            (tma_grid<16 * S + CAPR>(k_resid_c_tma<T, S, CAPR>, smem, r1 - r0)),
+            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, b, x, r, s->dev_err);
+}
+template <typename T>
+static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
+                      T *r) {
+  s->waits_used = true;
+  if (r) {
+    if (G == -1) resid_tma<T, 2, 8>(s, r0, r1, pv, b, x, r);
+    else if (G == -2) resid_tma<T, 3, 6>(s, r0, r1, pv, b, x, r);
+    else resid_tma<T, 2, 4>(s, r0, r1, pv, b, x, r);
+  } else {
+    if (G == -1) gs_tma<T, 2, 8>(s, r0, r1, pv, dinv, b, x);
+    else if (G == -2) gs_tma<T, 3, 6>(s, r0, r1, pv, dinv, b, x);
+    else gs_tma<T, 2, 4>(s, r0, r1, pv, dinv, b, x);
+  }
+}
+
 template <typename T> struct L0C;
 template <> struct L0C<double> {
   static const double *pv(const Sim *s) { return s->l0_pv; }
@@ -1231,11 +1405,22 @@ template <> struct L0C<float> {
 // level or the cluster cycle takes level 0 itself
 static bool l0c_on(const Sim *s) { return s->l0c && s->lev.size() > 1 && s->cl_level != 0; }
 
+// The level-0 colour kernel to launch: the autotuned one, except that the
+// bulk-copy kernel (-1) needs its arrays at 16-byte boundaries (an
+// allocator passed by the caller may give less) and otherwise runs as the
+// thread-per-row kernel, which has the same results.
+template <typename T>
+static int l0_lanes(const Sim *s) {
+  if (s->l0_G >= 0) return s->l0_G;
+  auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+  return a16(s->lu_rowptr) && a16(s->l0_colp) && a16(L0C<T>::pv(s)) ? s->l0_G : 1;
+}
+
 // from_zero: x = 0 on entry (the pre-smoothing), so the first colour is the
 // reduced formula of k_gs_c_first
 template <typename T>
 static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false) {
-  int nc = s->ncolour;
+  int nc = s->ncolour, G = l0_lanes<T>(s);
   bool first = from_zero;
   for (int t = 0; t < nc; ++t) {
     int c = forward ? t : nc - 1 - t;
@@ -1249,13 +1434,15 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
     if (s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, k_gs_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
                 s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
-    else if (s->l0_G > 1) {
-      DP_SWITCH_G(s->l0_G, DP_LAUNCH(s, (k_gs_cg<GG, T>), nblk((long long)(r1 - r0) * GG), kBlock,
+    else if (G > 1) {
+      DP_SWITCH_G(G, DP_LAUNCH(s, (k_gs_cg<GG, T>), nblk((long long)(r1 - r0) * GG), kBlock,
                                      0, r0, r1, s->lu_rowptr, s->l0_colp, L0C<T>::pv(s),
                                      L0C<T>::dinv(s), b, x));
-    } else if (s->l0_G == 0)
+    } else if (G == 0)
       DP_LAUNCH(s, k_gs_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
+    else if (G < 0)
+      sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), L0C<T>::dinv(s), b, x, nullptr);
     else
       DP_LAUNCH(s, k_gs_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
@@ -1265,7 +1452,7 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
 
 template <typename T>
 static int resid_c(Sim *s, const T *b, const T *x, T *r) {
-  int nc = s->ncolour, c = 0;
+  int nc = s->ncolour, c = 0, G = l0_lanes<T>(s);
   while (c < nc) {   // runs of short-row colours in one launch, long-row colours a warp per row
     int r0 = s->lu_cstart[c];
     bool lng = s->lu_cmaxlen[c] > kLongRow;
@@ -1276,13 +1463,15 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
       if (lng)
         DP_LAUNCH(s, k_resid_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
                   s->l0_colp, L0C<T>::pv(s), b, (T *)x, r);
-      else if (s->l0_G > 1) {
-        DP_SWITCH_G(s->l0_G, DP_LAUNCH(s, (k_resid_cg<GG, T>), nblk((long long)(r1 - r0) * GG),
+      else if (G > 1) {
+        DP_SWITCH_G(G, DP_LAUNCH(s, (k_resid_cg<GG, T>), nblk((long long)(r1 - r0) * GG),
                                        kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                                        L0C<T>::pv(s), b, x, r));
-      } else if (s->l0_G == 0)
+      } else if (G == 0)
         DP_LAUNCH(s, k_resid_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, (T *)x, r);
+      else if (G < 0)
+        sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), nullptr, b, (T *)x, r);
       else
         DP_LAUNCH(s, k_resid_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, x, r);
@@ -1472,13 +1661,15 @@ static int tune_level(Sim *s, int l, int reps, std::string &rep) {
 // Level 0 in colour order: the kernel of its short-row Gauss-Seidel colours
 // and residual, timed as one forward sweep and one residual on the level's
 // own vectors: a thread per row (1), a CTA's rows staged in shared memory
-// (0), or 2, 4, 8 lanes per row.
+// (0), the tiles brought in by a producer warp's bulk copies (-1, -2, -3),
+// or 2, 4, 8 lanes per row.
 template <typename T>
 static int tune_l0(Sim *s, int reps, std::string &rep) {
   if (!l0c_on(s)) return DP_OK;
   Level &L = s->lev[0];
   T *x = LV<T>::x(L), *b = LV<T>::b(L), *r = LV<T>::r(L);
-  static const int cand[] = {1, 0, 2, 4, 8};   // 0: the rows staged in shared memory
+  // 0: the CTA's rows staged in shared memory; -1, -2, -3: the pipelined bulk-copy kernels
+  static const int cand[] = {1, 0, -1, -2, -3, 2, 4, 8};
   int old = s->l0_G, best = old;
   float best_ms = 1e30f;
   std::string line;

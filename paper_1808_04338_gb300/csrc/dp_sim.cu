@@ -89,15 +89,30 @@ LaunchScope::~LaunchScope() {
 // A realisation whose allocator failed, or that met a CUDA failure, does no
 // further work.
 static int unusable(Sim *s) {
-  if (s->err.code == DP_ECUDA) return DP_ECUDA;
+  if (s->err.code) return s->err.code;
   return s->alloc_failed ? DP_ENOMEM : DP_OK;
 }
 
 static int check(Sim *s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { s->fail(DP_ECUDA, cudaGetErrorString(e)); return DP_ECUDA; }
-  if (s->err.code == DP_ECUDA) return DP_ECUDA;
+  if (s->err.code) return s->err.code;
   return s->alloc_failed ? DP_ENOMEM : DP_OK;
+}
+
+// Reads and clears the flag of the kernels with bounded device waits (after
+// they ran): DP_ETIMEOUT when one of their waits gave up.
+int device_waits(Sim *s) {
+  if (!s->waits_used || !s->dev_err) return DP_OK;
+  s->waits_used = false;
+  int h = 0;
+  DP_CUDA(s, cudaMemcpyAsync(&h, s->dev_err, 4, cudaMemcpyDeviceToHost, s->stream));
+  DP_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (h) {
+    s->fail(DP_ETIMEOUT, "a bounded device-side wait gave up (a bulk copy did not land)");
+    return DP_ETIMEOUT;
+  }
+  return DP_OK;
 }
 
 // Forcing term of Algorithm 1 (Section 3.1): fixed, or one of the three
@@ -259,14 +274,15 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   s->norm_blocks = std::min(nblk(P.nb), 1024);
   s->norm_part = (double *)dalloc(s, (size_t)s->norm_blocks * 64);
   s->norm_out = (double *)dalloc(s, 80);
+  s->dev_err = (int *)dalloc(s, 4);
   s->norm_w = (double *)dalloc(s, 2 * nc8);
   if (!s->p || !s->sw || !s->bhp || !s->pn || !s->swn || !s->bhpn || !s->Mn || !s->R || !s->bh ||
-      !s->y || !s->norm_part || !s->norm_out || !s->norm_w || !s->pr || !s->Macc)
+      !s->y || !s->norm_part || !s->norm_out || !s->norm_w || !s->pr || !s->Macc || !s->dev_err)
     return fail(DP_ENOMEM);
   if ((rc = phys_norm_weights(s))) return fail(rc);
   cudaMemsetAsync(s->p, 0, nc8, st); cudaMemsetAsync(s->sw, 0, nc8, st);
   cudaMemsetAsync(s->bhp, 0, nw8, st); cudaMemsetAsync(s->Mn, 0, 2 * nc8, st);
-  cudaMemsetAsync(s->y, 0, nb16, st);
+  cudaMemsetAsync(s->y, 0, nb16, st); cudaMemsetAsync(s->dev_err, 0, 4, st);
   if ((rc = phys_solver_view(s))) return fail(rc);
   if ((rc = ilu_setup(s))) return fail(rc);
   if ((rc = la_alloc(s))) return fail(rc);
@@ -464,6 +480,7 @@ int solve_finish(Sim *s, int rc, int it, double rr, double eta, float ms_setup, 
   L.amg_levels = (int)s->lev.size(); L.converged = rc == DP_OK;
   L.ms_setup = ms_setup; L.ms_solve = ms_solve;
   if (st) *st = L;
+  DP_TRY(device_waits(s));
   if (rc == DP_ELINEAR) {
     s->fail(DP_ELINEAR, "FGMRES did not reach the forcing term; no update was made");
     DP_TRY(check(s));
@@ -606,10 +623,24 @@ extern "C" int sim_solver_sizes(dp_sim *s, int32_t *nb, int32_t *nnzb) {
   return DP_OK;
 }
 
+extern "C" int sim_set_l0_kernel(dp_sim *s, int32_t variant) {
+  if (!s || variant < -3 || variant > 8 || (variant > 2 && variant != 4 && variant != 8))
+    return DP_EINVAL;
+  DP_TRY(unusable(s));
+  if (s->l0_G != variant) {
+    s->l0_G = variant;
+    graphs_free(s);   // the Arnoldi steps are captured again
+    ++s->shapes;      // and a batch holding this realisation rebuilds its plan
+  }
+  return DP_OK;
+}
+
 extern "C" int sim_autotune(dp_sim *s, int32_t reps, char *report, int32_t report_len) {
   if (!s || reps < 1 || (report && report_len < 1)) return DP_EINVAL;
+  DP_TRY(unusable(s));
   std::string rep;
   DP_TRY(autotune(s, reps, rep));
+  DP_TRY(device_waits(s));
   if (report) {
     size_t n = std::min(rep.size(), (size_t)report_len - 1);
     std::memcpy(report, rep.data(), n);

@@ -162,6 +162,7 @@ def load():
     L.sim_advance_many.argtypes = [P, I, P, I, P, P]
     L.sim_footprint.argtypes = [P, P, P]
     L.sim_autotune.argtypes = [P, I, C.c_char_p, I]
+    L.sim_set_l0_kernel.argtypes = [P, I]
     L.sim_solver_sizes.argtypes = [P, P, P]
     L.dp_stream_create.argtypes = [P]
     L.dp_stream_destroy.argtypes = [P]
@@ -567,6 +568,12 @@ class Sim:
         c = np.zeros(self.snb, np.int32)
         n = self._check(load().sim_get_colours(self.h, _p(c)), "sim_get_colours")
         return c, n
+
+    def set_l0_kernel(self, variant: int):
+        """The kernel of level 0's Gauss-Seidel colours and residual (1: a
+        thread per row, 0: rows staged in shared memory, -1/-2/-3: the
+        pipelined bulk-copy kernels, 2/4/8: lanes per row)."""
+        self._check(load().sim_set_l0_kernel(self.h, int(variant)), "sim_set_l0_kernel")
 
     def autotune(self, reps: int = 20) -> str:
         """Time the AMG level kernels' launch shapes and keep the fastest;
