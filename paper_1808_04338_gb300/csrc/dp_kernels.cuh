@@ -147,27 +147,47 @@ __device__ __forceinline__ T row_dot(int e0, int e1, int lane, const int *__rest
 }
 
 // A warp per (long) row: RESID = false, one colour of Gauss-Seidel;
-// RESID = true, r = b - A x for those rows.
+// RESID = true, r = b - A x for those rows.  Row q, the warp's lane: the
+// lanes take entries lane, lane + 32, ... (two strides a trip, their loads
+// issued together), the partial sums meet in a shuffle tree; b_q and 1/a_qq
+// are read before the row.
+template <typename T, bool RESID>
+__device__ __forceinline__ void warp_row_c(int q, int lane, const int *__restrict__ rowptr,
+                                           const int *__restrict__ colp,
+                                           const T *__restrict__ pv, const T *__restrict__ dinv,
+                                           const T *__restrict__ b, T *x, T *r) {
+  T bq = T(0), di = T(0);
+  if (lane == 0) {
+    bq = b[q];
+    if (!RESID) di = dinv[q];
+  }
+  T s = T(0);
+  int e = __ldg(rowptr + q) + lane, e1 = __ldg(rowptr + q + 1);
+  for (; e + 32 < e1; e += 64) {
+    T v0 = __ldg(pv + e), v1 = __ldg(pv + e + 32);
+    int c0 = __ldg(colp + e), c1 = __ldg(colp + e + 32);
+    s = fma(v0, x[c0], s);
+    s = fma(v1, x[c1], s);
+  }
+  if (e < e1) s = fma(__ldg(pv + e), x[__ldg(colp + e)], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (RESID) {
+      r[q] = bq - s;
+    } else {
+      if (di != T(0)) x[q] = fma(bq - s, di, x[q]);
+    }
+  }
+}
+
 template <typename T, bool RESID>
 __device__ __forceinline__ void row_c_w(int bx, int r0, int r1, const int *__restrict__ rowptr,
                                         const int *__restrict__ colp, const T *__restrict__ pv,
                                         const T *__restrict__ dinv, const T *__restrict__ b,
                                         T *x, T *r) {
   int q = r0 + (int)((bx * (long long)blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
   if (q >= r1) return;   // whole warps
-  T s = T(0);
-  for (int e = __ldg(rowptr + q) + lane, e1 = __ldg(rowptr + q + 1); e < e1; e += 32)
-    s = fma(__ldg(pv + e), x[__ldg(colp + e)], s);
-  s = warp_sum(s);
-  if (lane == 0) {
-    if (RESID) {
-      r[q] = b[q] - s;
-    } else {
-      T di = dinv[q];
-      if (di != T(0)) x[q] = fma(b[q] - s, di, x[q]);
-    }
-  }
+  warp_row_c<T, RESID>(q, threadIdx.x & 31, rowptr, colp, pv, dinv, b, x, r);
 }
 
 // Deterministic reductions: a grid of dot_blocks(N) blocks writes one

@@ -1389,6 +1389,226 @@ static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv,
   }
 }
 
+// One whole Gauss-Seidel sweep of level 0 in colour order as a single
+// cooperative persistent launch (the CTAs are resident together): the
+// sweep's phases (the colours in sweep order, and for the pre-smoothing
+// first the initialisation x = b/a_ii on colour 0's rows, x = 0 on the
+// others) are separated by grid barriers.  Short-row colours go tile by tile
+// through the producer/consumer pipeline of sweep_tma_body; the producer
+// warp walks all of the sweep's tiles without waiting at the barriers (the
+// matrix does not change), so the next colour's tiles are already in
+// shared memory when its phase starts.  Long-row colours (the wells) take a
+// consumer warp per row.  Every row's arithmetic is that of k_gs_c_first,
+// k_gs_c and k_gs_c_w, so the sweep's result is theirs bit for bit.  The
+// barrier counts arrivals on bar[0] (the k-th barrier is passed at (k+1)
+// gridDim.x arrivals) and the last CTA to finish resets it (with bar[1],
+// the exit count) for the next launch; its waits, like the pipeline's,
+// give up after kWaitNs, set *err and end the CTA, and a CTA that finds
+// *err set does no more.
+constexpr int kSweepPhases = 8;
+struct SweepPlan {
+  int n;                      // rows of level 0
+  int nphase;
+  int kind[kSweepPhases];     // 0: initialisation, 1: short rows (tiles), 2: long rows
+  int r0[kSweepPhases], r1[kSweepPhases];
+};
+
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kTT) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// grid barrier of the consumer threads (every one of them reaches it: none
+// leaves the kernel before); false, for all of the CTA's consumers, when
+// the CTA has given up (abort_flag) or the wait gave up or *err is set
+__device__ __forceinline__ bool grid_barrier(unsigned *cnt, unsigned target, int *err,
+                                             volatile int *abort_flag) {
+  consumers_sync();
+  if (threadIdx.x == 0) {
+    if (*abort_flag || *(volatile int *)err) {
+      *abort_flag = 1;
+    } else {
+      __threadfence();
+      atomicAdd(cnt, 1u);
+      uint64_t t0 = global_ns();
+      while (ld_acquire(cnt) < target) {
+        if (*(volatile int *)err || global_ns() - t0 > kWaitNs) {
+          *abort_flag = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    if (*abort_flag) atomicExch(err, 1);
+  }
+  consumers_sync();
+  return !*abort_flag;
+}
+
+template <typename T, int S, int CAPR>
+__global__ void __launch_bounds__(kTT + 32) k_gs_c_sweep(SweepPlan plan,
+                                                         const int *__restrict__ rowptr,
+                                                         const int *__restrict__ colp,
+                                                         const T *__restrict__ pv,
+                                                         const T *__restrict__ dinv,
+                                                         const T *__restrict__ b, T *x,
+                                                         unsigned *bar, int *err) {
+  constexpr int kCap = CAPR * kTT;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  TStage<T, CAPR> *st = reinterpret_cast<TStage<T, CAPR> *>(tma_smem);
+  __shared__ __align__(8) uint64_t full[S], empty[S];
+  __shared__ int abort_flag;
+  const int G = (int)gridDim.x, B = (int)blockIdx.x;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < S; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kTT);
+    }
+    mbar_init_fence();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x >= kTT) {   // the producer warp
+    if (threadIdx.x != kTT) return;
+    int i = 0;
+    bool ok = true;
+    for (int p = 0; p < plan.nphase && ok; ++p) {
+      if (plan.kind[p] != 1) continue;
+      int r0 = plan.r0[p], r1 = plan.r1[p], ntile = (r1 - r0 + kTT - 1) / kTT;
+      for (int tile = B; tile < ntile; tile += G, ++i) {
+        int k = i % S;
+        if (i >= S && !mbar_wait(&empty[k], (i / S - 1) & 1)) {
+          atomicExch(err, 1);
+          ok = false;
+          break;
+        }
+        int q0 = r0 + tile * kTT, nrow = min(kTT, r1 - q0);
+        int e0 = __ldg(rowptr + q0), e1 = __ldg(rowptr + q0 + nrow);
+        int aq = q0 & ~3, nrp = (q0 + nrow + 1 - aq + 3) & ~3;
+        int ae = e0 & ~3, ne = (e1 - ae + 3) & ~3;
+        bool fits = ne <= kCap;
+        mbar_arrive_tx(&full[k], (uint32_t)(4 * nrp + (fits ? ne * (4 + (int)sizeof(T)) : 0)));
+        bulk_load(st[k].rp, rowptr + aq, 4u * nrp, &full[k]);
+        if (fits && ne > 0) {
+          bulk_load(st[k].col, colp + ae, 4u * ne, &full[k]);
+          bulk_load(st[k].val, pv + ae, (uint32_t)sizeof(T) * ne, &full[k]);
+        }
+      }
+    }
+    if (!ok)   // the copies in flight land before the thread ends
+      for (int j = max(0, i - S); j < i; ++j) mbar_wait(&full[j % S], (j / S) & 1);
+    return;
+  }
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  volatile int *abort_v = &abort_flag;
+  int i = 0, nbar = 0;
+  for (int p = 0; p < plan.nphase; ++p) {
+    if (p > 0 && !grid_barrier(bar, (unsigned)(++nbar) * (unsigned)G, err, abort_v)) return;
+    int r0 = plan.r0[p], r1 = plan.r1[p];
+    if (plan.kind[p] == 0) {   // x = b/a_ii on [r0, r1), 0 elsewhere
+      for (int q = B * kTT + t; q < plan.n; q += G * kTT) {
+        T v = T(0);
+        if (q >= r0 && q < r1) {
+          T di = dinv[q];
+          v = di != T(0) ? fma(b[q] - T(0), di, T(0)) : T(0);
+        }
+        x[q] = v;
+      }
+    } else if (plan.kind[p] == 2) {   // a warp per row
+      for (int q = r0 + B * (kTT / 32) + warp; q < r1; q += G * (kTT / 32))
+        warp_row_c<T, false>(q, lane, rowptr, colp, pv, dinv, b, x, nullptr);
+    } else {
+      int ntile = (r1 - r0 + kTT - 1) / kTT;
+      for (int tile = B; tile < ntile; tile += G, ++i) {
+        int k = i % S;
+        int q0 = r0 + tile * kTT, nrow = min(kTT, r1 - q0);
+        int q = q0 + t;
+        bool in = t < nrow;
+        T bq = T(0), dq = T(0);
+        if (in) {
+          bq = b[q];
+          dq = dinv[q];
+        }
+        // a consumer that gives up does not leave: it marks the CTA, which
+        // then skips its work up to the next barrier and ends there
+        bool ok = !*abort_v && mbar_wait(&full[k], (i / S) & 1);
+        if (!ok) *abort_v = 1;
+        if (ok && in) {
+          const int *rp = st[k].rp + (q0 & 3);
+          int ae = rp[0] & ~3;
+          bool fits = ((rp[nrow] - ae + 3) & ~3) <= kCap;
+          int e = rp[t], e1 = rp[t + 1];
+          T s0 = T(0), s1 = T(0);
+          for (int j = 0; e + j < e1; ++j) {
+            int ej = e + j;
+            T v = fits ? st[k].val[ej - ae] : __ldcs(pv + ej);
+            int c = fits ? st[k].col[ej - ae] : __ldcs(colp + ej);
+            if (j < 8 && (j & 1)) s1 = fma(v, x[c], s1);
+            else s0 = fma(v, x[c], s0);
+          }
+          T sum = s0 + s1;
+          if (dq != T(0)) x[q] = fma(bq - sum, dq, x[q]);
+        }
+        mbar_arrive(&empty[k]);
+      }
+    }
+  }
+  consumers_sync();
+  if (t == 0) {
+    if (*abort_v) {
+      atomicExch(err, 1);
+    } else if (atomicAdd(bar + 1, 1u) == (unsigned)G - 1) {   // the last CTA out
+      bar[0] = 0;
+      bar[1] = 0;
+      __threadfence();
+    }
+  }
+}
+
+// the persistent sweep: grid = the CTAs resident at once (capped by the
+// largest phase's tiles), launched cooperatively
+template <typename T, int S, int CAPR>
+static int gs_sweep_persistent(Sim *s, const SweepPlan &plan, const T *pv, const T *dinv,
+                               const T *b, T *x) {
+  constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
+  auto kern = k_gs_c_sweep<T, S, CAPR>;
+  static const int slots = [&]() {
+    int dev = 0, nsm = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kTT + 32, smem);
+    return std::max(n, 1) * std::max(nsm, 1);
+  }();
+  int tiles = 1;
+  for (int p = 0; p < plan.nphase; ++p)
+    tiles = std::max(tiles, (plan.r1[p] - plan.r0[p] + kTT - 1) / kTT);
+  int grid = std::min(slots, tiles);
+  if (s->alloc_failed) return DP_ENOMEM;
+  s->waits_used = true;
+  LaunchScope ls(s, "k_gs_c_sweep");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kTT + 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  DP_CUDA(s, cudaLaunchKernelEx(&cfg, kern, plan, (const int *)s->lu_rowptr,
+                                (const int *)s->l0_colp, pv, dinv, b, x,
+                                (unsigned *)(s->dev_err + 4), s->dev_err));
+  return DP_OK;
+}
+
 template <typename T> struct L0C;
 template <> struct L0C<double> {
   static const double *pv(const Sim *s) { return s->l0_pv; }
@@ -1421,6 +1641,29 @@ static int l0_lanes(const Sim *s) {
 template <typename T>
 static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false) {
   int nc = s->ncolour, G = l0_lanes<T>(s);
+  if (G <= -4 && nc + 1 <= kSweepPhases) {   // the whole sweep in one launch
+    SweepPlan plan{};
+    plan.n = s->lu_cstart[nc];
+    for (int t = 0; t < nc; ++t) {
+      int c = forward ? t : nc - 1 - t;
+      int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
+      if (r1 <= r0) continue;
+      int kind = s->lu_cmaxlen[c] > kLongRow ? 2 : 1;
+      if (from_zero && plan.nphase == 0) kind = 0;
+      plan.kind[plan.nphase] = kind;
+      plan.r0[plan.nphase] = r0;
+      plan.r1[plan.nphase] = r1;
+      ++plan.nphase;
+    }
+    if (from_zero && plan.nphase == 0) {   // no rows: x = 0
+      DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)plan.n * sizeof(T), s->stream));
+      return DP_OK;
+    }
+    return gs_sweep_persistent<T, 3, 6>(s, plan, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
+  }
+  if (G <= -4) G = 1;
+  if (from_zero)
+    DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)s->lu_cstart[nc] * sizeof(T), s->stream));
   bool first = from_zero;
   for (int t = 0; t < nc; ++t) {
     int c = forward ? t : nc - 1 - t;
@@ -1453,6 +1696,7 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
 template <typename T>
 static int resid_c(Sim *s, const T *b, const T *x, T *r) {
   int nc = s->ncolour, c = 0, G = l0_lanes<T>(s);
+  if (G <= -4) G = 1;   // the persistent sweep's residual: a thread per row
   while (c < nc) {   // runs of short-row colours in one launch, long-row colours a warp per row
     int r0 = s->lu_cstart[c];
     bool lng = s->lu_cmaxlen[c] > kLongRow;
@@ -1532,8 +1776,7 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x) {
   if (l == 0 && l0c_on(s)) {   // b and x in colour order
     Level &L = s->lev[0], &N = s->lev[1];
     T *r = LV<T>::r(L), *nb = LV<T>::b(N), *nx = LV<T>::x(N);
-    DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)L.n * sizeof(T), s->stream));
-    DP_TRY(gs_sweep_c<T>(s, b, x, true, true));
+    DP_TRY(gs_sweep_c<T>(s, b, x, true, true));   // sets x = 0 first
     DP_TRY(resid_c<T>(s, b, x, r));
     DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, s->r0_colp, LV<T>::rval(L), r, nb, 0));
     DP_TRY(vcycle_t<T>(s, 1, nb, nx));
@@ -1669,7 +1912,7 @@ static int tune_l0(Sim *s, int reps, std::string &rep) {
   Level &L = s->lev[0];
   T *x = LV<T>::x(L), *b = LV<T>::b(L), *r = LV<T>::r(L);
   // 0: the CTA's rows staged in shared memory; -1, -2, -3: the pipelined bulk-copy kernels
-  static const int cand[] = {1, 0, -1, -2, -3, 2, 4, 8};
+  static const int cand[] = {1, 0, -1, -2, -3, -4, 2, 4, 8};
   int old = s->l0_G, best = old;
   float best_ms = 1e30f;
   std::string line;

@@ -3,11 +3,12 @@ on a 201x199x21 field (1.68M cells, about 840k rows per colour, colour
 starts off the 16-byte grid): from the same state and hierarchy, one
 timestep with each kernel.
 
-* a thread per row (1), the CTA-staged rows (0) and the three pipelined
+* a thread per row (1), the CTA-staged rows (0), the three pipelined
   bulk-copy kernels (-1: every tile's entries fit its stage; -2: three
-  stages; -3: no tile fits, so the entries come from global memory) sum
-  every row in the same order: the timesteps end in the same state bit for
-  bit, in FP32 and in FP64;
+  stages; -3: no tile fits, so the entries come from global memory) and the
+  whole sweep as one cooperative persistent launch with grid barriers (-4)
+  sum every row in the same order: the timesteps end in the same state bit
+  for bit, in FP32 and in FP64;
 * with several tiles per CTA, the pipelined kernels reuse their stages, and
   none of their bounded waits gives up (the timestep returns DP_OK);
 * the lanes-per-row kernels (2, 4, 8) converge to the same state within the
@@ -20,7 +21,7 @@ import dp_inputs as di
 
 pytestmark = pytest.mark.gpu
 
-SAME = (1, 0, -1, -2, -3)
+SAME = (1, 0, -1, -2, -3, -4)
 
 
 def gpu():
@@ -47,7 +48,7 @@ def test_level0_kernels_agree(prob, precision):
     for v in SAME + (2, 4, 8):
         g.set_state(*start)
         g.set_l0_kernel(v)
-        g.time_kernel("_tma")
+        g.time_kernel("_tma" if v > -4 else "_sweep")
         g.kernel_timing(reset=True)
         rc, st = g.advance(prob.dt)
         _, launches[v] = g.kernel_timing(reset=True)
