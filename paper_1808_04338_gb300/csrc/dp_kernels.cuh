@@ -703,6 +703,33 @@ __device__ __forceinline__ void k_gs_cg_b(int bx, int gx, int r0, int r1,
   }
 }
 
+// Sum of a level-0 row's products from its n entries (columns cs, values
+// vs: in a shared-memory stage or in global memory): the first 8 entries'
+// columns and values, then their x, are loaded before any product, as in
+// k_gs_c, and summed in k_gs_c's order (entries 1, 3, 5, 7 into s1, the
+// others into s0), so the result is that kernel's bit for bit.
+template <typename T>
+__device__ __forceinline__ T stage_row_sum(int n, const int *cs, const T *vs, const T *x) {
+  constexpr int kB = 8;
+  int c[kB];
+  T v[kB], xv[kB];
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    c[j] = j < n ? cs[j] : 0;
+    v[j] = j < n ? vs[j] : T(0);
+  }
+#pragma unroll
+  for (int j = 0; j < kB; ++j) xv[j] = j < n ? x[c[j]] : T(0);
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int j = 0; j < kB; j += 2) {
+    if (j < n) s0 = fma(v[j], xv[j], s0);
+    if (j + 1 < n) s1 = fma(v[j + 1], xv[j + 1], s1);
+  }
+  for (int j = kB; j < n; ++j) s0 = fma(vs[j], x[cs[j]], s0);
+  return s0 + s1;
+}
+
 // Level-0 Gauss-Seidel colour (RESID false) or residual rows (RESID true)
 // with the CTA's rows staged: a CTA of kBlock threads takes rows q0 ..
 // q0+255 of the colour range, loads their row pointers and then all their
@@ -738,15 +765,8 @@ __device__ __forceinline__ void k_sweep_cs_b(int bx, int gx, int r0, int r1,
   if (t >= nrow) return;
   int q = q0 + t;
   int e = srp[t] - base, e1 = srp[t + 1] - base;
-  T s0 = T(0), s1 = T(0);
-  for (int k = 0; e + k < e1; ++k) {
-    int ek = e + k;
-    T v = staged ? sval[ek] : __ldcs(pv + base + ek);
-    int c = staged ? scol[ek] : __ldcs(colp + base + ek);
-    if (k < 8 && (k & 1)) s1 = fma(v, x[c], s1);
-    else s0 = fma(v, x[c], s0);
-  }
-  T sum = s0 + s1;
+  T sum = staged ? stage_row_sum<T>(e1 - e, scol + e, sval + e, x)
+                 : stage_row_sum<T>(e1 - e, colp + base + e, pv + base + e, x);
   if (RESID) {
     r[q] = b[q] - sum;
   } else {

@@ -1222,8 +1222,9 @@ __global__ void __launch_bounds__(kBlock) k_resid_cs(int r0, int r1, const int *
 // brings a tile's row pointers, columns and values into shared memory with
 // bulk asynchronous copies (S stages, full/empty mbarriers), so the matrix
 // stream of the next tiles is in flight while the kTT consumer threads (a
-// thread per row) gather x for the current one; 1/a_ii and b are read per
-// thread before the wait.  A stage holds CAPR entries a row on average;
+// thread per row) gather x for the current one (stage_row_sum); 1/a_ii
+// and b are read per thread before the wait.  A stage holds CAPR entries a
+// row on average;
 // a tile with more entries brings only its row pointers and its threads
 // read their entries from global memory.  The row's products are summed as
 // in k_gs_c (entries 1, 3, 5, 7 into one accumulator, the others into the
@@ -1239,6 +1240,71 @@ template <typename T, int CAPR> struct TStage {
   int col[CAPR * kTT];
   T val[CAPR * kTT];
 };
+
+// The producer warp of the pipelined kernels: the CTA's tiles are tiles
+// B, B + G, ... of each of the nph row ranges [pr0[p], pr1[p]) in turn
+// (the consumers take them in the same order).  The warp's 32 lanes read
+// the row-pointer bounds of 32 coming tiles at once, then lane 0 issues
+// their copies one by one as stages come free (the bounds shuffled from
+// the lane that read them): the row pointers always, the columns and
+// values when they fit the stage.  A stage's full barrier expects exactly
+// the bytes copied into it.  When a wait gives up the warp sets *err, lets
+// the copies in flight land (bounded) and ends.
+template <typename T, int S, int CAPR>
+__device__ __forceinline__ void tile_producer(int nph, const int *pr0, const int *pr1, int B, int G,
+                                              const int *__restrict__ rowptr,
+                                              const int *__restrict__ colp,
+                                              const T *__restrict__ pv, TStage<T, CAPR> *st,
+                                              uint64_t *full, uint64_t *empty, int *err) {
+  constexpr int kCap = CAPR * kTT;
+  const int lane = threadIdx.x & 31;
+  auto mine = [&](int p) {
+    int ntile = (pr1[p] - pr0[p] + kTT - 1) / kTT;
+    return ntile > B ? (ntile - 1 - B) / G + 1 : 0;
+  };
+  int total = 0;
+  for (int p = 0; p < nph; ++p) total += mine(p);
+  int i = 0;
+  bool ok = true;
+  for (int base = 0; base < total && ok; base += 32) {
+    int q0 = 0, nrow = 0, e0 = 0, e1 = 0;
+    if (base + lane < total) {
+      int p = 0, rem = base + lane;
+      while (rem >= mine(p)) rem -= mine(p++);
+      q0 = pr0[p] + (B + rem * G) * kTT;
+      nrow = min(kTT, pr1[p] - q0);
+      e0 = __ldg(rowptr + q0);
+      e1 = __ldg(rowptr + q0 + nrow);
+    }
+    int cnt = min(32, total - base);
+    for (int j = 0; j < cnt; ++j, ++i) {
+      int tq0 = __shfl_sync(0xffffffffu, q0, j), tn = __shfl_sync(0xffffffffu, nrow, j);
+      int te0 = __shfl_sync(0xffffffffu, e0, j), te1 = __shfl_sync(0xffffffffu, e1, j);
+      int k = i % S;
+      int w = 1;
+      if (lane == 0 && i >= S) w = mbar_wait(&empty[k], (i / S - 1) & 1);
+      if (!__shfl_sync(0xffffffffu, w, 0)) {
+        ok = false;
+        break;
+      }
+      if (lane == 0) {
+        int aq = tq0 & ~3, nrp = (tq0 + tn + 1 - aq + 3) & ~3;
+        int ae = te0 & ~3, ne = (te1 - ae + 3) & ~3;
+        bool fits = ne <= kCap;
+        mbar_arrive_tx(&full[k], (uint32_t)(4 * nrp + (fits ? ne * (4 + (int)sizeof(T)) : 0)));
+        bulk_load(st[k].rp, rowptr + aq, 4u * nrp, &full[k]);
+        if (fits && ne > 0) {
+          bulk_load(st[k].col, colp + ae, 4u * ne, &full[k]);
+          bulk_load(st[k].val, pv + ae, (uint32_t)sizeof(T) * ne, &full[k]);
+        }
+      }
+    }
+  }
+  if (!ok && lane == 0) {   // the copies in flight land before the warp ends
+    atomicExch(err, 1);
+    for (int j = max(0, i - S); j < i; ++j) mbar_wait(&full[j % S], (j / S) & 1);
+  }
+}
 
 template <typename T, bool RESID, int S, int CAPR>
 __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__restrict__ rowptr,
@@ -1261,30 +1327,9 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
     mbar_init_fence();
   }
   __syncthreads();
-  if (threadIdx.x >= kTT) {   // the producer warp: one lane issues the copies
-    if (threadIdx.x != kTT) return;
-    int issued = 0;
-    for (int i = 0; i < mine; ++i) {
-      int k = i % S;
-      if (i >= S && !mbar_wait(&empty[k], (i / S - 1) & 1)) {
-        atomicExch(err, 1);
-        break;
-      }
-      int q0 = r0 + ((int)blockIdx.x + i * (int)gridDim.x) * kTT, nrow = min(kTT, r1 - q0);
-      int e0 = __ldg(rowptr + q0), e1 = __ldg(rowptr + q0 + nrow);
-      int aq = q0 & ~3, nrp = (q0 + nrow + 1 - aq + 3) & ~3;
-      int ae = e0 & ~3, ne = (e1 - ae + 3) & ~3;
-      bool fits = ne <= kCap;
-      mbar_arrive_tx(&full[k], (uint32_t)(4 * nrp + (fits ? ne * (4 + (int)sizeof(T)) : 0)));
-      bulk_load(st[k].rp, rowptr + aq, 4u * nrp, &full[k]);
-      if (fits && ne > 0) {
-        bulk_load(st[k].col, colp + ae, 4u * ne, &full[k]);
-        bulk_load(st[k].val, pv + ae, (uint32_t)sizeof(T) * ne, &full[k]);
-      }
-      issued = i + 1;
-    }
-    if (issued < mine)   // gave up: the copies in flight land before the thread ends
-      for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(&full[i % S], (i / S) & 1);
+  if (threadIdx.x >= kTT) {   // the producer warp
+    tile_producer<T, S, CAPR>(1, &r0, &r1, (int)blockIdx.x, (int)gridDim.x, rowptr, colp, pv, st,
+                              full, empty, err);
     return;
   }
   int t = threadIdx.x;
@@ -1307,15 +1352,8 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
       int ae = rp[0] & ~3;
       bool fits = ((rp[nrow] - ae + 3) & ~3) <= kCap;
       int e = rp[t], e1 = rp[t + 1];
-      T s0 = T(0), s1 = T(0);
-      for (int j = 0; e + j < e1; ++j) {
-        int ej = e + j;
-        T v = fits ? st[k].val[ej - ae] : __ldcs(pv + ej);
-        int c = fits ? st[k].col[ej - ae] : __ldcs(colp + ej);
-        if (j < 8 && (j & 1)) s1 = fma(v, x[c], s1);
-        else s0 = fma(v, x[c], s0);
-      }
-      T sum = s0 + s1;
+      T sum = fits ? stage_row_sum<T>(e1 - e, st[k].col + (e - ae), st[k].val + (e - ae), x)
+                   : stage_row_sum<T>(e1 - e, colp + e, pv + e, x);
       if (RESID) r[q] = bq - sum;
       else if (dq != T(0)) x[q] = fma(bq - sum, dq, x[q]);
     }
@@ -1474,35 +1512,14 @@ __global__ void __launch_bounds__(kTT + 32) k_gs_c_sweep(SweepPlan plan,
     abort_flag = 0;
   }
   __syncthreads();
-  if (threadIdx.x >= kTT) {   // the producer warp
-    if (threadIdx.x != kTT) return;
-    int i = 0;
-    bool ok = true;
-    for (int p = 0; p < plan.nphase && ok; ++p) {
-      if (plan.kind[p] != 1) continue;
-      int r0 = plan.r0[p], r1 = plan.r1[p], ntile = (r1 - r0 + kTT - 1) / kTT;
-      for (int tile = B; tile < ntile; tile += G, ++i) {
-        int k = i % S;
-        if (i >= S && !mbar_wait(&empty[k], (i / S - 1) & 1)) {
-          atomicExch(err, 1);
-          ok = false;
-          break;
-        }
-        int q0 = r0 + tile * kTT, nrow = min(kTT, r1 - q0);
-        int e0 = __ldg(rowptr + q0), e1 = __ldg(rowptr + q0 + nrow);
-        int aq = q0 & ~3, nrp = (q0 + nrow + 1 - aq + 3) & ~3;
-        int ae = e0 & ~3, ne = (e1 - ae + 3) & ~3;
-        bool fits = ne <= kCap;
-        mbar_arrive_tx(&full[k], (uint32_t)(4 * nrp + (fits ? ne * (4 + (int)sizeof(T)) : 0)));
-        bulk_load(st[k].rp, rowptr + aq, 4u * nrp, &full[k]);
-        if (fits && ne > 0) {
-          bulk_load(st[k].col, colp + ae, 4u * ne, &full[k]);
-          bulk_load(st[k].val, pv + ae, (uint32_t)sizeof(T) * ne, &full[k]);
-        }
+  if (threadIdx.x >= kTT) {   // the producer warp, over the sweep's short-row phases
+    int pr0[kSweepPhases], pr1[kSweepPhases], nph = 0;
+    for (int p = 0; p < plan.nphase; ++p)
+      if (plan.kind[p] == 1) {
+        pr0[nph] = plan.r0[p];
+        pr1[nph++] = plan.r1[p];
       }
-    }
-    if (!ok)   // the copies in flight land before the thread ends
-      for (int j = max(0, i - S); j < i; ++j) mbar_wait(&full[j % S], (j / S) & 1);
+    tile_producer<T, S, CAPR>(nph, pr0, pr1, B, G, rowptr, colp, pv, st, full, empty, err);
     return;
   }
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -1544,15 +1561,8 @@ __global__ void __launch_bounds__(kTT + 32) k_gs_c_sweep(SweepPlan plan,
           int ae = rp[0] & ~3;
           bool fits = ((rp[nrow] - ae + 3) & ~3) <= kCap;
           int e = rp[t], e1 = rp[t + 1];
-          T s0 = T(0), s1 = T(0);
-          for (int j = 0; e + j < e1; ++j) {
-            int ej = e + j;
-            T v = fits ? st[k].val[ej - ae] : __ldcs(pv + ej);
-            int c = fits ? st[k].col[ej - ae] : __ldcs(colp + ej);
-            if (j < 8 && (j & 1)) s1 = fma(v, x[c], s1);
-            else s0 = fma(v, x[c], s0);
-          }
-          T sum = s0 + s1;
+          T sum = fits ? stage_row_sum<T>(e1 - e, st[k].col + (e - ae), st[k].val + (e - ae), x)
+                       : stage_row_sum<T>(e1 - e, colp + e, pv + e, x);
           if (dq != T(0)) x[q] = fma(bq - sum, dq, x[q]);
         }
         mbar_arrive(&empty[k]);
