@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kBlock) kb_ilu_result(const ARes *args, const 
 __global__ void __launch_bounds__(kBlock) kb_presid(const APres *args, const Seg seg, int j) {
   TILE(APres)
   k_bsr_presid_f32_b(t.bx, a.gx, a.n, a.nL, a.nc, a.nlong, a.rowptr, a.col, a.pf, a.x,
-                     a.b + (long long)j * a.bjs, a.rp, a.omap);
+                     a.b + (long long)j * a.bjs, a.rp, a.omap, X0Init{});
 }
 
 __global__ void __launch_bounds__(kBlock) kb_resid(const AResid *args, const Seg seg, int j) {

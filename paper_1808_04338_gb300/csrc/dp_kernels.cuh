@@ -296,6 +296,28 @@ __device__ __forceinline__ void k_bsr_resid_f32_b(int bx, int gx, int n, int nL,
   }
 }
 
+// The start of level 0's pre-smoothing fused into the kernel that writes
+// its right-hand side (level 0 in colour order, the sweep starting from x =
+// 0): with x set, every row's x is written as well, b/a_ii (the reduced
+// Gauss-Seidel formula, as in k_gs_c_first) on the first colour's rows
+// [f0, f1), 0 on the others.
+struct X0Init {
+  float *x = nullptr;
+  const float *dinv = nullptr;
+  int f0 = 0, f1 = 0;
+};
+__device__ __forceinline__ void put_b0(float *rp, int pos, float v, const X0Init &xi) {
+  rp[pos] = v;
+  if (xi.x) {
+    float o = 0.f;
+    if (pos >= xi.f0 && pos < xi.f1) {
+      float di = xi.dinv[pos];
+      o = di != 0.f ? fmaf(v - 0.f, di, 0.f) : 0.f;
+    }
+    xi.x[pos] = o;
+  }
+}
+
 __device__ __forceinline__ void k_bsr_presid_f32_b(int bx, int gx, int n, int nL, int nc, int nlong,
                                                           const int *__restrict__ rowptr,
                                                           const int *__restrict__ col,
@@ -303,7 +325,8 @@ __device__ __forceinline__ void k_bsr_presid_f32_b(int bx, int gx, int n, int nL
                                                           const float *__restrict__ x,
                                                           const double *__restrict__ b,
                                                           float *__restrict__ rp,
-                                                          const int *__restrict__ omap) {
+                                                          const int *__restrict__ omap,
+                                                          const X0Init &xi) {
   const float2 *x2 = reinterpret_cast<const float2 *>(x);
   if (bx == 0) {
     int lane = threadIdx.x & 31;
@@ -316,7 +339,7 @@ __device__ __forceinline__ void k_bsr_presid_f32_b(int bx, int gx, int n, int nL
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) rp[omap ? omap[row] : row] = float(b[2 * (size_t)row]) - s;
+      if (lane == 0) put_b0(rp, omap ? omap[row] : row, float(b[2 * (size_t)row]) - s, xi);
     }
     return;
   }
@@ -336,7 +359,7 @@ __device__ __forceinline__ void k_bsr_presid_f32_b(int bx, int gx, int n, int nL
     sh[row - q0] = s;
   }
   __syncthreads();
-  if (t < nlong) rp[omap ? __ldg(omap + t) : t] = float(b[2 * (size_t)t]) - sh[threadIdx.x];
+  if (t < nlong) put_b0(rp, omap ? __ldg(omap + t) : t, float(b[2 * (size_t)t]) - sh[threadIdx.x], xi);
 }
 
 template <typename T, typename TR>

@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc
                                                           const float *__restrict__ x,
                                                           const double *__restrict__ b,
                                                           float *__restrict__ rp,
-                                                          const int *__restrict__ omap) {
-  k_bsr_presid_f32_b(blockIdx.x, gridDim.x, n, nL, nc, nlong, rowptr, col, pf, x, b, rp, omap);
+                                                          const int *__restrict__ omap,
+                                                          X0Init xi) {
+  k_bsr_presid_f32_b(blockIdx.x, gridDim.x, n, nL, nc, nlong, rowptr, col, pf, x, b, rp, omap, xi);
 }
 
 int bsr_spmv(Sim *s, const double *x, double *y) {
@@ -1647,32 +1648,40 @@ static int l0_lanes(const Sim *s) {
 }
 
 // from_zero: x = 0 on entry (the pre-smoothing), so the first colour is the
-// reduced formula of k_gs_c_first
+// reduced formula of k_gs_c_first; preset: the kernel that wrote b has also
+// written that x (X0Init), so the sweep starts with the second colour
 template <typename T>
-static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false) {
+static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false,
+                      bool preset = false) {
   int nc = s->ncolour, G = l0_lanes<T>(s);
   if (G <= -4 && nc + 1 <= kSweepPhases) {   // the whole sweep in one launch
     SweepPlan plan{};
     plan.n = s->lu_cstart[nc];
+    bool first = from_zero;
     for (int t = 0; t < nc; ++t) {
       int c = forward ? t : nc - 1 - t;
       int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
       if (r1 <= r0) continue;
       int kind = s->lu_cmaxlen[c] > kLongRow ? 2 : 1;
-      if (from_zero && plan.nphase == 0) kind = 0;
+      if (first) {
+        first = false;
+        if (preset) continue;
+        kind = 0;
+      }
       plan.kind[plan.nphase] = kind;
       plan.r0[plan.nphase] = r0;
       plan.r1[plan.nphase] = r1;
       ++plan.nphase;
     }
-    if (from_zero && plan.nphase == 0) {   // no rows: x = 0
-      DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)plan.n * sizeof(T), s->stream));
+    if (plan.nphase == 0) {   // nothing left to do (or no rows: x = 0)
+      if (from_zero && !preset)
+        DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)plan.n * sizeof(T), s->stream));
       return DP_OK;
     }
     return gs_sweep_persistent<T, 3, 6>(s, plan, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
   }
   if (G <= -4) G = 1;
-  if (from_zero)
+  if (from_zero && !preset)
     DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)s->lu_cstart[nc] * sizeof(T), s->stream));
   bool first = from_zero;
   for (int t = 0; t < nc; ++t) {
@@ -1681,7 +1690,8 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
     if (r1 <= r0) continue;
     if (first) {
       first = false;
-      DP_LAUNCH(s, k_gs_c_first<T>, nblk(r1 - r0), kBlock, 0, r0, r1, L0C<T>::dinv(s), b, x);
+      if (!preset)
+        DP_LAUNCH(s, k_gs_c_first<T>, nblk(r1 - r0), kBlock, 0, r0, r1, L0C<T>::dinv(s), b, x);
       continue;
     }
     if (s->lu_cmaxlen[c] > kLongRow)
@@ -1780,13 +1790,15 @@ static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
 // or one l1-Jacobi sweep), residual, restriction, coarse correction,
 // prolongation, post-smoothing (colours reversed, or one l1-Jacobi sweep);
 // dense LU on the coarsest level.
+// x_preset: level 0 in colour order and the pre-smoothing's first colour
+// (and x = 0 on the other rows) already written with b (X0Init)
 template <typename T>
-static int vcycle_t(Sim *s, int l, const T *b, T *x) {
+static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
   if (l == s->cl_level) return coarse_cycle<T>(s, l, b, x);
   if (l == 0 && l0c_on(s)) {   // b and x in colour order
     Level &L = s->lev[0], &N = s->lev[1];
     T *r = LV<T>::r(L), *nb = LV<T>::b(N), *nx = LV<T>::x(N);
-    DP_TRY(gs_sweep_c<T>(s, b, x, true, true));   // sets x = 0 first
+    DP_TRY(gs_sweep_c<T>(s, b, x, true, true, x_preset));   // from x = 0
     DP_TRY(resid_c<T>(s, b, x, r));
     DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, s->r0_colp, LV<T>::rval(L), r, nb, 0));
     DP_TRY(vcycle_t<T>(s, 1, nb, nx));
@@ -2051,10 +2063,21 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
   DP_TRY(ilu_result<float>(s, nullptr, s->z1, s->z1f));
   const int *m = l0c_on(s) ? s->iperm : nullptr;     // level-0 vectors in colour order
+  X0Init xi;   // in colour order, the pre-smoothing's start written with b
+  if (m) {
+    int f = 0;
+    while (f < s->ncolour && s->lu_cstart[f + 1] <= s->lu_cstart[f]) ++f;
+    if (f < s->ncolour) {
+      xi.x = L0.xf;
+      xi.dinv = s->dinv_cf;
+      xi.f0 = s->lu_cstart[f];
+      xi.f1 = s->lu_cstart[f + 1];
+    }
+  }
   DP_LAUNCH(s, k_bsr_presid_f32, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
             s->sv_long0, s->srowptr, s->scol, reinterpret_cast<const float2 *>(s->spf), s->z1f,
-            r, L0.bf, m);
-  DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf));
+            r, L0.bf, m, xi);
+  DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf, xi.x != nullptr));
   DP_LAUNCH(s, k_inject_f32, nblk(nb), kBlock, 0, nb, L0.xf, s->z1f, m);
   DP_LAUNCH(s, k_bsr_resid_f32, 1 + nblk(2LL * s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
             s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1f, r, s->r1f);
