@@ -190,6 +190,124 @@ __device__ __forceinline__ void row_c_w(int bx, int r0, int r1, const int *__res
   warp_row_c<T, RESID>(q, threadIdx.x & 31, rowptr, colp, pv, dinv, b, x, r);
 }
 
+// ---- long rows (the wells) done at the end of the launch before them.
+// Every CTA of that launch, once its own rows are written, takes a ticket;
+// the CTA that takes the last one sees all of the launch's writes (each
+// CTA fences before its ticket, the last one after) and then does the long
+// rows [w0, w1), R of them per warp at once, reading through L2 (__ldcg)
+// what the other CTAs wrote.  Each row's arithmetic is that of its own
+// kernel (warp_row_c, k_ilu_fwd_w), so the results are the same bit for
+// bit; the launch the rows would have had is saved.
+struct Tail {
+  int w0 = 0, w1 = 0;           // the long rows; none: no tail
+  unsigned *ticket = nullptr;   // 0 between launches: the last CTA resets it
+};
+
+// called by one thread after its CTA's rows are written
+__device__ __forceinline__ bool tail_ticket(unsigned *ticket) {
+  __threadfence();
+  bool last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (last) {
+    atomicExch(ticket, 0u);
+    __threadfence();
+  }
+  return last;
+}
+
+// R long rows per warp at once (q[k] < 0: no row), each with warp_row_c's
+// arithmetic: per lane the strides lane, lane + 32 (two a trip), then the
+// last single stride, then the shuffle tree
+template <typename T, bool RESID, int R>
+__device__ __forceinline__ void warp_rows_c(const int (&q)[R], int lane,
+                                            const int *__restrict__ rowptr,
+                                            const int *__restrict__ colp,
+                                            const T *__restrict__ pv, const T *__restrict__ dinv,
+                                            const T *__restrict__ b, T *x, T *r) {
+  int e[R], e1[R];
+  T s[R], bq[R], di[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    bool ok = q[k] >= 0;
+    e[k] = ok ? __ldcg(rowptr + q[k]) + lane : 0;
+    e1[k] = ok ? __ldcg(rowptr + q[k] + 1) : 0;
+    s[k] = bq[k] = di[k] = T(0);
+    if (ok && lane == 0) {
+      bq[k] = b[q[k]];
+      if (!RESID) di[k] = dinv[q[k]];
+    }
+  }
+  for (;;) {
+    bool two[R], any = false;
+    T v0[R], v1[R], x0[R], x1[R];
+    int c0[R], c1[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      two[k] = e[k] + 32 < e1[k];
+      any |= two[k];
+      if (two[k]) {
+        v0[k] = __ldcg(pv + e[k]);
+        v1[k] = __ldcg(pv + e[k] + 32);
+        c0[k] = __ldcg(colp + e[k]);
+        c1[k] = __ldcg(colp + e[k] + 32);
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (two[k]) {
+        x0[k] = __ldcg(x + c0[k]);
+        x1[k] = __ldcg(x + c1[k]);
+      }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (two[k]) {
+        s[k] = fma(v0[k], x0[k], s[k]);
+        s[k] = fma(v1[k], x1[k], s[k]);
+        e[k] += 64;
+      }
+  }
+  T vt[R], xt[R];
+  int ct[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    if (e[k] < e1[k]) {
+      vt[k] = __ldcg(pv + e[k]);
+      ct[k] = __ldcg(colp + e[k]);
+    }
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    if (e[k] < e1[k]) xt[k] = __ldcg(x + ct[k]);
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    if (e[k] < e1[k]) s[k] = fma(vt[k], xt[k], s[k]);
+    s[k] = warp_sum(s[k]);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (q[k] < 0) continue;
+      if (RESID) r[q[k]] = bq[k] - s[k];
+      else if (di[k] != T(0)) x[q[k]] = fma(bq[k] - s[k], di[k], __ldcg(x + q[k]));
+    }
+}
+
+// the tail's long Gauss-Seidel (or residual) rows: warp w of nwarps takes
+// rows w0 + w, w0 + w + nwarps, ..., kTailR at a time
+constexpr int kTailR = 4;
+template <typename T, bool RESID>
+__device__ __forceinline__ void gs_tail(const Tail &tl, int warp, int nwarps, int lane,
+                                        const int *__restrict__ rowptr,
+                                        const int *__restrict__ colp, const T *__restrict__ pv,
+                                        const T *__restrict__ dinv, const T *__restrict__ b,
+                                        T *x, T *r) {
+  for (int q0 = tl.w0 + warp; q0 < tl.w1; q0 += kTailR * nwarps) {
+    int q[kTailR];
+#pragma unroll
+    for (int k = 0; k < kTailR; ++k) q[k] = q0 + k * nwarps < tl.w1 ? q0 + k * nwarps : -1;
+    warp_rows_c<T, RESID, kTailR>(q, lane, rowptr, colp, pv, dinv, b, x, r);
+  }
+}
+
 // Deterministic reductions: a grid of dot_blocks(N) blocks writes one
 // partial per vector, a single warp sums the partials in block order.
 constexpr int kDotBlocks = 608;   // 4 x 152 SMs
@@ -492,6 +610,94 @@ __device__ __forceinline__ void k_ilu_fwd_w_b(int bx, int gx, int r0, int r1, in
       zp[2 * (size_t)r] = y0;
       zp[2 * (size_t)r + 1] = y1;
     }
+  }
+}
+
+// R long rows of the ILU(0) forward sweep per warp at once (rw[k] < 0: no
+// row), each with k_ilu_fwd_w's arithmetic (PIVOT: the last colour, its
+// inverted pivot applied), zp of the earlier colours read through L2
+template <typename T, typename TR, bool PIVOT, int R>
+__device__ __forceinline__ void warp_rows_ilu_fwd(const int (&rw)[R], int lane, int nL,
+                                                  const int *__restrict__ perm,
+                                                  const int *__restrict__ Lptr,
+                                                  const int *__restrict__ colp,
+                                                  const T *__restrict__ lu,
+                                                  const TR *__restrict__ rhs, T *zp) {
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  int e[R], eb[R];
+  T s0[R], s1[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    bool ok = rw[k] >= 0;
+    e[k] = ok ? __ldcg(Lptr + rw[k]) + lane : 0;
+    eb[k] = ok ? __ldcg(Lptr + rw[k] + 1) : 0;
+    s0[k] = s1[k] = T(0);
+  }
+  for (;;) {
+    bool act[R], any = false;
+    T a[R][4];
+    int c[R];
+    T2 xk[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      act[k] = e[k] < eb[k];
+      any |= act[k];
+      if (act[k]) {
+        V4<T>::load(lu + 4 * (size_t)e[k], a[k]);
+        c[k] = __ldcg(colp + e[k]);
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (act[k]) xk[k] = __ldcg(z2 + c[k]);
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (act[k]) {
+        s0[k] = fma(a[k][0], xk[k].x, fma(a[k][1], xk[k].y, s0[k]));
+        s1[k] = fma(a[k][2], xk[k].x, fma(a[k][3], xk[k].y, s1[k]));
+        e[k] += 32;
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    s0[k] = warp_sum(s0[k]);
+    s1[k] = warp_sum(s1[k]);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      int r = rw[k];
+      if (r < 0) continue;
+      int i = __ldg(perm + r);
+      T y0 = T(rhs[2 * (size_t)i]) - s0[k], y1 = T(rhs[2 * (size_t)i + 1]) - s1[k];
+      if (PIVOT) {
+        y0 = y0 - T(0);
+        y1 = y1 - T(0);
+        T d[4];
+        V4<T>::load(lu + 4 * ((size_t)nL + r), d);
+        zp[2 * (size_t)r] = fma(d[0], y0, d[1] * y1);
+        zp[2 * (size_t)r + 1] = fma(d[2], y0, d[3] * y1);
+      } else {
+        zp[2 * (size_t)r] = y0;
+        zp[2 * (size_t)r + 1] = y1;
+      }
+    }
+}
+
+template <typename T, typename TR, bool PIVOT>
+__device__ __forceinline__ void ilu_fwd_tail(const Tail &tl, int warp, int nwarps, int lane,
+                                             int nL, const int *__restrict__ perm,
+                                             const int *__restrict__ Lptr,
+                                             const int *__restrict__ colp,
+                                             const T *__restrict__ lu,
+                                             const TR *__restrict__ rhs, T *zp) {
+  for (int q0 = tl.w0 + warp; q0 < tl.w1; q0 += kTailR * nwarps) {
+    int rw[kTailR];
+#pragma unroll
+    for (int k = 0; k < kTailR; ++k) rw[k] = q0 + k * nwarps < tl.w1 ? q0 + k * nwarps : -1;
+    warp_rows_ilu_fwd<T, TR, PIVOT, kTailR>(rw, lane, nL, perm, Lptr, colp, lu, rhs, zp);
   }
 }
 

@@ -309,6 +309,25 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *_
   k_ilu_fwd_b<T, TR>(blockIdx.x, gridDim.x, r0, r1, perm, Lptr, colp, lu, rhs, zp);
 }
 
+// the same, followed in its last CTA by the next colour's long rows (the
+// wells; PIVOT: they are the last colour, their pivots applied as well)
+template <typename T, typename TR, bool PIVOT>
+__global__ void __launch_bounds__(kBlock) k_ilu_fwd_t(int r0, int r1, const int *__restrict__ perm,
+                                                      const int *__restrict__ Lptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ lu,
+                                                      const TR *__restrict__ rhs, T *zp, int nL,
+                                                      Tail tl) {
+  k_ilu_fwd_b<T, TR>(blockIdx.x, gridDim.x, r0, r1, perm, Lptr, colp, lu, rhs, zp);
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
+  __syncthreads();
+  if (last)
+    ilu_fwd_tail<T, TR, PIVOT>(tl, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31, nL, perm,
+                               Lptr, colp, lu, rhs, zp);
+}
+
 
 // Forward sweep of the first colour, whose rows have no L blocks: zp_r =
 // r_{perm[r]}, a copy.  A thread takes kRes rows (r, r + S, ...) with their
@@ -555,6 +574,23 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
   for (int c = 0; c < nc; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
+    int nx = c + 1;   // the next non-empty colour
+    while (nx < nc && s->lu_cstart[nx + 1] <= s->lu_cstart[nx]) ++nx;
+    if (c != first && s->lu_cmaxlen[c] <= kLongRow && nx < nc && s->lu_cmaxlen[nx] > kLongRow) {
+      // a short colour followed by a long one: its last CTA takes the long rows
+      Tail tl;
+      tl.w0 = s->lu_cstart[nx];
+      tl.w1 = s->lu_cstart[nx + 1];
+      tl.ticket = (unsigned *)(s->dev_err + 8);
+      if (nx == last)
+        DP_LAUNCH(s, (k_ilu_fwd_t<T, TR, true>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
+                  s->lu_Lptr, s->lu_colp, lu, r, zp, nL, tl);
+      else
+        DP_LAUNCH(s, (k_ilu_fwd_t<T, TR, false>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1,
+                  s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp, nL, tl);
+      c = nx;
+      continue;
+    }
     if (c == last && s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, (k_ilu_fwd_w<T, TR, true>), nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL,
                 s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp);
@@ -1242,6 +1278,12 @@ template <typename T, int CAPR> struct TStage {
   T val[CAPR * kTT];
 };
 
+// a barrier of the kTT consumer threads only (named barrier 1; the
+// producer warp is not waited for)
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kTT) : "memory");
+}
+
 // The producer warp of the pipelined kernels: the CTA's tiles are tiles
 // B, B + G, ... of each of the nph row ranges [pr0[p], pr1[p]) in turn
 // (the consumers take them in the same order).  The warp's 32 lanes read
@@ -1313,7 +1355,7 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
                                                const T *__restrict__ pv,
                                                const T *__restrict__ dinv,
                                                const T *__restrict__ b, T *x,
-                                               T *__restrict__ r, int *err) {
+                                               T *__restrict__ r, int *err, const Tail &tl) {
   constexpr int kCap = CAPR * kTT;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   TStage<T, CAPR> *st = reinterpret_cast<TStage<T, CAPR> *>(tma_smem);
@@ -1334,6 +1376,10 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
     return;
   }
   int t = threadIdx.x;
+  __shared__ int abort_flag, last;
+  volatile int *abort_v = &abort_flag;
+  if (t == 0) abort_flag = 0;
+  consumers_sync();
   for (int i = 0; i < mine; ++i) {
     int k = i % S;
     int q0 = r0 + ((int)blockIdx.x + i * (int)gridDim.x) * kTT, nrow = min(kTT, r1 - q0);
@@ -1344,11 +1390,11 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
       bq = b[q];
       if (!RESID) dq = dinv[q];
     }
-    if (!mbar_wait(&full[k], (i / S) & 1)) {
-      atomicExch(err, 1);
-      return;
-    }
-    if (in) {
+    // a consumer that gives up does not leave (the CTA's consumers meet at
+    // the tail's barrier): it marks the CTA, which skips the rest
+    bool ok = !*abort_v && mbar_wait(&full[k], (i / S) & 1);
+    if (!ok) *abort_v = 1;
+    if (ok && in) {
       const int *rp = st[k].rp + (q0 & 3);
       int ae = rp[0] & ~3;
       bool fits = ((rp[nrow] - ae + 3) & ~3) <= kCap;
@@ -1360,6 +1406,14 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
     }
     mbar_arrive(&empty[k]);
   }
+  if (tl.w1 <= tl.w0) {
+    if (*abort_v) atomicExch(err, 1);
+    return;
+  }
+  consumers_sync();
+  if (t == 0) last = *abort_v ? (atomicExch(err, 1), 0) : tail_ticket(tl.ticket);
+  consumers_sync();
+  if (last) gs_tail<T, RESID>(tl, t >> 5, kTT / 32, t & 31, rowptr, colp, pv, dinv, b, x, r);
 }
 
 template <typename T, int S, int CAPR>
@@ -1367,8 +1421,9 @@ __global__ void __launch_bounds__(kTT + 32) k_gs_c_tma(int r0, int r1, const int
                                                        const int *__restrict__ colp,
                                                        const T *__restrict__ pv,
                                                        const T *__restrict__ dinv,
-                                                       const T *__restrict__ b, T *x, int *err) {
-  sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err);
+                                                       const T *__restrict__ b, T *x, int *err,
+                                                       Tail tl) {
+  sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err, tl);
 }
 
 template <typename T, int S, int CAPR>
@@ -1377,8 +1432,8 @@ __global__ void __launch_bounds__(kTT + 32) k_resid_c_tma(int r0, int r1,
                                                           const int *__restrict__ colp,
                                                           const T *__restrict__ pv,
                                                           const T *__restrict__ b, T *x,
-                                                          T *__restrict__ r, int *err) {
-  sweep_tma_body<T, true, S, CAPR>(r0, r1, rowptr, colp, pv, nullptr, b, x, r, err);
+                                                          T *__restrict__ r, int *err, Tail tl) {
+  sweep_tma_body<T, true, S, CAPR>(r0, r1, rowptr, colp, pv, nullptr, b, x, r, err, tl);
 }
 
 // grid of a pipelined kernel: its tiles, at most the CTAs that fit on the
@@ -1401,32 +1456,94 @@ static int tma_grid(K kern, int smem, int rows) {
 // stages of 6, -3 two stages of 4 (level 0's mixed fracture/matrix tiles
 // average about 5, so those bring their row pointers only)
 template <typename T, int S, int CAPR>
-static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x) {
+static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
+                   const Tail &tl) {
   constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
   DP_LAUNCH(s, (k_gs_c_tma<T, S, CAPR>), (tma_grid<16 * S + CAPR>(k_gs_c_tma<T, S, CAPR>, smem, r1 - r0)),
-            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err);
+            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err, tl);
 }
 template <typename T, int S, int CAPR>
-static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *r) {
+static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *r,
+                      const Tail &tl) {
   constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
   DP_LAUNCH(s, (k_resid_c_tma<T, S, CAPR>),
             (tma_grid<16 * S + CAPR>(k_resid_c_tma<T, S, CAPR>, smem, r1 - r0)),
-            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, b, x, r, s->dev_err);
+            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, b, x, r, s->dev_err, tl);
 }
 template <typename T>
 static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
-                      T *r) {
+                      T *r, const Tail &tl) {
   s->waits_used = true;
   if (r) {
-    if (G == -1) resid_tma<T, 2, 8>(s, r0, r1, pv, b, x, r);
-    else if (G == -2) resid_tma<T, 3, 6>(s, r0, r1, pv, b, x, r);
-    else resid_tma<T, 2, 4>(s, r0, r1, pv, b, x, r);
+    if (G == -1) resid_tma<T, 2, 8>(s, r0, r1, pv, b, x, r, tl);
+    else if (G == -2) resid_tma<T, 3, 6>(s, r0, r1, pv, b, x, r, tl);
+    else resid_tma<T, 2, 4>(s, r0, r1, pv, b, x, r, tl);
   } else {
-    if (G == -1) gs_tma<T, 2, 8>(s, r0, r1, pv, dinv, b, x);
-    else if (G == -2) gs_tma<T, 3, 6>(s, r0, r1, pv, dinv, b, x);
-    else gs_tma<T, 2, 4>(s, r0, r1, pv, dinv, b, x);
+    if (G == -1) gs_tma<T, 2, 8>(s, r0, r1, pv, dinv, b, x, tl);
+    else if (G == -2) gs_tma<T, 3, 6>(s, r0, r1, pv, dinv, b, x, tl);
+    else gs_tma<T, 2, 4>(s, r0, r1, pv, dinv, b, x, tl);
   }
 }
+
+// Thread-per-row Gauss-Seidel colour, residual run and ILU(0) forward colour,
+// each followed by the long rows of the next colour in its last CTA (Tail)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_c_t(int r0, int r1, const int *__restrict__ rowptr,
+                                                   const int *__restrict__ colp,
+                                                   const T *__restrict__ pv,
+                                                   const T *__restrict__ dinv,
+                                                   const T *__restrict__ b, T *x, Tail tl) {
+  k_gs_c_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x);
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
+  __syncthreads();
+  if (last)
+    gs_tail<T, false>(tl, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31, rowptr, colp, pv,
+                      dinv, b, x, nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_resid_c_t(int r0, int r1,
+                                                      const int *__restrict__ rowptr,
+                                                      const int *__restrict__ colp,
+                                                      const T *__restrict__ pv,
+                                                      const T *__restrict__ b, T *x,
+                                                      T *__restrict__ r, Tail tl) {
+  k_resid_c_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
+  __syncthreads();
+  if (last)
+    gs_tail<T, true>(tl, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31, rowptr, colp, pv,
+                     nullptr, b, x, r);
+}
+
+// the level-0 prolongation in colour order (x += P e) followed by the
+// post-smoothing's first colour when that is the long rows (the wells)
+template <int G, typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong_c_t(int n, const int *__restrict__ prow,
+                                                        const int *__restrict__ pcol,
+                                                        const T *__restrict__ pval,
+                                                        const T *__restrict__ e, T *x,
+                                                        const int *__restrict__ rowptr,
+                                                        const int *__restrict__ colp,
+                                                        const T *__restrict__ pv,
+                                                        const T *__restrict__ dinv,
+                                                        const T *__restrict__ b, Tail tl) {
+  k_csr_mv_b<G, T, T>(blockIdx.x, gridDim.x, n, prow, pcol, pval, e, x, 1);
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
+  __syncthreads();
+  if (last)
+    gs_tail<T, false>(tl, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31, rowptr, colp, pv,
+                      dinv, b, x, nullptr);
+}
+
+// the level-0 kernels that can take the next colour's long rows
+static bool l0_tails(int G) { return G == 1 || (G <= -1 && G >= -3); }
 
 // One whole Gauss-Seidel sweep of level 0 in colour order as a single
 // cooperative persistent launch (the CTAs are resident together): the
@@ -1451,10 +1568,6 @@ struct SweepPlan {
   int kind[kSweepPhases];     // 0: initialisation, 1: short rows (tiles), 2: long rows
   int r0[kSweepPhases], r1[kSweepPhases];
 };
-
-__device__ __forceinline__ void consumers_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kTT) : "memory");
-}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   unsigned v;
@@ -1649,10 +1762,12 @@ static int l0_lanes(const Sim *s) {
 
 // from_zero: x = 0 on entry (the pre-smoothing), so the first colour is the
 // reduced formula of k_gs_c_first; preset: the kernel that wrote b has also
-// written that x (X0Init), so the sweep starts with the second colour
+// written that x (X0Init), so the sweep starts with the second colour;
+// lead_done: the sweep's first colour (long rows) was done by the last CTA
+// of the launch before it (the prolongation, k_prolong_c_t)
 template <typename T>
 static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false,
-                      bool preset = false) {
+                      bool preset = false, bool lead_done = false) {
   int nc = s->ncolour, G = l0_lanes<T>(s);
   if (G <= -4 && nc + 1 <= kSweepPhases) {   // the whole sweep in one launch
     SweepPlan plan{};
@@ -1683,18 +1798,32 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
   if (G <= -4) G = 1;
   if (from_zero && !preset)
     DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)s->lu_cstart[nc] * sizeof(T), s->stream));
-  bool first = from_zero;
+  std::vector<int> order;   // the non-empty colours in sweep order
   for (int t = 0; t < nc; ++t) {
     int c = forward ? t : nc - 1 - t;
+    if (s->lu_cstart[c + 1] > s->lu_cstart[c]) order.push_back(c);
+  }
+  auto lng = [&](int c) { return s->lu_cmaxlen[c] > kLongRow; };
+  bool first = from_zero;
+  for (size_t t = 0; t < order.size(); ++t) {
+    int c = order[t];
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
-    if (r1 <= r0) continue;
+    if (t == 0 && lead_done) continue;   // done by the launch before the sweep
     if (first) {
       first = false;
       if (!preset)
         DP_LAUNCH(s, k_gs_c_first<T>, nblk(r1 - r0), kBlock, 0, r0, r1, L0C<T>::dinv(s), b, x);
       continue;
     }
-    if (s->lu_cmaxlen[c] > kLongRow)
+    // a short colour followed by a long one takes it in its last CTA
+    Tail tl;
+    if (!lng(c) && l0_tails(G) && t + 1 < order.size() && lng(order[t + 1])) {
+      tl.w0 = s->lu_cstart[order[t + 1]];
+      tl.w1 = s->lu_cstart[order[t + 1] + 1];
+      tl.ticket = (unsigned *)(s->dev_err + 8);
+      ++t;
+    }
+    if (lng(c))
       DP_LAUNCH(s, k_gs_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
                 s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
     else if (G > 1) {
@@ -1705,7 +1834,10 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
       DP_LAUNCH(s, k_gs_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
     else if (G < 0)
-      sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), L0C<T>::dinv(s), b, x, nullptr);
+      sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), L0C<T>::dinv(s), b, x, nullptr, tl);
+    else if (tl.w1 > tl.w0)
+      DP_LAUNCH(s, k_gs_c_t<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+                L0C<T>::pv(s), L0C<T>::dinv(s), b, x, tl);
     else
       DP_LAUNCH(s, k_gs_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
@@ -1723,6 +1855,17 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
     int c1 = c + 1;
     while (c1 < nc && (s->lu_cmaxlen[c1] > kLongRow) == lng) ++c1;
     int r1 = s->lu_cstart[c1];
+    // a run of short colours followed by long ones takes them in its last CTA
+    Tail tl;
+    if (!lng && l0_tails(G) && c1 < nc) {
+      int c2 = c1;
+      while (c2 < nc && s->lu_cmaxlen[c2] > kLongRow) ++c2;
+      tl.w0 = s->lu_cstart[c1];
+      tl.w1 = s->lu_cstart[c2];
+      tl.ticket = (unsigned *)(s->dev_err + 8);
+      if (r1 > r0 && tl.w1 > tl.w0) c1 = c2;
+      else tl = Tail{};
+    }
     if (r1 > r0) {
       if (lng)
         DP_LAUNCH(s, k_resid_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
@@ -1735,7 +1878,10 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
         DP_LAUNCH(s, k_resid_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, (T *)x, r);
       else if (G < 0)
-        sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), nullptr, b, (T *)x, r);
+        sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), nullptr, b, (T *)x, r, tl);
+      else if (tl.w1 > tl.w0)
+        DP_LAUNCH(s, k_resid_c_t<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+                  L0C<T>::pv(s), b, (T *)x, r, tl);
       else
         DP_LAUNCH(s, k_resid_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, x, r);
@@ -1802,6 +1948,22 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
     DP_TRY(resid_c<T>(s, b, x, r));
     DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, s->r0_colp, LV<T>::rval(L), r, nb, 0));
     DP_TRY(vcycle_t<T>(s, 1, nb, nx));
+    // the post-smoothing starts with the last colour; when that is the long
+    // rows (the wells), the prolongation's last CTA does them
+    int last = s->ncolour - 1;
+    while (last >= 0 && s->lu_cstart[last + 1] <= s->lu_cstart[last]) --last;
+    int G = l0_lanes<T>(s);
+    if (last >= 0 && s->lu_cmaxlen[last] > kLongRow && l0_tails(G)) {
+      Tail tl;
+      tl.w0 = s->lu_cstart[last];
+      tl.w1 = s->lu_cstart[last + 1];
+      tl.ticket = (unsigned *)(s->dev_err + 8);
+      DP_SWITCH_G(L.p_G, DP_LAUNCH(s, (k_prolong_c_t<GG, T>), nblk((long long)L.n * GG), kBlock, 0,
+                                   L.n, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x,
+                                   s->lu_rowptr, s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b,
+                                   tl));
+      return gs_sweep_c<T>(s, b, x, false, false, false, true);
+    }
     DP_TRY(csr_mv<T>(s, L.n, L.p_G, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x, 1));
     return gs_sweep_c<T>(s, b, x, false);
   }
