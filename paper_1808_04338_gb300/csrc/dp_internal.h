@@ -12,6 +12,10 @@
 namespace dp {
 
 constexpr int kBlock = 256;
+// the last-CTA tickets of the long-row tails: a root count and
+// kTicketGroups group counts, each on its own 128-byte line
+constexpr int kTicketGroups = 128, kTicketStride = 32;
+constexpr int kTicketWords = (kTicketGroups + 1) * kTicketStride;
 
 // Error propagation inside the library: every CUDA call is checked, the
 // first failure is recorded on the Sim and the entry point returns DP_ECUDA.
@@ -360,6 +364,7 @@ struct Sim {
 
   // device flag of the bounded waits (set by a kernel whose wait gave up)
   int *dev_err = nullptr;
+  unsigned *tickets = nullptr;   // the last-CTA tickets of the long-row tails (zeroed)
   bool waits_used = false;   // a kernel with bounded waits ran since the flag was read
 
   // Records a failure's message; a CUDA failure or a device wait that gave

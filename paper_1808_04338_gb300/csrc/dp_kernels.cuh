@@ -200,13 +200,25 @@ __device__ __forceinline__ void row_c_w(int bx, int r0, int r1, const int *__res
 // bit; the launch the rows would have had is saved.
 struct Tail {
   int w0 = 0, w1 = 0;           // the long rows; none: no tail
-  unsigned *ticket = nullptr;   // 0 between launches: the last CTA resets it
+  unsigned *ticket = nullptr;   // kTicketWords: the counts, 0 between launches
 };
+
+// The tickets in two levels, so that thousands of CTAs do not queue on one
+// address: CTA b counts in group b mod g (g = min(gridDim.x, kTicketGroups),
+// each group's count on its own 128-byte line), the last CTA of a group
+// counts in the root, and the CTA that completes the root is the last of
+// the launch.  Each count is reset by the CTA that completes it.
 
 // called by one thread after its CTA's rows are written
 __device__ __forceinline__ bool tail_ticket(unsigned *ticket) {
+  unsigned ng = min(gridDim.x, (unsigned)kTicketGroups);
+  unsigned g = blockIdx.x % ng, gsize = (gridDim.x - g + ng - 1) / ng;
+  unsigned *grp = ticket + kTicketStride * (1 + g);
   __threadfence();
-  bool last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (atomicAdd(grp, 1u) != gsize - 1) return false;
+  atomicExch(grp, 0u);
+  __threadfence();
+  bool last = atomicAdd(ticket, 1u) == ng - 1;
   if (last) {
     atomicExch(ticket, 0u);
     __threadfence();

@@ -581,7 +581,7 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
       Tail tl;
       tl.w0 = s->lu_cstart[nx];
       tl.w1 = s->lu_cstart[nx + 1];
-      tl.ticket = (unsigned *)(s->dev_err + 8);
+      tl.ticket = s->tickets;
       if (nx == last)
         DP_LAUNCH(s, (k_ilu_fwd_t<T, TR, true>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
                   s->lu_Lptr, s->lu_colp, lu, r, zp, nL, tl);
@@ -1820,7 +1820,7 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
     if (!lng(c) && l0_tails(G) && t + 1 < order.size() && lng(order[t + 1])) {
       tl.w0 = s->lu_cstart[order[t + 1]];
       tl.w1 = s->lu_cstart[order[t + 1] + 1];
-      tl.ticket = (unsigned *)(s->dev_err + 8);
+      tl.ticket = s->tickets;
       ++t;
     }
     if (lng(c))
@@ -1862,7 +1862,7 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
       while (c2 < nc && s->lu_cmaxlen[c2] > kLongRow) ++c2;
       tl.w0 = s->lu_cstart[c1];
       tl.w1 = s->lu_cstart[c2];
-      tl.ticket = (unsigned *)(s->dev_err + 8);
+      tl.ticket = s->tickets;
       if (r1 > r0 && tl.w1 > tl.w0) c1 = c2;
       else tl = Tail{};
     }
@@ -1957,7 +1957,7 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
       Tail tl;
       tl.w0 = s->lu_cstart[last];
       tl.w1 = s->lu_cstart[last + 1];
-      tl.ticket = (unsigned *)(s->dev_err + 8);
+      tl.ticket = s->tickets;
       DP_SWITCH_G(L.p_G, DP_LAUNCH(s, (k_prolong_c_t<GG, T>), nblk((long long)L.n * GG), kBlock, 0,
                                    L.n, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x,
                                    s->lu_rowptr, s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b,

@@ -275,14 +275,17 @@ extern "C" int sim_create(const dp_grid *grid, const dp_rock *rock, const dp_flu
   s->norm_part = (double *)dalloc(s, (size_t)s->norm_blocks * 64);
   s->norm_out = (double *)dalloc(s, 80);
   s->dev_err = (int *)dalloc(s, 64);   // [0] the wait flag, [4..5] the grid barrier's counts
+  s->tickets = (unsigned *)dalloc(s, (size_t)kTicketWords * 4);
   s->norm_w = (double *)dalloc(s, 2 * nc8);
   if (!s->p || !s->sw || !s->bhp || !s->pn || !s->swn || !s->bhpn || !s->Mn || !s->R || !s->bh ||
-      !s->y || !s->norm_part || !s->norm_out || !s->norm_w || !s->pr || !s->Macc || !s->dev_err)
+      !s->y || !s->norm_part || !s->norm_out || !s->norm_w || !s->pr || !s->Macc || !s->dev_err ||
+      !s->tickets)
     return fail(DP_ENOMEM);
   if ((rc = phys_norm_weights(s))) return fail(rc);
   cudaMemsetAsync(s->p, 0, nc8, st); cudaMemsetAsync(s->sw, 0, nc8, st);
   cudaMemsetAsync(s->bhp, 0, nw8, st); cudaMemsetAsync(s->Mn, 0, 2 * nc8, st);
   cudaMemsetAsync(s->y, 0, nb16, st); cudaMemsetAsync(s->dev_err, 0, 64, st);
+  cudaMemsetAsync(s->tickets, 0, (size_t)kTicketWords * 4, st);
   if ((rc = phys_solver_view(s))) return fail(rc);
   if ((rc = ilu_setup(s))) return fail(rc);
   if ((rc = la_alloc(s))) return fail(rc);
