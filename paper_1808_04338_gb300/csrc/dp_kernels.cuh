@@ -209,6 +209,12 @@ struct Tail {
 // counts in the root, and the CTA that completes the root is the last of
 // the launch.  Each count is reset by the CTA that completes it.
 
+// The tail needs far more registers than the rows before it: the launch
+// bounds of a kernel with a tail keep it at the occupancy of its rows (8
+// CTAs of 256 threads an SM, 32 registers) and let the tail, which one CTA
+// runs, spill.
+constexpr int kTailMinBlocks = 8;
+
 // called by one thread after its CTA's rows are written
 __device__ __forceinline__ bool tail_ticket(unsigned *ticket) {
   unsigned ng = min(gridDim.x, (unsigned)kTicketGroups);

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *_
 // the same, followed in its last CTA by the next colour's long rows (the
 // wells; PIVOT: they are the last colour, their pivots applied as well)
 template <typename T, typename TR, bool PIVOT>
-__global__ void __launch_bounds__(kBlock) k_ilu_fwd_t(int r0, int r1, const int *__restrict__ perm,
+__global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_ilu_fwd_t(int r0, int r1, const int *__restrict__ perm,
                                                       const int *__restrict__ Lptr,
                                                       const int *__restrict__ colp,
                                                       const T *__restrict__ lu,
@@ -1272,6 +1272,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_cs(int r0, int r1, const int *
 // A bounded wait that gives up sets *err and ends the thread (the producer
 // first lets its copies in flight land, again with a bound).
 constexpr int kTT = 256;
+constexpr int kTmaMinBlocks = 6;   // the registers of the rows' loop, not of the tail's
 template <typename T, int CAPR> struct TStage {
   int rp[kTT + 8];
   int col[CAPR * kTT];
@@ -1417,7 +1418,7 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
 }
 
 template <typename T, int S, int CAPR>
-__global__ void __launch_bounds__(kTT + 32) k_gs_c_tma(int r0, int r1, const int *__restrict__ rowptr,
+__global__ void __launch_bounds__(kTT + 32, kTmaMinBlocks) k_gs_c_tma(int r0, int r1, const int *__restrict__ rowptr,
                                                        const int *__restrict__ colp,
                                                        const T *__restrict__ pv,
                                                        const T *__restrict__ dinv,
@@ -1427,7 +1428,7 @@ __global__ void __launch_bounds__(kTT + 32) k_gs_c_tma(int r0, int r1, const int
 }
 
 template <typename T, int S, int CAPR>
-__global__ void __launch_bounds__(kTT + 32) k_resid_c_tma(int r0, int r1,
+__global__ void __launch_bounds__(kTT + 32, kTmaMinBlocks) k_resid_c_tma(int r0, int r1,
                                                           const int *__restrict__ rowptr,
                                                           const int *__restrict__ colp,
                                                           const T *__restrict__ pv,
@@ -1486,9 +1487,10 @@ static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv,
 }
 
 // Thread-per-row Gauss-Seidel colour, residual run and ILU(0) forward colour,
-// each followed by the long rows of the next colour in its last CTA (Tail)
+// each followed by the long rows of the next colour in its last CTA (Tail).
+// (launch bounds: kTailMinBlocks)
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_gs_c_t(int r0, int r1, const int *__restrict__ rowptr,
+__global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_gs_c_t(int r0, int r1, const int *__restrict__ rowptr,
                                                    const int *__restrict__ colp,
                                                    const T *__restrict__ pv,
                                                    const T *__restrict__ dinv,
@@ -1504,7 +1506,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_c_t(int r0, int r1, const int *__
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_resid_c_t(int r0, int r1,
+__global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_resid_c_t(int r0, int r1,
                                                       const int *__restrict__ rowptr,
                                                       const int *__restrict__ colp,
                                                       const T *__restrict__ pv,
@@ -1523,7 +1525,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_c_t(int r0, int r1,
 // the level-0 prolongation in colour order (x += P e) followed by the
 // post-smoothing's first colour when that is the long rows (the wells)
 template <int G, typename T>
-__global__ void __launch_bounds__(kBlock) k_prolong_c_t(int n, const int *__restrict__ prow,
+__global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_prolong_c_t(int n, const int *__restrict__ prow,
                                                         const int *__restrict__ pcol,
                                                         const T *__restrict__ pval,
                                                         const T *__restrict__ e, T *x,
