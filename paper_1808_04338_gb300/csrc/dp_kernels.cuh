@@ -233,8 +233,9 @@ __device__ __forceinline__ bool tail_ticket(unsigned *ticket) {
 }
 
 // R long rows per warp at once (q[k] < 0: no row), each with warp_row_c's
-// arithmetic: per lane the strides lane, lane + 32 (two a trip), then the
-// last single stride, then the shuffle tree
+// arithmetic: per lane the products of entries lane, lane + 32, ... added
+// in that order (one stride a trip here, to keep the registers few), then
+// the shuffle tree; b and 1/a_ii read at the end
 template <typename T, bool RESID, int R>
 __device__ __forceinline__ void warp_rows_c(const int (&q)[R], int lane,
                                             const int *__restrict__ rowptr,
@@ -242,70 +243,48 @@ __device__ __forceinline__ void warp_rows_c(const int (&q)[R], int lane,
                                             const T *__restrict__ pv, const T *__restrict__ dinv,
                                             const T *__restrict__ b, T *x, T *r) {
   int e[R], e1[R];
-  T s[R], bq[R], di[R];
+  T s[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) {
     bool ok = q[k] >= 0;
     e[k] = ok ? __ldcg(rowptr + q[k]) + lane : 0;
     e1[k] = ok ? __ldcg(rowptr + q[k] + 1) : 0;
-    s[k] = bq[k] = di[k] = T(0);
-    if (ok && lane == 0) {
-      bq[k] = b[q[k]];
-      if (!RESID) di[k] = dinv[q[k]];
-    }
+    s[k] = T(0);
   }
   for (;;) {
-    bool two[R], any = false;
-    T v0[R], v1[R], x0[R], x1[R];
-    int c0[R], c1[R];
+    bool any = false;
+    T v[R], xv[R];
+    int c[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-      two[k] = e[k] + 32 < e1[k];
-      any |= two[k];
-      if (two[k]) {
-        v0[k] = __ldcg(pv + e[k]);
-        v1[k] = __ldcg(pv + e[k] + 32);
-        c0[k] = __ldcg(colp + e[k]);
-        c1[k] = __ldcg(colp + e[k] + 32);
+    for (int k = 0; k < R; ++k)
+      if (e[k] < e1[k]) {
+        any = true;
+        v[k] = __ldcg(pv + e[k]);
+        c[k] = __ldcg(colp + e[k]);
       }
-    }
     if (!any) break;
 #pragma unroll
     for (int k = 0; k < R; ++k)
-      if (two[k]) {
-        x0[k] = __ldcg(x + c0[k]);
-        x1[k] = __ldcg(x + c1[k]);
-      }
+      if (e[k] < e1[k]) xv[k] = __ldcg(x + c[k]);
 #pragma unroll
     for (int k = 0; k < R; ++k)
-      if (two[k]) {
-        s[k] = fma(v0[k], x0[k], s[k]);
-        s[k] = fma(v1[k], x1[k], s[k]);
-        e[k] += 64;
+      if (e[k] < e1[k]) {
+        s[k] = fma(v[k], xv[k], s[k]);
+        e[k] += 32;
       }
   }
-  T vt[R], xt[R];
-  int ct[R];
 #pragma unroll
-  for (int k = 0; k < R; ++k)
-    if (e[k] < e1[k]) {
-      vt[k] = __ldcg(pv + e[k]);
-      ct[k] = __ldcg(colp + e[k]);
-    }
-#pragma unroll
-  for (int k = 0; k < R; ++k)
-    if (e[k] < e1[k]) xt[k] = __ldcg(x + ct[k]);
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    if (e[k] < e1[k]) s[k] = fma(vt[k], xt[k], s[k]);
-    s[k] = warp_sum(s[k]);
-  }
+  for (int k = 0; k < R; ++k) s[k] = warp_sum(s[k]);
   if (lane == 0)
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       if (q[k] < 0) continue;
-      if (RESID) r[q[k]] = bq[k] - s[k];
-      else if (di[k] != T(0)) x[q[k]] = fma(bq[k] - s[k], di[k], __ldcg(x + q[k]));
+      if (RESID) {
+        r[q[k]] = b[q[k]] - s[k];
+      } else {
+        T di = dinv[q[k]];
+        if (di != T(0)) x[q[k]] = fma(b[q[k]] - s[k], di, __ldcg(x + q[k]));
+      }
     }
 }
 
@@ -704,6 +683,7 @@ __device__ __forceinline__ void warp_rows_ilu_fwd(const int (&rw)[R], int lane, 
     }
 }
 
+constexpr int kTailRIlu = 2;   // rows per warp at once in the ILU(0) tail
 template <typename T, typename TR, bool PIVOT>
 __device__ __forceinline__ void ilu_fwd_tail(const Tail &tl, int warp, int nwarps, int lane,
                                              int nL, const int *__restrict__ perm,
@@ -711,11 +691,11 @@ __device__ __forceinline__ void ilu_fwd_tail(const Tail &tl, int warp, int nwarp
                                              const int *__restrict__ colp,
                                              const T *__restrict__ lu,
                                              const TR *__restrict__ rhs, T *zp) {
-  for (int q0 = tl.w0 + warp; q0 < tl.w1; q0 += kTailR * nwarps) {
-    int rw[kTailR];
+  for (int q0 = tl.w0 + warp; q0 < tl.w1; q0 += kTailRIlu * nwarps) {
+    int rw[kTailRIlu];
 #pragma unroll
-    for (int k = 0; k < kTailR; ++k) rw[k] = q0 + k * nwarps < tl.w1 ? q0 + k * nwarps : -1;
-    warp_rows_ilu_fwd<T, TR, PIVOT, kTailR>(rw, lane, nL, perm, Lptr, colp, lu, rhs, zp);
+    for (int k = 0; k < kTailRIlu; ++k) rw[k] = q0 + k * nwarps < tl.w1 ? q0 + k * nwarps : -1;
+    warp_rows_ilu_fwd<T, TR, PIVOT, kTailRIlu>(rw, lane, nL, perm, Lptr, colp, lu, rhs, zp);
   }
 }
 
