@@ -201,6 +201,9 @@ __device__ __forceinline__ void row_c_w(int bx, int r0, int r1, const int *__res
 struct Tail {
   int w0 = 0, w1 = 0;           // the long rows; none: no tail
   unsigned *ticket = nullptr;   // kTicketWords: the counts, 0 between launches
+  int nb = 0;                   // the launch's blocks of rows, which its CTAs
+                                // walk (b, b + gridDim.x, ...): one wave of
+                                // CTAs, so each fences and takes a ticket once
 };
 
 // The tickets in two levels, so that thousands of CTAs do not queue on one

@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_ilu_fwd_t(int r0, in
                                                       const T *__restrict__ lu,
                                                       const TR *__restrict__ rhs, T *zp, int nL,
                                                       Tail tl) {
-  k_ilu_fwd_b<T, TR>(blockIdx.x, gridDim.x, r0, r1, perm, Lptr, colp, lu, rhs, zp);
+  for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
+    k_ilu_fwd_b<T, TR>(bx, tl.nb, r0, r1, perm, Lptr, colp, lu, rhs, zp);
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
@@ -558,6 +559,18 @@ int ilu_factor(Sim *s) {
   return DP_OK;
 }
 
+// CTAs of a launch with a long-row tail: one wave (kTailMinBlocks an SM) at
+// most, walking the launch's nb blocks of rows
+static int tail_grid(int nb) {
+  static const int slots = []() {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(nsm, 1) * kTailMinBlocks;
+  }();
+  return std::max(1, std::min(nb, slots));
+}
+
 // (LU)^-1 r with the factor in T and r (natural order) in TR; the result
 // is left in the colour-order work vector s->ilu_zp, from which the caller
 // gathers it (ilu_result) while converting or accumulating.
@@ -582,12 +595,13 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
       tl.w0 = s->lu_cstart[nx];
       tl.w1 = s->lu_cstart[nx + 1];
       tl.ticket = s->tickets;
+      tl.nb = nblk(2LL * (r1 - r0));
       if (nx == last)
-        DP_LAUNCH(s, (k_ilu_fwd_t<T, TR, true>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
+        DP_LAUNCH(s, (k_ilu_fwd_t<T, TR, true>), tail_grid(tl.nb), kBlock, 0, r0, r1, s->perm,
                   s->lu_Lptr, s->lu_colp, lu, r, zp, nL, tl);
       else
-        DP_LAUNCH(s, (k_ilu_fwd_t<T, TR, false>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1,
-                  s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp, nL, tl);
+        DP_LAUNCH(s, (k_ilu_fwd_t<T, TR, false>), tail_grid(tl.nb), kBlock, 0, r0, r1, s->perm,
+                  s->lu_Lptr, s->lu_colp, lu, r, zp, nL, tl);
       c = nx;
       continue;
     }
@@ -1495,7 +1509,8 @@ __global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_gs_c_t(int r0, int r
                                                    const T *__restrict__ pv,
                                                    const T *__restrict__ dinv,
                                                    const T *__restrict__ b, T *x, Tail tl) {
-  k_gs_c_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x);
+  for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
+    k_gs_c_b<T>(bx, tl.nb, r0, r1, rowptr, colp, pv, dinv, b, x);
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
@@ -1512,7 +1527,8 @@ __global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_resid_c_t(int r0, in
                                                       const T *__restrict__ pv,
                                                       const T *__restrict__ b, T *x,
                                                       T *__restrict__ r, Tail tl) {
-  k_resid_c_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
+  for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
+    k_resid_c_b<T>(bx, tl.nb, r0, r1, rowptr, colp, pv, b, x, r);
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
@@ -1534,7 +1550,8 @@ __global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_prolong_c_t(int n, c
                                                         const T *__restrict__ pv,
                                                         const T *__restrict__ dinv,
                                                         const T *__restrict__ b, Tail tl) {
-  k_csr_mv_b<G, T, T>(blockIdx.x, gridDim.x, n, prow, pcol, pval, e, x, 1);
+  for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
+    k_csr_mv_b<G, T, T>(bx, tl.nb, n, prow, pcol, pval, e, x, 1);
   __shared__ int last;
   __syncthreads();
   if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
@@ -1837,9 +1854,11 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
     else if (G < 0)
       sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), L0C<T>::dinv(s), b, x, nullptr, tl);
-    else if (tl.w1 > tl.w0)
-      DP_LAUNCH(s, k_gs_c_t<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
+    else if (tl.w1 > tl.w0) {
+      tl.nb = nblk(r1 - r0);
+      DP_LAUNCH(s, k_gs_c_t<T>, tail_grid(tl.nb), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x, tl);
+    }
     else
       DP_LAUNCH(s, k_gs_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
@@ -1881,9 +1900,11 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
                   L0C<T>::pv(s), b, (T *)x, r);
       else if (G < 0)
         sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), nullptr, b, (T *)x, r, tl);
-      else if (tl.w1 > tl.w0)
-        DP_LAUNCH(s, k_resid_c_t<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
-                  L0C<T>::pv(s), b, (T *)x, r, tl);
+      else if (tl.w1 > tl.w0) {
+        tl.nb = nblk(r1 - r0);
+        DP_LAUNCH(s, k_resid_c_t<T>, tail_grid(tl.nb), kBlock, 0, r0, r1, s->lu_rowptr,
+                  s->l0_colp, L0C<T>::pv(s), b, (T *)x, r, tl);
+      }
       else
         DP_LAUNCH(s, k_resid_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, x, r);
@@ -1960,7 +1981,8 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
       tl.w0 = s->lu_cstart[last];
       tl.w1 = s->lu_cstart[last + 1];
       tl.ticket = s->tickets;
-      DP_SWITCH_G(L.p_G, DP_LAUNCH(s, (k_prolong_c_t<GG, T>), nblk((long long)L.n * GG), kBlock, 0,
+      DP_SWITCH_G(L.p_G, tl.nb = nblk((long long)L.n * GG);
+                  DP_LAUNCH(s, (k_prolong_c_t<GG, T>), tail_grid(tl.nb), kBlock, 0,
                                    L.n, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x,
                                    s->lu_rowptr, s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b,
                                    tl));
