@@ -1538,29 +1538,6 @@ __global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_resid_c_t(int r0, in
                      nullptr, b, x, r);
 }
 
-// the level-0 prolongation in colour order (x += P e) followed by the
-// post-smoothing's first colour when that is the long rows (the wells)
-template <int G, typename T>
-__global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_prolong_c_t(int n, const int *__restrict__ prow,
-                                                        const int *__restrict__ pcol,
-                                                        const T *__restrict__ pval,
-                                                        const T *__restrict__ e, T *x,
-                                                        const int *__restrict__ rowptr,
-                                                        const int *__restrict__ colp,
-                                                        const T *__restrict__ pv,
-                                                        const T *__restrict__ dinv,
-                                                        const T *__restrict__ b, Tail tl) {
-  for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
-    k_csr_mv_b<G, T, T>(bx, tl.nb, n, prow, pcol, pval, e, x, 1);
-  __shared__ int last;
-  __syncthreads();
-  if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
-  __syncthreads();
-  if (last)
-    gs_tail<T, false>(tl, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31, rowptr, colp, pv,
-                      dinv, b, x, nullptr);
-}
-
 // the level-0 kernels that can take the next colour's long rows
 static bool l0_tails(int G) { return G == 1 || (G <= -1 && G >= -3); }
 
@@ -1781,12 +1758,10 @@ static int l0_lanes(const Sim *s) {
 
 // from_zero: x = 0 on entry (the pre-smoothing), so the first colour is the
 // reduced formula of k_gs_c_first; preset: the kernel that wrote b has also
-// written that x (X0Init), so the sweep starts with the second colour;
-// lead_done: the sweep's first colour (long rows) was done by the last CTA
-// of the launch before it (the prolongation, k_prolong_c_t)
+// written that x (X0Init), so the sweep starts with the second colour
 template <typename T>
 static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false,
-                      bool preset = false, bool lead_done = false) {
+                      bool preset = false) {
   int nc = s->ncolour, G = l0_lanes<T>(s);
   if (G <= -4 && nc + 1 <= kSweepPhases) {   // the whole sweep in one launch
     SweepPlan plan{};
@@ -1827,7 +1802,6 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
   for (size_t t = 0; t < order.size(); ++t) {
     int c = order[t];
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
-    if (t == 0 && lead_done) continue;   // done by the launch before the sweep
     if (first) {
       first = false;
       if (!preset)
@@ -1971,23 +1945,6 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
     DP_TRY(resid_c<T>(s, b, x, r));
     DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, s->r0_colp, LV<T>::rval(L), r, nb, 0));
     DP_TRY(vcycle_t<T>(s, 1, nb, nx));
-    // the post-smoothing starts with the last colour; when that is the long
-    // rows (the wells), the prolongation's last CTA does them
-    int last = s->ncolour - 1;
-    while (last >= 0 && s->lu_cstart[last + 1] <= s->lu_cstart[last]) --last;
-    int G = l0_lanes<T>(s);
-    if (last >= 0 && s->lu_cmaxlen[last] > kLongRow && l0_tails(G)) {
-      Tail tl;
-      tl.w0 = s->lu_cstart[last];
-      tl.w1 = s->lu_cstart[last + 1];
-      tl.ticket = s->tickets;
-      DP_SWITCH_G(L.p_G, tl.nb = nblk((long long)L.n * GG);
-                  DP_LAUNCH(s, (k_prolong_c_t<GG, T>), tail_grid(tl.nb), kBlock, 0,
-                                   L.n, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x,
-                                   s->lu_rowptr, s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b,
-                                   tl));
-      return gs_sweep_c<T>(s, b, x, false, false, false, true);
-    }
     DP_TRY(csr_mv<T>(s, L.n, L.p_G, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x, 1));
     return gs_sweep_c<T>(s, b, x, false);
   }
@@ -2110,8 +2067,8 @@ static int tune_level(Sim *s, int l, int reps, std::string &rep) {
 }
 
 // Level 0 in colour order: the kernel of its short-row Gauss-Seidel colours
-// and residual, timed as one forward sweep and one residual on the level's
-// own vectors: a thread per row (1), a CTA's rows staged in shared memory
+// and residual, timed as a V-cycle uses them (a forward sweep, the
+// residual, a backward sweep) on the level's own vectors: a thread per row (1), a CTA's rows staged in shared memory
 // (0), the tiles brought in by a producer warp's bulk copies (-1, -2, -3),
 // or 2, 4, 8 lanes per row.
 template <typename T>
@@ -2130,7 +2087,8 @@ static int tune_l0(Sim *s, int reps, std::string &rep) {
     float ms = 0.f;
     auto one = [&]() -> int {
       DP_TRY(gs_sweep_c<T>(s, b, x, true));
-      return resid_c<T>(s, b, x, r);
+      DP_TRY(resid_c<T>(s, b, x, r));
+      return gs_sweep_c<T>(s, b, x, false);
     };
     int rc = time_launches(s, reps, one, &ms);
     if (rc != DP_OK) { s->l0_G = old; return rc; }
@@ -2139,7 +2097,7 @@ static int tune_l0(Sim *s, int reps, std::string &rep) {
     if (ms < best_ms) { best_ms = ms; best = g; }
   }
   s->l0_G = best;
-  std::snprintf(buf, sizeof buf, "level 0 colour sweeps and residual lanes %d -> %d (us per sweep+residual:%s)\n",
+  std::snprintf(buf, sizeof buf, "level 0 colour sweeps and residual lanes %d -> %d (us per two sweeps+residual:%s)\n",
                 old, best, line.c_str());
   rep += buf;
   return DP_OK;
