@@ -196,8 +196,10 @@ __device__ __forceinline__ void row_c_w(int bx, int r0, int r1, const int *__res
 // CTA fences before its ticket, the last one after) and then does the long
 // rows [w0, w1), R of them per warp at once, reading through L2 (__ldcg)
 // what the other CTAs wrote.  Each row's arithmetic is that of its own
-// kernel (warp_row_c, k_ilu_fwd_w), so the results are the same bit for
-// bit; the launch the rows would have had is saved.
+// kernel (k_ilu_fwd_w), so the results are the same bit for bit; the
+// launch the rows would have had is saved.  Used by the ILU(0) forward
+// sweep, where it measured faster than the rows' own launch (the level-0
+// Gauss-Seidel wells measured slower this way and keep their launch).
 struct Tail {
   int w0 = 0, w1 = 0;           // the long rows; none: no tail
   unsigned *ticket = nullptr;   // kTicketWords: the counts, 0 between launches
@@ -233,79 +235,6 @@ __device__ __forceinline__ bool tail_ticket(unsigned *ticket) {
     __threadfence();
   }
   return last;
-}
-
-// R long rows per warp at once (q[k] < 0: no row), each with warp_row_c's
-// arithmetic: per lane the products of entries lane, lane + 32, ... added
-// in that order (one stride a trip here, to keep the registers few), then
-// the shuffle tree; b and 1/a_ii read at the end
-template <typename T, bool RESID, int R>
-__device__ __forceinline__ void warp_rows_c(const int (&q)[R], int lane,
-                                            const int *__restrict__ rowptr,
-                                            const int *__restrict__ colp,
-                                            const T *__restrict__ pv, const T *__restrict__ dinv,
-                                            const T *__restrict__ b, T *x, T *r) {
-  int e[R], e1[R];
-  T s[R];
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    bool ok = q[k] >= 0;
-    e[k] = ok ? __ldcg(rowptr + q[k]) + lane : 0;
-    e1[k] = ok ? __ldcg(rowptr + q[k] + 1) : 0;
-    s[k] = T(0);
-  }
-  for (;;) {
-    bool any = false;
-    T v[R], xv[R];
-    int c[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-      if (e[k] < e1[k]) {
-        any = true;
-        v[k] = __ldcg(pv + e[k]);
-        c[k] = __ldcg(colp + e[k]);
-      }
-    if (!any) break;
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-      if (e[k] < e1[k]) xv[k] = __ldcg(x + c[k]);
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-      if (e[k] < e1[k]) {
-        s[k] = fma(v[k], xv[k], s[k]);
-        e[k] += 32;
-      }
-  }
-#pragma unroll
-  for (int k = 0; k < R; ++k) s[k] = warp_sum(s[k]);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      if (q[k] < 0) continue;
-      if (RESID) {
-        r[q[k]] = b[q[k]] - s[k];
-      } else {
-        T di = dinv[q[k]];
-        if (di != T(0)) x[q[k]] = fma(b[q[k]] - s[k], di, __ldcg(x + q[k]));
-      }
-    }
-}
-
-// the tail's long Gauss-Seidel (or residual) rows: warp w of nwarps takes
-// rows w0 + w, w0 + w + nwarps, ..., kTailR at a time
-constexpr int kTailR = 4;
-template <typename T, bool RESID>
-__device__ __forceinline__ void gs_tail(const Tail &tl, int warp, int nwarps, int lane,
-                                        const int *__restrict__ rowptr,
-                                        const int *__restrict__ colp, const T *__restrict__ pv,
-                                        const T *__restrict__ dinv, const T *__restrict__ b,
-                                        T *x, T *r) {
-  for (int q0 = tl.w0 + warp; q0 < tl.w1; q0 += kTailR * nwarps) {
-    int q[kTailR];
-#pragma unroll
-    for (int k = 0; k < kTailR; ++k) q[k] = q0 + k * nwarps < tl.w1 ? q0 + k * nwarps : -1;
-    warp_rows_c<T, RESID, kTailR>(q, lane, rowptr, colp, pv, dinv, b, x, r);
-  }
 }
 
 // Deterministic reductions: a grid of dot_blocks(N) blocks writes one

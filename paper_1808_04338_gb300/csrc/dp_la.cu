@@ -1286,7 +1286,6 @@ __global__ void __launch_bounds__(kBlock) k_resid_cs(int r0, int r1, const int *
 // A bounded wait that gives up sets *err and ends the thread (the producer
 // first lets its copies in flight land, again with a bound).
 constexpr int kTT = 256;
-constexpr int kTmaMinBlocks = 6;   // the registers of the rows' loop, not of the tail's
 template <typename T, int CAPR> struct TStage {
   int rp[kTT + 8];
   int col[CAPR * kTT];
@@ -1370,7 +1369,7 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
                                                const T *__restrict__ pv,
                                                const T *__restrict__ dinv,
                                                const T *__restrict__ b, T *x,
-                                               T *__restrict__ r, int *err, const Tail &tl) {
+                                               T *__restrict__ r, int *err) {
   constexpr int kCap = CAPR * kTT;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   TStage<T, CAPR> *st = reinterpret_cast<TStage<T, CAPR> *>(tma_smem);
@@ -1391,7 +1390,7 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
     return;
   }
   int t = threadIdx.x;
-  __shared__ int abort_flag, last;
+  __shared__ int abort_flag;
   volatile int *abort_v = &abort_flag;
   if (t == 0) abort_flag = 0;
   consumers_sync();
@@ -1405,8 +1404,7 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
       bq = b[q];
       if (!RESID) dq = dinv[q];
     }
-    // a consumer that gives up does not leave (the CTA's consumers meet at
-    // the tail's barrier): it marks the CTA, which skips the rest
+    // a consumer that gives up marks the CTA, which skips the rest
     bool ok = !*abort_v && mbar_wait(&full[k], (i / S) & 1);
     if (!ok) *abort_v = 1;
     if (ok && in) {
@@ -1421,34 +1419,26 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
     }
     mbar_arrive(&empty[k]);
   }
-  if (tl.w1 <= tl.w0) {
-    if (*abort_v) atomicExch(err, 1);
-    return;
-  }
-  consumers_sync();
-  if (t == 0) last = *abort_v ? (atomicExch(err, 1), 0) : tail_ticket(tl.ticket);
-  consumers_sync();
-  if (last) gs_tail<T, RESID>(tl, t >> 5, kTT / 32, t & 31, rowptr, colp, pv, dinv, b, x, r);
+  if (*abort_v) atomicExch(err, 1);
 }
 
 template <typename T, int S, int CAPR>
-__global__ void __launch_bounds__(kTT + 32, kTmaMinBlocks) k_gs_c_tma(int r0, int r1, const int *__restrict__ rowptr,
+__global__ void __launch_bounds__(kTT + 32) k_gs_c_tma(int r0, int r1, const int *__restrict__ rowptr,
                                                        const int *__restrict__ colp,
                                                        const T *__restrict__ pv,
                                                        const T *__restrict__ dinv,
-                                                       const T *__restrict__ b, T *x, int *err,
-                                                       Tail tl) {
-  sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err, tl);
+                                                       const T *__restrict__ b, T *x, int *err) {
+  sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err);
 }
 
 template <typename T, int S, int CAPR>
-__global__ void __launch_bounds__(kTT + 32, kTmaMinBlocks) k_resid_c_tma(int r0, int r1,
+__global__ void __launch_bounds__(kTT + 32) k_resid_c_tma(int r0, int r1,
                                                           const int *__restrict__ rowptr,
                                                           const int *__restrict__ colp,
                                                           const T *__restrict__ pv,
                                                           const T *__restrict__ b, T *x,
-                                                          T *__restrict__ r, int *err, Tail tl) {
-  sweep_tma_body<T, true, S, CAPR>(r0, r1, rowptr, colp, pv, nullptr, b, x, r, err, tl);
+                                                          T *__restrict__ r, int *err) {
+  sweep_tma_body<T, true, S, CAPR>(r0, r1, rowptr, colp, pv, nullptr, b, x, r, err);
 }
 
 // grid of a pipelined kernel: its tiles, at most the CTAs that fit on the
@@ -1471,75 +1461,33 @@ static int tma_grid(K kern, int smem, int rows) {
 // stages of 6, -3 two stages of 4 (level 0's mixed fracture/matrix tiles
 // average about 5, so those bring their row pointers only)
 template <typename T, int S, int CAPR>
-static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
-                   const Tail &tl) {
+static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x) {
   constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
   DP_LAUNCH(s, (k_gs_c_tma<T, S, CAPR>), (tma_grid<16 * S + CAPR>(k_gs_c_tma<T, S, CAPR>, smem, r1 - r0)),
-            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err, tl);
+            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err);
 }
 template <typename T, int S, int CAPR>
-static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *r,
-                      const Tail &tl) {
+static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *r) {
   constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
   DP_LAUNCH(s, (k_resid_c_tma<T, S, CAPR>),
             (tma_grid<16 * S + CAPR>(k_resid_c_tma<T, S, CAPR>, smem, r1 - r0)),
-            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, b, x, r, s->dev_err, tl);
+            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, b, x, r, s->dev_err);
 }
 template <typename T>
 static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
-                      T *r, const Tail &tl) {
+                      T *r) {
   s->waits_used = true;
   if (r) {
-    if (G == -1) resid_tma<T, 2, 8>(s, r0, r1, pv, b, x, r, tl);
-    else if (G == -2) resid_tma<T, 3, 6>(s, r0, r1, pv, b, x, r, tl);
-    else resid_tma<T, 2, 4>(s, r0, r1, pv, b, x, r, tl);
+    if (G == -1) resid_tma<T, 2, 8>(s, r0, r1, pv, b, x, r);
+    else if (G == -2) resid_tma<T, 3, 6>(s, r0, r1, pv, b, x, r);
+    else resid_tma<T, 2, 4>(s, r0, r1, pv, b, x, r);
   } else {
-    if (G == -1) gs_tma<T, 2, 8>(s, r0, r1, pv, dinv, b, x, tl);
-    else if (G == -2) gs_tma<T, 3, 6>(s, r0, r1, pv, dinv, b, x, tl);
-    else gs_tma<T, 2, 4>(s, r0, r1, pv, dinv, b, x, tl);
+    if (G == -1) gs_tma<T, 2, 8>(s, r0, r1, pv, dinv, b, x);
+    else if (G == -2) gs_tma<T, 3, 6>(s, r0, r1, pv, dinv, b, x);
+    else gs_tma<T, 2, 4>(s, r0, r1, pv, dinv, b, x);
   }
 }
 
-// Thread-per-row Gauss-Seidel colour, residual run and ILU(0) forward colour,
-// each followed by the long rows of the next colour in its last CTA (Tail).
-// (launch bounds: kTailMinBlocks)
-template <typename T>
-__global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_gs_c_t(int r0, int r1, const int *__restrict__ rowptr,
-                                                   const int *__restrict__ colp,
-                                                   const T *__restrict__ pv,
-                                                   const T *__restrict__ dinv,
-                                                   const T *__restrict__ b, T *x, Tail tl) {
-  for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
-    k_gs_c_b<T>(bx, tl.nb, r0, r1, rowptr, colp, pv, dinv, b, x);
-  __shared__ int last;
-  __syncthreads();
-  if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
-  __syncthreads();
-  if (last)
-    gs_tail<T, false>(tl, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31, rowptr, colp, pv,
-                      dinv, b, x, nullptr);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_resid_c_t(int r0, int r1,
-                                                      const int *__restrict__ rowptr,
-                                                      const int *__restrict__ colp,
-                                                      const T *__restrict__ pv,
-                                                      const T *__restrict__ b, T *x,
-                                                      T *__restrict__ r, Tail tl) {
-  for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
-    k_resid_c_b<T>(bx, tl.nb, r0, r1, rowptr, colp, pv, b, x, r);
-  __shared__ int last;
-  __syncthreads();
-  if (threadIdx.x == 0) last = tail_ticket(tl.ticket);
-  __syncthreads();
-  if (last)
-    gs_tail<T, true>(tl, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31, rowptr, colp, pv,
-                     nullptr, b, x, r);
-}
-
-// the level-0 kernels that can take the next colour's long rows
-static bool l0_tails(int G) { return G == 1 || (G <= -1 && G >= -3); }
 
 // One whole Gauss-Seidel sweep of level 0 in colour order as a single
 // cooperative persistent launch (the CTAs are resident together): the
@@ -1808,14 +1756,6 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
         DP_LAUNCH(s, k_gs_c_first<T>, nblk(r1 - r0), kBlock, 0, r0, r1, L0C<T>::dinv(s), b, x);
       continue;
     }
-    // a short colour followed by a long one takes it in its last CTA
-    Tail tl;
-    if (!lng(c) && l0_tails(G) && t + 1 < order.size() && lng(order[t + 1])) {
-      tl.w0 = s->lu_cstart[order[t + 1]];
-      tl.w1 = s->lu_cstart[order[t + 1] + 1];
-      tl.ticket = s->tickets;
-      ++t;
-    }
     if (lng(c))
       DP_LAUNCH(s, k_gs_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
                 s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
@@ -1827,12 +1767,7 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
       DP_LAUNCH(s, k_gs_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
     else if (G < 0)
-      sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), L0C<T>::dinv(s), b, x, nullptr, tl);
-    else if (tl.w1 > tl.w0) {
-      tl.nb = nblk(r1 - r0);
-      DP_LAUNCH(s, k_gs_c_t<T>, tail_grid(tl.nb), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
-                L0C<T>::pv(s), L0C<T>::dinv(s), b, x, tl);
-    }
+      sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), L0C<T>::dinv(s), b, x, nullptr);
     else
       DP_LAUNCH(s, k_gs_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                 L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
@@ -1850,17 +1785,6 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
     int c1 = c + 1;
     while (c1 < nc && (s->lu_cmaxlen[c1] > kLongRow) == lng) ++c1;
     int r1 = s->lu_cstart[c1];
-    // a run of short colours followed by long ones takes them in its last CTA
-    Tail tl;
-    if (!lng && l0_tails(G) && c1 < nc) {
-      int c2 = c1;
-      while (c2 < nc && s->lu_cmaxlen[c2] > kLongRow) ++c2;
-      tl.w0 = s->lu_cstart[c1];
-      tl.w1 = s->lu_cstart[c2];
-      tl.ticket = s->tickets;
-      if (r1 > r0 && tl.w1 > tl.w0) c1 = c2;
-      else tl = Tail{};
-    }
     if (r1 > r0) {
       if (lng)
         DP_LAUNCH(s, k_resid_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
@@ -1873,12 +1797,7 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
         DP_LAUNCH(s, k_resid_cs<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, (T *)x, r);
       else if (G < 0)
-        sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), nullptr, b, (T *)x, r, tl);
-      else if (tl.w1 > tl.w0) {
-        tl.nb = nblk(r1 - r0);
-        DP_LAUNCH(s, k_resid_c_t<T>, tail_grid(tl.nb), kBlock, 0, r0, r1, s->lu_rowptr,
-                  s->l0_colp, L0C<T>::pv(s), b, (T *)x, r, tl);
-      }
+        sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), nullptr, b, (T *)x, r);
       else
         DP_LAUNCH(s, k_resid_c<T>, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,
                   L0C<T>::pv(s), b, x, r);
