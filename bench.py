@@ -607,8 +607,8 @@ def main():
     ap.add_argument("--mode", default="bench",
                     choices=["bench", "newton2", "ensemble", "serve", "period"],
                     help="newton2: create the realisation, run the first Newton solve of the "
-                         "first step (AMG set-up) and the second one, print their timings "
-                         "(a short run for profilers)")
+                         "first step (AMG set-up), autotune (unless --no-autotune) and run the "
+                         "second one, print their timings (a short run for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -644,6 +644,9 @@ def main():
             rc, st = sim.solve_step()
             out[k] = {"fgmres_iters": st.linear_iters, "ms_setup": st.ms_setup,
                       "ms_solve": st.ms_solve}
+            if k == "first" and args.autotune:   # the bench's launch shapes for the second
+                rep = sim.autotune(10)
+                out["autotune"] = [l for l in rep.splitlines() if "->" in l]
         torch.cuda.synchronize()
         out["launches"] = sim.launch_count()
         print(json.dumps(out), flush=True)
