@@ -602,6 +602,9 @@ def main():
                     help="skip the autotuner (sim_autotune: launch shapes of the AMG level "
                          "kernels and of level 0's colour sweeps, the V-cycle schedule), which "
                          "otherwise runs after one untimed timestep")
+    ap.add_argument("--l0-kernel", type=int, default=None,
+                    help="level 0's colour-sweep kernel (sim_set_l0_kernel), set after the "
+                         "autotuner: for profiling a given kernel")
     ap.add_argument("--threads", type=int, default=16,
                     help="ensemble mode: host threads driving realisations concurrently")
     ap.add_argument("--mode", default="bench",
@@ -647,6 +650,8 @@ def main():
             if k == "first" and args.autotune:   # the bench's launch shapes for the second
                 rep = sim.autotune(10)
                 out["autotune"] = [l for l in rep.splitlines() if "->" in l]
+            if k == "first" and args.l0_kernel is not None:
+                sim.set_l0_kernel(args.l0_kernel)
         torch.cuda.synchronize()
         out["launches"] = sim.launch_count()
         print(json.dumps(out), flush=True)
@@ -724,6 +729,8 @@ def main():
                 "report": [l for l in lines if changed(l)]}
 
     tuned = tune(sim, opts) if args.autotune else None
+    if args.l0_kernel is not None:
+        sim.set_l0_kernel(args.l0_kernel)
     clk = Clocks(local)
     main = measure(sim, opts, args.steps, args.warmup, clk)
     timestep(sim, opts)
