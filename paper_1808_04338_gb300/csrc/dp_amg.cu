@@ -21,7 +21,6 @@ namespace dp {
 constexpr int kScanBlock = 1024;
 
 __global__ void k_scan_block(const int *in, int *out, int n, long long *bsum) {
-  DP_KERNEL_BEGIN();
   __shared__ long long ws[32];
   int i = blockIdx.x * kScanBlock + threadIdx.x;
   long long v = i < n ? in[i] : 0;
@@ -50,7 +49,6 @@ __global__ void k_scan_block(const int *in, int *out, int n, long long *bsum) {
 }
 
 __global__ void k_scan_top(long long *bsum, int nb, int *out, int n, int *overflow) {
-  DP_KERNEL_BEGIN();
   if (threadIdx.x != 0) return;
   long long run = 0;
   for (int b = 0; b < nb; ++b) { long long t = bsum[b]; bsum[b] = run; run += t; }
@@ -59,7 +57,6 @@ __global__ void k_scan_top(long long *bsum, int nb, int *out, int n, int *overfl
 }
 
 __global__ void k_scan_add(int *out, int n, const long long *bsum) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * kScanBlock + threadIdx.x;
   if (i < n) out[i] = (int)(out[i] + bsum[blockIdx.x]);
 }
@@ -94,7 +91,6 @@ constexpr int kMaxColours = 256;
 
 __global__ void k_colour_round(int n, const int *rowptr, const int *col, int *colour,
                                int *pending, int *overflow) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   volatile int *vc = colour;
@@ -114,13 +110,11 @@ __global__ void k_colour_round(int n, const int *rowptr, const int *col, int *co
 }
 
 __global__ void k_fill_i32(int *a, int n, int v) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = v;
 }
 
 __global__ void k_max_i32(const int *a, int n, int *out) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) atomicMax(out, a[i]);
 }
@@ -146,14 +140,12 @@ int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour,
 }
 
 __global__ void k_eq_flag(const int *a, int n, int v, int *flag) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) flag[i] = a[i] == v;
 }
 
 __global__ void k_scatter_colour(const int *colour, int n, int c, const int *pos, int base,
                                  int *clist, int *iperm) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || colour[i] != c) return;
   int p = base + pos[i];
@@ -218,13 +210,11 @@ __device__ void heap_sort2(int *key, int *pay, int n) {
 }
 
 __global__ void k_diag_pos(int n, const int *rowptr, const int *col, int *dpos) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dpos[i] = find_sorted(col, rowptr[i], rowptr[i + 1], i);
 }
 
 __global__ void k_tpos(int n, const int *rowptr, const int *col, int *tpos) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
@@ -238,7 +228,6 @@ __global__ void k_tpos(int n, const int *rowptr, const int *col, int *tpos) {
 __global__ void k_strength(int n, const int *rowptr, const int *col, const int *dpos,
                            const int *tpos, const double *val, double theta, uint8_t *strong,
                            int *state) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double aii = dpos[i] >= 0 ? val[dpos[i]] : 0.0;
@@ -271,7 +260,6 @@ __device__ __forceinline__ uint32_t hash32(uint32_t i) {
 }
 
 __global__ void k_tuple_init(int n, const int *state, unsigned long long *t) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n)
     t[i] = ((unsigned long long)state[i] << 62) | ((unsigned long long)hash32((uint32_t)i) << 30) |
@@ -280,7 +268,6 @@ __global__ void k_tuple_init(int n, const int *state, unsigned long long *t) {
 
 __global__ void k_tuple_max(int n, const int *rowptr, const int *col, const uint8_t *strong,
                             const unsigned long long *tin, unsigned long long *tout) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   unsigned long long m = tin[i];
@@ -290,7 +277,6 @@ __global__ void k_tuple_max(int n, const int *rowptr, const int *col, const uint
 }
 
 __global__ void k_mis_update(int n, const unsigned long long *t, int *state, int *undecided) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || state[i] != 1) return;
   unsigned long long m = t[i];
@@ -300,13 +286,11 @@ __global__ void k_mis_update(int n, const unsigned long long *t, int *state, int
 }
 
 __global__ void k_root_flag(int n, const int *state, int *flag) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) flag[i] = state[i] == 2;
 }
 
 __global__ void k_agg_roots(int n, const int *state, const int *pos, int *agg) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) agg[i] = state[i] == 2 ? pos[i] : -1;
 }
@@ -314,7 +298,6 @@ __global__ void k_agg_roots(int n, const int *state, const int *pos, int *agg) {
 // pass 1: a node next to roots joins the root with the largest (hash, index)
 __global__ void k_agg_pass1(int n, const int *rowptr, const int *col, const uint8_t *strong,
                             const int *state, const int *agg, int *a1) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int v = agg[i];
@@ -336,7 +319,6 @@ __global__ void k_agg_pass1(int n, const int *rowptr, const int *col, const uint
 // with the largest (hash, index), as assigned after pass 1
 __global__ void k_agg_pass2(int n, const int *rowptr, const int *col, const uint8_t *strong,
                             const int *a1, int *a2) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int v = a1[i];
@@ -358,7 +340,6 @@ __global__ void k_agg_pass2(int n, const int *rowptr, const int *col, const uint
 // Pattern of P: the aggregates of the filtered row F(i) = {i} u {strong j}.
 __global__ void k_p_collect(int n, const int *rowptr, const int *col, const uint8_t *strong,
                             const int *agg, int *scratch, int *cnt) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int base = rowptr[i], m = 0;
@@ -375,7 +356,6 @@ __global__ void k_p_collect(int n, const int *rowptr, const int *col, const uint
 
 __global__ void k_copy_rows(int n, const int *src_rowptr, const int *scratch, const int *dst_rowptr,
                             int *dst_col) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s0 = src_rowptr[i], d0 = dst_rowptr[i], m = dst_rowptr[i + 1] - d0;
@@ -386,7 +366,6 @@ __global__ void k_copy_rows(int n, const int *src_rowptr, const int *scratch, co
 // Gershgorin ratio sum_{F(i)} |aF_ij| / |d_i| whose maximum sets omega.
 __global__ void k_filtered_diag(int n, const int *rowptr, const int *col, const uint8_t *strong,
                                 const double *val, double *fdiag, unsigned long long *rho_bits) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool valid = i < n;                   // every lane reaches the shuffles
   double d = 0.0;
@@ -410,7 +389,6 @@ __global__ void k_filtered_diag(int n, const int *rowptr, const int *col, const 
 }
 
 __global__ void k_omega(const unsigned long long *rho_bits, double *omega) {
-  DP_KERNEL_BEGIN();
   double rho = __longlong_as_double((long long)*rho_bits);
   *omega = rho > 0.0 ? (4.0 / 3.0) / rho : 0.0;
 }
@@ -420,7 +398,6 @@ __global__ void k_p_values(int n, const int *rowptr, const int *col, const uint8
                            const double *val, const double *fdiag, const int *agg,
                            const double *omega, const int *p_rowptr, const int *p_col,
                            double *p_val) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int q0 = p_rowptr[i], q1 = p_rowptr[i + 1];
@@ -447,14 +424,12 @@ __global__ void k_p_values(int n, const int *rowptr, const int *col, const uint8
 
 // ---------------------------------------------------------------- transpose
 __global__ void k_col_count(int nnz, const int *col, int *cnt) {
-  DP_KERNEL_BEGIN();
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < nnz) atomicAdd(&cnt[col[e]], 1);
 }
 
 __global__ void k_transpose_fill(int n, const int *rowptr, const int *col, const int *t_rowptr,
                                  int *fill, int *t_col, int *t_src) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
@@ -466,14 +441,12 @@ __global__ void k_transpose_fill(int n, const int *rowptr, const int *col, const
 }
 
 __global__ void k_sort_rows(int n, const int *rowptr, int *key, int *pay) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   heap_sort2(key + rowptr[i], pay + rowptr[i], rowptr[i + 1] - rowptr[i]);
 }
 
 __global__ void k_gather(int nnz, const int *src, const double *in, double *out) {
-  DP_KERNEL_BEGIN();
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < nnz) out[e] = in[src[e]];
 }
@@ -483,7 +456,6 @@ __global__ void k_gather(int nnz, const int *src, const double *in, double *out)
 // of R named by the row of L.  Numeric: per row of C, for each entry (r, k)
 // of L in increasing k and each (k, c) of R, C_rc += L_rk R_kc.
 __global__ void k_spgemm_ub(int n, const int *lrp, const int *lcol, const int *rrp, int *ub) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int s = 0;
@@ -493,7 +465,6 @@ __global__ void k_spgemm_ub(int n, const int *lrp, const int *lcol, const int *r
 
 __global__ void k_spgemm_expand(int n, const int *lrp, const int *lcol, const int *rrp,
                                 const int *rcol, const int *off, int *scratch, int *cnt) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int base = off[r], m = 0;
@@ -514,7 +485,6 @@ __global__ void k_spgemm_expand(int n, const int *lrp, const int *lcol, const in
 __global__ void k_spgemm_positions(int n, const int *lrp, const int *lcol, const int *rrp,
                                    const int *rcol, const int *off, const int *crp,
                                    const int *ccol, int *pos) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int c0 = crp[r], c1 = crp[r + 1], t = off[r];
@@ -532,7 +502,6 @@ template <int G>
 __global__ void k_spgemm_numeric(int n, const int *lrp, const int *lcol, const double *lval,
                                  const int *rrp, const double *rval, const int *off,
                                  const int *pos, const int *crp, double *cval) {
-  DP_KERNEL_BEGIN();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = t / G, lane = t % G;
   if (r >= n) return;                   // groups of G lanes leave together
@@ -616,7 +585,6 @@ static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const
 // 1 / sum_j |a_ij| for l1-Jacobi (0 where that is zero: the row is left as is)
 __global__ void k_level_dinv(int n, const int *dpos, const int *rowptr, const double *val, int l1,
                              double *dinv) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double d = 0.0;

@@ -269,7 +269,6 @@ template <typename T>
 __global__ void __launch_bounds__(kClusterThreads, 1)
     k_coarse_cycle(const LevelDev<T> *__restrict__ lv, int l0, int nl, const T *b0, T *x0,
                    const double *lu, const int *piv, const double *inv, int dense_n) {
-  DP_KERNEL_BEGIN();
   cg::cluster_group cl = cg::this_cluster();
   int gt = (int)cl.block_rank() * blockDim.x + threadIdx.x;
   int nt = (int)cl.num_blocks() * blockDim.x;
@@ -412,7 +411,6 @@ static int upload_levels(Sim *s, void **dst) {
 }
 
 __global__ void k_ell_maxlen(int n, const int *rowptr, const int *colour, int *K) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) atomicMax(&K[colour[i]], rowptr[i + 1] - rowptr[i]);
 }
@@ -422,7 +420,6 @@ __global__ void k_ell_maxlen(int n, const int *rowptr, const int *colour, int *K
 __global__ void k_ell_fill(int n, const int *clist, const int *colour, const int *cstart,
                            const int *eoff, const int *eK, const int *rowptr, const int *col,
                            int *ecol, int *esrc) {
-  DP_KERNEL_BEGIN();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   int i = clist[q], c = colour[i];
@@ -437,7 +434,6 @@ __global__ void k_ell_fill(int n, const int *clist, const int *colour, const int
 
 template <typename T>
 __global__ void k_ell_values(long long total, const int *esrc, const T *val, T *eval) {
-  DP_KERNEL_BEGIN();
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < total) { int q = esrc[p]; eval[p] = q >= 0 ? val[q] : T(0); }
 }

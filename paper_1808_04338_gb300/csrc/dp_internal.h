@@ -5,7 +5,6 @@
 #include <stdint.h>
 
 #include <string>
-#include <utility>
 #include <vector>
 
 #include "dpsim.h"
@@ -118,31 +117,13 @@ struct LaunchScope {
 };
 // After an allocation has failed nothing more is launched for the
 // realisation (its calls return DP_ENOMEM until it is destroyed), so no
-// kernel can be handed a buffer that was never obtained.  Launches go
-// through launch_kernel (programmatic dependent launch, below).
-#define DP_LAUNCH(sim, name, grid, block, smem, ...)                           \
-  do {                                                                         \
-    if ((sim)->alloc_failed) break;                                            \
-    ::dp::LaunchScope ls__((sim), #name);                                      \
-    ::dp::launch_kernel((sim), name, dim3(grid), dim3(block), (smem), __VA_ARGS__); \
+// kernel can be handed a buffer that was never obtained.
+#define DP_LAUNCH(sim, name, grid, block, smem, ...)                    \
+  do {                                                                  \
+    if ((sim)->alloc_failed) break;                                     \
+    ::dp::LaunchScope ls__((sim), #name);                               \
+    name<<<(grid), (block), (smem), (sim)->stream>>>(__VA_ARGS__);      \
   } while (0)
-
-// Programmatic dependent launch: a kernel launched by DP_LAUNCH may be
-// scheduled while the kernel before it on the stream still runs, so its
-// CTAs are resident when that one ends (the launch gap and the CTA ramp
-// overlap the previous kernel's tail).  Every kernel of the library
-// therefore starts with DP_KERNEL_BEGIN: it first waits until the previous
-// grid has completed and its memory is visible (griddepcontrol.wait, a
-// no-op for a kernel launched without the attribute), so no memory access
-// of the kernel overlaps the previous one; then it allows the next kernel's
-// launch (griddepcontrol.launch_dependents).  tests/test_kernels_begin.py
-// checks that every __global__ function starts with it.
-__device__ __forceinline__ void kernel_begin() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-#define DP_KERNEL_BEGIN() ::dp::kernel_begin()
-bool pdl_enabled();   // off when the environment sets DPSIM_PDL=0
 
 // Storage order of the Krylov operator's copy: locations in chunks of
 // kChunk; storage rows 2 kChunk c .. of chunk c hold its fracture rows (cells
@@ -398,23 +379,4 @@ struct Sim {
 }  // namespace dp
 
 // The opaque handle of the C ABI is the library's realisation.
-namespace dp {
-template <typename... P, typename... A>
-inline void launch_kernel(Sim *s, void (*k)(P...), dim3 grid, dim3 block, size_t smem,
-                          A &&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s->stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
-  if (e != cudaSuccess) s->fail(DP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-}
-}  // namespace dp
-
 struct dp_sim : dp::Sim {};

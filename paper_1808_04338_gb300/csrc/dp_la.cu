@@ -38,7 +38,6 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc, int 
                                                      const double *__restrict__ x,
                                                      const double *__restrict__ b,
                                                      double *__restrict__ y) {
-  DP_KERNEL_BEGIN();
   k_bsr_spmv_b<MODE>(blockIdx.x, gridDim.x, n, nL, nc, nlong, rowptr, col, val, x, b, y);
 }
 
@@ -52,7 +51,6 @@ __global__ void __launch_bounds__(kBlock) k_lin_residual(int n, const int *__res
                                                          const double *__restrict__ R,
                                                          const double *__restrict__ y,
                                                          double *__restrict__ lq) {
-  DP_KERNEL_BEGIN();
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int i = (int)(t >> 1), comp = (int)(t & 1);
   if (i >= n) return;
@@ -87,7 +85,6 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
                                                        const double *__restrict__ b,
                                                        double *__restrict__ rp,
                                                        const int *__restrict__ omap) {
-  DP_KERNEL_BEGIN();
   if (blockIdx.x == 0) {   // the well rows, a warp per row (as in k_bsr_spmv)
     int lane = threadIdx.x & 31;
     const double2 *x2 = reinterpret_cast<const double2 *>(x);
@@ -143,7 +140,6 @@ __global__ void __launch_bounds__(kBlock) k_bsr_resid_f32(int n, int nL, int nc,
                                                          const float *__restrict__ x,
                                                          const double *__restrict__ b,
                                                          float *__restrict__ y) {
-  DP_KERNEL_BEGIN();
   k_bsr_resid_f32_b(blockIdx.x, gridDim.x, n, nL, nc, nlong, rowptr, col, valf, x, b, y);
 }
 
@@ -158,7 +154,6 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid_f32(int n, int nL, int nc
                                                           float *__restrict__ rp,
                                                           const int *__restrict__ omap,
                                                           X0Init xi) {
-  DP_KERNEL_BEGIN();
   k_bsr_presid_f32_b(blockIdx.x, gridDim.x, n, nL, nc, nlong, rowptr, col, pf, x, b, rp, omap, xi);
 }
 
@@ -182,7 +177,6 @@ int bsr_residual(Sim *s, const double *b, const double *x, double *r) {
 // their column: L blocks, the inverted pivot block, U blocks.
 
 __global__ void k_perm_len(int n, const int *perm, const int *rowptr, int *len) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) { int i = perm[r]; len[r] = rowptr[i + 1] - rowptr[i]; }
 }
@@ -190,7 +184,6 @@ __global__ void k_perm_len(int n, const int *perm, const int *rowptr, int *len) 
 __global__ void k_lu_pattern(int n, const int *perm, const int *iperm, const int *rowptr,
                              const int *col, const int *lu_rowptr, int *lu_col, int *lu_src,
                              int *lu_dpos) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int i = perm[r], s0 = rowptr[i], m = rowptr[i + 1] - s0, d0 = lu_rowptr[r];
@@ -238,7 +231,6 @@ __device__ __forceinline__ int find_in(const int *col, int lo, int hi, int c) {
 __global__ void k_ilu_upd(int n, int fill, const int *iperm, const int *lu_rowptr,
                           const int *lu_col, const int *lu_dpos, const int *upd_ptr, int *cnt,
                           int *upd_e2, int *upd_q) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int s1 = lu_rowptr[r + 1], dp = lu_dpos[r];
@@ -276,7 +268,6 @@ __global__ void k_ilu_factor(int r0, int r1, int nL, const int *lu_rowptr, const
                              const int *dst, const int *colp, const int *upd_ptr,
                              const int *__restrict__ upd_e2, const int *__restrict__ upd_q,
                              T *lu) {
-  DP_KERNEL_BEGIN();
   int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= r1) return;
   // every block moves as one 16-byte (FP32) or two 16-byte (FP64) accesses;
@@ -315,7 +306,6 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *_
                                                     const int *__restrict__ colp,
                                                     const T *__restrict__ lu,
                                                     const TR *__restrict__ rhs, T *zp) {
-  DP_KERNEL_BEGIN();
   k_ilu_fwd_b<T, TR>(blockIdx.x, gridDim.x, r0, r1, perm, Lptr, colp, lu, rhs, zp);
 }
 
@@ -328,7 +318,6 @@ __global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_ilu_fwd_t(int r0, in
                                                       const T *__restrict__ lu,
                                                       const TR *__restrict__ rhs, T *zp, int nL,
                                                       Tail tl) {
-  DP_KERNEL_BEGIN();
   for (int bx = blockIdx.x; bx < tl.nb; bx += gridDim.x)
     k_ilu_fwd_b<T, TR>(bx, tl.nb, r0, r1, perm, Lptr, colp, lu, rhs, zp);
   __shared__ int last;
@@ -347,7 +336,6 @@ __global__ void __launch_bounds__(kBlock, kTailMinBlocks) k_ilu_fwd_t(int r0, in
 template <typename T, typename TR>
 __global__ void __launch_bounds__(kBlock) k_ilu_fwd_copy(int r0, int r1, const int *__restrict__ perm,
                                                      const TR *__restrict__ rhs, T *zp) {
-  DP_KERNEL_BEGIN();
   k_ilu_fwd_copy_b<T, TR>(blockIdx.x, gridDim.x, r0, r1, perm, rhs, zp);
 }
 
@@ -362,7 +350,6 @@ __global__ void __launch_bounds__(kBlock) k_ilu_bwd_r(int r0, int r1, int nL, in
                                                       const int *__restrict__ Uptr,
                                                       const int *__restrict__ colp,
                                                       const T *__restrict__ lu, T *zp) {
-  DP_KERNEL_BEGIN();
   k_ilu_bwd_r_b<T>(blockIdx.x, gridDim.x, r0, r1, nL, n, Uptr, colp, lu, zp);
 }
 
@@ -376,7 +363,6 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd_w(int r0, int r1, int nL,
                                                       const int *__restrict__ colp,
                                                       const T *__restrict__ lu,
                                                       const TR *__restrict__ rhs, T *zp) {
-  DP_KERNEL_BEGIN();
   k_ilu_fwd_w_b<T, TR, PIVOT>(blockIdx.x, gridDim.x, r0, r1, nL, perm, Lptr, colp, lu, rhs, zp);
 }
 
@@ -385,7 +371,6 @@ __global__ void __launch_bounds__(kBlock) k_ilu_bwd_w(int r0, int r1, int nL, in
                                                       const int *__restrict__ Uptr,
                                                       const int *__restrict__ colp,
                                                       const T *__restrict__ lu, T *zp) {
-  DP_KERNEL_BEGIN();
   k_ilu_bwd_w_b<T>(blockIdx.x, gridDim.x, r0, r1, nL, n, Uptr, colp, lu, zp);
 }
 
@@ -394,7 +379,6 @@ __global__ void __launch_bounds__(kBlock) k_ilu_bwd_w(int r0, int r1, int nL, in
 __global__ void k_ilu_split(int n, int nL, const int *iperm, const int *lu_rowptr,
                             const int *lu_col, const int *lu_dpos, const int *Lptr,
                             const int *Uptr, int *dst, int *colp) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int s0 = lu_rowptr[r], dp = lu_dpos[r], s1 = lu_rowptr[r + 1];
@@ -409,7 +393,6 @@ __global__ void k_ilu_split(int n, int nL, const int *iperm, const int *lu_rowpt
 // factor-order position (inverse of lu_src).
 __global__ void k_entry_maps(int n, const int *rowptr, const int *lu_rowptr, const int *lu_src,
                              const int *dst, int *erow, int *ilupos, int *l0pos) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) erow[e] = r;
@@ -422,7 +405,6 @@ __global__ void k_entry_maps(int n, const int *rowptr, const int *lu_rowptr, con
 // Position of entry (j, i) for every entry (i, j) of the structurally
 // symmetric block pattern (columns sorted within rows).
 __global__ void k_block_tpos(int n, const int *rowptr, const int *col, int *tpos) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
@@ -437,13 +419,11 @@ __global__ void k_block_tpos(int n, const int *rowptr, const int *col, int *tpos
 }
 
 __global__ void k_remap(long long n, const int *map, int *v) {
-  DP_KERNEL_BEGIN();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = map[v[i]];
 }
 
 __global__ void k_lu_lens(int n, const int *lu_rowptr, const int *lu_dpos, int *nl, int *nu) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   nl[r] = lu_dpos[r] - lu_rowptr[r];
@@ -453,7 +433,6 @@ __global__ void k_lu_lens(int n, const int *lu_rowptr, const int *lu_dpos, int *
 // longest row of each colour (blocks), for choosing the sweep variant
 __global__ void k_colour_maxlen(int n, const int *cstart_dev, int ncolour, const int *rowptr,
                                 int *out) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   int c = 0;
@@ -668,7 +647,6 @@ __global__ void __launch_bounds__(kBlock) k_ilu_result(int n, const int *__restr
                                                        T *__restrict__ outT,
                                                        const float *__restrict__ inj,
                                                        int inj_perm) {
-  DP_KERNEL_BEGIN();
   k_ilu_result_b<T>(blockIdx.x, gridDim.x, n, iperm, zp, base, out, outT, inj, inj_perm);
 }
 
@@ -702,7 +680,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int 
                                                       const TV *__restrict__ val,
                                                       const T *__restrict__ dinv,
                                                       const T *__restrict__ b, T *x) {
-  DP_KERNEL_BEGIN();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int q = r0 + t / G, lane = t % G;
   bool valid = q < r1;
@@ -725,7 +702,6 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restr
                                                        const T *__restrict__ d,
                                                        const T *__restrict__ b, T *__restrict__ x,
                                                        T *__restrict__ r) {
-  DP_KERNEL_BEGIN();
   k_jacobi_pre_b<G, T, TV>(blockIdx.x, gridDim.x, n, rowptr, col, val, d, b, x, r);
 }
 
@@ -739,7 +715,6 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_sweep(int n, const int *__res
                                                          const T *__restrict__ b,
                                                          const T *__restrict__ x,
                                                          T *__restrict__ tout) {
-  DP_KERNEL_BEGIN();
   k_jacobi_sweep_b<G, T, TV>(blockIdx.x, gridDim.x, n, rowptr, col, val, d, b, x, tout);
 }
 
@@ -750,7 +725,6 @@ __global__ void __launch_bounds__(kBlock) k_csr_resid(int n, const int *__restri
                                                       const TV *__restrict__ val,
                                                       const T *__restrict__ b,
                                                       const T *__restrict__ x, T *__restrict__ r) {
-  DP_KERNEL_BEGIN();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int i = t / G, lane = t % G;
   bool valid = i < n;
@@ -767,7 +741,6 @@ __global__ void __launch_bounds__(kBlock) k_csr_mv(int n, const int *__restrict_
                                                    const TV *__restrict__ val,
                                                    const T *__restrict__ x, T *__restrict__ y,
                                                    int add) {
-  DP_KERNEL_BEGIN();
   k_csr_mv_b<G, T, TV>(blockIdx.x, gridDim.x, n, rowptr, col, val, x, y, add);
 }
 
@@ -861,7 +834,6 @@ static int transfer_mv(Sim *s, int n, int G, const int *rowptr, const int *col, 
 // coarsest level: dense copy, LU with partial pivoting, solve (one block)
 __global__ void k_csr_to_dense(int n, const int *rowptr, const int *col, const double *val,
                                double *a) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int j = 0; j < n; ++j) a[(size_t)i * n + j] = 0.0;
@@ -869,7 +841,6 @@ __global__ void k_csr_to_dense(int n, const int *rowptr, const int *col, const d
 }
 
 __global__ void __launch_bounds__(1024) k_dense_lu(int n, double *a, int *piv) {
-  DP_KERNEL_BEGIN();
   __shared__ double sv[1024];
   __shared__ int si[1024];
   int t = threadIdx.x, nt = blockDim.x;
@@ -923,7 +894,6 @@ constexpr int kInverseMax = 1024;   // coarsest levels up to this size keep an e
 template <typename T>
 __global__ void __launch_bounds__(1024) k_dense_solve(int n, const double *a, const int *piv,
                                                       const T *b, T *x) {
-  DP_KERNEL_BEGIN();
   __shared__ double xs[kDenseMax];
   int t = threadIdx.x, nt = blockDim.x;
   for (int i = t; i < n; i += nt) xs[i] = double(b[i]);
@@ -952,7 +922,6 @@ __global__ void __launch_bounds__(1024) k_dense_solve(int n, const double *a, co
 // column per thread: the solve of k_dense_solve applied to the unit vector
 // e_c (the same steps in the same order), kept in column c of `inv`.
 __global__ void k_dense_inverse(int n, const double *a, const int *piv, double *inv) {
-  DP_KERNEL_BEGIN();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = i == c ? 1.0 : 0.0;
@@ -978,7 +947,6 @@ __global__ void k_dense_inverse(int n, const double *a, const int *piv, double *
 template <typename T>
 __global__ void k_dense_mv(int n, const double *__restrict__ inv, const T *__restrict__ b,
                            T *__restrict__ x) {
-  DP_KERNEL_BEGIN();
   k_dense_mv_b<T>(blockIdx.x, gridDim.x, n, inv, b, x);
 }
 
@@ -1057,7 +1025,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_lu(int r0, int r1, const int *__r
                                                   const T *__restrict__ pv,
                                                   const T *__restrict__ dinv,
                                                   const T *__restrict__ b, T *x) {
-  DP_KERNEL_BEGIN();
   int q = r0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= r1) return;
   int i = __ldcs(perm + q);
@@ -1093,7 +1060,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_lu_w(int r0, int r1, const int *_
                                                     const T *__restrict__ pv,
                                                     const T *__restrict__ dinv,
                                                     const T *__restrict__ b, T *x) {
-  DP_KERNEL_BEGIN();
   int q = r0 + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (q >= r1) return;   // whole warps
@@ -1111,7 +1077,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_lu_w(int r0, int r1, const int *_
 template <typename T>
 __global__ void k_gather_vals(long long n, const int *__restrict__ src, const double *__restrict__ v,
                               T *__restrict__ out) {
-  DP_KERNEL_BEGIN();
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) out[e] = T(v[__ldg(src + e)]);
 }
@@ -1125,7 +1090,6 @@ __global__ void k_gather_vals(long long n, const int *__restrict__ src, const do
 // every Newton step, P0's values whenever the coarse values are refreshed.
 __global__ void k_perm_rows(int n, const int *perm, const int *rowptr, const int *col,
                             const int *prow, int *pcol, int *psrc) {
-  DP_KERNEL_BEGIN();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   int i = perm[q], e0 = rowptr[i], m = rowptr[i + 1] - e0, d0 = prow[q];
@@ -1133,7 +1097,6 @@ __global__ void k_perm_rows(int n, const int *perm, const int *rowptr, const int
 }
 
 __global__ void k_map_copy(long long n, const int *map, const int *in, int *out) {
-  DP_KERNEL_BEGIN();
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) out[e] = map[in[e]];
 }
@@ -1228,7 +1191,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_c(int r0, int r1, const int *__re
                                                  const T *__restrict__ pv,
                                                  const T *__restrict__ dinv,
                                                  const T *__restrict__ b, T *x) {
-  DP_KERNEL_BEGIN();
   k_gs_c_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x);
 }
 
@@ -1238,7 +1200,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_c(int r0, int r1, const int *__re
 template <typename T>
 __global__ void k_gs_c_first(int r0, int r1, const T *__restrict__ dinv, const T *__restrict__ b,
                              T *__restrict__ x) {
-  DP_KERNEL_BEGIN();
   k_gs_c_first_b<T>(blockIdx.x, gridDim.x, r0, r1, dinv, b, x);
 }
 
@@ -1249,7 +1210,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_c_w(int r0, int r1, const int *__
                                                    const T *__restrict__ pv,
                                                    const T *__restrict__ dinv,
                                                    const T *__restrict__ b, T *x) {
-  DP_KERNEL_BEGIN();
   k_gs_c_w_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x);
 }
 
@@ -1258,7 +1218,6 @@ __global__ void __launch_bounds__(kBlock) k_resid_c_w(int r0, int r1, const int 
                                                       const int *__restrict__ colp,
                                                       const T *__restrict__ pv,
                                                       const T *__restrict__ b, T *x, T *r) {
-  DP_KERNEL_BEGIN();
   k_resid_c_w_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
 }
 
@@ -1269,7 +1228,6 @@ __global__ void __launch_bounds__(kBlock) k_resid_c(int r0, int r1, const int *_
                                                     const T *__restrict__ pv,
                                                     const T *__restrict__ b,
                                                     const T *__restrict__ x, T *__restrict__ r) {
-  DP_KERNEL_BEGIN();
   k_resid_c_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
 }
 
@@ -1279,7 +1237,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_cg(int r0, int r1, const int *__r
                                                   const T *__restrict__ pv,
                                                   const T *__restrict__ dinv,
                                                   const T *__restrict__ b, T *x) {
-  DP_KERNEL_BEGIN();
   k_gs_cg_b<G, T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x);
 }
 
@@ -1289,7 +1246,6 @@ __global__ void __launch_bounds__(kBlock) k_resid_cg(int r0, int r1, const int *
                                                      const T *__restrict__ pv,
                                                      const T *__restrict__ b, const T *x,
                                                      T *__restrict__ r) {
-  DP_KERNEL_BEGIN();
   k_resid_cg_b<G, T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
 }
 
@@ -1299,7 +1255,6 @@ __global__ void __launch_bounds__(kBlock) k_gs_cs(int r0, int r1, const int *__r
                                                   const T *__restrict__ pv,
                                                   const T *__restrict__ dinv,
                                                   const T *__restrict__ b, T *x) {
-  DP_KERNEL_BEGIN();
   k_sweep_cs_b<T, false>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x, nullptr);
 }
 
@@ -1309,7 +1264,6 @@ __global__ void __launch_bounds__(kBlock) k_resid_cs(int r0, int r1, const int *
                                                      const T *__restrict__ pv,
                                                      const T *__restrict__ b, T *x,
                                                      T *__restrict__ r) {
-  DP_KERNEL_BEGIN();
   k_sweep_cs_b<T, true>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, nullptr, b, x, r);
 }
 
@@ -1474,7 +1428,6 @@ __global__ void __launch_bounds__(kTT + 32) k_gs_c_tma(int r0, int r1, const int
                                                        const T *__restrict__ pv,
                                                        const T *__restrict__ dinv,
                                                        const T *__restrict__ b, T *x, int *err) {
-  DP_KERNEL_BEGIN();
   sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err);
 }
 
@@ -1485,7 +1438,6 @@ __global__ void __launch_bounds__(kTT + 32) k_resid_c_tma(int r0, int r1,
                                                           const T *__restrict__ pv,
                                                           const T *__restrict__ b, T *x,
                                                           T *__restrict__ r, int *err) {
-  DP_KERNEL_BEGIN();
   sweep_tma_body<T, true, S, CAPR>(r0, r1, rowptr, colp, pv, nullptr, b, x, r, err);
 }
 
@@ -1603,7 +1555,6 @@ __global__ void __launch_bounds__(kTT + 32) k_gs_c_sweep(SweepPlan plan,
                                                          const T *__restrict__ dinv,
                                                          const T *__restrict__ b, T *x,
                                                          unsigned *bar, int *err) {
-  DP_KERNEL_BEGIN();
   constexpr int kCap = CAPR * kTT;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   TStage<T, CAPR> *st = reinterpret_cast<TStage<T, CAPR> *>(tma_smem);
@@ -2126,7 +2077,6 @@ int autotune(Sim *s, int reps, std::string &rep) {
 
 template <typename T>
 __global__ void k_inject_add(int n, const T *xp, double *z, const int *imap) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) z[2 * i] += double(xp[imap ? __ldg(imap + i) : i]);
 }
@@ -2135,13 +2085,11 @@ __global__ void k_inject_add(int n, const T *xp, double *z, const int *imap) {
 // conversions on the FP64 pipe); the FP64 z1 takes the same correction in
 // the final result gather (ilu_result's inj).
 __global__ void k_inject_f32(int n, const float *xp, float *zf, const int *imap) {
-  DP_KERNEL_BEGIN();
   k_inject_f32_b(blockIdx.x, gridDim.x, n, xp, zf, imap);
 }
 
 
 __global__ void k_to_f32(long long n, const double *x, float *y) {
-  DP_KERNEL_BEGIN();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = float(x[i]);
 }
@@ -2215,7 +2163,6 @@ __global__ void __launch_bounds__(kBlock, kDotBlocks / 152) k_multidot(long long
                                                      const double *__restrict__ w,
                                                      double *__restrict__ part, int part_off,
                                                      const double *__restrict__ gate) {
-  DP_KERNEL_BEGIN();
   k_multidot_b<NV, SELF>(blockIdx.x, gridDim.x, N, V, ldv, w, part, part_off, gate);
 }
 
@@ -2233,7 +2180,6 @@ __global__ void __launch_bounds__(kBlock, kDotBlocks / 152) k_multidot(long long
 __global__ void __launch_bounds__(256) k_dot_final(const double *part, int nblocks, int nv,
                                                    double *dots, double *H, int m, int j,
                                                    int mode, double *scal, double reorth) {
-  DP_KERNEL_BEGIN();
   k_dot_final_b(blockIdx.x, gridDim.x, part, nblocks, nv, dots, H, m, j, mode, scal, reorth);
 }
 
@@ -2247,7 +2193,6 @@ __global__ void __launch_bounds__(kBlock) k_project(long long N, const double *_
                                                     double *__restrict__ w,
                                                     double *__restrict__ out,
                                                     const double *__restrict__ scal, int pass) {
-  DP_KERNEL_BEGIN();
   k_project_b(blockIdx.x, gridDim.x, N, V, ldv, nv, c, w, out, scal, pass);
 }
 
@@ -2256,14 +2201,12 @@ __global__ void __launch_bounds__(kBlock) k_multi_axpy(long long N, const double
                                                        long long ldv, int nv,
                                                        const double *__restrict__ c, double sign,
                                                        double *__restrict__ w) {
-  DP_KERNEL_BEGIN();
   k_multi_axpy_b(blockIdx.x, gridDim.x, N, V, ldv, nv, c, sign, w);
 }
 
 // y = x * alpha, or x / alpha (the reciprocal taken once per block: an FP64
 // division is a long instruction sequence on GB300)
 __global__ void k_scale(long long N, const double *x, const double *alpha, int invert, double *y) {
-  DP_KERNEL_BEGIN();
   k_scale_b(blockIdx.x, gridDim.x, N, x, alpha, invert, y);
 }
 
@@ -2271,17 +2214,14 @@ __global__ void k_scale(long long N, const double *x, const double *alpha, int i
 // right-hand side g; res_out = |g_{j+1}|.
 __global__ void k_givens(double *H, double *cs, double *sn, double *g, int m, int j,
                          double *res_out) {
-  DP_KERNEL_BEGIN();
   k_givens_b(blockIdx.x, gridDim.x, H, cs, sn, g, m, j, res_out);
 }
 
 __global__ void k_backsub(const double *H, const double *g, int m, int jend, double *y) {
-  DP_KERNEL_BEGIN();
   k_backsub_b(blockIdx.x, gridDim.x, H, g, m, jend, y);
 }
 
 __global__ void k_init_g(double *g, int m, const double *beta) {
-  DP_KERNEL_BEGIN();
   k_init_g_b(blockIdx.x, gridDim.x, g, m, beta);
 }
 
@@ -2325,7 +2265,6 @@ static int norm_into(Sim *s, const double *x, double *dst) {
 }
 
 __global__ void k_sqrt_inplace(double *v) {
-  DP_KERNEL_BEGIN();
   k_sqrt_inplace_b(blockIdx.x, gridDim.x, v);
 }
 
@@ -2486,13 +2425,11 @@ int la_alloc(Sim *s) {
 }
 
 __global__ void k_to_f32_i(long long n, const double *x, float *y) {
-  DP_KERNEL_BEGIN();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = float(x[i]);
 }
 
 __global__ void k_to_bf16(long long n, const double *x, __nv_bfloat16 *y) {
-  DP_KERNEL_BEGIN();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = __double2bfloat16(x[i]);
 }

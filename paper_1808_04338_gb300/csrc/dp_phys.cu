@@ -171,7 +171,6 @@ __device__ __forceinline__ void perf_range(const int *pc_cell, int np, int c, in
 
 __global__ void k_pattern_count(Phys P, const int *pc_cell, int np, const int *pw_start,
                                 int *len) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= P.nb) return;
   if (r >= P.nc) { int w = r - P.nc; len[r] = 1 + pw_start[w + 1] - pw_start[w]; return; }
@@ -205,7 +204,6 @@ __global__ void k_pattern_fill(Phys P, const double *kf, const double *km, const
                                const int *pc_well, const double *pc_wi, int np,
                                const int *pw_start, const int *pw_cell, const double *pw_wi,
                                const int *rowptr, int *col, int *diag, double *trans) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= P.nb) return;
   int e0 = rowptr[r];
@@ -256,7 +254,6 @@ __global__ void k_pattern_fill(Phys P, const double *kf, const double *km, const
 }
 
 __global__ void k_storage_len(int nb, int nL, int nc, const int *rowptr, int *len) {
-  DP_KERNEL_BEGIN();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nb) return;
   int i = row_of_pair(q, nL, nc);
@@ -265,7 +262,6 @@ __global__ void k_storage_len(int nb, int nL, int nc, const int *rowptr, int *le
 
 __global__ void k_storage_cols(int nb, int nL, int nc, const int *rowptr, const int *col,
                                const int *srowptr, int *scol) {
-  DP_KERNEL_BEGIN();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nb) return;
   int i = row_of_pair(q, nL, nc);
@@ -414,7 +410,6 @@ int phys_build_pattern(Sim *s) {
 
 __global__ void __launch_bounds__(kBlock) k_props(Phys P, const double *phi_f, const double *phi_m,
                                                   const double *p, const double *sw, double *pr) {
-  DP_KERNEL_BEGIN();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.nc) return;
   Props q;
@@ -485,7 +480,6 @@ __device__ __forceinline__ int find_entry(const int *__restrict__ rowptr,
 // the same, bit for bit: the same call with the same arguments.)
 template <bool GRAV, bool CAP>
 __global__ void __launch_bounds__(kBlock) k_conn_flux(AsmArgs a) {
-  DP_KERNEL_BEGIN();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   const Phys &P = a.P;
   if (c >= 4 * P.nL) return;
@@ -540,7 +534,6 @@ __global__ void __launch_bounds__(kBlock) k_conn_flux(AsmArgs a) {
 // rows: the rate or pressure constraint.
 template <bool GRAV, bool CAP>
 __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
-  DP_KERNEL_BEGIN();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const Phys &P = a.P;
   int r;
@@ -645,7 +638,6 @@ __global__ void __launch_bounds__(kBlock) k_assemble(AsmArgs a) {
 __global__ void k_save_old(Phys P, const double *phi_f, const double *phi_m, const double *p,
                            const double *sw, const double *bhp, double *pn, double *swn,
                            double *bhpn, double *Mn) {
-  DP_KERNEL_BEGIN();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < P.nw) bhpn[c] = bhp[c];
   if (c >= P.nc) return;
@@ -676,7 +668,6 @@ __global__ void k_well_rates(Phys P, const double *phi_f, const double *phi_m, c
                              const double *sw, const double *bhp, const int *perf_cell,
                              const int *perf_well, const double *perf_wi, int np,
                              const int *well_kind, double *q_oil, double *q_water) {
-  DP_KERNEL_BEGIN();
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= P.nw) return;
   double qo = 0.0, qw = 0.0;
@@ -708,7 +699,6 @@ int phys_well_rates(Sim *s, double *q) {
 // limit, or an oil-rate producer below it, goes on BHP control at the limit.
 __global__ void k_well_controls(int nw, int restore, const int *ctl_kind, const double *ctl_target,
                                 const double *limit, const double *bhp, int *kind, double *target) {
-  DP_KERNEL_BEGIN();
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nw) return;
   if (restore) {
@@ -778,7 +768,6 @@ __device__ __forceinline__ double warp_max(double v) {
 // cell and phase, formed once (an FP64 division per entry is a long
 // instruction sequence on this GPU; the norms then multiply).
 __global__ void k_norm_weights(Phys P, const double *phi_f, const double *phi_m, double *w) {
-  DP_KERNEL_BEGIN();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.nc) return;
   int loc = c >> 1;
@@ -803,7 +792,6 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *__r
                                                        const double *well_target, double dt,
                                                        const double *__restrict__ lq,
                                                        double *part) {
-  DP_KERNEL_BEGIN();
   double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // s2, max, sro, srw, dmo, dmw, |lq|^2, |R-lq|^2
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.nb; r += gridDim.x * blockDim.x) {
     if (r < P.nc) {
@@ -860,7 +848,6 @@ __global__ void __launch_bounds__(kBlock) k_norms_final(Phys P, const double *ph
                                                         const double *perf_wi, int np,
                                                         const int *well_kind, const double *part,
                                                         int nparts, double *out) {
-  DP_KERNEL_BEGIN();
   double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
     for (int k = 0; k < 6; ++k) v[k] = k == 1 ? fmax(v[k], part[b * 8 + k]) : v[k] + part[b * 8 + k];
@@ -930,7 +917,6 @@ __global__ void __launch_bounds__(kBlock) k_decouple_rows(int nb, int nc, int mo
                                                           const int *tpos, const double *val,
                                                           const double *R, double *fct,
                                                           double *bh) {
-  DP_KERNEL_BEGIN();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   double b0 = -R[2 * i], b1 = -R[2 * i + 1];
@@ -987,7 +973,6 @@ struct DecArgs {
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_decouple(DecArgs a) {
-  DP_KERNEL_BEGIN();
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.nnz) return;
   int i = __ldg(a.erow + e);
@@ -1059,7 +1044,6 @@ int phys_decouple_extract(Sim *s) {
 __global__ void k_natural_from_storage(long long nnz, int nc, int nL, const int *erow,
                                        const int *rowptr, const int *srowptr, const double *sval,
                                        double *out) {
-  DP_KERNEL_BEGIN();
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nnz) return;
   int i = erow[e];
@@ -1087,7 +1071,6 @@ __device__ __forceinline__ int kcol(int c, int nL, int nc) {   // -1: a matrix c
 }
 
 __global__ void k_schur_len(int nk, int nL, int nc, const int *rowptr, const int *col, int *len) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nk) return;
   int jr = r < nL ? 2 * r : nc + (r - nL), c = 0;
@@ -1097,7 +1080,6 @@ __global__ void k_schur_len(int nk, int nL, int nc, const int *rowptr, const int
 
 __global__ void k_schur_fill(int nk, int nL, int nc, const int *rowptr, const int *col,
                              const int *krowptr, int *kcolv, int *kdiag, int *kmap) {
-  DP_KERNEL_BEGIN();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nk) return;
   int jr = r < nL ? 2 * r : nc + (r - nL), k = krowptr[r];
@@ -1121,7 +1103,6 @@ __device__ __forceinline__ int find_col_in(const int *col, int lo, int hi, int c
 }
 
 __global__ void k_schur_pos(int nL, const int *rowptr, const int *col, int *pos_fm, int *pos_mf) {
-  DP_KERNEL_BEGIN();
   int loc = blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= nL) return;
   int f = 2 * loc, m = f + 1;
@@ -1130,7 +1111,6 @@ __global__ void k_schur_pos(int nL, const int *rowptr, const int *col, int *pos_
 }
 
 __global__ void k_schur_copy(long long nnzk, const int *kmap, const double *val, double *kval) {
-  DP_KERNEL_BEGIN();
   long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnzk) return;
   int e = kmap[k];
@@ -1144,7 +1124,6 @@ __global__ void k_schur_copy(long long nnzk, const int *kmap, const double *val,
 __global__ void k_schur_loc(int nL, int nc, int nw, const int *diag, const int *pos_fm,
                             const int *pos_mf, const int *kdiag, const double *val,
                             const double *R, double *kval, double *RK, double *Minv) {
-  DP_KERNEL_BEGIN();
   int loc = blockIdx.x * blockDim.x + threadIdx.x;
   if (loc < nw) {
     RK[2 * (nL + loc)] = R[2 * (nc + loc)];
@@ -1178,7 +1157,6 @@ __global__ void k_schur_loc(int nL, int nc, int nw, const int *diag, const int *
 
 __global__ void k_schur_back(int nL, int nc, int nw, const int *pos_mf, const double *val,
                              const double *Minv, const double *R, const double *yk, double *y) {
-  DP_KERNEL_BEGIN();
   int loc = blockIdx.x * blockDim.x + threadIdx.x;
   if (loc < nw) {
     y[2 * (nc + loc)] = yk[2 * (nL + loc)];
@@ -1266,7 +1244,6 @@ int phys_schur_back(Sim *s) {
 // ---------------------------------------------------------------- update
 __global__ void k_update(int nc, int nw, double ds_max, const double *y, double *p, double *sw,
                          double *bhp) {
-  DP_KERNEL_BEGIN();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < nw) bhp[c] += y[2 * (nc + c)];
   if (c >= nc) return;

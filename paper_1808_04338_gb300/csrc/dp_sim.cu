@@ -5,7 +5,6 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -63,14 +62,6 @@ void dfree(Sim *s, void *p) {
 }
 
 // ---------------------------------------------------------------- launches
-bool pdl_enabled() {
-  static const bool on = []() {
-    const char *e = std::getenv("DPSIM_PDL");
-    return !(e && e[0] == '0');
-  }();
-  return on;
-}
-
 LaunchScope::LaunchScope(Sim *sim, const char *name) : s(sim), timed(false) {
   ++s->launches;
   Timing &t = s->timing;
