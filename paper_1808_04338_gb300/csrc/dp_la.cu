@@ -43,20 +43,49 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int n, int nL, int nc, int 
 
 // lq = R + A y over every block row of the Jacobian as assembled (natural
 // order): the linear residual of the Newton equation A y = -R, whose scaled
-// norms the forcing terms 1 and 2 of Section 3.1 take.  Two lanes per block
-// row, one per component (as in k_bsr_spmv), writing natural order directly.
-__global__ void __launch_bounds__(kBlock) k_lin_residual(int n, const int *__restrict__ rowptr,
+// norms the forcing terms 1 and 2 of Section 3.1 take.  Two lanes per cell
+// block row, one per component, the rows taken in the storage order of the
+// Krylov operator's copy (as in k_bsr_spmv) so that a warp's rows have one
+// length; the well rows a warp each in block 0.  Natural order throughout.
+__global__ void __launch_bounds__(kBlock) k_lin_residual(int n, int nL, int nc,
+                                                         const int *__restrict__ rowptr,
                                                          const int *__restrict__ col,
                                                          const double *__restrict__ val,
                                                          const double *__restrict__ R,
                                                          const double *__restrict__ y,
                                                          double *__restrict__ lq) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int i = (int)(t >> 1), comp = (int)(t & 1);
-  if (i >= n) return;
-  const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
   const double2 *y2 = reinterpret_cast<const double2 *>(y);
+  if (blockIdx.x == 0) {   // the well rows (long): a warp per row, lanes over its blocks
+    int lane = threadIdx.x & 31;
+    for (int i = nc + (threadIdx.x >> 5); i < n; i += blockDim.x >> 5) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int e = __ldg(rowptr + i) + lane, e1 = __ldg(rowptr + i + 1); e < e1; e += 32) {
+        const double *b = val + 4 * (size_t)e;
+        double2 x = __ldg(y2 + __ldg(col + e));
+        a0 = fma(__ldg(b), x.x, fma(__ldg(b + 1), x.y, a0));
+        a1 = fma(__ldg(b + 2), x.x, fma(__ldg(b + 3), x.y, a1));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      }
+      if (lane == 0) {
+        lq[2 * (size_t)i] = R[2 * (size_t)i] + a0;
+        lq[2 * (size_t)i + 1] = R[2 * (size_t)i + 1] + a1;
+      }
+    }
+    return;
+  }
+  // cell rows in the storage order (row_of_pair): a warp holds rows of one
+  // kind (fracture rows of up to 8 blocks, or matrix rows of 2), two lanes a row
+  long long t = (long long)(blockIdx.x - 1) * blockDim.x + threadIdx.x;
+  int q = (int)(t >> 1), comp = (int)(t & 1);
+  if (q >= nc) return;
+  int i = row_of_pair(q, nL, nc);
+  const double2 *v2 = reinterpret_cast<const double2 *>(val) + comp;
   double a = R[2 * (size_t)i + comp];
+#pragma unroll 4
   for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) {
     double2 b = __ldg(v2 + 2 * (size_t)e);
     double2 x = __ldg(y2 + __ldg(col + e));
@@ -67,8 +96,9 @@ __global__ void __launch_bounds__(kBlock) k_lin_residual(int n, const int *__res
 
 int lin_residual(Sim *s) {
   const Bsr &A = s->A;
-  DP_LAUNCH(s, k_lin_residual, nblk(2LL * A.n), kBlock, 0, A.n, A.rowptr, A.col, A.val, s->R,
-            s->y, s->lq);
+  // the assembled Jacobian of the full system (also with the Schur option)
+  DP_LAUNCH(s, k_lin_residual, 1 + nblk(2LL * s->ph.nc), kBlock, 0, A.n, s->ph.nL, s->ph.nc,
+            A.rowptr, A.col, A.val, s->R, s->y, s->lq);
   DP_CUDA(s, cudaGetLastError());
   return DP_OK;
 }

@@ -796,15 +796,15 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *__r
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.nb; r += gridDim.x * blockDim.x) {
     if (r < P.nc) {
 #pragma unroll
-      for (int al = 0; al < 2; ++al) {
+      for (int al = 0; al < 2; ++al) {   // explicit FMAs: this kernel is FP64-bound
         double x = (R[2 * r + al] * dt) * w[2 * r + al];
-        v[0] += x * x;
+        v[0] = fma(x, x, v[0]);
         v[1] = fmax(v[1], fabs(x));
         if (lq) {
           double a = (lq[2 * r + al] * dt) * w[2 * r + al];
-          double d = ((R[2 * r + al] - lq[2 * r + al]) * dt) * w[2 * r + al];
-          v[6] += a * a;
-          v[7] += d * d;
+          double d = x - a;   // R~(R - lq), scaled as R and lq are
+          v[6] = fma(a, a, v[6]);
+          v[7] = fma(d, d, v[7]);
         }
       }
       v[2] += R[2 * r];
@@ -815,12 +815,12 @@ __global__ void __launch_bounds__(kBlock) k_norms_part(Phys P, const double *__r
       int w = r - P.nc;
       double sc = well_kind[w] == 0 ? fmax(well_target[w], 1e-12) : well_target[w];
       double x = R[2 * r] / sc;
-      v[0] += x * x;
+      v[0] = fma(x, x, v[0]);
       v[1] = fmax(v[1], fabs(x));
       if (lq) {
         double a = lq[2 * r] / sc, d = (R[2 * r] - lq[2 * r]) / sc;
-        v[6] += a * a;
-        v[7] += d * d;
+        v[6] = fma(a, a, v[6]);
+        v[7] = fma(d, d, v[7]);
       }
     }
   }
