@@ -323,9 +323,8 @@ int sim_solver_sizes(dp_sim *sim, int32_t *nb, int32_t *nnzb);
  * level, times each lanes-per-row variant (1..32) of the kernel of its
  * smoother's level operator, of the prolongation and of the restriction;
  * for level 0 in colour order, the kernel of its Gauss-Seidel colours and
- * residual (see sim_set_l0_kernel); the kernel of the ILU(0) forward colours
- * (see sim_set_ilu_kernel); and the V-cycle schedule below the cluster level
- * (one cluster launch or a launch per phase).  Each candidate
+ * residual (see sim_set_l0_kernel); and the V-cycle schedule below the
+ * cluster level (one cluster launch or a launch per phase).  Each candidate
  * runs `reps` times, timed with CUDA events on the simulation stream on the
  * level's own work vectors, and the fastest is kept; the Arnoldi steps'
  * CUDA graphs are captured again on the next solve.  Colourings, aggregates
@@ -356,18 +355,6 @@ int sim_autotune(dp_sim *sim, int32_t reps, char *report, int32_t report_len);
  * same results bit for bit; 2, 4 and 8 differ from them at rounding level.
  * Returns DP_EINVAL for another value.  Takes effect from the next solve. */
 int sim_set_l0_kernel(dp_sim *sim, int32_t variant);
-
-/* Sets the kernel of the ILU(0) forward sweep's colours after the first
- * (what sim_autotune chooses; the default is 0): 0 two lanes a row, the
- * last colour's long rows (the wells) done by the last CTA of the launch
- * before them; -1 a persistent kernel whose producer warp brings tiles of
- * 256 rows (L-row pointers, columns, 2x2 blocks) into shared memory with
- * bulk asynchronous copies while the other warps compute the previous tile
- * (needs the factor's arrays at 16-byte boundaries, else it runs as 0; its
- * waits are bounded as in sim_set_l0_kernel), the long rows in their own
- * launch.  Both give the same results bit for bit.  Returns DP_EINVAL for
- * another value.  Takes effect from the next solve. */
-int sim_set_ilu_kernel(dp_sim *sim, int32_t variant);
 
 /* Device bytes the realisation holds through its allocator now, and the
  * most it has held at once (both may be NULL).  Host only, no CUDA call. */

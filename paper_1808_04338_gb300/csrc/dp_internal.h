@@ -329,7 +329,6 @@ struct Sim {
   double *p0c_val = nullptr, *dinv_c = nullptr;
   float *p0c_valf = nullptr, *dinv_cf = nullptr;
   bool l0_lu = false;
-  int ilu_fwd_kernel = 0;   // ILU(0) forward colours: 0 two lanes a row (wells in the last CTA), -1 pipelined
   int l0_G = 1;       // lanes per row of the level-0 colour-order sweeps (autotuned; 1: a thread)
   int shapes = 0;     // bumped whenever launch shapes change (autotune, AMG set-up)
   double *l0_pv = nullptr;

@@ -486,8 +486,8 @@ int ilu_setup(Sim *s) {
   s->lu_dpos = (int *)dalloc(s, (size_t)n * 4);
   s->lu_col = (int *)dalloc(s, (size_t)s->K.nnz * 4);
   s->lu_src = (int *)dalloc(s, (size_t)s->K.nnz * 4);
-  s->lu_val = (double *)dalloc(s, (size_t)s->K.nnz * 32 + 96);
-  s->lu_valf = (float *)dalloc(s, (size_t)s->K.nnz * 16 + 48);
+  s->lu_val = (double *)dalloc(s, (size_t)s->K.nnz * 32);
+  s->lu_valf = (float *)dalloc(s, (size_t)s->K.nnz * 16);
   int *len = (int *)dalloc(s, (size_t)n * 4);
   if (!s->colour || !s->perm || !s->iperm || !s->lu_rowptr || !s->lu_dpos || !s->lu_col ||
       !s->lu_src || !s->lu_val || !s->lu_valf || !len) {
@@ -531,10 +531,10 @@ int ilu_setup(Sim *s) {
             s->upd_ptr, cnt, s->upd_e2, s->upd_q);
   // split layout: L and U row pointers, each entry's block, permuted columns
   int *nu = cnt;   // reused: n <= nnz
-  s->lu_Lptr = (int *)dalloc(s, ((size_t)n + 1) * 4 + 16);   // + the bulk copies' overrun
+  s->lu_Lptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
   s->lu_Uptr = (int *)dalloc(s, ((size_t)n + 1) * 4);
   s->lu_dst = (int *)dalloc(s, (size_t)nnz * 4);
-  s->lu_colp = (int *)dalloc(s, (size_t)nnz * 4 + 16);
+  s->lu_colp = (int *)dalloc(s, (size_t)nnz * 4);
   s->ilu_zp = (double *)dalloc(s, (size_t)2 * n * 8);
   if (!s->lu_Lptr || !s->lu_Uptr || !s->lu_dst || !s->lu_colp || !s->ilu_zp) {
     s->fail(DP_ENOMEM, "allocation failed");
@@ -601,10 +601,6 @@ static int tail_grid(int nb) {
   return std::max(1, std::min(nb, slots));
 }
 
-template <typename T, typename TR>
-static void ilu_fwd_tma(Sim *s, int r0, int r1, const T *lu, const TR *r, T *zp);
-static bool ilu_tma_ok(const Sim *s, const void *lu);
-
 // (LU)^-1 r with the factor in T and r (natural order) in TR; the result
 // is left in the colour-order work vector s->ilu_zp, from which the caller
 // gathers it (ilu_result) while converting or accumulating.
@@ -623,10 +619,6 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
     if (r1 <= r0) continue;
     int nx = c + 1;   // the next non-empty colour
     while (nx < nc && s->lu_cstart[nx + 1] <= s->lu_cstart[nx]) ++nx;
-    if (c != first && s->lu_cmaxlen[c] <= kLongRow && s->ilu_fwd_kernel < 0 && ilu_tma_ok(s, lu)) {
-      ilu_fwd_tma<T, TR>(s, r0, r1, lu, r, zp);   // the pipelined colour; long colours follow alone
-      continue;
-    }
     if (c != first && s->lu_cmaxlen[c] <= kLongRow && nx < nc && s->lu_cmaxlen[nx] > kLongRow) {
       // a short colour followed by a long one: its last CTA takes the long rows
       Tail tl;
@@ -1324,10 +1316,10 @@ __global__ void __launch_bounds__(kBlock) k_resid_cs(int r0, int r1, const int *
 // A bounded wait that gives up sets *err and ends the thread (the producer
 // first lets its copies in flight land, again with a bound).
 constexpr int kTT = 256;
-template <typename T, int CAPR, int VPE = 1> struct TStage {   // VPE values an entry
+template <typename T, int CAPR> struct TStage {
   int rp[kTT + 8];
   int col[CAPR * kTT];
-  T val[VPE * CAPR * kTT];
+  T val[CAPR * kTT];
 };
 
 // a barrier of the kTT consumer threads only (named barrier 1; the
@@ -1345,13 +1337,12 @@ __device__ __forceinline__ void consumers_sync() {
 // values when they fit the stage.  A stage's full barrier expects exactly
 // the bytes copied into it.  When a wait gives up the warp sets *err, lets
 // the copies in flight land (bounded) and ends.
-template <typename T, int S, int CAPR, int VPE = 1>
+template <typename T, int S, int CAPR>
 __device__ __forceinline__ void tile_producer(int nph, const int *pr0, const int *pr1, int B, int G,
                                               const int *__restrict__ rowptr,
                                               const int *__restrict__ colp,
-                                              const T *__restrict__ pv,
-                                              TStage<T, CAPR, VPE> *st, uint64_t *full,
-                                              uint64_t *empty, int *err) {
+                                              const T *__restrict__ pv, TStage<T, CAPR> *st,
+                                              uint64_t *full, uint64_t *empty, int *err) {
   constexpr int kCap = CAPR * kTT;
   const int lane = threadIdx.x & 31;
   auto mine = [&](int p) {
@@ -1387,12 +1378,11 @@ __device__ __forceinline__ void tile_producer(int nph, const int *pr0, const int
         int aq = tq0 & ~3, nrp = (tq0 + tn + 1 - aq + 3) & ~3;
         int ae = te0 & ~3, ne = (te1 - ae + 3) & ~3;
         bool fits = ne <= kCap;
-        mbar_arrive_tx(&full[k],
-                       (uint32_t)(4 * nrp + (fits ? ne * (4 + VPE * (int)sizeof(T)) : 0)));
+        mbar_arrive_tx(&full[k], (uint32_t)(4 * nrp + (fits ? ne * (4 + (int)sizeof(T)) : 0)));
         bulk_load(st[k].rp, rowptr + aq, 4u * nrp, &full[k]);
         if (fits && ne > 0) {
           bulk_load(st[k].col, colp + ae, 4u * ne, &full[k]);
-          bulk_load(st[k].val, pv + (size_t)VPE * ae, (uint32_t)(VPE * sizeof(T)) * ne, &full[k]);
+          bulk_load(st[k].val, pv + ae, (uint32_t)sizeof(T) * ne, &full[k]);
         }
       }
     }
@@ -1715,141 +1705,6 @@ static int gs_sweep_persistent(Sim *s, const SweepPlan &plan, const T *pv, const
                                 (const int *)s->l0_colp, pv, dinv, b, x,
                                 (unsigned *)(s->dev_err + 4), s->dev_err));
   return DP_OK;
-}
-
-// ILU(0) forward sweep of one colour (rows [r0, r1) of the colour order) as
-// a pipelined persistent kernel, on the producer/consumer scheme of
-// sweep_tma_body: a CTA walks tiles of kTT rows; its producer warp brings a
-// tile's L-row pointers, L columns and 2x2 L blocks (split layout) into
-// shared memory with bulk copies; its kTT consumer threads take a row each,
-// both components: the first 8 blocks and columns, then the 8 gathered zp
-// pairs, then the products in k_ilu_fwd's order for each component, so the
-// results are that kernel's bit for bit.  perm and the right-hand side are
-// read per thread before the wait.  Rows with more blocks than the stage
-// holds read them from global memory.  The L-row pointers, the columns and
-// the factor are allocated with 16 spare bytes at least, and the blocks and
-// columns that follow the L part lie in the same arrays.
-template <typename T>
-__device__ __forceinline__ void ld_blk(const T *p, T (&a)[4]) {   // plain loads (shared or global)
-  if constexpr (sizeof(T) == 4) {
-    float4 v = *reinterpret_cast<const float4 *>(p);
-    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
-  } else {
-    double2 u = reinterpret_cast<const double2 *>(p)[0], w = reinterpret_cast<const double2 *>(p)[1];
-    a[0] = u.x; a[1] = u.y; a[2] = w.x; a[3] = w.y;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void ilu_row_sum(int n, const int *cs, const T *vs, const T *zp,
-                                            T &s0, T &s1) {
-  using T2 = typename V2<T>::t;
-  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
-  constexpr int kB = 8;
-  for (int j0 = 0; j0 < n; j0 += kB) {
-    int c[kB];
-    T a[kB][4];
-    T2 x[kB];
-#pragma unroll
-    for (int j = 0; j < kB; ++j)
-      if (j0 + j < n) {
-        c[j] = cs[j0 + j];
-        ld_blk<T>(vs + 4 * (size_t)(j0 + j), a[j]);
-      }
-#pragma unroll
-    for (int j = 0; j < kB; ++j)
-      if (j0 + j < n) x[j] = z2[c[j]];
-#pragma unroll
-    for (int j = 0; j < kB; ++j)
-      if (j0 + j < n) {
-        s0 = fma(a[j][0], x[j].x, s0);
-        s0 = fma(a[j][1], x[j].y, s0);
-        s1 = fma(a[j][2], x[j].x, s1);
-        s1 = fma(a[j][3], x[j].y, s1);
-      }
-  }
-}
-
-template <typename T, typename TR, int S, int CAPR>
-__global__ void __launch_bounds__(kTT + 32) k_ilu_fwd_tma(int r0, int r1,
-                                                          const int *__restrict__ perm,
-                                                          const int *__restrict__ Lptr,
-                                                          const int *__restrict__ colp,
-                                                          const T *__restrict__ lu,
-                                                          const TR *__restrict__ rhs, T *zp,
-                                                          int *err) {
-  constexpr int kCap = CAPR * kTT;
-  extern __shared__ __align__(128) unsigned char tma_smem[];
-  TStage<T, CAPR, 4> *st = reinterpret_cast<TStage<T, CAPR, 4> *>(tma_smem);
-  __shared__ __align__(8) uint64_t full[S], empty[S];
-  int ntile = (r1 - r0 + kTT - 1) / kTT;
-  int mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < S; ++k) {
-      mbar_init(&full[k], 1);
-      mbar_init(&empty[k], kTT);
-    }
-    mbar_init_fence();
-  }
-  __syncthreads();
-  if (threadIdx.x >= kTT) {   // the producer warp
-    tile_producer<T, S, CAPR, 4>(1, &r0, &r1, (int)blockIdx.x, (int)gridDim.x, Lptr, colp, lu, st,
-                                 full, empty, err);
-    return;
-  }
-  int t = threadIdx.x;
-  __shared__ int abort_flag;
-  volatile int *abort_v = &abort_flag;
-  if (t == 0) abort_flag = 0;
-  consumers_sync();
-  for (int i = 0; i < mine; ++i) {
-    int k = i % S;
-    int q0 = r0 + ((int)blockIdx.x + i * (int)gridDim.x) * kTT, nrow = min(kTT, r1 - q0);
-    int r = q0 + t;
-    bool in = t < nrow;
-    TR h0 = TR(0), h1 = TR(0);
-    if (in) {
-      int pi = __ldg(perm + r);
-      h0 = rhs[2 * (size_t)pi];
-      h1 = rhs[2 * (size_t)pi + 1];
-    }
-    bool ok = !*abort_v && mbar_wait(&full[k], (i / S) & 1);
-    if (!ok) *abort_v = 1;
-    if (ok && in) {
-      const int *rp = st[k].rp + (q0 & 3);
-      int ae = rp[0] & ~3;
-      bool fits = ((rp[nrow] - ae + 3) & ~3) <= kCap;
-      int e = rp[t], e1 = rp[t + 1];
-      T s0 = T(0), s1 = T(0);
-      if (fits)
-        ilu_row_sum<T>(e1 - e, st[k].col + (e - ae), st[k].val + 4 * (e - ae), zp, s0, s1);
-      else
-        ilu_row_sum<T>(e1 - e, colp + e, lu + 4 * (size_t)e, zp, s0, s1);
-      zp[2 * (size_t)r] = T(h0) - s0;
-      zp[2 * (size_t)r + 1] = T(h1) - s1;
-    }
-    mbar_arrive(&empty[k]);
-  }
-  if (*abort_v) atomicExch(err, 1);
-}
-
-// the pipelined forward colour: two stages of up to 5 L blocks a row on
-// average (a colour's rows have 1 or 7 L blocks: 4 on average)
-template <typename T, typename TR>
-static void ilu_fwd_tma(Sim *s, int r0, int r1, const T *lu, const TR *r, T *zp) {
-  constexpr int S = 2, CAPR = 5;
-  constexpr int smem = S * (int)sizeof(TStage<T, CAPR, 4>);
-  s->waits_used = true;
-  DP_LAUNCH(s, (k_ilu_fwd_tma<T, TR, S, CAPR>),
-            (tma_grid<1000 + 16 * S + CAPR>(k_ilu_fwd_tma<T, TR, S, CAPR>, smem, r1 - r0)),
-            kTT + 32, smem, r0, r1, s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp, s->dev_err);
-}
-
-// the pipelined ILU(0) kernel's arrays at 16-byte boundaries (an allocator
-// passed by the caller may give less)
-static bool ilu_tma_ok(const Sim *s, const void *lu) {
-  auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
-  return a16(s->lu_Lptr) && a16(s->lu_colp) && a16(lu);
 }
 
 template <typename T> struct L0C;
@@ -2224,38 +2079,6 @@ static int tune_cycle(Sim *s, int reps, std::string &rep) {
   return DP_OK;
 }
 
-// The ILU(0) forward colours: two lanes a row with the wells in the last
-// CTA (0) or the pipelined bulk-copy kernel with the wells in their own
-// launch (-1), timed as whole applications (forward and backward) to the
-// decoupled right-hand side.
-template <typename T>
-static int tune_ilu(Sim *s, int reps, std::string &rep) {
-  if (!s->bh) return DP_OK;
-  const T *lu;
-  if constexpr (sizeof(T) == 4) lu = s->lu_valf; else lu = s->lu_val;
-  if (!lu) return DP_OK;
-  static const int cand[] = {0, -1};
-  int old = s->ilu_fwd_kernel, best = old;
-  float best_ms = 1e30f;
-  std::string line;
-  char buf[160];
-  for (int g : cand) {
-    s->ilu_fwd_kernel = g;
-    float ms = 0.f;
-    auto one = [&]() -> int { return ilu_apply_t<T, double>(s, lu, s->bh); };
-    int rc = time_launches(s, reps, one, &ms);
-    if (rc != DP_OK) { s->ilu_fwd_kernel = old; return rc; }
-    std::snprintf(buf, sizeof buf, " %d:%.1f", g, 1000.f * ms / reps);
-    line += buf;
-    if (ms < best_ms) { best_ms = ms; best = g; }
-  }
-  s->ilu_fwd_kernel = best;
-  std::snprintf(buf, sizeof buf, "ILU(0) forward colours kernel %d -> %d (us per application:%s)\n",
-                old, best, line.c_str());
-  rep += buf;
-  return DP_OK;
-}
-
 int autotune(Sim *s, int reps, std::string &rep) {
   if (!s->amg_ready || s->opt.precond != 2) {
     s->fail(DP_EINVAL, "autotune needs the AMG hierarchy (one CPR-FPF solve first)");
@@ -2269,11 +2092,9 @@ int autotune(Sim *s, int reps, std::string &rep) {
   if (s->opt.precision >= 1) {
     DP_TRY(tune_l0<float>(s, reps, rep));
     DP_TRY(tune_cycle<float>(s, reps, rep));
-    DP_TRY(tune_ilu<float>(s, reps, rep));
   } else {
     DP_TRY(tune_l0<double>(s, reps, rep));
     DP_TRY(tune_cycle<double>(s, reps, rep));
-    DP_TRY(tune_ilu<double>(s, reps, rep));
   }
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
   graphs_free(s);   // the Arnoldi steps are captured again with the new launch shapes

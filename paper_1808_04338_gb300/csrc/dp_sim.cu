@@ -638,17 +638,6 @@ extern "C" int sim_set_l0_kernel(dp_sim *s, int32_t variant) {
   return DP_OK;
 }
 
-extern "C" int sim_set_ilu_kernel(dp_sim *s, int32_t variant) {
-  if (!s || (variant != 0 && variant != -1)) return DP_EINVAL;
-  DP_TRY(unusable(s));
-  if (s->ilu_fwd_kernel != variant) {
-    s->ilu_fwd_kernel = variant;
-    graphs_free(s);
-    ++s->shapes;
-  }
-  return DP_OK;
-}
-
 extern "C" int sim_autotune(dp_sim *s, int32_t reps, char *report, int32_t report_len) {
   if (!s || reps < 1 || (report && report_len < 1)) return DP_EINVAL;
   DP_TRY(unusable(s));

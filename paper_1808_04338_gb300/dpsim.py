@@ -163,7 +163,6 @@ def load():
     L.sim_footprint.argtypes = [P, P, P]
     L.sim_autotune.argtypes = [P, I, C.c_char_p, I]
     L.sim_set_l0_kernel.argtypes = [P, I]
-    L.sim_set_ilu_kernel.argtypes = [P, I]
     L.sim_solver_sizes.argtypes = [P, P, P]
     L.dp_stream_create.argtypes = [P]
     L.dp_stream_destroy.argtypes = [P]
@@ -575,11 +574,6 @@ class Sim:
         thread per row, 0: rows staged in shared memory, -1/-2/-3: the
         pipelined bulk-copy kernels, 2/4/8: lanes per row)."""
         self._check(load().sim_set_l0_kernel(self.h, int(variant)), "sim_set_l0_kernel")
-
-    def set_ilu_kernel(self, variant: int):
-        """The kernel of the ILU(0) forward colours (0: two lanes a row, the
-        wells in the last CTA; -1: the pipelined bulk-copy kernel)."""
-        self._check(load().sim_set_ilu_kernel(self.h, int(variant)), "sim_set_ilu_kernel")
 
     def autotune(self, reps: int = 20) -> str:
         """Time the AMG level kernels' launch shapes and keep the fastest;

@@ -12,11 +12,7 @@ timestep with each kernel.
 * with several tiles per CTA, the pipelined kernels reuse their stages, and
   none of their bounded waits gives up (the timestep returns DP_OK);
 * the lanes-per-row kernels (2, 4, 8) converge to the same state within the
-  Newton tolerance;
-* the ILU(0) forward colours through the pipelined bulk-copy kernel
-  (sim_set_ilu_kernel -1, the wells in their own launch) end in the same
-  state bit for bit as through the two-lanes-a-row kernel whose last CTA does
-  the wells.
+  Newton tolerance.
 """
 import numpy as np
 import pytest
@@ -49,29 +45,25 @@ def test_level0_kernels_agree(prob, precision):
     counts = np.bincount(colour, minlength=nc)
     assert nc >= 2 and counts[0] > 4 * 256 * 152 and counts[0] % 4 != 0
     states, launches = {}, {}
-    runs = [(v, 0) for v in SAME + (2, 4, 8)] + [(1, -1), (-1, -1)]
-    for v, ilu in runs:
+    for v in SAME + (2, 4, 8):
         g.set_state(*start)
         g.set_l0_kernel(v)
-        g.set_ilu_kernel(ilu)
-        g.time_kernel("k_ilu_fwd_tma" if ilu else "_tma" if v > -4 else "_sweep")
+        g.time_kernel("_tma" if v > -4 else "_sweep")
         g.kernel_timing(reset=True)
         rc, st = g.advance(prob.dt)
-        _, launches[v, ilu] = g.kernel_timing(reset=True)
+        _, launches[v] = g.kernel_timing(reset=True)
         g.time_kernel(None)
-        assert rc == 0 and st.converged, (v, ilu, rc)
-        states[v, ilu] = g.get_state()
-    for v, ilu in [(v, 0) for v in SAME] + [(1, -1), (-1, -1)]:
-        assert (launches[v, ilu] > 0) == (v < 0 or ilu < 0), (v, ilu, launches[v, ilu])
-        for a, b in zip(states[v, ilu], states[1, 0]):
-            assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), (v, ilu)
-    p1, s1, b1 = states[1, 0]
+        assert rc == 0 and st.converged, (v, rc)
+        states[v] = g.get_state()
+    for v in SAME:
+        assert (launches[v] > 0) == (v < 0), (v, launches[v])
+        for a, b in zip(states[v], states[1]):
+            assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), v
+    p1, s1, b1 = states[1]
     for v in (2, 4, 8):
-        p, s, b = states[v, 0]
+        p, s, b = states[v]
         assert np.abs(p - p1).max() <= 1e-5 * np.abs(p1).max(), v
         assert np.abs(s - s1).max() <= 1e-5, v
     with pytest.raises(RuntimeError):
         g.set_l0_kernel(3)
-    with pytest.raises(RuntimeError):
-        g.set_ilu_kernel(1)
     g.close()
