@@ -311,29 +311,31 @@ def run_ensemble(args):
         for s in sims:
             tuned += sum(1 for l in s.autotune(10).splitlines() if "->" in l)
 
-    def step(threads):
-        for s, (p, sw, b) in zip(sims, x0):
+    def step(threads, ss=None):
+        ss = ss or sims
+        for s, (p, sw, b) in zip(ss, x0):
             s.set_state_device(p, sw, b)
-        rc, stats, _ = dpsim.advance_many(sims, dts, threads=threads)
+        rc, stats, _ = dpsim.advance_many(ss, dts, threads=threads)
         if rc != 0:
             raise RuntimeError(f"sim_advance_many failed ({rc})")
         return sum(st.newton_iters for st in stats), sum(st.linear_iters for st in stats)
 
-    def timed(threads):
+    def timed(threads, ss=None):
+        ss = ss or sims
         for _ in range(args.warmup):
-            step(threads)
+            step(threads, ss)
         torch.cuda.synchronize()
-        l0 = sum(s.launch_count() for s in sims)
+        l0 = sum(s.launch_count() for s in ss)
         t0 = time.perf_counter()
         solves = its = 0
         for _ in range(args.steps):
-            a, b = step(threads)
+            a, b = step(threads, ss)
             solves += a
             its += b
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         return {"sec": sec, "solves": solves, "its": its,
-                "launches": sum(s.launch_count() for s in sims) - l0}
+                "launches": sum(s.launch_count() for s in ss) - l0}
 
     # the lockstep batched engine: one launch per phase over all members of a
     # batch; `groups` batches (members dealt round-robin by size) advance
@@ -395,6 +397,24 @@ def run_ensemble(args):
     clk.__enter__()
     bat = btimed(best)
     clk.__exit__()
+    # the plain FP64 path on the same members, run the fastest plain way
+    # (host threads, a stream each), for the comparison at equal tolerance
+    fp64 = None
+    if args.precision >= 1:
+        o64 = dpsim.options("report", precision=0, schur=args.schur, cluster_rows=-1)
+        s64 = [dpsim.Sim(prob, o64, stream=st.torch) for prob, st in zip(members, streams)]
+        if args.autotune:
+            step(args.threads, s64)
+            for s in s64:
+                s.autotune(10)
+        r64 = timed(args.threads, s64)
+        fp64 = {"value": 64 * args.steps / r64["sec"], "unit": "realisation timesteps/s",
+                "threads": args.threads, "ms_per_step": 1000.0 * r64["sec"] / args.steps,
+                "newton_solves_per_s": r64["solves"] / r64["sec"],
+                "fgmres_iters_per_solve": r64["its"] / max(r64["solves"], 1),
+                "note": "plain FP64 path (FP64 ILU(0) and AMG), sim_advance_many"}
+        for s in s64:
+            s.close()
     cells = sum(p.n_cells for p in members)
     line = {"metric": "batched ensemble timesteps", "value": 64 * args.steps / bat["sec"],
             "unit": "realisation timesteps/s", "n_gpus": 1, "steps": args.steps,
@@ -418,6 +438,7 @@ def run_ensemble(args):
             "autotune_decisions": tuned if args.autotune else None,
             "batch_profile": bat["profile"],
             "batch_groups": {g: 64 * args.steps / v["sec"] for g, v in by_groups.items()},
+            "fp64_path": fp64,
             "gpu_launches": bat["launches"], "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     for s in sims:
