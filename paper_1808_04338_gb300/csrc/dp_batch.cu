@@ -16,6 +16,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -428,6 +429,10 @@ struct dp_batch {
   dp::Phase backsub, axpy, gather;
   std::string err;
   int64_t launches = 0;
+  // captured Arnoldi steps: key (column j, activity mask) -> the executable
+  // graph and the launches it holds; the same Newton rounds recur with the
+  // same masks in every timestep, so the cache is replayed from the second on
+  std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;
   // the per-realisation parts (assembly, set-up, update) run on the
   // realisations' own streams from a pool of host threads
   std::vector<cudaEvent_t> ev;   // per realisation: its set-up is queued
@@ -447,6 +452,11 @@ struct dp_batch {
 };
 
 namespace dp {
+
+static void graphs_clear(dp_batch *b) {
+  for (auto &g : b->graphs) cudaGraphExecDestroy(g.second.first);
+  b->graphs.clear();
+}
 
 static void *balloc(dp_batch *b, size_t bytes) {
   void *p = nullptr;
@@ -699,6 +709,7 @@ static int one_phase(dp_batch *b, std::vector<Phase> *into, Phase *ph, int kind,
 // the FP32 preconditioner) and the pieces of the restart cycle
 static int build_plan(dp_batch *b) {
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ECUDA;
+  graphs_clear(b);   // they hold the old records' addresses
   for (void *p : b->blocks) cudaFree(p);
   b->blocks.clear();
   b->step.clear();
@@ -1028,6 +1039,38 @@ static int run_step(dp_batch *b, int j, const unsigned char *act) {
   return DP_OK;
 }
 
+// run_step through the graph cache: captured the first time a (j, mask)
+// comes (thread-local capture: the member streams' host threads keep
+// working meanwhile), replayed after
+constexpr size_t kMaxGraphs = 4096;
+static int run_step_graph(dp_batch *b, int j, const unsigned char *act) {
+  std::string key(reinterpret_cast<const char *>(&j), sizeof j);
+  key.append(reinterpret_cast<const char *>(act), (size_t)b->nm);
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    if (b->graphs.size() >= kMaxGraphs) graphs_clear(b);
+    int64_t l0 = b->launches;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return DP_ECUDA;
+    int rc = run_step(b, j, act);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != DP_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != DP_OK ? rc : DP_ECUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return DP_ECUDA;
+    it = b->graphs.emplace(key, std::make_pair(ex, b->launches - l0)).first;
+    b->launches = l0;
+  }
+  if (cudaGraphLaunch(it->second.first, b->stream) != cudaSuccess) return DP_ECUDA;
+  b->launches += it->second.second;
+  return DP_OK;
+}
+
 static int fetch_gather(dp_batch *b) {
   if (cudaMemcpyAsync(b->h_gath, b->gath, 32 * (size_t)b->nm, cudaMemcpyDeviceToHost, b->stream) !=
           cudaSuccess ||
@@ -1108,7 +1151,7 @@ static int batch_fgmres(dp_batch *b, const std::vector<int> &in, const std::vect
         any = any || hs[k];
       }
       if (!any) break;
-      DP_TRY(run_step(b, j, act));
+      DP_TRY(run_step_graph(b, j, act));
       ++b->arnoldi_steps;
       DP_TRY(fetch_gather(b));
       for (int k = 0; k < nm; ++k) {
@@ -1259,6 +1302,7 @@ extern "C" void batch_destroy(dp_batch *b) {
   if (b->gath) cudaFree(b->gath);
   if (b->h_gath) cudaFreeHost(b->h_gath);
   if (b->h_norms) cudaFreeHost(b->h_norms);
+  dp::graphs_clear(b);
   delete b;
 }
 
