@@ -1041,9 +1041,12 @@ static int run_step(dp_batch *b, int j, const unsigned char *act) {
 
 // run_step through the graph cache: captured the first time a (j, mask)
 // comes (thread-local capture: the member streams' host threads keep
-// working meanwhile), replayed after
+// working meanwhile), replayed after; on the legacy default stream (which
+// cannot be captured) the launches are made directly
 constexpr size_t kMaxGraphs = 4096;
 static int run_step_graph(dp_batch *b, int j, const unsigned char *act) {
+  // the legacy default stream cannot be captured: launch directly there
+  if (b->stream == nullptr || b->stream == cudaStreamLegacy) return run_step(b, j, act);
   std::string key(reinterpret_cast<const char *>(&j), sizeof j);
   key.append(reinterpret_cast<const char *>(act), (size_t)b->nm);
   auto it = b->graphs.find(key);

@@ -89,17 +89,23 @@ def test_owned_streams_are_distinct():
 
 def _batch_run(members, opts, steps, owned=True):
     """Each member advanced `steps` timesteps by one lockstep batch; returns
-    per step [(status, newton, linear, state)] and the batch's launch count."""
+    per step [(status, newton, linear, state)] and the batch's launch count.
+    owned: the batch on a stream of its own, where its Arnoldi steps are
+    captured into CUDA graphs and replayed (else torch's current stream,
+    the legacy default stream, where they are launched directly)."""
     import torch
     sims = [gpu().Sim(p, opts, stream=torch.cuda.Stream()) for p in members]
-    b = gpu().Batch(sims)
+    bst = gpu().OwnedStream() if owned else None
+    b = gpu().Batch(sims, stream=bst.torch if owned else None)
     out = []
-    for _ in range(steps):
+    for _ in range(steps):   # (j, mask) keys recur across Newton rounds: graphs replayed
         rc, stats, status = b.advance([p.dt for p in members])
         out.append([(status[k], stats[k].newton_iters, stats[k].linear_iters, s.get_state())
                     for k, s in enumerate(sims)])
     n = b.launch_count()
     b.close()
+    if bst:
+        bst.close()
     for s in sims:
         s.close()
     return out, n
@@ -122,19 +128,22 @@ def test_batch_equals_alone_bit_for_bit(precision):
     """The lockstep batch (one launch per phase over all members' tiles)
     gives every member exactly what sim_advance gives it alone: the same
     codes, Newton and FGMRES counts and states, bit for bit, over two
-    timesteps (the second reuses the AMG hierarchy); a batch of one gives
-    the same too."""
+    timesteps (the second reuses the AMG hierarchy), with its Arnoldi steps
+    replayed from CUDA graphs (its own stream) or launched directly (the
+    legacy default stream); a batch of one gives the same too."""
     members = [di.ensemble_member(r) for r in (0, 7, 14, 21, 28, 3, 10, 17)]
     opts = gpu().options("report", precision=precision, cluster_rows=-1)
     alone = _alone_run(members, opts, 2)
     mix, launches = _batch_run(members, opts, 2)
+    direct, _ = _batch_run(members, opts, 2, owned=False)
     single, _ = _batch_run(members[3:4], opts, 2)
     for t in range(2):
-        for k, (a, m) in enumerate(zip(alone[t], mix[t])):
-            assert a[0] == m[0] == 0, (t, k)
-            assert a[1:3] == m[1:3], (t, k, a[1:3], m[1:3])
-            for x, y in zip(a[3], m[3]):
+        for k, (a, m, d) in enumerate(zip(alone[t], mix[t], direct[t])):
+            assert a[0] == m[0] == d[0] == 0, (t, k)
+            assert a[1:3] == m[1:3] == d[1:3], (t, k, a[1:3], m[1:3])
+            for x, y, z in zip(a[3], m[3], d[3]):
                 np.testing.assert_array_equal(x, y)
+                np.testing.assert_array_equal(x, z)
         for x, y in zip(single[t][0][3], mix[t][3][3]):
             np.testing.assert_array_equal(x, y)
     assert launches > 0
