@@ -13,6 +13,7 @@
 #include <cstdlib>
 
 #include "dp_internal.h"
+#include "dp_tma.cuh"
 
 namespace dp {
 
@@ -84,29 +85,59 @@ int scan_i32(Sim *s, const int *in, int *out, int n, int *total) {
 
 // ---------------------------------------------------------------- colouring
 // Greedy first-fit colouring in natural row order: row i takes the smallest
-// colour unused by its neighbours of smaller index.  Evaluated in rounds: a
-// row is coloured once all its lower-index neighbours are; the result is the
-// same function of the pattern whatever the timing of the rounds.
+// colour unused by its neighbours of smaller index.  One launch: warps take
+// tickets of 32 rows in row order (an atomic counter), so every row a lane
+// waits for (a neighbour of smaller index) belongs to a ticket taken
+// before, by a warp that is running or done; the lane waits (bounded) until
+// those neighbours are coloured, then takes the smallest colour they leave
+// free.  The lowest uncoloured row can always proceed, so the launch
+// finishes, and the colours do not depend on the timing (first fit in row
+// order is one function of the pattern).  A colour is written once, as its
+// own flag (a volatile int store).  The launch is cooperative (its CTAs
+// resident together).  A wait that gives up sets err[0] and colours its row
+// 0 so that no row waits on it.
 constexpr int kMaxColours = 256;
 
-__global__ void k_colour_round(int n, const int *rowptr, const int *col, int *colour,
-                               int *pending, int *overflow) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void __launch_bounds__(kBlock) k_colour_tickets(int n, const int *__restrict__ rowptr,
+                                                          const int *__restrict__ col,
+                                                          int *colour, int *ticket,
+                                                          int *overflow, int *err) {
   volatile int *vc = colour;
-  if (vc[i] >= 0) return;
-  unsigned long long used[kMaxColours / 64] = {0, 0, 0, 0};
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-    int j = col[e];
-    if (j >= i) continue;
-    int c = vc[j];
-    if (c < 0) { atomicAdd(pending, 1); return; }
-    if (c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
+  volatile int *verr = err;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ticket, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    int i = base + lane;
+    if (i < n) {
+      unsigned long long used[kMaxColours / 64] = {0, 0, 0, 0};
+      bool ok = true;
+      for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1 && ok; ++e) {
+        int j = __ldg(col + e);
+        if (j >= i) continue;
+        int c = vc[j];
+        if (c < 0) {
+          uint64_t t0 = global_ns();
+          while ((c = vc[j]) < 0) {
+            if (*verr || global_ns() - t0 > kWaitNs) {
+              atomicExch(err, 1);
+              ok = false;
+              break;
+            }
+          }
+        }
+        if (ok && c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
+      }
+      int c = 0;
+      if (ok) {
+        while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
+        if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
+      }
+      vc[i] = c;
+    }
   }
-  int c = 0;
-  while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
-  if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
-  vc[i] = c;
 }
 
 __global__ void k_fill_i32(int *a, int n, int v) {
@@ -119,17 +150,44 @@ __global__ void k_max_i32(const int *a, int n, int *out) {
   if (i < n) atomicMax(out, a[i]);
 }
 
+// the cooperative launch of k_colour_tickets: its CTAs resident together
+static int colour_tickets(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
+  static const int slots = []() {
+    int dev = 0, nsm = 0, k = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_tickets, kBlock, 0);
+    return std::max(k, 1) * std::max(nsm, 1);
+  }();
+  int grid = std::max(1, std::min(slots, nblk(n, 8 * kBlock)));   // a ticket of 32 rows a warp
+  if (s->alloc_failed) return DP_ENOMEM;
+  LaunchScope ls(s, "k_colour_tickets");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.stream = s->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_tickets, n, rowptr, col, colour, s->counter + 2,
+                                s->counter + 1, s->counter + 3));
+  return DP_OK;
+}
+
 int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour, int *ncolour) {
   DP_LAUNCH(s, k_fill_i32, nblk(n), kBlock, 0, colour, n, -1);
-  int *dflag = s->counter + 1;  // overflow flag
-  DP_CUDA(s, cudaMemsetAsync(dflag, 0, 4, s->stream));
-  for (int round = 0; round < 1 << 20; ++round) {
-    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 4, s->stream));
-    DP_LAUNCH(s, k_colour_round, nblk(n), kBlock, 0, n, rowptr, col, colour, s->counter, dflag);
-    DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 8, cudaMemcpyDeviceToHost, s->stream));
+  if (n > 0) {
+    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 16, s->stream));   // ticket, overflow, err
+    DP_TRY(colour_tickets(s, n, rowptr, col, colour));
+    DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 16, cudaMemcpyDeviceToHost, s->stream));
     DP_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (s->h_counter[3]) {
+      s->fail(DP_ETIMEOUT, "greedy colouring: a bounded device-side wait gave up");
+      return DP_ETIMEOUT;
+    }
     if (s->h_counter[1]) { s->fail(DP_EINVAL, "greedy colouring needs more than 256 colours"); return DP_EINVAL; }
-    if (s->h_counter[0] == 0) break;
   }
   DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 4, s->stream));
   DP_LAUNCH(s, k_max_i32, nblk(n), kBlock, 0, colour, n, s->counter);
@@ -139,40 +197,77 @@ int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour,
   return DP_OK;
 }
 
-__global__ void k_eq_flag(const int *a, int n, int v, int *flag) {
+// Rows sorted by (colour, index), a stable counting sort over the colours:
+// per block of kBlock rows the count of each colour (colour-major array
+// cnt[c * nb + block]); one exclusive scan of those counts gives every
+// (colour, block) its first position; within a block a row's place among
+// its colour's rows of smaller index comes from the warps' match masks and
+// the earlier warps' counts.
+__global__ void __launch_bounds__(kBlock) k_colour_count(const int *__restrict__ colour, int n,
+                                                        int ncolour, int nb, int *__restrict__ cnt) {
+  __shared__ int hist[kMaxColours];
+  for (int c = threadIdx.x; c < ncolour; c += blockDim.x) hist[c] = 0;
+  __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) flag[i] = a[i] == v;
+  if (i < n) atomicAdd(&hist[colour[i]], 1);
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncolour; c += blockDim.x)
+    cnt[(size_t)c * nb + blockIdx.x] = hist[c];
 }
 
-__global__ void k_scatter_colour(const int *colour, int n, int c, const int *pos, int base,
-                                 int *clist, int *iperm) {
+__global__ void __launch_bounds__(kBlock) k_colour_place(const int *__restrict__ colour, int n,
+                                                        int ncolour, int nb,
+                                                        const int *__restrict__ off,
+                                                        int *__restrict__ clist,
+                                                        int *__restrict__ iperm) {
+  constexpr int kW = kBlock / 32;
+  __shared__ int wcnt[kW][kMaxColours];
+  for (int k = threadIdx.x; k < kW * kMaxColours; k += blockDim.x) (&wcnt[0][0])[k] = 0;
+  __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || colour[i] != c) return;
-  int p = base + pos[i];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  bool in = i < n;
+  int c = in ? colour[i] : -1;
+  unsigned same = __match_any_sync(0xffffffffu, c);
+  int rank = __popc(same & ((1u << lane) - 1u));
+  if (in && rank == 0) wcnt[w][c] = __popc(same);
+  __syncthreads();
+  if (!in) return;
+  int p = off[(size_t)c * nb + blockIdx.x] + rank;
+  for (int v = 0; v < w; ++v) p += wcnt[v][c];
   clist[p] = i;
   if (iperm) iperm[i] = p;
+}
+
+__global__ void k_colour_starts(const int *__restrict__ off, int nb, int ncolour, int n,
+                                int *__restrict__ out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncolour) out[c] = off[(size_t)c * nb];
+  if (c == ncolour) out[c] = n;
 }
 
 // Rows sorted by (colour, index): clist, the colour starts, and optionally
 // the inverse map (row -> position).
 int colour_lists(Sim *s, int n, const int *colour, int ncolour, int *clist,
                  std::vector<int> &cstart, int *iperm) {
-  int *flag = (int *)dalloc(s, (size_t)n * 4), *pos = (int *)dalloc(s, ((size_t)n + 1) * 4);
-  if (!flag || !pos) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   cstart.assign(ncolour + 1, 0);
-  int base = 0;
-  for (int c = 0; c < ncolour; ++c) {
-    cstart[c] = base;
-    DP_LAUNCH(s, k_eq_flag, nblk(n), kBlock, 0, colour, n, c, flag);
-    int cnt = 0;
-    DP_TRY(scan_i32(s, flag, pos, n, &cnt));
-    DP_LAUNCH(s, k_scatter_colour, nblk(n), kBlock, 0, colour, n, c, pos, base, clist, iperm);
-    base += cnt;
-  }
-  cstart[ncolour] = base;
-  DP_CUDA(s, cudaGetLastError());
-  dfree(s, flag);
-  dfree(s, pos);
+  if (n == 0 || ncolour == 0) return DP_OK;
+  int nb = nblk(n);
+  long long m = (long long)ncolour * nb;
+  int *cnt = (int *)dalloc(s, (size_t)m * 4), *off = (int *)dalloc(s, ((size_t)m + 1) * 4);
+  int *st = (int *)dalloc(s, ((size_t)ncolour + 1) * 4);
+  if (!cnt || !off || !st) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  DP_LAUNCH(s, k_colour_count, nb, kBlock, 0, colour, n, ncolour, nb, cnt);
+  int total = 0;
+  DP_TRY(scan_i32(s, cnt, off, (int)m, &total));
+  DP_LAUNCH(s, k_colour_place, nb, kBlock, 0, colour, n, ncolour, nb, off, clist, iperm);
+  DP_LAUNCH(s, k_colour_starts, nblk(ncolour + 1), kBlock, 0, off, nb, ncolour, n, st);
+  DP_CUDA(s, cudaMemcpyAsync(cstart.data(), st, ((size_t)ncolour + 1) * 4, cudaMemcpyDeviceToHost,
+                             s->stream));
+  DP_CUDA(s, cudaStreamSynchronize(s->stream));
+  dfree(s, st);
+  dfree(s, off);
+  dfree(s, cnt);
   return DP_OK;
 }
 

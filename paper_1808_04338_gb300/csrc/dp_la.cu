@@ -464,10 +464,17 @@ __global__ void k_lu_lens(int n, const int *lu_rowptr, const int *lu_dpos, int *
 __global__ void k_colour_maxlen(int n, const int *cstart_dev, int ncolour, const int *rowptr,
                                 int *out) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int c = 0;
-  while (c + 1 < ncolour && r >= cstart_dev[c + 1]) ++c;
-  atomicMax(out + c, rowptr[r + 1] - rowptr[r]);
+  int c = -1, len = 0;
+  if (r < n) {
+    c = 0;
+    while (c + 1 < ncolour && r >= cstart_dev[c + 1]) ++c;
+    len = rowptr[r + 1] - rowptr[r];
+  }
+  // one atomic per colour present in the warp (rows of a colour are
+  // contiguous, so a warp spans one or two colours)
+  unsigned same = __match_any_sync(0xffffffffu, c);
+  int m = __reduce_max_sync(same, len);
+  if (c >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicMax(out + c, m);
 }
 
 
