@@ -85,59 +85,49 @@ int scan_i32(Sim *s, const int *in, int *out, int n, int *total) {
 
 // ---------------------------------------------------------------- colouring
 // Greedy first-fit colouring in natural row order: row i takes the smallest
-// colour unused by its neighbours of smaller index.  One launch: warps take
-// tickets of 32 rows in row order (an atomic counter), so every row a lane
-// waits for (a neighbour of smaller index) belongs to a ticket taken
-// before, by a warp that is running or done; the lane waits (bounded) until
-// those neighbours are coloured, then takes the smallest colour they leave
-// free.  The lowest uncoloured row can always proceed, so the launch
-// finishes, and the colours do not depend on the timing (first fit in row
-// order is one function of the pattern).  A colour is written once, as its
-// own flag (a volatile int store).  The launch is cooperative (its CTAs
-// resident together).  A wait that gives up sets err[0] and colours its row
-// 0 so that no row waits on it.
+// colour unused by its neighbours of smaller index.  Evaluated in rounds: a
+// row is coloured once all its lower-index neighbours are (colours written
+// earlier in the same round count), so the result is the same function of
+// the pattern whatever the timing.  All rounds run in one cooperative
+// launch, separated by grid barriers (bounded waits; a failure sets
+// err[0]): each round every thread tries the uncoloured rows of its
+// grid-stride set and counts those still waiting in pend[round % 3]; after
+// the barrier every thread reads that count, and the launch ends when it
+// is 0.  Three rotating counts: the one reset during round r was last read
+// after barrier r - 2.
 constexpr int kMaxColours = 256;
 
-__global__ void __launch_bounds__(kBlock) k_colour_tickets(int n, const int *__restrict__ rowptr,
-                                                          const int *__restrict__ col,
-                                                          int *colour, int *ticket,
-                                                          int *overflow, int *err) {
+__global__ void __launch_bounds__(kBlock) k_colour_rounds(int n, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         int *colour, int *pend, int *overflow,
+                                                         unsigned *bar, int *err) {
   volatile int *vc = colour;
-  volatile int *verr = err;
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(ticket, 32);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n) break;
-    int i = base + lane;
-    if (i < n) {
+  const int G = (int)gridDim.x;
+  for (int round = 0; round < (1 << 20); ++round) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) pend[(round + 1) % 3] = 0;
+    int waiting = 0;
+    for (int i = (int)blockIdx.x * kBlock + threadIdx.x; i < n; i += G * kBlock) {
+      if (vc[i] >= 0) continue;
       unsigned long long used[kMaxColours / 64] = {0, 0, 0, 0};
-      bool ok = true;
-      for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1 && ok; ++e) {
+      bool ready = true;
+      for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) {
         int j = __ldg(col + e);
         if (j >= i) continue;
         int c = vc[j];
-        if (c < 0) {
-          uint64_t t0 = global_ns();
-          while ((c = vc[j]) < 0) {
-            if (*verr || global_ns() - t0 > kWaitNs) {
-              atomicExch(err, 1);
-              ok = false;
-              break;
-            }
-          }
-        }
-        if (ok && c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
+        if (c < 0) { ready = false; break; }
+        if (c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
       }
+      if (!ready) { ++waiting; continue; }
       int c = 0;
-      if (ok) {
-        while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
-        if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
-      }
+      while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
+      if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
       vc[i] = c;
     }
+    if (waiting) atomicAdd(pend + round % 3, waiting);
+    if (!grid_sync_all(bar, (unsigned)(round + 1) * (unsigned)G, err)) return;
+    if (*(volatile int *)(pend + round % 3) == 0) break;
   }
+  grid_exit(bar);
 }
 
 __global__ void k_fill_i32(int *a, int n, int v) {
@@ -150,18 +140,18 @@ __global__ void k_max_i32(const int *a, int n, int *out) {
   if (i < n) atomicMax(out, a[i]);
 }
 
-// the cooperative launch of k_colour_tickets: its CTAs resident together
-static int colour_tickets(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
+// the cooperative launch of k_colour_rounds: its CTAs resident together
+static int colour_rounds(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
   static const int slots = []() {
     int dev = 0, nsm = 0, k = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_tickets, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_rounds, kBlock, 0);
     return std::max(k, 1) * std::max(nsm, 1);
   }();
-  int grid = std::max(1, std::min(slots, nblk(n, 8 * kBlock)));   // a ticket of 32 rows a warp
+  int grid = std::max(1, std::min(slots, nblk(n)));
   if (s->alloc_failed) return DP_ENOMEM;
-  LaunchScope ls(s, "k_colour_tickets");
+  LaunchScope ls(s, "k_colour_rounds");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBlock);
@@ -171,16 +161,17 @@ static int colour_tickets(Sim *s, int n, const int *rowptr, const int *col, int 
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_tickets, n, rowptr, col, colour, s->counter + 2,
-                                s->counter + 1, s->counter + 3));
+  // counter: [1] overflow, [3] err, [4..6] the rotating counts; dev_err + 4: the barrier's
+  DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_rounds, n, rowptr, col, colour, s->counter + 4,
+                                s->counter + 1, (unsigned *)(s->dev_err + 4), s->counter + 3));
   return DP_OK;
 }
 
 int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour, int *ncolour) {
   DP_LAUNCH(s, k_fill_i32, nblk(n), kBlock, 0, colour, n, -1);
   if (n > 0) {
-    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 16, s->stream));   // ticket, overflow, err
-    DP_TRY(colour_tickets(s, n, rowptr, col, colour));
+    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 32, s->stream));   // overflow, err, counts
+    DP_TRY(colour_rounds(s, n, rowptr, col, colour));
     DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 16, cudaMemcpyDeviceToHost, s->stream));
     DP_CUDA(s, cudaStreamSynchronize(s->stream));
     if (s->h_counter[3]) {

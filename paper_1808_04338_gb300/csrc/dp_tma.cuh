@@ -76,4 +76,46 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
       : "memory");
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier of all threads of a cooperative launch: the k-th barrier of
+// the launch is passed when cnt[0] reaches k * gridDim.x arrivals (target);
+// false, for every thread of the CTA, when the wait gave up or *err is set.
+// The launch's last CTA resets the count (grid_exit).
+__device__ __forceinline__ bool grid_sync_all(unsigned *cnt, unsigned target, int *err) {
+  __shared__ int gave_up;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gave_up = 0;
+    __threadfence();
+    atomicAdd(cnt, 1u);
+    uint64_t t0 = global_ns();
+    while (ld_acquire_u32(cnt) < target) {
+      if (*(volatile int *)err || global_ns() - t0 > kWaitNs) {
+        atomicExch(err, 1);
+        gave_up = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return !gave_up;
+}
+
+// called by every CTA when it leaves: the last one resets cnt[0] and cnt[1]
+__device__ __forceinline__ void grid_exit(unsigned *cnt) {
+  __syncthreads();
+  if (threadIdx.x == 0 && atomicAdd(cnt + 1, 1u) == gridDim.x - 1) {
+    cnt[0] = 0;
+    cnt[1] = 0;
+    __threadfence();
+  }
+}
+
 }  // namespace dp
