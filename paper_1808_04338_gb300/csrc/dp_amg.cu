@@ -103,11 +103,18 @@ __global__ void __launch_bounds__(kBlock) k_colour_rounds(int n, const int *__re
                                                          unsigned *bar, int *err) {
   volatile int *vc = colour;
   const int G = (int)gridDim.x;
+  // the thread's rows i0, i0 + stride, ...: bit k of `done` says its k-th
+  // row is coloured (rows past the 64th are looked up in memory)
+  const int i0 = (int)blockIdx.x * kBlock + threadIdx.x, stride = G * kBlock;
+  unsigned long long done = 0;
   for (int round = 0; round < (1 << 20); ++round) {
     if (blockIdx.x == 0 && threadIdx.x == 0) pend[(round + 1) % 3] = 0;
     int waiting = 0;
-    for (int i = (int)blockIdx.x * kBlock + threadIdx.x; i < n; i += G * kBlock) {
-      if (vc[i] >= 0) continue;
+    int k = 0;
+    for (int i = i0; i < n; i += stride, ++k) {
+      unsigned long long bit = k < 64 ? 1ull << k : 0ull;
+      if (done & bit) continue;
+      if (vc[i] >= 0) { done |= bit; continue; }
       unsigned long long used[kMaxColours / 64] = {0, 0, 0, 0};
       bool ready = true;
       for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) {
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(kBlock) k_colour_rounds(int n, const int *__re
       while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
       if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
       vc[i] = c;
+      done |= bit;
     }
     if (waiting) atomicAdd(pend + round % 3, waiting);
     if (!grid_sync_all(bar, (unsigned)(round + 1) * (unsigned)G, err)) return;
@@ -149,7 +157,9 @@ static int colour_rounds(Sim *s, int n, const int *rowptr, const int *col, int *
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_rounds, kBlock, 0);
     return std::max(k, 1) * std::max(nsm, 1);
   }();
-  int grid = std::max(1, std::min(slots, nblk(n)));
+  // few CTAs (two an SM): each barrier costs an atomic per CTA
+  int nsm2 = std::max(1, slots / 4);
+  int grid = std::max(1, std::min({slots, nsm2, nblk(n)}));
   if (s->alloc_failed) return DP_ENOMEM;
   LaunchScope ls(s, "k_colour_rounds");
   cudaLaunchConfig_t cfg = {};
@@ -549,34 +559,87 @@ __global__ void k_spgemm_ub(int n, const int *lrp, const int *lcol, const int *r
   ub[r] = s;
 }
 
-__global__ void k_spgemm_expand(int n, const int *lrp, const int *lcol, const int *rrp,
-                                const int *rcol, const int *off, int *scratch, int *cnt) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int base = off[r], m = 0;
-  for (int e = lrp[r]; e < lrp[r + 1]; ++e) {
-    int k = lcol[e];
-    for (int q = rrp[k]; q < rrp[k + 1]; ++q) scratch[base + m++] = rcol[q];
+// Symbolic product, a warp per output row: the row's products (at most
+// kExpCap) are gathered into shared memory in the order of the entries of L
+// and R, sorted there (bitonic) and deduplicated with ballots; a longer row
+// is expanded, heap-sorted and deduplicated in its own scratch by the
+// warp's first lane.  Either way the row's scratch starts with its sorted
+// distinct columns, and cnt[r] is their count.
+constexpr int kExpWarps = 4, kExpCap = 1024;
+__global__ void __launch_bounds__(32 * kExpWarps) k_spgemm_expand_w(int n, const int *lrp,
+                                                                    const int *lcol,
+                                                                    const int *rrp,
+                                                                    const int *rcol,
+                                                                    const int *off, int *scratch,
+                                                                    int *cnt) {
+  __shared__ int buf[kExpWarps][kExpCap];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int r = blockIdx.x * kExpWarps + w;
+  if (r >= n) return;   // whole warps
+  int base = off[r], m = off[r + 1] - base;
+  if (m > kExpCap) {
+    if (lane == 0) {
+      int t = 0;
+      for (int e = lrp[r]; e < lrp[r + 1]; ++e) {
+        int k = lcol[e];
+        for (int q = rrp[k]; q < rrp[k + 1]; ++q) scratch[base + t++] = rcol[q];
+      }
+      heap_sort2(scratch + base, nullptr, m);
+      int u = 0;
+      for (int i = 0; i < m; ++i)
+        if (u == 0 || scratch[base + i] != scratch[base + u - 1]) scratch[base + u++] = scratch[base + i];
+      cnt[r] = u;
+    }
+    return;
   }
-  heap_sort2(scratch + base, nullptr, m);
+  int *b = buf[w];
+  int t = 0;
+  for (int e = __ldg(lrp + r), e1 = __ldg(lrp + r + 1); e < e1; ++e) {
+    int k = __ldg(lcol + e), q0 = __ldg(rrp + k), q1 = __ldg(rrp + k + 1);
+    for (int q = q0 + lane; q < q1; q += 32) b[t + q - q0] = __ldg(rcol + q);
+    t += q1 - q0;
+  }
+  int p2 = 1;
+  while (p2 < m) p2 <<= 1;
+  for (int i = m + lane; i < p2; i += 32) b[i] = 0x7fffffff;
+  __syncwarp();
+  for (int size = 2; size <= p2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = lane; i < (p2 >> 1); i += 32) {
+        int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+        bool asc = (lo & size) == 0;
+        int a = b[lo], c = b[hi];
+        if ((a > c) == asc) { b[lo] = c; b[hi] = a; }
+      }
+      __syncwarp();
+    }
   int u = 0;
-  for (int t = 0; t < m; ++t)
-    if (u == 0 || scratch[base + t] != scratch[base + u - 1]) scratch[base + u++] = scratch[base + t];
-  cnt[r] = u;
+  for (int i0 = 0; i0 < m; i0 += 32) {
+    int i = i0 + lane;
+    bool keep = i < m && (i == 0 || b[i] != b[i - 1]);
+    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) scratch[base + u + __popc(bal & ((1u << lane) - 1u))] = b[i];
+    u += __popc(bal);
+  }
+  if (lane == 0) cnt[r] = u;
 }
 
 // Positions of every product in the output: for row r, the products are
 // enumerated (entry (r, k) of L in increasing k, entry (k, c) of R in
-// increasing c) and pos[off[r] + t] is the index of C_rc for product t.
-__global__ void k_spgemm_positions(int n, const int *lrp, const int *lcol, const int *rrp,
-                                   const int *rcol, const int *off, const int *crp,
-                                   const int *ccol, int *pos) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+// increasing c) and pos[off[r] + t] is the index of C_rc for product t.  A
+// warp per row: the lanes take the products of each entry (r, k) together.
+__global__ void __launch_bounds__(kBlock) k_spgemm_positions_w(int n, const int *lrp,
+                                                              const int *lcol, const int *rrp,
+                                                              const int *rcol, const int *off,
+                                                              const int *crp, const int *ccol,
+                                                              int *pos) {
+  int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (r >= n) return;   // whole warps
   int c0 = crp[r], c1 = crp[r + 1], t = off[r];
-  for (int e = lrp[r]; e < lrp[r + 1]; ++e) {
-    int k = lcol[e];
-    for (int q = rrp[k]; q < rrp[k + 1]; ++q) pos[t++] = find_sorted(ccol, c0, c1, rcol[q]);
+  for (int e = __ldg(lrp + r), e1 = __ldg(lrp + r + 1); e < e1; ++e) {
+    int k = __ldg(lcol + e), q0 = __ldg(rrp + k), q1 = __ldg(rrp + k + 1);
+    for (int q = q0 + lane; q < q1; q += 32) pos[t + q - q0] = find_sorted(ccol, c0, c1, __ldg(rcol + q));
+    t += q1 - q0;
   }
 }
 
@@ -645,7 +708,8 @@ static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const
   prod->G = lanes_for(n > 0 ? (double)tot / n : 0.0);
   int *scratch = (int *)dalloc(s, (size_t)std::max(tot, 1) * 4);
   if (!scratch) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
-  DP_LAUNCH(s, k_spgemm_expand, nblk(n, 64), 64, 0, n, lrp, lcol, rrp, rcol, off, scratch, ub);
+  DP_LAUNCH(s, k_spgemm_expand_w, nblk(n, kExpWarps), 32 * kExpWarps, 0, n, lrp, lcol, rrp, rcol,
+            off, scratch, ub);
   int nnz = 0;
   DP_TRY(scan_i32(s, ub, crp, n, &nnz));
   int *ccol = (int *)dalloc(s, (size_t)std::max(nnz, 1) * 4);
@@ -657,8 +721,8 @@ static int spgemm_symbolic(Sim *s, int n, const int *lrp, const int *lcol, const
   prod->off = off;
   prod->pos = (int *)dalloc(s, (size_t)std::max(tot, 1) * 4);
   if (!prod->pos) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
-  DP_LAUNCH(s, k_spgemm_positions, nblk(n), kBlock, 0, n, lrp, lcol, rrp, rcol, off, crp, ccol,
-            prod->pos);
+  DP_LAUNCH(s, k_spgemm_positions_w, nblk(32LL * n), kBlock, 0, n, lrp, lcol, rrp, rcol, off, crp,
+            ccol, prod->pos);
   *crp_out = crp;
   *ccol_out = ccol;
   *nnz_out = nnz;
