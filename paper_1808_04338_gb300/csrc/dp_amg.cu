@@ -85,57 +85,64 @@ int scan_i32(Sim *s, const int *in, int *out, int n, int *total) {
 
 // ---------------------------------------------------------------- colouring
 // Greedy first-fit colouring in natural row order: row i takes the smallest
-// colour unused by its neighbours of smaller index.  Evaluated in rounds: a
-// row is coloured once all its lower-index neighbours are (colours written
-// earlier in the same round count), so the result is the same function of
-// the pattern whatever the timing.  All rounds run in one cooperative
-// launch, separated by grid barriers (bounded waits; a failure sets
-// err[0]): each round every thread tries the uncoloured rows of its
-// grid-stride set and counts those still waiting in pend[round % 3]; after
-// the barrier every thread reads that count, and the launch ends when it
-// is 0.  Three rotating counts: the one reset during round r was last read
-// after barrier r - 2.
+// colour unused by its neighbours of smaller index.  One cooperative launch
+// (its CTAs resident together): warps take tickets of 32 consecutive rows in
+// row order (an atomic counter) and colour a ticket's rows one after the
+// other, the lanes sharing each row's neighbours and meeting in OR
+// reductions of the used colours.  A row waits (bounded) only for
+// neighbours of smaller index, which are earlier rows of its own ticket
+// (already done) or rows of tickets taken before by warps that are running
+// or done; so the lowest uncoloured row can always proceed and the launch
+// finishes, and the colours do not depend on the timing (first fit in row
+// order is one function of the pattern).  A colour is written once, as its
+// own flag (a volatile int store).  A wait that gives up sets err[0] and
+// takes colour 0 for the neighbour, so that no row waits on it.
 constexpr int kMaxColours = 256;
 
-__global__ void __launch_bounds__(kBlock) k_colour_rounds(int n, const int *__restrict__ rowptr,
-                                                         const int *__restrict__ col,
-                                                         int *colour, int *pend, int *overflow,
-                                                         unsigned *bar, int *err) {
+__global__ void __launch_bounds__(kBlock) k_colour_warps(int n, const int *__restrict__ rowptr,
+                                                        const int *__restrict__ col, int *colour,
+                                                        int *ticket, int *overflow, int *err) {
   volatile int *vc = colour;
-  const int G = (int)gridDim.x;
-  // the thread's rows i0, i0 + stride, ...: bit k of `done` says its k-th
-  // row is coloured (rows past the 64th are looked up in memory)
-  const int i0 = (int)blockIdx.x * kBlock + threadIdx.x, stride = G * kBlock;
-  unsigned long long done = 0;
-  for (int round = 0; round < (1 << 20); ++round) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) pend[(round + 1) % 3] = 0;
-    int waiting = 0;
-    int k = 0;
-    for (int i = i0; i < n; i += stride, ++k) {
-      unsigned long long bit = k < 64 ? 1ull << k : 0ull;
-      if (done & bit) continue;
-      if (vc[i] >= 0) { done |= bit; continue; }
-      unsigned long long used[kMaxColours / 64] = {0, 0, 0, 0};
-      bool ready = true;
-      for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) {
+  volatile int *verr = err;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ticket, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    int rend = min(base + 32, n);
+    for (int r = base; r < rend; ++r) {
+      unsigned m[kMaxColours / 32] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int e = __ldg(rowptr + r) + lane, e1 = __ldg(rowptr + r + 1); e < e1; e += 32) {
         int j = __ldg(col + e);
-        if (j >= i) continue;
+        if (j >= r) continue;
         int c = vc[j];
-        if (c < 0) { ready = false; break; }
-        if (c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
+        if (c < 0) {
+          uint64_t t0 = global_ns();
+          while ((c = vc[j]) < 0) {
+            if (*verr || global_ns() - t0 > kWaitNs) {
+              atomicExch(err, 1);
+              c = 0;
+              break;
+            }
+          }
+        }
+        if (c < kMaxColours) m[c >> 5] |= 1u << (c & 31);
       }
-      if (!ready) { ++waiting; continue; }
-      int c = 0;
-      while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
-      if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
-      vc[i] = c;
-      done |= bit;
+      int c = kMaxColours;
+#pragma unroll
+      for (int w = kMaxColours / 32 - 1; w >= 0; --w) {
+        unsigned used = __reduce_or_sync(0xffffffffu, m[w]);
+        if (~used) c = 32 * w + __ffs(~used) - 1;   // the lowest free colour of the lowest such word
+      }
+      if (c >= kMaxColours) {
+        if (lane == 0) *overflow = 1;
+        c = kMaxColours - 1;
+      }
+      if (lane == 0) vc[r] = c;
+      __syncwarp();
     }
-    if (waiting) atomicAdd(pend + round % 3, waiting);
-    if (!grid_sync_all(bar, (unsigned)(round + 1) * (unsigned)G, err)) return;
-    if (*(volatile int *)(pend + round % 3) == 0) break;
   }
-  grid_exit(bar);
 }
 
 __global__ void k_fill_i32(int *a, int n, int v) {
@@ -148,20 +155,18 @@ __global__ void k_max_i32(const int *a, int n, int *out) {
   if (i < n) atomicMax(out, a[i]);
 }
 
-// the cooperative launch of k_colour_rounds: its CTAs resident together
-static int colour_rounds(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
+// the cooperative launch of k_colour_warps: its CTAs resident together
+static int colour_warps(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
   static const int slots = []() {
     int dev = 0, nsm = 0, k = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_rounds, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_warps, kBlock, 0);
     return std::max(k, 1) * std::max(nsm, 1);
   }();
-  // few CTAs (two an SM): each barrier costs an atomic per CTA
-  int nsm2 = std::max(1, slots / 4);
-  int grid = std::max(1, std::min({slots, nsm2, nblk(n)}));
+  int grid = std::max(1, std::min(slots, nblk(n, 8 * 32)));   // a 32-row ticket a warp
   if (s->alloc_failed) return DP_ENOMEM;
-  LaunchScope ls(s, "k_colour_rounds");
+  LaunchScope ls(s, "k_colour_warps");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBlock);
@@ -171,17 +176,17 @@ static int colour_rounds(Sim *s, int n, const int *rowptr, const int *col, int *
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  // counter: [1] overflow, [3] err, [4..6] the rotating counts; dev_err + 4: the barrier's
-  DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_rounds, n, rowptr, col, colour, s->counter + 4,
-                                s->counter + 1, (unsigned *)(s->dev_err + 4), s->counter + 3));
+  // counter: [1] overflow, [2] the ticket, [3] err
+  DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_warps, n, rowptr, col, colour, s->counter + 2,
+                                s->counter + 1, s->counter + 3));
   return DP_OK;
 }
 
 int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour, int *ncolour) {
   DP_LAUNCH(s, k_fill_i32, nblk(n), kBlock, 0, colour, n, -1);
   if (n > 0) {
-    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 32, s->stream));   // overflow, err, counts
-    DP_TRY(colour_rounds(s, n, rowptr, col, colour));
+    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 16, s->stream));   // overflow, ticket, err
+    DP_TRY(colour_warps(s, n, rowptr, col, colour));
     DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 16, cudaMemcpyDeviceToHost, s->stream));
     DP_CUDA(s, cudaStreamSynchronize(s->stream));
     if (s->h_counter[3]) {
