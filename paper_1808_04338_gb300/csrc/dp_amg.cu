@@ -85,64 +85,61 @@ int scan_i32(Sim *s, const int *in, int *out, int n, int *total) {
 
 // ---------------------------------------------------------------- colouring
 // Greedy first-fit colouring in natural row order: row i takes the smallest
-// colour unused by its neighbours of smaller index.  One cooperative launch
-// (its CTAs resident together): warps take tickets of 32 consecutive rows in
-// row order (an atomic counter) and colour a ticket's rows one after the
-// other, the lanes sharing each row's neighbours and meeting in OR
-// reductions of the used colours.  A row waits (bounded) only for
-// neighbours of smaller index, which are earlier rows of its own ticket
-// (already done) or rows of tickets taken before by warps that are running
-// or done; so the lowest uncoloured row can always proceed and the launch
-// finishes, and the colours do not depend on the timing (first fit in row
-// order is one function of the pattern).  A colour is written once, as its
-// own flag (a volatile int store).  A wait that gives up sets err[0] and
-// takes colour 0 for the neighbour, so that no row waits on it.
+// colour unused by its neighbours of smaller index.  A row's colour depends
+// only on those neighbours, so the rows are coloured level by level of that
+// dependence (Kahn's order): level 0 the rows with no lower neighbour; a row
+// joins the next level when its last lower neighbour is coloured (its count
+// of uncoloured lower neighbours, indeg, drops to 0).  All levels run in one
+// cooperative launch, one bounded grid barrier after each (a failure sets
+// err[0]); the colours do not depend on the order inside a level.  The
+// pattern is symmetric: a row's higher neighbours are in its own row.
+// cnt[L % 3] holds the size of level L; the count reset during level L's
+// pass, cnt[(L + 2) % 3], was last read at the start of level L - 1.
 constexpr int kMaxColours = 256;
 
-__global__ void __launch_bounds__(kBlock) k_colour_warps(int n, const int *__restrict__ rowptr,
-                                                        const int *__restrict__ col, int *colour,
-                                                        int *ticket, int *overflow, int *err) {
-  volatile int *vc = colour;
-  volatile int *verr = err;
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(ticket, 32);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n) break;
-    int rend = min(base + 32, n);
-    for (int r = base; r < rend; ++r) {
-      unsigned m[kMaxColours / 32] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int e = __ldg(rowptr + r) + lane, e1 = __ldg(rowptr + r + 1); e < e1; e += 32) {
-        int j = __ldg(col + e);
-        if (j >= r) continue;
-        int c = vc[j];
-        if (c < 0) {
-          uint64_t t0 = global_ns();
-          while ((c = vc[j]) < 0) {
-            if (*verr || global_ns() - t0 > kWaitNs) {
-              atomicExch(err, 1);
-              c = 0;
-              break;
-            }
-          }
-        }
-        if (c < kMaxColours) m[c >> 5] |= 1u << (c & 31);
-      }
-      int c = kMaxColours;
-#pragma unroll
-      for (int w = kMaxColours / 32 - 1; w >= 0; --w) {
-        unsigned used = __reduce_or_sync(0xffffffffu, m[w]);
-        if (~used) c = 32 * w + __ffs(~used) - 1;   // the lowest free colour of the lowest such word
-      }
-      if (c >= kMaxColours) {
-        if (lane == 0) *overflow = 1;
-        c = kMaxColours - 1;
-      }
-      if (lane == 0) vc[r] = c;
-      __syncwarp();
-    }
+__global__ void __launch_bounds__(kBlock) k_colour_levels(int n, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col, int *colour,
+                                                         int *indeg, int *fa, int *fb, int *cnt,
+                                                         int *overflow, unsigned *bar, int *err) {
+  const int G = (int)gridDim.x, stride = G * kBlock;
+  const int t0 = (int)blockIdx.x * kBlock + threadIdx.x;
+  for (int i = t0; i < n; i += stride) {
+    int d = 0;
+    for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) d += __ldg(col + e) < i;
+    indeg[i] = d;
+    if (d == 0) fa[atomicAdd(cnt, 1)] = i;
   }
+  unsigned nbar = 1;
+  if (!grid_sync_all(bar, nbar * G, err)) return;
+  int *cur = fa, *nxt = fb;
+  for (int level = 0; level < n + 1; ++level) {
+    int size = *(volatile int *)(cnt + level % 3);
+    if (size == 0) break;
+    if (t0 == 0) cnt[(level + 2) % 3] = 0;
+    int *next_cnt = cnt + (level + 1) % 3;
+    for (int t = t0; t < size; t += stride) {
+      int i = __ldcg(cur + t);
+      int e0 = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1);
+      unsigned long long used[kMaxColours / 64] = {0, 0, 0, 0};
+      for (int e = e0; e < e1; ++e) {
+        int j = __ldg(col + e);
+        if (j >= i) continue;
+        int c = __ldcg(colour + j);
+        if (c >= 0 && c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
+      }
+      int c = 0;
+      while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
+      if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
+      colour[i] = c;
+      for (int e = e0; e < e1; ++e) {
+        int k = __ldg(col + e);
+        if (k > i && atomicSub(indeg + k, 1) == 1) nxt[atomicAdd(next_cnt, 1)] = k;
+      }
+    }
+    if (!grid_sync_all(bar, ++nbar * G, err)) return;
+    int *tmp = cur; cur = nxt; nxt = tmp;
+  }
+  grid_exit(bar);
 }
 
 __global__ void k_fill_i32(int *a, int n, int v) {
@@ -150,43 +147,52 @@ __global__ void k_fill_i32(int *a, int n, int v) {
   if (i < n) a[i] = v;
 }
 
-__global__ void k_max_i32(const int *a, int n, int *out) {
+// the largest colour (out[0]) and whether a row was left uncoloured (out[1])
+__global__ void k_colour_check(const int *a, int n, int *out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicMax(out, a[i]);
+  if (i >= n) return;
+  atomicMax(out, a[i]);
+  if (a[i] < 0) out[1] = 1;
 }
 
-// the cooperative launch of k_colour_warps: its CTAs resident together
-static int colour_warps(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
+// the cooperative launch of k_colour_levels: its CTAs resident together,
+// two an SM (each barrier costs an atomic per CTA)
+static int colour_levels(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
   static const int slots = []() {
     int dev = 0, nsm = 0, k = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_warps, kBlock, 0);
-    return std::max(k, 1) * std::max(nsm, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_levels, kBlock, 0);
+    return std::min(std::max(k, 1), 2) * std::max(nsm, 1);
   }();
-  int grid = std::max(1, std::min(slots, nblk(n, 8 * 32)));   // a 32-row ticket a warp
-  if (s->alloc_failed) return DP_ENOMEM;
-  LaunchScope ls(s, "k_colour_warps");
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kBlock);
-  cfg.stream = s->stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;
-  at[0].val.cooperative = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  // counter: [1] overflow, [2] the ticket, [3] err
-  DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_warps, n, rowptr, col, colour, s->counter + 2,
-                                s->counter + 1, s->counter + 3));
+  int grid = std::max(1, std::min(slots, nblk(n)));
+  int *work = (int *)dalloc(s, (size_t)n * 12);   // indeg, two levels' rows
+  if (!work) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
+  {
+    LaunchScope ls(s, "k_colour_levels");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = s->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // counter: [1] overflow, [3] err, [4..6] the level sizes; dev_err + 4: the barrier's counts
+    DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_levels, n, rowptr, col, colour, work, work + n,
+                                  work + 2 * (size_t)n, s->counter + 4, s->counter + 1,
+                                  (unsigned *)(s->dev_err + 4), s->counter + 3));
+  }
+  dfree(s, work);
   return DP_OK;
 }
 
 int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour, int *ncolour) {
   DP_LAUNCH(s, k_fill_i32, nblk(n), kBlock, 0, colour, n, -1);
   if (n > 0) {
-    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 16, s->stream));   // overflow, ticket, err
-    DP_TRY(colour_warps(s, n, rowptr, col, colour));
+    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 32, s->stream));   // overflow, err, level sizes
+    DP_TRY(colour_levels(s, n, rowptr, col, colour));
     DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 16, cudaMemcpyDeviceToHost, s->stream));
     DP_CUDA(s, cudaStreamSynchronize(s->stream));
     if (s->h_counter[3]) {
@@ -195,10 +201,14 @@ int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour,
     }
     if (s->h_counter[1]) { s->fail(DP_EINVAL, "greedy colouring needs more than 256 colours"); return DP_EINVAL; }
   }
-  DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 4, s->stream));
-  DP_LAUNCH(s, k_max_i32, nblk(n), kBlock, 0, colour, n, s->counter);
-  DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 4, cudaMemcpyDeviceToHost, s->stream));
+  DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 8, s->stream));
+  DP_LAUNCH(s, k_colour_check, nblk(n), kBlock, 0, colour, n, s->counter);
+  DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 8, cudaMemcpyDeviceToHost, s->stream));
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (n > 0 && s->h_counter[1]) {   // a lower neighbour whose row does not name the row
+    s->fail(DP_EINVAL, "greedy colouring needs a structurally symmetric pattern");
+    return DP_EINVAL;
+  }
   *ncolour = n > 0 ? s->h_counter[0] + 1 : 0;
   return DP_OK;
 }
