@@ -85,59 +85,47 @@ int scan_i32(Sim *s, const int *in, int *out, int n, int *total) {
 
 // ---------------------------------------------------------------- colouring
 // Greedy first-fit colouring in natural row order: row i takes the smallest
-// colour unused by its neighbours of smaller index.  A row's colour depends
-// only on those neighbours, so the rows are coloured level by level of that
-// dependence (Kahn's order): level 0 the rows with no lower neighbour; a row
-// joins the next level when its last lower neighbour is coloured (its count
-// of uncoloured lower neighbours, indeg, drops to 0).  All levels run in one
-// cooperative launch, one bounded grid barrier after each (a failure sets
-// err[0]); the colours do not depend on the order inside a level.  The
-// pattern is symmetric: a row's higher neighbours are in its own row.
-// cnt[L % 3] holds the size of level L; the count reset during level L's
-// pass, cnt[(L + 2) % 3], was last read at the start of level L - 1.
+// colour unused by its neighbours of smaller index.  Evaluated in rounds: a
+// row is coloured once all its lower-index neighbours are (colours written
+// earlier in the same round count), so the result is the same function of
+// the pattern whatever the timing.  All rounds run in one cooperative
+// launch, separated by grid barriers (bounded waits; a failure sets
+// err[0]): each round every thread tries the uncoloured rows of its
+// grid-stride set and counts those still waiting in pend[round % 3]; after
+// the barrier every thread reads that count, and the launch ends when it
+// is 0.  Three rotating counts: the one reset during round r was last read
+// after barrier r - 2.
 constexpr int kMaxColours = 256;
 
-__global__ void __launch_bounds__(kBlock) k_colour_levels(int n, const int *__restrict__ rowptr,
-                                                         const int *__restrict__ col, int *colour,
-                                                         int *indeg, int *fa, int *fb, int *cnt,
-                                                         int *overflow, unsigned *bar, int *err) {
-  const int G = (int)gridDim.x, stride = G * kBlock;
-  const int t0 = (int)blockIdx.x * kBlock + threadIdx.x;
-  for (int i = t0; i < n; i += stride) {
-    int d = 0;
-    for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) d += __ldg(col + e) < i;
-    indeg[i] = d;
-    if (d == 0) fa[atomicAdd(cnt, 1)] = i;
-  }
-  unsigned nbar = 1;
-  if (!grid_sync_all(bar, nbar * G, err)) return;
-  int *cur = fa, *nxt = fb;
-  for (int level = 0; level < n + 1; ++level) {
-    int size = *(volatile int *)(cnt + level % 3);
-    if (size == 0) break;
-    if (t0 == 0) cnt[(level + 2) % 3] = 0;
-    int *next_cnt = cnt + (level + 1) % 3;
-    for (int t = t0; t < size; t += stride) {
-      int i = __ldcg(cur + t);
-      int e0 = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1);
+__global__ void __launch_bounds__(kBlock) k_colour_rounds(int n, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         int *colour, int *pend, int *overflow,
+                                                         unsigned *bar, int *err) {
+  volatile int *vc = colour;
+  const int G = (int)gridDim.x;
+  for (int round = 0; round < (1 << 20); ++round) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) pend[(round + 1) % 3] = 0;
+    int waiting = 0;
+    for (int i = (int)blockIdx.x * kBlock + threadIdx.x; i < n; i += G * kBlock) {
+      if (vc[i] >= 0) continue;
       unsigned long long used[kMaxColours / 64] = {0, 0, 0, 0};
-      for (int e = e0; e < e1; ++e) {
+      bool ready = true;
+      for (int e = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1); e < e1; ++e) {
         int j = __ldg(col + e);
         if (j >= i) continue;
-        int c = __ldcg(colour + j);
-        if (c >= 0 && c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
+        int c = vc[j];
+        if (c < 0) { ready = false; break; }
+        if (c < kMaxColours) used[c >> 6] |= 1ull << (c & 63);
       }
+      if (!ready) { ++waiting; continue; }
       int c = 0;
       while (c < kMaxColours && (used[c >> 6] >> (c & 63)) & 1ull) ++c;
       if (c >= kMaxColours) { *overflow = 1; c = kMaxColours - 1; }
-      colour[i] = c;
-      for (int e = e0; e < e1; ++e) {
-        int k = __ldg(col + e);
-        if (k > i && atomicSub(indeg + k, 1) == 1) nxt[atomicAdd(next_cnt, 1)] = k;
-      }
+      vc[i] = c;
     }
-    if (!grid_sync_all(bar, ++nbar * G, err)) return;
-    int *tmp = cur; cur = nxt; nxt = tmp;
+    if (waiting) atomicAdd(pend + round % 3, waiting);
+    if (!grid_sync_all(bar, (unsigned)(round + 1) * (unsigned)G, err)) return;
+    if (*(volatile int *)(pend + round % 3) == 0) break;
   }
   grid_exit(bar);
 }
@@ -155,44 +143,38 @@ __global__ void k_colour_check(const int *a, int n, int *out) {
   if (a[i] < 0) out[1] = 1;
 }
 
-// the cooperative launch of k_colour_levels: its CTAs resident together,
-// two an SM (each barrier costs an atomic per CTA)
-static int colour_levels(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
+// the cooperative launch of k_colour_rounds: its CTAs resident together
+static int colour_rounds(Sim *s, int n, const int *rowptr, const int *col, int *colour) {
   static const int slots = []() {
     int dev = 0, nsm = 0, k = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_levels, kBlock, 0);
-    return std::min(std::max(k, 1), 2) * std::max(nsm, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_colour_rounds, kBlock, 0);
+    return std::max(k, 1) * std::max(nsm, 1);
   }();
   int grid = std::max(1, std::min(slots, nblk(n)));
-  int *work = (int *)dalloc(s, (size_t)n * 12);   // indeg, two levels' rows
-  if (!work) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
-  {
-    LaunchScope ls(s, "k_colour_levels");
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kBlock);
-    cfg.stream = s->stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    // counter: [1] overflow, [3] err, [4..6] the level sizes; dev_err + 4: the barrier's counts
-    DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_levels, n, rowptr, col, colour, work, work + n,
-                                  work + 2 * (size_t)n, s->counter + 4, s->counter + 1,
-                                  (unsigned *)(s->dev_err + 4), s->counter + 3));
-  }
-  dfree(s, work);
+  if (s->alloc_failed) return DP_ENOMEM;
+  LaunchScope ls(s, "k_colour_rounds");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.stream = s->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  // counter: [1] overflow, [3] err, [4..6] the rotating counts; dev_err + 4: the barrier's
+  DP_CUDA(s, cudaLaunchKernelEx(&cfg, k_colour_rounds, n, rowptr, col, colour, s->counter + 4,
+                                s->counter + 1, (unsigned *)(s->dev_err + 4), s->counter + 3));
   return DP_OK;
 }
 
 int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour, int *ncolour) {
   DP_LAUNCH(s, k_fill_i32, nblk(n), kBlock, 0, colour, n, -1);
   if (n > 0) {
-    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 32, s->stream));   // overflow, err, level sizes
-    DP_TRY(colour_levels(s, n, rowptr, col, colour));
+    DP_CUDA(s, cudaMemsetAsync(s->counter, 0, 32, s->stream));   // overflow, err, counts
+    DP_TRY(colour_rounds(s, n, rowptr, col, colour));
     DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 16, cudaMemcpyDeviceToHost, s->stream));
     DP_CUDA(s, cudaStreamSynchronize(s->stream));
     if (s->h_counter[3]) {
@@ -205,8 +187,8 @@ int greedy_colour(Sim *s, int n, const int *rowptr, const int *col, int *colour,
   DP_LAUNCH(s, k_colour_check, nblk(n), kBlock, 0, colour, n, s->counter);
   DP_CUDA(s, cudaMemcpyAsync(s->h_counter, s->counter, 8, cudaMemcpyDeviceToHost, s->stream));
   DP_CUDA(s, cudaStreamSynchronize(s->stream));
-  if (n > 0 && s->h_counter[1]) {   // a lower neighbour whose row does not name the row
-    s->fail(DP_EINVAL, "greedy colouring needs a structurally symmetric pattern");
+  if (n > 0 && s->h_counter[1]) {
+    s->fail(DP_EINVAL, "greedy colouring left a row uncoloured");
     return DP_EINVAL;
   }
   *ncolour = n > 0 ? s->h_counter[0] + 1 : 0;
