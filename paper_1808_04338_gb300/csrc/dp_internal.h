@@ -329,7 +329,6 @@ struct Sim {
   double *p0c_val = nullptr, *dinv_c = nullptr;
   float *p0c_valf = nullptr, *dinv_cf = nullptr;
   bool l0_lu = false;
-  int l0_adj_key[3] = {-1, -1, -1}, l0_adj = 0;   // rows meeting the wells (WellLink mode 1)
   int l0_G = 1;       // lanes per row of the level-0 colour-order sweeps (autotuned; 1: a thread)
   int shapes = 0;     // bumped whenever launch shapes change (autotune, AMG set-up)
   double *l0_pv = nullptr;

@@ -151,7 +151,7 @@ __device__ __forceinline__ T row_dot(int e0, int e1, int lane, const int *__rest
 // lanes take entries lane, lane + 32, ... (two strides a trip, their loads
 // issued together), the partial sums meet in a shuffle tree; b_q and 1/a_qq
 // are read before the row.
-template <typename T, bool RESID, bool CG = false>   // CG: x read through L2 (__ldcg)
+template <typename T, bool RESID>
 __device__ __forceinline__ void warp_row_c(int q, int lane, const int *__restrict__ rowptr,
                                            const int *__restrict__ colp,
                                            const T *__restrict__ pv, const T *__restrict__ dinv,
@@ -166,19 +166,16 @@ __device__ __forceinline__ void warp_row_c(int q, int lane, const int *__restric
   for (; e + 32 < e1; e += 64) {
     T v0 = __ldg(pv + e), v1 = __ldg(pv + e + 32);
     int c0 = __ldg(colp + e), c1 = __ldg(colp + e + 32);
-    s = fma(v0, CG ? __ldcg(x + c0) : x[c0], s);
-    s = fma(v1, CG ? __ldcg(x + c1) : x[c1], s);
+    s = fma(v0, x[c0], s);
+    s = fma(v1, x[c1], s);
   }
-  if (e < e1) {
-    int c = __ldg(colp + e);
-    s = fma(__ldg(pv + e), CG ? __ldcg(x + c) : x[c], s);
-  }
+  if (e < e1) s = fma(__ldg(pv + e), x[__ldg(colp + e)], s);
   s = warp_sum(s);
   if (lane == 0) {
     if (RESID) {
       r[q] = bq - s;
     } else {
-      if (di != T(0)) x[q] = fma(bq - s, di, CG ? __ldcg(x + q) : x[q]);
+      if (di != T(0)) x[q] = fma(bq - s, di, x[q]);
     }
   }
 }

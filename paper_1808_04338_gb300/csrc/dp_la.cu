@@ -1139,7 +1139,6 @@ __global__ void k_map_copy(long long n, const int *map, const int *in, int *out)
 }
 
 static int l0c_setup(Sim *s) {
-  s->l0_adj_key[0] = -1;   // the count of rows meeting the wells is taken again
   Level &L = s->lev[0];
   int n = L.n;
   s->l0_colp = (int *)dalloc(s, (size_t)std::max(L.nnz, 1) * 4 + 16);
@@ -1401,71 +1400,13 @@ __device__ __forceinline__ void tile_producer(int nph, const int *pr0, const int
   }
 }
 
-// The long rows (the wells, the last colour) linked into the launch of the
-// short colour next to them in a Gauss-Seidel sweep, so that they need no
-// launch of their own (the launch is cooperative: its CTAs are resident
-// together, so the waits below end).  mode 1, the wells after this colour
-// (forward sweep): every row of the colour with a column in [w0, w1) counts
-// itself in sync[0] once written (after a fence); CTA 0, when its tiles are
-// done, waits (bounded) until the count reaches nadj and then does the
-// wells.  mode 2, the wells before this colour (backward sweep): CTA 0 does
-// the wells first and then raises sync[1]; a row with a column in
-// [w0, w1) waits (bounded) for it before its gathers.  In both the rows
-// that meet the wells read x through L2, and every row's arithmetic is its
-// own kernel's (stage_row_sum, warp_row_c), so the results are those of
-// the separate launches bit for bit.
-struct WellLink {
-  int mode = 0;           // 0 none, 1 wells after, 2 wells before
-  int w0 = 0, w1 = 0;     // the well rows
-  int nadj = 0;           // mode 1: rows of the colour with a column in [w0, w1)
-  int *sync = nullptr;    // [0] those rows written, [1] the wells done (zero before the launch)
-};
-
-// stage_row_sum for a row that may meet the wells: tw says whether it does;
-// if so and flag is given, the gathers wait (bounded) for *flag
-template <typename T>
-__device__ __forceinline__ T stage_row_sum_w(int n, const int *cs, const T *vs, const T *x,
-                                             int w0, const int *flag, int *err, bool &tw) {
-  constexpr int kB = 8;
-  int c[kB];
-  T v[kB], xv[kB];
-  tw = false;
-#pragma unroll
-  for (int j = 0; j < kB; ++j) {
-    c[j] = j < n ? cs[j] : 0;
-    v[j] = j < n ? vs[j] : T(0);
-    tw |= j < n && c[j] >= w0;
-  }
-  for (int j = kB; j < n; ++j) tw |= cs[j] >= w0;
-  if (tw && flag && !*(const volatile int *)flag) {
-    uint64_t t0 = global_ns();
-    while (!*(const volatile int *)flag) {
-      if (*(volatile int *)err || global_ns() - t0 > kWaitNs) {
-        atomicExch(err, 1);
-        break;
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kB; ++j) xv[j] = j < n ? (tw ? __ldcg(x + c[j]) : x[c[j]]) : T(0);
-  T s0 = T(0), s1 = T(0);
-#pragma unroll
-  for (int j = 0; j < kB; j += 2) {
-    if (j < n) s0 = fma(v[j], xv[j], s0);
-    if (j + 1 < n) s1 = fma(v[j + 1], xv[j + 1], s1);
-  }
-  for (int j = kB; j < n; ++j) s0 = fma(vs[j], tw ? __ldcg(x + cs[j]) : x[cs[j]], s0);
-  return s0 + s1;
-}
-
 template <typename T, bool RESID, int S, int CAPR>
 __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__restrict__ rowptr,
                                                const int *__restrict__ colp,
                                                const T *__restrict__ pv,
                                                const T *__restrict__ dinv,
                                                const T *__restrict__ b, T *x,
-                                               T *__restrict__ r, int *err,
-                                               const WellLink &wl = WellLink{}) {
+                                               T *__restrict__ r, int *err) {
   constexpr int kCap = CAPR * kTT;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   TStage<T, CAPR> *st = reinterpret_cast<TStage<T, CAPR> *>(tma_smem);
@@ -1490,17 +1431,6 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
   volatile int *abort_v = &abort_flag;
   if (t == 0) abort_flag = 0;
   consumers_sync();
-  const bool link = !RESID && wl.mode != 0;
-  if (link && wl.mode == 2 && blockIdx.x == 0) {   // the wells first, then the flag
-    for (int q = wl.w0 + (t >> 5); q < wl.w1; q += kTT / 32)
-      warp_row_c<T, false, true>(q, t & 31, rowptr, colp, pv, dinv, b, x, nullptr);
-    consumers_sync();
-    if (t == 0) {
-      __threadfence();
-      atomicExch(wl.sync + 1, 1);
-    }
-  }
-  const int *flag = link && wl.mode == 2 ? wl.sync + 1 : nullptr;
   for (int i = 0; i < mine; ++i) {
     int k = i % S;
     int q0 = r0 + ((int)blockIdx.x + i * (int)gridDim.x) * kTT, nrow = min(kTT, r1 - q0);
@@ -1519,37 +1449,12 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
       int ae = rp[0] & ~3;
       bool fits = ((rp[nrow] - ae + 3) & ~3) <= kCap;
       int e = rp[t], e1 = rp[t + 1];
-      const int *cs = fits ? st[k].col + (e - ae) : colp + e;
-      const T *vs = fits ? st[k].val + (e - ae) : pv + e;
-      bool tw = false;
-      T sum = link ? stage_row_sum_w<T>(e1 - e, cs, vs, x, wl.w0, flag, err, tw)
-                   : stage_row_sum<T>(e1 - e, cs, vs, x);
+      T sum = fits ? stage_row_sum<T>(e1 - e, st[k].col + (e - ae), st[k].val + (e - ae), x)
+                   : stage_row_sum<T>(e1 - e, colp + e, pv + e, x);
       if (RESID) r[q] = bq - sum;
-      else if (dq != T(0)) x[q] = fma(bq - sum, dq, tw ? __ldcg(x + q) : x[q]);
-      if (link && wl.mode == 1 && tw) {   // counted once written
-        __threadfence();
-        atomicAdd(wl.sync, 1);
-      }
+      else if (dq != T(0)) x[q] = fma(bq - sum, dq, x[q]);
     }
     mbar_arrive(&empty[k]);
-  }
-  if (link && wl.mode == 1 && blockIdx.x == 0 && !*abort_v) {   // the wells last
-    consumers_sync();
-    if (t == 0) {
-      uint64_t t0 = global_ns();
-      while (ld_acquire_u32((const unsigned *)wl.sync) < (unsigned)wl.nadj) {
-        if (*(volatile int *)err || global_ns() - t0 > kWaitNs) {
-          atomicExch(err, 1);
-          *abort_v = 1;
-          break;
-        }
-      }
-      __threadfence();
-    }
-    consumers_sync();
-    if (!*abort_v)
-      for (int q = wl.w0 + (t >> 5); q < wl.w1; q += kTT / 32)
-        warp_row_c<T, false, true>(q, t & 31, rowptr, colp, pv, dinv, b, x, nullptr);
   }
   if (*abort_v) atomicExch(err, 1);
 }
@@ -1559,9 +1464,8 @@ __global__ void __launch_bounds__(kTT + 32) k_gs_c_tma(int r0, int r1, const int
                                                        const int *__restrict__ colp,
                                                        const T *__restrict__ pv,
                                                        const T *__restrict__ dinv,
-                                                       const T *__restrict__ b, T *x, int *err,
-                                                       WellLink wl) {
-  sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err, wl);
+                                                       const T *__restrict__ b, T *x, int *err) {
+  sweep_tma_body<T, false, S, CAPR>(r0, r1, rowptr, colp, pv, dinv, b, x, nullptr, err);
 }
 
 template <typename T, int S, int CAPR>
@@ -1594,31 +1498,10 @@ static int tma_grid(K kern, int smem, int rows) {
 // stages of 6, -3 two stages of 4 (level 0's mixed fracture/matrix tiles
 // average about 5, so those bring their row pointers only)
 template <typename T, int S, int CAPR>
-static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
-                   const WellLink &wl) {
+static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x) {
   constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
-  int grid = tma_grid<16 * S + CAPR>(k_gs_c_tma<T, S, CAPR>, smem, r1 - r0);
-  if (wl.mode == 0) {
-    DP_LAUNCH(s, (k_gs_c_tma<T, S, CAPR>), grid, kTT + 32, smem, r0, r1, s->lu_rowptr,
-              s->l0_colp, pv, dinv, b, x, s->dev_err, wl);
-    return;
-  }
-  // linked to the wells: CTAs that wait on one another, so a cooperative launch
-  if (s->alloc_failed) return;
-  LaunchScope ls(s, "k_gs_c_tma");
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kTT + 32);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s->stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;
-  at[0].val.cooperative = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_gs_c_tma<T, S, CAPR>, r0, r1, (const int *)s->lu_rowptr,
-                                     (const int *)s->l0_colp, pv, dinv, b, x, s->dev_err, wl);
-  if (e != cudaSuccess) s->fail(DP_ECUDA, std::string("k_gs_c_tma launch: ") + cudaGetErrorString(e));
+  DP_LAUNCH(s, (k_gs_c_tma<T, S, CAPR>), (tma_grid<16 * S + CAPR>(k_gs_c_tma<T, S, CAPR>, smem, r1 - r0)),
+            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err);
 }
 template <typename T, int S, int CAPR>
 static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *r) {
@@ -1629,48 +1512,17 @@ static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *
 }
 template <typename T>
 static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
-                      T *r, const WellLink &wl = WellLink{}) {
+                      T *r) {
   s->waits_used = true;
   if (r) {
     if (G == -1) resid_tma<T, 2, 8>(s, r0, r1, pv, b, x, r);
     else if (G == -2) resid_tma<T, 3, 6>(s, r0, r1, pv, b, x, r);
     else resid_tma<T, 2, 4>(s, r0, r1, pv, b, x, r);
   } else {
-    if (G == -1) gs_tma<T, 2, 8>(s, r0, r1, pv, dinv, b, x, wl);
-    else if (G == -2) gs_tma<T, 3, 6>(s, r0, r1, pv, dinv, b, x, wl);
-    else gs_tma<T, 2, 4>(s, r0, r1, pv, dinv, b, x, wl);
+    if (G == -1) gs_tma<T, 2, 8>(s, r0, r1, pv, dinv, b, x);
+    else if (G == -2) gs_tma<T, 3, 6>(s, r0, r1, pv, dinv, b, x);
+    else gs_tma<T, 2, 4>(s, r0, r1, pv, dinv, b, x);
   }
-}
-
-// rows of [r0, r1) with a column in [w0, w1)
-__global__ void k_count_touch(int r0, int r1, const int *__restrict__ rowptr,
-                              const int *__restrict__ colp, int w0, int w1, int *out) {
-  int q = r0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= r1) return;
-  bool t = false;
-  for (int e = rowptr[q]; e < rowptr[q + 1]; ++e) t |= colp[e] >= w0 && colp[e] < w1;
-  if (t) atomicAdd(out, 1);
-}
-
-// the count for a WellLink of mode 1, kept while level 0's colour copy lives
-static int l0_touch_count(Sim *s, int r0, int r1, int w0, int w1, int *out) {
-  if (s->l0_adj_key[0] == r0 && s->l0_adj_key[1] == r1 && s->l0_adj_key[2] == w0) {
-    *out = s->l0_adj;
-    return DP_OK;
-  }
-  int *d = s->dev_err + 12;
-  DP_CUDA(s, cudaMemsetAsync(d, 0, 4, s->stream));
-  DP_LAUNCH(s, k_count_touch, nblk(r1 - r0), kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp, w0, w1,
-            d);
-  int h = 0;
-  DP_CUDA(s, cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, s->stream));
-  DP_CUDA(s, cudaStreamSynchronize(s->stream));
-  s->l0_adj_key[0] = r0;
-  s->l0_adj_key[1] = r1;
-  s->l0_adj_key[2] = w0;
-  s->l0_adj = h;
-  *out = h;
-  return DP_OK;
 }
 
 
@@ -1931,36 +1783,14 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
     if (s->lu_cstart[c + 1] > s->lu_cstart[c]) order.push_back(c);
   }
   auto lng = [&](int c) { return s->lu_cmaxlen[c] > kLongRow; };
-  // with the pipelined kernels the wells (the last colour, long rows) go
-  // into the launch of the short colour next to them (WellLink)
-  bool linkable = G <= -1 && G >= -3 && order.size() >= 2 && order.size() <= 3 &&
-                  lng(forward ? order.back() : order.front()) && !lng(order[order.size() == 3 ? 1 : (forward ? 0 : 1)]);
-  int cw = forward ? order.back() : order.front();   // the wells' colour
-  bool wells_pending = false;
   bool first = from_zero;
   for (size_t t = 0; t < order.size(); ++t) {
     int c = order[t];
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
-    if (linkable && c == cw && (wells_pending || !forward)) {
-      if (!forward) wells_pending = true;   // done with the next colour's launch
-      continue;
-    }
     if (first) {
       first = false;
       if (!preset)
         DP_LAUNCH(s, k_gs_c_first<T>, nblk(r1 - r0), kBlock, 0, r0, r1, L0C<T>::dinv(s), b, x);
-      continue;
-    }
-    if (linkable && !lng(c) && ((forward && t + 1 == order.size() - 1) || (!forward && t == 1))) {
-      WellLink wl;
-      wl.mode = forward ? 1 : 2;
-      wl.w0 = s->lu_cstart[cw];
-      wl.w1 = s->lu_cstart[cw + 1];
-      wl.sync = s->dev_err + 8;
-      if (forward) DP_TRY(l0_touch_count(s, r0, r1, wl.w0, wl.w1, &wl.nadj));
-      DP_CUDA(s, cudaMemsetAsync(wl.sync, 0, 8, s->stream));
-      sweep_tma<T>(s, G, r0, r1, L0C<T>::pv(s), L0C<T>::dinv(s), b, x, nullptr, wl);
-      if (forward) wells_pending = true;   // the wells are done: skip their colour
       continue;
     }
     if (lng(c))
