@@ -448,8 +448,9 @@ int sim_well_rates(dp_sim *sim, double *q_oil, double *q_water);
 
 /* AMG hierarchy of the pressure stage after the first sim_solve_step:
  * level sizes (returns the number of levels) and level arrays (CSR of the
- * level operator, aggregate of each row or -1, greedy colour of each row);
- * any pointer may be NULL. */
+ * level operator, aggregate of each row or -1, greedy colour of each row:
+ * -1 on a level smoothed by l1-Jacobi, which uses no colouring and gets
+ * none); any pointer may be NULL. */
 int sim_amg_level_info(dp_sim *sim, int32_t level, int32_t *n, int32_t *nnz, int32_t *nagg);
 int sim_amg_level_arrays(dp_sim *sim, int32_t level, int32_t *rowptr, int32_t *col,
                          double *val, int32_t *agg, int32_t *colour);

@@ -769,8 +769,23 @@ static int level_prepare(Sim *s, Level &L) {
   }
   DP_LAUNCH(s, k_diag_pos, nblk(n), kBlock, 0, n, L.rowptr, L.col, L.dpos);
   DP_LAUNCH(s, k_tpos, nblk(n), kBlock, 0, n, L.rowptr, L.col, L.tpos);
-  DP_TRY(greedy_colour(s, n, L.rowptr, L.col, L.colour, &L.ncolour));
-  DP_TRY(colour_lists(s, n, L.colour, L.ncolour, L.clist, L.cstart, nullptr));
+  if (L.rowptr == s->K.rowptr && L.col == s->K.col && s->colour && s->perm && s->ncolour > 0) {
+    // level 0 is the pattern the ILU(0) coloured: its colouring and lists are those
+    DP_CUDA(s, cudaMemcpyAsync(L.colour, s->colour, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                               s->stream));
+    DP_CUDA(s, cudaMemcpyAsync(L.clist, s->perm, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                               s->stream));
+    L.ncolour = s->ncolour;
+    L.cstart = s->lu_cstart;
+  } else if (L.l1) {
+    // an l1-Jacobi level uses no colouring: none is made (colours -1)
+    DP_LAUNCH(s, k_fill_i32, nblk(n), kBlock, 0, L.colour, n, -1);
+    L.ncolour = 0;
+    L.cstart.assign(1, 0);
+  } else {
+    DP_TRY(greedy_colour(s, n, L.rowptr, L.col, L.colour, &L.ncolour));
+    DP_TRY(colour_lists(s, n, L.colour, L.ncolour, L.clist, L.cstart, nullptr));
+  }
   return DP_OK;
 }
 

@@ -20,6 +20,16 @@ import oracle as O
 pytestmark = pytest.mark.gpu
 
 
+def same_colours(lev, a, b):
+    """Report options smooth level 0 by Gauss-Seidel (its colouring is the
+    oracle's) and the coarser levels by l1-Jacobi, for which the library
+    makes no colouring (colours -1)."""
+    if lev == 0:
+        np.testing.assert_array_equal(a["colour"], b["colour"])
+    else:
+        assert (a["colour"] == -1).all(), lev
+
+
 def test_bench_size_assembly_solve_and_timestep():
     import scipy.sparse as sp
     from paper_1808_04338_gb300 import dpsim
@@ -89,9 +99,9 @@ def test_bench_size_decoupling_colours_and_amg_setup_bit_exact():
     np.testing.assert_array_equal(gc, oc)
     Lg, Lo = g.amg_levels(), o.amg_levels()
     assert len(Lg) == len(Lo) > 2
-    for a, b in zip(Lg, Lo):
+    for lev, (a, b) in enumerate(zip(Lg, Lo)):
         np.testing.assert_array_equal(a["agg"], b["agg"])
-        np.testing.assert_array_equal(a["colour"], b["colour"])
+        same_colours(lev, a, b)
         assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
 
 
@@ -130,8 +140,9 @@ def test_example3_size_assembly_and_setup_bit_exact():
     del gc, oc
     Lg, Lo = g.amg_levels(), o.amg_levels()
     assert len(Lg) == len(Lo) > 2
-    for a, b in zip(Lg, Lo):
+    for lev, (a, b) in enumerate(zip(Lg, Lo)):
         assert (a["n"], a["nnz"], a["nagg"]) == (b["n"], b["nnz"], b["nagg"])
-        for k in ("rowptr", "col", "agg", "colour"):
+        for k in ("rowptr", "col", "agg"):
             np.testing.assert_array_equal(a[k], b[k])
+        same_colours(lev, a, b)
         assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))

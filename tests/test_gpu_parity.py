@@ -319,9 +319,12 @@ def test_layered_200k_first_step_parity():
     o.solve_step()
     Lg, Lo = g.amg_levels(), o.amg_levels()
     assert len(Lg) == len(Lo)
-    for a, b in zip(Lg, Lo):
+    for lev, (a, b) in enumerate(zip(Lg, Lo)):
         np.testing.assert_array_equal(a["agg"], b["agg"])
-        np.testing.assert_array_equal(a["colour"], b["colour"])
+        if lev == 0:   # report options: Gauss-Seidel on level 0 only
+            np.testing.assert_array_equal(a["colour"], b["colour"])
+        else:          # l1-Jacobi levels get no colouring
+            assert (a["colour"] == -1).all(), lev
         assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
 
 
