@@ -283,6 +283,7 @@ struct Sim {
   int lu_nL = 0;
   int *lu_Lptr = nullptr, *lu_Uptr = nullptr, *lu_dst = nullptr, *lu_colp = nullptr;
   double *ilu_zp = nullptr;       // colour-order work vector (2 nb values of the sweep type)
+  double *ilu_zp2 = nullptr;      // the FP32 second application's result (2 nb floats)
   // maps of the decoupling's entry-parallel writes: natural row of each
   // entry, its block in the factor's split layout, its factor-order position
   int *erow = nullptr, *ilupos = nullptr, *l0pos = nullptr;

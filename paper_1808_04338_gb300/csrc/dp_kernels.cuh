@@ -668,7 +668,8 @@ __device__ __forceinline__ void k_ilu_result_b(int bx, int gx, int n, const int 
                                                        double *__restrict__ out,
                                                        T *__restrict__ outT,
                                                        const float *__restrict__ inj,
-                                                       int inj_perm) {
+                                                       int inj_perm,
+                                                       const T *__restrict__ zb = nullptr) {
   using T2 = typename V2<T>::t;
   const T2 *z2 = reinterpret_cast<const T2 *>(zp);
   int S = gx * blockDim.x;
@@ -686,7 +687,12 @@ __device__ __forceinline__ void k_ilu_result_b(int bx, int gx, int n, const int 
     int i = i0 + k * S;
     if (i < n) {
       z[k] = z2[p[k]];
-      bs[k] = base ? reinterpret_cast<const double2 *>(base)[i] : make_double2(0.0, 0.0);
+      if (zb) {   // the base in colour order, in T (an earlier result): widened exactly
+        T2 u = reinterpret_cast<const T2 *>(zb)[p[k]];
+        bs[k] = make_double2(double(u.x), double(u.y));
+      } else {
+        bs[k] = base ? reinterpret_cast<const double2 *>(base)[i] : make_double2(0.0, 0.0);
+      }
       // the coarse correction injected into the base's pressure component
       if (inj) bs[k].x = bs[k].x + double(__ldg(inj + (inj_perm ? p[k] : i)));
     }
@@ -696,8 +702,9 @@ __device__ __forceinline__ void k_ilu_result_b(int bx, int gx, int n, const int 
     int i = i0 + k * S;
     if (i >= n) continue;
     double v0 = double(z[k].x), v1 = double(z[k].y);
-    reinterpret_cast<double2 *>(out)[i] =
-        base ? make_double2(bs[k].x + v0, bs[k].y + v1) : make_double2(v0, v1);
+    if (out)
+      reinterpret_cast<double2 *>(out)[i] =
+          base || zb ? make_double2(bs[k].x + v0, bs[k].y + v1) : make_double2(v0, v1);
     if (outT) reinterpret_cast<T2 *>(outT)[i] = z[k];
   }
 }

@@ -543,7 +543,8 @@ int ilu_setup(Sim *s) {
   s->lu_dst = (int *)dalloc(s, (size_t)nnz * 4);
   s->lu_colp = (int *)dalloc(s, (size_t)nnz * 4);
   s->ilu_zp = (double *)dalloc(s, (size_t)2 * n * 8);
-  if (!s->lu_Lptr || !s->lu_Uptr || !s->lu_dst || !s->lu_colp || !s->ilu_zp) {
+  s->ilu_zp2 = (double *)dalloc(s, (size_t)2 * n * 4);   // the FP32 second result
+  if (!s->lu_Lptr || !s->lu_Uptr || !s->lu_dst || !s->lu_colp || !s->ilu_zp || !s->ilu_zp2) {
     s->fail(DP_ENOMEM, "allocation failed");
     return DP_ENOMEM;
   }
@@ -612,9 +613,9 @@ static int tail_grid(int nb) {
 // is left in the colour-order work vector s->ilu_zp, from which the caller
 // gathers it (ilu_result) while converting or accumulating.
 template <typename T, typename TR>
-static int ilu_apply_t(Sim *s, const T *lu, const TR *r) {
+static int ilu_apply_t(Sim *s, const T *lu, const TR *r, T *zpo = nullptr) {
   int n = s->K.n, nL = s->lu_nL, nc = s->ncolour;
-  T *zp = reinterpret_cast<T *>(s->ilu_zp);
+  T *zp = zpo ? zpo : reinterpret_cast<T *>(s->ilu_zp);
   // the last colour is solved forward and its pivots applied in one launch:
   // its rows have no U blocks, so that is also the backward sweep's first step
   int last = nc - 1;
@@ -683,19 +684,22 @@ __global__ void __launch_bounds__(kBlock) k_ilu_result(int n, const int *__restr
                                                        double *__restrict__ out,
                                                        T *__restrict__ outT,
                                                        const float *__restrict__ inj,
-                                                       int inj_perm) {
-  k_ilu_result_b<T>(blockIdx.x, gridDim.x, n, iperm, zp, base, out, outT, inj, inj_perm);
+                                                       int inj_perm, const T *__restrict__ zb) {
+  k_ilu_result_b<T>(blockIdx.x, gridDim.x, n, iperm, zp, base, out, outT, inj, inj_perm, zb);
 }
 
 // out = base + result; with inj, out = (base + inj injected) + result, inj
 // (a level-0 vector, natural or, with inj_perm, colour order) added to the
-// base's pressure component first.
+// base's pressure component first.  out may be NULL (only outT written);
+// zb, a colour-order vector in T, may stand for the base (widened exactly);
+// zp: the colour-order result (s->ilu_zp by default).
 template <typename T>
 static int ilu_result(Sim *s, const double *base, double *out, T *outT = nullptr,
-                      const float *inj = nullptr, int inj_perm = 0) {
+                      const float *inj = nullptr, int inj_perm = 0, const T *zb = nullptr,
+                      const T *zp = nullptr) {
   int n = s->K.n;
   DP_LAUNCH(s, k_ilu_result<T>, nblk((n + kRes - 1) / kRes), kBlock, 0, n, s->iperm,
-            reinterpret_cast<const T *>(s->ilu_zp), base, out, outT, inj, inj_perm);
+            zp ? zp : reinterpret_cast<const T *>(s->ilu_zp), base, out, outT, inj, inj_perm, zb);
   return DP_OK;
 }
 
@@ -2159,9 +2163,12 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   }
   // the stage residuals from the FP32 copy of the operator
   // (z1 and z2 also kept in FP32 for the residuals' gathers; r - A z2 in FP32)
+  // z1 in FP32 only (z1f, natural order): its FP64 value is the colour-order
+  // result itself, kept in s->ilu_zp for the final sum (the second
+  // application writes s->ilu_zp2)
   Level &L0 = s->lev[0];
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
-  DP_TRY(ilu_result<float>(s, nullptr, s->z1, s->z1f));
+  DP_TRY(ilu_result<float>(s, nullptr, nullptr, s->z1f));
   const int *m = l0c_on(s) ? s->iperm : nullptr;     // level-0 vectors in colour order
   X0Init xi;   // in colour order, the pre-smoothing's start written with b
   if (m) {
@@ -2181,9 +2188,11 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   DP_LAUNCH(s, k_inject_f32, nblk(nb), kBlock, 0, nb, L0.xf, s->z1f, m);
   DP_LAUNCH(s, k_bsr_resid_f32, 1 + nblk(2LL * s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
             s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1f, r, s->r1f);
-  DP_TRY((ilu_apply_t<float, float>(s, s->lu_valf, s->r1f)));
-  // z = z2 + F (r - A z2), z2 = z1 + P e formed here
-  return ilu_result<float>(s, s->z1, z, nullptr, L0.xf, m ? 1 : 0);
+  float *zp2 = reinterpret_cast<float *>(s->ilu_zp2);
+  DP_TRY((ilu_apply_t<float, float>(s, s->lu_valf, s->r1f, zp2)));
+  // z = z2 + F (r - A z2), z2 = z1 + P e formed here (z1 from the first result)
+  return ilu_result<float>(s, nullptr, z, nullptr, L0.xf, m ? 1 : 0,
+                           reinterpret_cast<const float *>(s->ilu_zp), zp2);
 }
 
 // ---------------------------------------------------------------- FGMRES
