@@ -456,8 +456,11 @@ int sim_amg_level_arrays(dp_sim *sim, int32_t level, int32_t *rowptr, int32_t *c
                          double *val, int32_t *agg, int32_t *colour);
 
 /* Time every launch of one kernel (by name, e.g. "bsr_spmv") with CUDA
- * events on the simulation stream; NULL stops.  sim_kernel_timing returns
- * the accumulated milliseconds and launch count since the last reset. */
+ * events on the simulation stream; NULL stops.  A name with a dot names a
+ * region instead, timed from before its first launch to after its last:
+ * "sweep.gs", each level-0 Gauss-Seidel sweep in the ILU(0) colour order.
+ * sim_kernel_timing returns the accumulated milliseconds and the count of
+ * launches (regions) since the last reset. */
 int sim_time_kernel(dp_sim *sim, const char *name);
 int sim_kernel_timing(dp_sim *sim, double *ms, int64_t *launches, int32_t reset);
 

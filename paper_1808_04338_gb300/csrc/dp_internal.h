@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "dpsim.h"
@@ -115,6 +116,17 @@ struct LaunchScope {
   LaunchScope(Sim *s, const char *name);
   ~LaunchScope();
 };
+// CUDA-event timing of a region of launches (one whole colour sweep, say),
+// when the name being timed is the region's name exactly: one event before
+// its first launch and one after its last, none between them (an event
+// between two launches would end a programmatic dependence).  Region names
+// hold a dot, which no kernel name does.
+struct RegionScope {
+  Sim *s;
+  bool timed;
+  RegionScope(Sim *s, const char *name);
+  ~RegionScope();
+};
 // After an allocation has failed nothing more is launched for the
 // realisation (its calls return DP_ENOMEM until it is destroyed), so no
 // kernel can be handed a buffer that was never obtained.
@@ -124,6 +136,28 @@ struct LaunchScope {
     ::dp::LaunchScope ls__((sim), #name);                               \
     name<<<(grid), (block), (smem), (sim)->stream>>>(__VA_ARGS__);      \
   } while (0)
+
+// A launch as a programmatic dependent of the kernel before it on the
+// stream: its CTAs may be scheduled once every CTA of that kernel has
+// triggered (griddepcontrol.launch_dependents) or exited, before that
+// kernel's completion.  The kernel must execute griddep_wait() before it
+// touches anything the kernel before it writes (launch_pdl, after Sim).
+#define DP_LAUNCH_PDL(sim, name, grid, block, smem, ...)                              \
+  do {                                                                               \
+    if ((sim)->alloc_failed) break;                                                  \
+    ::dp::LaunchScope ls__((sim), #name);                                            \
+    ::dp::launch_pdl((sim), name, dim3(grid), dim3(block), (smem), __VA_ARGS__);     \
+  } while (0)
+// Waits until the grids this one depends on have completed and their
+// writes are visible (a no-op in a kernel launched without the attribute).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the programmatic dependents of this grid be scheduled once every CTA
+// has executed it (or exited); it orders nothing: they still wait in
+// griddep_wait for this grid's completion.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+bool pdl_enabled();   // off when the environment sets DPSIM_PDL=0
 
 // Storage order of the Krylov operator's copy: locations in chunks of
 // kChunk; storage rows 2 kChunk c .. of chunk c hold its fracture rows (cells
@@ -376,6 +410,22 @@ struct Sim {
     last_error = m;
   }
 };
+
+template <typename... P, typename... A>
+inline void launch_pdl(Sim *s, void (*k)(P...), dim3 grid, dim3 block, size_t smem, A &&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+  if (e != cudaSuccess) s->fail(DP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
 
 }  // namespace dp
 

@@ -782,6 +782,7 @@ __global__ void __launch_bounds__(kBlock) k_csr_mv(int n, const int *__restrict_
                                                    const TV *__restrict__ val,
                                                    const T *__restrict__ x, T *__restrict__ y,
                                                    int add) {
+  griddep_launch_dependents();   // the wells' rows after a prolongation (k_gs_c_wp)
   k_csr_mv_b<G, T, TV>(blockIdx.x, gridDim.x, n, rowptr, col, val, x, y, add);
 }
 
@@ -1245,21 +1246,61 @@ __global__ void k_gs_c_first(int r0, int r1, const T *__restrict__ dinv, const T
 }
 
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_gs_c_w(int r0, int r1, const int *__restrict__ rowptr,
-                                                   const int *__restrict__ colp,
-                                                   const T *__restrict__ pv,
-                                                   const T *__restrict__ dinv,
-                                                   const T *__restrict__ b, T *x) {
-  k_gs_c_w_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, dinv, b, x);
+// Level-0 long rows (the wells) launched as programmatic dependents of the
+// launch before them, a CTA of one warp per row: what no kernel of the
+// V-cycle writes (the row's pointers, columns and values, 1/a_ii) is loaded
+// before griddep_wait, so the rows' launch and these loads overlap the end
+// of the kernel before; b and x are read after it.  The first 64 entries of
+// a row stay in registers, longer rows read the rest after the wait.  The
+// products and their order are warp_row_c's, so the results equal
+// the batch's well rows (k_gs_c_w_b, k_resid_c_w_b) bit for bit.
+template <typename T, bool RESID>
+__device__ __forceinline__ void row_c_wp(int q, const int *__restrict__ rowptr,
+                                         const int *__restrict__ colp, const T *__restrict__ pv,
+                                         const T *__restrict__ dinv, const T *b, T *x, T *r) {
+  int lane = threadIdx.x;
+  int e = __ldg(rowptr + q) + lane, e1 = __ldg(rowptr + q + 1);
+  bool h0 = e < e1, h1 = e + 32 < e1;
+  T v0 = h0 ? __ldg(pv + e) : T(0), v1 = h1 ? __ldg(pv + e + 32) : T(0);
+  int c0 = h0 ? __ldg(colp + e) : 0, c1 = h1 ? __ldg(colp + e + 32) : 0;
+  T di = (!RESID && lane == 0) ? dinv[q] : T(0);
+  griddep_wait();
+  T bq = lane == 0 ? b[q] : T(0);
+  T s = T(0);
+  if (h1) {
+    s = fma(v0, x[c0], s);
+    s = fma(v1, x[c1], s);
+    for (e += 64; e + 32 < e1; e += 64) {
+      T w0 = __ldg(pv + e), w1 = __ldg(pv + e + 32);
+      int d0 = __ldg(colp + e), d1 = __ldg(colp + e + 32);
+      s = fma(w0, x[d0], s);
+      s = fma(w1, x[d1], s);
+    }
+    if (e < e1) s = fma(__ldg(pv + e), x[__ldg(colp + e)], s);
+  } else if (h0) {
+    s = fma(v0, x[c0], s);
+  }
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (RESID) r[q] = bq - s;
+    else if (di != T(0)) x[q] = fma(bq - s, di, x[q]);
+  }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_resid_c_w(int r0, int r1, const int *__restrict__ rowptr,
-                                                      const int *__restrict__ colp,
-                                                      const T *__restrict__ pv,
-                                                      const T *__restrict__ b, T *x, T *r) {
-  k_resid_c_w_b<T>(blockIdx.x, gridDim.x, r0, r1, rowptr, colp, pv, b, x, r);
+__global__ void __launch_bounds__(32) k_gs_c_wp(int r0, const int *__restrict__ rowptr,
+                                                const int *__restrict__ colp,
+                                                const T *__restrict__ pv,
+                                                const T *__restrict__ dinv, const T *b, T *x) {
+  row_c_wp<T, false>(r0 + (int)blockIdx.x, rowptr, colp, pv, dinv, b, x, nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_resid_c_wp(int r0, const int *__restrict__ rowptr,
+                                                   const int *__restrict__ colp,
+                                                   const T *__restrict__ pv, const T *b, T *x,
+                                                   T *r) {
+  row_c_wp<T, true>(r0 + (int)blockIdx.x, rowptr, colp, pv, nullptr, b, x, r);
 }
 
 // r = b - A x over the rows [r0, r1) of the colour copy, a thread per row.
@@ -1415,6 +1456,7 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
   extern __shared__ __align__(128) unsigned char tma_smem[];
   TStage<T, CAPR> *st = reinterpret_cast<TStage<T, CAPR> *>(tma_smem);
   __shared__ __align__(8) uint64_t full[S], empty[S];
+  griddep_launch_dependents();   // the wells' rows after this colour (k_gs_c_wp, k_resid_c_wp)
   int ntile = (r1 - r0 + kTT - 1) / kTT;
   int mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (threadIdx.x == 0) {
@@ -1540,7 +1582,7 @@ static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv,
 // matrix does not change), so the next colour's tiles are already in
 // shared memory when its phase starts.  Long-row colours (the wells) take a
 // consumer warp per row.  Every row's arithmetic is that of k_gs_c_first,
-// k_gs_c and k_gs_c_w, so the sweep's result is theirs bit for bit.  The
+// k_gs_c and k_gs_c_wp, so the sweep's result is theirs bit for bit.  The
 // barrier counts arrivals on bar[0] (the k-th barrier is passed at (k+1)
 // gridDim.x arrivals) and the last CTA to finish resets it (with bar[1],
 // the exit count) for the next launch; its waits, like the pipeline's,
@@ -1751,6 +1793,7 @@ static int l0_lanes(const Sim *s) {
 template <typename T>
 static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = false,
                       bool preset = false) {
+  RegionScope region(s, "sweep.gs");   // the sweep's launches, timed as one
   int nc = s->ncolour, G = l0_lanes<T>(s);
   if (G <= -4 && nc + 1 <= kSweepPhases) {   // the whole sweep in one launch
     SweepPlan plan{};
@@ -1798,8 +1841,8 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
       continue;
     }
     if (lng(c))
-      DP_LAUNCH(s, k_gs_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
-                s->l0_colp, L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
+      DP_LAUNCH_PDL(s, k_gs_c_wp<T>, r1 - r0, 32, 0, r0, s->lu_rowptr, s->l0_colp,
+                    L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
     else if (G > 1) {
       DP_SWITCH_G(G, DP_LAUNCH(s, (k_gs_cg<GG, T>), nblk((long long)(r1 - r0) * GG), kBlock,
                                      0, r0, r1, s->lu_rowptr, s->l0_colp, L0C<T>::pv(s),
@@ -1828,8 +1871,8 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
     int r1 = s->lu_cstart[c1];
     if (r1 > r0) {
       if (lng)
-        DP_LAUNCH(s, k_resid_c_w<T>, nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, s->lu_rowptr,
-                  s->l0_colp, L0C<T>::pv(s), b, (T *)x, r);
+        DP_LAUNCH_PDL(s, k_resid_c_wp<T>, r1 - r0, 32, 0, r0, s->lu_rowptr, s->l0_colp,
+                      L0C<T>::pv(s), b, (T *)x, r);
       else if (G > 1) {
         DP_SWITCH_G(G, DP_LAUNCH(s, (k_resid_cg<GG, T>), nblk((long long)(r1 - r0) * GG),
                                        kBlock, 0, r0, r1, s->lu_rowptr, s->l0_colp,

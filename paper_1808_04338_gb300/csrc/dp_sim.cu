@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -84,6 +85,38 @@ LaunchScope::~LaunchScope() {
   cudaEventRecord(t.ev[t.used + 1], s->stream);
   t.used += 2;
   t.launches += 1;
+}
+
+// Event pairs are taken the same way for a region; its count is the number
+// of regions timed.
+RegionScope::RegionScope(Sim *sim, const char *name) : s(sim), timed(false) {
+  Timing &t = s->timing;
+  if (t.kernel_id < 0 || t.name != name) return;
+  if (t.used + 2 > t.ev.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      t.ev.push_back(e);
+    }
+  }
+  cudaEventRecord(t.ev[t.used], s->stream);
+  timed = true;
+}
+
+RegionScope::~RegionScope() {
+  if (!timed) return;
+  Timing &t = s->timing;
+  cudaEventRecord(t.ev[t.used + 1], s->stream);
+  t.used += 2;
+  t.launches += 1;
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char *v = std::getenv("DPSIM_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
 }
 
 // A realisation whose allocator failed, or that met a CUDA failure, does no
