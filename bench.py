@@ -109,6 +109,37 @@ def assembly_bytes(nb, nnzb, nc):
     return 44 * nnzb + 56 * nc + 24 * nb
 
 
+def coarse_cycle_bytes(levels, precision):
+    """Algorithmic bytes of the part of one V-cycle below level 0 (levels
+    1 .. L-1, the region "cycle.coarse"): per level above the coarsest, the
+    pre-smoothing with its residual (the operator once: 4 B column and the
+    value per entry, 4 B row pointer a row, b and 1/a_ii read, x and r
+    written: 16 B a row), the restriction (P's entries as R's, R's row
+    pointers, r read, the coarse b written), the prolongation (P's entries
+    and row pointers, the coarse x read, x read and written) and the
+    post-smoothing (the operator once more, b, 1/a_ii and x read, the result
+    written: 16 B a row); on the coarsest level the dense FP64 inverse and
+    b, x (or, smoothed there, the two sweeps).  Values are FP32, or BF16 on
+    levels 1 .. L-2 with precision 2."""
+    total = 0
+    nl = len(levels)
+    for l in range(1, nl):
+        L = levels[l]
+        n, nnz = L["n"], L["nnz"]
+        vb = 2 if precision == 2 and l <= nl - 2 else 4
+        if l == nl - 1:
+            if L["smoother"] == 2:
+                total += 8 * n * n + 8 * n
+            else:
+                total += 2 * ((4 + vb) * nnz + 4 * (n + 1) + 16 * n)
+            continue
+        nagg, pn = L["nagg"], L["p_nnz"]
+        total += 2 * ((4 + vb) * nnz + 4 * (n + 1) + 16 * n)          # both smoothings
+        total += (4 + vb) * pn + 4 * (nagg + 1) + 4 * n + 4 * nagg    # restriction
+        total += (4 + vb) * pn + 4 * (n + 1) + 4 * nagg + 8 * n       # prolongation
+    return total
+
+
 def state_error(a, b):
     """Max |dp| / max |p| and max |ds_w| between two states."""
     import numpy as np
@@ -820,6 +851,22 @@ def main():
                 sweeps[name]["timed_as"] = ("one event pair around each whole sweep ("
                                             + region + "), its launches back to back")
 
+    # the V-cycle below level 0 as one region per V-cycle (its kernels are
+    # small and latency-bound: the figure is their share of the copy rate)
+    coarse = None
+    levels = sim.amg_level_sizes()
+    if len(levels) > 1:
+        sim.time_kernel("cycle.coarse")
+        sim.kernel_timing(reset=True)
+        timestep(sim, opts)
+        t_ms, t_n = sim.kernel_timing(reset=True)
+        sim.time_kernel(None)
+        if t_n:
+            nbytes = coarse_cycle_bytes(levels, args.precision)
+            coarse = {"ms_per_cycle": t_ms / t_n, "cycles": t_n, "bytes_per_cycle": nbytes,
+                      "achieved_gbs": nbytes * t_n / (t_ms / 1000.0) / 1e9,
+                      "levels": [[L["n"], L["nnz"], L["p_nnz"]] for L in levels[1:]]}
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     hp = torch.from_numpy(prob.p0).pin_memory()
     hs = torch.from_numpy(prob.sw0).pin_memory()
@@ -957,6 +1004,7 @@ def main():
             "sweeps": {k: dict(v, frac=v["achieved_gbs"] / peak) for k, v in sweeps.items()},
             "assembly": dict(assembly, frac=assembly["achieved_gbs"] / peak)
                         if "achieved_gbs" in assembly else assembly,
+            "coarse_cycle": dict(coarse, frac=coarse["achieved_gbs"] / peak) if coarse else None,
             "errors_vs_oracle": errors,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_all / e2e_s if e2e_steps else None, "unit": UNIT,

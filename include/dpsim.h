@@ -454,11 +454,21 @@ int sim_well_rates(dp_sim *sim, double *q_oil, double *q_water);
 int sim_amg_level_info(dp_sim *sim, int32_t level, int32_t *n, int32_t *nnz, int32_t *nagg);
 int sim_amg_level_arrays(dp_sim *sim, int32_t level, int32_t *rowptr, int32_t *col,
                          double *val, int32_t *agg, int32_t *colour);
+/* Entries of level `level`'s prolongation P (n x nagg; R = P^T has as
+ * many; 0 on the coarsest level) and how the V-cycle treats the level:
+ * 0 Gauss-Seidel, 1 l1-Jacobi, 2 a direct solve (the coarsest level's dense
+ * inverse or LU); returns the number of levels.  For the algorithmic bytes
+ * of a V-cycle.  Either pointer may be NULL; DP_EINVAL as
+ * sim_amg_level_info. */
+int sim_amg_transfer_info(dp_sim *sim, int32_t level, int32_t *p_nnz, int32_t *smoother);
 
 /* Time every launch of one kernel (by name, e.g. "bsr_spmv") with CUDA
  * events on the simulation stream; NULL stops.  A name with a dot names a
  * region instead, timed from before its first launch to after its last:
- * "sweep.gs", each level-0 Gauss-Seidel sweep in the ILU(0) colour order.
+ * "sweep.gs", each level-0 Gauss-Seidel sweep in the ILU(0) colour order;
+ * "cycle.coarse", the part of each V-cycle below level 0 (its levels 1 and
+ * below, between level 0's restriction and prolongation) when level 0 runs
+ * in that order.
  * sim_kernel_timing returns the accumulated milliseconds and the count of
  * launches (regions) since the last reset. */
 int sim_time_kernel(dp_sim *sim, const char *name);

@@ -141,13 +141,16 @@ struct RegionScope {
 // stream: its CTAs may be scheduled once every CTA of that kernel has
 // triggered (griddepcontrol.launch_dependents) or exited, before that
 // kernel's completion.  The kernel must execute griddep_wait() before it
-// touches anything the kernel before it writes (launch_pdl, after Sim).
-#define DP_LAUNCH_PDL(sim, name, grid, block, smem, ...)                              \
+// touches anything the kernel before it writes, and write nothing before
+// it (launch_pdl, after Sim).  cls: kPdlWells, the level-0 well rows;
+// kPdlCoarse, the kernels of the V-cycle's transfers and coarse levels.
+#define DP_LAUNCH_PDL(sim, cls, name, grid, block, smem, ...)                         \
   do {                                                                               \
     if ((sim)->alloc_failed) break;                                                  \
     ::dp::LaunchScope ls__((sim), #name);                                            \
-    ::dp::launch_pdl((sim), name, dim3(grid), dim3(block), (smem), __VA_ARGS__);     \
+    ::dp::launch_pdl((sim), (cls), name, dim3(grid), dim3(block), (smem), __VA_ARGS__); \
   } while (0)
+constexpr int kPdlWells = 1, kPdlCoarse = 2;
 // Waits until the grids this one depends on have completed and their
 // writes are visible (a no-op in a kernel launched without the attribute).
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -157,7 +160,12 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
-bool pdl_enabled();   // off when the environment sets DPSIM_PDL=0
+// Which launches are programmatic dependents: DPSIM_PDL=0 none, 1 the well
+// rows, 2 also the coarse kernels, 3 (the default) also with the coarse
+// kernels letting their own dependents launch as soon as they have passed
+// their wait (pdl_trigger)
+int pdl_mode();
+inline bool pdl_trigger() { return pdl_mode() >= 3; }
 
 // Storage order of the Krylov operator's copy: locations in chunks of
 // kChunk; storage rows 2 kChunk c .. of chunk c hold its fracture rows (cells
@@ -412,7 +420,8 @@ struct Sim {
 };
 
 template <typename... P, typename... A>
-inline void launch_pdl(Sim *s, void (*k)(P...), dim3 grid, dim3 block, size_t smem, A &&... args) {
+inline void launch_pdl(Sim *s, int cls, void (*k)(P...), dim3 grid, dim3 block, size_t smem,
+                       A &&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -422,7 +431,7 @@ inline void launch_pdl(Sim *s, void (*k)(P...), dim3 grid, dim3 block, size_t sm
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cfg.numAttrs = pdl_mode() >= cls ? 1 : 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
   if (e != cudaSuccess) s->fail(DP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }

@@ -734,29 +734,150 @@ __global__ void __launch_bounds__(kBlock) k_gs_colour(int r0, int r1, const int 
   }
 }
 
+// ---- the V-cycle's transfer and coarse-level kernels as programmatic
+// dependents (launched by DP_LAUNCH_PDL): each loads what no kernel of a
+// V-cycle writes (row pointers, the first round of a row's columns and
+// values, 1/a_ii) before griddep_wait, and the vectors after it; with trig
+// set it then lets its own dependents launch.  Their arithmetic is that of
+// the batch's k_jacobi_pre_b, k_jacobi_sweep_b, k_csr_mv_b and k_dense_mv_b,
+// term for term.
+
+// the first round of a row's entries for G lanes: entries e0+lane+kG,
+// k = 0..3, those below e1
+template <int G, typename T, typename TV>
+struct RowHead {
+  int e, e1;
+  int c[4];
+  T v[4];
+  __device__ __forceinline__ void load(int e0, int e1_, int lane, const int *__restrict__ col,
+                                       const TV *__restrict__ val) {
+    e = e0 + lane;
+    e1 = e1_;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bool h = e + k * G < e1;
+      c[k] = h ? __ldg(col + e + k * G) : 0;
+      v[k] = h ? ldv<T>(val + e + k * G) : T(0);
+    }
+  }
+};
+
+// row_dot's sum (four accumulators, the remainder into the first) with
+// the head's entries taken from registers; X(c) is the vector entry.
+template <int G, typename T, typename TV, typename F>
+__device__ __forceinline__ T row_dot_head(const RowHead<G, T, TV> &h, const int *__restrict__ col,
+                                          const TV *__restrict__ val, F X) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int e = h.e, e1 = h.e1;
+  if (e + 3 * G < e1) {
+    s0 = fma(h.v[0], X(h.c[0]), s0);
+    s1 = fma(h.v[1], X(h.c[1]), s1);
+    s2 = fma(h.v[2], X(h.c[2]), s2);
+    s3 = fma(h.v[3], X(h.c[3]), s3);
+    for (e += 4 * G; e + 3 * G < e1; e += 4 * G) {
+      int c0 = __ldg(col + e), c1 = __ldg(col + e + G), c2 = __ldg(col + e + 2 * G),
+          c3 = __ldg(col + e + 3 * G);
+      T v0 = ldv<T>(val + e), v1 = ldv<T>(val + e + G), v2 = ldv<T>(val + e + 2 * G),
+        v3 = ldv<T>(val + e + 3 * G);
+      s0 = fma(v0, X(c0), s0);
+      s1 = fma(v1, X(c1), s1);
+      s2 = fma(v2, X(c2), s2);
+      s3 = fma(v3, X(c3), s3);
+    }
+    for (; e < e1; e += G) s0 = fma(ldv<T>(val + e), X(__ldg(col + e)), s0);
+  } else {   // at most three entries, all in the head
+    if (e < e1) s0 = fma(h.v[0], X(h.c[0]), s0);
+    if (e + G < e1) s0 = fma(h.v[1], X(h.c[1]), s0);
+    if (e + 2 * G < e1) s0 = fma(h.v[2], X(h.c[2]), s0);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
 // l1-Jacobi pre-smoothing from x = 0 fused with the residual: x_i = b_i d_i
 // and r_i = b_i - sum_j a_ij b_j d_j (d = 1 / sum_j |a_ij|, 0 for an empty row).
 template <int G, typename T, typename TV = T>
-__global__ void __launch_bounds__(kBlock) k_jacobi_pre(int n, const int *__restrict__ rowptr,
-                                                       const int *__restrict__ col,
-                                                       const TV *__restrict__ val,
-                                                       const T *__restrict__ d,
-                                                       const T *__restrict__ b, T *__restrict__ x,
-                                                       T *__restrict__ r) {
-  k_jacobi_pre_b<G, T, TV>(blockIdx.x, gridDim.x, n, rowptr, col, val, d, b, x, r);
+__global__ void __launch_bounds__(kBlock) k_jacobi_pre_p(int n, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col,
+                                                         const TV *__restrict__ val,
+                                                         const T *__restrict__ d, const T *b,
+                                                         T *x, T *r, int trig) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  RowHead<G, T, TV> h;
+  h.load(e0, e1, lane, col, val);
+  T di = valid && lane == 0 ? d[i] : T(0);
+  griddep_wait();
+  if (trig) griddep_launch_dependents();
+  T s = row_dot_head<G>(h, col, val, [&](int c) { return __ldg(b + c) * __ldg(d + c); });
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) {
+    T bi = b[i];
+    x[i] = bi * di;
+    r[i] = bi - s;
+  }
 }
 
 // One l1-Jacobi sweep: t_i = x_i + (b_i - (A x)_i) d_i for every row from
 // the old x (t must not alias x).
 template <int G, typename T, typename TV = T>
-__global__ void __launch_bounds__(kBlock) k_jacobi_sweep(int n, const int *__restrict__ rowptr,
-                                                         const int *__restrict__ col,
-                                                         const TV *__restrict__ val,
-                                                         const T *__restrict__ d,
-                                                         const T *__restrict__ b,
-                                                         const T *__restrict__ x,
-                                                         T *__restrict__ tout) {
-  k_jacobi_sweep_b<G, T, TV>(blockIdx.x, gridDim.x, n, rowptr, col, val, d, b, x, tout);
+__global__ void __launch_bounds__(kBlock) k_jacobi_sweep_p(int n, const int *__restrict__ rowptr,
+                                                           const int *__restrict__ col,
+                                                           const TV *__restrict__ val,
+                                                           const T *__restrict__ d, const T *b,
+                                                           const T *x, T *tout, int trig) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  RowHead<G, T, TV> h;
+  h.load(e0, e1, lane, col, val);
+  T di = valid && lane == 0 ? d[i] : T(0);
+  griddep_wait();
+  if (trig) griddep_launch_dependents();
+  T s = row_dot_head<G>(h, col, val, [&](int c) { return x[c]; });
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) tout[i] = fma(b[i] - s, di, x[i]);
+}
+
+// y = A x (add = 0) or y += A x (add = 1)
+template <int G, typename T, typename TV = T>
+__global__ void __launch_bounds__(kBlock) k_csr_mv_p(int n, const int *__restrict__ rowptr,
+                                                     const int *__restrict__ col,
+                                                     const TV *__restrict__ val, const T *x, T *y,
+                                                     int add, int trig) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = t / G, lane = t % G;
+  bool valid = i < n;
+  int e0 = valid ? rowptr[i] : 0, e1 = valid ? rowptr[i + 1] : 0;
+  RowHead<G, T, TV> h;
+  h.load(e0, e1, lane, col, val);
+  griddep_wait();
+  if (trig) griddep_launch_dependents();
+  T s = row_dot_head<G>(h, col, val, [&](int c) { return x[c]; });
+  if (G > 1) s = group_sum<G, T>(s);
+  if (valid && lane == 0) y[i] = add ? y[i] + s : s;
+}
+
+// x = inv b on the coarsest level, a warp per row, FP64 accumulation: the
+// row's first 64 entries of the inverse are loaded before the wait
+template <typename T>
+__global__ void k_dense_mv_p(int n, const double *__restrict__ inv, const T *b, T *x, int trig) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  bool valid = w < n;
+  const double *row = inv + (size_t)(valid ? w : 0) * n;
+  double a0 = valid && lane < n ? row[lane] : 0.0, a1 = valid && lane + 32 < n ? row[lane + 32] : 0.0;
+  griddep_wait();
+  if (trig) griddep_launch_dependents();
+  if (!valid) return;   // whole warps leave together
+  double s = 0.0;
+  if (lane < n) s = fma(a0, double(b[lane]), s);
+  if (lane + 32 < n) s = fma(a1, double(b[lane + 32]), s);
+  for (int j = lane + 64; j < n; j += 32) s = fma(row[j], double(b[j]), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[w] = T(s);
 }
 
 // r = b - A x
@@ -775,16 +896,6 @@ __global__ void __launch_bounds__(kBlock) k_csr_resid(int n, const int *__restri
   if (valid && lane == 0) r[i] = b[i] - s;
 }
 
-// y = A x (add = 0) or y += A x (add = 1)
-template <int G, typename T, typename TV = T>
-__global__ void __launch_bounds__(kBlock) k_csr_mv(int n, const int *__restrict__ rowptr,
-                                                   const int *__restrict__ col,
-                                                   const TV *__restrict__ val,
-                                                   const T *__restrict__ x, T *__restrict__ y,
-                                                   int add) {
-  griddep_launch_dependents();   // the wells' rows after a prolongation (k_gs_c_wp)
-  k_csr_mv_b<G, T, TV>(blockIdx.x, gridDim.x, n, rowptr, col, val, x, y, add);
-}
 
 // Lanes per row for a mean row length: enough lanes that each walks about
 // eight entries (two rounds of four loads in flight), no more, because on
@@ -849,12 +960,15 @@ static int csr_resid(Sim *s, const Level &L, const T *b, const T *x, T *r) {
   return DP_OK;
 }
 
+// y = A x or y += A x for the V-cycle's transfers, as a programmatic
+// dependent; trig: let the next launch start once past the wait (always
+// for level 0's prolongation, whose next launch is the wells' rows)
 template <typename T>
 static int csr_mv(Sim *s, int n, int G, const int *rowptr, const int *col, const T *val,
-                  const T *x, T *y, int add) {
+                  const T *x, T *y, int add, bool trig = pdl_trigger()) {
   long long thr = (long long)n * G;
-  DP_SWITCH_G(G, DP_LAUNCH(s, (k_csr_mv<GG, T>), nblk(thr), kBlock, 0, n, rowptr, col, val, x, y,
-                           add));
+  DP_SWITCH_G(G, DP_LAUNCH_PDL(s, kPdlCoarse, (k_csr_mv_p<GG, T>), nblk(thr), kBlock, 0, n, rowptr,
+                               col, val, x, y, add, (int)trig));
   return DP_OK;
 }
 
@@ -865,8 +979,9 @@ static int transfer_mv(Sim *s, int n, int G, const int *rowptr, const int *col, 
   if constexpr (std::is_same<T, float>::value) {
     if (use_bf16<T>(valh)) {
       long long thr = (long long)n * G;
-      DP_SWITCH_G(G, DP_LAUNCH(s, (k_csr_mv<GG, float, __nv_bfloat16>), nblk(thr), kBlock, 0, n,
-                               rowptr, col, valh, x, y, add));
+      DP_SWITCH_G(G, DP_LAUNCH_PDL(s, kPdlCoarse, (k_csr_mv_p<GG, float, __nv_bfloat16>),
+                                   nblk(thr), kBlock, 0, n, rowptr, col, valh, x, y, add,
+                                   (int)pdl_trigger()));
       return DP_OK;
     }
   }
@@ -985,12 +1100,6 @@ __global__ void k_dense_inverse(int n, const double *a, const int *piv, double *
   }
 }
 
-// x = inv b, one warp per row, FP64 accumulation
-template <typename T>
-__global__ void k_dense_mv(int n, const double *__restrict__ inv, const T *__restrict__ b,
-                           T *__restrict__ x) {
-  k_dense_mv_b<T>(blockIdx.x, gridDim.x, n, inv, b, x);
-}
 
 int coarse_factor(Sim *s) {
   Level &L = s->lev.back();
@@ -1020,19 +1129,22 @@ int coarse_factor(Sim *s) {
 }
 
 // l1-Jacobi: pre-smoothing from zero fused with the residual into r, and a
-// sweep after the coarse correction through r (free by then) back into x.
+// sweep after the coarse correction into r (free by then), where the
+// prolongation of the level above reads the result.
 template <typename T>
 static int jacobi_pre(Sim *s, Level &L, const T *b, T *x, T *r) {
   long long thr = (long long)L.n * L.G;
   if constexpr (std::is_same<T, float>::value) {
     if (use_bf16<T>(L.valh)) {
-      DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_pre<GG, float, __nv_bfloat16>), nblk(thr), kBlock, 0,
-                                 L.n, L.rowptr, L.col, L.valh, L.dinvf, b, x, r));
+      DP_SWITCH_G(L.G, DP_LAUNCH_PDL(s, kPdlCoarse, (k_jacobi_pre_p<GG, float, __nv_bfloat16>),
+                                     nblk(thr), kBlock, 0, L.n, L.rowptr, L.col, L.valh, L.dinvf,
+                                     b, x, r, (int)pdl_trigger()));
       return DP_OK;
     }
   }
-  DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_pre<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
-                             L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
+  DP_SWITCH_G(L.G, DP_LAUNCH_PDL(s, kPdlCoarse, (k_jacobi_pre_p<GG, T>), nblk(thr), kBlock, 0,
+                                 L.n, L.rowptr, L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r,
+                                 (int)pdl_trigger()));
   return DP_OK;
 }
 
@@ -1042,15 +1154,16 @@ static int jacobi_post(Sim *s, Level &L, const T *b, T *x, T *r) {
   bool done = false;
   if constexpr (std::is_same<T, float>::value) {
     if (use_bf16<T>(L.valh)) {
-      DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_sweep<GG, float, __nv_bfloat16>), nblk(thr), kBlock,
-                                 0, L.n, L.rowptr, L.col, L.valh, L.dinvf, b, x, r));
+      DP_SWITCH_G(L.G, DP_LAUNCH_PDL(s, kPdlCoarse, (k_jacobi_sweep_p<GG, float, __nv_bfloat16>),
+                                     nblk(thr), kBlock, 0, L.n, L.rowptr, L.col, L.valh, L.dinvf,
+                                     b, x, r, (int)pdl_trigger()));
       done = true;
     }
   }
   if (!done)
-    DP_SWITCH_G(L.G, DP_LAUNCH(s, (k_jacobi_sweep<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
-                               L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
-  DP_CUDA(s, cudaMemcpyAsync(x, r, (size_t)L.n * sizeof(T), cudaMemcpyDeviceToDevice, s->stream));
+    DP_SWITCH_G(L.G, DP_LAUNCH_PDL(s, kPdlCoarse, (k_jacobi_sweep_p<GG, T>), nblk(thr), kBlock,
+                                   0, L.n, L.rowptr, L.col, LV<T>::val(L), LV<T>::dinv(L), b, x,
+                                   r, (int)pdl_trigger()));
   return DP_OK;
 }
 
@@ -1841,7 +1954,7 @@ static int gs_sweep_c(Sim *s, const T *b, T *x, bool forward, bool from_zero = f
       continue;
     }
     if (lng(c))
-      DP_LAUNCH_PDL(s, k_gs_c_wp<T>, r1 - r0, 32, 0, r0, s->lu_rowptr, s->l0_colp,
+      DP_LAUNCH_PDL(s, kPdlWells, k_gs_c_wp<T>, r1 - r0, 32, 0, r0, s->lu_rowptr, s->l0_colp,
                     L0C<T>::pv(s), L0C<T>::dinv(s), b, x);
     else if (G > 1) {
       DP_SWITCH_G(G, DP_LAUNCH(s, (k_gs_cg<GG, T>), nblk((long long)(r1 - r0) * GG), kBlock,
@@ -1871,7 +1984,7 @@ static int resid_c(Sim *s, const T *b, const T *x, T *r) {
     int r1 = s->lu_cstart[c1];
     if (r1 > r0) {
       if (lng)
-        DP_LAUNCH_PDL(s, k_resid_c_wp<T>, r1 - r0, 32, 0, r0, s->lu_rowptr, s->l0_colp,
+        DP_LAUNCH_PDL(s, kPdlWells, k_resid_c_wp<T>, r1 - r0, 32, 0, r0, s->lu_rowptr, s->l0_colp,
                       L0C<T>::pv(s), b, (T *)x, r);
       else if (G > 1) {
         DP_SWITCH_G(G, DP_LAUNCH(s, (k_resid_cg<GG, T>), nblk((long long)(r1 - r0) * GG),
@@ -1935,20 +2048,28 @@ static int gs_sweep(Sim *s, Level &L, const T *b, T *x, bool forward) {
 // V(1,1) cycle from level l in precision T: pre-smoothing (colours forward,
 // or one l1-Jacobi sweep), residual, restriction, coarse correction,
 // prolongation, post-smoothing (colours reversed, or one l1-Jacobi sweep);
-// dense LU on the coarsest level.
+// dense LU on the coarsest level.  *res: where the result is, x or, after an
+// l1-Jacobi post-smoothing (which cannot run in place), the level's r; the
+// prolongation above reads it there.
 // x_preset: level 0 in colour order and the pre-smoothing's first colour
 // (and x = 0 on the other rows) already written with b (X0Init)
 template <typename T>
-static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
+static int vcycle_r(Sim *s, int l, const T *b, T *x, const T **res, bool x_preset = false) {
+  *res = x;
   if (l == s->cl_level) return coarse_cycle<T>(s, l, b, x);
+  const T *nres = nullptr;
   if (l == 0 && l0c_on(s)) {   // b and x in colour order
     Level &L = s->lev[0], &N = s->lev[1];
     T *r = LV<T>::r(L), *nb = LV<T>::b(N), *nx = LV<T>::x(N);
     DP_TRY(gs_sweep_c<T>(s, b, x, true, true, x_preset));   // from x = 0
     DP_TRY(resid_c<T>(s, b, x, r));
     DP_TRY(csr_mv<T>(s, N.n, L.r_G, L.r_rowptr, s->r0_colp, LV<T>::rval(L), r, nb, 0));
-    DP_TRY(vcycle_t<T>(s, 1, nb, nx));
-    DP_TRY(csr_mv<T>(s, L.n, L.p_G, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nx, x, 1));
+    {
+      RegionScope region(s, "cycle.coarse");   // levels 1 and below, timed as one
+      DP_TRY(vcycle_r<T>(s, 1, nb, nx, &nres));
+    }
+    DP_TRY(csr_mv<T>(s, L.n, L.p_G, s->p0c_rowptr, s->p0c_col, L0C<T>::pval(s), nres, x, 1,
+                     true));
     return gs_sweep_c<T>(s, b, x, false);
   }
   Level &L = s->lev[l];
@@ -1956,7 +2077,8 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
   if (l == (int)s->lev.size() - 1) {
     if (s->coarse_n == n && n > 0) {
       if (s->coarse_inv)
-        DP_LAUNCH(s, k_dense_mv<T>, nblk(32LL * n), kBlock, 0, n, s->coarse_inv, b, x);
+        DP_LAUNCH_PDL(s, kPdlCoarse, k_dense_mv_p<T>, nblk(32LL * n), kBlock, 0, n,
+                      s->coarse_inv, b, x, (int)pdl_trigger());
       else
         DP_LAUNCH(s, k_dense_solve<T>, 1, 1024, 0, n, s->coarse_lu, s->coarse_piv, b, x);
       return DP_OK;
@@ -1964,6 +2086,7 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
     if (L.l1) {
       DP_TRY(jacobi_pre<T>(s, L, b, x, LV<T>::r(L)));
       DP_TRY(jacobi_post<T>(s, L, b, x, LV<T>::r(L)));
+      *res = LV<T>::r(L);
       return DP_OK;
     }
     DP_CUDA(s, cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), s->stream));
@@ -1981,10 +2104,25 @@ static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
     DP_TRY(csr_resid<T>(s, L, b, x, r));
   }
   DP_TRY(transfer_mv<T>(s, N.n, L.r_G, L.r_rowptr, L.r_col, LV<T>::rval(L), L.r_valh, r, nb, 0));
-  DP_TRY(vcycle_t<T>(s, l + 1, nb, nx));
-  DP_TRY(transfer_mv<T>(s, n, L.p_G, L.p_rowptr, L.p_col, LV<T>::pval(L), L.p_valh, nx, x, 1));
-  if (L.l1) DP_TRY(jacobi_post<T>(s, L, b, x, r));
-  else DP_TRY(gs_sweep<T>(s, L, b, x, false));
+  DP_TRY(vcycle_r<T>(s, l + 1, nb, nx, &nres));
+  DP_TRY(transfer_mv<T>(s, n, L.p_G, L.p_rowptr, L.p_col, LV<T>::pval(L), L.p_valh, nres, x, 1));
+  if (L.l1) {
+    DP_TRY(jacobi_post<T>(s, L, b, x, r));
+    *res = r;
+  } else {
+    DP_TRY(gs_sweep<T>(s, L, b, x, false));
+  }
+  return DP_OK;
+}
+
+// the V-cycle with its result in x
+template <typename T>
+static int vcycle_t(Sim *s, int l, const T *b, T *x, bool x_preset = false) {
+  const T *res = x;
+  DP_TRY(vcycle_r<T>(s, l, b, x, &res, x_preset));
+  if (res != x)
+    DP_CUDA(s, cudaMemcpyAsync(x, res, (size_t)s->lev[l].n * sizeof(T), cudaMemcpyDeviceToDevice,
+                               s->stream));
   return DP_OK;
 }
 
@@ -2046,8 +2184,9 @@ static int tune_level(Sim *s, int l, int reps, std::string &rep) {
   auto op = [&](int g) -> int {
     long long thr = (long long)L.n * g;
     if (L.l1) {
-      DP_SWITCH_G(g, DP_LAUNCH(s, (k_jacobi_sweep<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
-                               L.col, LV<T>::val(L), LV<T>::dinv(L), b, x, r));
+      DP_SWITCH_G(g, DP_LAUNCH_PDL(s, kPdlCoarse, (k_jacobi_sweep_p<GG, T>), nblk(thr), kBlock,
+                                   0, L.n, L.rowptr, L.col, LV<T>::val(L), LV<T>::dinv(L), b, x,
+                                   r, (int)pdl_trigger()));
     } else {
       DP_SWITCH_G(g, DP_LAUNCH(s, (k_csr_resid<GG, T>), nblk(thr), kBlock, 0, L.n, L.rowptr,
                                L.col, LV<T>::val(L), b, x, r));

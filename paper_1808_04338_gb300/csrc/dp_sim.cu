@@ -111,12 +111,12 @@ RegionScope::~RegionScope() {
   t.launches += 1;
 }
 
-bool pdl_enabled() {
-  static const bool on = [] {
+int pdl_mode() {
+  static const int mode = [] {
     const char *v = std::getenv("DPSIM_PDL");
-    return !(v && v[0] == '0');
+    return v && v[0] >= '0' && v[0] <= '3' && !v[1] ? v[0] - '0' : 3;
   }();
-  return on;
+  return mode;
 }
 
 // A realisation whose allocator failed, or that met a CUDA failure, does no
@@ -799,6 +799,16 @@ extern "C" int sim_amg_level_info(dp_sim *s, int32_t level, int32_t *n, int32_t 
   if (n) *n = L.n;
   if (nnz) *nnz = L.nnz;
   if (nagg) *nagg = L.nagg;
+  return (int)s->lev.size();
+}
+
+extern "C" int sim_amg_transfer_info(dp_sim *s, int32_t level, int32_t *p_nnz,
+                                     int32_t *smoother) {
+  if (!s || !s->amg_ready || level < 0 || level >= (int)s->lev.size()) return DP_EINVAL;
+  const Level &L = s->lev[level];
+  bool last = level + 1 == (int)s->lev.size();
+  if (p_nnz) *p_nnz = last ? 0 : L.p_nnz;
+  if (smoother) *smoother = last && s->coarse_n == L.n && L.n > 0 ? 2 : L.l1 ? 1 : 0;
   return (int)s->lev.size();
 }
 

@@ -153,6 +153,7 @@ def load():
     L.sim_well_rates.argtypes = [P, P, P]
     L.sim_amg_level_info.argtypes = [P, I, P, P, P]
     L.sim_amg_level_arrays.argtypes = [P, I, P, P, P, P, P]
+    L.sim_amg_transfer_info.argtypes = [P, I, P, P]
     L.sim_time_kernel.argtypes = [P, C.c_char_p]
     L.sim_kernel_timing.argtypes = [P, P, P, I]
     L.sim_launch_count.argtypes = [P]
@@ -622,6 +623,28 @@ class Sim:
                                                _p(d["val"]), _p(d["agg"]), _p(d["colour"])),
                         "sim_amg_level_arrays")
             out.append(d)
+            lev += 1
+            if lev >= nl:
+                break
+        return out
+
+    def amg_level_sizes(self):
+        """Per AMG level: dict(n, nnz, nagg, p_nnz, smoother) without the
+        arrays (sim_amg_level_info, sim_amg_transfer_info; smoother 0
+        Gauss-Seidel, 1 l1-Jacobi, 2 direct solve)."""
+        L = load()
+        out = []
+        lev = 0
+        while True:
+            n, nnz, nagg = C.c_int32(), C.c_int32(), C.c_int32()
+            pn, sm = C.c_int32(), C.c_int32()
+            nl = L.sim_amg_level_info(self.h, lev, C.byref(n), C.byref(nnz), C.byref(nagg))
+            if nl < 0:
+                break
+            self._check(L.sim_amg_transfer_info(self.h, lev, C.byref(pn), C.byref(sm)),
+                        "sim_amg_transfer_info")
+            out.append(dict(n=n.value, nnz=nnz.value, nagg=nagg.value, p_nnz=pn.value,
+                            smoother=sm.value))
             lev += 1
             if lev >= nl:
                 break

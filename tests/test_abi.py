@@ -69,6 +69,9 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert L.sim_run(None, 1.0, 1.0, 1.0, 0.1, 10, None) == dpsim.DP_EINVAL
     assert L.sim_autotune(None, 1, None, 0) == dpsim.DP_EINVAL
     assert L.sim_set_l0_kernel(None, 1) == dpsim.DP_EINVAL
+    assert L.sim_amg_level_info(None, 0, None, None, None) == dpsim.DP_EINVAL
+    assert L.sim_amg_transfer_info(None, 0, None, None) == dpsim.DP_EINVAL
+    assert L.sim_time_kernel(None, b"sweep.gs") == dpsim.DP_EINVAL
     bat = ctypes.c_void_p()
     assert L.batch_create(None, 0, None, ctypes.byref(bat)) == dpsim.DP_EINVAL
     assert L.batch_advance(None, None, None, None) == dpsim.DP_EINVAL
