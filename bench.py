@@ -33,9 +33,12 @@ METRIC = "CPR-FPF Newton-step solve time & HBM GB/s at 8M unknowns; served p99 l
 UNIT = "Newton-step solves/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TIMED_KERNEL = "k_bsr_spmv<0>"
-# DRAM bytes (read + written) per launch of TIMED_KERNEL on the 200x200x50 field, from the
-# ncu capture summarised in profiles/bsr_spmv_field200x200x50_dram.md (this kernel version)
-TIMED_TRAFFIC = {(200, 200, 50, 0): 795957760 + 56835072}
+# DRAM bytes (read + written) per launch of TIMED_KERNEL on the 200x200x50 field: one
+# launch captured on the 200x200x20 field (316,643,072 + 21,299,968 bytes against its
+# 342,181,804 algorithmic bytes, profiles/bsr_spmv_field200x200x20_dram.md), scaled by the
+# algorithmic bytes of a 200x200x50 launch (859,771,804): the kernel streams every block
+# once, so its traffic grows with them
+TIMED_TRAFFIC = {(200, 200, 50, 0): round((316643072 + 21299968) * 859771804 / 342181804)}
 
 
 def workload(args):

@@ -262,7 +262,6 @@ __device__ __forceinline__ void k_bsr_spmv_b(int bx, int gx, int n, int nL, int 
     spmv_well_rows<MODE>(n, nlong, rowptr, col, val, x, b, y);
     return;
   }
-  __shared__ double sh[kBlock];
   int q0 = (bx - 1) * (kBlock / 2);
   int comp = threadIdx.x & 1, q = q0 + (threadIdx.x >> 1);
   if (q < nlong) {
@@ -278,13 +277,12 @@ __device__ __forceinline__ void k_bsr_spmv_b(int bx, int gx, int n, int nL, int 
       s = fma(a.x, xj.x, s);
       s = fma(a.y, xj.y, s);
     }
-    sh[2 * (row - q0) + comp] = s;
-  }
-  __syncthreads();
-  int cnt = nlong - q0 < kBlock / 2 ? nlong - q0 : kBlock / 2;
-  if ((int)threadIdx.x < 2 * cnt) {
-    size_t k = 2 * (size_t)q0 + threadIdx.x;
-    y[k] = MODE == 0 ? sh[threadIdx.x] : b[k] - sh[threadIdx.x];
+    // each warp stores its own rows: a fracture row's and the matrix row's
+    // halves of a 32-byte sector of y come from warps of the same CTA, a
+    // few microseconds apart, and meet in L2 before it is written back; no
+    // CTA barrier holds the short matrix-row warps for the fracture rows
+    size_t k = 2 * (size_t)row + comp;
+    y[k] = MODE == 0 ? s : b[k] - s;
   }
 }
 
@@ -319,7 +317,6 @@ __device__ __forceinline__ void k_bsr_resid_f32_b(int bx, int gx, int n, int nL,
     }
     return;
   }
-  __shared__ float sh[kBlock];
   int q0 = (bx - 1) * (kBlock / 2);
   int comp = threadIdx.x & 1, q = q0 + (threadIdx.x >> 1);
   if (q < nlong) {
@@ -333,13 +330,8 @@ __device__ __forceinline__ void k_bsr_resid_f32_b(int bx, int gx, int n, int nL,
       s = fmaf(a.x, xj.x, s);
       s = fmaf(a.y, xj.y, s);
     }
-    sh[2 * (row - q0) + comp] = s;
-  }
-  __syncthreads();
-  int cnt = nlong - q0 < kBlock / 2 ? nlong - q0 : kBlock / 2;
-  if ((int)threadIdx.x < 2 * cnt) {
-    size_t k = 2 * (size_t)q0 + threadIdx.x;
-    y[k] = float(b[k]) - sh[threadIdx.x];
+    size_t k = 2 * (size_t)row + comp;   // stored by its own warp, as in k_bsr_spmv_b
+    y[k] = float(b[k]) - s;
   }
 }
 
@@ -390,8 +382,7 @@ __device__ __forceinline__ void k_bsr_presid_f32_b(int bx, int gx, int n, int nL
     }
     return;
   }
-  __shared__ float sh[kBlock];
-  int q0 = (bx - 1) * kBlock, t = q0 + threadIdx.x;
+  int t = (bx - 1) * kBlock + threadIdx.x;
   if (t < nlong) {
     int row = row_of_pair(t, nL, nc);
     int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
@@ -403,10 +394,9 @@ __device__ __forceinline__ void k_bsr_presid_f32_b(int bx, int gx, int n, int nL
       s = fmaf(a.x, xj.x, s);
       s = fmaf(a.y, xj.y, s);
     }
-    sh[row - q0] = s;
+    // stored by its own thread at its natural row's place, as in k_bsr_spmv_b
+    put_b0(rp, omap ? __ldg(omap + row) : row, float(b[2 * (size_t)row]) - s, xi);
   }
-  __syncthreads();
-  if (t < nlong) put_b0(rp, omap ? __ldg(omap + t) : t, float(b[2 * (size_t)t]) - sh[threadIdx.x], xi);
 }
 
 template <typename T, typename TR>

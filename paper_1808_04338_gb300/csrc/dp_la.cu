@@ -24,10 +24,14 @@ namespace dp {
 // The operator is read from its storage-order copy (chunks of fracture rows
 // then matrix rows, then wells): pair q processes storage row q, whose
 // blocks are contiguous with those of pair q+1.  A CTA takes 128 storage
-// rows, which are, as a set, the natural rows q0..q0+127; the results meet
-// in shared memory at their natural position and leave in one coalesced
-// write (a direct store to natural row row_of_pair(q) would write half
-// sectors: the fracture and matrix rows of a location are 16 bytes apart).
+// rows, which are, as a set, the natural rows q0..q0+127, and each lane
+// stores its result at natural row row_of_pair(q): the fracture and matrix
+// rows of a location are 16 bytes apart, so a 32-byte sector of y is
+// written in halves by two warps of the same CTA, which meet in L2 (DRAM
+// sees whole sectors).  Staging the results in shared memory for one
+// coalesced store instead made the short matrix-row warps wait at the CTA
+// barrier for the fracture rows (0.170 against 0.151 ms a product at 8M
+// unknowns).
 
 
 template <int MODE>  // MODE 0: y = A x; 1: y = b - A x
@@ -131,9 +135,9 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
     return;
   }
   // a CTA takes storage rows q0..q0+255 (two chunks: the natural rows
-  // q0..q0+255 as a set) and writes rp through shared memory, coalesced
-  __shared__ double sh[kBlock];
-  int q0 = (blockIdx.x - 1) * kBlock, t = q0 + threadIdx.x;
+  // q0..q0+255 as a set); each thread stores its own row's result (the
+  // fracture and matrix halves of a sector meet in L2, as in k_bsr_spmv)
+  int t = (blockIdx.x - 1) * kBlock + threadIdx.x;
   if (t < nlong) {
     int row = row_of_pair(t, nL, nc);
     int e0 = __ldg(rowptr + t), e1 = __ldg(rowptr + t + 1);
@@ -145,10 +149,8 @@ __global__ void __launch_bounds__(kBlock) k_bsr_presid(int n, int nL, int nc, in
       s = fma(__ldg(a00 + e), xj.x, s);
       s = fma(__ldg(a01 + e), xj.y, s);
     }
-    sh[row - q0] = s;
+    rp[omap ? __ldg(omap + row) : row] = b[2 * (size_t)row] - s;
   }
-  __syncthreads();
-  if (t < nlong) rp[omap ? __ldg(omap + t) : t] = b[2 * (size_t)t] - sh[threadIdx.x];
 }
 
 // Residuals inside the CPR preconditioner with the FP32 preconditioner
