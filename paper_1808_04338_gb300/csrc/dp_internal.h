@@ -160,12 +160,12 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
-// Which launches are programmatic dependents: DPSIM_PDL=0 none, 1 the well
-// rows, 2 also the coarse kernels, 3 (the default) also with the coarse
-// kernels letting their own dependents launch as soon as they have passed
-// their wait (pdl_trigger)
+// Which launches are programmatic dependents, a bit mask (the environment's
+// DPSIM_PDL, by default all): the classes above, and 4, the dependents'
+// own dependents let in as soon as they have passed their wait
+// (pdl_trigger)
 int pdl_mode();
-inline bool pdl_trigger() { return pdl_mode() >= 3; }
+inline bool pdl_trigger() { return (pdl_mode() & 4) != 0; }
 
 // Storage order of the Krylov operator's copy: locations in chunks of
 // kChunk; storage rows 2 kChunk c .. of chunk c hold its fracture rows (cells
@@ -431,7 +431,7 @@ inline void launch_pdl(Sim *s, int cls, void (*k)(P...), dim3 grid, dim3 block, 
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = pdl_mode() >= cls ? 1 : 0;
+  cfg.numAttrs = (pdl_mode() & cls) ? 1 : 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
   if (e != cudaSuccess) s->fail(DP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }

@@ -114,7 +114,9 @@ RegionScope::~RegionScope() {
 int pdl_mode() {
   static const int mode = [] {
     const char *v = std::getenv("DPSIM_PDL");
-    return v && v[0] >= '0' && v[0] <= '3' && !v[1] ? v[0] - '0' : 3;
+    char *end = nullptr;
+    long m = v ? std::strtol(v, &end, 10) : -1;
+    return v && *v && end && !*end && m >= 0 && m <= 7 ? (int)m : 7;
   }();
   return mode;
 }
