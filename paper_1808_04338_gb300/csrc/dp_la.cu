@@ -1380,6 +1380,7 @@ __device__ __forceinline__ void row_c_wp(int q, const int *__restrict__ rowptr,
   int c0 = h0 ? __ldg(colp + e) : 0, c1 = h1 ? __ldg(colp + e + 32) : 0;
   T di = (!RESID && lane == 0) ? dinv[q] : T(0);
   griddep_wait();
+  griddep_launch_dependents();   // the colour launch after the wells (backward sweep)
   T bq = lane == 0 ? b[q] : T(0);
   T s = T(0);
   if (h1) {
@@ -1592,6 +1593,10 @@ __device__ __forceinline__ void sweep_tma_body(int r0, int r1, const int *__rest
   volatile int *abort_v = &abort_flag;
   if (t == 0) abort_flag = 0;
   consumers_sync();
+  // launched as a programmatic dependent (kPdlL0), the producer has been
+  // bringing in the operator's tiles, which no kernel of the cycle writes,
+  // while the kernel before finished; b and x are read after this
+  griddep_wait();
   for (int i = 0; i < mine; ++i) {
     int k = i % S;
     int q0 = r0 + ((int)blockIdx.x + i * (int)gridDim.x) * kTT, nrow = min(kTT, r1 - q0);
@@ -1661,15 +1666,16 @@ static int tma_grid(K kern, int smem, int rows) {
 template <typename T, int S, int CAPR>
 static void gs_tma(Sim *s, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x) {
   constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
-  DP_LAUNCH(s, (k_gs_c_tma<T, S, CAPR>), (tma_grid<16 * S + CAPR>(k_gs_c_tma<T, S, CAPR>, smem, r1 - r0)),
-            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err);
+  DP_LAUNCH_PDL(s, kPdlL0, (k_gs_c_tma<T, S, CAPR>),
+                (tma_grid<16 * S + CAPR>(k_gs_c_tma<T, S, CAPR>, smem, r1 - r0)), kTT + 32, smem, r0,
+                r1, s->lu_rowptr, s->l0_colp, pv, dinv, b, x, s->dev_err);
 }
 template <typename T, int S, int CAPR>
 static void resid_tma(Sim *s, int r0, int r1, const T *pv, const T *b, T *x, T *r) {
   constexpr int smem = S * (int)sizeof(TStage<T, CAPR>);
-  DP_LAUNCH(s, (k_resid_c_tma<T, S, CAPR>),
-            (tma_grid<16 * S + CAPR>(k_resid_c_tma<T, S, CAPR>, smem, r1 - r0)),
-            kTT + 32, smem, r0, r1, s->lu_rowptr, s->l0_colp, pv, b, x, r, s->dev_err);
+  DP_LAUNCH_PDL(s, kPdlL0, (k_resid_c_tma<T, S, CAPR>),
+                (tma_grid<16 * S + CAPR>(k_resid_c_tma<T, S, CAPR>, smem, r1 - r0)), kTT + 32, smem,
+                r0, r1, s->lu_rowptr, s->l0_colp, pv, b, x, r, s->dev_err);
 }
 template <typename T>
 static void sweep_tma(Sim *s, int G, int r0, int r1, const T *pv, const T *dinv, const T *b, T *x,
