@@ -999,9 +999,11 @@ void amg_free(Sim *s) {
   s->l0_lu = false;
   for (void *p : {(void *)s->l0_colp, (void *)s->r0_colp, (void *)s->p0c_rowptr,
                   (void *)s->p0c_col, (void *)s->p0c_src, (void *)s->p0c_val,
-                  (void *)s->p0c_valf, (void *)s->dinv_c, (void *)s->dinv_cf})
+                  (void *)s->p0c_valf, (void *)s->dinv_c, (void *)s->dinv_cf,
+                  (void *)s->scolc, (void *)s->z2c})
     if (p) dfree(s, p);
-  s->l0_colp = s->r0_colp = s->p0c_rowptr = s->p0c_col = s->p0c_src = nullptr;
+  s->l0_colp = s->r0_colp = s->p0c_rowptr = s->p0c_col = s->p0c_src = s->scolc = nullptr;
+  s->z2c = nullptr;
   s->p0c_val = s->dinv_c = nullptr;
   s->p0c_valf = s->dinv_cf = nullptr;
   s->l0c = false;

@@ -368,6 +368,11 @@ struct Sim {
   // matrix rows fall in different colours).
   bool l0c = false;
   int *l0_colp = nullptr;                                 // colour position of each column
+  // the colour positions of the stage operator copy's columns (scol), so
+  // that the FP32 stage residuals gather z1 and z2 in the ILU(0) colour
+  // order (precision >= 1, level 0 in colour order); z2c: z2 in that order
+  int *scolc = nullptr;
+  float *z2c = nullptr;
   int *r0_colp = nullptr;                                 // R0's columns, colour positions
   int *p0c_rowptr = nullptr, *p0c_col = nullptr, *p0c_src = nullptr;  // P0, rows in colour order
   double *p0c_val = nullptr, *dinv_c = nullptr;

@@ -1271,6 +1271,9 @@ static int l0c_setup(Sim *s) {
   if (f32) {
     s->p0c_valf = (float *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 4);
     s->dinv_cf = (float *)dalloc(s, (size_t)n * 4);
+    s->scolc = (int *)dalloc(s, (size_t)std::max(s->K.nnz, 1) * 4);
+    s->z2c = (float *)dalloc(s, (size_t)s->K.n * 8);
+    if (!s->scolc || !s->z2c) { s->fail(DP_ENOMEM, "allocation failed"); return DP_ENOMEM; }
   } else {
     s->p0c_val = (double *)dalloc(s, (size_t)std::max(L.p_nnz, 1) * 8);
     s->dinv_c = (double *)dalloc(s, (size_t)n * 8);
@@ -1284,6 +1287,9 @@ static int l0c_setup(Sim *s) {
             s->l0_colp);
   DP_LAUNCH(s, k_map_copy, nblk(L.r_nnz), kBlock, 0, (long long)L.r_nnz, s->iperm, L.r_col,
             s->r0_colp);
+  if (s->scolc)
+    DP_LAUNCH(s, k_map_copy, nblk(s->K.nnz), kBlock, 0, (long long)s->K.nnz, s->iperm, s->scol,
+              s->scolc);
   DP_LAUNCH(s, k_perm_len, nblk(n), kBlock, 0, n, s->perm, L.p_rowptr, len);
   int pn = 0;
   DP_TRY(scan_i32(s, len, s->p0c_rowptr, n, &pn));
@@ -2319,6 +2325,19 @@ __global__ void k_inject_f32(int n, const float *xp, float *zf, const int *imap)
   k_inject_f32_b(blockIdx.x, gridDim.x, n, xp, zf, imap);
 }
 
+// z2 = z1 + P e in the ILU(0) colour order, FP32: the pressure component
+// of row q gets the level-0 correction of the same position (level 0 runs
+// in that order), the other is z1's; the same sum as k_inject_f32's.
+__global__ void __launch_bounds__(kBlock) k_inject_colour_f32(int n, const float2 *__restrict__ z1,
+                                                              const float *__restrict__ xp,
+                                                              float2 *__restrict__ z2) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  float2 v = z1[q];
+  v.x += xp[q];
+  z2[q] = v;
+}
+
 
 __global__ void k_to_f32(long long n, const double *x, float *y) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2353,13 +2372,20 @@ int cpr_apply(Sim *s, const double *r, double *z) {
   }
   // the stage residuals from the FP32 copy of the operator
   // (z1 and z2 also kept in FP32 for the residuals' gathers; r - A z2 in FP32)
-  // z1 in FP32 only (z1f, natural order): its FP64 value is the colour-order
-  // result itself, kept in s->ilu_zp for the final sum (the second
-  // application writes s->ilu_zp2)
+  // z1 in FP32 only: the colour-order result itself (s->ilu_zp, kept for
+  // the final sum; the second application writes s->ilu_zp2), or, when level
+  // 0 is not in colour order, gathered into natural order (z1f)
   Level &L0 = s->lev[0];
   DP_TRY((ilu_apply_t<float, double>(s, s->lu_valf, r)));
-  DP_TRY(ilu_result<float>(s, nullptr, nullptr, s->z1f));
   const int *m = l0c_on(s) ? s->iperm : nullptr;     // level-0 vectors in colour order
+  // with level 0 in colour order, z1 stays in the ILU(0) colour order: the
+  // stage residuals gather it, and z2, there through the colour positions
+  // of the operator's columns (scolc), so z1 is not gathered into natural
+  // order at all; the products see the same values as from natural order
+  bool cz = m && s->scolc && s->z2c;
+  const float *z1s = cz ? reinterpret_cast<const float *>(s->ilu_zp) : s->z1f;
+  const int *scs = cz ? s->scolc : s->scol;
+  if (!cz) DP_TRY(ilu_result<float>(s, nullptr, nullptr, s->z1f));
   X0Init xi;   // in colour order, the pre-smoothing's start written with b
   if (m) {
     int f = 0;
@@ -2372,12 +2398,19 @@ int cpr_apply(Sim *s, const double *r, double *z) {
     }
   }
   DP_LAUNCH(s, k_bsr_presid_f32, 1 + nblk(s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
-            s->sv_long0, s->srowptr, s->scol, reinterpret_cast<const float2 *>(s->spf), s->z1f,
-            r, L0.bf, m, xi);
+            s->sv_long0, s->srowptr, scs, reinterpret_cast<const float2 *>(s->spf), z1s, r, L0.bf,
+            m, xi);
   DP_TRY(vcycle_t<float>(s, 0, L0.bf, L0.xf, xi.x != nullptr));
-  DP_LAUNCH(s, k_inject_f32, nblk(nb), kBlock, 0, nb, L0.xf, s->z1f, m);
+  const float *z2s = s->z1f;
+  if (cz) {
+    DP_LAUNCH(s, k_inject_colour_f32, nblk(nb), kBlock, 0, nb,
+              reinterpret_cast<const float2 *>(s->ilu_zp), L0.xf, reinterpret_cast<float2 *>(s->z2c));
+    z2s = s->z2c;
+  } else {
+    DP_LAUNCH(s, k_inject_f32, nblk(nb), kBlock, 0, nb, L0.xf, s->z1f, m);
+  }
   DP_LAUNCH(s, k_bsr_resid_f32, 1 + nblk(2LL * s->sv_long0), kBlock, 0, nb, s->sv_sL, s->sv_sc,
-            s->sv_long0, s->srowptr, s->scol, s->svalf, s->z1f, r, s->r1f);
+            s->sv_long0, s->srowptr, scs, s->svalf, z2s, r, s->r1f);
   float *zp2 = reinterpret_cast<float *>(s->ilu_zp2);
   DP_TRY((ilu_apply_t<float, float>(s, s->lu_valf, s->r1f, zp2)));
   // z = z2 + F (r - A z2), z2 = z1 + P e formed here (z1 from the first result)
