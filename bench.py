@@ -92,10 +92,10 @@ def sweep_bytes(nb, nnzb, c0_rows, c0_nnz, first_fused=True):
 
 
 # Sweeps timed as a region (one event pair around the whole sweep) instead
-# of launch by launch: the level-0 Gauss-Seidel's well rows are launched as
-# programmatic dependents of the colour launch before them, which an event
-# between the two launches would prevent.
-SWEEP_REGIONS = {"k_gs_c": "sweep.gs"}
+# of launch by launch: the well rows of the level-0 Gauss-Seidel and of the
+# ILU(0) forward sweep are launched as programmatic dependents of the colour
+# launch before them, which an event between the two launches would prevent.
+SWEEP_REGIONS = {"k_ilu_fwd": "sweep.ilu_fwd", "k_ilu_bwd": "sweep.ilu_bwd", "k_gs_c": "sweep.gs"}
 
 ASSEMBLY_KERNELS = ("k_props", "k_conn_flux", "k_assemble")
 

@@ -466,6 +466,8 @@ int sim_amg_transfer_info(dp_sim *sim, int32_t level, int32_t *p_nnz, int32_t *s
  * events on the simulation stream; NULL stops.  A name with a dot names a
  * region instead, timed from before its first launch to after its last:
  * "sweep.gs", each level-0 Gauss-Seidel sweep in the ILU(0) colour order;
+ * "sweep.ilu_fwd" and "sweep.ilu_bwd", each forward and backward sweep of
+ * an ILU(0) application;
  * "cycle.coarse", the part of each V-cycle below level 0 (its levels 1 and
  * below, between level 0's restriction and prolongation) when level 0 runs
  * in that order.

@@ -144,14 +144,15 @@ struct RegionScope {
 // touches anything the kernel before it writes, and write nothing before
 // it (launch_pdl, after Sim).  cls: kPdlWells, the level-0 well rows;
 // kPdlCoarse, the kernels of the V-cycle's transfers and coarse levels;
-// kPdlL0, level 0's pipelined colour kernels (Gauss-Seidel and residual).
+// kPdlL0, level 0's pipelined colour kernels (Gauss-Seidel and residual);
+// kPdlIluW, the ILU(0) forward sweep's long rows (the wells).
 #define DP_LAUNCH_PDL(sim, cls, name, grid, block, smem, ...)                         \
   do {                                                                               \
     if ((sim)->alloc_failed) break;                                                  \
     ::dp::LaunchScope ls__((sim), #name);                                            \
     ::dp::launch_pdl((sim), (cls), name, dim3(grid), dim3(block), (smem), __VA_ARGS__); \
   } while (0)
-constexpr int kPdlWells = 1, kPdlCoarse = 2, kPdlL0 = 8;
+constexpr int kPdlWells = 1, kPdlCoarse = 2, kPdlL0 = 8, kPdlIluW = 16;
 // Waits until the grids this one depends on have completed and their
 // writes are visible (a no-op in a kernel launched without the attribute).
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_ilu_fwd(int r0, int r1, const int *_
                                                     const int *__restrict__ colp,
                                                     const T *__restrict__ lu,
                                                     const TR *__restrict__ rhs, T *zp) {
+  griddep_launch_dependents();   // the long rows after this colour (k_ilu_fwd_wp)
   k_ilu_fwd_b<T, TR>(blockIdx.x, gridDim.x, r0, r1, perm, Lptr, colp, lu, rhs, zp);
 }
 
@@ -611,6 +612,70 @@ static int tail_grid(int nb) {
   return std::max(1, std::min(nb, slots));
 }
 
+// The same long rows as a programmatic dependent of the colour launch before
+// them (class kPdlIluW), a one-warp CTA per row: the row's pointers, its
+// first 64 L blocks and their columns, its permutation and (PIVOT) its
+// inverted pivot, which no kernel of the solve writes, are loaded before
+// griddep_wait; zp and the right-hand side after it.  The products and
+// their order are k_ilu_fwd_w_b's, so the results are the same bit for bit.
+template <typename T, typename TR, bool PIVOT>
+__global__ void __launch_bounds__(32) k_ilu_fwd_wp(int r0, int nL, const int *__restrict__ perm,
+                                                   const int *__restrict__ Lptr,
+                                                   const int *__restrict__ colp,
+                                                   const T *__restrict__ lu, const TR *rhs,
+                                                   T *zp) {
+  using T2 = typename V2<T>::t;
+  const T2 *z2 = reinterpret_cast<const T2 *>(zp);
+  int r = r0 + (int)blockIdx.x, lane = threadIdx.x;
+  int e = __ldg(Lptr + r) + lane, eb = __ldg(Lptr + r + 1);
+  bool h0 = e < eb, h1 = e + 32 < eb;
+  T a0[4] = {T(0), T(0), T(0), T(0)}, a1[4] = {T(0), T(0), T(0), T(0)}, d[4];
+  int c0 = 0, c1 = 0;
+  if (h0) {
+    V4<T>::load(lu + 4 * (size_t)e, a0);
+    c0 = __ldg(colp + e);
+  }
+  if (h1) {
+    V4<T>::load(lu + 4 * (size_t)(e + 32), a1);
+    c1 = __ldg(colp + e + 32);
+  }
+  int i = lane == 0 ? __ldg(perm + r) : 0;
+  if (PIVOT && lane == 0) V4<T>::load(lu + 4 * ((size_t)nL + r), d);
+  griddep_wait();
+  T s0 = T(0), s1 = T(0);
+  if (h0) {
+    T2 xk = z2[c0];
+    s0 = fma(a0[0], xk.x, fma(a0[1], xk.y, s0));
+    s1 = fma(a0[2], xk.x, fma(a0[3], xk.y, s1));
+  }
+  if (h1) {
+    T2 xk = z2[c1];
+    s0 = fma(a1[0], xk.x, fma(a1[1], xk.y, s0));
+    s1 = fma(a1[2], xk.x, fma(a1[3], xk.y, s1));
+  }
+  for (e += 64; e < eb; e += 32) {
+    T a[4];
+    V4<T>::load(lu + 4 * (size_t)e, a);
+    T2 xk = z2[__ldg(colp + e)];
+    s0 = fma(a[0], xk.x, fma(a[1], xk.y, s0));
+    s1 = fma(a[2], xk.x, fma(a[3], xk.y, s1));
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  if (lane == 0) {
+    T y0 = T(rhs[2 * (size_t)i]) - s0, y1 = T(rhs[2 * (size_t)i + 1]) - s1;
+    if (PIVOT) {
+      y0 = y0 - T(0);   // the backward sweep's y - (sum over no U blocks)
+      y1 = y1 - T(0);
+      zp[2 * (size_t)r] = fma(d[0], y0, d[1] * y1);
+      zp[2 * (size_t)r + 1] = fma(d[2], y0, d[3] * y1);
+    } else {
+      zp[2 * (size_t)r] = y0;
+      zp[2 * (size_t)r + 1] = y1;
+    }
+  }
+}
+
 // (LU)^-1 r with the factor in T and r (natural order) in TR; the result
 // is left in the colour-order work vector s->ilu_zp, from which the caller
 // gathers it (ilu_result) while converting or accumulating.
@@ -618,18 +683,25 @@ template <typename T, typename TR>
 static int ilu_apply_t(Sim *s, const T *lu, const TR *r, T *zpo = nullptr) {
   int n = s->K.n, nL = s->lu_nL, nc = s->ncolour;
   T *zp = zpo ? zpo : reinterpret_cast<T *>(s->ilu_zp);
+  // with kPdlIluW the long rows are a launch of their own, a programmatic
+  // dependent of the colour before them; otherwise that colour's last CTA
+  // takes them (a tail)
+  bool wp = (pdl_mode() & kPdlIluW) != 0;
   // the last colour is solved forward and its pivots applied in one launch:
   // its rows have no U blocks, so that is also the backward sweep's first step
   int last = nc - 1;
   while (last >= 0 && s->lu_cstart[last + 1] <= s->lu_cstart[last]) --last;
   int first = 0;
   while (first < nc && s->lu_cstart[first + 1] <= s->lu_cstart[first]) ++first;
+  {
+  RegionScope region(s, "sweep.ilu_fwd");   // the forward sweep's launches, timed as one
   for (int c = 0; c < nc; ++c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;
     int nx = c + 1;   // the next non-empty colour
     while (nx < nc && s->lu_cstart[nx + 1] <= s->lu_cstart[nx]) ++nx;
-    if (c != first && s->lu_cmaxlen[c] <= kLongRow && nx < nc && s->lu_cmaxlen[nx] > kLongRow) {
+    if (!wp && c != first && s->lu_cmaxlen[c] <= kLongRow && nx < nc &&
+        s->lu_cmaxlen[nx] > kLongRow) {
       // a short colour followed by a long one: its last CTA takes the long rows
       Tail tl;
       tl.w0 = s->lu_cstart[nx];
@@ -645,7 +717,14 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r, T *zpo = nullptr) {
       c = nx;
       continue;
     }
-    if (c == last && s->lu_cmaxlen[c] > kLongRow)
+    if (wp && c != first && s->lu_cmaxlen[c] > kLongRow) {
+      if (c == last)
+        DP_LAUNCH_PDL(s, kPdlIluW, (k_ilu_fwd_wp<T, TR, true>), r1 - r0, 32, 0, r0, nL, s->perm,
+                      s->lu_Lptr, s->lu_colp, lu, r, zp);
+      else
+        DP_LAUNCH_PDL(s, kPdlIluW, (k_ilu_fwd_wp<T, TR, false>), r1 - r0, 32, 0, r0, nL, s->perm,
+                      s->lu_Lptr, s->lu_colp, lu, r, zp);
+    } else if (c == last && s->lu_cmaxlen[c] > kLongRow)
       DP_LAUNCH(s, (k_ilu_fwd_w<T, TR, true>), nblk(32LL * (r1 - r0)), kBlock, 0, r0, r1, nL,
                 s->perm, s->lu_Lptr, s->lu_colp, lu, r, zp);
     else if (s->lu_cmaxlen[c] > kLongRow)
@@ -658,6 +737,8 @@ static int ilu_apply_t(Sim *s, const T *lu, const TR *r, T *zpo = nullptr) {
       DP_LAUNCH(s, (k_ilu_fwd<T, TR>), nblk(2LL * (r1 - r0)), kBlock, 0, r0, r1, s->perm,
                 s->lu_Lptr, s->lu_colp, lu, r, zp);
   }
+  }
+  RegionScope region(s, "sweep.ilu_bwd");   // the backward sweep's launches, timed as one
   for (int c = nc - 1; c >= 0; --c) {
     int r0 = s->lu_cstart[c], r1 = s->lu_cstart[c + 1];
     if (r1 <= r0) continue;

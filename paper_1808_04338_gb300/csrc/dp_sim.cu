@@ -116,7 +116,7 @@ int pdl_mode() {
     const char *v = std::getenv("DPSIM_PDL");
     char *end = nullptr;
     long m = v ? std::strtol(v, &end, 10) : -1;
-    return v && *v && end && !*end && m >= 0 && m <= 15 ? (int)m : 15;
+    return v && *v && end && !*end && m >= 0 && m <= 31 ? (int)m : 31;
   }();
   return mode;
 }

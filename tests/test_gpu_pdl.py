@@ -1,11 +1,12 @@
 """Programmatic dependent launches (the level-0 well rows, level 0's
-pipelined colour kernels, the V-cycle below level 0 and its transfers)
-change when a kernel may start, never what it computes: two timesteps of a
-field in the bench's options (report mode, FP32 preconditioner, the
-pipelined level-0 kernel) end in the same state bit for bit with every
-class of them (DPSIM_PDL=15, the default) and with none (DPSIM_PDL=0), and
-with the early trigger off (DPSIM_PDL=11).  DPSIM_PDL is read once per
-process, so each setting runs in a child process of its own."""
+pipelined colour kernels, the V-cycle below level 0 and its transfers, the
+ILU(0) forward sweep's well rows) change when a kernel may start, never
+what it computes: two timesteps of a field in the bench's options (report
+mode, FP32 preconditioner, the pipelined level-0 kernel) end in the same
+state bit for bit with every class of them (DPSIM_PDL=31, the default),
+with none (0), with the early trigger off (27) and with the ILU(0) forward
+wells in the colour launch's last CTA instead (15).  DPSIM_PDL is read once
+per process, so each setting runs in a child process of its own."""
 import os
 import subprocess
 import sys
@@ -45,9 +46,9 @@ def run_child(mode, out):
 
 
 def test_dependent_launches_change_no_result(tmp_path):
-    res = {m: run_child(m, str(tmp_path / f"pdl{m}.npz")) for m in (15, 0, 11)}
-    assert int(res[15]["nlev"]) >= 3   # coarse levels below level 0 exist
-    for m in (0, 11):
+    res = {m: run_child(m, str(tmp_path / f"pdl{m}.npz")) for m in (31, 0, 27, 15)}
+    assert int(res[31]["nlev"]) >= 3   # coarse levels below level 0 exist
+    for m in (0, 27, 15):
         for k in ("p", "sw", "bhp"):
-            assert np.array_equal(res[m][k], res[15][k]), (m, k)
-        assert int(res[m]["its"]) == int(res[15]["its"])
+            assert np.array_equal(res[m][k], res[31][k]), (m, k)
+        assert int(res[m]["its"]) == int(res[31]["its"])
