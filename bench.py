@@ -34,9 +34,9 @@ UNIT = "Newton-step solves/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TIMED_KERNEL = "k_bsr_spmv<0>"
 # DRAM bytes (read + written) per launch of TIMED_KERNEL on the 200x200x50 field: one
-# launch captured on the 200x200x20 field (316,643,072 + 21,299,968 bytes against its
-# 342,181,804 algorithmic bytes, profiles/bsr_spmv_field200x200x20_dram.md), scaled by the
-# algorithmic bytes of a 200x200x50 launch (859,771,804): the kernel streams every block
+# launch captured with ncu on the 200x200x20 field (316,643,072 + 21,299,968 bytes against
+# its 342,181,804 algorithmic bytes; the capture's summary is kept under profiles/), scaled by
+# the algorithmic bytes of a 200x200x50 launch (859,771,804): the kernel streams every block
 # once, so its traffic grows with them
 TIMED_TRAFFIC = {(200, 200, 50, 0): round((316643072 + 21299968) * 859771804 / 342181804)}
 
