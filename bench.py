@@ -66,6 +66,22 @@ def spmv_bytes(nb, nnzb):
     return 32 * nnzb + 4 * nnzb + 4 * (nb + 1) + 16 * nb + 16 * nb
 
 
+# GB300's FP64 rate: 1.20 TFLOP/s, measured on this machine's GB300 with independent FMA
+# chains on every SM (the nominal figure is 1.25)
+FP64_TFLOPS = 1.20
+
+
+def spmv_fp64(nnzb, ms_per_launch):
+    """The FP64 side of the product's roofline: four FMAs (8 flops) per 2x2
+    block, against GB300's FP64 rate; the product is bound by HBM and by the
+    FP64 pipe together."""
+    flops = 8 * nnzb
+    tf = flops / (ms_per_launch / 1000.0) / 1e12
+    return {"flops_per_launch": flops, "achieved_tflops": tf, "peak_tflops": FP64_TFLOPS,
+            "frac": tf / FP64_TFLOPS,
+            "peak_source": "FP64 FMA microbenchmark (independent chains, all SMs)"}
+
+
 def sweep_bytes(nb, nnzb, c0_rows, c0_nnz, first_fused=True):
     """Algorithmic bytes of one full sweep (all colours) of the FP32 ILU(0)
     forward and backward solves and of one level-0 Gauss-Seidel sweep.  The
@@ -1003,7 +1019,8 @@ def main():
                          "traffic": TIMED_TRAFFIC.get((args.nx, args.ny, args.nz, args.schur)),
                          "launches_timed": k_n,
                          "avg_launch_ms": (k_ms / k_n) if k_n else None,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback",
+                         "fp64": spmv_fp64(sim.snnzb, k_ms / k_n) if k_n else None},
             "sweeps": {k: dict(v, frac=v["achieved_gbs"] / peak) for k, v in sweeps.items()},
             "assembly": dict(assembly, frac=assembly["achieved_gbs"] / peak)
                         if "achieved_gbs" in assembly else assembly,

@@ -72,3 +72,10 @@ def test_coarse_cycle_bytes_by_hand(bench):
 
 def test_assembly_bytes_by_hand(bench):
     assert bench.assembly_bytes(5, 13, 4) == 44 * 13 + 56 * 4 + 24 * 5
+
+
+def test_spmv_fp64_side(bench):
+    r = bench.spmv_fp64(19882525, 0.1515)
+    assert r["flops_per_launch"] == 8 * 19882525
+    assert abs(r["achieved_tflops"] - 8 * 19882525 / 0.1515e-3 / 1e12) < 1e-12
+    assert 0.8 < r["frac"] < 0.95
