@@ -178,6 +178,17 @@ typedef struct {
 
 typedef struct dp_sim dp_sim;
 
+/* Launch scheduling (no counterpart in the paper): the short, latency-bound
+ * kernels of a solve (the well rows of level 0's Gauss-Seidel and of the
+ * ILU(0) forward sweep, level 0's pipelined colour kernels, the V-cycle below
+ * level 0 and its transfers) are launched as programmatic dependents of the
+ * kernel before them on the stream, so that their launch and the loads that
+ * do not depend on that kernel overlap its end.  The environment variable
+ * DPSIM_PDL, read once per process, is a bit mask of the classes to launch
+ * that way (1 level-0 well rows, 2 the V-cycle below level 0, 4 the latter
+ * letting their own dependents in early, 8 level 0's colour kernels, 16 the
+ * ILU(0) forward well rows; default 31, all); results do not depend on it. */
+
 /* Create a realisation: copies grid, rock, fluid and wells, computes the
  * well indices (Peaceman's radius for a vertical well, Section 2), builds
  * the block pattern (fracture 7-point stencil, fracture-matrix pairs, well
